@@ -1,0 +1,154 @@
+/*
+ * librbf -- compactly supported RBF least-squares surface approximation of
+ * scattered 2.5-D data on one GB300 (sm_103a).
+ *
+ * Method (Majdisova & Skala, "Big Geo Data Surface Approximation using Radial
+ * Basis Functions: A Comparative Study"):
+ *   f(x) = sum_{j=1..M} c_j phi(||x - xi_j|| / R)                    (Eq. 3)
+ *   A_ij = phi(||x_i - xi_j|| / R),  N x M, N >> M,  A c ~= h       (Eq. 4-5)
+ *   c solves the normal equations  B c = b,  B = A^T A,  b = A^T h   (Section 2, Eq. 11-12)
+ *   phi is a Wendland function of Table 2 (cut-off of Eq. 18), R = 1/alpha.
+ *
+ * Pipeline and entry points:
+ *   rbf_bin        bin centres and points into a uniform grid of cell size R
+ *                  (replaces the kd-tree range query of Algorithm 1)
+ *   rbf_assemble   evaluate each point's sparse row of A and accumulate the
+ *                  upper triangle of B and b in one fused pass (Eq. 11-13);
+ *                  A is never stored
+ *   rbf_solve      Jacobi-preconditioned CG on B c = b (FP64), or FP32 CG inside
+ *                  FP64 iterative refinement with a matrix-free FP64 residual
+ *   rbf_eval       f at arbitrary query points (Eq. 3); rbf_eval_grid on a grid
+ *
+ * Conventions (all entry points):
+ *   - Array arguments are DEVICE pointers owned by the caller unless stated
+ *     otherwise; they must stay valid until the work on `stream` completes.
+ *     `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *   - Calls are asynchronous on `stream` except where a result must come back
+ *     to the host (rbf_bin, rbf_solve): those synchronise `stream` before return.
+ *   - Errors are returned as rbf_status; no exception crosses this boundary.
+ *     rbf_last_error(ctx) gives a message for the last failure on that context.
+ *   - Device-side failures (CG breakdown, non-convergence) are reported through
+ *     the status of rbf_solve; no kernel traps.
+ *   - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef RBF_H_
+#define RBF_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RBF_OK = 0,
+    RBF_ERR_ARG = 1,            /* invalid argument (size, pointer, NaN, order of calls) */
+    RBF_ERR_ALLOC = 2,          /* workspace allocation failed */
+    RBF_ERR_CUDA = 3,           /* a CUDA runtime call failed */
+    RBF_ERR_NOT_CONVERGED = 4,  /* solver hit maxit before reaching tol */
+    RBF_ERR_BREAKDOWN = 5,      /* CG breakdown: p^T B p <= 0 or a non-finite scalar */
+    RBF_ERR_LIMIT = 6           /* input exceeds a documented kernel limit */
+} rbf_status;
+
+/* Wendland functions phi_{3,s}(r), r = ||x - xi|| / R, zero for r >= 1 (Table 2, Eq. 18).
+ * RBF_W32 is not in Table 2: it is (1-r)^6 (35 r^2 + 18 r + 3) / 3, scaled so phi(0) = 1. */
+typedef enum { RBF_W30 = 0, RBF_W31 = 1, RBF_W32 = 2, RBF_W33 = 3 } rbf_kernel;
+
+/* Arithmetic of the assembled matrix and of the CG iterations. */
+typedef enum {
+    RBF_FP64 = 0,          /* B, b and CG in FP64 */
+    RBF_FP32_REFINE = 1    /* B and inner CG in FP32 (FP32 accumulation); FP64 matrix-free
+                              residual A^T (h - A c) and FP64 correction updates of c */
+} rbf_prec;
+
+typedef struct rbf_ctx rbf_ctx;
+
+/* Workspace allocator. alloc returns a device pointer of at least `bytes` bytes usable on
+ * `stream` (NULL on failure); free releases it. user is passed through. When both are NULL
+ * the library uses cudaMalloc / cudaFree. */
+typedef void* (*rbf_alloc_fn)(size_t bytes, void* stream, void* user);
+typedef void (*rbf_free_fn)(void* ptr, size_t bytes, void* stream, void* user);
+
+/* Result of rbf_solve. */
+typedef struct {
+    int iterations;          /* total CG iterations (inner iterations for RBF_FP32_REFINE) */
+    int refinements;         /* outer FP64 refinement steps (0 for RBF_FP64) */
+    double rel_residual;     /* ||b - B c||_2 / ||b||_2 at exit, over unpinned centres.
+                                For RBF_FP32_REFINE this is the FP64 matrix-free
+                                ||A^T(h - A c)||_2 / ||A^T h||_2 */
+    int64_t pinned;          /* centres with fewer than min_support points in support */
+} rbf_solve_info;
+
+/* Create / destroy a context bound to CUDA device `device`. */
+rbf_status rbf_create(rbf_ctx** out, int device, rbf_alloc_fn alloc, rbf_free_fn free_fn,
+                      void* user);
+rbf_status rbf_destroy(rbf_ctx* ctx);
+const char* rbf_last_error(const rbf_ctx* ctx);
+
+/* Step (a): bin M centres (cx, cy) and N points (px, py) with heights h into a uniform
+ * grid of cell side R (plus a 2^-30 relative margin) over bbox = {x0, y0, x1, y1}
+ * (HOST array of 4 doubles). Items outside bbox are clamped to the edge cells, which
+ * stays correct. The context keeps cell-sorted copies of the inputs and the permutation
+ * back to the caller's centre order, and sizes the block-sparse B (Section 5: symmetric,
+ * only the upper triangle stored, in cell-pair blocks). Requires M >= 1, N >= 1, R > 0,
+ * finite coordinates and heights. Synchronises `stream`.
+ * Returns RBF_ERR_LIMIT if some 3x3 cell neighbourhood holds more than
+ * rbf_max_candidates() centres. */
+rbf_status rbf_bin(rbf_ctx* ctx, const double* cx, const double* cy, int64_t M,
+                   const double* px, const double* py, const double* h, int64_t N,
+                   double R, const double* bbox, void* stream);
+
+/* Largest number of centres in one 3x3 cell neighbourhood that rbf_bin accepts. */
+int rbf_max_candidates(void);
+
+/* Steps (b)+(c): one fused pass over the binned points computes every nonzero
+ * A_ij = phi(||x_i - xi_j|| / R) (Algorithm 1 semantics: a pair counts iff
+ * ||x_i - xi_j|| < R) and accumulates B = A^T A (upper triangle, Eq. 11-13) and b = A^T h
+ * (Section 2) in the precision `prec`; also counts the data points inside each support.
+ * Asynchronous. Requires a preceding rbf_bin. */
+rbf_status rbf_assemble(rbf_ctx* ctx, rbf_kernel kernel, rbf_prec prec, void* stream);
+
+/* Step (d): solve B c = b (Section 2) by Jacobi-preconditioned CG.
+ * c       : device array of M doubles in the caller's centre order; on entry the
+ *           starting guess if use_c0 != 0 (else ignored), on exit the weights.
+ * tol     : stop when the relative residual (see rbf_solve_info) <= tol.
+ * maxit   : iteration limit (for RBF_FP32_REFINE: per inner solve; at most 30 outer steps).
+ * min_support: centres whose support disc holds fewer data points are removed from
+ *           the system and get c_j = 0 (the paper leaves empty supports undefined).
+ * info    : HOST pointer, may be NULL.
+ * Synchronises `stream`. Returns RBF_ERR_NOT_CONVERGED / RBF_ERR_BREAKDOWN with c
+ * holding the last iterate. */
+rbf_status rbf_solve(rbf_ctx* ctx, double* c, int use_c0, double tol, int maxit,
+                     int min_support, rbf_solve_info* info, void* stream);
+
+/* Step (e): f(q) = sum_j c_j phi(||q - xi_j|| / R) (Eq. 3) at Q query points.
+ * c: device, M doubles in the caller's centre order; qx, qy: device, Q doubles;
+ * f: device, Q doubles (output). Uses the centres binned by the last rbf_bin and
+ * the kernel of the last rbf_assemble. Asynchronous. */
+rbf_status rbf_eval(rbf_ctx* ctx, const double* c, const double* qx, const double* qy,
+                    int64_t Q, double* f, void* stream);
+
+/* Step (e) on the node-centred nx x ny grid over box = {x0, y0, x1, y1} (HOST array):
+ * node (i, j) = (x0 + j (x1-x0)/(nx-1), y0 + i (y1-y0)/(ny-1)); f is a device array of
+ * nx*ny doubles, row-major f[i*nx + j]. Asynchronous. */
+rbf_status rbf_eval_grid(rbf_ctx* ctx, const double* c, int nx, int ny, const double* box,
+                         double* f, void* stream);
+
+/* Diagnostics: number of stored B values (upper cell-pair blocks) and bytes per value
+ * of the last assembly; sizes of the cell grid. HOST outputs, any may be NULL. */
+rbf_status rbf_get_layout(const rbf_ctx* ctx, int64_t* nvals, int* value_bytes, int* gx,
+                          int* gy);
+
+/* Diagnostics: copy the assembled B as COO triplets (upper triangle incl. diagonal,
+ * caller's centre indices) into DEVICE arrays of capacity cap; *nnz gets the count.
+ * Entries that are exactly zero are skipped. Synchronises `stream`. */
+rbf_status rbf_export_upper(rbf_ctx* ctx, int64_t cap, int32_t* row, int32_t* col,
+                            double* val, double* bvec, int32_t* support, int64_t* nnz,
+                            void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RBF_H_ */

@@ -40,7 +40,7 @@ __all__ = [
     "phi", "pairs_bruteforce", "pairs_kdtree", "design_matrix", "normal_system",
     "normal_system_blocked", "support_counts", "pinned_mask", "solve_normal",
     "solve_lstsq_qr", "pcg", "evaluate", "evaluate_grid", "fit", "normal_residual",
-    "coo_spmv", "rel_err", "error_measures",
+    "coo_spmv", "rel_err", "error_measures", "SampledOracle",
 ]
 
 _KINDS = ("w30", "w31", "w32", "w33")
@@ -306,3 +306,68 @@ def error_measures(f_approx, f_true):
     rng = float(np.max(f_true) - np.min(f_true))
     return dict(mae=float(np.mean(np.abs(e))), var=float(np.var(e)), std=float(np.std(e)),
                 mre_range=float(np.mean(np.abs(e)) / rng) if rng > 0 else float("nan"))
+
+
+# ----------------------------------------------------------------------------
+# sampled quantities at sizes where the whole system is too large for the CPU
+# ----------------------------------------------------------------------------
+
+class SampledOracle:
+    """Entries of A, B = A^T A, b = A^T h, the normal residual and f, computed one by one
+    from their definitions (Eq. 3-5, 11-12) with kd-tree range queries."""
+
+    def __init__(self, P, h, C, R, kind="w31"):
+        self.P = np.asarray(P, np.float64)
+        self.h = np.asarray(h, np.float64)
+        self.C = np.asarray(C, np.float64)
+        self.R = float(R)
+        self.kind = kind
+        self.tp = cKDTree(self.P)
+        self.tc = cKDTree(self.C)
+
+    def _near(self, tree, X, q):
+        idx = np.asarray(tree.query_ball_point(q, self.R * (1.0 + 1e-9)), dtype=np.int64)
+        if idx.size == 0:
+            return idx, np.zeros(0)
+        dx = X[idx, 0] - q[0]
+        dy = X[idx, 1] - q[1]
+        r = np.sqrt(dx * dx + dy * dy) / self.R
+        keep = r < 1.0
+        return idx[keep], r[keep]
+
+    def row(self, i):
+        """Nonzeros of row i of A: (centre indices, values)."""
+        j, r = self._near(self.tc, self.C, self.P[i])
+        return j, phi(r, self.kind)
+
+    def column(self, j):
+        """Nonzeros of column j of A: (point indices, values)."""
+        i, r = self._near(self.tp, self.P, self.C[j])
+        return i, phi(r, self.kind)
+
+    def B_entry(self, j, k):
+        ij, vj = self.column(j)
+        ik, vk = self.column(k)
+        common, aj, ak = np.intersect1d(ij, ik, assume_unique=True, return_indices=True)
+        return float(np.sum(vj[aj] * vk[ak]))
+
+    def b_entry(self, j):
+        i, v = self.column(j)
+        return float(np.sum(v * self.h[i]))
+
+    def support(self, j):
+        return int(self.column(j)[0].size)
+
+    def normal_residual(self, c, j):
+        """(A^T (h - A c))_j."""
+        i, v = self.column(j)
+        e = np.empty(i.size)
+        for t, ii in enumerate(i):
+            jj, vv = self.row(ii)
+            e[t] = self.h[ii] - np.sum(vv * c[jj])
+        return float(np.sum(v * e))
+
+    def f(self, c, q):
+        """f(q) = sum_j c_j phi(||q - xi_j|| / R)."""
+        j, r = self._near(self.tc, self.C, np.asarray(q, np.float64))
+        return float(np.sum(np.asarray(c)[j] * phi(r, self.kind)))

@@ -1,0 +1,202 @@
+"""GB300-native compactly supported RBF least-squares surface approximation.
+
+A thin Python layer over the C-ABI library librbf (include/rbf.h). PyTorch supplies
+device memory (through the caching allocator, wired in as librbf's workspace
+allocator) and streams; every step of the method runs in the library's CUDA kernels:
+
+    ctx = Context()
+    ctx.bin(centres, points, h, R, bbox)      # step (a): uniform cell grid of side R
+    ctx.assemble("w31", "fp64")               # steps (b)+(c): B = A^T A, b = A^T h (Eq. 11-12)
+    c, info = ctx.solve(tol=1e-10)            # step (d): Jacobi-PCG (+ FP64 refinement)
+    f = ctx.eval_grid(c, 256, 256)            # step (e): f = sum_j c_j phi(|x - xi_j| / R) (Eq. 3)
+
+``fit`` runs the whole path in one call. Coordinates, heights and weights are float64.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+from . import _lib
+from ._lib import KERNELS, PRECS, RBFError
+
+__all__ = ["Context", "fit", "RBFError", "KERNELS", "PRECS", "max_candidates"]
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def max_candidates() -> int:
+    return int(_lib.load().rbf_max_candidates())
+
+
+def _dptr(t, name):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or t.device.type != "cuda":
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.float64:
+        raise TypeError(f"{name} must be float64")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return C.c_void_p(t.data_ptr())
+
+
+class Context:
+    """One librbf context on one CUDA device (not thread-safe)."""
+
+    def __init__(self, device: int = 0, torch_allocator: bool = True):
+        torch = _torch()
+        self.lib = _lib.load()
+        self.device = int(device)
+        if torch_allocator:
+            dev = self.device
+
+            def _alloc(nbytes, stream, user):
+                try:
+                    return torch.cuda.caching_allocator_alloc(int(nbytes), dev, int(stream or 0))
+                except Exception:       # out of memory: the library reports RBF_ERR_ALLOC
+                    return None
+
+            def _free(ptr, nbytes, stream, user):
+                torch.cuda.caching_allocator_delete(int(ptr))
+
+            self._alloc = _lib.ALLOC_FN(_alloc)
+            self._free = _lib.FREE_FN(_free)
+        else:
+            self._alloc = C.cast(None, _lib.ALLOC_FN)
+            self._free = C.cast(None, _lib.FREE_FN)
+        h = C.c_void_p()
+        s = self.lib.rbf_create(C.byref(h), self.device, self._alloc, self._free, None)
+        if s != 0:
+            raise RBFError(s, "rbf_create failed")
+        self._h = h
+        self.M = self.N = 0
+        self.kernel = None
+        self.prec = None
+
+    # -- plumbing ---------------------------------------------------------------------
+    def _check(self, status: int, what: str):
+        if status != 0:
+            msg = self.lib.rbf_last_error(self._h)
+            raise RBFError(status, f"{what}: {msg.decode() if msg else ''}")
+
+    def _stream(self, stream):
+        torch = _torch()
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        return C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self.lib.rbf_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- steps --------------------------------------------------------------------------
+    def bin(self, cx, cy, px, py, h, R: float, bbox=(0.0, 0.0, 1.0, 1.0), stream=None):
+        """Step (a). cx, cy: M centre coordinates; px, py, h: N points and heights (CUDA float64)."""
+        M, N = int(cx.numel()), int(px.numel())
+        box = (C.c_double * 4)(*[float(v) for v in bbox])
+        s = self.lib.rbf_bin(self._h, _dptr(cx, "cx"), _dptr(cy, "cy"), M, _dptr(px, "px"),
+                             _dptr(py, "py"), _dptr(h, "h"), N, float(R), box,
+                             self._stream(stream))
+        self._check(s, "rbf_bin")
+        self.M, self.N = M, N
+
+    def assemble(self, kernel: str = "w31", prec: str = "fp64", stream=None):
+        """Steps (b)+(c): fused rows of A and B = A^T A, b = A^T h."""
+        s = self.lib.rbf_assemble(self._h, KERNELS[kernel], PRECS[prec], self._stream(stream))
+        self._check(s, "rbf_assemble")
+        self.kernel, self.prec = kernel, prec
+
+    def solve(self, tol: float = 1e-10, maxit: int = 100000, min_support: int = 3, c0=None,
+              out=None, stream=None, raise_on_fail: bool = True):
+        """Step (d): returns (c, info). c0: optional warm start (CUDA float64, length M)."""
+        torch = _torch()
+        c = out if out is not None else torch.empty(self.M, dtype=torch.float64,
+                                                    device=f"cuda:{self.device}")
+        if c0 is not None and c0.data_ptr() != c.data_ptr():
+            c.copy_(c0)
+        info = _lib.SolveInfo()
+        s = self.lib.rbf_solve(self._h, _dptr(c, "c"), 1 if c0 is not None else 0, float(tol),
+                               int(maxit), int(min_support), C.byref(info), self._stream(stream))
+        d = dict(iterations=info.iterations, refinements=info.refinements,
+                 rel_residual=info.rel_residual, pinned=info.pinned, status=s)
+        if s != 0 and raise_on_fail:
+            self._check(s, "rbf_solve")
+        return c, d
+
+    def eval(self, c, qx, qy, out=None, stream=None):
+        """Step (e) at query points."""
+        torch = _torch()
+        Q = int(qx.numel())
+        f = out if out is not None else torch.empty(Q, dtype=torch.float64, device=qx.device)
+        s = self.lib.rbf_eval(self._h, _dptr(c, "c"), _dptr(qx, "qx"), _dptr(qy, "qy"), Q,
+                              _dptr(f, "f"), self._stream(stream))
+        self._check(s, "rbf_eval")
+        return f
+
+    def eval_grid(self, c, nx: int, ny: int, box=(0.0, 0.0, 1.0, 1.0), out=None, stream=None):
+        """Step (e) on the node-centred nx x ny grid; returns f with shape (ny, nx)."""
+        torch = _torch()
+        f = out if out is not None else torch.empty((ny, nx), dtype=torch.float64, device=c.device)
+        b = (C.c_double * 4)(*[float(v) for v in box])
+        s = self.lib.rbf_eval_grid(self._h, _dptr(c, "c"), int(nx), int(ny), b, _dptr(f, "f"),
+                                   self._stream(stream))
+        self._check(s, "rbf_eval_grid")
+        return f
+
+    # -- diagnostics --------------------------------------------------------------------
+    def layout(self):
+        nv, vb, gx, gy = C.c_int64(), C.c_int(), C.c_int(), C.c_int()
+        self._check(self.lib.rbf_get_layout(self._h, C.byref(nv), C.byref(vb), C.byref(gx),
+                                            C.byref(gy)), "rbf_get_layout")
+        return dict(nvals=nv.value, value_bytes=vb.value, gx=gx.value, gy=gy.value)
+
+    def export_upper(self, stream=None):
+        """The assembled upper triangle of B as COO (caller's centre indices), plus b and the
+        support counts, as CUDA tensors."""
+        torch = _torch()
+        dev = f"cuda:{self.device}"
+        cap = self.layout()["nvals"]
+        row = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
+        col = torch.empty_like(row)
+        val = torch.empty(max(cap, 1), dtype=torch.float64, device=dev)
+        b = torch.empty(self.M, dtype=torch.float64, device=dev)
+        sup = torch.empty(self.M, dtype=torch.int32, device=dev)
+        nnz = C.c_int64()
+        s = self.lib.rbf_export_upper(self._h, cap, C.c_void_p(row.data_ptr()),
+                                      C.c_void_p(col.data_ptr()), C.c_void_p(val.data_ptr()),
+                                      C.c_void_p(b.data_ptr()), C.c_void_p(sup.data_ptr()),
+                                      C.byref(nnz), self._stream(stream))
+        self._check(s, "rbf_export_upper")
+        n = nnz.value
+        return row[:n], col[:n], val[:n], b, sup
+
+
+def fit(points, h, centres, R: float, kernel: str = "w31", prec: str = "fp64",
+        bbox=(0.0, 0.0, 1.0, 1.0), tol: float = 1e-10, maxit: int = 200000, min_support: int = 3,
+        c0=None, ctx: Context | None = None, device: int = 0):
+    """Whole fit. points (N,2), h (N,), centres (M,2): torch tensors or numpy arrays (host
+    inputs are copied to the device). Returns (c on the device, info dict, ctx)."""
+    torch = _torch()
+    dev = f"cuda:{device}"
+
+    def dev64(a):
+        t = a if isinstance(a, torch.Tensor) else torch.as_tensor(a)
+        return t.to(device=dev, dtype=torch.float64, non_blocking=True)
+
+    P, H, Cc = dev64(points), dev64(h), dev64(centres)
+    ctx = ctx or Context(device)
+    ctx.bin(Cc[:, 0].contiguous(), Cc[:, 1].contiguous(), P[:, 0].contiguous(),
+            P[:, 1].contiguous(), H.contiguous(), R, bbox)
+    ctx.assemble(kernel, prec)
+    c, info = ctx.solve(tol=tol, maxit=maxit, min_support=min_support,
+                        c0=None if c0 is None else dev64(c0))
+    return c, info, ctx

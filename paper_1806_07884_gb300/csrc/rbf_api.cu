@@ -1,0 +1,260 @@
+// C-ABI entry points of librbf (declared in include/rbf.h): argument checks, context
+// and workspace management; the work itself is done by the kernels of the other units.
+#include <math.h>
+#include <stdio.h>
+
+#include <algorithm>
+#include <new>
+
+#include "rbf_internal.h"
+
+namespace rbf {
+
+rbf_status set_err(rbf_ctx* ctx, rbf_status s, const char* msg) {
+    if (ctx) ctx->err = msg;
+    return s;
+}
+
+rbf_status cuda_fail(rbf_ctx* ctx, cudaError_t e, const char* what, const char* file, int line) {
+    char buf[512];
+    snprintf(buf, sizeof(buf), "CUDA error %s (%s) in %s at %s:%d", cudaGetErrorName(e),
+             cudaGetErrorString(e), what, file, line);
+    if (ctx) ctx->err = buf;
+    return RBF_ERR_CUDA;
+}
+
+void release(rbf_ctx* ctx, rbf_buf& b) {
+    if (!b.p) return;
+    if (ctx->free_fn)
+        ctx->free_fn(b.p, b.bytes, nullptr, ctx->user);
+    else
+        cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+rbf_status ensure(rbf_ctx* ctx, rbf_buf& b, size_t bytes, cudaStream_t st) {
+    bytes = std::max<size_t>(bytes, 256);
+    if (b.p && b.bytes >= bytes) return RBF_OK;
+    if (b.p) {
+        // the old buffer may still be read by queued work on this stream
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamSynchronize", __FILE__, __LINE__);
+        release(ctx, b);
+    }
+    // round up to limit reallocations when sizes grow slowly
+    const size_t want = bytes + bytes / 8;
+    void* p = nullptr;
+    if (ctx->alloc) {
+        p = ctx->alloc(want, st, ctx->user);
+    } else if (cudaMalloc(&p, want) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (!p) return set_err(ctx, RBF_ERR_ALLOC, "workspace allocation failed");
+    b.p = p;
+    b.bytes = want;
+    return RBF_OK;
+}
+
+Binned view(const rbf_ctx* ctx) {
+    Binned v;
+    v.g = ctx->g;
+    v.M = ctx->M;
+    v.N = ctx->N;
+    v.cstart = ctx->cstart.as<int>();
+    v.pstart = ctx->pstart.as<int>();
+    v.cx = ctx->cx.as<double>();
+    v.cy = ctx->cy.as<double>();
+    v.cu = ctx->cu.as<float>();
+    v.cv = ctx->cv.as<float>();
+    v.px = ctx->px.as<double>();
+    v.py = ctx->py.as<double>();
+    v.ph = ctx->ph.as<double>();
+    v.pu = ctx->pu.as<float>();
+    v.pv = ctx->pv.as<float>();
+    v.cperm = ctx->cperm.as<int>();
+    v.seg = ctx->seg.as<RowSeg>();
+    v.rboff = ctx->rboff.as<int64_t>();
+    return v;
+}
+
+}  // namespace rbf
+
+using namespace rbf;
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+inline cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
+
+}  // namespace
+
+extern "C" {
+
+rbf_status rbf_create(rbf_ctx** out, int device, rbf_alloc_fn alloc, rbf_free_fn free_fn,
+                      void* user) {
+    if (!out) return RBF_ERR_ARG;
+    *out = nullptr;
+    if ((alloc == nullptr) != (free_fn == nullptr)) return RBF_ERR_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return RBF_ERR_CUDA;
+    }
+    rbf_ctx* ctx = new (std::nothrow) rbf_ctx();
+    if (!ctx) return RBF_ERR_ALLOC;
+    ctx->device = device;
+    ctx->alloc = alloc;
+    ctx->free_fn = free_fn;
+    ctx->user = user;
+    DeviceGuard dg(device);
+    if (cudaMallocHost(&ctx->hpinned, 4096) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        if (ctx->hpinned) cudaFreeHost(ctx->hpinned);
+        delete ctx;
+        return RBF_ERR_CUDA;
+    }
+    *out = ctx;
+    return RBF_OK;
+}
+
+rbf_status rbf_destroy(rbf_ctx* ctx) {
+    if (!ctx) return RBF_ERR_ARG;
+    DeviceGuard dg(ctx->device);
+    cudaDeviceSynchronize();
+    for (auto& row : ctx->graphs)
+        for (auto& gc : row)
+            if (gc.exec) cudaGraphExecDestroy(gc.exec);
+    rbf_buf* bufs[] = {&ctx->ccount, &ctx->pcount, &ctx->cstart, &ctx->pstart, &ctx->ckey,
+                       &ctx->crank, &ctx->pkey, &ctx->prank, &ctx->cx, &ctx->cy, &ctx->cu,
+                       &ctx->cv, &ctx->cperm, &ctx->px, &ctx->py, &ctx->ph, &ctx->pu, &ctx->pv,
+                       &ctx->seg, &ctx->rbsize, &ctx->rboff, &ctx->wcount, &ctx->wstart,
+                       &ctx->work, &ctx->scan_tmp, &ctx->stats, &ctx->bvals, &ctx->bvec,
+                       &ctx->support, &ctx->x, &ctx->r, &ctx->z, &ctx->p, &ctx->q, &ctx->dinv,
+                       &ctx->x32, &ctx->r32, &ctx->z32, &ctx->p32, &ctx->q32, &ctx->dinv32,
+                       &ctx->partial, &ctx->scal, &ctx->csort};
+    for (rbf_buf* b : bufs) release(ctx, *b);
+    if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
+    if (ctx->hpinned) cudaFreeHost(ctx->hpinned);
+    delete ctx;
+    return RBF_OK;
+}
+
+const char* rbf_last_error(const rbf_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int rbf_max_candidates(void) { return kMaxCand; }
+
+rbf_status rbf_bin(rbf_ctx* ctx, const double* cx, const double* cy, int64_t M, const double* px,
+                   const double* py, const double* h, int64_t N, double R, const double* bbox,
+                   void* stream) {
+    if (!ctx) return RBF_ERR_ARG;
+    ctx->binned = false;
+    ctx->assembled = false;
+    if (!cx || !cy || !px || !py || !h || !bbox)
+        return set_err(ctx, RBF_ERR_ARG, "null pointer argument");
+    if (M < 1 || N < 1 || M > (int64_t(1) << 30) || N > (int64_t(1) << 30))
+        return set_err(ctx, RBF_ERR_ARG, "need 1 <= M, N <= 2^30");
+    if (!(R > 0.0) || !isfinite(R)) return set_err(ctx, RBF_ERR_ARG, "R must be finite and > 0");
+    for (int k = 0; k < 4; ++k)
+        if (!isfinite(bbox[k])) return set_err(ctx, RBF_ERR_ARG, "non-finite bbox");
+    if (!(bbox[2] >= bbox[0]) || !(bbox[3] >= bbox[1]))
+        return set_err(ctx, RBF_ERR_ARG, "bbox must be {x0, y0, x1, y1} with x1 >= x0, y1 >= y0");
+    Grid g;
+    g.x0 = bbox[0];
+    g.y0 = bbox[1];
+    g.R = R;
+    g.invR = 1.0 / R;
+    g.R2 = R * R;
+    g.h = R * kCellMargin;
+    g.invh = 1.0 / g.h;
+    const double nxf = std::max(1.0, ceil((bbox[2] - bbox[0]) * g.invh));
+    const double nyf = std::max(1.0, ceil((bbox[3] - bbox[1]) * g.invh));
+    if (nxf * nyf > double(1 << 24))
+        return set_err(ctx, RBF_ERR_LIMIT, "cell grid larger than 2^24 cells (R too small for bbox)");
+    g.gx = int(nxf);
+    g.gy = int(nyf);
+    g.ncell = g.gx * g.gy;
+    ctx->g = g;
+    ctx->M = int(M);
+    ctx->N = int(N);
+    DeviceGuard dg(ctx->device);
+    rbf_status s = bin_run(ctx, cx, cy, px, py, h, as_stream(stream));
+    if (s == RBF_OK) ctx->binned = true;
+    return s;
+}
+
+rbf_status rbf_assemble(rbf_ctx* ctx, rbf_kernel kernel, rbf_prec prec, void* stream) {
+    if (!ctx) return RBF_ERR_ARG;
+    if (!ctx->binned) return set_err(ctx, RBF_ERR_ARG, "rbf_assemble before rbf_bin");
+    if (kernel < RBF_W30 || kernel > RBF_W33) return set_err(ctx, RBF_ERR_ARG, "unknown kernel");
+    if (prec != RBF_FP64 && prec != RBF_FP32_REFINE) return set_err(ctx, RBF_ERR_ARG, "unknown precision");
+    DeviceGuard dg(ctx->device);
+    ctx->kernel = kernel;
+    ctx->prec = prec;
+    rbf_status s = assemble_run(ctx, kernel, prec, as_stream(stream));
+    ctx->assembled = s == RBF_OK;
+    return s;
+}
+
+rbf_status rbf_solve(rbf_ctx* ctx, double* c, int use_c0, double tol, int maxit, int min_support,
+                     rbf_solve_info* info, void* stream) {
+    if (!ctx) return RBF_ERR_ARG;
+    if (!ctx->assembled) return set_err(ctx, RBF_ERR_ARG, "rbf_solve before rbf_assemble");
+    if (!c) return set_err(ctx, RBF_ERR_ARG, "null c");
+    if (!(tol >= 0.0) || maxit < 0) return set_err(ctx, RBF_ERR_ARG, "need tol >= 0, maxit >= 0");
+    DeviceGuard dg(ctx->device);
+    return solve_run(ctx, c, use_c0, tol, maxit, min_support, info, as_stream(stream));
+}
+
+rbf_status rbf_eval(rbf_ctx* ctx, const double* c, const double* qx, const double* qy, int64_t Q,
+                    double* f, void* stream) {
+    if (!ctx) return RBF_ERR_ARG;
+    if (!ctx->binned || ctx->kernel < 0) return set_err(ctx, RBF_ERR_ARG, "rbf_eval before rbf_assemble");
+    if (Q < 0 || (Q > 0 && (!c || !qx || !qy || !f))) return set_err(ctx, RBF_ERR_ARG, "bad arguments");
+    DeviceGuard dg(ctx->device);
+    return eval_points_run(ctx, c, qx, qy, Q, f, as_stream(stream));
+}
+
+rbf_status rbf_eval_grid(rbf_ctx* ctx, const double* c, int nx, int ny, const double* box,
+                         double* f, void* stream) {
+    if (!ctx) return RBF_ERR_ARG;
+    if (!ctx->binned || ctx->kernel < 0) return set_err(ctx, RBF_ERR_ARG, "rbf_eval_grid before rbf_assemble");
+    if (nx < 1 || ny < 1 || !c || !box || !f) return set_err(ctx, RBF_ERR_ARG, "bad arguments");
+    for (int k = 0; k < 4; ++k)
+        if (!isfinite(box[k])) return set_err(ctx, RBF_ERR_ARG, "non-finite box");
+    DeviceGuard dg(ctx->device);
+    return eval_grid_run(ctx, c, nx, ny, box, f, as_stream(stream));
+}
+
+rbf_status rbf_get_layout(const rbf_ctx* ctx, int64_t* nvals, int* value_bytes, int* gx, int* gy) {
+    if (!ctx) return RBF_ERR_ARG;
+    if (nvals) *nvals = ctx->nvals;
+    if (value_bytes) *value_bytes = ctx->prec == RBF_FP32_REFINE ? 4 : 8;
+    if (gx) *gx = ctx->g.gx;
+    if (gy) *gy = ctx->g.gy;
+    return RBF_OK;
+}
+
+rbf_status rbf_export_upper(rbf_ctx* ctx, int64_t cap, int32_t* row, int32_t* col, double* val,
+                            double* bvec, int32_t* support, int64_t* nnz, void* stream) {
+    if (!ctx) return RBF_ERR_ARG;
+    if (!ctx->assembled) return set_err(ctx, RBF_ERR_ARG, "rbf_export_upper before rbf_assemble");
+    if (!nnz || cap < 0 || (cap > 0 && (!row || !col || !val))) return set_err(ctx, RBF_ERR_ARG, "bad arguments");
+    DeviceGuard dg(ctx->device);
+    return export_upper_run(ctx, cap, row, col, val, bvec, support, nnz, as_stream(stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,438 @@
+// Steps (b)+(c): fused evaluation of the sparse rows of A and assembly of the
+// normal equations B = A^T A, b = A^T h (Eq. 4-5, 11-12); also the matrix-free FP64
+// normal residual r = A^T (h - A c) used by iterative refinement.
+//
+// Work decomposition: one CTA per work item = (point cell, up to kWorkPoints points of
+// it). The centres that can lie within R of those points are the centres of the 3x3
+// cells around the point cell -- three contiguous ranges of the sorted centre order --
+// and are staged in shared memory ("candidates", n <= kMaxCand). For each sub-chunk of
+// kSubChunk points the CTA fills a dense tile Phi[p][a] = phi(||x_p - xi_a|| / R)
+// (zero outside the support, Eq. 18), i.e. the rows of A restricted to the candidates
+// (Algorithm 1's triplets, never written to memory). The local Gram matrix
+// G = Phi^T Phi (upper triangle only, Section 5) is accumulated in registers, 4x4
+// entries per thread, and finally added into the stored upper triangle of B with
+// atomics; b and the support counts are reduced per candidate.
+#include <algorithm>
+
+#include "rbf_internal.h"
+
+namespace rbf {
+namespace {
+
+constexpr int kThreads = 256;
+
+// Shared-memory layout of the candidate staging area.
+template <typename CT>
+struct CandSmem {
+    CT* x;              // [npad] candidate coordinates (FP64 global or FP32 point-cell frame)
+    CT* y;
+    int* s;             // [npad] sorted centre index
+    int* a9;            // [npad] local cell 0..8 (row-major in the 3x3 block)
+    long long* rowbase; // [npad] offset of the candidate's row of B
+    double* cval;       // [npad] coefficient (residual pass only)
+};
+
+struct LocalCells {
+    int start[9], len[9], off[10], cell[9];
+    int colshift[9][3];   // column offset of a centre t in the row block of local cell k,
+                          // for t in segment dy: segbase - segstart
+    int n;
+};
+
+// Thread 0 describes the 3x3 block of cells around point cell `cell`.
+__device__ void describe_cells(const Binned& bd, int cell, LocalCells& lc) {
+    const Grid& g = bd.g;
+    const int ix = cell % g.gx, iy = cell / g.gx;
+    int off = 0;
+    for (int k = 0; k < 9; ++k) {
+        const int cx = ix - 1 + (k % 3), cy = iy - 1 + (k / 3);
+        int s = 0, l = 0, cc = -1;
+        if (cx >= 0 && cx < g.gx && cy >= 0 && cy < g.gy) {
+            cc = cy * g.gx + cx;
+            s = bd.cstart[cc];
+            l = bd.cstart[cc + 1] - s;
+            const RowSeg sg = bd.seg[cc];
+            lc.colshift[k][0] = -sg.s0;
+            lc.colshift[k][1] = sg.l0 - sg.s1;
+            lc.colshift[k][2] = sg.l0 + sg.l1 - sg.s2;
+        }
+        lc.start[k] = s;
+        lc.len[k] = l;
+        lc.cell[k] = cc;
+        lc.off[k] = off;
+        off += l;
+    }
+    lc.off[9] = off;
+    lc.n = off;
+}
+
+// Stage the candidates of the work item's 3x3 block. FP64 candidates keep global
+// coordinates; FP32 candidates are moved into the point cell's local frame (units of R).
+template <typename CT>
+__device__ void stage_candidates(const Binned& bd, const LocalCells& lc, const CandSmem<CT>& cs,
+                                 int npad, const double* c_sorted) {
+    for (int a = threadIdx.x; a < npad; a += blockDim.x) {
+        if (a < lc.n) {
+            int k = 0;
+            while (a >= lc.off[k + 1]) ++k;
+            const int s = lc.start[k] + (a - lc.off[k]);
+            const int cc = lc.cell[k];
+            cs.s[a] = s;
+            cs.a9[a] = k;
+            const RowSeg sg = bd.seg[cc];
+            cs.rowbase[a] = (long long)bd.rboff[cc] +
+                            (long long)(s - bd.cstart[cc]) * (long long)(sg.l0 + sg.l1 + sg.l2);
+            if constexpr (sizeof(CT) == 8) {
+                cs.x[a] = bd.cx[s];
+                cs.y[a] = bd.cy[s];
+            } else {
+                cs.x[a] = bd.cu[s] + float((k % 3) - 1);
+                cs.y[a] = bd.cv[s] + float((k / 3) - 1);
+            }
+            if (cs.cval) cs.cval[a] = c_sorted ? c_sorted[s] : 0.0;
+        } else {
+            cs.s[a] = 0;
+            cs.a9[a] = 0;
+            cs.rowbase[a] = 0;
+            cs.x[a] = CT(1e30);
+            cs.y[a] = CT(1e30);
+            if (cs.cval) cs.cval[a] = 0.0;
+        }
+    }
+}
+
+// Fill Phi[pp][a] for the points q0 .. q0+kSubChunk-1 (rows beyond p1 are zero).
+// FP64: global coordinates, support decided by the exact test; counts supports if asked.
+template <int KIND, typename T>
+__device__ void fill_phi(const Binned& bd, const CandSmem<T>& cs, int n, int npad, int q0, int p1,
+                         T* phi, double* hsm, int* cnt) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int pp = warp; pp < kSubChunk; pp += nw) {
+        const int p = q0 + pp;
+        const bool valid = p < p1;
+        T* row = phi + pp * npad;
+        if constexpr (sizeof(T) == 8) {
+            const double xp = valid ? bd.px[p] : 1e300;
+            const double yp = valid ? bd.py[p] : 1e300;
+            if (lane == 0 && hsm) hsm[pp] = valid ? bd.ph[p] : 0.0;
+            for (int a = lane; a < npad; a += 32) {
+                double v = 0.0;
+                if (valid && a < n) {
+                    const double dx = xp - cs.x[a], dy = yp - cs.y[a];
+                    if (inside_exact(dx, dy, bd.g.R, bd.g.R2)) {
+                        const double r = sqrt(fma(dx, dx, dy * dy)) * bd.g.invR;
+                        v = wendland<KIND, double>(r);
+                        if (cnt) atomicAdd(&cnt[a], 1);
+                    }
+                }
+                row[a] = v;
+            }
+        } else {
+            const float up = valid ? bd.pu[p] : 1e30f;
+            const float vp = valid ? bd.pv[p] : 1e30f;
+            for (int a = lane; a < npad; a += 32) {
+                float v = 0.0f;
+                const float du = up - cs.x[a], dv = vp - cs.y[a];
+                const float r2 = du * du + dv * dv;
+                if (r2 < 1.0f) v = wendland<KIND, float>(sqrtf(r2));
+                row[a] = v;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Assembly kernel
+// ---------------------------------------------------------------------------
+template <int KIND, typename T>
+__global__ void __launch_bounds__(kThreads) k_assemble(Binned bd, const int4* __restrict__ work,
+                                                       int npad, T* __restrict__ B,
+                                                       double* __restrict__ bvec,
+                                                       int* __restrict__ support) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ LocalCells lc;
+    constexpr bool kFP64 = sizeof(T) == 8;
+    const int4 wi = work[blockIdx.x];
+    const int cell = wi.x, p0 = wi.y, p1 = wi.z;
+    if (threadIdx.x == 0) describe_cells(bd, cell, lc);
+    __syncthreads();
+    const int n = lc.n;
+
+    // carve shared memory
+    unsigned char* sp = smem;
+    T* phi = reinterpret_cast<T*>(sp);
+    sp += sizeof(T) * kSubChunk * npad;
+    CandSmem<T> cs;
+    cs.rowbase = reinterpret_cast<long long*>(sp);
+    sp += sizeof(long long) * npad;
+    cs.x = reinterpret_cast<T*>(sp);
+    sp += sizeof(T) * npad;
+    cs.y = reinterpret_cast<T*>(sp);
+    sp += sizeof(T) * npad;
+    cs.s = reinterpret_cast<int*>(sp);
+    sp += sizeof(int) * npad;
+    cs.a9 = reinterpret_cast<int*>(sp);
+    sp += sizeof(int) * npad;
+    int* cnt = reinterpret_cast<int*>(sp);
+    sp += sizeof(int) * npad;
+    double* hsm = reinterpret_cast<double*>(sp);
+    sp += sizeof(double) * kSubChunk;
+    cs.cval = nullptr;
+
+    stage_candidates<T>(bd, lc, cs, npad, nullptr);
+    for (int a = threadIdx.x; a < npad; a += blockDim.x) cnt[a] = 0;
+    __syncthreads();
+
+    const int nb = npad / 4;
+    const int nblk = nb * (nb + 1) / 2;
+    const int npass = (nblk + kThreads - 1) / kThreads;
+    double bacc0 = 0.0, bacc1 = 0.0;   // b for candidates tid and tid + kThreads
+
+    for (int pass = 0; pass < npass; ++pass) {
+        const int blk = pass * kThreads + threadIdx.x;
+        const bool active = blk < nblk;
+        int bi = 0, bj = 0;
+        if (active) {
+            int rem = blk;
+            while (rem >= nb - bi) {
+                rem -= nb - bi;
+                ++bi;
+            }
+            bj = bi + rem;
+        }
+        T acc[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = T(0);
+
+        for (int q0 = p0; q0 < p1; q0 += kSubChunk) {
+            __syncthreads();
+            fill_phi<KIND, T>(bd, cs, n, npad, q0, p1, phi, kFP64 ? hsm : nullptr,
+                              (kFP64 && pass == 0) ? cnt : nullptr);
+            __syncthreads();
+            const int np = min(kSubChunk, p1 - q0);
+            if (kFP64 && pass == 0) {
+                for (int pp = 0; pp < np; ++pp) {
+                    const double hp = hsm[pp];
+                    if (threadIdx.x < n) bacc0 += hp * double(phi[pp * npad + threadIdx.x]);
+                    if (threadIdx.x + kThreads < n)
+                        bacc1 += hp * double(phi[pp * npad + threadIdx.x + kThreads]);
+                }
+            }
+            if (active) {
+                const T* pa = phi + 4 * bi;
+                const T* pb = phi + 4 * bj;
+                for (int pp = 0; pp < np; ++pp) {
+                    T va[4], vb[4];
+                    if constexpr (kFP64) {
+                        const double2 a01 = *reinterpret_cast<const double2*>(pa + pp * npad);
+                        const double2 a23 = *reinterpret_cast<const double2*>(pa + pp * npad + 2);
+                        const double2 b01 = *reinterpret_cast<const double2*>(pb + pp * npad);
+                        const double2 b23 = *reinterpret_cast<const double2*>(pb + pp * npad + 2);
+                        va[0] = a01.x; va[1] = a01.y; va[2] = a23.x; va[3] = a23.y;
+                        vb[0] = b01.x; vb[1] = b01.y; vb[2] = b23.x; vb[3] = b23.y;
+                    } else {
+                        const float4 a4 = *reinterpret_cast<const float4*>(pa + pp * npad);
+                        const float4 b4 = *reinterpret_cast<const float4*>(pb + pp * npad);
+                        va[0] = a4.x; va[1] = a4.y; va[2] = a4.z; va[3] = a4.w;
+                        vb[0] = b4.x; vb[1] = b4.y; vb[2] = b4.z; vb[3] = b4.w;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) acc[u][v] = fma(va[u], vb[v], acc[u][v]);
+                }
+            }
+        }
+        // scatter the thread's 4x4 block of the local Gram matrix into B (upper triangle)
+        if (active) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int a = 4 * bi + u;
+                if (a >= n) continue;
+                const int ka = cs.a9[a];
+                const long long rba = cs.rowbase[a];
+                const int sa = cs.s[a];
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    const int b = 4 * bj + v;
+                    if (b >= n || b < a) continue;
+                    const T val = acc[u][v];
+                    if (val == T(0)) continue;
+                    const int kb = cs.a9[b];
+                    const int dy = kb / 3 - ka / 3;
+                    atomicAdd(&B[rba + lc.colshift[ka][dy] + cs.s[b]], val);
+                    if (b != a && kb == ka)
+                        atomicAdd(&B[cs.rowbase[b] + lc.colshift[kb][0] + sa], val);
+                }
+            }
+        }
+    }
+    if constexpr (kFP64) {
+        __syncthreads();
+        if (threadIdx.x < n) {
+            if (bacc0 != 0.0) atomicAdd(&bvec[cs.s[threadIdx.x]], bacc0);
+            if (cnt[threadIdx.x]) atomicAdd(&support[cs.s[threadIdx.x]], cnt[threadIdx.x]);
+        }
+        if (threadIdx.x + kThreads < n) {
+            const int a = threadIdx.x + kThreads;
+            if (bacc1 != 0.0) atomicAdd(&bvec[cs.s[a]], bacc1);
+            if (cnt[a]) atomicAdd(&support[cs.s[a]], cnt[a]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Matrix-free FP64 normal residual r = A^T (h - A c), optionally with support counts.
+// ---------------------------------------------------------------------------
+template <int KIND>
+__global__ void __launch_bounds__(kThreads) k_residual(Binned bd, const int4* __restrict__ work,
+                                                       int npad, const double* __restrict__ c,
+                                                       double* __restrict__ r,
+                                                       int* __restrict__ support) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ LocalCells lc;
+    __shared__ double esm[kSubChunk];
+    const int4 wi = work[blockIdx.x];
+    const int cell = wi.x, p0 = wi.y, p1 = wi.z;
+    if (threadIdx.x == 0) describe_cells(bd, cell, lc);
+    __syncthreads();
+    const int n = lc.n;
+    unsigned char* sp = smem;
+    double* phi = reinterpret_cast<double*>(sp);
+    sp += sizeof(double) * kSubChunk * npad;
+    CandSmem<double> cs;
+    cs.rowbase = reinterpret_cast<long long*>(sp);
+    sp += sizeof(long long) * npad;
+    cs.x = reinterpret_cast<double*>(sp);
+    sp += sizeof(double) * npad;
+    cs.y = reinterpret_cast<double*>(sp);
+    sp += sizeof(double) * npad;
+    cs.cval = reinterpret_cast<double*>(sp);
+    sp += sizeof(double) * npad;
+    cs.s = reinterpret_cast<int*>(sp);
+    sp += sizeof(int) * npad;
+    cs.a9 = reinterpret_cast<int*>(sp);
+    sp += sizeof(int) * npad;
+    int* cnt = reinterpret_cast<int*>(sp);
+    sp += sizeof(int) * npad;
+    double* hsm = reinterpret_cast<double*>(sp);
+
+    stage_candidates<double>(bd, lc, cs, npad, c);
+    for (int a = threadIdx.x; a < npad; a += blockDim.x) cnt[a] = 0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    double racc0 = 0.0, racc1 = 0.0;
+    for (int q0 = p0; q0 < p1; q0 += kSubChunk) {
+        __syncthreads();
+        fill_phi<KIND, double>(bd, cs, n, npad, q0, p1, phi, hsm, support ? cnt : nullptr);
+        __syncthreads();
+        const int np = min(kSubChunk, p1 - q0);
+        // e_p = h_p - sum_a Phi[p][a] c_a  (one warp per point)
+        for (int pp = warp; pp < np; pp += nw) {
+            double s = 0.0;
+            for (int a = lane; a < n; a += 32) s = fma(phi[pp * npad + a], cs.cval[a], s);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) esm[pp] = hsm[pp] - s;
+        }
+        __syncthreads();
+        // r_a += sum_p Phi[p][a] e_p
+        for (int pp = 0; pp < np; ++pp) {
+            const double e = esm[pp];
+            if (threadIdx.x < n) racc0 = fma(phi[pp * npad + threadIdx.x], e, racc0);
+            if (threadIdx.x + kThreads < n) racc1 = fma(phi[pp * npad + threadIdx.x + kThreads], e, racc1);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < n) {
+        if (racc0 != 0.0) atomicAdd(&r[cs.s[threadIdx.x]], racc0);
+        if (support && cnt[threadIdx.x]) atomicAdd(&support[cs.s[threadIdx.x]], cnt[threadIdx.x]);
+    }
+    if (threadIdx.x + kThreads < n) {
+        const int a = threadIdx.x + kThreads;
+        if (racc1 != 0.0) atomicAdd(&r[cs.s[a]], racc1);
+        if (support && cnt[a]) atomicAdd(&support[cs.s[a]], cnt[a]);
+    }
+}
+
+template <typename T>
+size_t asm_smem(int npad, bool resid) {
+    size_t b = sizeof(T) * kSubChunk * npad + sizeof(long long) * npad + 2 * sizeof(T) * npad +
+               3 * sizeof(int) * npad + sizeof(double) * kSubChunk;
+    if (resid) b += sizeof(double) * npad;
+    return b;
+}
+
+template <int KIND, typename T>
+rbf_status launch_assemble(rbf_ctx* ctx, cudaStream_t st, int npad) {
+    const size_t sm = asm_smem<T>(npad, false);
+    auto kfn = k_assemble<KIND, T>;
+    RBF_CUDA_TRY(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
+    kfn<<<ctx->nwork, kThreads, sm, st>>>(view(ctx), ctx->work.as<int4>(), npad, ctx->bvals.as<T>(),
+                                          ctx->bvec.as<double>(), ctx->support.as<int>());
+    RBF_CUDA_TRY(cudaGetLastError());
+    return RBF_OK;
+}
+
+template <int KIND>
+rbf_status launch_residual(rbf_ctx* ctx, const double* c, double* r, bool count, cudaStream_t st,
+                           int npad) {
+    const size_t sm = asm_smem<double>(npad, true);
+    auto kfn = k_residual<KIND>;
+    RBF_CUDA_TRY(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
+    kfn<<<ctx->nwork, kThreads, sm, st>>>(view(ctx), ctx->work.as<int4>(), npad, c, r,
+                                          count ? ctx->support.as<int>() : nullptr);
+    RBF_CUDA_TRY(cudaGetLastError());
+    return RBF_OK;
+}
+
+}  // namespace
+
+rbf_status assemble_run(rbf_ctx* ctx, int kernel, int prec, cudaStream_t st) {
+    const int M = ctx->M;
+    const size_t vb = prec == RBF_FP64 ? sizeof(double) : sizeof(float);
+    rbf_status s;
+    if ((s = ensure(ctx, ctx->bvals, vb * std::max<int64_t>(ctx->nvals, 1), st)) != RBF_OK) return s;
+    if ((s = ensure(ctx, ctx->bvec, sizeof(double) * M, st)) != RBF_OK) return s;
+    if ((s = ensure(ctx, ctx->support, sizeof(int) * M, st)) != RBF_OK) return s;
+    RBF_CUDA_TRY(cudaMemsetAsync(ctx->bvals.p, 0, vb * ctx->nvals, st));
+    RBF_CUDA_TRY(cudaMemsetAsync(ctx->bvec.p, 0, sizeof(double) * M, st));
+    RBF_CUDA_TRY(cudaMemsetAsync(ctx->support.p, 0, sizeof(int) * M, st));
+    if (ctx->nwork == 0) return RBF_OK;
+    const int npad = std::max(4, (ctx->max_cand + 3) / 4 * 4);
+    if (prec == RBF_FP64) {
+        switch (kernel) {
+            case RBF_W30: s = launch_assemble<0, double>(ctx, st, npad); break;
+            case RBF_W31: s = launch_assemble<1, double>(ctx, st, npad); break;
+            case RBF_W32: s = launch_assemble<2, double>(ctx, st, npad); break;
+            default: s = launch_assemble<3, double>(ctx, st, npad); break;
+        }
+        return s;
+    }
+    switch (kernel) {
+        case RBF_W30: s = launch_assemble<0, float>(ctx, st, npad); break;
+        case RBF_W31: s = launch_assemble<1, float>(ctx, st, npad); break;
+        case RBF_W32: s = launch_assemble<2, float>(ctx, st, npad); break;
+        default: s = launch_assemble<3, float>(ctx, st, npad); break;
+    }
+    if (s != RBF_OK) return s;
+    // b = A^T h and the support counts in FP64: the residual with c = 0
+    RBF_CUDA_TRY(cudaMemsetAsync(ctx->bvec.p, 0, sizeof(double) * M, st));
+    return residual_run(ctx, nullptr, ctx->bvec.as<double>(), true, st);
+}
+
+rbf_status residual_run(rbf_ctx* ctx, const double* c_sorted, double* r_sorted, bool count,
+                        cudaStream_t st) {
+    if (ctx->nwork == 0) return RBF_OK;
+    const double* c = c_sorted;   // nullptr stands for c = 0, i.e. r = A^T h
+    const int npad = std::max(4, (ctx->max_cand + 3) / 4 * 4);
+    switch (ctx->kernel) {
+        case RBF_W30: return launch_residual<0>(ctx, c, r_sorted, count, st, npad);
+        case RBF_W31: return launch_residual<1>(ctx, c, r_sorted, count, st, npad);
+        case RBF_W32: return launch_residual<2>(ctx, c, r_sorted, count, st, npad);
+        default: return launch_residual<3>(ctx, c, r_sorted, count, st, npad);
+    }
+}
+
+}  // namespace rbf

@@ -1,0 +1,123 @@
+// Device-side definitions shared by the librbf kernels: the Wendland basis
+// functions, the uniform cell grid, the context layout and CUDA error helpers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/rbf.h"
+
+namespace rbf {
+
+// Largest number of centres in a 3x3 cell neighbourhood that the assembly and
+// residual kernels stage in shared memory (a point's candidate list).
+constexpr int kMaxCand = 384;
+// Points per staged sub-chunk of the fused assembly / residual passes.
+constexpr int kSubChunk = 32;
+// Points per assembly work item (one CTA); larger cells are split.
+constexpr int kWorkPoints = 256;
+// Relative enlargement of the cell side over R, so that a pair closer than R is never
+// more than one computed cell apart whatever the rounding of the cell index.
+constexpr double kCellMargin = 1.0 + 1.0 / 1073741824.0;
+
+// ---------------------------------------------------------------------------
+// Wendland functions phi_{3,s}(r), r = ||x - xi|| / R in [0, 1) (Table 2, Eq. 18).
+// Callers apply the cut-off (r >= 1 -> 0) themselves. KIND 2 is phi_{3,2} / 3.
+// ---------------------------------------------------------------------------
+template <int KIND, typename T>
+__device__ __forceinline__ T wendland(T r) {
+    const T t = T(1) - r;
+    const T t2 = t * t;
+    if constexpr (KIND == 0) {
+        return t2;
+    } else if constexpr (KIND == 1) {
+        const T t4 = t2 * t2;
+        return t4 * (T(4) * r + T(1));
+    } else if constexpr (KIND == 2) {
+        const T t6 = t2 * t2 * t2;
+        return t6 * ((T(35) * r + T(18)) * r + T(3)) * T(1.0 / 3.0);
+    } else {
+        const T t4 = t2 * t2;
+        const T t8 = t4 * t4;
+        return t8 * (((T(32) * r + T(25)) * r + T(8)) * r + T(1));
+    }
+}
+
+// Exact form of the support test ||x - xi|| / R < 1 in FP64 with the operation order
+// sqrt(dx*dx + dy*dy) / R (separately rounded products and sum, IEEE sqrt and division),
+// so that integer support counts agree bit for bit with a CPU evaluation of the same
+// expression. The division is only evaluated for pairs within 1e-9 of the boundary.
+__device__ __forceinline__ bool inside_exact(double dx, double dy, double R, double R2) {
+    const double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+    if (d2 < R2 * (1.0 - 1e-9)) return true;
+    if (d2 > R2 * (1.0 + 1e-9)) return false;
+    return __ddiv_rn(__dsqrt_rn(d2), R) < 1.0;
+}
+
+// ---------------------------------------------------------------------------
+// Uniform grid of square cells of side h = R * kCellMargin over a bounding box.
+// Cell key = iy * gx + ix (row-major, x fastest); items outside are clamped.
+// ---------------------------------------------------------------------------
+struct Grid {
+    double x0, y0;     // lower-left corner
+    double h, invh;    // cell side and its inverse
+    double R, invR, R2;
+    int gx, gy;        // cells per axis
+    int ncell;         // gx * gy
+};
+
+__device__ __forceinline__ int cell_ix(const Grid& g, double x) {
+    double f = floor((x - g.x0) * g.invh);
+    f = fmin(fmax(f, 0.0), double(g.gx - 1));
+    return int(f);
+}
+__device__ __forceinline__ int cell_iy(const Grid& g, double y) {
+    double f = floor((y - g.y0) * g.invh);
+    f = fmin(fmax(f, 0.0), double(g.gy - 1));
+    return int(f);
+}
+
+// Per-cell description of the stored upper part of B. The rows of B that belong to
+// the centres of cell c = (ix, iy) form one dense row-major block of m_c x L_c values:
+// columns are the centres of the 13 "upper" neighbour cells, i.e. three contiguous
+// ranges of the cell-sorted centre order:
+//   seg 0: cells (ix .. ix+2, iy)        seg 1: cells (ix-2 .. ix+2, iy+1)
+//   seg 2: cells (ix-2 .. ix+2, iy+2)    (clipped to the grid)
+// Any centre pair closer than 2R (the only pairs with B_st != 0) with cell(s) <= cell(t)
+// in key order has t inside one of these ranges of cell(s).
+struct RowSeg {
+    int s0, l0, s1, l1, s2, l2;   // first centre and length of each segment
+};
+
+// Views of the context's device buffers passed by value to kernels.
+struct Binned {
+    Grid g;
+    int M, N;
+    const int* cstart;      // [ncell+1] first sorted centre of each cell
+    const int* pstart;      // [ncell+1] first sorted point of each cell
+    const double* cx;       // [M] sorted centre coordinates (FP64, global frame)
+    const double* cy;
+    const float* cu;        // [M] centre coordinates local to its cell, units of R (FP32)
+    const float* cv;
+    const double* px;       // [N] sorted point coordinates and heights (FP64)
+    const double* py;
+    const double* ph;
+    const float* pu;        // [N] point coordinates local to its cell, units of R (FP32)
+    const float* pv;
+    const int* cperm;       // [M] sorted -> caller centre index
+    const RowSeg* seg;      // [ncell]
+    const int64_t* rboff;   // [ncell+1] offset of each cell's row block in the value array
+};
+
+// ---------------------------------------------------------------------------
+// Host-side error helpers
+// ---------------------------------------------------------------------------
+#define RBF_CUDA_TRY(expr)                                        \
+    do {                                                          \
+        cudaError_t _e = (expr);                                  \
+        if (_e != cudaSuccess) return ::rbf::cuda_fail(ctx, _e, #expr, __FILE__, __LINE__); \
+    } while (0)
+
+rbf_status cuda_fail(rbf_ctx* ctx, cudaError_t e, const char* what, const char* file, int line);
+
+}  // namespace rbf

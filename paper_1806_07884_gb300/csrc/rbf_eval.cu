@@ -1,0 +1,152 @@
+// Step (e): evaluate the approximant f(x) = sum_j c_j phi(||x - xi_j|| / R) (Eq. 3) at
+// query points or on a node-centred grid. Only the centres of the 3x3 cells around the
+// query's cell can contribute (compact support, Eq. 18); they are three contiguous ranges
+// of the cell-sorted centre order. Also: export of the assembled B for diagnostics.
+#include <algorithm>
+
+#include "rbf_internal.h"
+
+namespace rbf {
+namespace {
+
+template <int KIND>
+__device__ __forceinline__ double eval_at(const Binned& bd, const double* __restrict__ c,
+                                          double x, double y) {
+    const Grid& g = bd.g;
+    const int ix = cell_ix(g, x), iy = cell_iy(g, y);
+    const int xa = max(ix - 1, 0), xb = min(ix + 1, g.gx - 1);
+    double f = 0.0;
+    for (int row = max(iy - 1, 0); row <= min(iy + 1, g.gy - 1); ++row) {
+        const int s0 = bd.cstart[row * g.gx + xa], s1 = bd.cstart[row * g.gx + xb + 1];
+        for (int s = s0; s < s1; ++s) {
+            const double dx = x - bd.cx[s], dy = y - bd.cy[s];
+            if (inside_exact(dx, dy, g.R, g.R2)) {
+                const double r = sqrt(fma(dx, dx, dy * dy)) * g.invR;
+                f = fma(c[s], wendland<KIND, double>(r), f);
+            }
+        }
+    }
+    return f;
+}
+
+template <int KIND>
+__global__ void k_eval_points(Binned bd, const double* __restrict__ c, const double* __restrict__ qx,
+                              const double* __restrict__ qy, int64_t Q, double* __restrict__ f) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < Q;
+         i += int64_t(gridDim.x) * blockDim.x)
+        f[i] = eval_at<KIND>(bd, c, qx[i], qy[i]);
+}
+
+// Grid node coordinates follow an inclusive linspace: start + j * step (separately
+// rounded), the last node exactly at the end of the box.
+template <int KIND>
+__global__ void k_eval_grid(Binned bd, const double* __restrict__ c, int nx, int ny, double x0,
+                            double y0, double x1, double y1, double sx, double sy,
+                            double* __restrict__ f) {
+    const int64_t Q = int64_t(nx) * ny;
+    for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < Q;
+         q += int64_t(gridDim.x) * blockDim.x) {
+        const int i = int(q / nx), j = int(q % nx);
+        const double x = (j == nx - 1 && nx > 1) ? x1 : __dadd_rn(__dmul_rn(double(j), sx), x0);
+        const double y = (i == ny - 1 && ny > 1) ? y1 : __dadd_rn(__dmul_rn(double(i), sy), y0);
+        f[q] = eval_at<KIND>(bd, c, x, y);
+    }
+}
+
+template <typename T>
+__global__ void k_export(Binned bd, const T* __restrict__ B, const double* __restrict__ bvec,
+                         const int* __restrict__ support, int64_t cap, int32_t* __restrict__ row,
+                         int32_t* __restrict__ col, double* __restrict__ val,
+                         double* __restrict__ bout, int32_t* __restrict__ sout,
+                         unsigned long long* __restrict__ counter) {
+    const int c = blockIdx.x;
+    const int cs = bd.cstart[c], m = bd.cstart[c + 1] - cs;
+    const RowSeg sg = bd.seg[c];
+    const int L = sg.l0 + sg.l1 + sg.l2;
+    const T* Bc = B + bd.rboff[c];
+    for (int e = threadIdx.x; e < m * L; e += blockDim.x) {
+        const int i = e / L, k = e % L;
+        const double v = double(Bc[int64_t(i) * L + k]);
+        const int t = k < sg.l0 ? sg.s0 + k : (k < sg.l0 + sg.l1 ? sg.s1 + k - sg.l0 : sg.s2 + k - sg.l0 - sg.l1);
+        const int s = cs + i;
+        if (t < s || v == 0.0) continue;   // diagonal block: keep the upper triangle only
+        const unsigned long long pos = atomicAdd(counter, 1ull);
+        if (pos < (unsigned long long)cap) {
+            row[pos] = bd.cperm[s];
+            col[pos] = bd.cperm[t];
+            val[pos] = v;
+        }
+    }
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        if (bout) bout[bd.cperm[cs + i]] = bvec[cs + i];
+        if (sout) sout[bd.cperm[cs + i]] = support[cs + i];
+    }
+}
+
+int eval_grid_size(int64_t Q) { return int(std::min<int64_t>((Q + 255) / 256, 152 * 32)); }
+
+}  // namespace
+
+rbf_status eval_points_run(rbf_ctx* ctx, const double* c, const double* qx, const double* qy,
+                           int64_t Q, double* f, cudaStream_t st) {
+    rbf_status s = ensure(ctx, ctx->csort, sizeof(double) * ctx->M, st);
+    if (s != RBF_OK) return s;
+    const Binned bd = view(ctx);
+    launch_gather_sorted(c, bd.cperm, ctx->csort.as<double>(), ctx->M, st);
+    if (Q <= 0) return RBF_OK;
+    const double* cs = ctx->csort.as<double>();
+    const int gb = eval_grid_size(Q);
+    switch (ctx->kernel) {
+        case RBF_W30: k_eval_points<0><<<gb, 256, 0, st>>>(bd, cs, qx, qy, Q, f); break;
+        case RBF_W31: k_eval_points<1><<<gb, 256, 0, st>>>(bd, cs, qx, qy, Q, f); break;
+        case RBF_W32: k_eval_points<2><<<gb, 256, 0, st>>>(bd, cs, qx, qy, Q, f); break;
+        default: k_eval_points<3><<<gb, 256, 0, st>>>(bd, cs, qx, qy, Q, f); break;
+    }
+    RBF_CUDA_TRY(cudaGetLastError());
+    return RBF_OK;
+}
+
+rbf_status eval_grid_run(rbf_ctx* ctx, const double* c, int nx, int ny, const double* box,
+                         double* f, cudaStream_t st) {
+    rbf_status s = ensure(ctx, ctx->csort, sizeof(double) * ctx->M, st);
+    if (s != RBF_OK) return s;
+    const Binned bd = view(ctx);
+    launch_gather_sorted(c, bd.cperm, ctx->csort.as<double>(), ctx->M, st);
+    const double* cs = ctx->csort.as<double>();
+    const double x0 = box[0], y0 = box[1], x1 = box[2], y1 = box[3];
+    const double sx = nx > 1 ? (x1 - x0) / double(nx - 1) : 0.0;
+    const double sy = ny > 1 ? (y1 - y0) / double(ny - 1) : 0.0;
+    const int gb = eval_grid_size(int64_t(nx) * ny);
+    switch (ctx->kernel) {
+        case RBF_W30: k_eval_grid<0><<<gb, 256, 0, st>>>(bd, cs, nx, ny, x0, y0, x1, y1, sx, sy, f); break;
+        case RBF_W31: k_eval_grid<1><<<gb, 256, 0, st>>>(bd, cs, nx, ny, x0, y0, x1, y1, sx, sy, f); break;
+        case RBF_W32: k_eval_grid<2><<<gb, 256, 0, st>>>(bd, cs, nx, ny, x0, y0, x1, y1, sx, sy, f); break;
+        default: k_eval_grid<3><<<gb, 256, 0, st>>>(bd, cs, nx, ny, x0, y0, x1, y1, sx, sy, f); break;
+    }
+    RBF_CUDA_TRY(cudaGetLastError());
+    return RBF_OK;
+}
+
+rbf_status export_upper_run(rbf_ctx* ctx, int64_t cap, int32_t* row, int32_t* col, double* val,
+                            double* bvec, int32_t* support, int64_t* nnz, cudaStream_t st) {
+    const Binned bd = view(ctx);
+    unsigned long long* counter = reinterpret_cast<unsigned long long*>(ctx->stats.as<char>() + 32);
+    RBF_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st));
+    if (ctx->prec == RBF_FP64)
+        k_export<double><<<ctx->g.ncell, 256, 0, st>>>(bd, ctx->bvals.as<double>(), ctx->bvec.as<double>(),
+                                                        ctx->support.as<int>(), cap, row, col, val,
+                                                        bvec, support, counter);
+    else
+        k_export<float><<<ctx->g.ncell, 256, 0, st>>>(bd, ctx->bvals.as<float>(), ctx->bvec.as<double>(),
+                                                       ctx->support.as<int>(), cap, row, col, val,
+                                                       bvec, support, counter);
+    RBF_CUDA_TRY(cudaGetLastError());
+    unsigned long long* h = static_cast<unsigned long long*>(ctx->hpinned);
+    RBF_CUDA_TRY(cudaMemcpyAsync(h, counter, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    RBF_CUDA_TRY(cudaStreamSynchronize(st));
+    *nnz = int64_t(*h);
+    if (*nnz > cap) return set_err(ctx, RBF_ERR_ARG, "export capacity too small");
+    return RBF_OK;
+}
+
+}  // namespace rbf

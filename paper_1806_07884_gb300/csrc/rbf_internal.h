@@ -1,0 +1,116 @@
+// Host-side context of librbf and the launchers each translation unit provides.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "rbf_common.cuh"
+
+// A device buffer obtained from the context's allocator.
+struct rbf_buf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    template <typename T> T* as() const { return static_cast<T*>(p); }
+};
+
+struct rbf_ctx {
+    int device = 0;
+    rbf_alloc_fn alloc = nullptr;
+    rbf_free_fn free_fn = nullptr;
+    void* user = nullptr;
+    std::string err;
+
+    // ---- binning (rbf_bin) ----
+    rbf::Grid g{};
+    int M = 0, N = 0;
+    int max_cand = 0;          // largest 3x3 neighbourhood centre count
+    int max_cell_pts = 0;      // largest points-per-cell count
+    int nwork = 0;             // assembly work items
+    int64_t nvals = 0;         // stored B values (upper cell-pair blocks)
+    bool binned = false;
+
+    rbf_buf ccount, pcount;    // [ncell] counts, reused as scratch
+    rbf_buf cstart, pstart;    // [ncell+1]
+    rbf_buf ckey, crank;       // [M]
+    rbf_buf pkey, prank;       // [N]
+    rbf_buf cx, cy, cu, cv, cperm;      // [M]
+    rbf_buf px, py, ph, pu, pv;         // [N]
+    rbf_buf seg;               // [ncell] RowSeg
+    rbf_buf rbsize, rboff;     // [ncell], [ncell+1] int64
+    rbf_buf wcount, wstart;    // [ncell], [ncell+1]
+    rbf_buf work;              // [nwork] int4 {cell, p0, p1, 0}
+    rbf_buf scan_tmp;          // block sums of the device scans
+    rbf_buf stats;             // small int counters read back by rbf_bin
+
+    // ---- assembly (rbf_assemble) ----
+    int kernel = -1;
+    int prec = -1;
+    bool assembled = false;
+    rbf_buf bvals;             // B values (double or float)
+    rbf_buf bvec;              // [M] b = A^T h, sorted order (FP64)
+    rbf_buf support;           // [M] points inside each support, sorted order
+
+    // ---- solver workspace ----
+    rbf_buf x, r, z, p, q, dinv;        // [M] FP64 CG vectors, sorted order
+    rbf_buf x32, r32, z32, p32, q32, dinv32;   // [M] FP32 inner-solve vectors
+    rbf_buf partial;           // per-block partial sums
+    rbf_buf scal;              // device scalars (struct CgScalars)
+    rbf_buf csort;             // [M] FP64 coefficients in sorted order (evaluation)
+    void* hpinned = nullptr;   // pinned host scratch for scalar read-back (4 KiB)
+    cudaStream_t capture_stream = nullptr;   // private stream used only to capture graphs
+
+    // CG graphs: [precision: 0 FP64, 1 FP32][chunk = 8 << k, k = 0..5]
+    struct GraphCache {
+        cudaGraphExec_t exec = nullptr;
+        int M = 0, ncell = 0, gx = 0;
+        const void* key[8] = {};
+    };
+    GraphCache graphs[2][6];
+};
+
+namespace rbf {
+
+rbf_status set_err(rbf_ctx* ctx, rbf_status s, const char* msg);
+rbf_status ensure(rbf_ctx* ctx, rbf_buf& b, size_t bytes, cudaStream_t st);
+void release(rbf_ctx* ctx, rbf_buf& b);
+Binned view(const rbf_ctx* ctx);
+
+// rbf_bin.cu
+rbf_status bin_run(rbf_ctx* ctx, const double* cx, const double* cy, const double* px,
+                   const double* py, const double* h, cudaStream_t st);
+// exclusive scan of n int32 counts into n+1 outputs (int32 or int64), device-wide
+rbf_status scan_i32(rbf_ctx* ctx, const int* in, int* out, int n, cudaStream_t st);
+rbf_status scan_i64(rbf_ctx* ctx, const int64_t* in, int64_t* out, int n, cudaStream_t st);
+
+// rbf_assemble.cu
+rbf_status assemble_run(rbf_ctx* ctx, int kernel, int prec, cudaStream_t st);
+
+// rbf_resid.cu : r = A^T (h - A c) in FP64, matrix-free (c in sorted order). With
+// count_support the support counts are recomputed.
+rbf_status residual_run(rbf_ctx* ctx, const double* c_sorted, double* r_sorted,
+                        bool count_support, cudaStream_t st);
+
+// rbf_solve.cu
+rbf_status solve_run(rbf_ctx* ctx, double* c, int use_c0, double tol, int maxit,
+                     int min_support, rbf_solve_info* info, cudaStream_t st);
+
+// rbf_eval.cu
+rbf_status eval_points_run(rbf_ctx* ctx, const double* c, const double* qx, const double* qy,
+                           int64_t Q, double* f, cudaStream_t st);
+rbf_status eval_grid_run(rbf_ctx* ctx, const double* c, int nx, int ny, const double* box,
+                         double* f, cudaStream_t st);
+rbf_status export_upper_run(rbf_ctx* ctx, int64_t cap, int32_t* row, int32_t* col, double* val,
+                            double* bvec, int32_t* support, int64_t* nnz, cudaStream_t st);
+
+// permutation helpers (rbf_solve.cu)
+void launch_gather_sorted(const double* c_orig, const int* cperm, double* c_sorted, int M,
+                          cudaStream_t st);
+void launch_scatter_orig(const double* c_sorted, const int* cperm, double* c_orig, int M,
+                         cudaStream_t st);
+
+inline int div_up(int64_t a, int64_t b) { return int((a + b - 1) / b); }
+
+}  // namespace rbf

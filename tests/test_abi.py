@@ -1,0 +1,81 @@
+"""The C-ABI library builds, loads and exports every function include/rbf.h declares;
+the Python binding declares exactly those; host-side argument checks need no GPU."""
+import ctypes
+import os
+import re
+import shutil
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "rbf.h")
+
+
+def _header_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:rbf_status|int|const char\s*\*)\s+(rbf_\w+)\s*\(",
+                                 text, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_1806_07884_gb300 import build as b
+    if not os.path.exists(b.LIB):
+        if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+            pytest.skip("nvcc not available to build librbf")
+        b.build()
+    return b.LIB
+
+
+def test_header_declares_the_pipeline():
+    names = _header_functions()
+    for required in ("rbf_bin", "rbf_assemble", "rbf_solve", "rbf_eval"):
+        assert required in names
+
+
+def test_library_exports_every_header_symbol(libpath):
+    lib = ctypes.CDLL(libpath)
+    missing = [n for n in _header_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_header(libpath):
+    from paper_1806_07884_gb300 import _lib
+    assert sorted(_lib.SIGNATURES) == _header_functions()
+    lib = _lib.load(libpath)
+    assert lib.rbf_max_candidates() >= 128
+
+
+def test_status_codes_match_header():
+    from paper_1806_07884_gb300 import _lib
+    text = open(HEADER).read()
+    for name, code in re.findall(r"(RBF_\w+)\s*=\s*(\d+)", text):
+        if name in _lib.STATUS_NAMES.values():
+            assert _lib.STATUS_NAMES[int(code)] == name
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    from paper_1806_07884_gb300 import _lib
+    saved = _lib._lib
+    _lib._lib = None
+    try:
+        with pytest.raises(ImportError):
+            _lib.load(str(tmp_path / "librbf.so"))
+    finally:
+        _lib._lib = saved
+
+
+def test_null_arguments_rejected_without_gpu(libpath):
+    from paper_1806_07884_gb300 import _lib
+    lib = _lib.load(libpath)
+    box = (ctypes.c_double * 4)(0, 0, 1, 1)
+    assert lib.rbf_bin(None, None, None, 1, None, None, None, 1, 0.1, box, None) == _lib.RBF_ERR_ARG
+    assert lib.rbf_assemble(None, 1, 0, None) == _lib.RBF_ERR_ARG
+    assert lib.rbf_destroy(None) == _lib.RBF_ERR_ARG
+    out = ctypes.c_void_p()
+    nullf = ctypes.cast(None, _lib.ALLOC_FN)
+    nullfree = ctypes.cast(None, _lib.FREE_FN)
+    assert lib.rbf_create(None, 0, nullf, nullfree, None) == _lib.RBF_ERR_ARG
+    # bad device index: rejected without touching a GPU
+    assert lib.rbf_create(ctypes.byref(out), 1 << 20, nullf, nullfree, None) != 0

@@ -1,0 +1,276 @@
+"""GPU parity: the CUDA path through the C-ABI against the CPU FP64 oracle on the
+same seeded inputs.
+
+Bars: integer results (support counts, pinned centres, the sparsity pattern) exact;
+FP64 path: B, b to 1e-12; f at the data points and on the grid to 1e-9 max relative
+error (norm-wise, see oracle.rel_err); c to max(1e-9, 1e-14 kappa): both sides round B
+differently (about 100 terms per entry, relative 1e-14), which moves c by up to
+kappa times that, kappa the condition number of the Jacobi-scaled B. FP32 assembly
+with FP64 refinement: f to 1e-6."""
+import numpy as np
+import pytest
+import scipy.sparse
+
+import datagen as dg
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_1806_07884_gb300 as pkg  # noqa: E402
+
+FP64_BAR = 1e-9
+MIXED_BAR = 1e-6
+
+
+def _dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def _binned(pb, kind=None, prec="fp64", bbox=None):
+    ctx = pkg.Context()
+    C, P = pb.centres, pb.points
+    ctx.bin(_dev(C[:, 0]), _dev(C[:, 1]), _dev(P[:, 0]), _dev(P[:, 1]), _dev(pb.h), pb.R,
+            bbox or pb.bbox)
+    ctx.assemble(kind or pb.kernel, prec)
+    return ctx
+
+
+def _assembly_case(name):
+    if name == "franke":
+        return dg.config_franke(seed=1, N=5000, M=500)
+    if name == "terrain":
+        return dg.config_terrain(seed=2, N=20000, M=2000)
+    if name == "clustered":
+        return dg.config_small(3, 6000, 400, clustered=True)
+    if name == "ragged":
+        return dg.config_small(4, 777, 61, K=9.0)
+    if name == "multipass":        # ~144 candidates per cell neighbourhood: several Gram passes
+        return dg.config_small(5, 3000, 400, K=60.0)
+    if name == "dense_cell":       # > 256 points per cell: several work items per cell
+        pb = dg.config_small(6, 8000, 100, K=20.0)
+        pb.points[:3000] = 0.5 + 0.01 * np.random.default_rng(0).random((3000, 2))
+        return pb
+    if name == "tiny":
+        return dg.config_small(7, 5, 3, K=2.0)
+    if name == "single":
+        pb = dg.config_small(8, 1, 1, K=1.0)
+        pb.centres[:] = pb.points[0] + 0.01
+        return pb
+    raise KeyError(name)
+
+
+ASSEMBLY_CASES = ["franke", "terrain", "clustered", "ragged", "multipass", "dense_cell", "tiny",
+                  "single"]
+
+
+@pytest.mark.parametrize("case", ASSEMBLY_CASES)
+@pytest.mark.parametrize("kind", ["w31", "w33"])
+def test_assembly_fp64_matches_oracle(case, kind):
+    pb = _assembly_case(case)
+    ctx = _binned(pb, kind)
+    row, col, val, b, sup = [t.cpu().numpy() for t in ctx.export_upper()]
+    A = O.design_matrix(pb.points, pb.centres, pb.R, kind)
+    B, bref = O.normal_system(A, pb.h)
+    Bu = scipy.sparse.triu(B).tocoo()
+    ref = {(int(i), int(j)): v for i, j, v in zip(Bu.row, Bu.col, Bu.data) if v != 0.0}
+    got = {}
+    for i, j, v in zip(row, col, val):
+        i, j = (int(i), int(j)) if i <= j else (int(j), int(i))
+        got[(i, j)] = got.get((i, j), 0.0) + float(v)
+    assert set(got) == set(ref)                              # identical sparsity pattern
+    scale = max(abs(v) for v in ref.values()) if ref else 1.0
+    err = max((abs(got[k] - ref[k]) for k in ref), default=0.0) / scale
+    assert err <= 1e-12, err
+    assert O.rel_err(b, bref) <= 1e-12
+    np.testing.assert_array_equal(sup, O.support_counts(A))   # integer: exact
+    ctx.close()
+
+
+@pytest.mark.parametrize("case", ["franke", "terrain", "multipass"])
+def test_assembly_fp32_within_fp32_rounding(case):
+    pb = _assembly_case(case)
+    ctx = _binned(pb, "w31", "fp32_refine")
+    row, col, val, b, sup = [t.cpu().numpy() for t in ctx.export_upper()]
+    A = O.design_matrix(pb.points, pb.centres, pb.R, "w31")
+    B, bref = O.normal_system(A, pb.h)
+    # each stored pair appears once, as (row, col) or (col, row) in the caller's order
+    Bg = scipy.sparse.coo_matrix((val, (row, col)), shape=B.shape).toarray()
+    Bg = Bg + Bg.T - np.diag(np.diag(Bg))
+    # FP32 products and sums of about 100 terms: relative error well below 1e-5 of max|B|
+    assert O.rel_err(Bg, B.toarray()) <= 2e-6
+    assert O.rel_err(b, bref) <= 1e-12                        # b is accumulated in FP64
+    np.testing.assert_array_equal(sup, O.support_counts(A))
+    ctx.close()
+
+
+SOLVE_CASES = [("franke", "w30"), ("franke", "w31"), ("franke", "w32"), ("franke", "w33"),
+               ("terrain", "w31"), ("clustered", "w31"), ("ragged", "w31"),
+               ("multipass", "w31"), ("dense_cell", "w31")]
+
+
+def _kappa(info_ref):
+    """Condition number of the Jacobi-scaled normal matrix on the unpinned centres."""
+    free = ~info_ref["pinned"]
+    B = info_ref["B"].toarray()[free][:, free]
+    if B.size == 0:
+        return 1.0
+    d = np.sqrt(np.diag(B))
+    ev = np.linalg.eigvalsh(B / d[:, None] / d[None, :])
+    return float(ev[-1] / ev[0])
+
+
+@pytest.mark.parametrize("case,kind", SOLVE_CASES)
+def test_fit_fp64_matches_oracle(case, kind):
+    pb = _assembly_case(case)
+    c_ref, info_ref = O.fit(pb.points, pb.h, pb.centres, pb.R, kind, method="cholesky")
+    c, info, ctx = pkg.fit(pb.points, pb.h, pb.centres, pb.R, kind, prec="fp64", tol=1e-14,
+                           maxit=200000)
+    c = c.cpu().numpy()
+    assert info["pinned"] == int(info_ref["pinned"].sum())
+    assert np.all(c[info_ref["pinned"]] == 0.0)
+    assert O.rel_err(c, c_ref) <= max(FP64_BAR, 1e-14 * _kappa(info_ref))
+    A = info_ref["A"]
+    assert O.rel_err(A @ c, A @ c_ref) <= FP64_BAR          # f at the data points
+    f = ctx.eval_grid(torch.as_tensor(c, device="cuda"), 65, 65).cpu().numpy()
+    f_ref = O.evaluate_grid(c_ref, pb.centres, pb.R, kind, 65)
+    assert O.rel_err(f, f_ref) <= FP64_BAR
+    ctx.close()
+
+
+@pytest.mark.parametrize("case,kind", [("franke", "w31"), ("terrain", "w31"), ("franke", "w33"),
+                                       ("clustered", "w31"), ("ragged", "w30")])
+def test_fit_fp32_refine_surface_matches_oracle(case, kind):
+    pb = _assembly_case(case)
+    c_ref, _ = O.fit(pb.points, pb.h, pb.centres, pb.R, kind, method="cholesky")
+    c, info, ctx = pkg.fit(pb.points, pb.h, pb.centres, pb.R, kind, prec="fp32_refine",
+                           tol=1e-10, maxit=100000)
+    assert info["refinements"] >= 1
+    f = ctx.eval_grid(c, 65, 65).cpu().numpy()
+    f_ref = O.evaluate_grid(c_ref, pb.centres, pb.R, kind, 65)
+    assert O.rel_err(f, f_ref) <= MIXED_BAR
+    ctx.close()
+
+
+def test_franke_20k_2k_full_parity():
+    """The small workload at its full size: N = 20,000, M = 2,000, 256 x 256 grid."""
+    pb = dg.config_franke()
+    c_ref, _ = O.fit(pb.points, pb.h, pb.centres, pb.R, pb.kernel, method="cholesky")
+    f_ref = O.evaluate_grid(c_ref, pb.centres, pb.R, pb.kernel, 256)
+    c, info, ctx = pkg.fit(pb.points, pb.h, pb.centres, pb.R, pb.kernel, prec="fp64", tol=1e-14)
+    assert O.rel_err(c.cpu().numpy(), c_ref) <= FP64_BAR
+    assert O.rel_err(ctx.eval_grid(c, 256, 256).cpu().numpy(), f_ref) <= FP64_BAR
+    # the data points themselves through rbf_eval
+    P = _dev(pb.points)
+    fP = ctx.eval(c, P[:, 0].contiguous(), P[:, 1].contiguous()).cpu().numpy()
+    A = O.design_matrix(pb.points, pb.centres, pb.R, pb.kernel)
+    assert O.rel_err(fP, A @ c_ref) <= FP64_BAR
+    ctx.close()
+    c2, _, ctx2 = pkg.fit(pb.points, pb.h, pb.centres, pb.R, pb.kernel, prec="fp32_refine",
+                          tol=1e-10)
+    assert O.rel_err(ctx2.eval_grid(c2, 256, 256).cpu().numpy(), f_ref) <= MIXED_BAR
+    ctx2.close()
+
+
+def test_pinned_centre_far_from_data():
+    pb = dg.config_small(17, 2000, 200)
+    C = pb.centres.copy()
+    C[5] = (0.5, 0.5)
+    keep = np.hypot(pb.points[:, 0] - 0.5, pb.points[:, 1] - 0.5) > 2 * pb.R
+    P, h = pb.points[keep], pb.h[keep]
+    c_ref, info_ref = O.fit(P, h, C, pb.R, pb.kernel)
+    for prec in ("fp64", "fp32_refine"):
+        c, info, ctx = pkg.fit(P, h, C, pb.R, pb.kernel, prec=prec, tol=1e-13)
+        c = c.cpu().numpy()
+        assert info["pinned"] == int(info_ref["pinned"].sum()) >= 1
+        assert c[5] == 0.0
+        if prec == "fp64":
+            assert O.rel_err(c, c_ref) <= FP64_BAR
+        ctx.close()
+
+
+def test_warm_start_and_determinism():
+    pb = dg.config_franke(seed=9, N=8000, M=800)
+    c_ref, _ = O.fit(pb.points, pb.h, pb.centres, pb.R, pb.kernel)
+    ctx = _binned(pb)
+    c1, i1 = ctx.solve(tol=1e-14)
+    c2, i2 = ctx.solve(tol=1e-14)
+    assert O.rel_err(c1.cpu().numpy(), c2.cpu().numpy()) <= 1e-12
+    c0 = torch.as_tensor(c_ref * (1 + 1e-3), device="cuda")
+    c3, i3 = ctx.solve(tol=1e-14, c0=c0)
+    assert i3["iterations"] < i1["iterations"]
+    assert O.rel_err(c3.cpu().numpy(), c_ref) <= FP64_BAR
+    ctx.close()
+
+
+def test_points_outside_bbox_are_clamped_correctly():
+    pb = dg.config_small(12, 3000, 300)
+    # fit on a smaller box than the data: outside items go to the edge cells
+    c_ref, _ = O.fit(pb.points, pb.h, pb.centres, pb.R, pb.kernel)
+    c, _, ctx = pkg.fit(pb.points, pb.h, pb.centres, pb.R, pb.kernel, bbox=(0.2, 0.2, 0.8, 0.8),
+                        tol=1e-14)
+    assert O.rel_err(c.cpu().numpy(), c_ref) <= FP64_BAR
+    ctx.close()
+
+
+def test_limit_and_argument_errors():
+    pb = dg.config_small(13, 2000, 2000, K=2000.0)       # every centre in every neighbourhood
+    ctx = pkg.Context()
+    with pytest.raises(pkg.RBFError) as e:
+        ctx.bin(_dev(pb.centres[:, 0]), _dev(pb.centres[:, 1]), _dev(pb.points[:, 0]),
+                _dev(pb.points[:, 1]), _dev(pb.h), pb.R)
+    assert "RBF_ERR_LIMIT" in str(e.value)
+    h = pb.h.copy()
+    h[3] = np.nan
+    with pytest.raises(pkg.RBFError) as e:
+        ctx.bin(_dev(pb.centres[:50, 0]), _dev(pb.centres[:50, 1]), _dev(pb.points[:, 0]),
+                _dev(pb.points[:, 1]), _dev(h), 0.1)
+    assert "RBF_ERR_ARG" in str(e.value)
+    with pytest.raises(pkg.RBFError):
+        ctx.assemble("w31", "fp64")          # no successful bin
+    ctx.close()
+
+
+def test_maxit_reports_not_converged():
+    pb = dg.config_franke(seed=4, N=5000, M=500)
+    ctx = _binned(pb)
+    c, info = ctx.solve(tol=1e-14, maxit=5, raise_on_fail=False)
+    assert info["status"] == 4 and info["iterations"] == 5
+    ctx.close()
+
+
+@pytest.mark.slow
+def test_terrain_full_size_properties():
+    """The clustered 1M x 100k workload at full size: properties the oracle checks one
+    entry at a time (sampled B, b and support counts, the FP64 normal residual, sampled
+    surface values), and the FP32+refinement surface against the FP64 surface."""
+    pb = dg.config_terrain()
+    so = O.SampledOracle(pb.points, pb.h, pb.centres, pb.R, pb.kernel)
+    rng = np.random.default_rng(0)
+    ctx = _binned(pb)
+    row, col, val, b, sup = [t.cpu().numpy() for t in ctx.export_upper()]
+    js = rng.choice(pb.M, 40, replace=False)
+    for j in js:
+        assert sup[j] == so.support(j)
+        assert abs(b[j] - so.b_entry(j)) <= 1e-12 * np.abs(b).max()
+    pick = rng.choice(len(val), 60, replace=False)
+    for t in pick:
+        assert abs(val[t] - so.B_entry(row[t], col[t])) <= 1e-12 * np.abs(val).max()
+    c, info = ctx.solve(tol=1e-12)
+    cn = c.cpu().numpy()
+    res = np.array([so.normal_residual(cn, j) for j in js[:20]])
+    assert np.abs(res).max() <= 1e-9 * np.abs(b).max()
+    f = ctx.eval_grid(c, 1024, 1024).cpu().numpy()
+    gx = np.linspace(0, 1, 1024)
+    for _ in range(30):
+        i, j = rng.integers(0, 1024, 2)
+        assert abs(f[i, j] - so.f(cn, (gx[j], gx[i]))) <= 1e-12 * np.abs(f).max()
+    ctx.close()
+    ctx32 = _binned(pb, prec="fp32_refine")
+    c32, info32 = ctx32.solve(tol=1e-10)
+    f32 = ctx32.eval_grid(c32, 1024, 1024).cpu().numpy()
+    assert O.rel_err(f32, f) <= MIXED_BAR
+    ctx32.close()

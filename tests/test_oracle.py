@@ -253,3 +253,24 @@ def test_table4_synthetic_mean_absolute_error(golden_dir):
 def test_rel_err_definition():
     assert O.rel_err([1.0, 2.0], [1.0, 4.0]) == 0.5
     assert O.rel_err([0.0], [0.0]) == 0.0
+
+
+def test_sampled_oracle_matches_full_system():
+    pb = dg.config_terrain(N=6000, M=600)
+    A = O.design_matrix(pb.points, pb.centres, pb.R, pb.kernel)
+    B, b = O.normal_system(A, pb.h)
+    c, _ = O.fit(pb.points, pb.h, pb.centres, pb.R, pb.kernel)
+    cpert = c + 1e-3 * np.random.default_rng(1).standard_normal(pb.M)
+    res = O.normal_residual(A, pb.h, cpert)
+    so = O.SampledOracle(pb.points, pb.h, pb.centres, pb.R, pb.kernel)
+    Bd = B.toarray()
+    sup = O.support_counts(A)
+    F = A @ cpert
+    for j in [0, 7, 123, 599]:
+        assert abs(so.b_entry(j) - b[j]) <= 1e-12 * max(1.0, abs(b[j]))
+        assert so.support(j) == sup[j]
+        assert abs(so.normal_residual(cpert, j) - res[j]) <= 1e-10 * np.abs(res).max()
+        for k in [j, (j + 1) % 600, (j + 37) % 600]:
+            assert abs(so.B_entry(j, k) - Bd[j, k]) <= 1e-13 * Bd.max()
+    for i in [0, 5, 4000]:
+        assert abs(so.f(cpert, pb.points[i]) - F[i]) <= 1e-12 * np.abs(F).max()
