@@ -1,0 +1,369 @@
+#!/usr/bin/env python3
+"""Benchmark of the CS-RBF least-squares fit on GB300: points fitted per second.
+
+One step = the whole hot path on one synthetic workload: bin (a), fused assembly of
+B = A^T A and b = A^T h (b, c), Jacobi-PCG solve (d) -- FP32 inner CG with FP64
+matrix-free refinement, or plain FP64 -- and evaluation on the output grid (e).
+Workload (default): the clustered terrain, N = 1,000,000 points (64-Gaussian mixture
+over a 20 % uniform floor), M = 100,000 Halton centres, Wendland phi_{3,1}, about 30
+centres per support, 1024 x 1024 output grid, seed = rank.
+
+value      = N / device time per step, inputs resident in HBM, L2 flushed before each
+             step (a 512 MiB write).
+e2e        = the same through the public API with host inputs: pinned host -> device
+             copies of points, heights and centres, the step, device -> host copies of c
+             and of the surface f, all inside the timed region.
+roofline   = the solver's SpMV kernel (the dominant kernel of the step), algorithmic
+             bytes per launch / its mean duration measured with CUDA events on the
+             launching stream, against the measured HBM copy bandwidth.
+Accuracy   = the surface of the timed path against a tightly converged FP64 solve of the
+             same workload (``accuracy`` key), which the GPU parity tests tie to the oracle.
+
+--impl reference runs the CPU FP64 oracle (tests' reference implementation) on a bounded
+sample of the same workload instead. Multi-GPU (torchrun): independent replicas (the fit of
+one system does not shard), weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="fp32_refine", choices=["fp32_refine", "fp64"])
+    ap.add_argument("--tol", type=float, default=1e-9)
+    ap.add_argument("--N", type=int, default=1_000_000)
+    ap.add_argument("--M", type=int, default=100_000)
+    ap.add_argument("--grid", type=int, default=1024)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--quiet-extra", action="store_true")
+    return ap.parse_args()
+
+
+def env_rank():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+# ----------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ----------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 8:
+                continue
+            try:
+                sm.append(float(p[0]))
+                smax = float(p[1])
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if p[4 + k].lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------------------
+# the CPU FP64 oracle on a bounded sample (cpu_baseline and --impl reference)
+# ----------------------------------------------------------------------------------------
+def oracle_sample(seed: int, N: int, M: int, tol: float):
+    """Time the oracle fit + grid evaluation on a same-statistics sample (N/M = 10, K = 30)."""
+    import datagen as dg
+    import oracle as O
+    pb = dg.config_terrain(seed=seed, N=N, M=M, eval_n=max(32, int(1024 * (N / 1e6) ** 0.5)))
+    t0 = time.perf_counter()
+    c, _ = O.fit(pb.points, pb.h, pb.centres, pb.R, pb.kernel, tol=tol)
+    O.evaluate_grid(c, pb.centres, pb.R, pb.kernel, pb.eval_n)
+    return time.perf_counter() - t0, pb
+
+
+def run_reference(args):
+    rank, _, world = env_rank()
+    if rank != 0:
+        return
+    N, M = 50_000, 5_000
+    times = []
+    for k in range(args.warmup + args.steps):
+        t, pb = oracle_sample(seed=k, N=N, M=M, tol=args.tol)
+        if k >= args.warmup:
+            times.append(t)
+    sec = statistics.mean(times)
+    value = N / sec
+    sample = (f"oracle fit (kd-tree, scipy A^T A, Jacobi-PCG tol {args.tol:g}) + {pb.eval_n}^2 grid "
+              f"evaluation on the terrain workload at N={N}, M={M} (same N/M and K as 1M x 100k)")
+    line = {"impl": "reference", "metric": "points fitted/s at 1e-6 rel. error", "value": value,
+            "unit": "points/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "terrain 1M points x 100k centres, phi_3,1, K=30 (CPU sample)",
+                       "N": N, "M": M},
+            "cpu_baseline": {"value": value, "unit": "points/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------------------
+# the GPU path
+# ----------------------------------------------------------------------------------------
+def main():
+    args = parse()
+    if args.impl == "reference":
+        os.environ.setdefault("OMP_NUM_THREADS", "1")
+        os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import datagen as dg
+    import paper_1806_07884_gb300 as pkg
+
+    rank, local, world = env_rank()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+
+    pb = dg.config_terrain(seed=rank, N=args.N, M=args.M, eval_n=args.grid)
+    N, M, n = pb.N, pb.M, args.grid
+    host = {k: torch.as_tensor(np.ascontiguousarray(v)).pin_memory() for k, v in
+            dict(cx=pb.centres[:, 0], cy=pb.centres[:, 1], px=pb.points[:, 0],
+                 py=pb.points[:, 1], h=pb.h).items()}
+    d = {k: v.to(dev) for k, v in host.items()}
+    cbuf = torch.empty(M, dtype=torch.float64, device=dev)
+    fbuf = torch.empty((n, n), dtype=torch.float64, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    ctx = pkg.Context(local)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(inp, prec=args.prec, tol=args.tol):
+        ctx.bin(inp["cx"], inp["cy"], inp["px"], inp["py"], inp["h"], pb.R, pb.bbox)
+        ctx.assemble(pb.kernel, prec)
+        c, info = ctx.solve(tol=tol, maxit=20000, out=cbuf)
+        ctx.eval_grid(c, n, n, out=fbuf)
+        return info
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # ---- warm-up
+    for _ in range(args.warmup):
+        flush.zero_()
+        info = step(d)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, device-resident inputs, L2 flushed before each step
+    sampler = ClockSampler(local)
+    sampler.start()
+    launches0 = ctx.launch_count()
+    barrier()
+    torch.cuda.synchronize()
+    step_ms = []
+    infos = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        infos.append(step(d))
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    barrier()
+    launches = ctx.launch_count() - launches0
+    clocks = sampler.stop()
+    ms = statistics.mean(step_ms)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * N / (ms * 1e-3)
+
+    # ---- per-phase split of one step (not part of the timed number)
+    phases = {}
+    flush.zero_()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    ev[0].record(stream)
+    ctx.bin(d["cx"], d["cy"], d["px"], d["py"], d["h"], pb.R, pb.bbox)
+    ev[1].record(stream)
+    ctx.assemble(pb.kernel, args.prec)
+    ev[2].record(stream)
+    c, info = ctx.solve(tol=args.tol, maxit=20000, out=cbuf)
+    ev[3].record(stream)
+    ctx.eval_grid(c, n, n, out=fbuf)
+    ev[4].record(stream)
+    torch.cuda.synchronize()
+    for k, name in enumerate(["bin", "assemble", "solve", "eval"]):
+        phases[name] = round(ev[k].elapsed_time(ev[k + 1]), 4)
+
+    # ---- roofline of the dominant kernel: the solver's SpMV, timed on its stream
+    lay = ctx.layout()
+    vb = lay["value_bytes"]
+    ncell = lay["gx"] * lay["gy"]
+    spmv_bytes = lay["nvals"] * vb + 3 * M * vb + ncell * (4 + 24 + 8)
+    reps = 200
+    ctx.bench_spmv(10)
+    s0 = torch.cuda.Event(enable_timing=True)
+    s1 = torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    ctx.bench_spmv(reps)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    spmv_ms = s0.elapsed_time(s1) / reps
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    achieved = spmv_bytes / (spmv_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": f"k_spmv<{'float' if vb == 4 else 'double'}>",
+                "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(achieved / hbm, 4), "traffic": None,
+                "algorithmic_bytes": spmv_bytes, "launch_ms": round(spmv_ms, 5),
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+
+    # ---- accuracy: this path's surface against a tight FP64 solve of the same workload
+    f_fast = fbuf.clone()
+    acc = {}
+    fp64 = None
+    if not args.no_fp64_compare:
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        info64 = step(d, prec="fp64", tol=args.tol)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        fp64_ms = t0.elapsed_time(t1)
+        fp64 = {"value": N / (fp64_ms * 1e-3), "ms_per_step": round(fp64_ms, 3),
+                "iterations": info64["iterations"], "tol": args.tol}
+        step(d, prec="fp64", tol=1e-13)
+        f_ref = fbuf.clone()
+        err = float((f_fast - f_ref).abs().max() / f_ref.abs().max())
+        acc = {"rel_err_f_vs_fp64_tight": err, "bar": 1e-6, "ok": err <= 1e-6}
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        c_host = torch.empty(M, dtype=torch.float64).pin_memory()
+        f_host = torch.empty((n, n), dtype=torch.float64).pin_memory()
+        h2d = sum(v.numel() * v.element_size() for v in host.values())
+        d2h = c_host.numel() * 8 + f_host.numel() * 8
+        e_ms = []
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            dd = {k: v.to(dev, non_blocking=True) for k, v in host.items()}
+            step(dd)
+            c_host.copy_(cbuf, non_blocking=True)
+            f_host.copy_(fbuf, non_blocking=True)
+            e1.record(stream)
+            e1.synchronize()
+            e_ms.append(e0.elapsed_time(e1))
+        ems = statistics.mean(e_ms)
+        if world > 1:
+            t = torch.tensor([ems], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        e2e = {"value": world * N / (ems * 1e-3), "unit": "points/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": round(ems, 3)}
+
+    # ---- CPU baseline: the oracle on a bounded sample (rank 0, single GPU only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        Ns, Ms = 100_000, 10_000
+        t, pbs = oracle_sample(seed=0, N=Ns, M=Ms, tol=args.tol)
+        cpu = {"value": Ns / t, "unit": "points/s", "cores": 1, "kind": "oracle",
+               "sample": f"oracle fit + {pbs.eval_n}^2 grid eval of the terrain workload at "
+                         f"N={Ns}, M={Ms} (same N/M, K), {t:.1f} s single-threaded"}
+
+    if rank == 0:
+        last = infos[-1]
+        line = {
+            "metric": "points fitted/s at 1e-6 rel. error",
+            "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if args.prec == "fp32_refine" else "f64",
+            "data": "synthetic",
+            "config": {"workload": f"terrain {N} points x {M} Halton centres, Wendland phi_3,1, "
+                                   f"K=30, {n}x{n} eval grid",
+                       "N": N, "M": M, "kernel": pb.kernel, "prec": args.prec, "tol": args.tol,
+                       "warm_start": "none", "l2": "flushed before each step (512 MiB write)",
+                       "parallelism": f"replicas x{world}"},
+            "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu,
+            "clocks": clocks, "accuracy": acc, "fp64_path": fp64, "phases_ms": phases,
+            "solver": {"iterations": last["iterations"], "refinements": last["refinements"],
+                       "rel_residual": last["rel_residual"], "pinned": last["pinned"]},
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -147,6 +147,16 @@ rbf_status rbf_export_upper(rbf_ctx* ctx, int64_t cap, int32_t* row, int32_t* co
                             double* val, double* bvec, int32_t* support, int64_t* nnz,
                             void* stream);
 
+/* Diagnostics: number of kernels this context has launched since rbf_create (kernels
+ * inside replayed CUDA graphs included). HOST output. */
+rbf_status rbf_get_launch_count(const rbf_ctx* ctx, int64_t* launches);
+
+/* Diagnostics / timing: launch the solver's SpMV kernel y = B x (Section 4's y = Q x on
+ * this library's cell-blocked symmetric storage) `reps` times on `stream`, on the solver's
+ * own workspace vectors, exactly as one CG iteration launches it. Requires a preceding
+ * rbf_solve on this context (so the workspace exists). Asynchronous. */
+rbf_status rbf_bench_spmv(rbf_ctx* ctx, int reps, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

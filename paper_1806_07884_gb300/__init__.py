@@ -159,6 +159,16 @@ class Context:
                                             C.byref(gy)), "rbf_get_layout")
         return dict(nvals=nv.value, value_bytes=vb.value, gx=gx.value, gy=gy.value)
 
+    def launch_count(self) -> int:
+        n = C.c_int64()
+        self._check(self.lib.rbf_get_launch_count(self._h, C.byref(n)), "rbf_get_launch_count")
+        return n.value
+
+    def bench_spmv(self, reps: int, stream=None):
+        """Launch the solver's SpMV kernel reps times (timing hook; needs a prior solve)."""
+        self._check(self.lib.rbf_bench_spmv(self._h, int(reps), self._stream(stream)),
+                    "rbf_bench_spmv")
+
     def export_upper(self, stream=None):
         """The assembled upper triangle of B as COO (caller's centre indices), plus b and the
         support counts, as CUDA tensors."""

@@ -43,6 +43,8 @@ SIGNATURES = {
     "rbf_eval_grid": (_I, [_P, _P, _I, _I, C.POINTER(_D), _P, _P]),
     "rbf_get_layout": (_I, [_P, C.POINTER(_I64), C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)]),
     "rbf_export_upper": (_I, [_P, _I64, _P, _P, _P, _P, _P, C.POINTER(_I64), _P]),
+    "rbf_get_launch_count": (_I, [_P, C.POINTER(_I64)]),
+    "rbf_bench_spmv": (_I, [_P, _I, _P]),
 }
 
 _lib = None

@@ -163,6 +163,7 @@ rbf_status rbf_bin(rbf_ctx* ctx, const double* cx, const double* cy, int64_t M, 
     if (!ctx) return RBF_ERR_ARG;
     ctx->binned = false;
     ctx->assembled = false;
+    ctx->solved = false;
     if (!cx || !cy || !px || !py || !h || !bbox)
         return set_err(ctx, RBF_ERR_ARG, "null pointer argument");
     if (M < 1 || N < 1 || M > (int64_t(1) << 30) || N > (int64_t(1) << 30))
@@ -204,6 +205,7 @@ rbf_status rbf_assemble(rbf_ctx* ctx, rbf_kernel kernel, rbf_prec prec, void* st
     DeviceGuard dg(ctx->device);
     ctx->kernel = kernel;
     ctx->prec = prec;
+    ctx->solved = false;
     rbf_status s = assemble_run(ctx, kernel, prec, as_stream(stream));
     ctx->assembled = s == RBF_OK;
     return s;
@@ -255,6 +257,20 @@ rbf_status rbf_export_upper(rbf_ctx* ctx, int64_t cap, int32_t* row, int32_t* co
     if (!nnz || cap < 0 || (cap > 0 && (!row || !col || !val))) return set_err(ctx, RBF_ERR_ARG, "bad arguments");
     DeviceGuard dg(ctx->device);
     return export_upper_run(ctx, cap, row, col, val, bvec, support, nnz, as_stream(stream));
+}
+
+rbf_status rbf_get_launch_count(const rbf_ctx* ctx, int64_t* launches) {
+    if (!ctx || !launches) return RBF_ERR_ARG;
+    *launches = ctx->launches;
+    return RBF_OK;
+}
+
+rbf_status rbf_bench_spmv(rbf_ctx* ctx, int reps, void* stream) {
+    if (!ctx) return RBF_ERR_ARG;
+    if (!ctx->solved || !ctx->assembled) return set_err(ctx, RBF_ERR_ARG, "rbf_bench_spmv before rbf_solve");
+    if (reps < 0) return set_err(ctx, RBF_ERR_ARG, "reps < 0");
+    DeviceGuard dg(ctx->device);
+    return bench_spmv_run(ctx, reps, as_stream(stream));
 }
 
 }  // extern "C"

@@ -372,6 +372,7 @@ rbf_status launch_assemble(rbf_ctx* ctx, cudaStream_t st, int npad) {
     kfn<<<ctx->nwork, kThreads, sm, st>>>(view(ctx), ctx->work.as<int4>(), npad, ctx->bvals.as<T>(),
                                           ctx->bvec.as<double>(), ctx->support.as<int>());
     RBF_CUDA_TRY(cudaGetLastError());
+    ctx->launches += 1;
     return RBF_OK;
 }
 
@@ -384,6 +385,7 @@ rbf_status launch_residual(rbf_ctx* ctx, const double* c, double* r, bool count,
     kfn<<<ctx->nwork, kThreads, sm, st>>>(view(ctx), ctx->work.as<int4>(), npad, c, r,
                                           count ? ctx->support.as<int>() : nullptr);
     RBF_CUDA_TRY(cudaGetLastError());
+    ctx->launches += 1;
     return RBF_OK;
 }
 

@@ -117,6 +117,7 @@ rbf_status scan_impl(rbf_ctx* ctx, const TI* in, TO* out, int n, cudaStream_t st
     k_scan_bsum<TO><<<1, kScanThreads, 0, st>>>(bsum, nb);
     k_scan_apply<TI, TO><<<nb, kScanThreads, 0, st>>>(in, n, bsum, out);
     RBF_CUDA_TRY(cudaGetLastError());
+    ctx->launches += 3;
     return RBF_OK;
 }
 
@@ -292,6 +293,7 @@ rbf_status bin_run(rbf_ctx* ctx, const double* cx, const double* cy, const doubl
                                         ctx->seg.as<RowSeg>(), ctx->rbsize.as<int64_t>(),
                                         ctx->wcount.as<int>(), stats);
     RBF_CUDA_TRY(cudaGetLastError());
+    ctx->launches += 5;
     if ((s = scan_i64(ctx, ctx->rbsize.as<int64_t>(), ctx->rboff.as<int64_t>(), nc, st)) != RBF_OK)
         return s;
     if ((s = scan_i32(ctx, ctx->wcount.as<int>(), ctx->wstart.as<int>(), nc, st)) != RBF_OK) return s;
@@ -317,6 +319,7 @@ rbf_status bin_run(rbf_ctx* ctx, const double* cx, const double* cy, const doubl
     k_work_fill<<<div_up(nc, T), T, 0, st>>>(nc, ctx->pstart.as<int>(), ctx->wstart.as<int>(),
                                              ctx->work.as<int4>());
     RBF_CUDA_TRY(cudaGetLastError());
+    ctx->launches += 1;
 #undef ENS
     return RBF_OK;
 }

@@ -93,6 +93,7 @@ rbf_status eval_points_run(rbf_ctx* ctx, const double* c, const double* qx, cons
     if (s != RBF_OK) return s;
     const Binned bd = view(ctx);
     launch_gather_sorted(c, bd.cperm, ctx->csort.as<double>(), ctx->M, st);
+    ctx->launches += 1;
     if (Q <= 0) return RBF_OK;
     const double* cs = ctx->csort.as<double>();
     const int gb = eval_grid_size(Q);
@@ -103,6 +104,7 @@ rbf_status eval_points_run(rbf_ctx* ctx, const double* c, const double* qx, cons
         default: k_eval_points<3><<<gb, 256, 0, st>>>(bd, cs, qx, qy, Q, f); break;
     }
     RBF_CUDA_TRY(cudaGetLastError());
+    ctx->launches += 1;
     return RBF_OK;
 }
 
@@ -124,6 +126,7 @@ rbf_status eval_grid_run(rbf_ctx* ctx, const double* c, int nx, int ny, const do
         default: k_eval_grid<3><<<gb, 256, 0, st>>>(bd, cs, nx, ny, x0, y0, x1, y1, sx, sy, f); break;
     }
     RBF_CUDA_TRY(cudaGetLastError());
+    ctx->launches += 2;
     return RBF_OK;
 }
 
@@ -141,6 +144,7 @@ rbf_status export_upper_run(rbf_ctx* ctx, int64_t cap, int32_t* row, int32_t* co
                                                        ctx->support.as<int>(), cap, row, col, val,
                                                        bvec, support, counter);
     RBF_CUDA_TRY(cudaGetLastError());
+    ctx->launches += 1;
     unsigned long long* h = static_cast<unsigned long long*>(ctx->hpinned);
     RBF_CUDA_TRY(cudaMemcpyAsync(h, counter, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
     RBF_CUDA_TRY(cudaStreamSynchronize(st));

@@ -60,6 +60,8 @@ struct rbf_ctx {
     rbf_buf scal;              // device scalars (struct CgScalars)
     rbf_buf csort;             // [M] FP64 coefficients in sorted order (evaluation)
     void* hpinned = nullptr;   // pinned host scratch for scalar read-back (4 KiB)
+    int64_t launches = 0;      // kernels launched by this context (graph nodes included)
+    bool solved = false;       // solver workspace exists
     cudaStream_t capture_stream = nullptr;   // private stream used only to capture graphs
 
     // CG graphs: [precision: 0 FP64, 1 FP32][chunk = 8 << k, k = 0..5]
@@ -104,6 +106,8 @@ rbf_status eval_grid_run(rbf_ctx* ctx, const double* c, int nx, int ny, const do
                          double* f, cudaStream_t st);
 rbf_status export_upper_run(rbf_ctx* ctx, int64_t cap, int32_t* row, int32_t* col, double* val,
                             double* bvec, int32_t* support, int64_t* nnz, cudaStream_t st);
+
+rbf_status bench_spmv_run(rbf_ctx* ctx, int reps, cudaStream_t st);
 
 // permutation helpers (rbf_solve.cu)
 void launch_gather_sorted(const double* c_orig, const int* cperm, double* c_sorted, int M,

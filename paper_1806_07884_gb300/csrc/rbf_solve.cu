@@ -357,6 +357,13 @@ int spmv_grid(const rbf_ctx* ctx) { return div_up(ctx->g.ncell, kSpmvWarps); }
 int vec_grid(const rbf_ctx* ctx) { return std::min(div_up(ctx->M, kVecThreads), 152 * 8); }
 
 // CUDA graph holding `chunk` CG iterations for precision T (cached per context).
+// Graph chunk sizes are powers of two from 8 to 256.
+int chunk_of(const rbf_ctx*, int chunk) {
+    int ck = 0;
+    while ((8 << ck) < chunk && ck < 5) ++ck;
+    return 8 << ck;
+}
+
 template <typename T>
 rbf_status cg_graph(rbf_ctx* ctx, int chunk, cudaGraphExec_t* out) {
     const int slot = sizeof(T) == 8 ? 0 : 1;
@@ -427,6 +434,7 @@ rbf_status run_cg(rbf_ctx* ctx, const TB* b, double bscale, bool use_x0, double 
     k_cg_init<T, TB><<<vec_grid(ctx), kVecThreads, 0, st>>>(M, b, bscale, use_x0 ? v.q : nullptr,
                                                             v.r, v.z, v.p, v.dinv, sc, part);
     RBF_CUDA_TRY(cudaGetLastError());
+    ctx->launches += use_x0 ? 2 : 1;
     CgScalars* hs = static_cast<CgScalars*>(ctx->hpinned);
     RBF_CUDA_TRY(cudaMemcpyAsync(hs, sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
     RBF_CUDA_TRY(cudaStreamSynchronize(st));
@@ -439,6 +447,7 @@ rbf_status run_cg(rbf_ctx* ctx, const TB* b, double bscale, bool use_x0, double 
         rbf_status s = cg_graph<T>(ctx, chunk, &ex);
         if (s != RBF_OK) return s;
         RBF_CUDA_TRY(cudaGraphLaunch(ex, st));
+        ctx->launches += 3 * chunk_of(ctx, chunk);
         RBF_CUDA_TRY(cudaMemcpyAsync(hs, sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
         RBF_CUDA_TRY(cudaStreamSynchronize(st));
         if (hs->state != kRunning) break;
@@ -474,6 +483,23 @@ void launch_scatter_orig(const double* c_sorted, const int* cperm, double* c_ori
 
 size_t cg_scalars_bytes() { return sizeof(CgScalars); }
 
+rbf_status bench_spmv_run(rbf_ctx* ctx, int reps, cudaStream_t st) {
+    const Binned bd = view(ctx);
+    for (int k = 0; k < reps; ++k) {
+        if (ctx->prec == RBF_FP64)
+            k_spmv<double><<<spmv_grid(ctx), kSpmvWarps * 32, 0, st>>>(
+                bd, ctx->bvals.as<double>(), ctx->p.as<double>(), ctx->q.as<double>(),
+                ctx->dinv.as<double>(), nullptr, nullptr);
+        else
+            k_spmv<float><<<spmv_grid(ctx), kSpmvWarps * 32, 0, st>>>(
+                bd, ctx->bvals.as<float>(), ctx->p32.as<float>(), ctx->q32.as<float>(),
+                ctx->dinv32.as<float>(), nullptr, nullptr);
+    }
+    RBF_CUDA_TRY(cudaGetLastError());
+    ctx->launches += reps;
+    return RBF_OK;
+}
+
 static rbf_status finish_status(rbf_ctx* ctx, int state) {
     if (state == kConverged) return RBF_OK;
     if (state == kBreakdown) return set_err(ctx, RBF_ERR_BREAKDOWN, "CG breakdown (p^T B p <= 0 or non-finite)");
@@ -505,10 +531,12 @@ rbf_status solve_run(rbf_ctx* ctx, double* c, int use_c0, double tol, int maxit,
         k_dinv<double><<<div_up(ctx->g.ncell, 128), 128, 0, st>>>(
             bd, ctx->bvals.as<double>(), ctx->support.as<int>(), min_support,
             ctx->dinv.as<double>(), npin_d);
+        ctx->launches += 1;
         if (use_c0) {
             launch_gather_sorted(c, bd.cperm, ctx->x.as<double>(), M, st);
             k_mask_zero<<<div_up(M, 256), 256, 0, st>>>(M, ctx->x.as<double>(), nullptr,
                                                         ctx->dinv.as<double>());
+            ctx->launches += 2;
         }
         RBF_CUDA_TRY(cudaGetLastError());
         int it = 0;
@@ -528,6 +556,7 @@ rbf_status solve_run(rbf_ctx* ctx, double* c, int use_c0, double tol, int maxit,
         k_dinv<float><<<div_up(ctx->g.ncell, 128), 128, 0, st>>>(
             bd, ctx->bvals.as<float>(), ctx->support.as<int>(), min_support,
             ctx->dinv32.as<float>(), npin_d);
+        ctx->launches += 1;
         double* x64 = ctx->x.as<double>();
         double* r64 = ctx->r.as<double>();
         double* nrm_d = reinterpret_cast<double*>(ctx->scal.as<char>() + sizeof(CgScalars) + 8);
@@ -535,10 +564,12 @@ rbf_status solve_run(rbf_ctx* ctx, double* c, int use_c0, double tol, int maxit,
         const float* dinv32 = ctx->dinv32.as<float>();
         // ||b|| over unpinned rows
         k_norm2<<<1, 1024, 0, st>>>(M, ctx->bvec.as<double>(), dinv32, nrm_d);
+        ctx->launches += 1;
         RBF_CUDA_TRY(cudaMemcpyAsync(nrm_h, nrm_d, sizeof(double), cudaMemcpyDeviceToHost, st));
         if (use_c0) {
             launch_gather_sorted(c, bd.cperm, x64, M, st);
             k_mask_zero<<<div_up(M, 256), 256, 0, st>>>(M, x64, dinv32, nullptr);
+            ctx->launches += 2;
             RBF_CUDA_TRY(cudaMemsetAsync(r64, 0, sizeof(double) * M, st));
             if ((s = residual_run(ctx, x64, r64, false, st)) != RBF_OK) return s;
         } else {
@@ -556,6 +587,7 @@ rbf_status solve_run(rbf_ctx* ctx, double* c, int use_c0, double tol, int maxit,
         const double inner_tol = 1e-4;
         for (outer = 0; outer <= 30; ++outer) {
             k_norm2<<<1, 1024, 0, st>>>(M, r64, dinv32, nrm_d);
+            ctx->launches += 1;
             RBF_CUDA_TRY(cudaMemcpyAsync(nrm_h, nrm_d, sizeof(double), cudaMemcpyDeviceToHost, st));
             RBF_CUDA_TRY(cudaStreamSynchronize(st));
             const double rn = sqrt(nrm_h[0]);
@@ -576,6 +608,7 @@ rbf_status solve_run(rbf_ctx* ctx, double* c, int use_c0, double tol, int maxit,
                 break;
             }
             k_axpy_mixed<<<div_up(M, 256), 256, 0, st>>>(M, x64, ctx->x32.as<float>(), rn, dinv32);
+            ctx->launches += 2;   // with the mask below
             RBF_CUDA_TRY(cudaMemsetAsync(r64, 0, sizeof(double) * M, st));
             if ((s = residual_run(ctx, x64, r64, false, st)) != RBF_OK) return s;
             k_mask_zero<<<div_up(M, 256), 256, 0, st>>>(M, r64, dinv32, nullptr);
@@ -586,6 +619,8 @@ rbf_status solve_run(rbf_ctx* ctx, double* c, int use_c0, double tol, int maxit,
     }
     launch_scatter_orig(ctx->x.as<double>(), bd.cperm, c, M, st);
     RBF_CUDA_TRY(cudaGetLastError());
+    ctx->launches += 1;
+    ctx->solved = true;
     RBF_CUDA_TRY(cudaMemcpyAsync(npin_h, npin_d, sizeof(int), cudaMemcpyDeviceToHost, st));
     RBF_CUDA_TRY(cudaStreamSynchronize(st));
     inf.pinned = *reinterpret_cast<int*>(npin_h);
