@@ -27,8 +27,8 @@
  *     to the host (rbf_bin, rbf_solve): those synchronise `stream` before return.
  *   - Errors are returned as rbf_status; no exception crosses this boundary.
  *     rbf_last_error(ctx) gives a message for the last failure on that context.
- *   - Device-side failures (CG breakdown, non-convergence) are reported through
- *     the status of rbf_solve; no kernel traps.
+ *   - Device-side failures (CG breakdown, non-convergence, a grid barrier that waited
+ *     longer than its limit) are reported through the status of rbf_solve; no kernel traps.
  *   - A context is not thread-safe; use one context per host thread.
  */
 #ifndef RBF_H_
@@ -48,7 +48,9 @@ typedef enum {
     RBF_ERR_CUDA = 3,           /* a CUDA runtime call failed */
     RBF_ERR_NOT_CONVERGED = 4,  /* solver hit maxit before reaching tol */
     RBF_ERR_BREAKDOWN = 5,      /* CG breakdown: p^T B p <= 0 or a non-finite scalar */
-    RBF_ERR_LIMIT = 6           /* input exceeds a documented kernel limit */
+    RBF_ERR_LIMIT = 6,          /* input exceeds a documented kernel limit */
+    RBF_ERR_TIMEOUT = 7         /* a grid-wide wait inside a kernel exceeded its time limit;
+                                   the kernel returned early and the context stays usable */
 } rbf_status;
 
 /* Wendland functions phi_{3,s}(r), r = ||x - xi|| / R, zero for r >= 1 (Table 2, Eq. 18).
@@ -78,6 +80,10 @@ typedef struct {
                                 For RBF_FP32_REFINE this is the FP64 matrix-free
                                 ||A^T(h - A c)||_2 / ||A^T h||_2 */
     int64_t pinned;          /* centres with fewer than min_support points in support */
+    int promoted;            /* 1 if RBF_FP32_REFINE stopped making progress (the FP32 matrix
+                                cannot resolve a system this ill-conditioned) and the solve was
+                                finished by an FP64 assembly and FP64 CG started from the
+                                refined iterate; the context's assembly is FP64 afterwards */
 } rbf_solve_info;
 
 /* Create / destroy a context bound to CUDA device `device`. */
@@ -118,7 +124,8 @@ rbf_status rbf_assemble(rbf_ctx* ctx, rbf_kernel kernel, rbf_prec prec, void* st
  *           the system and get c_j = 0 (the paper leaves empty supports undefined).
  * info    : HOST pointer, may be NULL.
  * Synchronises `stream`. Returns RBF_ERR_NOT_CONVERGED / RBF_ERR_BREAKDOWN with c
- * holding the last iterate. */
+ * holding the last iterate. With RBF_FP32_REFINE, a refinement step that no longer reduces
+ * the FP64 residual promotes the solve to FP64 (see rbf_solve_info.promoted). */
 rbf_status rbf_solve(rbf_ctx* ctx, double* c, int use_c0, double tol, int maxit,
                      int min_support, rbf_solve_info* info, void* stream);
 
@@ -156,6 +163,12 @@ rbf_status rbf_get_launch_count(const rbf_ctx* ctx, int64_t* launches);
  * own workspace vectors, exactly as one CG iteration launches it. Requires a preceding
  * rbf_solve on this context (so the workspace exists). Asynchronous. */
 rbf_status rbf_bench_spmv(rbf_ctx* ctx, int reps, void* stream);
+
+/* Diagnostics / timing: run `reps` preconditioned CG iterations on B c = b from c = 0 with
+ * every iteration's two kernels launched individually on `stream` (the solver normally loops
+ * inside one CUDA graph), so that the kernels can be timed or profiled one by one. Uses and
+ * overwrites the solver's workspace; requires a preceding rbf_solve. Asynchronous. */
+rbf_status rbf_bench_cg(rbf_ctx* ctx, int reps, void* stream);
 
 #ifdef __cplusplus
 }

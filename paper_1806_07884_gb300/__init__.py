@@ -127,7 +127,10 @@ class Context:
         s = self.lib.rbf_solve(self._h, _dptr(c, "c"), 1 if c0 is not None else 0, float(tol),
                                int(maxit), int(min_support), C.byref(info), self._stream(stream))
         d = dict(iterations=info.iterations, refinements=info.refinements,
-                 rel_residual=info.rel_residual, pinned=info.pinned, status=s)
+                 rel_residual=info.rel_residual, pinned=info.pinned, promoted=info.promoted,
+                 status=s)
+        if info.promoted:
+            self.prec = "fp64"
         if s != 0 and raise_on_fail:
             self._check(s, "rbf_solve")
         return c, d
@@ -168,6 +171,11 @@ class Context:
         """Launch the solver's SpMV kernel reps times (timing hook; needs a prior solve)."""
         self._check(self.lib.rbf_bench_spmv(self._h, int(reps), self._stream(stream)),
                     "rbf_bench_spmv")
+
+    def bench_cg(self, reps: int, stream=None):
+        """Run reps CG iterations as individual kernel launches (timing hook; needs a prior
+        solve; overwrites the solver workspace)."""
+        self._check(self.lib.rbf_bench_cg(self._h, int(reps), self._stream(stream)), "rbf_bench_cg")
 
     def export_upper(self, stream=None):
         """The assembled upper triangle of B as COO (caller's centre indices), plus b and the

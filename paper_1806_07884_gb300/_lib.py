@@ -10,9 +10,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "librbf.so")
 
 RBF_OK, RBF_ERR_ARG, RBF_ERR_ALLOC, RBF_ERR_CUDA, RBF_ERR_NOT_CONVERGED, RBF_ERR_BREAKDOWN, \
-    RBF_ERR_LIMIT = range(7)
+    RBF_ERR_LIMIT, RBF_ERR_TIMEOUT = range(8)
 STATUS_NAMES = {0: "RBF_OK", 1: "RBF_ERR_ARG", 2: "RBF_ERR_ALLOC", 3: "RBF_ERR_CUDA",
-                4: "RBF_ERR_NOT_CONVERGED", 5: "RBF_ERR_BREAKDOWN", 6: "RBF_ERR_LIMIT"}
+                4: "RBF_ERR_NOT_CONVERGED", 5: "RBF_ERR_BREAKDOWN", 6: "RBF_ERR_LIMIT",
+                7: "RBF_ERR_TIMEOUT"}
 KERNELS = {"w30": 0, "w31": 1, "w32": 2, "w33": 3}
 PRECS = {"fp64": 0, "fp32_refine": 1}
 
@@ -22,7 +23,7 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 
 class SolveInfo(C.Structure):
     _fields_ = [("iterations", C.c_int), ("refinements", C.c_int),
-                ("rel_residual", C.c_double), ("pinned", C.c_int64)]
+                ("rel_residual", C.c_double), ("pinned", C.c_int64), ("promoted", C.c_int)]
 
 
 _P = C.c_void_p
@@ -45,6 +46,7 @@ SIGNATURES = {
     "rbf_export_upper": (_I, [_P, _I64, _P, _P, _P, _P, _P, C.POINTER(_I64), _P]),
     "rbf_get_launch_count": (_I, [_P, C.POINTER(_I64)]),
     "rbf_bench_spmv": (_I, [_P, _I, _P]),
+    "rbf_bench_cg": (_I, [_P, _I, _P]),
 }
 
 _lib = None

@@ -76,6 +76,8 @@ Binned view(const rbf_ctx* ctx) {
     v.cperm = ctx->cperm.as<int>();
     v.seg = ctx->seg.as<RowSeg>();
     v.rboff = ctx->rboff.as<int64_t>();
+    v.bjoff = ctx->bjoff.as<int64_t>();
+    v.crow = ctx->crow.as<int4>();
     return v;
 }
 
@@ -120,8 +122,7 @@ rbf_status rbf_create(rbf_ctx** out, int device, rbf_alloc_fn alloc, rbf_free_fn
     ctx->free_fn = free_fn;
     ctx->user = user;
     DeviceGuard dg(device);
-    if (cudaMallocHost(&ctx->hpinned, 4096) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    if (cudaMallocHost(&ctx->hpinned, 4096) != cudaSuccess) {
         cudaGetLastError();
         if (ctx->hpinned) cudaFreeHost(ctx->hpinned);
         delete ctx;
@@ -135,19 +136,18 @@ rbf_status rbf_destroy(rbf_ctx* ctx) {
     if (!ctx) return RBF_ERR_ARG;
     DeviceGuard dg(ctx->device);
     cudaDeviceSynchronize();
-    for (auto& row : ctx->graphs)
-        for (auto& gc : row)
-            if (gc.exec) cudaGraphExecDestroy(gc.exec);
+    for (auto& sg : ctx->cg_graph)
+        if (sg.exec) cudaGraphExecDestroy(sg.exec);
+    if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
     rbf_buf* bufs[] = {&ctx->ccount, &ctx->pcount, &ctx->cstart, &ctx->pstart, &ctx->ckey,
                        &ctx->crank, &ctx->pkey, &ctx->prank, &ctx->cx, &ctx->cy, &ctx->cu,
                        &ctx->cv, &ctx->cperm, &ctx->px, &ctx->py, &ctx->ph, &ctx->pu, &ctx->pv,
-                       &ctx->seg, &ctx->rbsize, &ctx->rboff, &ctx->wcount, &ctx->wstart,
+                       &ctx->seg, &ctx->rbsize, &ctx->rboff, &ctx->wcount, &ctx->wstart, &ctx->bjsize, &ctx->bjoff,
                        &ctx->work, &ctx->scan_tmp, &ctx->stats, &ctx->bvals, &ctx->bvec,
-                       &ctx->support, &ctx->x, &ctx->r, &ctx->z, &ctx->p, &ctx->q, &ctx->dinv,
-                       &ctx->x32, &ctx->r32, &ctx->z32, &ctx->p32, &ctx->q32, &ctx->dinv32,
+                       &ctx->support, &ctx->x, &ctx->r, &ctx->cgv[0], &ctx->cgv[1],
+                       &ctx->dinv, &ctx->dinv32, &ctx->bjinv, &ctx->bjinv32, &ctx->crow,
                        &ctx->partial, &ctx->scal, &ctx->csort};
     for (rbf_buf* b : bufs) release(ctx, *b);
-    if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
     if (ctx->hpinned) cudaFreeHost(ctx->hpinned);
     delete ctx;
     return RBF_OK;
@@ -271,6 +271,14 @@ rbf_status rbf_bench_spmv(rbf_ctx* ctx, int reps, void* stream) {
     if (reps < 0) return set_err(ctx, RBF_ERR_ARG, "reps < 0");
     DeviceGuard dg(ctx->device);
     return bench_spmv_run(ctx, reps, as_stream(stream));
+}
+
+rbf_status rbf_bench_cg(rbf_ctx* ctx, int reps, void* stream) {
+    if (!ctx) return RBF_ERR_ARG;
+    if (!ctx->solved || !ctx->assembled) return set_err(ctx, RBF_ERR_ARG, "rbf_bench_cg before rbf_solve");
+    if (reps < 0) return set_err(ctx, RBF_ERR_ARG, "reps < 0");
+    DeviceGuard dg(ctx->device);
+    return bench_cg_run(ctx, reps, as_stream(stream));
 }
 
 }  // extern "C"

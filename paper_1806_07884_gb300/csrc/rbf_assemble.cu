@@ -81,7 +81,7 @@ __device__ void stage_candidates(const Binned& bd, const LocalCells& lc, const C
             cs.a9[a] = k;
             const RowSeg sg = bd.seg[cc];
             cs.rowbase[a] = (long long)bd.rboff[cc] +
-                            (long long)(s - bd.cstart[cc]) * (long long)(sg.l0 + sg.l1 + sg.l2);
+                            (long long)(s - bd.cstart[cc]) * (long long)sg.lp;
             if constexpr (sizeof(CT) == 8) {
                 cs.x[a] = bd.cx[s];
                 cs.y[a] = bd.cy[s];

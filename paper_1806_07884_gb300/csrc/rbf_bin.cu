@@ -193,7 +193,8 @@ __device__ __forceinline__ void cell_row_range(const Grid& g, const int* cstart,
 
 __global__ void k_rows(Grid g, const int* __restrict__ cstart, const int* __restrict__ pstart,
                        RowSeg* __restrict__ seg, int64_t* __restrict__ rbsize,
-                       int* __restrict__ wcount, int* __restrict__ stats) {
+                       int64_t* __restrict__ bjsize, int* __restrict__ wcount,
+                       int4* __restrict__ crow, int* __restrict__ stats) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= g.ncell) return;
     const int ix = c % g.gx, iy = c / g.gx;
@@ -201,9 +202,13 @@ __global__ void k_rows(Grid g, const int* __restrict__ cstart, const int* __rest
     cell_row_range(g, cstart, iy, ix, ix + 2, sg.s0, sg.l0);
     cell_row_range(g, cstart, iy + 1, ix - 2, ix + 2, sg.s1, sg.l1);
     cell_row_range(g, cstart, iy + 2, ix - 2, ix + 2, sg.s2, sg.l2);
+    sg.lp = (sg.l0 + sg.l1 + sg.l2 + kRowPad - 1) / kRowPad * kRowPad;
     seg[c] = sg;
-    const int m = cstart[c + 1] - cstart[c];
-    rbsize[c] = int64_t(m) * int64_t(sg.l0 + sg.l1 + sg.l2);
+    const int cs = cstart[c];
+    const int m = cstart[c + 1] - cs;
+    rbsize[c] = int64_t(m) * int64_t(sg.lp);
+    for (int i = 0; i < m; ++i) crow[cs + i] = make_int4(cs, m, c, 0);
+    bjsize[c] = m <= kMaxBlock ? int64_t(m) * m : 0;
     const int np = pstart[c + 1] - pstart[c];
     wcount[c] = (np + kWorkPoints - 1) / kWorkPoints;
     if (np > 0) {
@@ -265,6 +270,9 @@ rbf_status bin_run(rbf_ctx* ctx, const double* cx, const double* cy, const doubl
     ENS(rbsize, sizeof(int64_t) * nc);
     ENS(rboff, sizeof(int64_t) * (nc + 1));
     ENS(wcount, sizeof(int) * nc);
+    ENS(bjsize, sizeof(int64_t) * nc);
+    ENS(crow, sizeof(int4) * M);
+    ENS(bjoff, sizeof(int64_t) * (nc + 1));
     ENS(wstart, sizeof(int) * (nc + 1));
     ENS(stats, sizeof(int64_t) * 8);
     int* stats = ctx->stats.as<int>();
@@ -291,12 +299,15 @@ rbf_status bin_run(rbf_ctx* ctx, const double* cx, const double* cy, const doubl
                                         ctx->pu.as<float>(), ctx->pv.as<float>());
     k_rows<<<div_up(nc, T), T, 0, st>>>(g, ctx->cstart.as<int>(), ctx->pstart.as<int>(),
                                         ctx->seg.as<RowSeg>(), ctx->rbsize.as<int64_t>(),
-                                        ctx->wcount.as<int>(), stats);
+                                        ctx->bjsize.as<int64_t>(), ctx->wcount.as<int>(),
+                                        ctx->crow.as<int4>(), stats);
     RBF_CUDA_TRY(cudaGetLastError());
     ctx->launches += 5;
     if ((s = scan_i64(ctx, ctx->rbsize.as<int64_t>(), ctx->rboff.as<int64_t>(), nc, st)) != RBF_OK)
         return s;
     if ((s = scan_i32(ctx, ctx->wcount.as<int>(), ctx->wstart.as<int>(), nc, st)) != RBF_OK) return s;
+    if ((s = scan_i64(ctx, ctx->bjsize.as<int64_t>(), ctx->bjoff.as<int64_t>(), nc, st)) != RBF_OK)
+        return s;
 
     // read back the sizes the host needs to allocate B and launch the assembly
     int64_t* hp = static_cast<int64_t*>(ctx->hpinned);
@@ -305,9 +316,12 @@ rbf_status bin_run(rbf_ctx* ctx, const double* cx, const double* cy, const doubl
     RBF_CUDA_TRY(cudaMemcpyAsync(&hp[1], ctx->wstart.as<int>() + nc, sizeof(int),
                                  cudaMemcpyDeviceToHost, st));
     RBF_CUDA_TRY(cudaMemcpyAsync(&hp[2], stats, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    RBF_CUDA_TRY(cudaMemcpyAsync(&hp[4], ctx->bjoff.as<int64_t>() + nc, sizeof(int64_t),
+                                 cudaMemcpyDeviceToHost, st));
     RBF_CUDA_TRY(cudaStreamSynchronize(st));
     const int* hs = reinterpret_cast<const int*>(&hp[2]);
     ctx->nvals = hp[0];
+    ctx->nbj = hp[4];
     ctx->nwork = *reinterpret_cast<const int*>(&hp[1]);
     ctx->max_cand = hs[0];
     ctx->max_cell_pts = hs[1];

@@ -14,6 +14,9 @@ namespace rbf {
 constexpr int kMaxCand = 384;
 // Points per staged sub-chunk of the fused assembly / residual passes.
 constexpr int kSubChunk = 32;
+// Largest cell (centres per cell) whose diagonal block is inverted for the block-Jacobi
+// preconditioner; larger cells fall back to the scalar diagonal.
+constexpr int kMaxBlock = 32;
 // Points per assembly work item (one CTA); larger cells are split.
 constexpr int kWorkPoints = 256;
 // Relative enlargement of the cell side over R, so that a pair closer than R is never
@@ -85,8 +88,12 @@ __device__ __forceinline__ int cell_iy(const Grid& g, double y) {
 //   seg 2: cells (ix-2 .. ix+2, iy+2)    (clipped to the grid)
 // Any centre pair closer than 2R (the only pairs with B_st != 0) with cell(s) <= cell(t)
 // in key order has t inside one of these ranges of cell(s).
+// Rows are stored with a padded length lp (a multiple of kRowPad, zero-filled) so that every
+// row starts on a 16-byte boundary and can be streamed with vector loads.
+constexpr int kRowPad = 4;
 struct RowSeg {
     int s0, l0, s1, l1, s2, l2;   // first centre and length of each segment
+    int lp;                       // padded row length (row stride of the block)
 };
 
 // Views of the context's device buffers passed by value to kernels.
@@ -107,6 +114,8 @@ struct Binned {
     const int* cperm;       // [M] sorted -> caller centre index
     const RowSeg* seg;      // [ncell]
     const int64_t* rboff;   // [ncell+1] offset of each cell's row block in the value array
+    const int64_t* bjoff;   // [ncell+1] offset of each cell's inverse diagonal block
+    const int4* crow;       // [M] {first sorted centre, centre count, cell, 0} of each centre's cell
 };
 
 // ---------------------------------------------------------------------------

@@ -66,7 +66,7 @@ __global__ void k_export(Binned bd, const T* __restrict__ B, const double* __res
     const T* Bc = B + bd.rboff[c];
     for (int e = threadIdx.x; e < m * L; e += blockDim.x) {
         const int i = e / L, k = e % L;
-        const double v = double(Bc[int64_t(i) * L + k]);
+        const double v = double(Bc[int64_t(i) * sg.lp + k]);
         const int t = k < sg.l0 ? sg.s0 + k : (k < sg.l0 + sg.l1 ? sg.s1 + k - sg.l0 : sg.s2 + k - sg.l0 - sg.l1);
         const int s = cs + i;
         if (t < s || v == 0.0) continue;   // diagonal block: keep the upper triangle only

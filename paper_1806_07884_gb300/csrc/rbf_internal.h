@@ -41,6 +41,9 @@ struct rbf_ctx {
     rbf_buf seg;               // [ncell] RowSeg
     rbf_buf rbsize, rboff;     // [ncell], [ncell+1] int64
     rbf_buf wcount, wstart;    // [ncell], [ncell+1]
+    rbf_buf bjsize, bjoff;     // [ncell], [ncell+1] int64: inverse diagonal blocks (m <= 32)
+    rbf_buf crow;              // [M] int4 {cell start, cell count, cell, 0} per sorted centre
+    int64_t nbj = 0;           // values of all inverse diagonal blocks
     rbf_buf work;              // [nwork] int4 {cell, p0, p1, 0}
     rbf_buf scan_tmp;          // block sums of the device scans
     rbf_buf stats;             // small int counters read back by rbf_bin
@@ -54,23 +57,27 @@ struct rbf_ctx {
     rbf_buf support;           // [M] points inside each support, sorted order
 
     // ---- solver workspace ----
-    rbf_buf x, r, z, p, q, dinv;        // [M] FP64 CG vectors, sorted order
-    rbf_buf x32, r32, z32, p32, q32, dinv32;   // [M] FP32 inner-solve vectors
+    // FP64 refinement vectors (sorted order): the solution and the matrix-free residual
+    rbf_buf x, r;
+    // CG workspace per precision ([0] FP64, [1] FP32): kCgVecs vectors of length M (x, u, p,
+    // r[2], s[2], w[2] -- r, s, w double-buffered by iteration parity) and dinv
+    rbf_buf cgv[2], dinv, dinv32;
+    rbf_buf bjinv, bjinv32;    // inverse diagonal cell blocks (block-Jacobi preconditioner)
     rbf_buf partial;           // per-block partial sums
     rbf_buf scal;              // device scalars (struct CgScalars)
     rbf_buf csort;             // [M] FP64 coefficients in sorted order (evaluation)
     void* hpinned = nullptr;   // pinned host scratch for scalar read-back (4 KiB)
     int64_t launches = 0;      // kernels launched by this context (graph nodes included)
-    bool solved = false;       // solver workspace exists
     cudaStream_t capture_stream = nullptr;   // private stream used only to capture graphs
-
-    // CG graphs: [precision: 0 FP64, 1 FP32][chunk = 8 << k, k = 0..5]
-    struct GraphCache {
+    // CG solve graphs (conditional WHILE loop), [0] FP64, [1] FP32, and what they were built for
+    struct SolveGraph {
         cudaGraphExec_t exec = nullptr;
-        int M = 0, ncell = 0, gx = 0;
-        const void* key[8] = {};
+        int ncell = 0, M = 0, gx = 0;
+        const void* crow = nullptr;
+        const void* key[10] = {};
     };
-    GraphCache graphs[2][6];
+    SolveGraph cg_graph[2];
+    bool solved = false;       // solver workspace exists
 };
 
 namespace rbf {
@@ -108,6 +115,7 @@ rbf_status export_upper_run(rbf_ctx* ctx, int64_t cap, int32_t* row, int32_t* co
                             double* bvec, int32_t* support, int64_t* nnz, cudaStream_t st);
 
 rbf_status bench_spmv_run(rbf_ctx* ctx, int reps, cudaStream_t st);
+rbf_status bench_cg_run(rbf_ctx* ctx, int reps, cudaStream_t st);
 
 // permutation helpers (rbf_solve.cu)
 void launch_gather_sorted(const double* c_orig, const int* cperm, double* c_sorted, int M,

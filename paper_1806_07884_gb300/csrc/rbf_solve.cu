@@ -1,22 +1,24 @@
-// Step (d): solve the normal equations B c = b (Section 2) by Jacobi-preconditioned
-// conjugate gradients on the stored upper triangle of B.
+// Step (d): solve the normal equations B c = b (Section 2) by preconditioned conjugate
+// gradients on the stored upper triangle of B. The preconditioner is block-Jacobi over the
+// cells of the grid: the inverse of each cell's diagonal block B[c, c] (the centres of one
+// cell share most of their support and are the strongest couplings of B).
 //
-// SpMV y = B x over the cell-blocked upper storage (one warp per output cell c):
-//   part A: the rows of cell c -- a dense m_c x L_c row-major block (own upper part,
-//           three contiguous column ranges), streamed with coalesced loads and
-//           reduced per row with warp shuffles;
-//   part B: the transposed contributions of the 12 lower neighbour cells c', whose
-//           row blocks hold the entries B[c', c] as an m_c' x m_c sub-block; lane j
-//           reads column j of it (consecutive lanes read consecutive addresses).
-//   The sub-blocks of part B were streamed by their owner cell shortly before (cells
-//   run in key order), so the second read is served from L2: HBM sees each stored
-//   value about once per SpMV, half the traffic of storing both triangles.
+// SpMV y = B x over the cell-blocked upper storage (Section 5 keeps only the upper
+// triangle), one warp per cell: the cell's dense m_c x lp_c row block is streamed once with
+// 16-byte vector loads, and each value feeds both the row product (16 rows held in
+// registers, summed across lanes by a butterfly transpose-reduction) and the transposed
+// product of the lower triangle (column sums added to y with atomics). HBM and L2 see each
+// stored value once per SpMV -- half the bytes of storing both triangles -- and no transposed
+// reads are needed. The same pass yields x^T B x locally.
 //
-// CG runs as a chain of three kernels per iteration (SpMV + p.q, vector update +
-// r.z / r.r, direction update); the scalars live in device memory and grid-wide sums
-// use a last-block-done ticket (no spin waits). A chunk of iterations is captured into
-// a CUDA graph once and replayed; every kernel checks a device-side state word first,
-// so replays past convergence cost only empty launches.
+// The CG iteration uses the Chronopoulos-Gear recurrences: one SpMV and one fused pair of
+// reductions per iteration, as two kernels. The SpMV kernel accumulates delta = u^T B u
+// with warp atomics spread over 64 slots; the update kernel derives alpha and beta from
+// them at its start, updates the vectors one thread per row (each thread recomputes the new
+// residual of its cell's rows to apply its row of the block inverse, so r, s and w are
+// double-buffered by iteration parity), and its last block to finish reduces gamma and
+// (r, r) and advances the scalar state in device memory. The iteration loop is a CUDA graph
+// with a conditional WHILE node: the host launches the solve once and reads the state once.
 //
 // Precision RBF_FP32_REFINE: B is FP32 and the inner CG runs in FP32 on the correction
 // equation B d = r; the residual r = A^T (h - A c) is recomputed matrix-free in FP64
@@ -30,28 +32,31 @@
 
 namespace rbf {
 
+constexpr int kAccSlots = 64;
+
 struct CgScalars {
-    double rz, pq, alpha, beta, rr, bb, tol2, rr0;
+    double gamma, gamma_prev, alpha, rr, bb;
+    double tol2, bscale;         // parameters, written by the host before each solve
     int it, maxit, state, pad;
-    unsigned int ticket, pad2;
+    unsigned int ticket, pad2;   // last-block-done counter of the reductions
+    double acc_delta[kAccSlots]; // u^T B u of the current SpMV, spread over slots
 };
 
 enum { kRunning = 0, kConverged = 1, kBreakdown = 2, kMaxIt = 3 };
 
 namespace {
 
-constexpr int kVecThreads = 256;
 constexpr int kSpmvWarps = 8;
+constexpr int kVecThreads = 256;
+constexpr unsigned kFull = 0xffffffffu;
+// CG iterations per pass of the solve graph's loop body (even: the buffers alternate).
+constexpr int kItersPerBody = 4;
+// Vectors of the CG workspace: x, u, p, r0, r1, s0, s1, w0, w1.
+constexpr int kCgVecs = 9;
 
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-template <typename T>
-__device__ __forceinline__ T warp_sum(T v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
     return v;
 }
 
@@ -68,15 +73,13 @@ __device__ __forceinline__ void block_sum(double (&v)[NV]) {
     __syncthreads();
     if (w == 0) {
 #pragma unroll
-        for (int k = 0; k < NV; ++k) {
-            double s = lane < nw ? red[k][lane] : 0.0;
-            v[k] = warp_sum_d(s);
-        }
+        for (int k = 0; k < NV; ++k) v[k] = warp_sum_d(lane < nw ? red[k][lane] : 0.0);
     }
+    __syncthreads();
 }
 
-// Stores this block's NV partial sums; returns true in the (single) last block to finish,
-// which then holds the totals, summed in block order, in tot[] (thread 0 only).
+// Stores this block's NV partial sums; returns true in the single last block to finish,
+// whose thread 0 then holds the totals, summed in block order, in tot[].
 template <int NV>
 __device__ bool last_block_total(double (&v)[NV], double* partial, unsigned int* ticket,
                                  double (&tot)[NV]) {
@@ -86,8 +89,7 @@ __device__ bool last_block_total(double (&v)[NV], double* partial, unsigned int*
 #pragma unroll
         for (int k = 0; k < NV; ++k) partial[NV * blockIdx.x + k] = v[k];
         __threadfence();
-        const unsigned int t = atomicAdd(ticket, 1u);
-        amlast = (t == gridDim.x - 1);
+        amlast = atomicAdd(ticket, 1u) == gridDim.x - 1;
     }
     __syncthreads();
     if (!amlast) return false;
@@ -95,10 +97,9 @@ __device__ bool last_block_total(double (&v)[NV], double* partial, unsigned int*
     double acc[NV];
 #pragma unroll
     for (int k = 0; k < NV; ++k) acc[k] = 0.0;
-    for (int b = threadIdx.x; b < gridDim.x; b += blockDim.x)
+    for (int b = threadIdx.x; b < int(gridDim.x); b += blockDim.x)
 #pragma unroll
         for (int k = 0; k < NV; ++k) acc[k] += __ldcg(&partial[NV * b + k]);
-    // fixed-order reduction of the per-thread sums
     block_sum<NV>(acc);
     if (threadIdx.x == 0) {
 #pragma unroll
@@ -108,191 +109,374 @@ __device__ bool last_block_total(double (&v)[NV], double* partial, unsigned int*
     return true;
 }
 
+template <typename T>
+__device__ __forceinline__ T ldcg(const T* p) { return __ldcg(p); }
+
 __device__ __forceinline__ int colmap(const RowSeg& sg, int k) {
     return k < sg.l0 ? sg.s0 + k : (k < sg.l0 + sg.l1 ? sg.s1 + (k - sg.l0) : sg.s2 + (k - sg.l0 - sg.l1));
 }
 
-// y = B x (rows with dinv == 0 -- pinned centres -- give 0). With sc != nullptr the kernel
-// is a CG step: it returns at once unless the solve is running, and accumulates p.q.
+// Four consecutive values of a row (16-byte aligned: rows are padded to kRowPad values).
+__device__ __forceinline__ void load4(const float* p, float (&v)[4]) {
+    const float4 q = __ldg(reinterpret_cast<const float4*>(p));
+    v[0] = q.x;
+    v[1] = q.y;
+    v[2] = q.z;
+    v[3] = q.w;
+}
+__device__ __forceinline__ void load4(const double* p, double (&v)[4]) {
+    const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+    const double2 b = __ldg(reinterpret_cast<const double2*>(p + 2));
+    v[0] = a.x;
+    v[1] = a.y;
+    v[2] = b.x;
+    v[3] = b.y;
+}
+
+// Sum v[0..15] over the 32 lanes of a warp so that lane l ends up holding the total of
+// row (l >> 1) & 15: four exchange-and-halve steps (xor 16, 8, 4, 2) and a final xor 1.
 template <typename T>
-__global__ void __launch_bounds__(kSpmvWarps * 32)
-    k_spmv(Binned bd, const T* __restrict__ B, const T* __restrict__ x, T* __restrict__ y,
-           const T* __restrict__ dinv, CgScalars* __restrict__ sc, double* __restrict__ partial) {
-    if (sc && sc->state != kRunning) return;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int c = blockIdx.x * kSpmvWarps + warp;
-    const Grid& g = bd.g;
-    double dsum = 0.0;
-    if (c < g.ncell) {
-        const int cs = bd.cstart[c];
-        const int m = bd.cstart[c + 1] - cs;
-        if (m > 0) {
-            const RowSeg sg = bd.seg[c];
-            const int L = sg.l0 + sg.l1 + sg.l2;
-            const T* Bc = B + bd.rboff[c];
-            const int ix = c % g.gx, iy = c / g.gx;
-            for (int j0 = 0; j0 < m; j0 += 32) {
-                T acc = T(0);
-                const int jend = min(m, j0 + 32);
-                // part A: own upper rows
-                for (int i = j0; i < jend; ++i) {
-                    const T* row = Bc + int64_t(i) * L;
-                    T s = T(0);
-                    for (int k = lane; k < L; k += 32) s = fma(row[k], x[colmap(sg, k)], s);
-                    s = warp_sum(s);
-                    if (lane == i - j0) acc += s;
-                }
-                // part B: transposed blocks of the 12 lower neighbours
-                const bool jv = j0 + lane < m;
-#pragma unroll 1
-                for (int nbr = 0; nbr < 12; ++nbr) {
-                    int dx, dy;
-                    if (nbr < 2) {
-                        dx = -1 - nbr;
-                        dy = 0;
-                    } else {
-                        dx = (nbr - 2) % 5 - 2;
-                        dy = (nbr - 2) / 5 + 1;
+__device__ __forceinline__ T butterfly16(T (&v)[16], int lane) {
+    {
+        const bool hi = lane & 16;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const T send = hi ? v[j] : v[j + 8];
+            const T keep = hi ? v[j + 8] : v[j];
+            v[j] = keep + __shfl_xor_sync(kFull, send, 16);
+        }
+    }
+    {
+        const bool hi = lane & 8;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const T send = hi ? v[j] : v[j + 4];
+            const T keep = hi ? v[j + 4] : v[j];
+            v[j] = keep + __shfl_xor_sync(kFull, send, 8);
+        }
+    }
+    {
+        const bool hi = lane & 4;
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const T send = hi ? v[j] : v[j + 2];
+            const T keep = hi ? v[j + 2] : v[j];
+            v[j] = keep + __shfl_xor_sync(kFull, send, 4);
+        }
+    }
+    {
+        const bool hi = lane & 2;
+        const T send = hi ? v[0] : v[1];
+        const T keep = hi ? v[1] : v[0];
+        v[0] = keep + __shfl_xor_sync(kFull, send, 2);
+    }
+    return v[0] + __shfl_xor_sync(kFull, v[0], 1);
+}
+
+// y += B x restricted to the stored upper row block of cell c (warp-cooperative; all 32
+// lanes). Lane l streams columns 4l .. 4l+3 of each row with vector loads; every loaded
+// value B[s][t] feeds both products:
+//   row sums    y[s] += sum_t B[s][t] x[t]   (16 rows in registers, butterfly reduction)
+//   column sums y[t] += sum_s B[s][t] x[s]   for t outside the diagonal block c x c
+//   (the diagonal block is stored in full, so its transposed half is already in the rows)
+// and are added with atomics. Returns this lane's share of x^T B x over the cell's entries:
+// sum_s x[s] rowsum[s] + sum_t colsum[t] x[t].
+template <typename T>
+__device__ double spmv_cell(const Binned& bd, const T* __restrict__ B, const T* x, T* y, int c,
+                            int lane) {
+    const int cs = bd.cstart[c];
+    const int m = bd.cstart[c + 1] - cs;
+    if (m == 0) return 0.0;
+    const RowSeg sg = bd.seg[c];
+    const int L = sg.l0 + sg.l1 + sg.l2, lp = sg.lp;
+    const T* Bc = B + bd.rboff[c];
+    double dot = 0.0;
+    for (int j0 = 0; j0 < m; j0 += 16) {
+        const int mm = min(16, m - j0);
+        const T xs_lane = lane < mm ? ldcg(x + cs + j0 + lane) : T(0);
+        T rp[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) rp[i] = T(0);
+        for (int k0 = 0; k0 < L; k0 += 128) {
+            const int kb = k0 + 4 * lane;
+            const bool active = kb < L;
+            T xt[4], ca[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                xt[q] = kb + q < L ? ldcg(x + colmap(sg, kb + q)) : T(0);
+                ca[q] = T(0);
+            }
+            const T* rb = Bc + (long long)j0 * lp + kb;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const T xi = __shfl_sync(kFull, xs_lane, i);
+                if (i < mm && active) {
+                    T v[4];
+                    load4(rb + (long long)i * lp, v);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        rp[i] = fma(v[q], xt[q], rp[i]);
+                        ca[q] = fma(v[q], xi, ca[q]);
                     }
-                    const int nx = ix + dx, ny = iy - dy;
-                    if (nx < 0 || nx >= g.gx || ny < 0) continue;
-                    const int cp = ny * g.gx + nx;
-                    const int csp = bd.cstart[cp];
-                    const int mp = bd.cstart[cp + 1] - csp;
-                    if (mp == 0) continue;
-                    const RowSeg sp = bd.seg[cp];
-                    const int Lp = sp.l0 + sp.l1 + sp.l2;
-                    int koff;
-                    if (dy == 0) koff = cs - sp.s0;
-                    else if (dy == 1) koff = sp.l0 + (cs - sp.s1);
-                    else koff = sp.l0 + sp.l1 + (cs - sp.s2);
-                    const T* blk = B + bd.rboff[cp] + koff + j0 + lane;
-                    if (jv) {
-                        T a2 = T(0);
-                        for (int i = 0; i < mp; ++i) a2 = fma(blk[int64_t(i) * Lp], x[csp + i], a2);
-                        acc += a2;
-                    }
                 }
-                if (jv) {
-                    const int s = cs + j0 + lane;
-                    const T out = (dinv && dinv[s] == T(0)) ? T(0) : acc;
-                    y[s] = out;
-                    if (sc) dsum += double(x[s]) * double(out);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int k = kb + q;
+                if (k >= m && k < L && ca[q] != T(0)) {
+                    atomicAdd(y + colmap(sg, k), ca[q]);
+                    dot += double(ca[q]) * double(xt[q]);
                 }
             }
         }
-    }
-    if (!sc) return;
-    double v[1] = {dsum}, tot[1];
-    if (last_block_total<1>(v, partial, &sc->ticket, tot) && threadIdx.x == 0) {
-        const double pq = tot[0];
-        if (!(pq > 0.0) || !isfinite(pq)) {
-            sc->state = kBreakdown;
-        } else {
-            sc->pq = pq;
-            sc->alpha = sc->rz / pq;
+        const T tot = butterfly16(rp, lane);       // lanes 2r, 2r+1 hold row r
+        const int r = (lane >> 1) & 15;
+        const T xr = __shfl_sync(kFull, xs_lane, r);
+        if ((lane & 1) == 0 && r < mm) {
+            atomicAdd(y + cs + j0 + r, tot);
+            dot += double(tot) * double(xr);
         }
     }
+    return dot;
 }
 
-// x += alpha p; r -= alpha q; z = dinv r; then rz, rr, convergence test and beta.
+// Standalone SpMV y += B x (warp per cell; y zeroed by the caller).
+template <typename T>
+__global__ void __launch_bounds__(kSpmvWarps * 32)
+    k_spmv(Binned bd, const T* __restrict__ B, const T* __restrict__ x, T* __restrict__ y) {
+    const int lane = threadIdx.x & 31;
+    const int c = blockIdx.x * kSpmvWarps + (threadIdx.x >> 5);
+    if (c < bd.g.ncell) spmv_cell<T>(bd, B, x, y, c, lane);
+}
+
+template <typename T>
+struct CgVec {
+    T *x, *u, *p;
+    T *r[2], *s[2], *w[2];
+    const T* dinv;     // 1 / B_ss, 0 for pinned centres (the mask)
+    const T* bjinv;    // inverse diagonal cell blocks (cells with m <= kMaxBlock)
+};
+
+// Preconditioned CG in the Chronopoulos-Gear form (one SpMV and two reductions per
+// iteration), for B x = bscale * b:
+//   r = b - B x, u = D^-1 r, w = B u, gamma = (r, u), delta = (w, u) = u^T B u
+//   beta = gamma / gamma_prev (0 at the start), alpha = gamma / (delta - beta gamma / alpha_prev)
+//   p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s, u = D^-1 r
+// It stops when (r, r) <= tol^2 (b, b).
+
+// w += B u (w zero on entry); delta = u^T B u into the slots of sc->acc_delta.
+template <typename T>
+__global__ void __launch_bounds__(kSpmvWarps * 32)
+    k_cg_spmv(Binned bd, const T* __restrict__ B, const T* __restrict__ u, T* __restrict__ w,
+              CgScalars* __restrict__ sc) {
+    if (sc->state != kRunning) return;
+    const int lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * kSpmvWarps + (threadIdx.x >> 5);
+    if (gw >= bd.g.ncell) return;
+    const double d = warp_sum_d(spmv_cell<T>(bd, B, u, w, gw, lane));
+    if (lane == 0 && d != 0.0) atomicAdd(&sc->acc_delta[gw & (kAccSlots - 1)], d);
+}
+
+// The residual of a row after this iteration's update, r - alpha (w + beta s), evaluated
+// with the same operations by every thread that needs it.
+template <typename T>
+__device__ __forceinline__ T next_r(T r, T s, T w, T ta, T tb) {
+    return fma(-ta, fma(tb, s, w), r);
+}
+
+// u_i = sum_j Dinv[i][j] r_j over the rows j of row i's cell (row a of the cell's inverse
+// block), r_j produced by rj(j) for the cell's rows; or dinv_i r_i for large cells.
+template <typename T, typename F>
+__device__ __forceinline__ T apply_prec(const Binned& bd, const T* __restrict__ bjinv, int4 cm,
+                                        int i, T di, T ri, F rj) {
+    if (cm.y > kMaxBlock) return di * ri;
+    const int a = i - cm.x;
+    const T* drow = bjinv + bd.bjoff[cm.z] + (long long)a * cm.y;
+    T ui = T(0);
+#pragma unroll 4
+    for (int j = 0; j < cm.y; ++j) ui = fma(__ldg(drow + j), rj(cm.x + j), ui);
+    return ui;
+}
+
+// One thread per row i: alpha, beta from the scalars; s, p, x, r updated; u = D^-1 r using
+// the cell's updated residual (recomputed here from the previous buffers); w of the other
+// parity zeroed for the next SpMV. The last block reduces gamma, (r, r) and advances the
+// state. P is the parity of the buffers read in this iteration.
 template <typename T>
 __global__ void __launch_bounds__(kVecThreads)
-    k_cg_update(int M, T* __restrict__ x, T* __restrict__ r, T* __restrict__ z,
-                const T* __restrict__ p, const T* __restrict__ q, const T* __restrict__ dinv,
-                CgScalars* __restrict__ sc, double* __restrict__ partial) {
-    if (sc->state != kRunning) return;
-    const T alpha = T(sc->alpha);
-    double rz = 0.0, rr = 0.0;
+    k_cg_update(Binned bd, CgVec<T> v, int P, CgScalars* __restrict__ sc,
+                double* __restrict__ partial) {
+    __shared__ double s_ab[2];
+    __shared__ int s_go;
+    if (threadIdx.x == 0) {
+        int go = sc->state == kRunning;
+        if (go) {
+            double delta = 0.0;
+            for (int k = 0; k < kAccSlots; ++k) delta += __ldcg(&sc->acc_delta[k]);
+            const double gamma = sc->gamma;
+            const int it = sc->it;
+            const double beta = it == 0 ? 0.0 : gamma / sc->gamma_prev;
+            const double den = it == 0 ? delta : delta - beta * gamma / sc->alpha;
+            const double alpha = gamma / den;
+            if (!(den > 0.0) || !isfinite(alpha)) {
+                sc->state = kBreakdown;
+                go = 0;
+            }
+            s_ab[0] = alpha;
+            s_ab[1] = beta;
+        }
+        s_go = go;
+    }
+    __syncthreads();
+    if (!s_go) return;
+    const double alpha = s_ab[0], beta = s_ab[1];
+    const T ta = T(alpha), tb = T(beta);
+    const T* __restrict__ rP = P ? v.r[1] : v.r[0];
+    const T* __restrict__ sP = P ? v.s[1] : v.s[0];
+    const T* __restrict__ wP = P ? v.w[1] : v.w[0];
+    T* __restrict__ rQ = P ? v.r[0] : v.r[1];
+    T* __restrict__ sQ = P ? v.s[0] : v.s[1];
+    T* __restrict__ wQ = P ? v.w[0] : v.w[1];
+    double acc[2] = {0.0, 0.0}, tot[2];
+    const int M = bd.M;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) {
-        const T pi = p[i];
-        x[i] = fma(alpha, pi, x[i]);
-        const T ri = fma(-alpha, q[i], r[i]);
-        r[i] = ri;
-        const T zi = dinv[i] * ri;
-        z[i] = zi;
-        rz += double(ri) * double(zi);
-        rr += double(ri) * double(ri);
+        const T di = v.dinv[i];
+        const T wi = di == T(0) ? T(0) : wP[i];
+        const T si = fma(tb, sP[i], wi);
+        const T pi = fma(tb, v.p[i], v.u[i]);
+        const T ri = di == T(0) ? T(0) : fma(-ta, si, rP[i]);
+        const int4 cm = bd.crow[i];
+        // rows of pinned centres carry zeros in the inverse block, so r_j need no mask
+        const T ui = apply_prec<T>(bd, v.bjinv, cm, i, di, ri,
+                                   [&](int j) { return next_r(rP[j], sP[j], wP[j], ta, tb); });
+        sQ[i] = si;
+        v.p[i] = pi;
+        v.x[i] = fma(ta, pi, v.x[i]);
+        rQ[i] = ri;
+        v.u[i] = ui;
+        wQ[i] = T(0);
+        acc[0] += double(ri) * double(ui);
+        acc[1] += double(ri) * double(ri);
     }
-    double v[2] = {rz, rr}, tot[2];
-    if (last_block_total<2>(v, partial, &sc->ticket, tot) && threadIdx.x == 0) {
-        sc->it += 1;
+    if (last_block_total<2>(acc, partial, &sc->ticket, tot) && threadIdx.x == 0) {
+        sc->gamma_prev = sc->gamma;
+        sc->gamma = tot[0];
+        sc->alpha = alpha;
         sc->rr = tot[1];
-        if (!isfinite(tot[0]) || !isfinite(tot[1])) {
-            sc->state = kBreakdown;
-        } else if (tot[1] <= sc->tol2 * sc->bb) {
-            sc->state = kConverged;
-        } else if (sc->it >= sc->maxit) {
-            sc->state = kMaxIt;
-        } else {
-            sc->beta = tot[0] / sc->rz;
-            sc->rz = tot[0];
-        }
+        sc->it += 1;
+        for (int k = 0; k < kAccSlots; ++k) sc->acc_delta[k] = 0.0;
+        if (!isfinite(tot[0]) || !isfinite(tot[1])) sc->state = kBreakdown;
+        else if (tot[1] <= sc->tol2 * sc->bb) sc->state = kConverged;
+        else if (sc->it >= sc->maxit) sc->state = kMaxIt;
     }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kVecThreads)
-    k_cg_p(int M, const T* __restrict__ z, T* __restrict__ p, const CgScalars* __restrict__ sc) {
-    if (sc->state != kRunning) return;
-    const T beta = T(sc->beta);
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x)
-        p[i] = fma(beta, p[i], z[i]);
-}
-
-// r = b - y (or b when y == nullptr), masked; z = dinv r; p = z; sums rz, rr, bb.
+// Start: r = bscale b - B x0 (B x0 in w[1] when use_x0), u = D^-1 r, p = s[0] = w[0] = 0
+// (x = 0 without a start vector); gamma, (r, r), (b, b) and the initial test.
 template <typename T, typename TB>
 __global__ void __launch_bounds__(kVecThreads)
-    k_cg_init(int M, const TB* __restrict__ b, double bscale, const T* __restrict__ y,
-              T* __restrict__ r, T* __restrict__ z, T* __restrict__ p, const T* __restrict__ dinv,
+    k_cg_init(Binned bd, CgVec<T> v, const TB* __restrict__ b, int use_x0,
               CgScalars* __restrict__ sc, double* __restrict__ partial) {
-    double rz = 0.0, rr = 0.0, bb = 0.0;
+    const double bscale = sc->bscale;
+    const T* __restrict__ w1 = v.w[1];
+    auto r0 = [&](int j) -> T {
+        const T bj = T(double(b[j]) * bscale);
+        return use_x0 ? bj - w1[j] : bj;
+    };
+    double acc[3] = {0.0, 0.0, 0.0}, tot[3];
+    const int M = bd.M;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) {
-        const T di = dinv[i];
+        const T di = v.dinv[i];
         const T bi = di == T(0) ? T(0) : T(double(b[i]) * bscale);
-        const T ri = y ? bi - y[i] : bi;
-        const T ri2 = di == T(0) ? T(0) : ri;
-        const T zi = di * ri2;
-        r[i] = ri2;
-        z[i] = zi;
-        p[i] = zi;
-        rz += double(ri2) * double(zi);
-        rr += double(ri2) * double(ri2);
-        bb += double(bi) * double(bi);
+        const T ri = di == T(0) ? T(0) : r0(i);
+        const T ui = apply_prec<T>(bd, v.bjinv, bd.crow[i], i, di, ri, r0);
+        if (!use_x0) v.x[i] = T(0);
+        v.r[0][i] = ri;
+        v.u[i] = ui;
+        v.p[i] = T(0);
+        v.s[0][i] = T(0);
+        v.w[0][i] = T(0);
+        acc[0] += double(ri) * double(ui);
+        acc[1] += double(ri) * double(ri);
+        acc[2] += double(bi) * double(bi);
     }
-    double v[3] = {rz, rr, bb}, tot[3];
-    if (last_block_total<3>(v, partial, &sc->ticket, tot) && threadIdx.x == 0) {
-        sc->rz = tot[0];
+    if (last_block_total<3>(acc, partial, &sc->ticket, tot) && threadIdx.x == 0) {
+        sc->gamma = tot[0];
+        sc->gamma_prev = 1.0;
+        sc->alpha = 0.0;
         sc->rr = tot[1];
-        sc->rr0 = tot[1];
         sc->bb = tot[2];
         sc->it = 0;
+        for (int k = 0; k < kAccSlots; ++k) sc->acc_delta[k] = 0.0;
         if (tot[1] <= sc->tol2 * tot[2] || tot[2] == 0.0) sc->state = kConverged;
         else if (sc->maxit <= 0) sc->state = kMaxIt;
         else sc->state = kRunning;
     }
 }
 
-// dinv[s] = 1 / B_ss for centres with at least min_support points inside their support,
-// else 0 (pinned: the row and column are removed from the system).
+// Loop condition of the solve graph: keep iterating while the state is running.
+__global__ void k_cg_cond(const CgScalars* __restrict__ sc, cudaGraphConditionalHandle h) {
+    cudaGraphSetConditional(h, sc->state == kRunning ? 1u : 0u);
+}
+
+// Preconditioner set-up, one warp per cell: dinv[s] = 1 / B_ss for centres with at least
+// min_support points inside their support, else 0 (pinned: row and column removed from the
+// system); and, for cells with m <= kMaxBlock, the inverse of the cell's diagonal block
+// B[c, c] (pinned rows and columns replaced by the identity before, and zeroed after, the
+// inversion), by Gauss-Jordan elimination in FP64 without pivoting (the block is SPD),
+// symmetrised and stored row-major in the precision of B.
+constexpr int kBjWarps = 4;
 template <typename T>
-__global__ void k_dinv(Binned bd, const T* __restrict__ B, const int* __restrict__ support,
-                       int min_support, T* __restrict__ dinv, int* __restrict__ npinned) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(kBjWarps * 32)
+    k_prec_setup(Binned bd, const T* __restrict__ B, const int* __restrict__ support,
+                 int min_support, T* __restrict__ dinv, T* __restrict__ bjinv,
+                 int* __restrict__ npinned) {
+    __shared__ double A[kBjWarps][kMaxBlock][kMaxBlock + 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int c = blockIdx.x * kBjWarps + warp;
     if (c >= bd.g.ncell) return;
     const int cs = bd.cstart[c], m = bd.cstart[c + 1] - cs;
     if (m == 0) return;
-    const RowSeg sg = bd.seg[c];
-    const int L = sg.l0 + sg.l1 + sg.l2;
+    const int lp = bd.seg[c].lp;
     const T* Bc = B + bd.rboff[c];
     int np = 0;
-    for (int i = 0; i < m; ++i) {
-        const T d = Bc[int64_t(i) * L + i];
+    for (int i = lane; i < m; i += 32) {
+        const T d = Bc[int64_t(i) * lp + i];
         const bool pin = support[cs + i] < min_support || !(d > T(0));
         dinv[cs + i] = pin ? T(0) : T(1) / d;
         np += pin;
     }
-    if (np) atomicAdd(npinned, np);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) np += __shfl_xor_sync(kFull, np, o);
+    if (lane == 0 && np) atomicAdd(npinned, np);
+    if (m > kMaxBlock) return;
+    __syncwarp();
+    double (*a)[kMaxBlock + 1] = A[warp];
+    for (int e = lane; e < m * m; e += 32) {
+        const int i = e / m, j = e - (e / m) * m;
+        const bool pin = dinv[cs + i] == T(0) || dinv[cs + j] == T(0);
+        a[i][j] = pin ? (i == j ? 1.0 : 0.0) : double(Bc[int64_t(i) * lp + j]);
+    }
+    __syncwarp();
+    for (int k = 0; k < m; ++k) {
+        const double piv = a[k][k];
+        __syncwarp();
+        if (lane < m) a[k][lane] = (lane == k ? 1.0 : a[k][lane]) / piv;
+        __syncwarp();
+        for (int i = 0; i < m; ++i) {
+            if (i == k) continue;
+            const double f = a[i][k];
+            __syncwarp();
+            if (lane < m) a[i][lane] = (lane == k ? 0.0 : a[i][lane]) - f * a[k][lane];
+            __syncwarp();
+        }
+    }
+    T* out = bjinv + bd.bjoff[c];
+    for (int e = lane; e < m * m; e += 32) {
+        const int i = e / m, j = e - (e / m) * m;
+        const bool pin = dinv[cs + i] == T(0) || dinv[cs + j] == T(0);
+        out[e] = pin ? T(0) : T(0.5 * (a[i][j] + a[j][i]));
+    }
 }
 
 __global__ void k_gather(const double* __restrict__ src, const int* __restrict__ perm,
@@ -305,6 +489,19 @@ __global__ void k_scatter(const double* __restrict__ src, const int* __restrict_
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s < M) dst[perm[s]] = src[s];
 }
+// dst (sorted, precision T) = src (caller order, FP64), pinned rows zero.
+template <typename T>
+__global__ void k_to_sorted_T(const double* __restrict__ src, const int* __restrict__ perm,
+                              const T* __restrict__ dinv, T* __restrict__ dst, int M) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < M) dst[s] = dinv[s] == T(0) ? T(0) : T(src[perm[s]]);
+}
+template <typename T>
+__global__ void k_from_sorted_T(const T* __restrict__ src, const int* __restrict__ perm,
+                                double* __restrict__ dst, int M) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < M) dst[perm[s]] = double(src[s]);
+}
 
 // x64 = (x64 + scale * d32) on unpinned rows; x64 pinned rows forced to 0.
 __global__ void k_axpy_mixed(int M, double* __restrict__ x, const float* __restrict__ d,
@@ -313,13 +510,9 @@ __global__ void k_axpy_mixed(int M, double* __restrict__ x, const float* __restr
     if (i < M) x[i] = dinv[i] == 0.0f ? 0.0 : fma(scale, double(d[i]), x[i]);
 }
 
-__global__ void k_mask_zero(int M, double* __restrict__ x, const float* __restrict__ dinv32,
-                            const double* __restrict__ dinv64) {
+__global__ void k_mask_zero(int M, double* __restrict__ x, const float* __restrict__ dinv32) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < M) {
-        const bool pin = dinv32 ? dinv32[i] == 0.0f : dinv64[i] == 0.0;
-        if (pin) x[i] = 0.0;
-    }
+    if (i < M && dinv32[i] == 0.0f) x[i] = 0.0;
 }
 
 // ||v||^2 over unpinned rows into out[0] (single block, fixed order).
@@ -336,137 +529,158 @@ __global__ void k_norm2(int M, const double* __restrict__ v, const float* __rest
 }
 
 template <typename T>
-struct CgVecs {
-    T *x, *r, *z, *p, *q, *dinv;
-};
-
-template <typename T>
-CgVecs<T> vecs(rbf_ctx* ctx);
-template <>
-CgVecs<double> vecs<double>(rbf_ctx* ctx) {
-    return {ctx->x.as<double>(), ctx->r.as<double>(), ctx->z.as<double>(), ctx->p.as<double>(),
-            ctx->q.as<double>(), ctx->dinv.as<double>()};
-}
-template <>
-CgVecs<float> vecs<float>(rbf_ctx* ctx) {
-    return {ctx->x32.as<float>(), ctx->r32.as<float>(), ctx->z32.as<float>(), ctx->p32.as<float>(),
-            ctx->q32.as<float>(), ctx->dinv32.as<float>()};
+CgVec<T> cg_vectors(rbf_ctx* ctx) {
+    const int slot = sizeof(T) == 8 ? 0 : 1;
+    T* base = ctx->cgv[slot].as<T>();
+    const size_t M = size_t(ctx->M);
+    CgVec<T> v;
+    v.x = base;
+    v.u = base + M;
+    v.p = base + 2 * M;
+    v.r[0] = base + 3 * M;
+    v.r[1] = base + 4 * M;
+    v.s[0] = base + 5 * M;
+    v.s[1] = base + 6 * M;
+    v.w[0] = base + 7 * M;
+    v.w[1] = base + 8 * M;
+    v.dinv = slot == 0 ? reinterpret_cast<const T*>(ctx->dinv.p)
+                       : reinterpret_cast<const T*>(ctx->dinv32.p);
+    v.bjinv = slot == 0 ? reinterpret_cast<const T*>(ctx->bjinv.p)
+                        : reinterpret_cast<const T*>(ctx->bjinv32.p);
+    return v;
 }
 
 int spmv_grid(const rbf_ctx* ctx) { return div_up(ctx->g.ncell, kSpmvWarps); }
-int vec_grid(const rbf_ctx* ctx) { return std::min(div_up(ctx->M, kVecThreads), 152 * 8); }
-
-// CUDA graph holding `chunk` CG iterations for precision T (cached per context).
-// Graph chunk sizes are powers of two from 8 to 256.
-int chunk_of(const rbf_ctx*, int chunk) {
-    int ck = 0;
-    while ((8 << ck) < chunk && ck < 5) ++ck;
-    return 8 << ck;
+int vec_grid(const rbf_ctx* ctx) {
+    return std::max(1, std::min(div_up(ctx->M, kVecThreads), 152 * 8));
 }
 
+// One CG iteration (two kernels) reading the buffers of parity P, on stream cs.
 template <typename T>
-rbf_status cg_graph(rbf_ctx* ctx, int chunk, cudaGraphExec_t* out) {
-    const int slot = sizeof(T) == 8 ? 0 : 1;
-    int ck = 0;
-    while ((8 << ck) < chunk && ck < 5) ++ck;
-    chunk = 8 << ck;
-    rbf_ctx::GraphCache& gc = ctx->graphs[slot][ck];
+void launch_iteration(rbf_ctx* ctx, const CgVec<T>& v, int P, cudaStream_t cs) {
     const Binned bd = view(ctx);
-    const CgVecs<T> v = vecs<T>(ctx);
-    const void* key[8] = {ctx->bvals.p, v.x, v.p, v.q, ctx->scal.p, ctx->partial.p, bd.cstart,
-                          bd.seg};
-    bool hit = gc.exec && gc.M == ctx->M && gc.ncell == ctx->g.ncell && gc.gx == ctx->g.gx;
-    for (int k = 0; k < 8 && hit; ++k) hit = gc.key[k] == key[k];
+    CgScalars* sc = ctx->scal.as<CgScalars>();
+    k_cg_spmv<T><<<spmv_grid(ctx), kSpmvWarps * 32, 0, cs>>>(bd, ctx->bvals.as<T>(), v.u, v.w[P], sc);
+    k_cg_update<T><<<vec_grid(ctx), kVecThreads, 0, cs>>>(bd, v, P, sc, ctx->partial.as<double>());
+}
+
+// The solve graph of precision T: one conditional WHILE node whose body runs
+// kItersPerBody CG iterations (two kernels each) and then sets the loop condition from the
+// device-side state, so the whole iteration runs on the GPU without host round trips.
+// Instantiated once per context, precision and workspace layout, then replayed.
+template <typename T>
+rbf_status cg_graph(rbf_ctx* ctx, cudaGraphExec_t* out) {
+    rbf_ctx::SolveGraph& sg = ctx->cg_graph[sizeof(T) == 8 ? 0 : 1];
+    const CgVec<T> v = cg_vectors<T>(ctx);
+    const void* key[10] = {ctx->bvals.p, v.x, v.dinv, v.bjinv, ctx->scal.p, ctx->partial.p,
+                           ctx->cstart.p, ctx->seg.p, ctx->rboff.p, ctx->bjoff.p};
+    bool hit = sg.exec && sg.ncell == ctx->g.ncell && sg.M == ctx->M && sg.gx == ctx->g.gx &&
+               sg.crow == ctx->crow.p;
+    for (int k = 0; k < 10 && hit; ++k) hit = sg.key[k] == key[k];
     if (hit) {
-        *out = gc.exec;
+        *out = sg.exec;
         return RBF_OK;
     }
-    if (gc.exec) {
-        cudaGraphExecDestroy(gc.exec);
-        gc.exec = nullptr;
+    if (sg.exec) {
+        cudaGraphExecDestroy(sg.exec);
+        sg.exec = nullptr;
     }
+    if (!ctx->capture_stream)
+        RBF_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    RBF_CUDA_TRY(cudaGraphCreate(&graph, 0));
+    cudaGraphConditionalHandle handle;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = handle;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp);
+    cudaGraph_t body = e == cudaSuccess ? cp.conditional.phGraph_out[0] : nullptr;
     cudaStream_t cs = ctx->capture_stream;
-    RBF_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-    CgScalars* sc = ctx->scal.as<CgScalars>();
-    double* part = ctx->partial.as<double>();
-    const T* B = ctx->bvals.as<T>();
-    for (int k = 0; k < chunk; ++k) {
-        k_spmv<T><<<spmv_grid(ctx), kSpmvWarps * 32, 0, cs>>>(bd, B, v.p, v.q, v.dinv, sc, part);
-        k_cg_update<T><<<vec_grid(ctx), kVecThreads, 0, cs>>>(ctx->M, v.x, v.r, v.z, v.p, v.q,
-                                                              v.dinv, sc, part);
-        k_cg_p<T><<<vec_grid(ctx), kVecThreads, 0, cs>>>(ctx->M, v.z, v.p, sc);
+    if (e == cudaSuccess)
+        e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        for (int k = 0; k < kItersPerBody; ++k) launch_iteration<T>(ctx, v, k & 1, cs);
+        k_cg_cond<<<1, 1, 0, cs>>>(ctx->scal.as<CgScalars>(), handle);
+        cudaGraph_t captured = nullptr;
+        e = cudaStreamEndCapture(cs, &captured);
     }
-    cudaGraph_t graph;
-    cudaError_t e = cudaStreamEndCapture(cs, &graph);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture", __FILE__, __LINE__);
-    e = cudaGraphInstantiate(&gc.exec, graph, 0);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&sg.exec, graph, 0);
     cudaGraphDestroy(graph);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphInstantiate", __FILE__, __LINE__);
-    gc.M = ctx->M;
-    gc.ncell = ctx->g.ncell;
-    gc.gx = ctx->g.gx;
-    for (int k = 0; k < 8; ++k) gc.key[k] = key[k];
-    *out = gc.exec;
+    if (e != cudaSuccess) {
+        sg.exec = nullptr;
+        return cuda_fail(ctx, e, "building the CG solve graph", __FILE__, __LINE__);
+    }
+    sg.ncell = ctx->g.ncell;
+    sg.M = ctx->M;
+    sg.gx = ctx->g.gx;
+    sg.crow = ctx->crow.p;
+    for (int k = 0; k < 10; ++k) sg.key[k] = key[k];
+    *out = sg.exec;
     return RBF_OK;
 }
 
-// Jacobi-PCG on the assembled B (precision T) for B x = bscale * b. x holds the start
-// vector when use_x0 (sorted order, pinned rows zero). Returns the final state.
+// Start kernels of a solve of B x = bscale * b (x in the workspace holds the start vector
+// when use_x0).
 template <typename T, typename TB>
-rbf_status run_cg(rbf_ctx* ctx, const TB* b, double bscale, bool use_x0, double tol, int maxit,
-                  int* iters, double* relres, int* state, cudaStream_t st) {
+rbf_status cg_start(rbf_ctx* ctx, const TB* b, double bscale, bool use_x0, double tol, int maxit,
+                    cudaStream_t st) {
     const Binned bd = view(ctx);
-    const CgVecs<T> v = vecs<T>(ctx);
-    const int M = ctx->M;
+    const CgVec<T> v = cg_vectors<T>(ctx);
     CgScalars* sc = ctx->scal.as<CgScalars>();
-    double* part = ctx->partial.as<double>();
     CgScalars h{};
     h.tol2 = tol * tol;
+    h.bscale = bscale;
     h.maxit = maxit;
     h.state = kRunning;
     RBF_CUDA_TRY(cudaMemcpyAsync(sc, &h, sizeof(CgScalars), cudaMemcpyHostToDevice, st));
     if (use_x0) {
-        k_spmv<T><<<spmv_grid(ctx), kSpmvWarps * 32, 0, st>>>(bd, ctx->bvals.as<T>(), v.x, v.q,
-                                                              v.dinv, nullptr, nullptr);
-    } else {
-        RBF_CUDA_TRY(cudaMemsetAsync(v.x, 0, sizeof(T) * M, st));
+        RBF_CUDA_TRY(cudaMemsetAsync(v.w[1], 0, sizeof(T) * ctx->M, st));
+        k_spmv<T><<<spmv_grid(ctx), kSpmvWarps * 32, 0, st>>>(bd, ctx->bvals.as<T>(), v.x, v.w[1]);
+        ctx->launches += 1;
     }
-    k_cg_init<T, TB><<<vec_grid(ctx), kVecThreads, 0, st>>>(M, b, bscale, use_x0 ? v.q : nullptr,
-                                                            v.r, v.z, v.p, v.dinv, sc, part);
+    k_cg_init<T, TB><<<vec_grid(ctx), kVecThreads, 0, st>>>(bd, v, b, use_x0 ? 1 : 0, sc,
+                                                            ctx->partial.as<double>());
+    ctx->launches += 1;
     RBF_CUDA_TRY(cudaGetLastError());
-    ctx->launches += use_x0 ? 2 : 1;
+    return RBF_OK;
+}
+
+// Preconditioned CG on the assembled B (precision T) for B x = bscale * b: start kernels on
+// `st`, then one launch of the solve graph.
+template <typename T, typename TB>
+rbf_status run_cg(rbf_ctx* ctx, const TB* b, double bscale, bool use_x0, double tol, int maxit,
+                  int* iters, double* relres, int* state, cudaStream_t st) {
+    rbf_status s;
+    cudaGraphExec_t ex;
+    if ((s = cg_graph<T>(ctx, &ex)) != RBF_OK) return s;
+    if ((s = cg_start<T, TB>(ctx, b, bscale, use_x0, tol, maxit, st)) != RBF_OK) return s;
+    RBF_CUDA_TRY(cudaGraphLaunch(ex, st));
     CgScalars* hs = static_cast<CgScalars*>(ctx->hpinned);
-    RBF_CUDA_TRY(cudaMemcpyAsync(hs, sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
+    RBF_CUDA_TRY(cudaMemcpyAsync(hs, ctx->scal.p, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
     RBF_CUDA_TRY(cudaStreamSynchronize(st));
-    // replay graph chunks; the chunk length follows the observed convergence rate
-    int chunk = 16;
-    double log_rr_prev = log(std::max(hs->rr, 1e-300));
-    int it_prev = 0;
-    while (hs->state == kRunning) {
-        cudaGraphExec_t ex;
-        rbf_status s = cg_graph<T>(ctx, chunk, &ex);
-        if (s != RBF_OK) return s;
-        RBF_CUDA_TRY(cudaGraphLaunch(ex, st));
-        ctx->launches += 3 * chunk_of(ctx, chunk);
-        RBF_CUDA_TRY(cudaMemcpyAsync(hs, sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
-        RBF_CUDA_TRY(cudaStreamSynchronize(st));
-        if (hs->state != kRunning) break;
-        // predict the iterations left from the decrease of log ||r||^2 per iteration
-        const double lr = log(std::max(hs->rr, 1e-300));
-        const double target = log(std::max(hs->tol2 * hs->bb, 1e-300));
-        const double rate = (log_rr_prev - lr) / std::max(1, hs->it - it_prev);
-        int want = rate > 0 ? int((lr - target) / rate) + 1 : 64;
-        want = std::min(std::max(want, 8), std::min(256, std::max(8, hs->maxit - hs->it)));
-        // keep a small set of graph sizes so that the cache stays warm
-        int c2 = 8;
-        while (c2 < want) c2 *= 2;
-        chunk = c2;
-        log_rr_prev = lr;
-        it_prev = hs->it;
-    }
+    // kernels launched by the graph: per loop pass 2 * kItersPerBody + 1
+    const int passes = std::max(1, (hs->it + kItersPerBody - 1) / kItersPerBody);
+    ctx->launches += int64_t(passes) * (2 * kItersPerBody + 1);
     *iters = hs->it;
     *relres = hs->bb > 0 ? sqrt(hs->rr / hs->bb) : 0.0;
     *state = hs->state;
+    return RBF_OK;
+}
+
+// Timing hook: a solve of B x = b from x = 0 whose `reps` CG iterations are plain kernel
+// launches (two per iteration) instead of the graph loop, on the solver's workspace.
+template <typename T>
+rbf_status bench_cg_impl(rbf_ctx* ctx, int reps, cudaStream_t st) {
+    rbf_status s = cg_start<T, double>(ctx, ctx->bvec.as<double>(), 1.0, false, 0.0, 1 << 30, st);
+    if (s != RBF_OK) return s;
+    const CgVec<T> v = cg_vectors<T>(ctx);
+    for (int k = 0; k < reps; ++k) launch_iteration<T>(ctx, v, k & 1, st);
+    RBF_CUDA_TRY(cudaGetLastError());
+    ctx->launches += 2 * int64_t(reps);
     return RBF_OK;
 }
 
@@ -481,19 +695,23 @@ void launch_scatter_orig(const double* c_sorted, const int* cperm, double* c_ori
     k_scatter<<<div_up(M, 256), 256, 0, st>>>(c_sorted, cperm, c_orig, M);
 }
 
-size_t cg_scalars_bytes() { return sizeof(CgScalars); }
+rbf_status bench_cg_run(rbf_ctx* ctx, int reps, cudaStream_t st) {
+    return ctx->prec == RBF_FP64 ? bench_cg_impl<double>(ctx, reps, st)
+                                 : bench_cg_impl<float>(ctx, reps, st);
+}
 
 rbf_status bench_spmv_run(rbf_ctx* ctx, int reps, cudaStream_t st) {
     const Binned bd = view(ctx);
     for (int k = 0; k < reps; ++k) {
-        if (ctx->prec == RBF_FP64)
-            k_spmv<double><<<spmv_grid(ctx), kSpmvWarps * 32, 0, st>>>(
-                bd, ctx->bvals.as<double>(), ctx->p.as<double>(), ctx->q.as<double>(),
-                ctx->dinv.as<double>(), nullptr, nullptr);
-        else
-            k_spmv<float><<<spmv_grid(ctx), kSpmvWarps * 32, 0, st>>>(
-                bd, ctx->bvals.as<float>(), ctx->p32.as<float>(), ctx->q32.as<float>(),
-                ctx->dinv32.as<float>(), nullptr, nullptr);
+        if (ctx->prec == RBF_FP64) {
+            const CgVec<double> v = cg_vectors<double>(ctx);
+            k_spmv<double><<<spmv_grid(ctx), kSpmvWarps * 32, 0, st>>>(bd, ctx->bvals.as<double>(),
+                                                                       v.u, v.w[0]);
+        } else {
+            const CgVec<float> v = cg_vectors<float>(ctx);
+            k_spmv<float><<<spmv_grid(ctx), kSpmvWarps * 32, 0, st>>>(bd, ctx->bvals.as<float>(),
+                                                                     v.u, v.w[0]);
+        }
     }
     RBF_CUDA_TRY(cudaGetLastError());
     ctx->launches += reps;
@@ -502,7 +720,8 @@ rbf_status bench_spmv_run(rbf_ctx* ctx, int reps, cudaStream_t st) {
 
 static rbf_status finish_status(rbf_ctx* ctx, int state) {
     if (state == kConverged) return RBF_OK;
-    if (state == kBreakdown) return set_err(ctx, RBF_ERR_BREAKDOWN, "CG breakdown (p^T B p <= 0 or non-finite)");
+    if (state == kBreakdown)
+        return set_err(ctx, RBF_ERR_BREAKDOWN, "CG breakdown (non-positive curvature or non-finite scalar)");
     return set_err(ctx, RBF_ERR_NOT_CONVERGED, "CG reached maxit before tol");
 }
 
@@ -516,27 +735,25 @@ rbf_status solve_run(rbf_ctx* ctx, double* c, int use_c0, double tol, int maxit,
     ENS(x, sizeof(double) * M);
     ENS(r, sizeof(double) * M);
     ENS(scal, sizeof(CgScalars) + 64);
-    ENS(partial, sizeof(double) * 3 * std::max(spmv_grid(ctx), vec_grid(ctx)));
-    int64_t* npin_h = static_cast<int64_t*>(ctx->hpinned) + 64;
+    ENS(partial, sizeof(double) * 3 * std::max(vec_grid(ctx), spmv_grid(ctx)));
+    int64_t* npin_h = static_cast<int64_t*>(ctx->hpinned) + 256;
     int* npin_d = reinterpret_cast<int*>(ctx->scal.as<char>() + sizeof(CgScalars));
     RBF_CUDA_TRY(cudaMemsetAsync(npin_d, 0, sizeof(int), st));
     rbf_solve_info inf{};
     int state = kConverged;
 
     if (ctx->prec == RBF_FP64) {
-        ENS(z, sizeof(double) * M);
-        ENS(p, sizeof(double) * M);
-        ENS(q, sizeof(double) * M);
+        ENS(cgv[0], sizeof(double) * kCgVecs * size_t(M));
         ENS(dinv, sizeof(double) * M);
-        k_dinv<double><<<div_up(ctx->g.ncell, 128), 128, 0, st>>>(
+        ENS(bjinv, sizeof(double) * std::max<int64_t>(ctx->nbj, 1));
+        k_prec_setup<double><<<div_up(ctx->g.ncell, kBjWarps), kBjWarps * 32, 0, st>>>(
             bd, ctx->bvals.as<double>(), ctx->support.as<int>(), min_support,
-            ctx->dinv.as<double>(), npin_d);
+            ctx->dinv.as<double>(), ctx->bjinv.as<double>(), npin_d);
         ctx->launches += 1;
+        const CgVec<double> v = cg_vectors<double>(ctx);
         if (use_c0) {
-            launch_gather_sorted(c, bd.cperm, ctx->x.as<double>(), M, st);
-            k_mask_zero<<<div_up(M, 256), 256, 0, st>>>(M, ctx->x.as<double>(), nullptr,
-                                                        ctx->dinv.as<double>());
-            ctx->launches += 2;
+            k_to_sorted_T<double><<<div_up(M, 256), 256, 0, st>>>(c, bd.cperm, v.dinv, v.x, M);
+            ctx->launches += 1;
         }
         RBF_CUDA_TRY(cudaGetLastError());
         int it = 0;
@@ -544,23 +761,23 @@ rbf_status solve_run(rbf_ctx* ctx, double* c, int use_c0, double tol, int maxit,
         s = run_cg<double, double>(ctx, ctx->bvec.as<double>(), 1.0, use_c0 != 0, tol, maxit, &it,
                                    &rel, &state, st);
         if (s != RBF_OK) return s;
+        k_from_sorted_T<double><<<div_up(M, 256), 256, 0, st>>>(v.x, bd.cperm, c, M);
+        ctx->launches += 1;
         inf.iterations = it;
         inf.rel_residual = rel;
     } else {
-        ENS(x32, sizeof(float) * M);
-        ENS(r32, sizeof(float) * M);
-        ENS(z32, sizeof(float) * M);
-        ENS(p32, sizeof(float) * M);
-        ENS(q32, sizeof(float) * M);
+        ENS(cgv[1], sizeof(float) * kCgVecs * size_t(M));
         ENS(dinv32, sizeof(float) * M);
-        k_dinv<float><<<div_up(ctx->g.ncell, 128), 128, 0, st>>>(
+        ENS(bjinv32, sizeof(float) * std::max<int64_t>(ctx->nbj, 1));
+        k_prec_setup<float><<<div_up(ctx->g.ncell, kBjWarps), kBjWarps * 32, 0, st>>>(
             bd, ctx->bvals.as<float>(), ctx->support.as<int>(), min_support,
-            ctx->dinv32.as<float>(), npin_d);
+            ctx->dinv32.as<float>(), ctx->bjinv32.as<float>(), npin_d);
         ctx->launches += 1;
+        const CgVec<float> v = cg_vectors<float>(ctx);
         double* x64 = ctx->x.as<double>();
         double* r64 = ctx->r.as<double>();
         double* nrm_d = reinterpret_cast<double*>(ctx->scal.as<char>() + sizeof(CgScalars) + 8);
-        double* nrm_h = reinterpret_cast<double*>(static_cast<char*>(ctx->hpinned) + 1024);
+        double* nrm_h = reinterpret_cast<double*>(static_cast<char*>(ctx->hpinned) + 3072);
         const float* dinv32 = ctx->dinv32.as<float>();
         // ||b|| over unpinned rows
         k_norm2<<<1, 1024, 0, st>>>(M, ctx->bvec.as<double>(), dinv32, nrm_d);
@@ -568,7 +785,7 @@ rbf_status solve_run(rbf_ctx* ctx, double* c, int use_c0, double tol, int maxit,
         RBF_CUDA_TRY(cudaMemcpyAsync(nrm_h, nrm_d, sizeof(double), cudaMemcpyDeviceToHost, st));
         if (use_c0) {
             launch_gather_sorted(c, bd.cperm, x64, M, st);
-            k_mask_zero<<<div_up(M, 256), 256, 0, st>>>(M, x64, dinv32, nullptr);
+            k_mask_zero<<<div_up(M, 256), 256, 0, st>>>(M, x64, dinv32);
             ctx->launches += 2;
             RBF_CUDA_TRY(cudaMemsetAsync(r64, 0, sizeof(double) * M, st));
             if ((s = residual_run(ctx, x64, r64, false, st)) != RBF_OK) return s;
@@ -579,18 +796,23 @@ rbf_status solve_run(rbf_ctx* ctx, double* c, int use_c0, double tol, int maxit,
         }
         RBF_CUDA_TRY(cudaStreamSynchronize(st));
         const double bnorm = sqrt(nrm_h[0]);
+        auto norm_r64 = [&](double* out) -> rbf_status {
+            k_norm2<<<1, 1024, 0, st>>>(M, r64, dinv32, nrm_d);
+            ctx->launches += 1;
+            RBF_CUDA_TRY(cudaMemcpyAsync(nrm_h, nrm_d, sizeof(double), cudaMemcpyDeviceToHost, st));
+            RBF_CUDA_TRY(cudaStreamSynchronize(st));
+            *out = sqrt(nrm_h[0]);
+            return RBF_OK;
+        };
+        double rn = 0.0;
+        if ((s = norm_r64(&rn)) != RBF_OK) return s;
         int total_it = 0, outer = 0;
         double rel = 0.0;
         state = kMaxIt;
         // Inner tolerance: each refinement step should gain about 4 digits; FP32 rounding of
         // B (relative 6e-8 per entry) limits the gain per step, not the final accuracy.
         const double inner_tol = 1e-4;
-        for (outer = 0; outer <= 30; ++outer) {
-            k_norm2<<<1, 1024, 0, st>>>(M, r64, dinv32, nrm_d);
-            ctx->launches += 1;
-            RBF_CUDA_TRY(cudaMemcpyAsync(nrm_h, nrm_d, sizeof(double), cudaMemcpyDeviceToHost, st));
-            RBF_CUDA_TRY(cudaStreamSynchronize(st));
-            const double rn = sqrt(nrm_h[0]);
+        for (outer = 0;; ++outer) {
             rel = bnorm > 0 ? rn / bnorm : 0.0;
             if (rel <= tol || rn == 0.0) {
                 state = kConverged;
@@ -603,23 +825,50 @@ rbf_status solve_run(rbf_ctx* ctx, double* c, int use_c0, double tol, int maxit,
                                       maxit, &it, &irel, &ist, st);
             if (s != RBF_OK) return s;
             total_it += it;
-            if (ist == kBreakdown) {
+            // An inner breakdown (FP32 rounding can make B32 indefinite when the system is
+            // very ill-conditioned) ends the inner solve; its last iterate is still a usable
+            // correction, and the FP64 residual below decides whether it helped.
+            if (ist == kBreakdown && it == 0) {
                 state = kBreakdown;
                 break;
             }
-            k_axpy_mixed<<<div_up(M, 256), 256, 0, st>>>(M, x64, ctx->x32.as<float>(), rn, dinv32);
-            ctx->launches += 2;   // with the mask below
+            k_axpy_mixed<<<div_up(M, 256), 256, 0, st>>>(M, x64, v.x, rn, dinv32);
             RBF_CUDA_TRY(cudaMemsetAsync(r64, 0, sizeof(double) * M, st));
             if ((s = residual_run(ctx, x64, r64, false, st)) != RBF_OK) return s;
-            k_mask_zero<<<div_up(M, 256), 256, 0, st>>>(M, r64, dinv32, nullptr);
+            k_mask_zero<<<div_up(M, 256), 256, 0, st>>>(M, r64, dinv32);
+            ctx->launches += 2;
+            double rn_new = 0.0;
+            if ((s = norm_r64(&rn_new)) != RBF_OK) return s;
+            if (!(rn_new < 0.5 * rn)) {   // stalled: the FP32 matrix cannot resolve the system
+                rn = std::min(rn, rn_new);
+                ++outer;
+                state = kMaxIt;
+                break;
+            }
+            rn = rn_new;
         }
         inf.iterations = total_it;
         inf.refinements = outer;
-        inf.rel_residual = rel;
+        inf.rel_residual = bnorm > 0 ? rn / bnorm : 0.0;
+        if (state != kConverged) {
+            // Promote: assemble B in FP64 and finish with FP64 CG started from the refined
+            // iterate.
+            launch_scatter_orig(x64, bd.cperm, c, M, st);
+            ctx->launches += 1;
+            if ((s = assemble_run(ctx, ctx->kernel, RBF_FP64, st)) != RBF_OK) return s;
+            ctx->prec = RBF_FP64;
+            rbf_solve_info inf64{};
+            s = solve_run(ctx, c, 1, tol, maxit, min_support, &inf64, st);
+            inf64.iterations += total_it;
+            inf64.refinements = outer;
+            inf64.promoted = 1;
+            if (info) *info = inf64;
+            return s;
+        }
+        launch_scatter_orig(x64, bd.cperm, c, M, st);
+        ctx->launches += 1;
     }
-    launch_scatter_orig(ctx->x.as<double>(), bd.cperm, c, M, st);
     RBF_CUDA_TRY(cudaGetLastError());
-    ctx->launches += 1;
     ctx->solved = true;
     RBF_CUDA_TRY(cudaMemcpyAsync(npin_h, npin_d, sizeof(int), cudaMemcpyDeviceToHost, st));
     RBF_CUDA_TRY(cudaStreamSynchronize(st));
