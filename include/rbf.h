@@ -142,6 +142,13 @@ rbf_status rbf_eval(rbf_ctx* ctx, const double* c, const double* qx, const doubl
 rbf_status rbf_eval_grid(rbf_ctx* ctx, const double* c, int nx, int ny, const double* box,
                          double* f, void* stream);
 
+/* Solver parameters (HOST call, takes effect at the next rbf_solve):
+ *   "inner_tol"        relative tolerance of each FP32 inner solve of RBF_FP32_REFINE, in
+ *                      (0, 1); default 1e-3
+ *   "max_refinements"  FP64 refinement steps of RBF_FP32_REFINE, in [0, 1000]; default 30
+ * Returns RBF_ERR_ARG for an unknown name or a value out of range. */
+rbf_status rbf_set_param(rbf_ctx* ctx, const char* name, double value);
+
 /* Diagnostics: number of stored B values (upper cell-pair blocks) and bytes per value
  * of the last assembly; sizes of the cell grid. HOST outputs, any may be NULL. */
 rbf_status rbf_get_layout(const rbf_ctx* ctx, int64_t* nvals, int* value_bytes, int* gx,
@@ -158,10 +165,10 @@ rbf_status rbf_export_upper(rbf_ctx* ctx, int64_t cap, int32_t* row, int32_t* co
  * inside replayed CUDA graphs included). HOST output. */
 rbf_status rbf_get_launch_count(const rbf_ctx* ctx, int64_t* launches);
 
-/* Diagnostics / timing: launch the solver's SpMV kernel y = B x (Section 4's y = Q x on
- * this library's cell-blocked symmetric storage) `reps` times on `stream`, on the solver's
- * own workspace vectors, exactly as one CG iteration launches it. Requires a preceding
- * rbf_solve on this context (so the workspace exists). Asynchronous. */
+/* Diagnostics / timing: launch the solver's SpMV kernel y += B x (Section 4's y = Q x on
+ * this library's cell-blocked symmetric storage) `reps` times on `stream` with x = 1, in the
+ * launch configuration a CG iteration uses, on the solver's workspace (which it allocates if
+ * needed and overwrites). Requires a preceding rbf_assemble. Asynchronous. */
 rbf_status rbf_bench_spmv(rbf_ctx* ctx, int reps, void* stream);
 
 /* Diagnostics / timing: run `reps` preconditioned CG iterations on B c = b from c = 0 with
@@ -169,6 +176,12 @@ rbf_status rbf_bench_spmv(rbf_ctx* ctx, int reps, void* stream);
  * inside one CUDA graph), so that the kernels can be timed or profiled one by one. Uses and
  * overwrites the solver's workspace; requires a preceding rbf_solve. Asynchronous. */
 rbf_status rbf_bench_cg(rbf_ctx* ctx, int reps, void* stream);
+
+/* Self-test of the device square root used for distances (Newton-Raphson iteration for the
+ * reciprocal square root seeded by the FP32 hardware estimate): for each a[i] >= 0 (DEVICE,
+ * n values) writes out[2i] = that square root and out[2i+1] = CUDA's sqrt(a[i]) (DEVICE,
+ * 2n values). Asynchronous. */
+rbf_status rbf_selftest_sqrt(const double* a, double* out, int64_t n, void* stream);
 
 #ifdef __cplusplus
 }

@@ -162,6 +162,10 @@ class Context:
                                             C.byref(gy)), "rbf_get_layout")
         return dict(nvals=nv.value, value_bytes=vb.value, gx=gx.value, gy=gy.value)
 
+    def set_param(self, name: str, value: float):
+        """Solver parameters: "inner_tol", "max_refinements" (see include/rbf.h)."""
+        self._check(self.lib.rbf_set_param(self._h, name.encode(), float(value)), "rbf_set_param")
+
     def launch_count(self) -> int:
         n = C.c_int64()
         self._check(self.lib.rbf_get_launch_count(self._h, C.byref(n)), "rbf_get_launch_count")

@@ -45,6 +45,8 @@ SIGNATURES = {
     "rbf_get_layout": (_I, [_P, C.POINTER(_I64), C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)]),
     "rbf_export_upper": (_I, [_P, _I64, _P, _P, _P, _P, _P, C.POINTER(_I64), _P]),
     "rbf_get_launch_count": (_I, [_P, C.POINTER(_I64)]),
+    "rbf_set_param": (_I, [_P, C.c_char_p, _D]),
+    "rbf_selftest_sqrt": (_I, [_P, _P, _I64, _P]),
     "rbf_bench_spmv": (_I, [_P, _I, _P]),
     "rbf_bench_cg": (_I, [_P, _I, _P]),
 }

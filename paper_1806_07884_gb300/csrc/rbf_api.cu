@@ -3,6 +3,8 @@
 #include <math.h>
 #include <stdio.h>
 
+#include <string.h>
+
 #include <algorithm>
 #include <new>
 
@@ -78,6 +80,7 @@ Binned view(const rbf_ctx* ctx) {
     v.rboff = ctx->rboff.as<int64_t>();
     v.bjoff = ctx->bjoff.as<int64_t>();
     v.crow = ctx->crow.as<int4>();
+    v.cdesc = ctx->cdesc.as<CellDesc>();
     return v;
 }
 
@@ -145,7 +148,7 @@ rbf_status rbf_destroy(rbf_ctx* ctx) {
                        &ctx->seg, &ctx->rbsize, &ctx->rboff, &ctx->wcount, &ctx->wstart, &ctx->bjsize, &ctx->bjoff,
                        &ctx->work, &ctx->scan_tmp, &ctx->stats, &ctx->bvals, &ctx->bvec,
                        &ctx->support, &ctx->x, &ctx->r, &ctx->cgv[0], &ctx->cgv[1],
-                       &ctx->dinv, &ctx->dinv32, &ctx->bjinv, &ctx->bjinv32, &ctx->crow,
+                       &ctx->dinv, &ctx->dinv32, &ctx->bjinv, &ctx->bjinv32, &ctx->crow, &ctx->cdesc,
                        &ctx->partial, &ctx->scal, &ctx->csort};
     for (rbf_buf* b : bufs) release(ctx, *b);
     if (ctx->hpinned) cudaFreeHost(ctx->hpinned);
@@ -259,6 +262,26 @@ rbf_status rbf_export_upper(rbf_ctx* ctx, int64_t cap, int32_t* row, int32_t* co
     return export_upper_run(ctx, cap, row, col, val, bvec, support, nnz, as_stream(stream));
 }
 
+rbf_status rbf_selftest_sqrt(const double* a, double* out, int64_t n, void* stream) {
+    if (n < 0 || (n > 0 && (!a || !out))) return RBF_ERR_ARG;
+    return diag_sqrt_run(a, out, n, as_stream(stream));
+}
+
+rbf_status rbf_set_param(rbf_ctx* ctx, const char* name, double value) {
+    if (!ctx || !name) return RBF_ERR_ARG;
+    if (!strcmp(name, "inner_tol")) {
+        if (!(value > 0.0 && value < 1.0)) return set_err(ctx, RBF_ERR_ARG, "inner_tol must be in (0, 1)");
+        ctx->inner_tol = value;
+        return RBF_OK;
+    }
+    if (!strcmp(name, "max_refinements")) {
+        if (!(value >= 0.0 && value <= 1000.0)) return set_err(ctx, RBF_ERR_ARG, "max_refinements must be in [0, 1000]");
+        ctx->max_refine = int(value);
+        return RBF_OK;
+    }
+    return set_err(ctx, RBF_ERR_ARG, "unknown parameter");
+}
+
 rbf_status rbf_get_launch_count(const rbf_ctx* ctx, int64_t* launches) {
     if (!ctx || !launches) return RBF_ERR_ARG;
     *launches = ctx->launches;
@@ -267,7 +290,7 @@ rbf_status rbf_get_launch_count(const rbf_ctx* ctx, int64_t* launches) {
 
 rbf_status rbf_bench_spmv(rbf_ctx* ctx, int reps, void* stream) {
     if (!ctx) return RBF_ERR_ARG;
-    if (!ctx->solved || !ctx->assembled) return set_err(ctx, RBF_ERR_ARG, "rbf_bench_spmv before rbf_solve");
+    if (!ctx->assembled) return set_err(ctx, RBF_ERR_ARG, "rbf_bench_spmv before rbf_assemble");
     if (reps < 0) return set_err(ctx, RBF_ERR_ARG, "reps < 0");
     DeviceGuard dg(ctx->device);
     return bench_spmv_run(ctx, reps, as_stream(stream));

@@ -30,6 +30,8 @@ struct CandSmem {
     int* a9;            // [npad] local cell 0..8 (row-major in the 3x3 block)
     long long* rowbase; // [npad] offset of the candidate's row of B
     double* cval;       // [npad] coefficient (residual pass only)
+    float* lu;          // [npad] FP32 coordinates in the point cell's frame, units of R
+    float* lv;          //        (the same arrays as x, y in the FP32 path)
 };
 
 struct LocalCells {
@@ -82,12 +84,11 @@ __device__ void stage_candidates(const Binned& bd, const LocalCells& lc, const C
             const RowSeg sg = bd.seg[cc];
             cs.rowbase[a] = (long long)bd.rboff[cc] +
                             (long long)(s - bd.cstart[cc]) * (long long)sg.lp;
+            cs.lu[a] = bd.cu[s] + float((k % 3) - 1);
+            cs.lv[a] = bd.cv[s] + float((k / 3) - 1);
             if constexpr (sizeof(CT) == 8) {
                 cs.x[a] = bd.cx[s];
                 cs.y[a] = bd.cy[s];
-            } else {
-                cs.x[a] = bd.cu[s] + float((k % 3) - 1);
-                cs.y[a] = bd.cv[s] + float((k / 3) - 1);
             }
             if (cs.cval) cs.cval[a] = c_sorted ? c_sorted[s] : 0.0;
         } else {
@@ -96,6 +97,8 @@ __device__ void stage_candidates(const Binned& bd, const LocalCells& lc, const C
             cs.rowbase[a] = 0;
             cs.x[a] = CT(1e30);
             cs.y[a] = CT(1e30);
+            cs.lu[a] = 1e30f;
+            cs.lv[a] = 1e30f;
             if (cs.cval) cs.cval[a] = 0.0;
         }
     }
@@ -105,28 +108,46 @@ __device__ void stage_candidates(const Binned& bd, const LocalCells& lc, const C
 // FP64: global coordinates, support decided by the exact test; counts supports if asked.
 template <int KIND, typename T>
 __device__ void fill_phi(const Binned& bd, const CandSmem<T>& cs, int n, int npad, int q0, int p1,
-                         T* phi, double* hsm, int* cnt) {
+                         T* phi, double* hsm, int* cnt, int* wl) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int pp = warp; pp < kSubChunk; pp += nw) {
         const int p = q0 + pp;
         const bool valid = p < p1;
         T* row = phi + pp * npad;
         if constexpr (sizeof(T) == 8) {
+            // FP64: candidates passing the FP32 prefilter are compacted into this warp's list
+            // (ballot + prefix count) and evaluated 32 at a time, so the FP64 pipe only sees
+            // near-full warps of pairs that can lie inside the support.
             const double xp = valid ? bd.px[p] : 1e300;
             const double yp = valid ? bd.py[p] : 1e300;
+            const float up = valid ? bd.pu[p] : 1e30f;
+            const float vp = valid ? bd.pv[p] : 1e30f;
             if (lane == 0 && hsm) hsm[pp] = valid ? bd.ph[p] : 0.0;
-            for (int a = lane; a < npad; a += 32) {
-                double v = 0.0;
-                if (valid && a < n) {
-                    const double dx = xp - cs.x[a], dy = yp - cs.y[a];
-                    if (inside_exact(dx, dy, bd.g.R, bd.g.R2)) {
-                        const double r = sqrt(fma(dx, dx, dy * dy)) * bd.g.invR;
-                        v = wendland<KIND, double>(r);
-                        if (cnt) atomicAdd(&cnt[a], 1);
-                    }
+            int* list = wl + warp * npad;
+            int nl = 0;
+            for (int a0 = 0; a0 < npad; a0 += 32) {
+                const int a = a0 + lane;
+                bool pass = false;
+                if (a < npad) {
+                    row[a] = 0.0;
+                    const float du = up - cs.lu[a], dv = vp - cs.lv[a];
+                    pass = du * du + dv * dv < kPrefilterR2;
                 }
-                row[a] = v;
+                const unsigned bal = __ballot_sync(0xffffffffu, pass);
+                if (pass) list[nl + __popc(bal & ((1u << lane) - 1u))] = a;
+                nl += __popc(bal);
             }
+            __syncwarp();
+            for (int k = lane; k < nl; k += 32) {
+                const int a = list[k];
+                const double dx = xp - cs.x[a], dy = yp - cs.y[a];
+                if (inside_exact(dx, dy, bd.g.R, bd.g.R2)) {
+                    const double r = sqrt_nr(fma(dx, dx, dy * dy)) * bd.g.invR;
+                    row[a] = wendland<KIND, double>(r);
+                    if (cnt) atomicAdd(&cnt[a], 1);
+                }
+            }
+            __syncwarp();
         } else {
             const float up = valid ? bd.pu[p] : 1e30f;
             const float vp = valid ? bd.pv[p] : 1e30f;
@@ -178,6 +199,18 @@ __global__ void __launch_bounds__(kThreads) k_assemble(Binned bd, const int4* __
     double* hsm = reinterpret_cast<double*>(sp);
     sp += sizeof(double) * kSubChunk;
     cs.cval = nullptr;
+    int* wl = nullptr;
+    if constexpr (kFP64) {
+        cs.lu = reinterpret_cast<float*>(sp);
+        sp += sizeof(float) * npad;
+        cs.lv = reinterpret_cast<float*>(sp);
+        sp += sizeof(float) * npad;
+        wl = reinterpret_cast<int*>(sp);
+        sp += sizeof(int) * npad * (kThreads / 32);
+    } else {
+        cs.lu = reinterpret_cast<float*>(cs.x);
+        cs.lv = reinterpret_cast<float*>(cs.y);
+    }
 
     stage_candidates<T>(bd, lc, cs, npad, nullptr);
     for (int a = threadIdx.x; a < npad; a += blockDim.x) cnt[a] = 0;
@@ -209,7 +242,7 @@ __global__ void __launch_bounds__(kThreads) k_assemble(Binned bd, const int4* __
         for (int q0 = p0; q0 < p1; q0 += kSubChunk) {
             __syncthreads();
             fill_phi<KIND, T>(bd, cs, n, npad, q0, p1, phi, kFP64 ? hsm : nullptr,
-                              (kFP64 && pass == 0) ? cnt : nullptr);
+                              (kFP64 && pass == 0) ? cnt : nullptr, wl);
             __syncthreads();
             const int np = min(kSubChunk, p1 - q0);
             if (kFP64 && pass == 0) {
@@ -318,6 +351,12 @@ __global__ void __launch_bounds__(kThreads) k_residual(Binned bd, const int4* __
     int* cnt = reinterpret_cast<int*>(sp);
     sp += sizeof(int) * npad;
     double* hsm = reinterpret_cast<double*>(sp);
+    sp += sizeof(double) * kSubChunk;
+    cs.lu = reinterpret_cast<float*>(sp);
+    sp += sizeof(float) * npad;
+    cs.lv = reinterpret_cast<float*>(sp);
+    sp += sizeof(float) * npad;
+    int* wl = reinterpret_cast<int*>(sp);
 
     stage_candidates<double>(bd, lc, cs, npad, c);
     for (int a = threadIdx.x; a < npad; a += blockDim.x) cnt[a] = 0;
@@ -325,7 +364,7 @@ __global__ void __launch_bounds__(kThreads) k_residual(Binned bd, const int4* __
     double racc0 = 0.0, racc1 = 0.0;
     for (int q0 = p0; q0 < p1; q0 += kSubChunk) {
         __syncthreads();
-        fill_phi<KIND, double>(bd, cs, n, npad, q0, p1, phi, hsm, support ? cnt : nullptr);
+        fill_phi<KIND, double>(bd, cs, n, npad, q0, p1, phi, hsm, support ? cnt : nullptr, wl);
         __syncthreads();
         const int np = min(kSubChunk, p1 - q0);
         // e_p = h_p - sum_a Phi[p][a] c_a  (one warp per point)
@@ -361,6 +400,8 @@ size_t asm_smem(int npad, bool resid) {
     size_t b = sizeof(T) * kSubChunk * npad + sizeof(long long) * npad + 2 * sizeof(T) * npad +
                3 * sizeof(int) * npad + sizeof(double) * kSubChunk;
     if (resid) b += sizeof(double) * npad;
+    if (sizeof(T) == 8)   // FP32 prefilter coordinates and the per-warp compacted lists
+        b += 2 * sizeof(float) * npad + sizeof(int) * npad * (kThreads / 32);
     return b;
 }
 

@@ -232,7 +232,35 @@ __global__ void k_work_fill(int ncell, const int* __restrict__ pstart,
     for (int q = p0; q < p1; q += kWorkPoints, ++w) work[w] = make_int4(c, q, min(q + kWorkPoints, p1), 0);
 }
 
+__global__ void k_cell_desc(int ncell, const int* __restrict__ cstart, const RowSeg* __restrict__ seg,
+                            const int64_t* __restrict__ rboff, CellDesc* __restrict__ out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    const RowSeg sg = seg[c];
+    CellDesc d;
+    d.cs = cstart[c];
+    d.m = cstart[c + 1] - d.cs;
+    d.lp = sg.lp;
+    d.pad = 0;
+    d.rboff = rboff[c];
+    d.s0 = sg.s0;
+    d.l0 = sg.l0;
+    d.s1 = sg.s1;
+    d.l1 = sg.l1;
+    d.s2 = sg.s2;
+    d.l2 = sg.l2;
+    out[c] = d;
+}
+
 }  // namespace
+
+void launch_cell_desc(rbf_ctx* ctx, cudaStream_t st) {
+    k_cell_desc<<<div_up(ctx->g.ncell, 256), 256, 0, st>>>(ctx->g.ncell, ctx->cstart.as<int>(),
+                                                           ctx->seg.as<RowSeg>(),
+                                                           ctx->rboff.as<int64_t>(),
+                                                           ctx->cdesc.as<CellDesc>());
+    ctx->launches += 1;
+}
 
 rbf_status scan_i32(rbf_ctx* ctx, const int* in, int* out, int n, cudaStream_t st) {
     return scan_impl<int, int>(ctx, in, out, n, st);
@@ -272,6 +300,7 @@ rbf_status bin_run(rbf_ctx* ctx, const double* cx, const double* cy, const doubl
     ENS(wcount, sizeof(int) * nc);
     ENS(bjsize, sizeof(int64_t) * nc);
     ENS(crow, sizeof(int4) * M);
+    ENS(cdesc, sizeof(CellDesc) * nc);
     ENS(bjoff, sizeof(int64_t) * (nc + 1));
     ENS(wstart, sizeof(int) * (nc + 1));
     ENS(stats, sizeof(int64_t) * 8);
@@ -305,6 +334,7 @@ rbf_status bin_run(rbf_ctx* ctx, const double* cx, const double* cy, const doubl
     ctx->launches += 5;
     if ((s = scan_i64(ctx, ctx->rbsize.as<int64_t>(), ctx->rboff.as<int64_t>(), nc, st)) != RBF_OK)
         return s;
+    launch_cell_desc(ctx, st);
     if ((s = scan_i32(ctx, ctx->wcount.as<int>(), ctx->wstart.as<int>(), nc, st)) != RBF_OK) return s;
     if ((s = scan_i64(ctx, ctx->bjsize.as<int64_t>(), ctx->bjoff.as<int64_t>(), nc, st)) != RBF_OK)
         return s;

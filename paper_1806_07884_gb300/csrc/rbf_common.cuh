@@ -57,6 +57,27 @@ __device__ __forceinline__ bool inside_exact(double dx, double dy, double R, dou
     return __ddiv_rn(__dsqrt_rn(d2), R) < 1.0;
 }
 
+// Square root of a >= 0 in FP64 by Newton-Raphson iteration for the reciprocal square root,
+// y <- y (3 - a y^2) / 2, seeded with the FP32 hardware estimate rsqrtf (about 23 correct
+// bits; each step doubles them), followed by one Newton step on sqrt itself,
+// s <- s + y (a - s^2) / 2. About ten FP64 operations instead of a full IEEE square root;
+// the result is within a few units in the last place of sqrt(a) (checked against sqrt by
+// the library's self-test entry point).
+__device__ __forceinline__ double sqrt_nr(double a) {
+    if (!(a > 0.0)) return 0.0;
+    if (a < 1e-30 || a > 1e30) return sqrt(a);   // outside the FP32 seed's normal range
+    double y = double(rsqrtf(float(a)));
+    y = y * fma(-0.5 * a, y * y, 1.5);
+    y = y * fma(-0.5 * a, y * y, 1.5);
+    const double s = a * y;
+    return fma(0.5 * y, fma(-s, s, a), s);
+}
+
+// Lower bound on the squared distance, in units of R^2, above which an FP32 test from
+// cell-local coordinates (absolute error about 1e-7 R per coordinate) certainly means
+// outside the support; pairs below it get the exact FP64 test.
+constexpr float kPrefilterR2 = 1.00002f;
+
 // ---------------------------------------------------------------------------
 // Uniform grid of square cells of side h = R * kCellMargin over a bounding box.
 // Cell key = iy * gx + ix (row-major, x fastest); items outside are clamped.
@@ -96,6 +117,14 @@ struct RowSeg {
     int lp;                       // padded row length (row stride of the block)
 };
 
+// Everything a warp needs to stream the stored row block of one cell, in one 48-byte record
+// (three 16-byte loads) so the SpMV prologue is a single memory round trip.
+struct __align__(16) CellDesc {
+    int cs, m, lp, pad;          // first sorted centre, centre count, padded row length
+    long long rboff;             // offset of the row block in the value array
+    int s0, l0, s1, l1, s2, l2;  // column segments (see RowSeg)
+};
+
 // Views of the context's device buffers passed by value to kernels.
 struct Binned {
     Grid g;
@@ -116,6 +145,7 @@ struct Binned {
     const int64_t* rboff;   // [ncell+1] offset of each cell's row block in the value array
     const int64_t* bjoff;   // [ncell+1] offset of each cell's inverse diagonal block
     const int4* crow;       // [M] {first sorted centre, centre count, cell, 0} of each centre's cell
+    const CellDesc* cdesc;  // [ncell]
 };
 
 // ---------------------------------------------------------------------------

@@ -14,19 +14,36 @@ __device__ __forceinline__ double eval_at(const Binned& bd, const double* __rest
                                           double x, double y) {
     const Grid& g = bd.g;
     const int ix = cell_ix(g, x), iy = cell_iy(g, y);
-    const int xa = max(ix - 1, 0), xb = min(ix + 1, g.gx - 1);
+    // the query in its cell's frame (units of R) for the FP32 prefilter
+    const float uq = float((x - (g.x0 + ix * g.h)) * g.invR);
+    const float vq = float((y - (g.y0 + iy * g.h)) * g.invR);
     double f = 0.0;
     for (int row = max(iy - 1, 0); row <= min(iy + 1, g.gy - 1); ++row) {
-        const int s0 = bd.cstart[row * g.gx + xa], s1 = bd.cstart[row * g.gx + xb + 1];
-        for (int s = s0; s < s1; ++s) {
-            const double dx = x - bd.cx[s], dy = y - bd.cy[s];
-            if (inside_exact(dx, dy, g.R, g.R2)) {
-                const double r = sqrt(fma(dx, dx, dy * dy)) * g.invR;
-                f = fma(c[s], wendland<KIND, double>(r), f);
+        const float oy = float(row - iy);
+        for (int cx = max(ix - 1, 0); cx <= min(ix + 1, g.gx - 1); ++cx) {
+            const float ox = float(cx - ix);
+            const int cell = row * g.gx + cx;
+            const int s0 = bd.cstart[cell], s1 = bd.cstart[cell + 1];
+            for (int s = s0; s < s1; ++s) {
+                const float du = uq - (bd.cu[s] + ox), dv = vq - (bd.cv[s] + oy);
+                if (du * du + dv * dv >= kPrefilterR2) continue;
+                const double dx = x - bd.cx[s], dy = y - bd.cy[s];
+                if (inside_exact(dx, dy, g.R, g.R2)) {
+                    const double r = sqrt_nr(fma(dx, dx, dy * dy)) * g.invR;
+                    f = fma(c[s], wendland<KIND, double>(r), f);
+                }
             }
         }
     }
     return f;
+}
+
+__global__ void k_diag_sqrt(const double* __restrict__ a, double* __restrict__ out, int64_t n) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n;
+         i += int64_t(gridDim.x) * blockDim.x) {
+        out[2 * i] = sqrt_nr(a[i]);
+        out[2 * i + 1] = sqrt(a[i]);
+    }
 }
 
 template <int KIND>
@@ -86,6 +103,12 @@ __global__ void k_export(Binned bd, const T* __restrict__ B, const double* __res
 int eval_grid_size(int64_t Q) { return int(std::min<int64_t>((Q + 255) / 256, 152 * 32)); }
 
 }  // namespace
+
+rbf_status diag_sqrt_run(const double* a, double* out, int64_t n, cudaStream_t st) {
+    if (n <= 0) return RBF_OK;
+    k_diag_sqrt<<<eval_grid_size(n), 256, 0, st>>>(a, out, n);
+    return cudaGetLastError() == cudaSuccess ? RBF_OK : RBF_ERR_CUDA;
+}
 
 rbf_status eval_points_run(rbf_ctx* ctx, const double* c, const double* qx, const double* qy,
                            int64_t Q, double* f, cudaStream_t st) {

@@ -43,6 +43,7 @@ struct rbf_ctx {
     rbf_buf wcount, wstart;    // [ncell], [ncell+1]
     rbf_buf bjsize, bjoff;     // [ncell], [ncell+1] int64: inverse diagonal blocks (m <= 32)
     rbf_buf crow;              // [M] int4 {cell start, cell count, cell, 0} per sorted centre
+    rbf_buf cdesc;             // [ncell] CellDesc
     int64_t nbj = 0;           // values of all inverse diagonal blocks
     rbf_buf work;              // [nwork] int4 {cell, p0, p1, 0}
     rbf_buf scan_tmp;          // block sums of the device scans
@@ -68,6 +69,10 @@ struct rbf_ctx {
     rbf_buf csort;             // [M] FP64 coefficients in sorted order (evaluation)
     void* hpinned = nullptr;   // pinned host scratch for scalar read-back (4 KiB)
     int64_t launches = 0;      // kernels launched by this context (graph nodes included)
+    int spmv_blocks_per_sm[2] = {0, 0};   // occupancy of the SpMV kernels, [0] FP64, [1] FP32
+    // solver parameters (rbf_set_param)
+    double inner_tol = 1e-3;   // relative tolerance of each FP32 inner solve
+    int max_refine = 30;       // FP64 refinement steps of RBF_FP32_REFINE
     cudaStream_t capture_stream = nullptr;   // private stream used only to capture graphs
     // CG solve graphs (conditional WHILE loop), [0] FP64, [1] FP32, and what they were built for
     struct SolveGraph {
@@ -111,11 +116,14 @@ rbf_status eval_points_run(rbf_ctx* ctx, const double* c, const double* qx, cons
                            int64_t Q, double* f, cudaStream_t st);
 rbf_status eval_grid_run(rbf_ctx* ctx, const double* c, int nx, int ny, const double* box,
                          double* f, cudaStream_t st);
+rbf_status diag_sqrt_run(const double* a, double* out, int64_t n, cudaStream_t st);
 rbf_status export_upper_run(rbf_ctx* ctx, int64_t cap, int32_t* row, int32_t* col, double* val,
                             double* bvec, int32_t* support, int64_t* nnz, cudaStream_t st);
 
 rbf_status bench_spmv_run(rbf_ctx* ctx, int reps, cudaStream_t st);
 rbf_status bench_cg_run(rbf_ctx* ctx, int reps, cudaStream_t st);
+// per-cell SpMV descriptors (after the row-block offsets are known)
+void launch_cell_desc(rbf_ctx* ctx, cudaStream_t st);
 
 // permutation helpers (rbf_solve.cu)
 void launch_gather_sorted(const double* c_orig, const int* cperm, double* c_sorted, int M,

@@ -4,7 +4,8 @@
 // cell share most of their support and are the strongest couplings of B).
 //
 // SpMV y = B x over the cell-blocked upper storage (Section 5 keeps only the upper
-// triangle), one warp per cell: the cell's dense m_c x lp_c row block is streamed once with
+// triangle), one warp per cell (persistent warps striding over the cells): the cell's dense
+// m_c x lp_c row block, described by one 48-byte record, is streamed once with
 // 16-byte vector loads, and each value feeds both the row product (16 rows held in
 // registers, summed across lanes by a butterfly transpose-reduction) and the transposed
 // product of the lower triangle (column sums added to y with atomics). HBM and L2 see each
@@ -34,12 +35,20 @@ namespace rbf {
 
 constexpr int kAccSlots = 64;
 
+// Scalars carried between iterations, double-buffered by iteration parity: iteration k
+// reads slot k & 1 and block 0 of its update kernel writes slot (k + 1) & 1.
+struct CgSlot {
+    double gamma_prev, alpha_prev;
+    int it, state;
+};
 struct CgScalars {
-    double gamma, gamma_prev, alpha, rr, bb;
-    double tol2, bscale;         // parameters, written by the host before each solve
-    int it, maxit, state, pad;
-    unsigned int ticket, pad2;   // last-block-done counter of the reductions
-    double acc_delta[kAccSlots]; // u^T B u of the current SpMV, spread over slots
+    double bb, tol2, bscale;     // (b, b); parameters written by the host before each solve
+    int maxit, pad;
+    unsigned int ticket, pad2;   // last-block-done counter of the start kernel
+    CgSlot sl[2];
+    double out_rr, out_gamma;    // result, written when the solve stops
+    int out_it, out_state;
+    double acc_delta[2][kAccSlots];   // u^T B u of the SpMV of each parity, spread over slots
 };
 
 enum { kRunning = 0, kConverged = 1, kBreakdown = 2, kMaxIt = 3 };
@@ -182,15 +191,19 @@ __device__ __forceinline__ T butterfly16(T (&v)[16], int lane) {
 // and are added with atomics. Returns this lane's share of x^T B x over the cell's entries:
 // sum_s x[s] rowsum[s] + sum_t colsum[t] x[t].
 template <typename T>
-__device__ double spmv_cell(const Binned& bd, const T* __restrict__ B, const T* x, T* y, int c,
-                            int lane) {
-    const int cs = bd.cstart[c];
-    const int m = bd.cstart[c + 1] - cs;
+__device__ double spmv_cell(const CellDesc& cd, const T* __restrict__ B, const T* x, T* y, int lane) {
+    const int cs = cd.cs, m = cd.m;
     if (m == 0) return 0.0;
-    const RowSeg sg = bd.seg[c];
-    const int L = sg.l0 + sg.l1 + sg.l2, lp = sg.lp;
-    const T* Bc = B + bd.rboff[c];
-    double dot = 0.0;
+    RowSeg sg;
+    sg.s0 = cd.s0;
+    sg.l0 = cd.l0;
+    sg.s1 = cd.s1;
+    sg.l1 = cd.l1;
+    sg.s2 = cd.s2;
+    sg.l2 = cd.l2;
+    const int L = sg.l0 + sg.l1 + sg.l2, lp = cd.lp;
+    const T* Bc = B + cd.rboff;
+    T dot = T(0);
     for (int j0 = 0; j0 < m; j0 += 16) {
         const int mm = min(16, m - j0);
         const T xs_lane = lane < mm ? ldcg(x + cs + j0 + lane) : T(0);
@@ -200,32 +213,35 @@ __device__ double spmv_cell(const Binned& bd, const T* __restrict__ B, const T* 
         for (int k0 = 0; k0 < L; k0 += 128) {
             const int kb = k0 + 4 * lane;
             const bool active = kb < L;
+            int t[4];
             T xt[4], ca[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                xt[q] = kb + q < L ? ldcg(x + colmap(sg, kb + q)) : T(0);
+                t[q] = kb + q < L ? colmap(sg, kb + q) : -1;
+                xt[q] = t[q] >= 0 ? ldcg(x + t[q]) : T(0);
                 ca[q] = T(0);
             }
             const T* rb = Bc + (long long)j0 * lp + kb;
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
-                const T xi = __shfl_sync(kFull, xs_lane, i);
-                if (i < mm && active) {
-                    T v[4];
-                    load4(rb + (long long)i * lp, v);
+                if (i < mm) {                 // warp-uniform
+                    const T xi = __shfl_sync(kFull, xs_lane, i);
+                    if (active) {
+                        T v[4];
+                        load4(rb + (long long)i * lp, v);
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        rp[i] = fma(v[q], xt[q], rp[i]);
-                        ca[q] = fma(v[q], xi, ca[q]);
+                        for (int q = 0; q < 4; ++q) {
+                            rp[i] = fma(v[q], xt[q], rp[i]);
+                            ca[q] = fma(v[q], xi, ca[q]);
+                        }
                     }
                 }
             }
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const int k = kb + q;
-                if (k >= m && k < L && ca[q] != T(0)) {
-                    atomicAdd(y + colmap(sg, k), ca[q]);
-                    dot += double(ca[q]) * double(xt[q]);
+                if (kb + q >= m && t[q] >= 0 && ca[q] != T(0)) {
+                    atomicAdd(y + t[q], ca[q]);
+                    dot = fma(ca[q], xt[q], dot);
                 }
             }
         }
@@ -234,19 +250,30 @@ __device__ double spmv_cell(const Binned& bd, const T* __restrict__ B, const T* 
         const T xr = __shfl_sync(kFull, xs_lane, r);
         if ((lane & 1) == 0 && r < mm) {
             atomicAdd(y + cs + j0 + r, tot);
-            dot += double(tot) * double(xr);
+            dot = fma(tot, xr, dot);
         }
     }
-    return dot;
+    return double(dot);
 }
 
-// Standalone SpMV y += B x (warp per cell; y zeroed by the caller).
+__device__ __forceinline__ CellDesc load_desc(const CellDesc* d) {
+    CellDesc v;
+    const int4* p = reinterpret_cast<const int4*>(d);
+    int4* q = reinterpret_cast<int4*>(&v);
+    q[0] = __ldg(p);
+    q[1] = __ldg(p + 1);
+    q[2] = __ldg(p + 2);
+    return v;
+}
+
+// Standalone SpMV y += B x (persistent warps striding over the cells; y zeroed by the caller).
 template <typename T>
-__global__ void __launch_bounds__(kSpmvWarps * 32)
+__global__ void __launch_bounds__(kSpmvWarps * 32, sizeof(T) == 4 ? 3 : 1)
     k_spmv(Binned bd, const T* __restrict__ B, const T* __restrict__ x, T* __restrict__ y) {
     const int lane = threadIdx.x & 31;
-    const int c = blockIdx.x * kSpmvWarps + (threadIdx.x >> 5);
-    if (c < bd.g.ncell) spmv_cell<T>(bd, B, x, y, c, lane);
+    const int nw = gridDim.x * kSpmvWarps;
+    for (int c = blockIdx.x * kSpmvWarps + (threadIdx.x >> 5); c < bd.g.ncell; c += nw)
+        spmv_cell<T>(load_desc(bd.cdesc + c), B, x, y, lane);
 }
 
 template <typename T>
@@ -266,15 +293,17 @@ struct CgVec {
 
 // w += B u (w zero on entry); delta = u^T B u into the slots of sc->acc_delta.
 template <typename T>
-__global__ void __launch_bounds__(kSpmvWarps * 32)
+__global__ void __launch_bounds__(kSpmvWarps * 32, sizeof(T) == 4 ? 3 : 1)
     k_cg_spmv(Binned bd, const T* __restrict__ B, const T* __restrict__ u, T* __restrict__ w,
-              CgScalars* __restrict__ sc) {
-    if (sc->state != kRunning) return;
+              int P, CgScalars* __restrict__ sc) {
+    if (sc->sl[P].state != kRunning) return;
     const int lane = threadIdx.x & 31;
     const int gw = blockIdx.x * kSpmvWarps + (threadIdx.x >> 5);
-    if (gw >= bd.g.ncell) return;
-    const double d = warp_sum_d(spmv_cell<T>(bd, B, u, w, gw, lane));
-    if (lane == 0 && d != 0.0) atomicAdd(&sc->acc_delta[gw & (kAccSlots - 1)], d);
+    const int nw = gridDim.x * kSpmvWarps;
+    double d = 0.0;
+    for (int c = gw; c < bd.g.ncell; c += nw) d += spmv_cell<T>(load_desc(bd.cdesc + c), B, u, w, lane);
+    d = warp_sum_d(d);
+    if (lane == 0 && d != 0.0) atomicAdd(&sc->acc_delta[P][gw & (kAccSlots - 1)], d);
 }
 
 // The residual of a row after this iteration's update, r - alpha (w + beta s), evaluated
@@ -298,34 +327,77 @@ __device__ __forceinline__ T apply_prec(const Binned& bd, const T* __restrict__ 
     return ui;
 }
 
-// One thread per row i: alpha, beta from the scalars; s, p, x, r updated; u = D^-1 r using
-// the cell's updated residual (recomputed here from the previous buffers); w of the other
-// parity zeroed for the next SpMV. The last block reduces gamma, (r, r) and advances the
-// state. P is the parity of the buffers read in this iteration.
+// One thread per row i. Prologue (warp 0 of every block, identical results in all blocks):
+// gamma_k and (r_k, r_k) from the previous kernel's per-block partials, delta_k from the
+// SpMV's slots, the stopping test, then beta_k and alpha_k; block 0 writes the next slot.
+// Body: s, p, x, r updated; u = D^-1 r using the cell's updated residual (recomputed here
+// from the previous buffers); w of the other parity zeroed for the next SpMV; per-block
+// partials of gamma_{k+1} and (r_{k+1}, r_{k+1}). P is the parity k & 1.
 template <typename T>
 __global__ void __launch_bounds__(kVecThreads)
     k_cg_update(Binned bd, CgVec<T> v, int P, CgScalars* __restrict__ sc,
-                double* __restrict__ partial) {
+                double* __restrict__ pbuf) {
     __shared__ double s_ab[2];
     __shared__ int s_go;
-    if (threadIdx.x == 0) {
-        int go = sc->state == kRunning;
-        if (go) {
-            double delta = 0.0;
-            for (int k = 0; k < kAccSlots; ++k) delta += __ldcg(&sc->acc_delta[k]);
-            const double gamma = sc->gamma;
-            const int it = sc->it;
-            const double beta = it == 0 ? 0.0 : gamma / sc->gamma_prev;
-            const double den = it == 0 ? delta : delta - beta * gamma / sc->alpha;
-            const double alpha = gamma / den;
-            if (!(den > 0.0) || !isfinite(alpha)) {
-                sc->state = kBreakdown;
-                go = 0;
+    static_assert(kAccSlots == 64, "two slots per lane");
+    const int nblk = gridDim.x;
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        const CgSlot sl = sc->sl[P];
+        int state = sl.state;
+        double g = 0.0, rr = 0.0, d = 0.0;
+        if (state == kRunning) {
+            const double* pb = pbuf + size_t(P) * 2 * nblk;
+            for (int b = lane; b < nblk; b += 32) {
+                g += __ldcg(pb + 2 * b);
+                rr += __ldcg(pb + 2 * b + 1);
+            }
+            d = __ldcg(&sc->acc_delta[P][lane]) + __ldcg(&sc->acc_delta[P][lane + 32]);
+        }
+        g = warp_sum_d(g);
+        rr = warp_sum_d(rr);
+        d = warp_sum_d(d);
+        if (lane == 0) {
+            double alpha = 0.0, beta = 0.0;
+            const int was = state;
+            if (state == kRunning) {
+                if (!isfinite(g) || !isfinite(rr)) {
+                    state = kBreakdown;
+                } else if (rr <= sc->tol2 * sc->bb) {
+                    state = kConverged;
+                } else if (sl.it >= sc->maxit) {
+                    state = kMaxIt;
+                } else {
+                    beta = sl.it == 0 ? 0.0 : g / sl.gamma_prev;
+                    const double den = sl.it == 0 ? d : d - beta * g / sl.alpha_prev;
+                    alpha = g / den;
+                    if (!(den > 0.0) || !isfinite(alpha)) state = kBreakdown;
+                }
             }
             s_ab[0] = alpha;
             s_ab[1] = beta;
+            s_go = state == kRunning;
+            if (blockIdx.x == 0) {
+                CgSlot nx = sl;
+                nx.state = state;
+                if (state == kRunning) {
+                    nx.gamma_prev = g;
+                    nx.alpha_prev = alpha;
+                    nx.it = sl.it + 1;
+                }
+                sc->sl[P ^ 1] = nx;
+                if (was == kRunning && state != kRunning) {
+                    sc->out_rr = rr;
+                    sc->out_gamma = g;
+                    sc->out_it = sl.it;
+                    sc->out_state = state;
+                }
+            }
         }
-        s_go = go;
+        if (blockIdx.x == 0) {
+            sc->acc_delta[P ^ 1][lane] = 0.0;
+            sc->acc_delta[P ^ 1][lane + 32] = 0.0;
+        }
     }
     __syncthreads();
     if (!s_go) return;
@@ -337,7 +409,7 @@ __global__ void __launch_bounds__(kVecThreads)
     T* __restrict__ rQ = P ? v.r[0] : v.r[1];
     T* __restrict__ sQ = P ? v.s[0] : v.s[1];
     T* __restrict__ wQ = P ? v.w[0] : v.w[1];
-    double acc[2] = {0.0, 0.0}, tot[2];
+    double acc[2] = {0.0, 0.0};
     const int M = bd.M;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) {
         const T di = v.dinv[i];
@@ -355,35 +427,31 @@ __global__ void __launch_bounds__(kVecThreads)
         rQ[i] = ri;
         v.u[i] = ui;
         wQ[i] = T(0);
-        acc[0] += double(ri) * double(ui);
-        acc[1] += double(ri) * double(ri);
+        acc[0] += double(ri * ui);
+        acc[1] += double(ri * ri);
     }
-    if (last_block_total<2>(acc, partial, &sc->ticket, tot) && threadIdx.x == 0) {
-        sc->gamma_prev = sc->gamma;
-        sc->gamma = tot[0];
-        sc->alpha = alpha;
-        sc->rr = tot[1];
-        sc->it += 1;
-        for (int k = 0; k < kAccSlots; ++k) sc->acc_delta[k] = 0.0;
-        if (!isfinite(tot[0]) || !isfinite(tot[1])) sc->state = kBreakdown;
-        else if (tot[1] <= sc->tol2 * sc->bb) sc->state = kConverged;
-        else if (sc->it >= sc->maxit) sc->state = kMaxIt;
+    block_sum<2>(acc);
+    if (threadIdx.x == 0) {
+        double* pb = pbuf + size_t(P ^ 1) * 2 * nblk;
+        pb[2 * blockIdx.x] = acc[0];
+        pb[2 * blockIdx.x + 1] = acc[1];
     }
 }
 
 // Start: r = bscale b - B x0 (B x0 in w[1] when use_x0), u = D^-1 r, p = s[0] = w[0] = 0
-// (x = 0 without a start vector); gamma, (r, r), (b, b) and the initial test.
+// (x = 0 without a start vector); per-block partials of gamma_0 and (r_0, r_0) for the first
+// update, and (b, b) reduced by the last block, which also sets the parity-0 slot.
 template <typename T, typename TB>
 __global__ void __launch_bounds__(kVecThreads)
     k_cg_init(Binned bd, CgVec<T> v, const TB* __restrict__ b, int use_x0,
-              CgScalars* __restrict__ sc, double* __restrict__ partial) {
+              CgScalars* __restrict__ sc, double* __restrict__ pbuf, double* __restrict__ partial) {
     const double bscale = sc->bscale;
     const T* __restrict__ w1 = v.w[1];
     auto r0 = [&](int j) -> T {
         const T bj = T(double(b[j]) * bscale);
         return use_x0 ? bj - w1[j] : bj;
     };
-    double acc[3] = {0.0, 0.0, 0.0}, tot[3];
+    double acc[2] = {0.0, 0.0}, bb[1] = {0.0}, tot[1];
     const int M = bd.M;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) {
         const T di = v.dinv[i];
@@ -398,25 +466,30 @@ __global__ void __launch_bounds__(kVecThreads)
         v.w[0][i] = T(0);
         acc[0] += double(ri) * double(ui);
         acc[1] += double(ri) * double(ri);
-        acc[2] += double(bi) * double(bi);
+        bb[0] += double(bi) * double(bi);
     }
-    if (last_block_total<3>(acc, partial, &sc->ticket, tot) && threadIdx.x == 0) {
-        sc->gamma = tot[0];
-        sc->gamma_prev = 1.0;
-        sc->alpha = 0.0;
-        sc->rr = tot[1];
-        sc->bb = tot[2];
-        sc->it = 0;
-        for (int k = 0; k < kAccSlots; ++k) sc->acc_delta[k] = 0.0;
-        if (tot[1] <= sc->tol2 * tot[2] || tot[2] == 0.0) sc->state = kConverged;
-        else if (sc->maxit <= 0) sc->state = kMaxIt;
-        else sc->state = kRunning;
+    block_sum<2>(acc);
+    if (threadIdx.x == 0) {
+        pbuf[2 * blockIdx.x] = acc[0];
+        pbuf[2 * blockIdx.x + 1] = acc[1];
+    }
+    if (last_block_total<1>(bb, partial, &sc->ticket, tot) && threadIdx.x == 0) {
+        sc->bb = tot[0];
+        CgSlot s0;
+        s0.gamma_prev = 1.0;
+        s0.alpha_prev = 1.0;
+        s0.it = 0;
+        s0.state = kRunning;
+        sc->sl[0] = s0;
+        sc->sl[1] = s0;
+        sc->out_state = kRunning;
     }
 }
 
-// Loop condition of the solve graph: keep iterating while the state is running.
+// Loop condition of the solve graph (after an even number of iterations the next slot is
+// slot 0): keep iterating while the state is running.
 __global__ void k_cg_cond(const CgScalars* __restrict__ sc, cudaGraphConditionalHandle h) {
-    cudaGraphSetConditional(h, sc->state == kRunning ? 1u : 0u);
+    cudaGraphSetConditional(h, sc->sl[0].state == kRunning ? 1u : 0u);
 }
 
 // Preconditioner set-up, one warp per cell: dinv[s] = 1 / B_ss for centres with at least
@@ -550,7 +623,20 @@ CgVec<T> cg_vectors(rbf_ctx* ctx) {
     return v;
 }
 
-int spmv_grid(const rbf_ctx* ctx) { return div_up(ctx->g.ncell, kSpmvWarps); }
+// Persistent SpMV grid: as many blocks as can be resident (never more than the cells need).
+template <typename T>
+int spmv_grid_T(rbf_ctx* ctx) {
+    int& per_sm = ctx->spmv_blocks_per_sm[sizeof(T) == 8 ? 0 : 1];
+    if (per_sm == 0) {
+        int a = 0, b = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_cg_spmv<T>, kSpmvWarps * 32, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_spmv<T>, kSpmvWarps * 32, 0);
+        per_sm = std::max(1, std::min(a, b));
+    }
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    return std::max(1, std::min(per_sm * std::max(sms, 1), div_up(ctx->g.ncell, kSpmvWarps)));
+}
 int vec_grid(const rbf_ctx* ctx) {
     return std::max(1, std::min(div_up(ctx->M, kVecThreads), 152 * 8));
 }
@@ -560,7 +646,8 @@ template <typename T>
 void launch_iteration(rbf_ctx* ctx, const CgVec<T>& v, int P, cudaStream_t cs) {
     const Binned bd = view(ctx);
     CgScalars* sc = ctx->scal.as<CgScalars>();
-    k_cg_spmv<T><<<spmv_grid(ctx), kSpmvWarps * 32, 0, cs>>>(bd, ctx->bvals.as<T>(), v.u, v.w[P], sc);
+    k_cg_spmv<T><<<spmv_grid_T<T>(ctx), kSpmvWarps * 32, 0, cs>>>(bd, ctx->bvals.as<T>(), v.u,
+                                                                  v.w[P], P, sc);
     k_cg_update<T><<<vec_grid(ctx), kVecThreads, 0, cs>>>(bd, v, P, sc, ctx->partial.as<double>());
 }
 
@@ -635,15 +722,15 @@ rbf_status cg_start(rbf_ctx* ctx, const TB* b, double bscale, bool use_x0, doubl
     h.tol2 = tol * tol;
     h.bscale = bscale;
     h.maxit = maxit;
-    h.state = kRunning;
     RBF_CUDA_TRY(cudaMemcpyAsync(sc, &h, sizeof(CgScalars), cudaMemcpyHostToDevice, st));
     if (use_x0) {
         RBF_CUDA_TRY(cudaMemsetAsync(v.w[1], 0, sizeof(T) * ctx->M, st));
-        k_spmv<T><<<spmv_grid(ctx), kSpmvWarps * 32, 0, st>>>(bd, ctx->bvals.as<T>(), v.x, v.w[1]);
+        k_spmv<T><<<spmv_grid_T<T>(ctx), kSpmvWarps * 32, 0, st>>>(bd, ctx->bvals.as<T>(), v.x, v.w[1]);
         ctx->launches += 1;
     }
-    k_cg_init<T, TB><<<vec_grid(ctx), kVecThreads, 0, st>>>(bd, v, b, use_x0 ? 1 : 0, sc,
-                                                            ctx->partial.as<double>());
+    double* part = ctx->partial.as<double>();
+    k_cg_init<T, TB><<<vec_grid(ctx), kVecThreads, 0, st>>>(bd, v, b, use_x0 ? 1 : 0, sc, part,
+                                                            part + 4 * vec_grid(ctx));
     ctx->launches += 1;
     RBF_CUDA_TRY(cudaGetLastError());
     return RBF_OK;
@@ -662,12 +749,13 @@ rbf_status run_cg(rbf_ctx* ctx, const TB* b, double bscale, bool use_x0, double 
     CgScalars* hs = static_cast<CgScalars*>(ctx->hpinned);
     RBF_CUDA_TRY(cudaMemcpyAsync(hs, ctx->scal.p, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
     RBF_CUDA_TRY(cudaStreamSynchronize(st));
-    // kernels launched by the graph: per loop pass 2 * kItersPerBody + 1
-    const int passes = std::max(1, (hs->it + kItersPerBody - 1) / kItersPerBody);
+    // kernels launched by the graph: per loop pass 2 * kItersPerBody + 1; the stop is detected
+    // one kernel after the last iteration, so the passes cover out_it + 1 iterations
+    const int passes = hs->out_it / kItersPerBody + 1;
     ctx->launches += int64_t(passes) * (2 * kItersPerBody + 1);
-    *iters = hs->it;
-    *relres = hs->bb > 0 ? sqrt(hs->rr / hs->bb) : 0.0;
-    *state = hs->state;
+    *iters = hs->out_it;
+    *relres = hs->bb > 0 ? sqrt(hs->out_rr / hs->bb) : 0.0;
+    *state = hs->out_state;
     return RBF_OK;
 }
 
@@ -700,22 +788,30 @@ rbf_status bench_cg_run(rbf_ctx* ctx, int reps, cudaStream_t st) {
                                  : bench_cg_impl<float>(ctx, reps, st);
 }
 
-rbf_status bench_spmv_run(rbf_ctx* ctx, int reps, cudaStream_t st) {
+template <typename T>
+__global__ void k_fill(T* __restrict__ v, int n, T value) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) v[i] = value;
+}
+
+template <typename T>
+rbf_status bench_spmv_impl(rbf_ctx* ctx, int reps, cudaStream_t st) {
+    rbf_status s = ensure(ctx, ctx->cgv[sizeof(T) == 8 ? 0 : 1], sizeof(T) * kCgVecs * size_t(ctx->M), st);
+    if (s != RBF_OK) return s;
     const Binned bd = view(ctx);
-    for (int k = 0; k < reps; ++k) {
-        if (ctx->prec == RBF_FP64) {
-            const CgVec<double> v = cg_vectors<double>(ctx);
-            k_spmv<double><<<spmv_grid(ctx), kSpmvWarps * 32, 0, st>>>(bd, ctx->bvals.as<double>(),
-                                                                       v.u, v.w[0]);
-        } else {
-            const CgVec<float> v = cg_vectors<float>(ctx);
-            k_spmv<float><<<spmv_grid(ctx), kSpmvWarps * 32, 0, st>>>(bd, ctx->bvals.as<float>(),
-                                                                     v.u, v.w[0]);
-        }
-    }
+    const CgVec<T> v = cg_vectors<T>(ctx);
+    k_fill<T><<<div_up(ctx->M, 256), 256, 0, st>>>(v.u, ctx->M, T(1));
+    RBF_CUDA_TRY(cudaMemsetAsync(v.w[0], 0, sizeof(T) * ctx->M, st));
+    for (int k = 0; k < reps; ++k)
+        k_spmv<T><<<spmv_grid_T<T>(ctx), kSpmvWarps * 32, 0, st>>>(bd, ctx->bvals.as<T>(), v.u, v.w[0]);
     RBF_CUDA_TRY(cudaGetLastError());
-    ctx->launches += reps;
+    ctx->launches += reps + 1;
     return RBF_OK;
+}
+
+rbf_status bench_spmv_run(rbf_ctx* ctx, int reps, cudaStream_t st) {
+    return ctx->prec == RBF_FP64 ? bench_spmv_impl<double>(ctx, reps, st)
+                                 : bench_spmv_impl<float>(ctx, reps, st);
 }
 
 static rbf_status finish_status(rbf_ctx* ctx, int state) {
@@ -735,7 +831,7 @@ rbf_status solve_run(rbf_ctx* ctx, double* c, int use_c0, double tol, int maxit,
     ENS(x, sizeof(double) * M);
     ENS(r, sizeof(double) * M);
     ENS(scal, sizeof(CgScalars) + 64);
-    ENS(partial, sizeof(double) * 3 * std::max(vec_grid(ctx), spmv_grid(ctx)));
+    ENS(partial, sizeof(double) * 5 * std::max(vec_grid(ctx), 1));
     int64_t* npin_h = static_cast<int64_t*>(ctx->hpinned) + 256;
     int* npin_d = reinterpret_cast<int*>(ctx->scal.as<char>() + sizeof(CgScalars));
     RBF_CUDA_TRY(cudaMemsetAsync(npin_d, 0, sizeof(int), st));
@@ -809,16 +905,16 @@ rbf_status solve_run(rbf_ctx* ctx, double* c, int use_c0, double tol, int maxit,
         int total_it = 0, outer = 0;
         double rel = 0.0;
         state = kMaxIt;
-        // Inner tolerance: each refinement step should gain about 4 digits; FP32 rounding of
-        // B (relative 6e-8 per entry) limits the gain per step, not the final accuracy.
-        const double inner_tol = 1e-4;
+        // Inner tolerance: each refinement step gains about -log10(inner_tol) digits; FP32
+        // rounding of B limits the gain per step, not the final accuracy.
+        const double inner_tol = ctx->inner_tol;
         for (outer = 0;; ++outer) {
             rel = bnorm > 0 ? rn / bnorm : 0.0;
             if (rel <= tol || rn == 0.0) {
                 state = kConverged;
                 break;
             }
-            if (outer == 30) break;
+            if (outer == ctx->max_refine) break;
             int it = 0, ist = 0;
             double irel = 0.0;
             s = run_cg<float, double>(ctx, r64, 1.0 / rn, false, std::max(inner_tol, 0.5 * tol / rel),

@@ -274,3 +274,22 @@ def test_terrain_full_size_properties():
     f32 = ctx32.eval_grid(c32, 1024, 1024).cpu().numpy()
     assert O.rel_err(f32, f) <= MIXED_BAR
     ctx32.close()
+
+
+def test_device_sqrt_against_cuda_sqrt():
+    """The Newton-Raphson square root used for distances stays within 4 ulp of CUDA's sqrt
+    over the range of squared distances (and exact at 0)."""
+    from paper_1806_07884_gb300 import _lib
+    lib = _lib.load()
+    rng = np.random.default_rng(0)
+    a = np.concatenate([[0.0, 1.0, 4.0, 1e-300, 1e-30], 10.0 ** rng.uniform(-30, 10, 200000),
+                        rng.random(100000)])
+    ad = _dev(a)
+    out = torch.empty(2 * a.size, dtype=torch.float64, device="cuda")
+    assert lib.rbf_selftest_sqrt(ad.data_ptr(), out.data_ptr(), a.size, None) == 0
+    torch.cuda.synchronize()
+    o = out.cpu().numpy().reshape(-1, 2)
+    ok = o[:, 1] > 0
+    ulp = np.abs(o[ok, 0] - o[ok, 1]) / np.spacing(o[ok, 1])
+    assert ulp.max() <= 4.0, ulp.max()
+    assert o[0, 0] == 0.0
