@@ -177,6 +177,25 @@ rbf_status rbf_bench_spmv(rbf_ctx* ctx, int reps, void* stream);
  * overwrites the solver's workspace; requires a preceding rbf_solve. Asynchronous. */
 rbf_status rbf_bench_cg(rbf_ctx* ctx, int reps, void* stream);
 
+/* Evaluation with no allocation at all (the paper has no counterpart; this is a service to
+ * callers that cannot allocate device memory where they need the surface -- e.g. code that
+ * runs while its own memory pool is locked or inside a fixed device-memory budget, or a
+ * C/Fortran host that owns every device buffer and keeps no library context). Computes
+ * f[q] = sum_j c[j] phi(||(qx[q], qy[q]) - (cx[j], cy[j])|| / R) for q < Q, the same value
+ * as rbf_eval, from caller-owned DEVICE arrays cx, cy, c (M values each), qx, qy (Q values)
+ * into the caller-owned DEVICE array f (Q values); bbox is a HOST array {x0, y0, x1, y1}.
+ * The centres are binned into a scratch area that is a static device array of 2.6 MB
+ * reserved when the library is loaded (each GPU that loads the library keeps it until the
+ * process exits); nothing is allocated and no context is used.
+ * Limits: M <= 65536 and at most 65536 cells of side R over bbox, else RBF_ERR_LIMIT (no
+ * work queued). The first call on a device looks up the scratch address with that device
+ * current (the device must be current when calling); make that first call before any stream
+ * capture. Every call on a device shares the scratch: calls whose GPU work overlaps (other
+ * streams or threads) race; calls ordered on one stream are safe. Asynchronous on `stream`. */
+rbf_status rbf_eval_noalloc(const double* cx, const double* cy, const double* c, int64_t M,
+                            double R, const double* bbox, rbf_kernel kernel, const double* qx,
+                            const double* qy, int64_t Q, double* f, void* stream);
+
 /* Self-test of the device square root used for distances (Newton-Raphson iteration for the
  * reciprocal square root seeded by the FP32 hardware estimate): for each a[i] >= 0 (DEVICE,
  * n values) writes out[2i] = that square root and out[2i+1] = CUDA's sqrt(a[i]) (DEVICE,

@@ -47,6 +47,7 @@ SIGNATURES = {
     "rbf_get_launch_count": (_I, [_P, C.POINTER(_I64)]),
     "rbf_set_param": (_I, [_P, C.c_char_p, _D]),
     "rbf_selftest_sqrt": (_I, [_P, _P, _I64, _P]),
+    "rbf_eval_noalloc": (_I, [_P, _P, _P, _I64, _D, C.POINTER(_D), _I, _P, _P, _I64, _P, _P]),
     "rbf_bench_spmv": (_I, [_P, _I, _P]),
     "rbf_bench_cg": (_I, [_P, _I, _P]),
 }
