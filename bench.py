@@ -38,6 +38,19 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 
+# DRAM bytes (read + write) per launch of the solver's SpMV from one ncu capture
+# (profiles/spmv_update_fp32_terrain_1M.md), valid while the solver source is unchanged.
+SPMV_TRAFFIC = {"src_sha256_16": "321c46b1a00541b1", "bytes": 76288 + 88064}
+
+
+def spmv_traffic():
+    import hashlib
+    path = os.path.join(ROOT, "paper_1806_07884_gb300", "csrc", "rbf_solve.cu")
+    with open(path, "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()[:16]
+    return SPMV_TRAFFIC["bytes"] if sha == SPMV_TRAFFIC["src_sha256_16"] else None
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -267,6 +280,13 @@ def main():
     s1.record(stream)
     torch.cuda.synchronize()
     spmv_ms = s0.elapsed_time(s1) / reps
+    # one CG iteration (SpMV + update kernels) launched individually, same workspace
+    ctx.bench_cg(10)
+    s0.record(stream)
+    ctx.bench_cg(100)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    cg_iter_us = s0.elapsed_time(s1) * 1e3 / 100
     peaks = {}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -277,9 +297,10 @@ def main():
     achieved = spmv_bytes / (spmv_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "kernel": f"k_spmv<{'float' if vb == 4 else 'double'}>",
                 "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                "frac": round(achieved / hbm, 4), "traffic": None,
+                "frac": round(achieved / hbm, 4), "traffic": spmv_traffic(),
                 "algorithmic_bytes": spmv_bytes, "launch_ms": round(spmv_ms, 5),
-                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                "cg_iteration_us_plain_launches": round(cg_iter_us, 2)}
 
     # ---- accuracy: this path's surface against a tight FP64 solve of the same workload
     f_fast = fbuf.clone()
