@@ -18,6 +18,9 @@
  *   rbf_solve      Jacobi-preconditioned CG on B c = b (FP64), or FP32 CG inside
  *                  FP64 iterative refinement with a matrix-free FP64 residual
  *   rbf_eval       f at arbitrary query points (Eq. 3); rbf_eval_grid on a grid
+ *   rbf_bin_tiles, rbf_solve_tiles
+ *                  many independent tiles of uneven size binned, assembled (rbf_assemble)
+ *                  and solved together, each kernel launched once for the whole batch
  *
  * Conventions (all entry points):
  *   - Array arguments are DEVICE pointers owned by the caller unless stated
@@ -86,6 +89,25 @@ typedef struct {
                                 refined iterate; the context's assembly is FP64 afterwards */
 } rbf_solve_info;
 
+/* One tile of a batch (rbf_bin_tiles): an independent fitting problem of the same kind as
+ * rbf_bin's, whose centres and points are ranges of concatenated arrays. */
+typedef struct {
+    int64_t c0, M;           /* centres c0 .. c0+M-1 of the concatenated centre arrays, M >= 1 */
+    int64_t p0, N;           /* points p0 .. p0+N-1 of the concatenated point arrays, N >= 0 */
+    double R;                /* support radius of this tile, > 0 */
+    double bbox[4];          /* {x0, y0, x1, y1} of this tile (items outside are clamped) */
+} rbf_tile;
+
+/* Per-tile result of rbf_solve_tiles. */
+typedef struct {
+    int iterations;          /* CG iterations of this tile (summed over refinement steps) */
+    int refinements;         /* FP64 refinement steps this tile took part in */
+    double rel_residual;     /* as rbf_solve_info.rel_residual, over this tile's centres */
+    int64_t pinned;          /* centres of this tile with fewer than min_support points */
+    int status;              /* rbf_status of this tile: RBF_OK, RBF_ERR_NOT_CONVERGED or
+                                RBF_ERR_BREAKDOWN */
+} rbf_tile_info;
+
 /* Create / destroy a context bound to CUDA device `device`. */
 rbf_status rbf_create(rbf_ctx** out, int device, rbf_alloc_fn alloc, rbf_free_fn free_fn,
                       void* user);
@@ -146,6 +168,13 @@ rbf_status rbf_eval_grid(rbf_ctx* ctx, const double* c, int nx, int ny, const do
  *   "inner_tol"        relative tolerance of each FP32 inner solve of RBF_FP32_REFINE, in
  *                      (0, 1); default 1e-3
  *   "max_refinements"  FP64 refinement steps of RBF_FP32_REFINE, in [0, 1000]; default 30
+ *   "autotune"         1 (default): rbf_solve_tiles times the candidate launch
+ *                      configurations of its CG loop on the first solve of a system of a
+ *                      new shape and keeps the fastest (see rbf_autotune); 0: it uses the
+ *                      forced values below, else a fixed default
+ *   "spmv_blocks_per_sm", "spmv_chunk", "update_threads"
+ *                      force the batched CG's SpMV blocks per SM (1..8), cells per warp
+ *                      step (1..64) and update block size (128, 256 or 512); 0 = automatic
  * Returns RBF_ERR_ARG for an unknown name or a value out of range. */
 rbf_status rbf_set_param(rbf_ctx* ctx, const char* name, double value);
 
@@ -176,6 +205,49 @@ rbf_status rbf_bench_spmv(rbf_ctx* ctx, int reps, void* stream);
  * inside one CUDA graph), so that the kernels can be timed or profiled one by one. Uses and
  * overwrites the solver's workspace; requires a preceding rbf_solve. Asynchronous. */
 rbf_status rbf_bench_cg(rbf_ctx* ctx, int reps, void* stream);
+
+/* Batched step (a): bin T independent tiles (HOST array `tiles`) into one packed system.
+ * cx, cy: DEVICE arrays of Mtot centre coordinates; px, py, h: DEVICE arrays of Ntot point
+ * coordinates and heights; tile t owns centres [c0, c0+M) and points [p0, p0+N). The centre
+ * ranges of all tiles must partition [0, Mtot) and the point ranges of the tiles with N > 0
+ * must partition [0, Ntot) (any order of tiles). Each tile is fitted exactly as rbf_bin +
+ * rbf_assemble + rbf_solve would fit it alone: A_ij = phi(||x_i - xi_j|| / R_t) over the
+ * tile's own points and centres only. Internally each tile is moved to its own frame
+ * (x - x0_t) / R_t, where its support radius is 1, and gets its own band of cell rows of one
+ * shared grid, two empty rows apart, so the packed B is block diagonal by tile.
+ * Follow with rbf_assemble (one launch for all tiles) and rbf_solve_tiles; rbf_solve,
+ * rbf_eval and rbf_eval_grid reject a batched context. Synchronises `stream`.
+ * Returns RBF_ERR_ARG for overlapping or non-covering ranges, RBF_ERR_LIMIT if the packed
+ * grid exceeds 2^24 cells or a 3x3 neighbourhood more than rbf_max_candidates() centres. */
+rbf_status rbf_bin_tiles(rbf_ctx* ctx, const rbf_tile* tiles, int T, const double* cx,
+                         const double* cy, int64_t Mtot, const double* px, const double* py,
+                         const double* h, int64_t Ntot, void* stream);
+
+/* Batched step (d): solve every tile's normal equations B_t c_t = b_t with its own CG
+ * (own step lengths, own stopping test, own iteration count), all tiles advancing together
+ * in one CUDA graph whose kernels each cover every tile still running. c: DEVICE array of
+ * Mtot doubles in the caller's concatenated centre order (start guess if use_c0). tol,
+ * maxit, min_support as for rbf_solve, applied per tile. tile_info: HOST array of T entries
+ * (may be NULL); info: HOST totals (may be NULL): iterations = largest per-tile count,
+ * refinements = most refinement steps, rel_residual = largest per-tile value, pinned = sum,
+ * promoted as for rbf_solve (applies to the whole batch). Synchronises `stream`. Returns
+ * RBF_OK when every tile converged, else RBF_ERR_BREAKDOWN if some tile broke down, else
+ * RBF_ERR_NOT_CONVERGED; c holds every tile's last iterate in all cases. */
+rbf_status rbf_solve_tiles(rbf_ctx* ctx, double* c, int use_c0, double tol, int maxit,
+                           int min_support, rbf_tile_info* tile_info, rbf_solve_info* info,
+                           void* stream);
+
+/* Autotuner of the batched CG loop: on the assembled batched system, times CG iterations in
+ * each candidate launch configuration (SpMV blocks per SM x cells per warp step, then the
+ * update block size) with CUDA events on `stream` and keeps the fastest for systems of this
+ * shape. Overwrites the solver workspace. Synchronises `stream`. */
+rbf_status rbf_autotune(rbf_ctx* ctx, void* stream);
+
+/* The launch configuration of the batched CG loop for the precision of the last assembly
+ * (HOST outputs, any may be NULL): SpMV blocks per SM, cells per warp step, update block
+ * size, and the measured time of one iteration in microseconds (0 if not tuned). */
+rbf_status rbf_get_tuning(const rbf_ctx* ctx, int* spmv_blocks_per_sm, int* spmv_chunk,
+                          int* update_threads, double* us_per_iteration);
 
 /* Evaluation with no allocation at all (the paper has no counterpart; this is a service to
  * callers that cannot allocate device memory where they need the surface -- e.g. code that

@@ -19,7 +19,8 @@ import ctypes as C
 from . import _lib
 from ._lib import KERNELS, PRECS, RBFError
 
-__all__ = ["Context", "fit", "RBFError", "KERNELS", "PRECS", "max_candidates"]
+__all__ = ["Context", "fit", "fit_tiles", "pack_tiles", "RBFError", "KERNELS", "PRECS",
+           "max_candidates"]
 
 
 def _torch():
@@ -71,7 +72,7 @@ class Context:
         if s != 0:
             raise RBFError(s, "rbf_create failed")
         self._h = h
-        self.M = self.N = 0
+        self.M = self.N = self.T = 0
         self.kernel = None
         self.prec = None
 
@@ -107,7 +108,7 @@ class Context:
                              _dptr(py, "py"), _dptr(h, "h"), N, float(R), box,
                              self._stream(stream))
         self._check(s, "rbf_bin")
-        self.M, self.N = M, N
+        self.M, self.N, self.T = M, N, 0
 
     def assemble(self, kernel: str = "w31", prec: str = "fp64", stream=None):
         """Steps (b)+(c): fused rows of A and B = A^T A, b = A^T h."""
@@ -155,6 +156,63 @@ class Context:
         self._check(s, "rbf_eval_grid")
         return f
 
+    # -- batched tiles --------------------------------------------------------------------
+    def bin_tiles(self, tiles, cx, cy, px, py, h, stream=None):
+        """Batched step (a). tiles: sequence of dicts {c0, M, p0, N, R, bbox}; cx, cy, px, py,
+        h: concatenated CUDA float64 arrays (see rbf_bin_tiles)."""
+        T = len(tiles)
+        arr = (_lib.Tile * T)()
+        for k, t in enumerate(tiles):
+            arr[k].c0, arr[k].M = int(t["c0"]), int(t["M"])
+            arr[k].p0, arr[k].N = int(t["p0"]), int(t["N"])
+            arr[k].R = float(t["R"])
+            for q in range(4):
+                arr[k].bbox[q] = float(t["bbox"][q])
+        M, N = int(cx.numel()), int(px.numel())
+        nul = C.c_void_p()
+        s = self.lib.rbf_bin_tiles(self._h, arr, T, _dptr(cx, "cx"), _dptr(cy, "cy"), M,
+                                   _dptr(px, "px") if N else nul, _dptr(py, "py") if N else nul,
+                                   _dptr(h, "h") if N else nul, N, self._stream(stream))
+        self._check(s, "rbf_bin_tiles")
+        self.M, self.N, self.T = M, N, T
+
+    def solve_tiles(self, tol: float = 1e-10, maxit: int = 100000, min_support: int = 3,
+                    c0=None, out=None, stream=None, raise_on_fail: bool = True):
+        """Batched step (d): returns (c, info, per-tile info list)."""
+        torch = _torch()
+        c = out if out is not None else torch.empty(self.M, dtype=torch.float64,
+                                                    device=f"cuda:{self.device}")
+        if c0 is not None and c0.data_ptr() != c.data_ptr():
+            c.copy_(c0)
+        T = self.T
+        tinfo = (_lib.TileInfo * T)()
+        info = _lib.SolveInfo()
+        s = self.lib.rbf_solve_tiles(self._h, _dptr(c, "c"), 1 if c0 is not None else 0,
+                                     float(tol), int(maxit), int(min_support), tinfo,
+                                     C.byref(info), self._stream(stream))
+        d = dict(iterations=info.iterations, refinements=info.refinements,
+                 rel_residual=info.rel_residual, pinned=info.pinned, promoted=info.promoted,
+                 status=s)
+        tl = [dict(iterations=t.iterations, refinements=t.refinements,
+                   rel_residual=t.rel_residual, pinned=t.pinned, status=t.status) for t in tinfo]
+        if info.promoted:
+            self.prec = "fp64"
+        if s != 0 and raise_on_fail:
+            self._check(s, "rbf_solve_tiles")
+        return c, d, tl
+
+    def autotune(self, stream=None):
+        """Time the batched CG loop's launch configurations and keep the fastest."""
+        self._check(self.lib.rbf_autotune(self._h, self._stream(stream)), "rbf_autotune")
+        return self.tuning()
+
+    def tuning(self):
+        b, ch, nt, us = C.c_int(), C.c_int(), C.c_int(), C.c_double()
+        self._check(self.lib.rbf_get_tuning(self._h, C.byref(b), C.byref(ch), C.byref(nt),
+                                            C.byref(us)), "rbf_get_tuning")
+        return dict(spmv_blocks_per_sm=b.value, spmv_chunk=ch.value, update_threads=nt.value,
+                    us_per_iteration=us.value)
+
     # -- diagnostics --------------------------------------------------------------------
     def layout(self):
         nv, vb, gx, gy = C.c_int64(), C.c_int(), C.c_int(), C.c_int()
@@ -200,6 +258,42 @@ class Context:
         self._check(s, "rbf_export_upper")
         n = nnz.value
         return row[:n], col[:n], val[:n], b, sup
+
+
+def pack_tiles(problems):
+    """Concatenate per-tile host arrays. problems: sequence of (points (N,2), h (N,),
+    centres (M,2), R, bbox). Returns (tiles, cx, cy, px, py, h) with numpy arrays."""
+    import numpy as np
+    tiles, C_, P_, H_ = [], [], [], []
+    c0 = p0 = 0
+    for pts, hh, cen, R, bbox in problems:
+        pts = np.asarray(pts, dtype=np.float64).reshape(-1, 2)
+        cen = np.asarray(cen, dtype=np.float64).reshape(-1, 2)
+        tiles.append(dict(c0=c0, M=len(cen), p0=p0, N=len(pts), R=float(R), bbox=tuple(bbox)))
+        c0 += len(cen)
+        p0 += len(pts)
+        C_.append(cen)
+        P_.append(pts)
+        H_.append(np.asarray(hh, dtype=np.float64).reshape(-1))
+    Cc, Pp, Hh = np.concatenate(C_), np.concatenate(P_), np.concatenate(H_)
+    return tiles, Cc[:, 0].copy(), Cc[:, 1].copy(), Pp[:, 0].copy(), Pp[:, 1].copy(), Hh
+
+
+def fit_tiles(problems, kernel: str = "w31", prec: str = "fp32_refine", tol: float = 1e-10,
+              maxit: int = 200000, min_support: int = 3, ctx: Context | None = None,
+              device: int = 0):
+    """Fit many independent tiles together. problems: as for pack_tiles. Returns
+    (list of per-tile c on the device, info, per-tile info, ctx)."""
+    torch = _torch()
+    dev = f"cuda:{device}"
+    tiles, cx, cy, px, py, hh = pack_tiles(problems)
+    t = [torch.as_tensor(a).to(dev) for a in (cx, cy, px, py, hh)]
+    ctx = ctx or Context(device)
+    ctx.bin_tiles(tiles, *t)
+    ctx.assemble(kernel, prec)
+    c, info, tinfo = ctx.solve_tiles(tol=tol, maxit=maxit, min_support=min_support)
+    cs = [c[d["c0"]:d["c0"] + d["M"]] for d in tiles]
+    return cs, info, tinfo, ctx
 
 
 def fit(points, h, centres, R: float, kernel: str = "w31", prec: str = "fp64",

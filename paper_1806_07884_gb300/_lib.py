@@ -26,6 +26,16 @@ class SolveInfo(C.Structure):
                 ("rel_residual", C.c_double), ("pinned", C.c_int64), ("promoted", C.c_int)]
 
 
+class Tile(C.Structure):
+    _fields_ = [("c0", C.c_int64), ("M", C.c_int64), ("p0", C.c_int64), ("N", C.c_int64),
+                ("R", C.c_double), ("bbox", C.c_double * 4)]
+
+
+class TileInfo(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("refinements", C.c_int),
+                ("rel_residual", C.c_double), ("pinned", C.c_int64), ("status", C.c_int)]
+
+
 _P = C.c_void_p
 _D = C.c_double
 _I = C.c_int
@@ -50,6 +60,10 @@ SIGNATURES = {
     "rbf_eval_noalloc": (_I, [_P, _P, _P, _I64, _D, C.POINTER(_D), _I, _P, _P, _I64, _P, _P]),
     "rbf_bench_spmv": (_I, [_P, _I, _P]),
     "rbf_bench_cg": (_I, [_P, _I, _P]),
+    "rbf_bin_tiles": (_I, [_P, C.POINTER(Tile), _I, _P, _P, _I64, _P, _P, _P, _I64, _P]),
+    "rbf_solve_tiles": (_I, [_P, _P, _I, _D, _I, _I, C.POINTER(TileInfo), C.POINTER(SolveInfo), _P]),
+    "rbf_autotune": (_I, [_P, _P]),
+    "rbf_get_tuning": (_I, [_P, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I), C.POINTER(_D)]),
 }
 
 _lib = None

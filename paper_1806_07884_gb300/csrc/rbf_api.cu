@@ -141,6 +141,7 @@ rbf_status rbf_destroy(rbf_ctx* ctx) {
     cudaDeviceSynchronize();
     for (auto& sg : ctx->cg_graph)
         if (sg.exec) cudaGraphExecDestroy(sg.exec);
+    tiles_release(ctx);
     if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
     rbf_buf* bufs[] = {&ctx->ccount, &ctx->pcount, &ctx->cstart, &ctx->pstart, &ctx->ckey,
                        &ctx->crank, &ctx->pkey, &ctx->prank, &ctx->cx, &ctx->cy, &ctx->cu,
@@ -194,6 +195,7 @@ rbf_status rbf_bin(rbf_ctx* ctx, const double* cx, const double* cy, int64_t M, 
     ctx->g = g;
     ctx->M = int(M);
     ctx->N = int(N);
+    ctx->T = 0;
     DeviceGuard dg(ctx->device);
     rbf_status s = bin_run(ctx, cx, cy, px, py, h, as_stream(stream));
     if (s == RBF_OK) ctx->binned = true;
@@ -220,14 +222,68 @@ rbf_status rbf_solve(rbf_ctx* ctx, double* c, int use_c0, double tol, int maxit,
     if (!ctx->assembled) return set_err(ctx, RBF_ERR_ARG, "rbf_solve before rbf_assemble");
     if (!c) return set_err(ctx, RBF_ERR_ARG, "null c");
     if (!(tol >= 0.0) || maxit < 0) return set_err(ctx, RBF_ERR_ARG, "need tol >= 0, maxit >= 0");
+    if (ctx->T > 0) return set_err(ctx, RBF_ERR_ARG, "batched context: use rbf_solve_tiles");
     DeviceGuard dg(ctx->device);
     return solve_run(ctx, c, use_c0, tol, maxit, min_support, info, as_stream(stream));
+}
+
+rbf_status rbf_bin_tiles(rbf_ctx* ctx, const rbf_tile* tiles, int T, const double* cx,
+                         const double* cy, int64_t Mtot, const double* px, const double* py,
+                         const double* h, int64_t Ntot, void* stream) {
+    if (!ctx) return RBF_ERR_ARG;
+    ctx->binned = false;
+    ctx->assembled = false;
+    ctx->solved = false;
+    if (!tiles || T < 1) return set_err(ctx, RBF_ERR_ARG, "need T >= 1 tiles");
+    if (!cx || !cy || (Ntot > 0 && (!px || !py || !h)))
+        return set_err(ctx, RBF_ERR_ARG, "null pointer argument");
+    if (Mtot < 1 || Ntot < 0 || Mtot > (int64_t(1) << 30) || Ntot > (int64_t(1) << 30))
+        return set_err(ctx, RBF_ERR_ARG, "need 1 <= Mtot <= 2^30, 0 <= Ntot <= 2^30");
+    DeviceGuard dg(ctx->device);
+    rbf_status s = bin_tiles_run(ctx, tiles, T, cx, cy, Mtot, px, py, h, Ntot, as_stream(stream));
+    if (s == RBF_OK) ctx->binned = true;
+    return s;
+}
+
+rbf_status rbf_solve_tiles(rbf_ctx* ctx, double* c, int use_c0, double tol, int maxit,
+                           int min_support, rbf_tile_info* tile_info, rbf_solve_info* info,
+                           void* stream) {
+    if (!ctx) return RBF_ERR_ARG;
+    if (!ctx->assembled || ctx->T < 1)
+        return set_err(ctx, RBF_ERR_ARG, "rbf_solve_tiles before rbf_bin_tiles + rbf_assemble");
+    if (!c) return set_err(ctx, RBF_ERR_ARG, "null c");
+    if (!(tol >= 0.0) || maxit < 0) return set_err(ctx, RBF_ERR_ARG, "need tol >= 0, maxit >= 0");
+    DeviceGuard dg(ctx->device);
+    return solve_tiles_run(ctx, c, use_c0, tol, maxit, min_support, tile_info, info,
+                           as_stream(stream));
+}
+
+rbf_status rbf_autotune(rbf_ctx* ctx, void* stream) {
+    if (!ctx) return RBF_ERR_ARG;
+    if (!ctx->assembled || ctx->T < 1)
+        return set_err(ctx, RBF_ERR_ARG, "rbf_autotune before rbf_bin_tiles + rbf_assemble");
+    DeviceGuard dg(ctx->device);
+    rbf_status s = autotune_run(ctx, as_stream(stream));
+    ctx->solved = false;
+    return s;
+}
+
+rbf_status rbf_get_tuning(const rbf_ctx* ctx, int* spmv_blocks_per_sm, int* spmv_chunk,
+                          int* update_threads, double* us_per_iteration) {
+    if (!ctx) return RBF_ERR_ARG;
+    const rbf_ctx::TileTuning& tu = ctx->tune[ctx->prec == RBF_FP64 ? 0 : 1];
+    if (spmv_blocks_per_sm) *spmv_blocks_per_sm = tu.spmv_bps;
+    if (spmv_chunk) *spmv_chunk = tu.chunk;
+    if (update_threads) *update_threads = tu.nt;
+    if (us_per_iteration) *us_per_iteration = tu.us_per_iter;
+    return RBF_OK;
 }
 
 rbf_status rbf_eval(rbf_ctx* ctx, const double* c, const double* qx, const double* qy, int64_t Q,
                     double* f, void* stream) {
     if (!ctx) return RBF_ERR_ARG;
     if (!ctx->binned || ctx->kernel < 0) return set_err(ctx, RBF_ERR_ARG, "rbf_eval before rbf_assemble");
+    if (ctx->T > 0) return set_err(ctx, RBF_ERR_ARG, "rbf_eval on a batched context");
     if (Q < 0 || (Q > 0 && (!c || !qx || !qy || !f))) return set_err(ctx, RBF_ERR_ARG, "bad arguments");
     DeviceGuard dg(ctx->device);
     return eval_points_run(ctx, c, qx, qy, Q, f, as_stream(stream));
@@ -237,6 +293,7 @@ rbf_status rbf_eval_grid(rbf_ctx* ctx, const double* c, int nx, int ny, const do
                          double* f, void* stream) {
     if (!ctx) return RBF_ERR_ARG;
     if (!ctx->binned || ctx->kernel < 0) return set_err(ctx, RBF_ERR_ARG, "rbf_eval_grid before rbf_assemble");
+    if (ctx->T > 0) return set_err(ctx, RBF_ERR_ARG, "rbf_eval_grid on a batched context");
     if (nx < 1 || ny < 1 || !c || !box || !f) return set_err(ctx, RBF_ERR_ARG, "bad arguments");
     for (int k = 0; k < 4; ++k)
         if (!isfinite(box[k])) return set_err(ctx, RBF_ERR_ARG, "non-finite box");
@@ -277,6 +334,29 @@ rbf_status rbf_set_param(rbf_ctx* ctx, const char* name, double value) {
     if (!strcmp(name, "max_refinements")) {
         if (!(value >= 0.0 && value <= 1000.0)) return set_err(ctx, RBF_ERR_ARG, "max_refinements must be in [0, 1000]");
         ctx->max_refine = int(value);
+        return RBF_OK;
+    }
+    if (!strcmp(name, "autotune")) {
+        if (!(value == 0.0 || value == 1.0)) return set_err(ctx, RBF_ERR_ARG, "autotune must be 0 or 1");
+        ctx->autotune = int(value);
+        return RBF_OK;
+    }
+    if (!strcmp(name, "spmv_blocks_per_sm")) {
+        if (!(value >= 0.0 && value <= 8.0 && value == floor(value)))
+            return set_err(ctx, RBF_ERR_ARG, "spmv_blocks_per_sm must be an integer in [0, 8]");
+        ctx->force_bps = int(value);
+        return RBF_OK;
+    }
+    if (!strcmp(name, "spmv_chunk")) {
+        if (!(value >= 0.0 && value <= 64.0 && value == floor(value)))
+            return set_err(ctx, RBF_ERR_ARG, "spmv_chunk must be an integer in [0, 64]");
+        ctx->force_chunk = int(value);
+        return RBF_OK;
+    }
+    if (!strcmp(name, "update_threads")) {
+        if (!(value == 0.0 || value == 128.0 || value == 256.0 || value == 512.0))
+            return set_err(ctx, RBF_ERR_ARG, "update_threads must be 0, 128, 256 or 512");
+        ctx->force_nt = int(value);
         return RBF_OK;
     }
     return set_err(ctx, RBF_ERR_ARG, "unknown parameter");

@@ -1,0 +1,1234 @@
+// Batched tiles: many independent fitting problems of uneven size, each kernel launched once
+// for all of them.
+//
+// Packing. Tile t is moved to its own frame u = (x - x0_t) / R_t, where its support radius
+// is 1, and its cells (side kCellMargin in that frame) become one band of rows of a single
+// cell grid: band t holds cell rows oy_t .. oy_t + gy_t - 1 and columns 0 .. gx_t - 1, and two
+// empty rows separate consecutive bands. Items of different tiles are then never in
+// neighbouring cells (3x3 for the rows of A, 5x5 for the blocks of B), so the packed normal
+// matrix is block diagonal with one block per tile, each tile's centres are contiguous in
+// the cell-sorted order, and the binning, assembly and FP64 residual kernels of the
+// single-system path run unchanged over every tile in one launch each. The FP64 coordinates
+// kept for those kernels are tile-local, so their rounding is that of one tile whatever the
+// packing.
+//
+// Solve. The CG iteration is the Chronopoulos-Gear iteration of the single-system solver
+// with its scalars held per tile: alpha_t, beta_t, the stopping test and the iteration count
+// of tile t depend only on tile t's own reductions, so every tile follows the iterates of its
+// own CG and stops at its own tolerance; stopped tiles drop out of the SpMV and the update.
+// Reductions are segmented by tile (warp segmented sums, then shared-memory atomics per
+// tile, then one global atomic per tile and block). The iteration loop is one CUDA graph
+// (conditional WHILE node) that runs until every tile has stopped. FP32 refinement works per
+// tile: own scale, own inner tolerance, own FP64 residual norm and stopping test.
+//
+// Launch configuration. The SpMV's blocks per SM, the number of consecutive cells a warp
+// takes per step and the update kernel's block size are picked by timing candidate
+// configurations on the assembled system and cached per system shape (rbf_autotune).
+#include <limits.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "rbf_cg.cuh"
+
+namespace rbf {
+namespace {
+
+// Placement of one tile in the packed grid (device copy of the host descriptor).
+struct TileDev {
+    long long c0, m, p0, n;    // centre and point ranges of the concatenated inputs
+    double x0, y0, R;          // frame: u = (x - x0) / R
+    int gx, gy, oy, pad;       // cells per axis, first cell row of the band
+};
+
+// Per-tile CG state, double-buffered by iteration parity like the single-system CgSlot.
+struct TSlot {
+    double gamma_prev, alpha_prev;
+    int it, state;
+};
+struct BatchScal {
+    unsigned int ndone;        // tiles that have stopped (or take no part in this solve)
+    int T, maxit, pad;
+};
+
+// Device view of the per-tile arrays (one allocation, layout in TileLayout).
+struct TileCg {
+    BatchScal* bs;
+    TSlot* sl[2];
+    double *g[2], *rr[2], *dl[2];   // gamma = (r, u), (r, r) and delta = u^T B u per tile
+    double *bb, *tol2, *bscale;     // (b, b) of the scaled right-hand side, tol^2, scale of b
+    double* out_rr;                 // (r, r) when the tile stopped
+    int *out_it, *out_state;
+};
+
+// Byte offsets of the per-tile arrays for T tiles; [0, init_end) is written by the host
+// before each solve, [init_end, total) read back after it.
+struct TileLayout {
+    size_t bs, sl0, sl1, g0, g1, rr0, rr1, dl0, dl1, bb, tol2, bscale, init_end;
+    size_t out_rr, out_it, out_state, total;
+    explicit TileLayout(int T) {
+        size_t o = 0;
+        auto take = [&](size_t n) {
+            const size_t r = o;
+            o += (n + 15) / 16 * 16;
+            return r;
+        };
+        const size_t t = size_t(T);
+        bs = take(sizeof(BatchScal));
+        sl0 = take(sizeof(TSlot) * t);
+        sl1 = take(sizeof(TSlot) * t);
+        g0 = take(8 * t);
+        g1 = take(8 * t);
+        rr0 = take(8 * t);
+        rr1 = take(8 * t);
+        dl0 = take(8 * t);
+        dl1 = take(8 * t);
+        bb = take(8 * t);
+        tol2 = take(8 * t);
+        bscale = take(8 * t);
+        init_end = o;
+        out_rr = take(8 * t);
+        out_it = take(4 * t);
+        out_state = take(4 * t);
+        total = o;
+    }
+    TileCg view(char* b) const {
+        TileCg v;
+        v.bs = reinterpret_cast<BatchScal*>(b + bs);
+        v.sl[0] = reinterpret_cast<TSlot*>(b + sl0);
+        v.sl[1] = reinterpret_cast<TSlot*>(b + sl1);
+        v.g[0] = reinterpret_cast<double*>(b + g0);
+        v.g[1] = reinterpret_cast<double*>(b + g1);
+        v.rr[0] = reinterpret_cast<double*>(b + rr0);
+        v.rr[1] = reinterpret_cast<double*>(b + rr1);
+        v.dl[0] = reinterpret_cast<double*>(b + dl0);
+        v.dl[1] = reinterpret_cast<double*>(b + dl1);
+        v.bb = reinterpret_cast<double*>(b + bb);
+        v.tol2 = reinterpret_cast<double*>(b + tol2);
+        v.bscale = reinterpret_cast<double*>(b + bscale);
+        v.out_rr = reinterpret_cast<double*>(b + out_rr);
+        v.out_it = reinterpret_cast<int*>(b + out_it);
+        v.out_state = reinterpret_cast<int*>(b + out_state);
+        return v;
+    }
+};
+
+// Per-tile reduction area (tred): norms [T] double, a second norm [T], pinned counts [T]
+// double, scale [T] double.
+struct RedLayout {
+    size_t n0, n1, pin, scale, total;
+    explicit RedLayout(int T) {
+        const size_t t = (size_t(T) * 8 + 15) / 16 * 16;
+        n0 = 0;
+        n1 = t;
+        pin = 2 * t;
+        scale = 3 * t;
+        total = 4 * t;
+    }
+};
+
+// ---------------------------------------------------------------------------
+// binning of a batch
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ int tile_cell(double l, double invh, int n) {
+    double f = floor(l * invh);
+    f = fmin(fmax(f, 0.0), double(n - 1));
+    return int(f);
+}
+
+// Cell key of every centre (which == 0) or point (which == 1) of tile blockIdx.y, in the
+// packed grid: key = (oy_t + iy) * gx + ix with (ix, iy) the cell of (x - x0_t) / R_t.
+__global__ void k_tile_count(const TileDev* __restrict__ td, int which, const double* __restrict__ x,
+                             const double* __restrict__ y, const double* __restrict__ h, Grid g,
+                             int* __restrict__ count, int* __restrict__ key,
+                             int* __restrict__ rank, int* __restrict__ stats) {
+    const TileDev t = td[blockIdx.y];
+    const long long b = which ? t.p0 : t.c0, n = which ? t.n : t.m;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long k = b + i;
+        const double xi = x[k], yi = y[k];
+        bool bad = !isfinite(xi) || !isfinite(yi);
+        if (h) bad = bad || !isfinite(h[k]);
+        if (bad) atomicOr(&stats[2], 1);
+        int kk = t.oy * g.gx;
+        if (!bad) {
+            const double xl = (xi - t.x0) / t.R, yl = (yi - t.y0) / t.R;
+            kk = (t.oy + tile_cell(yl, g.invh, t.gy)) * g.gx + tile_cell(xl, g.invh, t.gx);
+        }
+        key[k] = kk;
+        rank[k] = atomicAdd(&count[kk], 1);
+    }
+}
+
+// Scatter into cell-sorted order with tile-local FP64 coordinates and FP32 coordinates
+// local to the item's cell (units of R_t).
+__global__ void k_tile_scatter(const TileDev* __restrict__ td, int which,
+                               const double* __restrict__ x, const double* __restrict__ y,
+                               const double* __restrict__ h, Grid g, const int* __restrict__ key,
+                               const int* __restrict__ rank, const int* __restrict__ start,
+                               double* __restrict__ sx, double* __restrict__ sy,
+                               double* __restrict__ sh, float* __restrict__ su,
+                               float* __restrict__ sv, int* __restrict__ perm) {
+    const TileDev t = td[blockIdx.y];
+    const long long b = which ? t.p0 : t.c0, n = which ? t.n : t.m;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long k = b + i;
+        const int kk = key[k];
+        const int d = start[kk] + rank[k];
+        const double xl = (x[k] - t.x0) / t.R, yl = (y[k] - t.y0) / t.R;
+        sx[d] = xl;
+        sy[d] = yl;
+        if (sh) sh[d] = h[k];
+        if (perm) perm[d] = int(k);
+        const int ix = kk % g.gx, iy = kk / g.gx - t.oy;
+        su[d] = float(xl - ix * g.h);
+        sv[d] = float(yl - iy * g.h);
+    }
+}
+
+__global__ void k_cell_flags(int ncell, const int* __restrict__ cstart, int* __restrict__ flag) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < ncell) flag[c] = cstart[c + 1] > cstart[c] ? 1 : 0;
+}
+__global__ void k_cell_compact(int ncell, const int* __restrict__ cstart,
+                               const int* __restrict__ pos, int* __restrict__ list) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < ncell && cstart[c + 1] > cstart[c]) list[pos[c]] = c;
+}
+
+// ---------------------------------------------------------------------------
+// segmented (per-tile) reductions
+// ---------------------------------------------------------------------------
+
+// Warp segmented sum of NV values keyed by tile: keys are equal over contiguous runs of lanes
+// (rows are in tile order). Afterwards the first lane of each run holds the run's sums;
+// returns true in those lanes.
+template <int NV>
+__device__ __forceinline__ bool warp_segsum(int key, double (&v)[NV]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int ok = __shfl_down_sync(kFull, key, o);
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            const double ov = __shfl_down_sync(kFull, v[k], o);
+            if (lane + o < 32 && ok == key) v[k] += ov;
+        }
+    }
+    const int up = __shfl_up_sync(kFull, key, 1);
+    return lane == 0 || up != key;
+}
+
+// Rows i0 .. i1-1 of one block belong to tiles t0 .. t0+span-1. Adds each thread's NV values
+// (key = its row's tile, INT_MAX for none) into dst[k][tile]: warp segmented sums, shared
+// atomics per tile, then one global atomic per tile and value. sred: [NV][NT] shared doubles
+// zeroed for j < span before the call (with a barrier in between).
+template <int NV, int NT>
+__device__ __forceinline__ void tile_reduce(int key, double (&v)[NV], int t0, int span,
+                                            double (*sred)[NT], double* const (&dst)[NV]) {
+    if (warp_segsum<NV>(key, v) && key != INT_MAX) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k)
+            if (v[k] != 0.0) atomicAdd(&sred[k][key - t0], v[k]);
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < span; j += NT) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k)
+            if (sred[k][j] != 0.0) atomicAdd(dst[k] + t0 + j, sred[k][j]);
+    }
+}
+
+// Tiles of the rows of block `blk` (NT rows each): t0 and span.
+__device__ __forceinline__ void block_tiles(const Binned& bd, int i0, int i1, int& t0, int& span) {
+    t0 = bd.crow[i0].w;
+    span = bd.crow[i1 - 1].w - t0 + 1;
+}
+
+// Per-tile sum of v_i^2 (v may be null) over rows whose mask is nonzero, and per-tile count
+// of rows whose mask is zero (pinned centres), one block per 256 rows.
+template <typename TM>
+__global__ void __launch_bounds__(256)
+    k_tile_norm2(Binned bd, const double* __restrict__ v, const TM* __restrict__ mask,
+                 double* __restrict__ out2, double* __restrict__ npin) {
+    constexpr int NT = 256;
+    __shared__ double sred[2][NT];
+    const int i0 = blockIdx.x * NT;
+    if (i0 >= bd.M) return;
+    const int i1 = min(i0 + NT, bd.M);
+    int t0, span;
+    block_tiles(bd, i0, i1, t0, span);
+    for (int j = threadIdx.x; j < span; j += NT) sred[0][j] = sred[1][j] = 0.0;
+    __syncthreads();
+    const int i = i0 + threadIdx.x;
+    int key = INT_MAX;
+    double a[2] = {0.0, 0.0};
+    if (i < i1) {
+        key = bd.crow[i].w;
+        const bool pinned = mask[i] == TM(0);
+        if (v && !pinned) a[0] = v[i] * v[i];
+        a[1] = pinned ? 1.0 : 0.0;
+    }
+    double* const dst[2] = {out2, npin};
+    tile_reduce<2, NT>(key, a, t0, span, sred, dst);
+}
+
+// x = x + scale_t d on unpinned rows, x = 0 on pinned rows.
+__global__ void k_tile_axpy(Binned bd, double* __restrict__ x, const float* __restrict__ d,
+                            const double* __restrict__ scale, const float* __restrict__ dinv) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < bd.M) x[i] = dinv[i] == 0.0f ? 0.0 : fma(scale[bd.crow[i].w], double(d[i]), x[i]);
+}
+
+__global__ void k_zero_masked(int M, double* __restrict__ x, const float* __restrict__ dinv32) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < M && dinv32[i] == 0.0f) x[i] = 0.0;
+}
+
+template <typename T>
+__global__ void k_tile_to_sorted(const double* __restrict__ src, const int* __restrict__ perm,
+                                 const T* __restrict__ dinv, T* __restrict__ dst, int M) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < M) dst[s] = dinv[s] == T(0) ? T(0) : T(src[perm[s]]);
+}
+template <typename T>
+__global__ void k_tile_from_sorted(const T* __restrict__ src, const int* __restrict__ perm,
+                                   double* __restrict__ dst, int M) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < M) dst[perm[s]] = double(src[s]);
+}
+__global__ void k_copy_masked(int M, const double* __restrict__ src, const double* __restrict__ dinv,
+                              double* __restrict__ dst) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < M) dst[i] = dinv[i] == 0.0 ? 0.0 : src[i];
+}
+
+// ---------------------------------------------------------------------------
+// batched CG kernels
+// ---------------------------------------------------------------------------
+
+// w += B u over the non-empty cells of running tiles; delta_t = u^T B u per tile. Warps take
+// `chunk` consecutive cells of the list per step (consecutive cells are mostly of one tile,
+// so a warp adds its delta to the tile's total once per run of cells). Also zeroes the
+// per-tile sums the next update kernel accumulates (parity P ^ 1).
+template <typename T>
+__global__ void __launch_bounds__(kSpmvWarps * 32, sizeof(T) == 4 ? 3 : 1)
+    k_bcg_spmv(Binned bd, const int* __restrict__ clist, int ncl, int chunk,
+               const T* __restrict__ B, const T* __restrict__ u, T* __restrict__ w, int P,
+               int ntile, TileCg tc) {
+    // parity selection by value (indexing the parameter's arrays with P would copy them to
+    // local memory)
+    double* __restrict__ gQ = P ? tc.g[0] : tc.g[1];
+    double* __restrict__ rrQ = P ? tc.rr[0] : tc.rr[1];
+    double* __restrict__ dlP = P ? tc.dl[1] : tc.dl[0];
+    const TSlot* __restrict__ slP = P ? tc.sl[1] : tc.sl[0];
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntile; t += gridDim.x * blockDim.x) {
+        gQ[t] = 0.0;
+        rrQ[t] = 0.0;
+    }
+    const int lane = threadIdx.x & 31;
+    const long long gw = blockIdx.x * (long long)kSpmvWarps + (threadIdx.x >> 5);
+    const long long step = (long long)gridDim.x * kSpmvWarps * chunk;
+    int cur = -1;
+    bool run = false;
+    double acc = 0.0;
+    for (long long base = gw * chunk; base < ncl; base += step) {
+        const int e = int(min(base + chunk, (long long)ncl));
+        for (int k = int(base); k < e; ++k) {
+            const CellDesc cd = load_desc(bd.cdesc + __ldg(clist + k));
+            if (cd.pad != cur) {            // warp-uniform
+                const double s = warp_sum_d(acc);
+                if (lane == 0 && cur >= 0 && s != 0.0) atomicAdd(&dlP[cur], s);
+                acc = 0.0;
+                cur = cd.pad;
+                run = slP[cur].state == kRunning;
+            }
+            if (run) acc += spmv_cell<T>(cd, B, u, w, lane);
+        }
+    }
+    const double s = warp_sum_d(acc);
+    if (lane == 0 && cur >= 0 && s != 0.0) atomicAdd(&dlP[cur], s);
+}
+
+// One thread per row, one block per NT rows. Prologue: for each tile of the block's rows,
+// alpha_t and beta_t from the tile's sums (the same values in every block); the block holding
+// the tile's first row also writes the tile's next slot, clears its delta sum of the other
+// parity and, when the tile stops, records its result and counts it done. Body as the
+// single-system update with the row's tile scalars; per-tile sums of gamma and (r, r) for
+// the next iteration.
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT)
+    k_bcg_update(Binned bd, CgVec<T> v, int P, TileCg tc) {
+    __shared__ double s_alpha[NT], s_beta[NT];
+    __shared__ double sred[2][NT];
+    __shared__ int s_go[NT];
+    const TSlot* __restrict__ slP = P ? tc.sl[1] : tc.sl[0];
+    TSlot* __restrict__ slQ = P ? tc.sl[0] : tc.sl[1];
+    const double* __restrict__ gP = P ? tc.g[1] : tc.g[0];
+    const double* __restrict__ rrP = P ? tc.rr[1] : tc.rr[0];
+    const double* __restrict__ dlP = P ? tc.dl[1] : tc.dl[0];
+    double* __restrict__ gQ = P ? tc.g[0] : tc.g[1];
+    double* __restrict__ rrQ = P ? tc.rr[0] : tc.rr[1];
+    double* __restrict__ dlQ = P ? tc.dl[0] : tc.dl[1];
+    const int i0 = blockIdx.x * NT;
+    if (i0 >= bd.M) return;
+    const int i1 = min(i0 + NT, bd.M);
+    int t0, span;
+    block_tiles(bd, i0, i1, t0, span);
+    const int maxit = tc.bs->maxit;
+    for (int j = threadIdx.x; j < span; j += NT) {
+        const int t = t0 + j;
+        const TSlot sl = slP[t];
+        int state = sl.state;
+        double alpha = 0.0, beta = 0.0;
+        const double g = __ldcg(gP + t), rr = __ldcg(rrP + t);
+        if (state == kRunning) {
+            const double d = __ldcg(dlP + t);
+            if (!isfinite(g) || !isfinite(rr)) {
+                state = kBreakdown;
+            } else if (rr <= tc.tol2[t] * __ldcg(tc.bb + t)) {
+                state = kConverged;
+            } else if (sl.it >= maxit) {
+                state = kMaxIt;
+            } else {
+                beta = sl.it == 0 ? 0.0 : g / sl.gamma_prev;
+                const double den = sl.it == 0 ? d : d - beta * g / sl.alpha_prev;
+                alpha = g / den;
+                if (!(den > 0.0) || !isfinite(alpha)) state = kBreakdown;
+            }
+        }
+        const bool owner = j > 0 || i0 == 0 || bd.crow[i0 - 1].w != t0;
+        if (owner) {
+            TSlot nx = sl;
+            nx.state = state;
+            if (state == kRunning) {
+                nx.gamma_prev = g;
+                nx.alpha_prev = alpha;
+                nx.it = sl.it + 1;
+            }
+            slQ[t] = nx;
+            dlQ[t] = 0.0;
+            if (sl.state == kRunning && state != kRunning) {
+                tc.out_rr[t] = rr;
+                tc.out_it[t] = sl.it;
+                tc.out_state[t] = state;
+                atomicAdd(&tc.bs->ndone, 1u);
+            }
+        }
+        s_alpha[j] = alpha;
+        s_beta[j] = beta;
+        s_go[j] = state == kRunning;
+        sred[0][j] = 0.0;
+        sred[1][j] = 0.0;
+    }
+    __syncthreads();
+    const T* __restrict__ rP = P ? v.r[1] : v.r[0];
+    const T* __restrict__ sP = P ? v.s[1] : v.s[0];
+    const T* __restrict__ wP = P ? v.w[1] : v.w[0];
+    T* __restrict__ rQ = P ? v.r[0] : v.r[1];
+    T* __restrict__ sQ = P ? v.s[0] : v.s[1];
+    T* __restrict__ wQ = P ? v.w[0] : v.w[1];
+    const int i = i0 + threadIdx.x;
+    int key = INT_MAX;
+    double acc[2] = {0.0, 0.0};
+    if (i < i1) {
+        const int4 cm = bd.crow[i];
+        key = cm.w;
+        const int j = cm.w - t0;
+        if (s_go[j]) {
+            const T ta = T(s_alpha[j]), tb = T(s_beta[j]);
+            const T di = v.dinv[i];
+            const T wi = di == T(0) ? T(0) : wP[i];
+            const T si = fma(tb, sP[i], wi);
+            const T pi = fma(tb, v.p[i], v.u[i]);
+            const T ri = di == T(0) ? T(0) : fma(-ta, si, rP[i]);
+            const T ui = apply_prec<T>(bd, v.bjinv, cm, i, di, ri,
+                                       [&](int jj) { return next_r(rP[jj], sP[jj], wP[jj], ta, tb); });
+            sQ[i] = si;
+            v.p[i] = pi;
+            v.x[i] = fma(ta, pi, v.x[i]);
+            rQ[i] = ri;
+            v.u[i] = ui;
+            wQ[i] = T(0);
+            acc[0] = double(ri * ui);
+            acc[1] = double(ri * ri);
+        }
+    }
+    double* const dst[2] = {gQ, rrQ};
+    tile_reduce<2, NT>(key, acc, t0, span, sred, dst);
+}
+
+// Start of a batched solve of B x = bscale_t b per tile (tiles with bscale_t = 0 take no
+// part: their rows get r = u = 0 and keep x when use_x0, else x = 0):
+// r = bscale_t b - B x0 (B x0 in w[1] when use_x0), u = D^-1 r, p = s[0] = w[0] = 0;
+// per-tile gamma_0, (r_0, r_0) and (b, b).
+template <typename T, typename TB>
+__global__ void __launch_bounds__(256)
+    k_bcg_init(Binned bd, CgVec<T> v, const TB* __restrict__ b, int use_x0, TileCg tc) {
+    constexpr int NT = 256;
+    __shared__ double sred[3][NT];
+    const int i0 = blockIdx.x * NT;
+    if (i0 >= bd.M) return;
+    const int i1 = min(i0 + NT, bd.M);
+    int t0, span;
+    block_tiles(bd, i0, i1, t0, span);
+    for (int j = threadIdx.x; j < span; j += NT) sred[0][j] = sred[1][j] = sred[2][j] = 0.0;
+    __syncthreads();
+    const int i = i0 + threadIdx.x;
+    int key = INT_MAX;
+    double acc[3] = {0.0, 0.0, 0.0};
+    if (i < i1) {
+        const int4 cm = bd.crow[i];
+        key = cm.w;
+        const double bs = tc.bscale[cm.w];
+        const T* __restrict__ w1 = v.w[1];
+        auto r0 = [&](int j) -> T {
+            const T bj = T(double(b[j]) * bs);
+            return use_x0 ? bj - w1[j] : bj;
+        };
+        const T di = v.dinv[i];
+        const bool act = bs != 0.0;
+        const T bi = act && di != T(0) ? T(double(b[i]) * bs) : T(0);
+        const T ri = act && di != T(0) ? r0(i) : T(0);
+        const T ui = act ? apply_prec<T>(bd, v.bjinv, cm, i, di, ri, r0) : T(0);
+        if (!use_x0) v.x[i] = T(0);
+        v.r[0][i] = ri;
+        v.u[i] = ui;
+        v.p[i] = T(0);
+        v.s[0][i] = T(0);
+        v.w[0][i] = T(0);
+        acc[0] = double(ri) * double(ui);
+        acc[1] = double(ri) * double(ri);
+        acc[2] = double(bi) * double(bi);
+    }
+    double* const dst[3] = {tc.g[0], tc.rr[0], tc.bb};
+    tile_reduce<3, NT>(key, acc, t0, span, sred, dst);
+}
+
+__global__ void k_bcg_cond(const BatchScal* __restrict__ bs, cudaGraphConditionalHandle h) {
+    cudaGraphSetConditional(h, bs->ndone < unsigned(bs->T) ? 1u : 0u);
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+struct Cfg {
+    int bps, chunk, nt;
+};
+
+template <typename T>
+int spmv_occupancy() {
+    int a = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_bcg_spmv<T>, kSpmvWarps * 32, 0);
+    return std::max(1, a);
+}
+
+int sm_count(const rbf_ctx* ctx) {
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    return std::max(1, sms);
+}
+
+TileCg tile_view(rbf_ctx* ctx) { return TileLayout(ctx->T).view(ctx->tcg.as<char>()); }
+
+// One batched CG iteration (two kernels) reading the buffers of parity P.
+template <typename T>
+void launch_bcg_iteration(rbf_ctx* ctx, const CgVec<T>& v, const TileCg& tc, const Cfg& cf,
+                          int P, cudaStream_t cs) {
+    const Binned bd = view(ctx);
+    const int grid = std::max(1, std::min(cf.bps * sm_count(ctx),
+                                          div_up(ctx->ncl, int64_t(kSpmvWarps) * cf.chunk)));
+    k_bcg_spmv<T><<<grid, kSpmvWarps * 32, 0, cs>>>(bd, ctx->clist.as<int>(), ctx->ncl, cf.chunk,
+                                                    ctx->bvals.as<T>(), v.u, v.w[P], P, ctx->T, tc);
+    const int nb = std::max(1, div_up(ctx->M, cf.nt));
+    switch (cf.nt) {
+        case 128: k_bcg_update<T, 128><<<nb, 128, 0, cs>>>(bd, v, P, tc); break;
+        case 512: k_bcg_update<T, 512><<<nb, 512, 0, cs>>>(bd, v, P, tc); break;
+        default: k_bcg_update<T, 256><<<nb, 256, 0, cs>>>(bd, v, P, tc); break;
+    }
+}
+
+// Write the per-tile start state: tiles with active[t] run with scale bscale[t] and
+// tolerance tol[t]; the others are counted done.
+rbf_status write_tile_state(rbf_ctx* ctx, const std::vector<char>& active,
+                            const std::vector<double>& bscale, const std::vector<double>& tol,
+                            int maxit, cudaStream_t st) {
+    const int T = ctx->T;
+    const TileLayout L(T);
+    char* h = static_cast<char*>(ctx->hbt);
+    memset(h, 0, L.total);
+    TileCg hv = L.view(h);
+    unsigned int inactive = 0;
+    for (int t = 0; t < T; ++t) {
+        TSlot s;
+        s.gamma_prev = 1.0;
+        s.alpha_prev = 1.0;
+        s.it = 0;
+        s.state = active[t] ? kRunning : kInactive;
+        hv.sl[0][t] = s;
+        hv.sl[1][t] = s;
+        hv.tol2[t] = tol[t] * tol[t];
+        hv.bscale[t] = active[t] ? bscale[t] : 0.0;
+        hv.out_state[t] = s.state;
+        inactive += active[t] ? 0u : 1u;
+    }
+    hv.bs->ndone = inactive;
+    hv.bs->T = T;
+    hv.bs->maxit = maxit;
+    RBF_CUDA_TRY(cudaMemcpyAsync(ctx->tcg.p, h, L.total, cudaMemcpyHostToDevice, st));
+    return RBF_OK;
+}
+
+template <typename T, typename TB>
+rbf_status bcg_start(rbf_ctx* ctx, const TB* b, bool use_x0, cudaStream_t st) {
+    const Binned bd = view(ctx);
+    const CgVec<T> v = cg_vectors<T>(ctx);
+    if (use_x0) {
+        RBF_CUDA_TRY(cudaMemsetAsync(v.w[1], 0, sizeof(T) * ctx->M, st));
+        launch_spmv(ctx, sizeof(T) == 8 ? RBF_FP64 : RBF_FP32_REFINE, v.x, v.w[1], st);
+    }
+    k_bcg_init<T, TB><<<std::max(1, div_up(ctx->M, 256)), 256, 0, st>>>(bd, v, b, use_x0 ? 1 : 0,
+                                                                       tile_view(ctx));
+    ctx->launches += 1;
+    RBF_CUDA_TRY(cudaGetLastError());
+    return RBF_OK;
+}
+
+Cfg default_cfg(rbf_ctx* ctx, int slot) {
+    Cfg c;
+    c.bps = ctx->force_bps ? ctx->force_bps
+                           : (slot == 0 ? spmv_occupancy<double>() : spmv_occupancy<float>());
+    c.chunk = ctx->force_chunk ? ctx->force_chunk : 4;
+    c.nt = ctx->force_nt ? ctx->force_nt : 256;
+    return c;
+}
+
+// Time `iters` batched iterations in configuration cf from a fresh start (all tiles running,
+// never converging), after two warm-up iterations.
+template <typename T>
+rbf_status time_cfg(rbf_ctx* ctx, const Cfg& cf, int iters, cudaEvent_t e0, cudaEvent_t e1,
+                    double* us, cudaStream_t st) {
+    const int T_ = ctx->T;
+    std::vector<char> act(T_, 1);
+    std::vector<double> one(T_, 1.0), zero(T_, 0.0);
+    rbf_status s = write_tile_state(ctx, act, one, zero, 1 << 30, st);
+    if (s != RBF_OK) return s;
+    if ((s = bcg_start<T, double>(ctx, ctx->bvec.as<double>(), false, st)) != RBF_OK) return s;
+    const CgVec<T> v = cg_vectors<T>(ctx);
+    const TileCg tc = tile_view(ctx);
+    launch_bcg_iteration<T>(ctx, v, tc, cf, 0, st);
+    launch_bcg_iteration<T>(ctx, v, tc, cf, 1, st);
+    RBF_CUDA_TRY(cudaEventRecord(e0, st));
+    for (int k = 0; k < iters; ++k) launch_bcg_iteration<T>(ctx, v, tc, cf, k & 1, st);
+    RBF_CUDA_TRY(cudaEventRecord(e1, st));
+    RBF_CUDA_TRY(cudaEventSynchronize(e1));
+    RBF_CUDA_TRY(cudaGetLastError());
+    float ms = 0.0f;
+    RBF_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+    *us = 1000.0 * ms / iters;
+    ctx->launches += 2 * int64_t(iters + 2);
+    return RBF_OK;
+}
+
+// The autotuner: SpMV blocks per SM x cells per warp step (update block size 256), then the
+// update block size for the best SpMV choice; 8 timed iterations per candidate.
+template <typename T>
+rbf_status autotune_impl(rbf_ctx* ctx, cudaStream_t st) {
+    const int slot = sizeof(T) == 8 ? 0 : 1;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    RBF_CUDA_TRY(cudaEventCreate(&e0));
+    cudaError_t ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_fail(ctx, ce, "cudaEventCreate", __FILE__, __LINE__);
+    }
+    const int occ = spmv_occupancy<T>();
+    const int chunks[] = {1, 2, 4, 8, 16};
+    const int nts[] = {128, 256, 512};
+    Cfg best{occ, 4, 256};
+    double best_us = 1e300;
+    rbf_status s = RBF_OK;
+    for (int bps = 1; bps <= occ && s == RBF_OK; ++bps)
+        for (int ch : chunks) {
+            const Cfg cf{bps, ch, 256};
+            double us = 0.0;
+            if ((s = time_cfg<T>(ctx, cf, 8, e0, e1, &us, st)) != RBF_OK) break;
+            if (us < best_us) {
+                best_us = us;
+                best = cf;
+            }
+        }
+    for (int nt : nts) {
+        if (s != RBF_OK || nt == 256) continue;
+        const Cfg cf{best.bps, best.chunk, nt};
+        double us = 0.0;
+        if ((s = time_cfg<T>(ctx, cf, 8, e0, e1, &us, st)) != RBF_OK) break;
+        if (us < best_us) {
+            best_us = us;
+            best = cf;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != RBF_OK) return s;
+    rbf_ctx::TileTuning& tu = ctx->tune[slot];
+    tu.spmv_bps = best.bps;
+    tu.chunk = best.chunk;
+    tu.nt = best.nt;
+    tu.us_per_iter = best_us;
+    tu.ncl = ctx->ncl;
+    tu.M = ctx->M;
+    tu.nvals = ctx->nvals;
+    return RBF_OK;
+}
+
+// Configuration for this system: forced values, else the tuned one for this shape (tuning
+// now when enabled), else the default.
+template <typename T>
+rbf_status pick_cfg(rbf_ctx* ctx, Cfg* out, cudaStream_t st) {
+    const int slot = sizeof(T) == 8 ? 0 : 1;
+    const rbf_ctx::TileTuning& tu = ctx->tune[slot];
+    const bool fresh = tu.nt != 0 && tu.ncl == ctx->ncl && tu.M == ctx->M && tu.nvals == ctx->nvals;
+    if (!fresh && ctx->autotune && !(ctx->force_bps || ctx->force_chunk || ctx->force_nt)) {
+        rbf_status s = autotune_impl<T>(ctx, st);
+        if (s != RBF_OK) return s;
+    }
+    Cfg c = default_cfg(ctx, slot);
+    if (ctx->tune[slot].nt != 0 && ctx->tune[slot].ncl == ctx->ncl && ctx->tune[slot].M == ctx->M &&
+        ctx->tune[slot].nvals == ctx->nvals) {
+        if (!ctx->force_bps) c.bps = ctx->tune[slot].spmv_bps;
+        if (!ctx->force_chunk) c.chunk = ctx->tune[slot].chunk;
+        if (!ctx->force_nt) c.nt = ctx->tune[slot].nt;
+    }
+    *out = c;
+    return RBF_OK;
+}
+
+// The batched solve graph: a conditional WHILE node whose body runs kItersPerBody
+// iterations and then continues while some tile is still running.
+template <typename T>
+rbf_status bcg_graph(rbf_ctx* ctx, const Cfg& cf, cudaGraphExec_t* out) {
+    rbf_ctx::TileGraph& sg = ctx->bt_graph[sizeof(T) == 8 ? 0 : 1];
+    const CgVec<T> v = cg_vectors<T>(ctx);
+    const void* key[12] = {ctx->bvals.p, v.x, v.dinv, v.bjinv, ctx->tcg.p, ctx->clist.p,
+                           ctx->cdesc.p, ctx->crow.p, ctx->bjoff.p, ctx->cstart.p,
+                           ctx->seg.p, ctx->rboff.p};
+    bool hit = sg.exec && sg.T == ctx->T && sg.M == ctx->M && sg.ncl == ctx->ncl &&
+               sg.bps == cf.bps && sg.chunk == cf.chunk && sg.nt == cf.nt;
+    for (int k = 0; k < 12 && hit; ++k) hit = sg.key[k] == key[k];
+    if (hit) {
+        *out = sg.exec;
+        return RBF_OK;
+    }
+    if (sg.exec) {
+        cudaGraphExecDestroy(sg.exec);
+        sg.exec = nullptr;
+    }
+    if (!ctx->capture_stream)
+        RBF_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    RBF_CUDA_TRY(cudaGraphCreate(&graph, 0));
+    cudaGraphConditionalHandle handle;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = handle;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp);
+    cudaGraph_t body = e == cudaSuccess ? cp.conditional.phGraph_out[0] : nullptr;
+    cudaStream_t cs = ctx->capture_stream;
+    if (e == cudaSuccess)
+        e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        const TileCg tc = tile_view(ctx);
+        for (int k = 0; k < kItersPerBody; ++k) launch_bcg_iteration<T>(ctx, v, tc, cf, k & 1, cs);
+        k_bcg_cond<<<1, 1, 0, cs>>>(tc.bs, handle);
+        cudaGraph_t captured = nullptr;
+        e = cudaStreamEndCapture(cs, &captured);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&sg.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        sg.exec = nullptr;
+        return cuda_fail(ctx, e, "building the batched CG solve graph", __FILE__, __LINE__);
+    }
+    sg.T = ctx->T;
+    sg.M = ctx->M;
+    sg.ncl = ctx->ncl;
+    sg.bps = cf.bps;
+    sg.chunk = cf.chunk;
+    sg.nt = cf.nt;
+    for (int k = 0; k < 12; ++k) sg.key[k] = key[k];
+    *out = sg.exec;
+    return RBF_OK;
+}
+
+// Results of one batched CG run, per tile.
+struct BcgOut {
+    std::vector<int> it, state;
+    std::vector<double> rel;
+};
+
+// Batched CG on B (precision T) for B x_t = bscale_t b_t on the active tiles.
+template <typename T, typename TB>
+rbf_status run_bcg(rbf_ctx* ctx, const TB* b, bool use_x0, const std::vector<char>& active,
+                   const std::vector<double>& bscale, const std::vector<double>& tol, int maxit,
+                   BcgOut* out, cudaStream_t st) {
+    rbf_status s;
+    Cfg cf;
+    if ((s = pick_cfg<T>(ctx, &cf, st)) != RBF_OK) return s;
+    cudaGraphExec_t ex;
+    if ((s = bcg_graph<T>(ctx, cf, &ex)) != RBF_OK) return s;
+    if ((s = write_tile_state(ctx, active, bscale, tol, maxit, st)) != RBF_OK) return s;
+    if ((s = bcg_start<T, TB>(ctx, b, use_x0, st)) != RBF_OK) return s;
+    RBF_CUDA_TRY(cudaGraphLaunch(ex, st));
+    const TileLayout L(ctx->T);
+    char* h = static_cast<char*>(ctx->hbt);
+    RBF_CUDA_TRY(cudaMemcpyAsync(h, ctx->tcg.p, L.total, cudaMemcpyDeviceToHost, st));
+    RBF_CUDA_TRY(cudaStreamSynchronize(st));
+    const TileCg hv = L.view(h);
+    const int T_ = ctx->T;
+    out->it.assign(T_, 0);
+    out->state.assign(T_, kInactive);
+    out->rel.assign(T_, 0.0);
+    int max_it = 0;
+    for (int t = 0; t < T_; ++t) {
+        if (!active[t]) continue;
+        out->it[t] = hv.out_it[t];
+        out->state[t] = hv.out_state[t];
+        out->rel[t] = hv.bb[t] > 0.0 ? sqrt(hv.out_rr[t] / hv.bb[t]) : 0.0;
+        max_it = std::max(max_it, hv.out_it[t]);
+    }
+    ctx->launches += int64_t(max_it / kItersPerBody + 1) * (2 * kItersPerBody + 1);
+    return RBF_OK;
+}
+
+// Per-tile ||v||^2 over unpinned rows (mask = FP32 or FP64 dinv) into host vector n2, and,
+// when npin is not null, per-tile pinned counts.
+template <typename TM>
+rbf_status tile_norms(rbf_ctx* ctx, const double* v, const TM* mask, std::vector<double>* n2,
+                      std::vector<int64_t>* npin, cudaStream_t st) {
+    const int T = ctx->T;
+    const RedLayout R(T);
+    char* d = ctx->tred.as<char>();
+    RBF_CUDA_TRY(cudaMemsetAsync(d, 0, R.scale, st));
+    k_tile_norm2<TM><<<std::max(1, div_up(ctx->M, 256)), 256, 0, st>>>(
+        view(ctx), v, mask, reinterpret_cast<double*>(d + R.n0), reinterpret_cast<double*>(d + R.pin));
+    ctx->launches += 1;
+    char* h = static_cast<char*>(ctx->hbt);
+    RBF_CUDA_TRY(cudaMemcpyAsync(h, d, R.scale, cudaMemcpyDeviceToHost, st));
+    RBF_CUDA_TRY(cudaStreamSynchronize(st));
+    const double* hn = reinterpret_cast<const double*>(h + R.n0);
+    const double* hp = reinterpret_cast<const double*>(h + R.pin);
+    if (n2) n2->assign(hn, hn + T);
+    if (npin) {
+        npin->resize(T);
+        for (int t = 0; t < T; ++t) (*npin)[t] = int64_t(llround(hp[t]));
+    }
+    return RBF_OK;
+}
+
+rbf_status status_of(int state) {
+    if (state == kConverged) return RBF_OK;
+    if (state == kBreakdown) return RBF_ERR_BREAKDOWN;
+    return RBF_ERR_NOT_CONVERGED;
+}
+
+}  // namespace
+
+// ---- binning hooks called by bin_run ----
+
+rbf_status tiles_count(rbf_ctx* ctx, const double* cx, const double* cy, const double* px,
+                       const double* py, const double* h, cudaStream_t st) {
+    const dim3 grid(8, ctx->T);
+    const TileDev* td = ctx->tdesc.as<TileDev>();
+    int* stats = ctx->stats.as<int>();
+    k_tile_count<<<grid, 256, 0, st>>>(td, 0, cx, cy, nullptr, ctx->g, ctx->ccount.as<int>(),
+                                       ctx->ckey.as<int>(), ctx->crank.as<int>(), stats);
+    k_tile_count<<<grid, 256, 0, st>>>(td, 1, px, py, h, ctx->g, ctx->pcount.as<int>(),
+                                       ctx->pkey.as<int>(), ctx->prank.as<int>(), stats);
+    RBF_CUDA_TRY(cudaGetLastError());
+    return RBF_OK;
+}
+
+rbf_status tiles_scatter(rbf_ctx* ctx, const double* cx, const double* cy, const double* px,
+                         const double* py, const double* h, cudaStream_t st) {
+    const dim3 grid(8, ctx->T);
+    const TileDev* td = ctx->tdesc.as<TileDev>();
+    k_tile_scatter<<<grid, 256, 0, st>>>(td, 0, cx, cy, nullptr, ctx->g, ctx->ckey.as<int>(),
+                                         ctx->crank.as<int>(), ctx->cstart.as<int>(),
+                                         ctx->cx.as<double>(), ctx->cy.as<double>(), nullptr,
+                                         ctx->cu.as<float>(), ctx->cv.as<float>(),
+                                         ctx->cperm.as<int>());
+    k_tile_scatter<<<grid, 256, 0, st>>>(td, 1, px, py, h, ctx->g, ctx->pkey.as<int>(),
+                                         ctx->prank.as<int>(), ctx->pstart.as<int>(),
+                                         ctx->px.as<double>(), ctx->py.as<double>(),
+                                         ctx->ph.as<double>(), ctx->pu.as<float>(),
+                                         ctx->pv.as<float>(), nullptr);
+    RBF_CUDA_TRY(cudaGetLastError());
+    return RBF_OK;
+}
+
+// List of the cells that hold at least one centre (the batched SpMV's work list); reads the
+// count back (the caller synchronises later).
+rbf_status tiles_cell_list(rbf_ctx* ctx, cudaStream_t st) {
+    const int nc = ctx->g.ncell;
+    rbf_status s;
+    // the centre counts and the row-block sizes are no longer needed: reuse them for the
+    // flags and their scan
+    int* flag = ctx->ccount.as<int>();
+    if ((s = ensure(ctx, ctx->clist, sizeof(int) * (nc + 1), st)) != RBF_OK) return s;
+    if ((s = ensure(ctx, ctx->rbsize, sizeof(int64_t) * (nc + 1), st)) != RBF_OK) return s;
+    int* pos = ctx->rbsize.as<int>();
+    k_cell_flags<<<div_up(nc, 256), 256, 0, st>>>(nc, ctx->cstart.as<int>(), flag);
+    if ((s = scan_i32(ctx, flag, pos, nc, st)) != RBF_OK) return s;
+    k_cell_compact<<<div_up(nc, 256), 256, 0, st>>>(nc, ctx->cstart.as<int>(), pos,
+                                                    ctx->clist.as<int>());
+    ctx->launches += 2;
+    int* hp = static_cast<int*>(ctx->hpinned) + 64;
+    RBF_CUDA_TRY(cudaMemcpyAsync(hp, pos + nc, sizeof(int), cudaMemcpyDeviceToHost, st));
+    RBF_CUDA_TRY(cudaStreamSynchronize(st));
+    ctx->ncl = *hp;
+    RBF_CUDA_TRY(cudaGetLastError());
+    return RBF_OK;
+}
+
+void tiles_release(rbf_ctx* ctx) {
+    for (auto& sg : ctx->bt_graph)
+        if (sg.exec) {
+            cudaGraphExecDestroy(sg.exec);
+            sg.exec = nullptr;
+        }
+    rbf_buf* bufs[] = {&ctx->tdesc, &ctx->rowtile, &ctx->clist, &ctx->tcg, &ctx->tred};
+    for (rbf_buf* b : bufs) release(ctx, *b);
+    if (ctx->hbt) cudaFreeHost(ctx->hbt);
+    ctx->hbt = nullptr;
+    ctx->hbt_bytes = 0;
+}
+
+// Packing of the tiles (host) and the binning of the packed system.
+rbf_status bin_tiles_run(rbf_ctx* ctx, const rbf_tile* tiles, int T, const double* cx,
+                         const double* cy, int64_t Mtot, const double* px, const double* py,
+                         const double* h, int64_t Ntot, cudaStream_t st) {
+    // ranges must partition [0, Mtot) and [0, Ntot)
+    std::vector<std::pair<int64_t, int64_t>> cr, pr;
+    for (int t = 0; t < T; ++t) {
+        const rbf_tile& q = tiles[t];
+        if (q.M < 1 || q.N < 0 || q.c0 < 0 || q.p0 < 0 || q.c0 + q.M > Mtot || q.p0 + q.N > Ntot)
+            return set_err(ctx, RBF_ERR_ARG, "tile range outside the concatenated arrays");
+        if (!(q.R > 0.0) || !isfinite(q.R)) return set_err(ctx, RBF_ERR_ARG, "tile R must be finite and > 0");
+        for (int k = 0; k < 4; ++k)
+            if (!isfinite(q.bbox[k])) return set_err(ctx, RBF_ERR_ARG, "non-finite tile bbox");
+        if (!(q.bbox[2] >= q.bbox[0]) || !(q.bbox[3] >= q.bbox[1]))
+            return set_err(ctx, RBF_ERR_ARG, "tile bbox must be {x0, y0, x1, y1} with x1 >= x0, y1 >= y0");
+        cr.push_back({q.c0, q.M});
+        if (q.N > 0) pr.push_back({q.p0, q.N});
+    }
+    auto partitions = [](std::vector<std::pair<int64_t, int64_t>>& r, int64_t total) {
+        std::sort(r.begin(), r.end());
+        int64_t at = 0;
+        for (auto& x : r) {
+            if (x.first != at) return false;
+            at += x.second;
+        }
+        return at == total;
+    };
+    if (!partitions(cr, Mtot)) return set_err(ctx, RBF_ERR_ARG, "tile centre ranges must partition [0, Mtot)");
+    if (!partitions(pr, Ntot)) return set_err(ctx, RBF_ERR_ARG, "tile point ranges must partition [0, Ntot)");
+
+    // bands of cell rows, two empty rows apart
+    const double hcell = kCellMargin, invh = 1.0 / kCellMargin;
+    std::vector<TileDev> td(T);
+    int64_t W = 1, GY = 0;
+    for (int t = 0; t < T; ++t) {
+        const rbf_tile& q = tiles[t];
+        const double nx = std::max(1.0, ceil((q.bbox[2] - q.bbox[0]) / q.R * invh));
+        const double ny = std::max(1.0, ceil((q.bbox[3] - q.bbox[1]) / q.R * invh));
+        if (nx * ny > double(1 << 24))
+            return set_err(ctx, RBF_ERR_LIMIT, "tile cell grid larger than 2^24 cells");
+        TileDev d;
+        d.c0 = q.c0;
+        d.m = q.M;
+        d.p0 = q.p0;
+        d.n = q.N;
+        d.x0 = q.bbox[0];
+        d.y0 = q.bbox[1];
+        d.R = q.R;
+        d.gx = int(nx);
+        d.gy = int(ny);
+        d.oy = int(GY);
+        d.pad = 0;
+        td[t] = d;
+        W = std::max<int64_t>(W, d.gx);
+        GY += d.gy + (t + 1 < T ? 2 : 0);
+        if (GY > (int64_t(1) << 24)) break;
+    }
+    if (double(W) * double(GY) > double(1 << 24))
+        return set_err(ctx, RBF_ERR_LIMIT, "packed cell grid of the tiles larger than 2^24 cells");
+    Grid g;
+    g.x0 = 0.0;
+    g.y0 = 0.0;
+    g.R = 1.0;
+    g.invR = 1.0;
+    g.R2 = 1.0;
+    g.h = hcell;
+    g.invh = invh;
+    g.gx = int(W);
+    g.gy = int(GY);
+    g.ncell = g.gx * g.gy;
+    std::vector<int> rowtile(GY, -1);
+    for (int t = 0; t < T; ++t)
+        for (int r = 0; r < td[t].gy; ++r) rowtile[td[t].oy + r] = t;
+
+    tiles_release(ctx);
+    ctx->T = T;
+    ctx->tiles.assign(tiles, tiles + T);
+    ctx->g = g;
+    ctx->M = int(Mtot);
+    ctx->N = int(Ntot);
+    rbf_status s;
+    if ((s = ensure(ctx, ctx->tdesc, sizeof(TileDev) * T, st)) != RBF_OK) return s;
+    if ((s = ensure(ctx, ctx->rowtile, sizeof(int) * GY, st)) != RBF_OK) return s;
+    if ((s = ensure(ctx, ctx->tcg, TileLayout(T).total, st)) != RBF_OK) return s;
+    if ((s = ensure(ctx, ctx->tred, RedLayout(T).total, st)) != RBF_OK) return s;
+    const size_t hb = std::max(TileLayout(T).total, RedLayout(T).total);
+    if (cudaMallocHost(&ctx->hbt, hb) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->hbt = nullptr;
+        return set_err(ctx, RBF_ERR_ALLOC, "pinned host buffer for the tile scalars");
+    }
+    ctx->hbt_bytes = hb;
+    RBF_CUDA_TRY(cudaMemcpyAsync(ctx->tdesc.p, td.data(), sizeof(TileDev) * T,
+                                 cudaMemcpyHostToDevice, st));
+    RBF_CUDA_TRY(cudaMemcpyAsync(ctx->rowtile.p, rowtile.data(), sizeof(int) * GY,
+                                 cudaMemcpyHostToDevice, st));
+    // the host vectors are pageable: the copies above complete before returning
+    return bin_run(ctx, cx, cy, px, py, h, st);
+}
+
+rbf_status solve_tiles_run(rbf_ctx* ctx, double* c, int use_c0, double tol, int maxit,
+                           int min_support, rbf_tile_info* tinfo, rbf_solve_info* info,
+                           cudaStream_t st) {
+    const int M = ctx->M, T = ctx->T;
+    const Binned bd = view(ctx);
+    rbf_status s;
+#define ENS(buf, bytes) \
+    if ((s = ensure(ctx, ctx->buf, (bytes), st)) != RBF_OK) return s;
+    ENS(x, sizeof(double) * M);
+    ENS(r, sizeof(double) * M);
+    ENS(scal, 256);
+    int* npin_d = ctx->scal.as<int>();
+    RBF_CUDA_TRY(cudaMemsetAsync(npin_d, 0, sizeof(int), st));
+    std::vector<int> iters(T, 0), refs(T, 0), state(T, kConverged);
+    std::vector<double> rel(T, 0.0);
+    std::vector<int64_t> npin(T, 0);
+    int promoted = 0;
+    const int nb = div_up(M, 256);
+
+    auto fp64_solve = [&](const std::vector<char>& active, bool x_ready) -> rbf_status {
+        // FP64 batched CG; x_ready: the FP64 CG's x already holds the start vector
+        ENS(cgv[0], sizeof(double) * kCgVecs * size_t(M));
+        const CgVec<double> v = cg_vectors<double>(ctx);
+        bool use_x0 = x_ready;
+        if (!x_ready && use_c0) {
+            k_tile_to_sorted<double><<<nb, 256, 0, st>>>(c, bd.cperm, v.dinv, v.x, M);
+            ctx->launches += 1;
+            use_x0 = true;
+        }
+        std::vector<double> one(T, 1.0), tl(T, tol);
+        BcgOut o;
+        rbf_status s2 = run_bcg<double, double>(ctx, ctx->bvec.as<double>(), use_x0, active, one,
+                                                tl, maxit, &o, st);
+        if (s2 != RBF_OK) return s2;
+        for (int t = 0; t < T; ++t) {
+            if (!active[t]) continue;
+            iters[t] += o.it[t];
+            state[t] = o.state[t];
+            rel[t] = o.rel[t];
+        }
+        k_tile_from_sorted<double><<<nb, 256, 0, st>>>(v.x, bd.cperm, c, M);
+        ctx->launches += 1;
+        RBF_CUDA_TRY(cudaGetLastError());
+        return RBF_OK;
+    };
+
+    if (ctx->prec == RBF_FP64) {
+        ENS(dinv, sizeof(double) * M);
+        ENS(bjinv, sizeof(double) * std::max<int64_t>(ctx->nbj, 1));
+        if ((s = prec_setup_run(ctx, RBF_FP64, min_support, npin_d, st)) != RBF_OK) return s;
+        if ((s = tile_norms<double>(ctx, nullptr, ctx->dinv.as<double>(), nullptr, &npin, st)) != RBF_OK)
+            return s;
+        std::vector<char> all(T, 1);
+        if ((s = fp64_solve(all, false)) != RBF_OK) return s;
+    } else {
+        ENS(cgv[1], sizeof(float) * kCgVecs * size_t(M));
+        ENS(dinv32, sizeof(float) * M);
+        ENS(bjinv32, sizeof(float) * std::max<int64_t>(ctx->nbj, 1));
+        if ((s = prec_setup_run(ctx, RBF_FP32_REFINE, min_support, npin_d, st)) != RBF_OK) return s;
+        const float* dinv32 = ctx->dinv32.as<float>();
+        const CgVec<float> v = cg_vectors<float>(ctx);
+        double* x64 = ctx->x.as<double>();
+        double* r64 = ctx->r.as<double>();
+        std::vector<double> bn2, rn2;
+        if ((s = tile_norms<float>(ctx, ctx->bvec.as<double>(), dinv32, &bn2, &npin, st)) != RBF_OK)
+            return s;
+        if (use_c0) {
+            launch_gather_sorted(c, bd.cperm, x64, M, st);
+            k_zero_masked<<<nb, 256, 0, st>>>(M, x64, dinv32);
+            ctx->launches += 2;
+            RBF_CUDA_TRY(cudaMemsetAsync(r64, 0, sizeof(double) * M, st));
+            if ((s = residual_run(ctx, x64, r64, false, st)) != RBF_OK) return s;
+            k_zero_masked<<<nb, 256, 0, st>>>(M, r64, dinv32);
+            ctx->launches += 1;
+        } else {
+            RBF_CUDA_TRY(cudaMemsetAsync(x64, 0, sizeof(double) * M, st));
+            RBF_CUDA_TRY(cudaMemcpyAsync(r64, ctx->bvec.p, sizeof(double) * M,
+                                         cudaMemcpyDeviceToDevice, st));
+            k_zero_masked<<<nb, 256, 0, st>>>(M, r64, dinv32);
+            ctx->launches += 1;
+        }
+        if ((s = tile_norms<float>(ctx, r64, dinv32, &rn2, nullptr, st)) != RBF_OK) return s;
+        std::vector<double> bn(T), rn(T);
+        for (int t = 0; t < T; ++t) {
+            bn[t] = sqrt(bn2[t]);
+            rn[t] = sqrt(rn2[t]);
+        }
+        std::vector<char> conv(T, 0), active(T, 0);
+        bool stalled = false;
+        double* dscale = reinterpret_cast<double*>(ctx->tred.as<char>() + RedLayout(T).scale);
+        std::vector<double> hscale(T);
+        for (int outer = 0;; ++outer) {
+            int nact = 0;
+            for (int t = 0; t < T; ++t) {
+                const double rl = bn[t] > 0.0 ? rn[t] / bn[t] : 0.0;
+                rel[t] = rl;
+                if (!conv[t] && (rl <= tol || rn[t] == 0.0)) conv[t] = 1;
+                active[t] = !conv[t];
+                nact += active[t];
+            }
+            if (nact == 0 || outer == ctx->max_refine) break;
+            std::vector<double> bsc(T, 0.0), itol(T, 1.0);
+            for (int t = 0; t < T; ++t) {
+                if (!active[t]) continue;
+                bsc[t] = 1.0 / rn[t];
+                itol[t] = std::max(ctx->inner_tol, 0.5 * tol / rel[t]);
+            }
+            BcgOut o;
+            if ((s = run_bcg<float, double>(ctx, r64, false, active, bsc, itol, maxit, &o, st)) != RBF_OK)
+                return s;
+            for (int t = 0; t < T; ++t) {
+                hscale[t] = active[t] ? rn[t] : 0.0;
+                if (!active[t]) continue;
+                iters[t] += o.it[t];
+                refs[t] += 1;
+                // an inner breakdown before any step (FP32 rounding can make B32 indefinite on
+                // a very ill-conditioned tile) leaves nothing to apply: hand over to FP64
+                if (o.state[t] == kBreakdown && o.it[t] == 0) stalled = true;
+            }
+            RBF_CUDA_TRY(cudaMemcpyAsync(dscale, hscale.data(), sizeof(double) * T,
+                                         cudaMemcpyHostToDevice, st));
+            k_tile_axpy<<<nb, 256, 0, st>>>(bd, x64, v.x, dscale, dinv32);
+            RBF_CUDA_TRY(cudaMemsetAsync(r64, 0, sizeof(double) * M, st));
+            if ((s = residual_run(ctx, x64, r64, false, st)) != RBF_OK) return s;
+            k_zero_masked<<<nb, 256, 0, st>>>(M, r64, dinv32);
+            ctx->launches += 2;
+            if ((s = tile_norms<float>(ctx, r64, dinv32, &rn2, nullptr, st)) != RBF_OK) return s;
+            for (int t = 0; t < T; ++t) {
+                if (!active[t]) continue;   // converged tiles keep their iterate and residual
+                const double rnew = sqrt(rn2[t]);
+                if (!(rnew < 0.5 * rn[t])) {
+                    stalled = true;
+                    rn[t] = std::min(rn[t], rnew);
+                } else {
+                    rn[t] = rnew;
+                }
+            }
+            if (stalled) break;
+        }
+        for (int t = 0; t < T; ++t) {
+            rel[t] = bn[t] > 0.0 ? rn[t] / bn[t] : 0.0;
+            if (!conv[t] && (rel[t] <= tol || rn[t] == 0.0)) conv[t] = 1;
+            state[t] = conv[t] ? kConverged : kMaxIt;
+        }
+        bool all = true;
+        for (int t = 0; t < T; ++t) all = all && conv[t];
+        if (all) {
+            launch_scatter_orig(x64, bd.cperm, c, M, st);
+            ctx->launches += 1;
+        } else {
+            // Promote: assemble B in FP64 and finish the unconverged tiles with FP64 CG
+            // started from their refined iterates; converged tiles keep theirs.
+            if ((s = assemble_run(ctx, ctx->kernel, RBF_FP64, st)) != RBF_OK) return s;
+            ctx->prec = RBF_FP64;
+            promoted = 1;
+            ENS(dinv, sizeof(double) * M);
+            ENS(bjinv, sizeof(double) * std::max<int64_t>(ctx->nbj, 1));
+            RBF_CUDA_TRY(cudaMemsetAsync(npin_d, 0, sizeof(int), st));
+            if ((s = prec_setup_run(ctx, RBF_FP64, min_support, npin_d, st)) != RBF_OK) return s;
+            ENS(cgv[0], sizeof(double) * kCgVecs * size_t(M));
+            const CgVec<double> v64 = cg_vectors<double>(ctx);
+            k_copy_masked<<<nb, 256, 0, st>>>(M, x64, v64.dinv, v64.x);
+            ctx->launches += 1;
+            std::vector<char> todo(T);
+            for (int t = 0; t < T; ++t) todo[t] = !conv[t];
+            if ((s = fp64_solve(todo, true)) != RBF_OK) return s;
+        }
+    }
+    RBF_CUDA_TRY(cudaGetLastError());
+    ctx->solved = true;
+    rbf_solve_info tot{};
+    rbf_status worst = RBF_OK;
+    for (int t = 0; t < T; ++t) {
+        const rbf_status ts = status_of(state[t]);
+        if (ts == RBF_ERR_BREAKDOWN) worst = RBF_ERR_BREAKDOWN;
+        else if (ts != RBF_OK && worst == RBF_OK) worst = ts;
+        tot.iterations = std::max(tot.iterations, iters[t]);
+        tot.refinements = std::max(tot.refinements, refs[t]);
+        tot.rel_residual = std::max(tot.rel_residual, rel[t]);
+        tot.pinned += npin[t];
+        if (tinfo) {
+            tinfo[t].iterations = iters[t];
+            tinfo[t].refinements = refs[t];
+            tinfo[t].rel_residual = rel[t];
+            tinfo[t].pinned = npin[t];
+            tinfo[t].status = ts;
+        }
+    }
+    tot.promoted = promoted;
+    if (info) *info = tot;
+#undef ENS
+    if (worst == RBF_ERR_BREAKDOWN) return set_err(ctx, worst, "CG breakdown in some tile");
+    if (worst != RBF_OK) return set_err(ctx, worst, "some tile did not reach tol");
+    return RBF_OK;
+}
+
+rbf_status autotune_run(rbf_ctx* ctx, cudaStream_t st) {
+    const int M = ctx->M;
+    rbf_status s;
+    if ((s = ensure(ctx, ctx->scal, 256, st)) != RBF_OK) return s;
+    int* npin_d = ctx->scal.as<int>();
+    if (ctx->prec == RBF_FP64) {
+        if ((s = ensure(ctx, ctx->cgv[0], sizeof(double) * kCgVecs * size_t(M), st)) != RBF_OK) return s;
+        if ((s = ensure(ctx, ctx->dinv, sizeof(double) * M, st)) != RBF_OK) return s;
+        if ((s = ensure(ctx, ctx->bjinv, sizeof(double) * std::max<int64_t>(ctx->nbj, 1), st)) != RBF_OK)
+            return s;
+        if ((s = prec_setup_run(ctx, RBF_FP64, 3, npin_d, st)) != RBF_OK) return s;
+        return autotune_impl<double>(ctx, st);
+    }
+    if ((s = ensure(ctx, ctx->cgv[1], sizeof(float) * kCgVecs * size_t(M), st)) != RBF_OK) return s;
+    if ((s = ensure(ctx, ctx->dinv32, sizeof(float) * M, st)) != RBF_OK) return s;
+    if ((s = ensure(ctx, ctx->bjinv32, sizeof(float) * std::max<int64_t>(ctx->nbj, 1), st)) != RBF_OK)
+        return s;
+    if ((s = prec_setup_run(ctx, RBF_FP32_REFINE, 3, npin_d, st)) != RBF_OK) return s;
+    return autotune_impl<float>(ctx, st);
+}
+
+}  // namespace rbf

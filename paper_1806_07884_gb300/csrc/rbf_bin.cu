@@ -192,9 +192,9 @@ __device__ __forceinline__ void cell_row_range(const Grid& g, const int* cstart,
 }
 
 __global__ void k_rows(Grid g, const int* __restrict__ cstart, const int* __restrict__ pstart,
-                       RowSeg* __restrict__ seg, int64_t* __restrict__ rbsize,
-                       int64_t* __restrict__ bjsize, int* __restrict__ wcount,
-                       int4* __restrict__ crow, int* __restrict__ stats) {
+                       const int* __restrict__ rowtile, RowSeg* __restrict__ seg,
+                       int64_t* __restrict__ rbsize, int64_t* __restrict__ bjsize,
+                       int* __restrict__ wcount, int4* __restrict__ crow, int* __restrict__ stats) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= g.ncell) return;
     const int ix = c % g.gx, iy = c / g.gx;
@@ -207,7 +207,8 @@ __global__ void k_rows(Grid g, const int* __restrict__ cstart, const int* __rest
     const int cs = cstart[c];
     const int m = cstart[c + 1] - cs;
     rbsize[c] = int64_t(m) * int64_t(sg.lp);
-    for (int i = 0; i < m; ++i) crow[cs + i] = make_int4(cs, m, c, 0);
+    const int tile = rowtile ? rowtile[iy] : 0;
+    for (int i = 0; i < m; ++i) crow[cs + i] = make_int4(cs, m, c, tile);
     bjsize[c] = m <= kMaxBlock ? int64_t(m) * m : 0;
     const int np = pstart[c + 1] - pstart[c];
     wcount[c] = (np + kWorkPoints - 1) / kWorkPoints;
@@ -232,8 +233,9 @@ __global__ void k_work_fill(int ncell, const int* __restrict__ pstart,
     for (int q = p0; q < p1; q += kWorkPoints, ++w) work[w] = make_int4(c, q, min(q + kWorkPoints, p1), 0);
 }
 
-__global__ void k_cell_desc(int ncell, const int* __restrict__ cstart, const RowSeg* __restrict__ seg,
-                            const int64_t* __restrict__ rboff, CellDesc* __restrict__ out) {
+__global__ void k_cell_desc(int ncell, int gx, const int* __restrict__ cstart,
+                            const RowSeg* __restrict__ seg, const int64_t* __restrict__ rboff,
+                            const int* __restrict__ rowtile, CellDesc* __restrict__ out) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncell) return;
     const RowSeg sg = seg[c];
@@ -241,7 +243,7 @@ __global__ void k_cell_desc(int ncell, const int* __restrict__ cstart, const Row
     d.cs = cstart[c];
     d.m = cstart[c + 1] - d.cs;
     d.lp = sg.lp;
-    d.pad = 0;
+    d.pad = rowtile ? rowtile[c / gx] : 0;   // tile of the cell (batched systems)
     d.rboff = rboff[c];
     d.s0 = sg.s0;
     d.l0 = sg.l0;
@@ -255,10 +257,10 @@ __global__ void k_cell_desc(int ncell, const int* __restrict__ cstart, const Row
 }  // namespace
 
 void launch_cell_desc(rbf_ctx* ctx, cudaStream_t st) {
-    k_cell_desc<<<div_up(ctx->g.ncell, 256), 256, 0, st>>>(ctx->g.ncell, ctx->cstart.as<int>(),
-                                                           ctx->seg.as<RowSeg>(),
-                                                           ctx->rboff.as<int64_t>(),
-                                                           ctx->cdesc.as<CellDesc>());
+    k_cell_desc<<<div_up(ctx->g.ncell, 256), 256, 0, st>>>(
+        ctx->g.ncell, ctx->g.gx, ctx->cstart.as<int>(), ctx->seg.as<RowSeg>(),
+        ctx->rboff.as<int64_t>(), ctx->T > 0 ? ctx->rowtile.as<int>() : nullptr,
+        ctx->cdesc.as<CellDesc>());
     ctx->launches += 1;
 }
 
@@ -311,22 +313,33 @@ rbf_status bin_run(rbf_ctx* ctx, const double* cx, const double* cy, const doubl
 
     const int T = 256;
     const int gbM = std::min(div_up(M, T), 152 * 16), gbN = std::min(div_up(N, T), 152 * 16);
-    k_bin_count<<<gbM, T, 0, st>>>(cx, cy, nullptr, M, g, ctx->ccount.as<int>(), ctx->ckey.as<int>(),
-                                   ctx->crank.as<int>(), stats);
-    k_bin_count<<<gbN, T, 0, st>>>(px, py, h, N, g, ctx->pcount.as<int>(), ctx->pkey.as<int>(),
-                                   ctx->prank.as<int>(), stats);
+    if (ctx->T > 0) {
+        if ((s = tiles_count(ctx, cx, cy, px, py, h, st)) != RBF_OK) return s;
+    } else {
+        k_bin_count<<<gbM, T, 0, st>>>(cx, cy, nullptr, M, g, ctx->ccount.as<int>(),
+                                       ctx->ckey.as<int>(), ctx->crank.as<int>(), stats);
+        k_bin_count<<<gbN, T, 0, st>>>(px, py, h, N, g, ctx->pcount.as<int>(), ctx->pkey.as<int>(),
+                                       ctx->prank.as<int>(), stats);
+    }
     RBF_CUDA_TRY(cudaGetLastError());
     if ((s = scan_i32(ctx, ctx->ccount.as<int>(), ctx->cstart.as<int>(), nc, st)) != RBF_OK) return s;
     if ((s = scan_i32(ctx, ctx->pcount.as<int>(), ctx->pstart.as<int>(), nc, st)) != RBF_OK) return s;
-    k_scatter_centres<<<gbM, T, 0, st>>>(cx, cy, M, g, ctx->ckey.as<int>(), ctx->crank.as<int>(),
-                                         ctx->cstart.as<int>(), ctx->cx.as<double>(),
-                                         ctx->cy.as<double>(), ctx->cu.as<float>(),
-                                         ctx->cv.as<float>(), ctx->cperm.as<int>());
-    k_scatter_points<<<gbN, T, 0, st>>>(px, py, h, N, g, ctx->pkey.as<int>(), ctx->prank.as<int>(),
-                                        ctx->pstart.as<int>(), ctx->px.as<double>(),
-                                        ctx->py.as<double>(), ctx->ph.as<double>(),
-                                        ctx->pu.as<float>(), ctx->pv.as<float>());
+    if (ctx->T > 0) {
+        if ((s = tiles_scatter(ctx, cx, cy, px, py, h, st)) != RBF_OK) return s;
+    } else {
+        k_scatter_centres<<<gbM, T, 0, st>>>(cx, cy, M, g, ctx->ckey.as<int>(),
+                                             ctx->crank.as<int>(), ctx->cstart.as<int>(),
+                                             ctx->cx.as<double>(), ctx->cy.as<double>(),
+                                             ctx->cu.as<float>(), ctx->cv.as<float>(),
+                                             ctx->cperm.as<int>());
+        k_scatter_points<<<gbN, T, 0, st>>>(px, py, h, N, g, ctx->pkey.as<int>(),
+                                            ctx->prank.as<int>(), ctx->pstart.as<int>(),
+                                            ctx->px.as<double>(), ctx->py.as<double>(),
+                                            ctx->ph.as<double>(), ctx->pu.as<float>(),
+                                            ctx->pv.as<float>());
+    }
     k_rows<<<div_up(nc, T), T, 0, st>>>(g, ctx->cstart.as<int>(), ctx->pstart.as<int>(),
+                                        ctx->T > 0 ? ctx->rowtile.as<int>() : nullptr,
                                         ctx->seg.as<RowSeg>(), ctx->rbsize.as<int64_t>(),
                                         ctx->bjsize.as<int64_t>(), ctx->wcount.as<int>(),
                                         ctx->crow.as<int4>(), stats);
@@ -359,6 +372,7 @@ rbf_status bin_run(rbf_ctx* ctx, const double* cx, const double* cy, const doubl
     if (ctx->max_cand > kMaxCand)
         return set_err(ctx, RBF_ERR_LIMIT,
                        "more than rbf_max_candidates() centres in one 3x3 cell neighbourhood");
+    if (ctx->T > 0 && (s = tiles_cell_list(ctx, st)) != RBF_OK) return s;
     ENS(work, sizeof(int4) * std::max(ctx->nwork, 1));
     k_work_fill<<<div_up(nc, T), T, 0, st>>>(nc, ctx->pstart.as<int>(), ctx->wstart.as<int>(),
                                              ctx->work.as<int4>());

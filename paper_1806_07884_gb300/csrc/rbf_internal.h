@@ -83,6 +83,35 @@ struct rbf_ctx {
     };
     SolveGraph cg_graph[2];
     bool solved = false;       // solver workspace exists
+
+    // ---- batched tiles (rbf_bin_tiles / rbf_solve_tiles) ----
+    int T = 0;                       // tiles packed into this system (0: one plain system)
+    std::vector<rbf_tile> tiles;     // the caller's tile descriptors
+    rbf_buf tdesc;                   // [T] per-tile placement (device)
+    rbf_buf rowtile;                 // [gy] tile owning each cell row, -1 between bands
+    rbf_buf clist;                   // [ncl] cells holding at least one centre
+    int ncl = 0;
+    rbf_buf tcg;                     // per-tile CG scalars and results
+    rbf_buf tred;                    // per-tile reductions (norms, pinned counts, scales)
+    void* hbt = nullptr;             // pinned host mirror of tcg / tred
+    size_t hbt_bytes = 0;
+    // launch configuration of the batched CG loop, [0] FP64, [1] FP32
+    struct TileTuning {
+        int spmv_bps = 0, chunk = 0, nt = 0;   // SpMV blocks per SM, cells per warp step,
+                                               // update block size (0: not chosen yet)
+        double us_per_iter = 0.0;              // measured by the autotuner (0: not tuned)
+        int ncl = 0, M = 0;                    // shape it was chosen for
+        int64_t nvals = 0;
+    };
+    TileTuning tune[2];
+    int autotune = 1;                // tune on the first batched solve of a new shape
+    int force_bps = 0, force_chunk = 0, force_nt = 0;   // fixed configuration (0: automatic)
+    struct TileGraph {
+        cudaGraphExec_t exec = nullptr;
+        const void* key[12] = {};
+        int T = 0, M = 0, ncl = 0, bps = 0, chunk = 0, nt = 0;
+    };
+    TileGraph bt_graph[2];
 };
 
 namespace rbf {
@@ -98,6 +127,21 @@ rbf_status bin_run(rbf_ctx* ctx, const double* cx, const double* cy, const doubl
 // exclusive scan of n int32 counts into n+1 outputs (int32 or int64), device-wide
 rbf_status scan_i32(rbf_ctx* ctx, const int* in, int* out, int n, cudaStream_t st);
 rbf_status scan_i64(rbf_ctx* ctx, const int64_t* in, int64_t* out, int n, cudaStream_t st);
+
+// rbf_batch.cu: the tile-aware parts of the binning of a batched system
+rbf_status tiles_count(rbf_ctx* ctx, const double* cx, const double* cy, const double* px,
+                       const double* py, const double* h, cudaStream_t st);
+rbf_status tiles_scatter(rbf_ctx* ctx, const double* cx, const double* cy, const double* px,
+                         const double* py, const double* h, cudaStream_t st);
+rbf_status tiles_cell_list(rbf_ctx* ctx, cudaStream_t st);
+void tiles_release(rbf_ctx* ctx);
+rbf_status bin_tiles_run(rbf_ctx* ctx, const rbf_tile* tiles, int T, const double* cx,
+                         const double* cy, int64_t Mtot, const double* px, const double* py,
+                         const double* h, int64_t Ntot, cudaStream_t st);
+rbf_status solve_tiles_run(rbf_ctx* ctx, double* c, int use_c0, double tol, int maxit,
+                           int min_support, rbf_tile_info* tinfo, rbf_solve_info* info,
+                           cudaStream_t st);
+rbf_status autotune_run(rbf_ctx* ctx, cudaStream_t st);
 
 // rbf_assemble.cu
 rbf_status assemble_run(rbf_ctx* ctx, int kernel, int prec, cudaStream_t st);
@@ -119,6 +163,12 @@ rbf_status eval_grid_run(rbf_ctx* ctx, const double* c, int nx, int ny, const do
 rbf_status diag_sqrt_run(const double* a, double* out, int64_t n, cudaStream_t st);
 rbf_status export_upper_run(rbf_ctx* ctx, int64_t cap, int32_t* row, int32_t* col, double* val,
                             double* bvec, int32_t* support, int64_t* nnz, cudaStream_t st);
+
+// preconditioner set-up of the assembled B (precision prec): dinv / dinv32 and the inverse
+// diagonal cell blocks; pinned centres counted into *npin_d
+rbf_status prec_setup_run(rbf_ctx* ctx, int prec, int min_support, int* npin_d, cudaStream_t st);
+// y += B x over all cells (precision prec; x, y sorted order)
+void launch_spmv(rbf_ctx* ctx, int prec, const void* x, void* y, cudaStream_t st);
 
 rbf_status bench_spmv_run(rbf_ctx* ctx, int reps, cudaStream_t st);
 rbf_status bench_cg_run(rbf_ctx* ctx, int reps, cudaStream_t st);

@@ -29,7 +29,7 @@
 
 #include <algorithm>
 
-#include "rbf_internal.h"
+#include "rbf_cg.cuh"
 
 namespace rbf {
 
@@ -51,43 +51,11 @@ struct CgScalars {
     double acc_delta[2][kAccSlots];   // u^T B u of the SpMV of each parity, spread over slots
 };
 
-enum { kRunning = 0, kConverged = 1, kBreakdown = 2, kMaxIt = 3 };
 
 namespace {
 
-constexpr int kSpmvWarps = 8;
 constexpr int kVecThreads = 256;
-constexpr unsigned kFull = 0xffffffffu;
-// CG iterations per pass of the solve graph's loop body (even: the buffers alternate).
-constexpr int kItersPerBody = 4;
-// Vectors of the CG workspace: x, u, p, r0, r1, s0, s1, w0, w1.
-constexpr int kCgVecs = 9;
 
-__device__ __forceinline__ double warp_sum_d(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-    return v;
-}
-
-// Block-wide sum of NV doubles; the result is valid in thread 0.
-template <int NV>
-__device__ __forceinline__ void block_sum(double (&v)[NV]) {
-    __shared__ double red[NV][32];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
-        v[k] = warp_sum_d(v[k]);
-        if (lane == 0) red[k][w] = v[k];
-    }
-    __syncthreads();
-    if (w == 0) {
-#pragma unroll
-        for (int k = 0; k < NV; ++k) v[k] = warp_sum_d(lane < nw ? red[k][lane] : 0.0);
-    }
-    __syncthreads();
-}
-
-// Stores this block's NV partial sums; returns true in the single last block to finish,
 // whose thread 0 then holds the totals, summed in block order, in tot[].
 template <int NV>
 __device__ bool last_block_total(double (&v)[NV], double* partial, unsigned int* ticket,
@@ -118,154 +86,6 @@ __device__ bool last_block_total(double (&v)[NV], double* partial, unsigned int*
     return true;
 }
 
-template <typename T>
-__device__ __forceinline__ T ldcg(const T* p) { return __ldcg(p); }
-
-__device__ __forceinline__ int colmap(const RowSeg& sg, int k) {
-    return k < sg.l0 ? sg.s0 + k : (k < sg.l0 + sg.l1 ? sg.s1 + (k - sg.l0) : sg.s2 + (k - sg.l0 - sg.l1));
-}
-
-// Four consecutive values of a row (16-byte aligned: rows are padded to kRowPad values).
-__device__ __forceinline__ void load4(const float* p, float (&v)[4]) {
-    const float4 q = __ldg(reinterpret_cast<const float4*>(p));
-    v[0] = q.x;
-    v[1] = q.y;
-    v[2] = q.z;
-    v[3] = q.w;
-}
-__device__ __forceinline__ void load4(const double* p, double (&v)[4]) {
-    const double2 a = __ldg(reinterpret_cast<const double2*>(p));
-    const double2 b = __ldg(reinterpret_cast<const double2*>(p + 2));
-    v[0] = a.x;
-    v[1] = a.y;
-    v[2] = b.x;
-    v[3] = b.y;
-}
-
-// Sum v[0..15] over the 32 lanes of a warp so that lane l ends up holding the total of
-// row (l >> 1) & 15: four exchange-and-halve steps (xor 16, 8, 4, 2) and a final xor 1.
-template <typename T>
-__device__ __forceinline__ T butterfly16(T (&v)[16], int lane) {
-    {
-        const bool hi = lane & 16;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const T send = hi ? v[j] : v[j + 8];
-            const T keep = hi ? v[j + 8] : v[j];
-            v[j] = keep + __shfl_xor_sync(kFull, send, 16);
-        }
-    }
-    {
-        const bool hi = lane & 8;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const T send = hi ? v[j] : v[j + 4];
-            const T keep = hi ? v[j + 4] : v[j];
-            v[j] = keep + __shfl_xor_sync(kFull, send, 8);
-        }
-    }
-    {
-        const bool hi = lane & 4;
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            const T send = hi ? v[j] : v[j + 2];
-            const T keep = hi ? v[j + 2] : v[j];
-            v[j] = keep + __shfl_xor_sync(kFull, send, 4);
-        }
-    }
-    {
-        const bool hi = lane & 2;
-        const T send = hi ? v[0] : v[1];
-        const T keep = hi ? v[1] : v[0];
-        v[0] = keep + __shfl_xor_sync(kFull, send, 2);
-    }
-    return v[0] + __shfl_xor_sync(kFull, v[0], 1);
-}
-
-// y += B x restricted to the stored upper row block of cell c (warp-cooperative; all 32
-// lanes). Lane l streams columns 4l .. 4l+3 of each row with vector loads; every loaded
-// value B[s][t] feeds both products:
-//   row sums    y[s] += sum_t B[s][t] x[t]   (16 rows in registers, butterfly reduction)
-//   column sums y[t] += sum_s B[s][t] x[s]   for t outside the diagonal block c x c
-//   (the diagonal block is stored in full, so its transposed half is already in the rows)
-// and are added with atomics. Returns this lane's share of x^T B x over the cell's entries:
-// sum_s x[s] rowsum[s] + sum_t colsum[t] x[t].
-template <typename T>
-__device__ double spmv_cell(const CellDesc& cd, const T* __restrict__ B, const T* x, T* y, int lane) {
-    const int cs = cd.cs, m = cd.m;
-    if (m == 0) return 0.0;
-    RowSeg sg;
-    sg.s0 = cd.s0;
-    sg.l0 = cd.l0;
-    sg.s1 = cd.s1;
-    sg.l1 = cd.l1;
-    sg.s2 = cd.s2;
-    sg.l2 = cd.l2;
-    const int L = sg.l0 + sg.l1 + sg.l2, lp = cd.lp;
-    const T* Bc = B + cd.rboff;
-    T dot = T(0);
-    for (int j0 = 0; j0 < m; j0 += 16) {
-        const int mm = min(16, m - j0);
-        const T xs_lane = lane < mm ? ldcg(x + cs + j0 + lane) : T(0);
-        T rp[16];
-#pragma unroll
-        for (int i = 0; i < 16; ++i) rp[i] = T(0);
-        for (int k0 = 0; k0 < L; k0 += 128) {
-            const int kb = k0 + 4 * lane;
-            const bool active = kb < L;
-            int t[4];
-            T xt[4], ca[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                t[q] = kb + q < L ? colmap(sg, kb + q) : -1;
-                xt[q] = t[q] >= 0 ? ldcg(x + t[q]) : T(0);
-                ca[q] = T(0);
-            }
-            const T* rb = Bc + (long long)j0 * lp + kb;
-#pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                if (i < mm) {                 // warp-uniform
-                    const T xi = __shfl_sync(kFull, xs_lane, i);
-                    if (active) {
-                        T v[4];
-                        load4(rb + (long long)i * lp, v);
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            rp[i] = fma(v[q], xt[q], rp[i]);
-                            ca[q] = fma(v[q], xi, ca[q]);
-                        }
-                    }
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                if (kb + q >= m && t[q] >= 0 && ca[q] != T(0)) {
-                    atomicAdd(y + t[q], ca[q]);
-                    dot = fma(ca[q], xt[q], dot);
-                }
-            }
-        }
-        const T tot = butterfly16(rp, lane);       // lanes 2r, 2r+1 hold row r
-        const int r = (lane >> 1) & 15;
-        const T xr = __shfl_sync(kFull, xs_lane, r);
-        if ((lane & 1) == 0 && r < mm) {
-            atomicAdd(y + cs + j0 + r, tot);
-            dot = fma(tot, xr, dot);
-        }
-    }
-    return double(dot);
-}
-
-__device__ __forceinline__ CellDesc load_desc(const CellDesc* d) {
-    CellDesc v;
-    const int4* p = reinterpret_cast<const int4*>(d);
-    int4* q = reinterpret_cast<int4*>(&v);
-    q[0] = __ldg(p);
-    q[1] = __ldg(p + 1);
-    q[2] = __ldg(p + 2);
-    return v;
-}
-
 // Standalone SpMV y += B x (persistent warps striding over the cells; y zeroed by the caller).
 template <typename T>
 __global__ void __launch_bounds__(kSpmvWarps * 32, sizeof(T) == 4 ? 3 : 1)
@@ -276,13 +96,6 @@ __global__ void __launch_bounds__(kSpmvWarps * 32, sizeof(T) == 4 ? 3 : 1)
         spmv_cell<T>(load_desc(bd.cdesc + c), B, x, y, lane);
 }
 
-template <typename T>
-struct CgVec {
-    T *x, *u, *p;
-    T *r[2], *s[2], *w[2];
-    const T* dinv;     // 1 / B_ss, 0 for pinned centres (the mask)
-    const T* bjinv;    // inverse diagonal cell blocks (cells with m <= kMaxBlock)
-};
 
 // Preconditioned CG in the Chronopoulos-Gear form (one SpMV and two reductions per
 // iteration), for B x = bscale * b:
@@ -306,32 +119,6 @@ __global__ void __launch_bounds__(kSpmvWarps * 32, sizeof(T) == 4 ? 3 : 1)
     if (lane == 0 && d != 0.0) atomicAdd(&sc->acc_delta[P][gw & (kAccSlots - 1)], d);
 }
 
-// The residual of a row after this iteration's update, r - alpha (w + beta s), evaluated
-// with the same operations by every thread that needs it.
-template <typename T>
-__device__ __forceinline__ T next_r(T r, T s, T w, T ta, T tb) {
-    return fma(-ta, fma(tb, s, w), r);
-}
-
-// u_i = sum_j Dinv[i][j] r_j over the rows j of row i's cell (row a of the cell's inverse
-// block), r_j produced by rj(j) for the cell's rows; or dinv_i r_i for large cells.
-template <typename T, typename F>
-__device__ __forceinline__ T apply_prec(const Binned& bd, const T* __restrict__ bjinv, int4 cm,
-                                        int i, T di, T ri, F rj) {
-    if (cm.y > kMaxBlock) return di * ri;
-    const int a = i - cm.x;
-    const T* drow = bjinv + bd.bjoff[cm.z] + (long long)a * cm.y;
-    T ui = T(0);
-#pragma unroll 4
-    for (int j = 0; j < cm.y; ++j) ui = fma(__ldg(drow + j), rj(cm.x + j), ui);
-    return ui;
-}
-
-// One thread per row i. Prologue (warp 0 of every block, identical results in all blocks):
-// gamma_k and (r_k, r_k) from the previous kernel's per-block partials, delta_k from the
-// SpMV's slots, the stopping test, then beta_k and alpha_k; block 0 writes the next slot.
-// Body: s, p, x, r updated; u = D^-1 r using the cell's updated residual (recomputed here
-// from the previous buffers); w of the other parity zeroed for the next SpMV; per-block
 // partials of gamma_{k+1} and (r_{k+1}, r_{k+1}). P is the parity k & 1.
 template <typename T>
 __global__ void __launch_bounds__(kVecThreads)
@@ -601,28 +388,6 @@ __global__ void k_norm2(int M, const double* __restrict__ v, const float* __rest
     if (threadIdx.x == 0) out[0] = a[0];
 }
 
-template <typename T>
-CgVec<T> cg_vectors(rbf_ctx* ctx) {
-    const int slot = sizeof(T) == 8 ? 0 : 1;
-    T* base = ctx->cgv[slot].as<T>();
-    const size_t M = size_t(ctx->M);
-    CgVec<T> v;
-    v.x = base;
-    v.u = base + M;
-    v.p = base + 2 * M;
-    v.r[0] = base + 3 * M;
-    v.r[1] = base + 4 * M;
-    v.s[0] = base + 5 * M;
-    v.s[1] = base + 6 * M;
-    v.w[0] = base + 7 * M;
-    v.w[1] = base + 8 * M;
-    v.dinv = slot == 0 ? reinterpret_cast<const T*>(ctx->dinv.p)
-                       : reinterpret_cast<const T*>(ctx->dinv32.p);
-    v.bjinv = slot == 0 ? reinterpret_cast<const T*>(ctx->bjinv.p)
-                        : reinterpret_cast<const T*>(ctx->bjinv32.p);
-    return v;
-}
-
 // Persistent SpMV grid: as many blocks as can be resident (never more than the cells need).
 template <typename T>
 int spmv_grid_T(rbf_ctx* ctx) {
@@ -812,6 +577,35 @@ rbf_status bench_spmv_impl(rbf_ctx* ctx, int reps, cudaStream_t st) {
 rbf_status bench_spmv_run(rbf_ctx* ctx, int reps, cudaStream_t st) {
     return ctx->prec == RBF_FP64 ? bench_spmv_impl<double>(ctx, reps, st)
                                  : bench_spmv_impl<float>(ctx, reps, st);
+}
+
+rbf_status prec_setup_run(rbf_ctx* ctx, int prec, int min_support, int* npin_d, cudaStream_t st) {
+    const Binned bd = view(ctx);
+    const int nb = div_up(ctx->g.ncell, kBjWarps);
+    if (prec == RBF_FP64)
+        k_prec_setup<double><<<nb, kBjWarps * 32, 0, st>>>(bd, ctx->bvals.as<double>(),
+                                                           ctx->support.as<int>(), min_support,
+                                                           ctx->dinv.as<double>(),
+                                                           ctx->bjinv.as<double>(), npin_d);
+    else
+        k_prec_setup<float><<<nb, kBjWarps * 32, 0, st>>>(bd, ctx->bvals.as<float>(),
+                                                          ctx->support.as<int>(), min_support,
+                                                          ctx->dinv32.as<float>(),
+                                                          ctx->bjinv32.as<float>(), npin_d);
+    ctx->launches += 1;
+    RBF_CUDA_TRY(cudaGetLastError());
+    return RBF_OK;
+}
+
+void launch_spmv(rbf_ctx* ctx, int prec, const void* x, void* y, cudaStream_t st) {
+    const Binned bd = view(ctx);
+    if (prec == RBF_FP64)
+        k_spmv<double><<<spmv_grid_T<double>(ctx), kSpmvWarps * 32, 0, st>>>(
+            bd, ctx->bvals.as<double>(), static_cast<const double*>(x), static_cast<double*>(y));
+    else
+        k_spmv<float><<<spmv_grid_T<float>(ctx), kSpmvWarps * 32, 0, st>>>(
+            bd, ctx->bvals.as<float>(), static_cast<const float*>(x), static_cast<float*>(y));
+    ctx->launches += 1;
 }
 
 static rbf_status finish_status(rbf_ctx* ctx, int state) {
