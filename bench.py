@@ -66,6 +66,10 @@ def parse():
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--quiet-extra", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--tiles", type=int, default=512)
+    ap.add_argument("--batched-only", action="store_true",
+                    help="run only the batched workload and print its object (profiling)")
     return ap.parse_args()
 
 
@@ -172,6 +176,112 @@ def run_reference(args):
 # ----------------------------------------------------------------------------------------
 # the GPU path
 # ----------------------------------------------------------------------------------------
+def bench_batched(args, rank, dev, stream, flush, hbm, peak_source):
+    """The batched workload: 512 independent tiles (N log-uniform in [2e3, 2e5], M = N / 10,
+    phi_3,1, K = 30) binned, assembled and solved together; sum of N over the fit time."""
+    import numpy as np
+    import torch
+
+    import datagen as dg
+    import paper_1806_07884_gb300 as pkg
+
+    pbs = dg.tile_batch(1000 + 100_000 * rank, args.tiles)
+    tiles, cx, cy, px, py, hh = pkg.pack_tiles(
+        [(pb.points, pb.h, pb.centres, pb.R, pb.bbox) for pb in pbs])
+    d = [torch.as_tensor(a).to(dev) for a in (cx, cy, px, py, hh)]
+    Ntot, Mtot = int(px.size), int(cx.size)
+    cbuf = torch.empty(Mtot, dtype=torch.float64, device=dev)
+    ctx = pkg.Context(dev.index)
+
+    def step(prec, tol):
+        ctx.bin_tiles(tiles, *d)
+        ctx.assemble("w31", prec)
+        c, info, tinfo = ctx.solve_tiles(tol=tol, maxit=20000, out=cbuf)
+        return info, tinfo
+
+    def timed(prec, tol, k):
+        ms = []
+        for _ in range(k):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            info, tinfo = step(prec, tol)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return statistics.mean(ms), info, tinfo
+
+    for _ in range(2):                     # warm-up (the first one runs the autotuner)
+        step(args.prec, args.tol)
+    torch.cuda.synchronize()
+    launches0 = ctx.launch_count()
+    ms, info, tinfo = timed(args.prec, args.tol, max(2, min(args.steps, 3)))
+    launches = (ctx.launch_count() - launches0) // max(2, min(args.steps, 3))
+    c_fast = cbuf.clone()
+    tune = ctx.tuning()
+    # phases of one step
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    flush.zero_()
+    ev[0].record(stream)
+    ctx.bin_tiles(tiles, *d)
+    ev[1].record(stream)
+    ctx.assemble("w31", args.prec)
+    ev[2].record(stream)
+    ctx.solve_tiles(tol=args.tol, maxit=20000, out=cbuf)
+    ev[3].record(stream)
+    torch.cuda.synchronize()
+    phases = {n: round(ev[k].elapsed_time(ev[k + 1]), 3)
+              for k, n in enumerate(["bin", "assemble", "solve"])}
+    # roofline of the batched SpMV (FP32 B, every tile running), timed on its stream
+    lay = ctx.layout()
+    vb = lay["value_bytes"]
+    ctx.bench_spmv(5)
+    s0 = torch.cuda.Event(enable_timing=True)
+    s1 = torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    ctx.bench_spmv(30)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    spmv_ms = s0.elapsed_time(s1) / 30
+    spmv_bytes = lay["nvals"] * vb + 3 * Mtot * vb
+    ach = spmv_bytes / (spmv_ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "kernel": f"k_bcg_spmv<{'float' if vb == 4 else 'double'}>",
+            "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s", "frac": round(ach / hbm, 4),
+            "traffic": None, "algorithmic_bytes": spmv_bytes, "launch_ms": round(spmv_ms, 5),
+            "peak_source": peak_source}
+    out = {"workload": f"{args.tiles} tiles, N log-uniform in [2000, 200000], M = N/10, "
+                       f"Wendland phi_3,1, K=30, sum N = {Ntot}, sum M = {Mtot}",
+           "value": Ntot / (ms * 1e-3), "unit": "points/s", "ms_per_step": round(ms, 3),
+           "prec": args.prec, "tol": args.tol, "gpu_launches_per_step": launches,
+           "iterations_max": info["iterations"], "refinements_max": info["refinements"],
+           "iterations_mean": round(float(np.mean([t["iterations"] for t in tinfo])), 1),
+           "all_converged": all(t["status"] == 0 for t in tinfo), "promoted": info["promoted"],
+           "phases_ms": phases, "tuning": tune, "roofline": roof}
+    if not args.no_fp64_compare:
+        ms64, info64, _ = timed("fp64", args.tol, 1)
+        out["fp64_path"] = {"value": Ntot / (ms64 * 1e-3), "ms_per_step": round(ms64, 3),
+                            "iterations_max": info64["iterations"]}
+        step("fp64", 1e-13)
+        c_ref = cbuf.clone()
+        # each tile's surface on its own 64 x 64 grid, this path against the tight FP64 fit
+        f_fast = ctx.eval_tiles_grid(c_fast, 64, 64).reshape(len(tiles), -1)
+        f_ref = ctx.eval_tiles_grid(c_ref, 64, 64).reshape(len(tiles), -1)
+        den = f_ref.abs().amax(dim=1).clamp_min(1e-300)
+        errs = ((f_fast - f_ref).abs().amax(dim=1) / den).cpu().numpy()
+        cerr = []
+        for t in tiles:
+            a = c_fast[t["c0"]:t["c0"] + t["M"]]
+            b = c_ref[t["c0"]:t["c0"] + t["M"]]
+            cerr.append(float((a - b).abs().max()) / max(float(b.abs().max()), 1e-300))
+        out["accuracy"] = {"max_tile_rel_err_f_vs_fp64_tight": float(errs.max()),
+                           "median_tile_rel_err_f": float(np.median(errs)),
+                           "max_tile_rel_err_c": max(cerr), "bar": 1e-6,
+                           "ok": bool(errs.max() <= 1e-6)}
+    ctx.close()
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -191,6 +301,22 @@ def main():
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device(f"cuda:{local}")
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    if args.batched_only:
+        flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+        out = bench_batched(args, rank, dev, torch.cuda.current_stream(dev), flush, hbm,
+                            "measured" if "hbm_gbs" in peaks else "fallback")
+        if rank == 0:
+            print(json.dumps(out), flush=True)
+        if world > 1:
+            dist.destroy_process_group()
+        return
 
     pb = dg.config_terrain(seed=rank, N=args.N, M=args.M, eval_n=args.grid)
     N, M, n = pb.N, pb.M, args.grid
@@ -287,13 +413,6 @@ def main():
     s1.record(stream)
     torch.cuda.synchronize()
     cg_iter_us = s0.elapsed_time(s1) * 1e3 / 100
-    peaks = {}
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            peaks = json.load(f)
-    except OSError:
-        pass
-    hbm = peaks.get("hbm_gbs", 6800.0)
     achieved = spmv_bytes / (spmv_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "kernel": f"k_spmv<{'float' if vb == 4 else 'double'}>",
                 "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
@@ -352,6 +471,12 @@ def main():
         e2e = {"value": world * N / (ems * 1e-3), "unit": "points/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": round(ems, 3)}
 
+    # ---- the batched workload (its own sub-object of the line)
+    batched = None
+    if not args.no_batched:
+        batched = bench_batched(args, rank, dev, stream, flush, hbm,
+                                "measured" if "hbm_gbs" in peaks else "fallback")
+
     # ---- CPU baseline: the oracle on a bounded sample (rank 0, single GPU only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -377,6 +502,7 @@ def main():
                        "parallelism": f"replicas x{world}"},
             "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu,
             "clocks": clocks, "accuracy": acc, "fp64_path": fp64, "phases_ms": phases,
+            "batched": batched,
             "solver": {"iterations": last["iterations"], "refinements": last["refinements"],
                        "rel_residual": last["rel_residual"], "pinned": last["pinned"]},
         }

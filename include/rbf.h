@@ -197,13 +197,16 @@ rbf_status rbf_get_launch_count(const rbf_ctx* ctx, int64_t* launches);
 /* Diagnostics / timing: launch the solver's SpMV kernel y += B x (Section 4's y = Q x on
  * this library's cell-blocked symmetric storage) `reps` times on `stream` with x = 1, in the
  * launch configuration a CG iteration uses, on the solver's workspace (which it allocates if
- * needed and overwrites). Requires a preceding rbf_assemble. Asynchronous. */
+ * needed and overwrites). Requires a preceding rbf_assemble. On a batched context (after
+ * rbf_solve_tiles) it launches the batched SpMV with every tile running. Asynchronous. */
 rbf_status rbf_bench_spmv(rbf_ctx* ctx, int reps, void* stream);
 
 /* Diagnostics / timing: run `reps` preconditioned CG iterations on B c = b from c = 0 with
  * every iteration's two kernels launched individually on `stream` (the solver normally loops
  * inside one CUDA graph), so that the kernels can be timed or profiled one by one. Uses and
- * overwrites the solver's workspace; requires a preceding rbf_solve. Asynchronous. */
+ * overwrites the solver's workspace; requires a preceding rbf_solve (rbf_solve_tiles on a
+ * batched context, where the iterations are batched ones with every tile running).
+ * Asynchronous. */
 rbf_status rbf_bench_cg(rbf_ctx* ctx, int reps, void* stream);
 
 /* Batched step (a): bin T independent tiles (HOST array `tiles`) into one packed system.
@@ -236,6 +239,20 @@ rbf_status rbf_bin_tiles(rbf_ctx* ctx, const rbf_tile* tiles, int T, const doubl
 rbf_status rbf_solve_tiles(rbf_ctx* ctx, double* c, int use_c0, double tol, int maxit,
                            int min_support, rbf_tile_info* tile_info, rbf_solve_info* info,
                            void* stream);
+
+/* Batched step (e): f(q) = sum_j c_j phi(||q - xi_j|| / R_t) over the centres of tile t for
+ * queries grouped by tile: tile t's queries are qx, qy [qoff[t], qoff[t+1]) (DEVICE arrays;
+ * qoff a HOST array of T+1 non-decreasing offsets with qoff[0] = 0), values into f at the
+ * same positions (DEVICE). c: DEVICE, Mtot doubles in the caller's concatenated order.
+ * Requires rbf_bin_tiles + rbf_assemble. Synchronises `stream`. */
+rbf_status rbf_eval_tiles(rbf_ctx* ctx, const double* c, const double* qx, const double* qy,
+                          const int64_t* qoff, double* f, void* stream);
+
+/* Batched step (e) on each tile's own node-centred nx x ny grid over the tile's bbox (as
+ * rbf_eval_grid): tile t's node (i, j) at f[t*nx*ny + i*nx + j] (DEVICE, T*nx*ny doubles).
+ * Asynchronous. */
+rbf_status rbf_eval_tiles_grid(rbf_ctx* ctx, const double* c, int nx, int ny, double* f,
+                               void* stream);
 
 /* Autotuner of the batched CG loop: on the assembled batched system, times CG iterations in
  * each candidate launch configuration (SpMV blocks per SM x cells per warp step, then the

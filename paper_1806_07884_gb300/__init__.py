@@ -201,6 +201,28 @@ class Context:
             self._check(s, "rbf_solve_tiles")
         return c, d, tl
 
+    def eval_tiles(self, c, qx, qy, qoff, out=None, stream=None):
+        """Batched step (e) at queries grouped by tile: tile t's queries are
+        qx[qoff[t]:qoff[t+1]] (qoff: T+1 host integers)."""
+        torch = _torch()
+        Q = int(qx.numel())
+        f = out if out is not None else torch.empty(Q, dtype=torch.float64, device=qx.device)
+        off = (C.c_int64 * (self.T + 1))(*[int(v) for v in qoff])
+        s = self.lib.rbf_eval_tiles(self._h, _dptr(c, "c"), _dptr(qx, "qx"), _dptr(qy, "qy"),
+                                    off, _dptr(f, "f"), self._stream(stream))
+        self._check(s, "rbf_eval_tiles")
+        return f
+
+    def eval_tiles_grid(self, c, nx: int, ny: int, out=None, stream=None):
+        """Batched step (e) on each tile's nx x ny node grid over its bbox: shape (T, ny, nx)."""
+        torch = _torch()
+        f = out if out is not None else torch.empty((self.T, ny, nx), dtype=torch.float64,
+                                                    device=c.device)
+        s = self.lib.rbf_eval_tiles_grid(self._h, _dptr(c, "c"), int(nx), int(ny), _dptr(f, "f"),
+                                         self._stream(stream))
+        self._check(s, "rbf_eval_tiles_grid")
+        return f
+
     def autotune(self, stream=None):
         """Time the batched CG loop's launch configurations and keep the fastest."""
         self._check(self.lib.rbf_autotune(self._h, self._stream(stream)), "rbf_autotune")

@@ -63,6 +63,8 @@ SIGNATURES = {
     "rbf_bin_tiles": (_I, [_P, C.POINTER(Tile), _I, _P, _P, _I64, _P, _P, _P, _I64, _P]),
     "rbf_solve_tiles": (_I, [_P, _P, _I, _D, _I, _I, C.POINTER(TileInfo), C.POINTER(SolveInfo), _P]),
     "rbf_autotune": (_I, [_P, _P]),
+    "rbf_eval_tiles": (_I, [_P, _P, _P, _P, C.POINTER(_I64), _P, _P]),
+    "rbf_eval_tiles_grid": (_I, [_P, _P, _I, _I, _P, _P]),
     "rbf_get_tuning": (_I, [_P, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I), C.POINTER(_D)]),
 }
 

@@ -258,6 +258,30 @@ rbf_status rbf_solve_tiles(rbf_ctx* ctx, double* c, int use_c0, double tol, int 
                            as_stream(stream));
 }
 
+rbf_status rbf_eval_tiles(rbf_ctx* ctx, const double* c, const double* qx, const double* qy,
+                          const int64_t* qoff, double* f, void* stream) {
+    if (!ctx) return RBF_ERR_ARG;
+    if (!ctx->assembled || ctx->T < 1)
+        return set_err(ctx, RBF_ERR_ARG, "rbf_eval_tiles before rbf_bin_tiles + rbf_assemble");
+    if (!c || !qoff) return set_err(ctx, RBF_ERR_ARG, "null pointer argument");
+    if (qoff[0] != 0) return set_err(ctx, RBF_ERR_ARG, "qoff[0] must be 0");
+    for (int t = 0; t < ctx->T; ++t)
+        if (qoff[t + 1] < qoff[t]) return set_err(ctx, RBF_ERR_ARG, "qoff must be non-decreasing");
+    if (qoff[ctx->T] > 0 && (!qx || !qy || !f)) return set_err(ctx, RBF_ERR_ARG, "null pointer argument");
+    DeviceGuard dg(ctx->device);
+    return eval_tiles_run(ctx, c, qx, qy, qoff, 0, 0, f, as_stream(stream));
+}
+
+rbf_status rbf_eval_tiles_grid(rbf_ctx* ctx, const double* c, int nx, int ny, double* f,
+                               void* stream) {
+    if (!ctx) return RBF_ERR_ARG;
+    if (!ctx->assembled || ctx->T < 1)
+        return set_err(ctx, RBF_ERR_ARG, "rbf_eval_tiles_grid before rbf_bin_tiles + rbf_assemble");
+    if (nx < 1 || ny < 1 || !c || !f) return set_err(ctx, RBF_ERR_ARG, "bad arguments");
+    DeviceGuard dg(ctx->device);
+    return eval_tiles_run(ctx, c, nullptr, nullptr, nullptr, nx, ny, f, as_stream(stream));
+}
+
 rbf_status rbf_autotune(rbf_ctx* ctx, void* stream) {
     if (!ctx) return RBF_ERR_ARG;
     if (!ctx->assembled || ctx->T < 1)
@@ -373,6 +397,10 @@ rbf_status rbf_bench_spmv(rbf_ctx* ctx, int reps, void* stream) {
     if (!ctx->assembled) return set_err(ctx, RBF_ERR_ARG, "rbf_bench_spmv before rbf_assemble");
     if (reps < 0) return set_err(ctx, RBF_ERR_ARG, "reps < 0");
     DeviceGuard dg(ctx->device);
+    if (ctx->T > 0) {
+        if (!ctx->solved) return set_err(ctx, RBF_ERR_ARG, "rbf_bench_spmv on a batch before rbf_solve_tiles");
+        return bench_tiles_run(ctx, reps, true, as_stream(stream));
+    }
     return bench_spmv_run(ctx, reps, as_stream(stream));
 }
 
@@ -381,6 +409,7 @@ rbf_status rbf_bench_cg(rbf_ctx* ctx, int reps, void* stream) {
     if (!ctx->solved || !ctx->assembled) return set_err(ctx, RBF_ERR_ARG, "rbf_bench_cg before rbf_solve");
     if (reps < 0) return set_err(ctx, RBF_ERR_ARG, "reps < 0");
     DeviceGuard dg(ctx->device);
+    if (ctx->T > 0) return bench_tiles_run(ctx, reps, false, as_stream(stream));
     return bench_cg_run(ctx, reps, as_stream(stream));
 }
 

@@ -40,6 +40,7 @@ namespace {
 struct TileDev {
     long long c0, m, p0, n;    // centre and point ranges of the concatenated inputs
     double x0, y0, R;          // frame: u = (x - x0) / R
+    double x1, y1;             // upper corner of the tile's box
     int gx, gy, oy, pad;       // cells per axis, first cell row of the band
 };
 
@@ -306,6 +307,69 @@ __global__ void k_copy_masked(int M, const double* __restrict__ src, const doubl
                               double* __restrict__ dst) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < M) dst[i] = dinv[i] == 0.0 ? 0.0 : src[i];
+}
+
+// f(x) = sum_j c_j phi(||x - xi_j|| / R_t) for a query x of tile t: the centres of the 3x3
+// cells around the query's cell in the tile's band, FP32 prefilter on cell-local
+// coordinates, exact support test and FP64 evaluation on tile-local coordinates.
+template <int KIND>
+__device__ __forceinline__ double eval_tile_at(const Binned& bd, const TileDev& t,
+                                               const double* __restrict__ c, double x, double y) {
+    const Grid& g = bd.g;
+    const double xl = (x - t.x0) / t.R, yl = (y - t.y0) / t.R;
+    const int ix = tile_cell(xl, g.invh, t.gx), iy = tile_cell(yl, g.invh, t.gy);
+    const float uq = float(xl - ix * g.h), vq = float(yl - iy * g.h);
+    double f = 0.0;
+    for (int r = max(iy - 1, 0); r <= min(iy + 1, t.gy - 1); ++r) {
+        const float oy = float(r - iy);
+        for (int cx = max(ix - 1, 0); cx <= min(ix + 1, t.gx - 1); ++cx) {
+            const float ox = float(cx - ix);
+            const int cell = (t.oy + r) * g.gx + cx;
+            const int s0 = bd.cstart[cell], s1 = bd.cstart[cell + 1];
+            for (int s = s0; s < s1; ++s) {
+                const float du = uq - (bd.cu[s] + ox), dv = vq - (bd.cv[s] + oy);
+                if (du * du + dv * dv >= kPrefilterR2) continue;
+                const double dx = xl - bd.cx[s], dy = yl - bd.cy[s];
+                if (inside_exact(dx, dy, 1.0, 1.0)) {
+                    const double rr = sqrt_nr(fma(dx, dx, dy * dy));
+                    f = fma(c[s], wendland<KIND, double>(rr), f);
+                }
+            }
+        }
+    }
+    return f;
+}
+
+// Queries of tile blockIdx.y: [qoff[t], qoff[t+1]) of qx, qy, f.
+template <int KIND>
+__global__ void k_eval_tiles(Binned bd, const TileDev* __restrict__ td, const double* __restrict__ c,
+                             const double* __restrict__ qx, const double* __restrict__ qy,
+                             const long long* __restrict__ qoff, double* __restrict__ f) {
+    const TileDev t = td[blockIdx.y];
+    const long long q0 = qoff[blockIdx.y], q1 = qoff[blockIdx.y + 1];
+    for (long long q = q0 + blockIdx.x * (long long)blockDim.x + threadIdx.x; q < q1;
+         q += (long long)gridDim.x * blockDim.x)
+        f[q] = eval_tile_at<KIND>(bd, t, c, qx[q], qy[q]);
+}
+
+// The nx x ny node grid over each tile's own box (inclusive linspace, last node exactly at the
+// box's end), tile t's values at f[t nx ny + i nx + j].
+template <int KIND>
+__global__ void k_eval_tiles_grid(Binned bd, const TileDev* __restrict__ td,
+                                  const double* __restrict__ c, int nx, int ny,
+                                  double* __restrict__ f) {
+    const TileDev t = td[blockIdx.y];
+    const long long Q = (long long)nx * ny;
+    const double sx = nx > 1 ? (t.x1 - t.x0) / (nx - 1) : 0.0;
+    const double sy = ny > 1 ? (t.y1 - t.y0) / (ny - 1) : 0.0;
+    double* ft = f + (long long)blockIdx.y * Q;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < Q;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int i = int(q / nx), j = int(q % nx);
+        const double x = (j == nx - 1 && nx > 1) ? t.x1 : __dadd_rn(__dmul_rn(double(j), sx), t.x0);
+        const double y = (i == ny - 1 && ny > 1) ? t.y1 : __dadd_rn(__dmul_rn(double(i), sy), t.y0);
+        ft[q] = eval_tile_at<KIND>(bd, t, c, x, y);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -907,7 +971,7 @@ void tiles_release(rbf_ctx* ctx) {
             cudaGraphExecDestroy(sg.exec);
             sg.exec = nullptr;
         }
-    rbf_buf* bufs[] = {&ctx->tdesc, &ctx->rowtile, &ctx->clist, &ctx->tcg, &ctx->tred};
+    rbf_buf* bufs[] = {&ctx->tdesc, &ctx->rowtile, &ctx->clist, &ctx->tcg, &ctx->tred, &ctx->qoff};
     for (rbf_buf* b : bufs) release(ctx, *b);
     if (ctx->hbt) cudaFreeHost(ctx->hbt);
     ctx->hbt = nullptr;
@@ -961,6 +1025,8 @@ rbf_status bin_tiles_run(rbf_ctx* ctx, const rbf_tile* tiles, int T, const doubl
         d.n = q.N;
         d.x0 = q.bbox[0];
         d.y0 = q.bbox[1];
+        d.x1 = q.bbox[2];
+        d.y1 = q.bbox[3];
         d.R = q.R;
         d.gx = int(nx);
         d.gy = int(ny);
@@ -1207,6 +1273,91 @@ rbf_status solve_tiles_run(rbf_ctx* ctx, double* c, int use_c0, double tol, int 
 #undef ENS
     if (worst == RBF_ERR_BREAKDOWN) return set_err(ctx, worst, "CG breakdown in some tile");
     if (worst != RBF_OK) return set_err(ctx, worst, "some tile did not reach tol");
+    return RBF_OK;
+}
+
+template <typename T>
+__global__ void k_tile_fill(T* __restrict__ v, int n, T value) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) v[i] = value;
+}
+
+// Timing hooks on a batched system (after rbf_solve_tiles): `reps` launches of the batched
+// SpMV alone with every tile running and u = 1, or `reps` batched CG iterations from a cold
+// start, in the configuration the solver uses.
+template <typename T>
+rbf_status bench_tiles_impl(rbf_ctx* ctx, int reps, bool spmv_only, cudaStream_t st) {
+    Cfg cf;
+    rbf_status s = pick_cfg<T>(ctx, &cf, st);
+    if (s != RBF_OK) return s;
+    const int T_ = ctx->T;
+    std::vector<char> act(T_, 1);
+    std::vector<double> one(T_, 1.0), zero(T_, 0.0);
+    if ((s = write_tile_state(ctx, act, one, zero, 1 << 30, st)) != RBF_OK) return s;
+    const CgVec<T> v = cg_vectors<T>(ctx);
+    const TileCg tc = tile_view(ctx);
+    if (spmv_only) {
+        k_tile_fill<T><<<div_up(ctx->M, 256), 256, 0, st>>>(v.u, ctx->M, T(1));
+        RBF_CUDA_TRY(cudaMemsetAsync(v.w[0], 0, sizeof(T) * ctx->M, st));
+        const Binned bd = view(ctx);
+        const int grid = std::max(1, std::min(cf.bps * sm_count(ctx),
+                                              div_up(ctx->ncl, int64_t(kSpmvWarps) * cf.chunk)));
+        for (int k = 0; k < reps; ++k)
+            k_bcg_spmv<T><<<grid, kSpmvWarps * 32, 0, st>>>(bd, ctx->clist.as<int>(), ctx->ncl,
+                                                            cf.chunk, ctx->bvals.as<T>(), v.u,
+                                                            v.w[0], 0, ctx->T, tc);
+        ctx->launches += reps + 1;
+    } else {
+        if ((s = bcg_start<T, double>(ctx, ctx->bvec.as<double>(), false, st)) != RBF_OK) return s;
+        for (int k = 0; k < reps; ++k) launch_bcg_iteration<T>(ctx, v, tc, cf, k & 1, st);
+        ctx->launches += 2 * int64_t(reps);
+    }
+    RBF_CUDA_TRY(cudaGetLastError());
+    return RBF_OK;
+}
+
+rbf_status bench_tiles_run(rbf_ctx* ctx, int reps, bool spmv_only, cudaStream_t st) {
+    return ctx->prec == RBF_FP64 ? bench_tiles_impl<double>(ctx, reps, spmv_only, st)
+                                 : bench_tiles_impl<float>(ctx, reps, spmv_only, st);
+}
+
+// Batched step (e): queries grouped by tile (qoff: HOST, T+1 offsets), or each tile's own
+// nx x ny grid when qx is null.
+rbf_status eval_tiles_run(rbf_ctx* ctx, const double* c, const double* qx, const double* qy,
+                          const int64_t* qoff, int nx, int ny, double* f, cudaStream_t st) {
+    const int T = ctx->T;
+    rbf_status s = ensure(ctx, ctx->csort, sizeof(double) * ctx->M, st);
+    if (s != RBF_OK) return s;
+    const Binned bd = view(ctx);
+    launch_gather_sorted(c, bd.cperm, ctx->csort.as<double>(), ctx->M, st);
+    ctx->launches += 1;
+    const TileDev* td = ctx->tdesc.as<TileDev>();
+    const double* cs = ctx->csort.as<double>();
+    int64_t most = 0;
+    if (qx) {
+        for (int t = 0; t < T; ++t) most = std::max<int64_t>(most, qoff[t + 1] - qoff[t]);
+        if ((s = ensure(ctx, ctx->qoff, sizeof(long long) * (T + 1), st)) != RBF_OK) return s;
+        RBF_CUDA_TRY(cudaMemcpyAsync(ctx->qoff.p, qoff, sizeof(long long) * (T + 1),
+                                     cudaMemcpyHostToDevice, st));
+    } else {
+        most = int64_t(nx) * ny;
+    }
+    if (most == 0) return RBF_OK;
+    const dim3 grid(std::max(1, std::min(div_up(most, 256), 64)), T);
+    const long long* qo = ctx->qoff.as<long long>();
+#define EVAL_TILES(K)                                                                       \
+    if (qx) k_eval_tiles<K><<<grid, 256, 0, st>>>(bd, td, cs, qx, qy, qo, f);               \
+    else k_eval_tiles_grid<K><<<grid, 256, 0, st>>>(bd, td, cs, nx, ny, f);
+    switch (ctx->kernel) {
+        case RBF_W30: EVAL_TILES(0) break;
+        case RBF_W31: EVAL_TILES(1) break;
+        case RBF_W32: EVAL_TILES(2) break;
+        default: EVAL_TILES(3) break;
+    }
+#undef EVAL_TILES
+    ctx->launches += 1;
+    RBF_CUDA_TRY(cudaGetLastError());
+    if (qx) RBF_CUDA_TRY(cudaStreamSynchronize(st));   // qoff's host array is pageable
     return RBF_OK;
 }
 

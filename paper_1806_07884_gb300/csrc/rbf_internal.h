@@ -93,6 +93,7 @@ struct rbf_ctx {
     int ncl = 0;
     rbf_buf tcg;                     // per-tile CG scalars and results
     rbf_buf tred;                    // per-tile reductions (norms, pinned counts, scales)
+    rbf_buf qoff;                    // [T+1] query offsets of rbf_eval_tiles
     void* hbt = nullptr;             // pinned host mirror of tcg / tred
     size_t hbt_bytes = 0;
     // launch configuration of the batched CG loop, [0] FP64, [1] FP32
@@ -142,6 +143,10 @@ rbf_status solve_tiles_run(rbf_ctx* ctx, double* c, int use_c0, double tol, int 
                            int min_support, rbf_tile_info* tinfo, rbf_solve_info* info,
                            cudaStream_t st);
 rbf_status autotune_run(rbf_ctx* ctx, cudaStream_t st);
+// timing hooks of a batched system: the batched SpMV alone, or whole batched CG iterations
+rbf_status bench_tiles_run(rbf_ctx* ctx, int reps, bool spmv_only, cudaStream_t st);
+rbf_status eval_tiles_run(rbf_ctx* ctx, const double* c, const double* qx, const double* qy,
+                          const int64_t* qoff, int nx, int ny, double* f, cudaStream_t st);
 
 // rbf_assemble.cu
 rbf_status assemble_run(rbf_ctx* ctx, int kernel, int prec, cudaStream_t st);

@@ -306,3 +306,27 @@ def test_batched_workload_512_tiles_full_size():
             if so.support(j) >= 3:
                 assert abs(so.normal_residual(c, j)) <= 1e-8 * bmax
     ctx.close()
+
+
+def test_batched_eval_matches_oracle():
+    """Batched step (e): each tile's surface on its own grid (inclusive ends) and at its data
+    points, from the FP64 batched fit, against the oracle's surface of that tile."""
+    pbs = _tiles_small()
+    cs, info, tinfo, ctx = pkg.fit_tiles(_problems(pbs), prec="fp64", tol=1e-14)
+    c_all = torch.cat(cs)
+    fg = ctx.eval_tiles_grid(c_all, 33, 29).cpu().numpy()
+    qx = np.concatenate([pb.points[:, 0] for pb in pbs])
+    qy = np.concatenate([pb.points[:, 1] for pb in pbs])
+    qoff = np.concatenate([[0], np.cumsum([pb.N for pb in pbs])])
+    fp = ctx.eval_tiles(c_all, _dev(qx), _dev(qy), qoff).cpu().numpy()
+    for k, pb in enumerate(pbs):
+        c_ref, ref = _oracle(pb, ("small", k))
+        x0, y0, x1, y1 = pb.bbox
+        X, Y = np.meshgrid(np.linspace(x0, x1, 33), np.linspace(y0, y1, 29))
+        f_ref = O.evaluate(c_ref, pb.centres, np.column_stack([X.ravel(), Y.ravel()]), pb.R,
+                           pb.kernel)
+        assert O.rel_err(fg[k].ravel(), f_ref) <= FP64_BAR, k
+        assert O.rel_err(fp[qoff[k]:qoff[k + 1]], ref["A"] @ c_ref) <= FP64_BAR, k
+    with pytest.raises(pkg.RBFError):
+        ctx.eval_tiles(c_all, _dev(qx), _dev(qy), qoff[::-1].copy())
+    ctx.close()
