@@ -41,7 +41,7 @@ import numpy as np
 __all__ = [
     "Problem", "halton", "franke", "value_noise", "support_radius", "grid_nodes",
     "config_franke", "config_terrain", "config_bigdata", "tile", "tile_batch",
-    "config_small", "KERNELS",
+    "config_small", "KERNELS", "mlp_init", "MLP_NPARAM",
 ]
 
 KERNELS = ("w30", "w31", "w32", "w33")
@@ -292,3 +292,24 @@ def config_small(seed: int, N: int, M: int, K: float = 20.0, kernel: str = "w31"
     C = rng.random((M, 2))
     return Problem(pts, h, C, support_radius(M, K), kernel, eval_n=eval_n,
                    name=f"small_s{seed}_N{N}_M{M}", meta=dict(seed=seed, K=K))
+
+
+# ----------------------------------------------------------------------------
+# warm-start network: seeded initial weights (inputs of both the oracle and the library)
+# ----------------------------------------------------------------------------
+
+MLP_NFEAT, MLP_HID = 32, 64
+MLP_NPARAM = MLP_HID * MLP_NFEAT + MLP_HID + MLP_HID * MLP_HID + MLP_HID + MLP_HID + 1
+
+
+def mlp_init(seed: int = 0) -> np.ndarray:
+    """Flat FP32 parameters of the 32-64-64-1 network: weights uniform in
+    +-sqrt(6 / fan_in) (He), the output layer in +-sqrt(1 / fan_in), biases 0."""
+    rng = np.random.default_rng(seed)
+    parts = [rng.uniform(-1, 1, (MLP_HID, MLP_NFEAT)) * np.sqrt(6.0 / MLP_NFEAT),
+             np.zeros(MLP_HID),
+             rng.uniform(-1, 1, (MLP_HID, MLP_HID)) * np.sqrt(6.0 / MLP_HID),
+             np.zeros(MLP_HID),
+             rng.uniform(-1, 1, MLP_HID) * np.sqrt(1.0 / MLP_HID),
+             np.zeros(1)]
+    return np.concatenate([a.ravel() for a in parts]).astype(np.float32)

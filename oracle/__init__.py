@@ -6,3 +6,4 @@ only ``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` /
 shares no code with the CUDA library (no kernels, headers, helpers or tables).
 """
 from .rbf_oracle import *  # noqa: F401,F403
+from . import mlp_oracle  # noqa: F401

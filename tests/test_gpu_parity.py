@@ -269,8 +269,10 @@ def test_terrain_full_size_properties():
         i, j = rng.integers(0, 1024, 2)
         assert abs(f[i, j] - so.f(cn, (gx[j], gx[i]))) <= 1e-12 * np.abs(f).max()
     ctx.close()
+    # the clustered terrain is ill-conditioned (kappa ~ 6e6): a 1e-6 surface needs the
+    # normal residual at 1e-11, the tolerance the benchmark uses
     ctx32 = _binned(pb, prec="fp32_refine")
-    c32, info32 = ctx32.solve(tol=1e-10)
+    c32, info32 = ctx32.solve(tol=1e-11)
     f32 = ctx32.eval_grid(c32, 1024, 1024).cpu().numpy()
     assert O.rel_err(f32, f) <= MIXED_BAR
     ctx32.close()
