@@ -266,6 +266,48 @@ rbf_status rbf_autotune(rbf_ctx* ctx, void* stream);
 rbf_status rbf_get_tuning(const rbf_ctx* ctx, int* spmv_blocks_per_sm, int* spmv_chunk,
                           int* update_threads, double* us_per_iteration);
 
+/* ---- learned warm start (not in the paper: a start vector for the solver) ----
+ * A 32-64-64-1 network predicts c_j from 32 radial features of the data around centre j;
+ * rbf_solve / rbf_solve_tiles started from that guess (use_c0 = 1) reach the same solution,
+ * in fewer iterations when the guess is good. Parameters: a flat FP32 DEVICE vector of
+ * RBF_MLP_NPARAM values: W1 (row-major 64 x 32), b1 (64), W2 (row-major 64 x 64), b2 (64),
+ * W3 (64), b3 (1); the weights (not the biases) are rounded to BF16 where they enter a
+ * product, every product is accumulated in FP32. */
+#define RBF_MLP_NFEAT 32
+#define RBF_MLP_NPARAM 6337
+
+/* Features of every binned centre (after rbf_bin or rbf_bin_tiles): row j of feat (DEVICE,
+ * M x 32 floats, caller's centre order, 16-byte aligned) holds, for the 16 annuli
+ * k/16 <= ||x_i - xi_j|| / R < (k+1)/16 of the support, the fraction of the support's
+ * points in annulus k (0..15) and their mean height divided by sigma (16..31; 0 when
+ * empty), sigma = sqrt(mean h^2) over the system's (the tile's) points. The annulus of a
+ * point is that of an FP64 evaluation of sqrt(dx*dx + dy*dy) / R. sigma: DEVICE array of T
+ * (batched) or 1 doubles, may be NULL. Asynchronous. */
+rbf_status rbf_features(rbf_ctx* ctx, float* feat, double* sigma, void* stream);
+
+/* y[i] = network(feat row i) for i < n (DEVICE arrays; feat 16-byte aligned). The context
+ * supplies the device and the launch accounting only. Asynchronous. */
+rbf_status rbf_mlp_forward(rbf_ctx* ctx, const float* params, const float* feat, int64_t n,
+                           float* y, void* stream);
+
+/* One training step on the minibatch of n samples: sample i is feature row idx[i] (or i when
+ * idx is NULL) of feat with target target[idx[i]] (DEVICE arrays). Computes the loss
+ * mean (y - t)^2 and its gradient by back-propagation (with respect to the BF16-rounded
+ * weights as they enter the products, and the biases); with step >= 1 also applies Adam
+ * step number `step` (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr) to params, m and v
+ * (DEVICE, RBF_MLP_NPARAM floats each; m = v = 0 before step 1); with step = 0 nothing is
+ * updated. grad (DEVICE, RBF_MLP_NPARAM floats) and loss (DEVICE, 1 double) receive the
+ * gradient and the loss when not NULL. The gradient is summed in a fixed order
+ * (deterministic). Asynchronous. */
+rbf_status rbf_mlp_train_step(rbf_ctx* ctx, float* params, float* m, float* v, int step,
+                              double lr, const float* feat, const float* target,
+                              const int32_t* idx, int64_t n, float* grad, double* loss,
+                              void* stream);
+
+/* The warm start c0 (DEVICE, M doubles, caller's order) of the binned system:
+ * c0_j = sigma * network(features of centre j), sigma per tile for a batch. Asynchronous. */
+rbf_status rbf_warm_start(rbf_ctx* ctx, const float* params, double* c0, void* stream);
+
 /* Evaluation with no allocation at all (the paper has no counterpart; this is a service to
  * callers that cannot allocate device memory where they need the surface -- e.g. code that
  * runs while its own memory pool is locked or inside a fixed device-memory budget, or a

@@ -223,6 +223,49 @@ class Context:
         self._check(s, "rbf_eval_tiles_grid")
         return f
 
+    # -- learned warm start ----------------------------------------------------------------
+    def features(self, out=None, stream=None):
+        """Radial features of every centre (caller order, (M, 32) float32 CUDA tensor) and the
+        height scale(s) sigma (T or 1 values)."""
+        torch = _torch()
+        dev = f"cuda:{self.device}"
+        f = out if out is not None else torch.empty((self.M, 32), dtype=torch.float32, device=dev)
+        sig = torch.empty(max(self.T, 1), dtype=torch.float64, device=dev)
+        s = self.lib.rbf_features(self._h, C.c_void_p(f.data_ptr()), C.c_void_p(sig.data_ptr()),
+                                  self._stream(stream))
+        self._check(s, "rbf_features")
+        return f, sig
+
+    def mlp_forward(self, params, feat, out=None, stream=None):
+        torch = _torch()
+        n = int(feat.shape[0])
+        y = out if out is not None else torch.empty(n, dtype=torch.float32, device=feat.device)
+        s = self.lib.rbf_mlp_forward(self._h, C.c_void_p(params.data_ptr()),
+                                     C.c_void_p(feat.data_ptr()), n, C.c_void_p(y.data_ptr()),
+                                     self._stream(stream))
+        self._check(s, "rbf_mlp_forward")
+        return y
+
+    def mlp_train_step(self, params, m, v, step: int, lr: float, feat, target, idx=None,
+                       n=None, grad=None, loss=None, stream=None):
+        """One minibatch step (step 0: gradient only). idx: int32 CUDA tensor of sample rows."""
+        n = int(idx.numel() if idx is not None else (n if n is not None else feat.shape[0]))
+        ptr = lambda t: C.c_void_p(t.data_ptr() if t is not None else 0)  # noqa: E731
+        s = self.lib.rbf_mlp_train_step(self._h, ptr(params), ptr(m), ptr(v), int(step),
+                                        float(lr), ptr(feat), ptr(target), ptr(idx), n, ptr(grad),
+                                        ptr(loss), self._stream(stream))
+        self._check(s, "rbf_mlp_train_step")
+
+    def warm_start(self, params, out=None, stream=None):
+        """c0 = sigma * network(features) for every centre (caller order, float64)."""
+        torch = _torch()
+        c0 = out if out is not None else torch.empty(self.M, dtype=torch.float64,
+                                                     device=f"cuda:{self.device}")
+        s = self.lib.rbf_warm_start(self._h, C.c_void_p(params.data_ptr()),
+                                    C.c_void_p(c0.data_ptr()), self._stream(stream))
+        self._check(s, "rbf_warm_start")
+        return c0
+
     def autotune(self, stream=None):
         """Time the batched CG loop's launch configurations and keep the fastest."""
         self._check(self.lib.rbf_autotune(self._h, self._stream(stream)), "rbf_autotune")

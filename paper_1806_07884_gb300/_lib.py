@@ -65,6 +65,10 @@ SIGNATURES = {
     "rbf_autotune": (_I, [_P, _P]),
     "rbf_eval_tiles": (_I, [_P, _P, _P, _P, C.POINTER(_I64), _P, _P]),
     "rbf_eval_tiles_grid": (_I, [_P, _P, _I, _I, _P, _P]),
+    "rbf_features": (_I, [_P, _P, _P, _P]),
+    "rbf_mlp_forward": (_I, [_P, _P, _P, _I64, _P, _P]),
+    "rbf_mlp_train_step": (_I, [_P, _P, _P, _P, _I, _D, _P, _P, _P, _I64, _P, _P, _P]),
+    "rbf_warm_start": (_I, [_P, _P, _P, _P]),
     "rbf_get_tuning": (_I, [_P, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I), C.POINTER(_D)]),
 }
 

@@ -150,7 +150,8 @@ rbf_status rbf_destroy(rbf_ctx* ctx) {
                        &ctx->work, &ctx->scan_tmp, &ctx->stats, &ctx->bvals, &ctx->bvec,
                        &ctx->support, &ctx->x, &ctx->r, &ctx->cgv[0], &ctx->cgv[1],
                        &ctx->dinv, &ctx->dinv32, &ctx->bjinv, &ctx->bjinv32, &ctx->crow, &ctx->cdesc,
-                       &ctx->partial, &ctx->scal, &ctx->csort};
+                       &ctx->partial, &ctx->scal, &ctx->csort, &ctx->sigma, &ctx->feat,
+                       &ctx->mlp_part};
     for (rbf_buf* b : bufs) release(ctx, *b);
     if (ctx->hpinned) cudaFreeHost(ctx->hpinned);
     delete ctx;
@@ -280,6 +281,43 @@ rbf_status rbf_eval_tiles_grid(rbf_ctx* ctx, const double* c, int nx, int ny, do
     if (nx < 1 || ny < 1 || !c || !f) return set_err(ctx, RBF_ERR_ARG, "bad arguments");
     DeviceGuard dg(ctx->device);
     return eval_tiles_run(ctx, c, nullptr, nullptr, nullptr, nx, ny, f, as_stream(stream));
+}
+
+rbf_status rbf_features(rbf_ctx* ctx, float* feat, double* sigma, void* stream) {
+    if (!ctx) return RBF_ERR_ARG;
+    if (!ctx->binned) return set_err(ctx, RBF_ERR_ARG, "rbf_features before rbf_bin / rbf_bin_tiles");
+    if (!feat) return set_err(ctx, RBF_ERR_ARG, "null feat");
+    DeviceGuard dg(ctx->device);
+    return features_run(ctx, feat, sigma, as_stream(stream));
+}
+
+rbf_status rbf_mlp_forward(rbf_ctx* ctx, const float* params, const float* feat, int64_t n,
+                           float* y, void* stream) {
+    if (!ctx) return RBF_ERR_ARG;
+    if (n < 0 || (n > 0 && (!params || !feat || !y))) return set_err(ctx, RBF_ERR_ARG, "bad arguments");
+    if (reinterpret_cast<uintptr_t>(feat) % 16) return set_err(ctx, RBF_ERR_ARG, "feat must be 16-byte aligned");
+    DeviceGuard dg(ctx->device);
+    return mlp_forward_run(ctx, params, feat, n, y, as_stream(stream));
+}
+
+rbf_status rbf_mlp_train_step(rbf_ctx* ctx, float* params, float* m, float* v, int step, double lr,
+                              const float* feat, const float* target, const int32_t* idx,
+                              int64_t n, float* grad, double* loss, void* stream) {
+    if (!ctx) return RBF_ERR_ARG;
+    if (n < 1 || !params || !feat || !target) return set_err(ctx, RBF_ERR_ARG, "bad arguments");
+    if (step < 0 || (step > 0 && (!m || !v || !(lr > 0.0))))
+        return set_err(ctx, RBF_ERR_ARG, "an Adam step needs m, v and lr > 0");
+    DeviceGuard dg(ctx->device);
+    return mlp_step_run(ctx, params, m, v, step, lr, feat, target, idx, n, grad, loss,
+                        as_stream(stream));
+}
+
+rbf_status rbf_warm_start(rbf_ctx* ctx, const float* params, double* c0, void* stream) {
+    if (!ctx) return RBF_ERR_ARG;
+    if (!ctx->binned) return set_err(ctx, RBF_ERR_ARG, "rbf_warm_start before rbf_bin / rbf_bin_tiles");
+    if (!params || !c0) return set_err(ctx, RBF_ERR_ARG, "null pointer argument");
+    DeviceGuard dg(ctx->device);
+    return warm_start_run(ctx, params, c0, as_stream(stream));
 }
 
 rbf_status rbf_autotune(rbf_ctx* ctx, void* stream) {

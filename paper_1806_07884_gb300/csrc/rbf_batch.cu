@@ -209,15 +209,15 @@ __global__ void k_cell_compact(int ncell, const int* __restrict__ cstart,
 // Warp segmented sum of NV values keyed by tile: keys are equal over contiguous runs of lanes
 // (rows are in tile order). Afterwards the first lane of each run holds the run's sums;
 // returns true in those lanes.
-template <int NV>
-__device__ __forceinline__ bool warp_segsum(int key, double (&v)[NV]) {
+template <int NV, typename TV>
+__device__ __forceinline__ bool warp_segsum(int key, TV (&v)[NV]) {
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const int ok = __shfl_down_sync(kFull, key, o);
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
-            const double ov = __shfl_down_sync(kFull, v[k], o);
+            const TV ov = __shfl_down_sync(kFull, v[k], o);
             if (lane + o < 32 && ok == key) v[k] += ov;
         }
     }
@@ -229,13 +229,14 @@ __device__ __forceinline__ bool warp_segsum(int key, double (&v)[NV]) {
 // (key = its row's tile, INT_MAX for none) into dst[k][tile]: warp segmented sums, shared
 // atomics per tile, then one global atomic per tile and value. sred: [NV][NT] shared doubles
 // zeroed for j < span before the call (with a barrier in between).
-template <int NV, int NT>
-__device__ __forceinline__ void tile_reduce(int key, double (&v)[NV], int t0, int span,
+template <int NV, int NT, typename TV>
+__device__ __forceinline__ void tile_reduce(int key, TV (&v)[NV], int t0, int span,
                                             double (*sred)[NT], double* const (&dst)[NV]) {
-    if (warp_segsum<NV>(key, v) && key != INT_MAX) {
+    // warp sums in the values' own type (FP32 for the FP32 solver), totals in FP64
+    if (warp_segsum<NV, TV>(key, v) && key != INT_MAX) {
 #pragma unroll
         for (int k = 0; k < NV; ++k)
-            if (v[k] != 0.0) atomicAdd(&sred[k][key - t0], v[k]);
+            if (v[k] != TV(0)) atomicAdd(&sred[k][key - t0], double(v[k]));
     }
     __syncthreads();
     for (int j = threadIdx.x; j < span; j += NT) {
@@ -276,7 +277,7 @@ __global__ void __launch_bounds__(256)
         a[1] = pinned ? 1.0 : 0.0;
     }
     double* const dst[2] = {out2, npin};
-    tile_reduce<2, NT>(key, a, t0, span, sred, dst);
+    tile_reduce<2, NT, double>(key, a, t0, span, sred, dst);
 }
 
 // x = x + scale_t d on unpinned rows, x = 0 on pinned rows.
@@ -381,7 +382,7 @@ __global__ void k_eval_tiles_grid(Binned bd, const TileDev* __restrict__ td,
 // so a warp adds its delta to the tile's total once per run of cells). Also zeroes the
 // per-tile sums the next update kernel accumulates (parity P ^ 1).
 template <typename T>
-__global__ void __launch_bounds__(kSpmvWarps * 32, sizeof(T) == 4 ? 3 : 1)
+__global__ void __launch_bounds__(kSpmvWarps * 32, sizeof(T) == 4 ? 2 : 1)
     k_bcg_spmv(Binned bd, const int* __restrict__ clist, int ncl, int chunk,
                const T* __restrict__ B, const T* __restrict__ u, T* __restrict__ w, int P,
                int ntile, TileCg tc) {
@@ -400,23 +401,23 @@ __global__ void __launch_bounds__(kSpmvWarps * 32, sizeof(T) == 4 ? 3 : 1)
     const long long step = (long long)gridDim.x * kSpmvWarps * chunk;
     int cur = -1;
     bool run = false;
-    double acc = 0.0;
+    T acc = T(0);        // this lane's share of the current tile's delta (warp sums in T)
     for (long long base = gw * chunk; base < ncl; base += step) {
         const int e = int(min(base + chunk, (long long)ncl));
         for (int k = int(base); k < e; ++k) {
             const CellDesc cd = load_desc(bd.cdesc + __ldg(clist + k));
             if (cd.pad != cur) {            // warp-uniform
-                const double s = warp_sum_d(acc);
-                if (lane == 0 && cur >= 0 && s != 0.0) atomicAdd(&dlP[cur], s);
-                acc = 0.0;
+                const T s = warp_sum<T>(acc);
+                if (lane == 0 && cur >= 0 && s != T(0)) atomicAdd(&dlP[cur], double(s));
+                acc = T(0);
                 cur = cd.pad;
                 run = slP[cur].state == kRunning;
             }
-            if (run) acc += spmv_cell<T>(cd, B, u, w, lane);
+            if (run) acc += spmv_cell<T, (sizeof(T) == 4 ? kSpmvGroupHbm : kSpmvGroupL2)>(cd, B, u, w, lane);
         }
     }
-    const double s = warp_sum_d(acc);
-    if (lane == 0 && cur >= 0 && s != 0.0) atomicAdd(&dlP[cur], s);
+    const T s = warp_sum<T>(acc);
+    if (lane == 0 && cur >= 0 && s != T(0)) atomicAdd(&dlP[cur], double(s));
 }
 
 // One thread per row, one block per NT rows. Prologue: for each tile of the block's rows,
@@ -428,7 +429,7 @@ __global__ void __launch_bounds__(kSpmvWarps * 32, sizeof(T) == 4 ? 3 : 1)
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT)
     k_bcg_update(Binned bd, CgVec<T> v, int P, TileCg tc) {
-    __shared__ double s_alpha[NT], s_beta[NT];
+    __shared__ T s_alpha[NT], s_beta[NT];
     __shared__ double sred[2][NT];
     __shared__ int s_go[NT];
     const TSlot* __restrict__ slP = P ? tc.sl[1] : tc.sl[0];
@@ -484,8 +485,8 @@ __global__ void __launch_bounds__(NT)
                 atomicAdd(&tc.bs->ndone, 1u);
             }
         }
-        s_alpha[j] = alpha;
-        s_beta[j] = beta;
+        s_alpha[j] = T(alpha);
+        s_beta[j] = T(beta);
         s_go[j] = state == kRunning;
         sred[0][j] = 0.0;
         sred[1][j] = 0.0;
@@ -499,32 +500,46 @@ __global__ void __launch_bounds__(NT)
     T* __restrict__ wQ = P ? v.w[0] : v.w[1];
     const int i = i0 + threadIdx.x;
     int key = INT_MAX;
-    double acc[2] = {0.0, 0.0};
+    T acc[2] = {T(0), T(0)};
+    // new residuals of the block's rows, for the block-Jacobi step (rows of a cell outside the
+    // block are recomputed with the same operations)
+    __shared__ T rsm[NT];
+    bool go = false;
+    int4 cm = make_int4(0, 0, 0, 0);
+    T ta = T(0), tb = T(0), di = T(0), ri = T(0);
     if (i < i1) {
-        const int4 cm = bd.crow[i];
+        cm = bd.crow[i];
         key = cm.w;
         const int j = cm.w - t0;
-        if (s_go[j]) {
-            const T ta = T(s_alpha[j]), tb = T(s_beta[j]);
-            const T di = v.dinv[i];
+        go = s_go[j] != 0;
+        if (go) {
+            ta = s_alpha[j];
+            tb = s_beta[j];
+            di = v.dinv[i];
             const T wi = di == T(0) ? T(0) : wP[i];
             const T si = fma(tb, sP[i], wi);
             const T pi = fma(tb, v.p[i], v.u[i]);
-            const T ri = di == T(0) ? T(0) : fma(-ta, si, rP[i]);
-            const T ui = apply_prec<T>(bd, v.bjinv, cm, i, di, ri,
-                                       [&](int jj) { return next_r(rP[jj], sP[jj], wP[jj], ta, tb); });
+            ri = di == T(0) ? T(0) : fma(-ta, si, rP[i]);
             sQ[i] = si;
             v.p[i] = pi;
             v.x[i] = fma(ta, pi, v.x[i]);
             rQ[i] = ri;
-            v.u[i] = ui;
             wQ[i] = T(0);
-            acc[0] = double(ri * ui);
-            acc[1] = double(ri * ri);
         }
     }
+    rsm[threadIdx.x] = ri;
+    __syncthreads();
+    if (go) {
+        const T ui = apply_prec<T>(bd, v.bjinv, cm, i, di, ri, [&](int jj) {
+            const int o = jj - i0;
+            return o >= 0 && o < NT ? rsm[o] : next_r(rP[jj], sP[jj], wP[jj], ta, tb);
+        });
+        v.u[i] = ui;
+        acc[0] = ri * ui;
+        acc[1] = ri * ri;
+    }
     double* const dst[2] = {gQ, rrQ};
-    tile_reduce<2, NT>(key, acc, t0, span, sred, dst);
+    tile_reduce<2, NT, T>(key, acc, t0, span, sred, dst);
 }
 
 // Start of a batched solve of B x = bscale_t b per tile (tiles with bscale_t = 0 take no
@@ -571,7 +586,7 @@ __global__ void __launch_bounds__(256)
         acc[2] = double(bi) * double(bi);
     }
     double* const dst[3] = {tc.g[0], tc.rr[0], tc.bb};
-    tile_reduce<3, NT>(key, acc, t0, span, sred, dst);
+    tile_reduce<3, NT, double>(key, acc, t0, span, sred, dst);
 }
 
 __global__ void k_bcg_cond(const BatchScal* __restrict__ bs, cudaGraphConditionalHandle h) {

@@ -16,6 +16,11 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kItersPerBody = 4;
 // Vectors of the CG workspace: x, u, p, r0, r1, s0, s1, w0, w1.
 constexpr int kCgVecs = 9;
+// Rows of a cell's block whose values one SpMV lane loads together (16-byte loads in flight):
+// 4 suits a B that stays in L2 at three CTAs per SM, 8 an HBM-resident B at two CTAs per SM
+// (measured).
+constexpr int kSpmvGroupL2 = 4;
+constexpr int kSpmvGroupHbm = 8;
 
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
@@ -41,7 +46,32 @@ __device__ __forceinline__ void block_sum(double (&v)[NV]) {
     __syncthreads();
 }
 
-// Stores this block's NV partial sums; returns true in the single last block to finish,
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+// Block-wide sums of NV values of type T: each warp sums in T (FP32 for the FP32 solver,
+// keeping the slow FP64 pipe out of the per-row work), the warp totals are added in FP64.
+// The result is valid in thread 0.
+template <int NV, typename T>
+__device__ __forceinline__ void block_sum_t(const T (&v)[NV], double (&out)[NV]) {
+    __shared__ double red[NV][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        const T s = warp_sum<T>(v[k]);
+        if (lane == 0) red[k][w] = double(s);
+    }
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) out[k] = warp_sum_d(lane < nw ? red[k][lane] : 0.0);
+    }
+    __syncthreads();
+}
 
 template <typename T>
 __device__ __forceinline__ T ldcg(const T* p) { return __ldcg(p); }
@@ -113,12 +143,12 @@ __device__ __forceinline__ T butterfly16(T (&v)[16], int lane) {
 //   row sums    y[s] += sum_t B[s][t] x[t]   (16 rows in registers, butterfly reduction)
 //   column sums y[t] += sum_s B[s][t] x[s]   for t outside the diagonal block c x c
 //   (the diagonal block is stored in full, so its transposed half is already in the rows)
-// and are added with atomics. Returns this lane's share of x^T B x over the cell's entries:
+// and are added with atomics. Returns this lane's share (in T) of x^T B x over the cell's entries:
 // sum_s x[s] rowsum[s] + sum_t colsum[t] x[t].
-template <typename T>
-__device__ double spmv_cell(const CellDesc& cd, const T* __restrict__ B, const T* x, T* y, int lane) {
+template <typename T, int G>
+__device__ T spmv_cell(const CellDesc& cd, const T* __restrict__ B, const T* x, T* y, int lane) {
     const int cs = cd.cs, m = cd.m;
-    if (m == 0) return 0.0;
+    if (m == 0) return T(0);
     RowSeg sg;
     sg.s0 = cd.s0;
     sg.l0 = cd.l0;
@@ -146,18 +176,26 @@ __device__ double spmv_cell(const CellDesc& cd, const T* __restrict__ B, const T
                 xt[q] = t[q] >= 0 ? ldcg(x + t[q]) : T(0);
                 ca[q] = T(0);
             }
-            const T* rb = Bc + (long long)j0 * lp + kb;
+            // Rows are streamed in groups of G whose loads are all issued before any of them
+            // is used, so each lane keeps G 16-byte loads in flight. Loads are unconditional:
+            // rows past the block's last (i >= mm) re-read row mm-1 and lanes past the row's
+            // end (not active) read the row's start -- both valid addresses -- and contribute
+            // nothing (x_i = 0 for i >= mm, x_t = 0 and no column update when not active).
+            const T* rb = Bc + (long long)j0 * lp + (active ? kb : 0);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                if (i < mm) {                 // warp-uniform
-                    const T xi = __shfl_sync(kFull, xs_lane, i);
-                    if (active) {
-                        T v[4];
-                        load4(rb + (long long)i * lp, v);
+            for (int g0 = 0; g0 < 16; g0 += G) {
+                if (g0 < mm) {                // warp-uniform
+                    T v[G][4];
+#pragma unroll
+                    for (int i = 0; i < G; ++i)
+                        load4(rb + (long long)min(g0 + i, mm - 1) * lp, v[i]);
+#pragma unroll
+                    for (int i = 0; i < G; ++i) {
+                        const T xi = __shfl_sync(kFull, xs_lane, g0 + i);
 #pragma unroll
                         for (int q = 0; q < 4; ++q) {
-                            rp[i] = fma(v[q], xt[q], rp[i]);
-                            ca[q] = fma(v[q], xi, ca[q]);
+                            rp[g0 + i] = fma(v[i][q], xt[q], rp[g0 + i]);
+                            ca[q] = fma(v[i][q], xi, ca[q]);
                         }
                     }
                 }
@@ -178,7 +216,7 @@ __device__ double spmv_cell(const CellDesc& cd, const T* __restrict__ B, const T
             dot = fma(tot, xr, dot);
         }
     }
-    return double(dot);
+    return dot;
 }
 
 __device__ __forceinline__ CellDesc load_desc(const CellDesc* d) {

@@ -113,6 +113,11 @@ struct rbf_ctx {
         int T = 0, M = 0, ncl = 0, bps = 0, chunk = 0, nt = 0;
     };
     TileGraph bt_graph[2];
+
+    // ---- learned warm start (rbf_features / rbf_warm_start / rbf_mlp_*) ----
+    rbf_buf sigma;                   // [T or 1] height scales, then 2 T sums
+    rbf_buf feat;                    // [M x 32] features and [M] network outputs
+    rbf_buf mlp_part;                // per-block partial gradients
 };
 
 namespace rbf {
@@ -147,6 +152,15 @@ rbf_status autotune_run(rbf_ctx* ctx, cudaStream_t st);
 rbf_status bench_tiles_run(rbf_ctx* ctx, int reps, bool spmv_only, cudaStream_t st);
 rbf_status eval_tiles_run(rbf_ctx* ctx, const double* c, const double* qx, const double* qy,
                           const int64_t* qoff, int nx, int ny, double* f, cudaStream_t st);
+
+// rbf_mlp.cu
+rbf_status features_run(rbf_ctx* ctx, float* feat, double* sigma_out, cudaStream_t st);
+rbf_status mlp_forward_run(rbf_ctx* ctx, const float* params, const float* feat, int64_t n, float* y,
+                           cudaStream_t st);
+rbf_status warm_start_run(rbf_ctx* ctx, const float* params, double* c0, cudaStream_t st);
+rbf_status mlp_step_run(rbf_ctx* ctx, float* params, float* m, float* v, int step, double lr,
+                        const float* feat, const float* target, const int* idx, int64_t n,
+                        float* grad, double* loss, cudaStream_t st);
 
 // rbf_assemble.cu
 rbf_status assemble_run(rbf_ctx* ctx, int kernel, int prec, cudaStream_t st);

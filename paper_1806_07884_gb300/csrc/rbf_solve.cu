@@ -56,6 +56,7 @@ namespace {
 
 constexpr int kVecThreads = 256;
 
+// Stores this block's NV partial sums; returns true in the single last block to finish,
 // whose thread 0 then holds the totals, summed in block order, in tot[].
 template <int NV>
 __device__ bool last_block_total(double (&v)[NV], double* partial, unsigned int* ticket,
@@ -93,7 +94,7 @@ __global__ void __launch_bounds__(kSpmvWarps * 32, sizeof(T) == 4 ? 3 : 1)
     const int lane = threadIdx.x & 31;
     const int nw = gridDim.x * kSpmvWarps;
     for (int c = blockIdx.x * kSpmvWarps + (threadIdx.x >> 5); c < bd.g.ncell; c += nw)
-        spmv_cell<T>(load_desc(bd.cdesc + c), B, x, y, lane);
+        spmv_cell<T, kSpmvGroupL2>(load_desc(bd.cdesc + c), B, x, y, lane);
 }
 
 
@@ -113,10 +114,10 @@ __global__ void __launch_bounds__(kSpmvWarps * 32, sizeof(T) == 4 ? 3 : 1)
     const int lane = threadIdx.x & 31;
     const int gw = blockIdx.x * kSpmvWarps + (threadIdx.x >> 5);
     const int nw = gridDim.x * kSpmvWarps;
-    double d = 0.0;
-    for (int c = gw; c < bd.g.ncell; c += nw) d += spmv_cell<T>(load_desc(bd.cdesc + c), B, u, w, lane);
-    d = warp_sum_d(d);
-    if (lane == 0 && d != 0.0) atomicAdd(&sc->acc_delta[P][gw & (kAccSlots - 1)], d);
+    T d = T(0);
+    for (int c = gw; c < bd.g.ncell; c += nw) d += spmv_cell<T, kSpmvGroupL2>(load_desc(bd.cdesc + c), B, u, w, lane);
+    d = warp_sum<T>(d);
+    if (lane == 0 && d != T(0)) atomicAdd(&sc->acc_delta[P][gw & (kAccSlots - 1)], double(d));
 }
 
 // partials of gamma_{k+1} and (r_{k+1}, r_{k+1}). P is the parity k & 1.
@@ -188,40 +189,55 @@ __global__ void __launch_bounds__(kVecThreads)
     }
     __syncthreads();
     if (!s_go) return;
-    const double alpha = s_ab[0], beta = s_ab[1];
-    const T ta = T(alpha), tb = T(beta);
+    const T ta = T(s_ab[0]), tb = T(s_ab[1]);
     const T* __restrict__ rP = P ? v.r[1] : v.r[0];
     const T* __restrict__ sP = P ? v.s[1] : v.s[0];
     const T* __restrict__ wP = P ? v.w[1] : v.w[0];
     T* __restrict__ rQ = P ? v.r[0] : v.r[1];
     T* __restrict__ sQ = P ? v.s[0] : v.s[1];
     T* __restrict__ wQ = P ? v.w[0] : v.w[1];
-    double acc[2] = {0.0, 0.0};
+    T acc[2] = {T(0), T(0)};
     const int M = bd.M;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) {
-        const T di = v.dinv[i];
-        const T wi = di == T(0) ? T(0) : wP[i];
-        const T si = fma(tb, sP[i], wi);
-        const T pi = fma(tb, v.p[i], v.u[i]);
-        const T ri = di == T(0) ? T(0) : fma(-ta, si, rP[i]);
-        const int4 cm = bd.crow[i];
-        // rows of pinned centres carry zeros in the inverse block, so r_j need no mask
-        const T ui = apply_prec<T>(bd, v.bjinv, cm, i, di, ri,
-                                   [&](int j) { return next_r(rP[j], sP[j], wP[j], ta, tb); });
-        sQ[i] = si;
-        v.p[i] = pi;
-        v.x[i] = fma(ta, pi, v.x[i]);
-        rQ[i] = ri;
-        v.u[i] = ui;
-        wQ[i] = T(0);
-        acc[0] += double(ri * ui);
-        acc[1] += double(ri * ri);
+    // The new residual of each row of the chunk is kept in shared memory for the block-Jacobi
+    // step; rows of a cell outside the chunk are recomputed with the same operations.
+    __shared__ T rsm[kVecThreads];
+    for (int base = blockIdx.x * kVecThreads; base < M; base += gridDim.x * kVecThreads) {
+        const int i = base + threadIdx.x;
+        const bool valid = i < M;
+        T di = T(0), ri = T(0);
+        if (valid) {
+            di = v.dinv[i];
+            const T wi = di == T(0) ? T(0) : wP[i];
+            const T si = fma(tb, sP[i], wi);
+            const T pi = fma(tb, v.p[i], v.u[i]);
+            ri = di == T(0) ? T(0) : fma(-ta, si, rP[i]);
+            sQ[i] = si;
+            v.p[i] = pi;
+            v.x[i] = fma(ta, pi, v.x[i]);
+            rQ[i] = ri;
+            wQ[i] = T(0);
+        }
+        rsm[threadIdx.x] = ri;
+        __syncthreads();
+        if (valid) {
+            const int4 cm = bd.crow[i];
+            // rows of pinned centres carry zeros in the inverse block, so r_j need no mask
+            const T ui = apply_prec<T>(bd, v.bjinv, cm, i, di, ri, [&](int j) {
+                const int o = j - base;
+                return o >= 0 && o < kVecThreads ? rsm[o] : next_r(rP[j], sP[j], wP[j], ta, tb);
+            });
+            v.u[i] = ui;
+            acc[0] = fma(ri, ui, acc[0]);
+            acc[1] = fma(ri, ri, acc[1]);
+        }
+        __syncthreads();
     }
-    block_sum<2>(acc);
+    double tot[2];
+    block_sum_t<2, T>(acc, tot);
     if (threadIdx.x == 0) {
         double* pb = pbuf + size_t(P ^ 1) * 2 * nblk;
-        pb[2 * blockIdx.x] = acc[0];
-        pb[2 * blockIdx.x + 1] = acc[1];
+        pb[2 * blockIdx.x] = tot[0];
+        pb[2 * blockIdx.x + 1] = tot[1];
     }
 }
 
