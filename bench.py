@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--quiet-extra", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-learned", dest="learned", action="store_false",
+                    help="cold start instead of the learned warm start in the timed step")
     ap.add_argument("--tiles", type=int, default=512)
     ap.add_argument("--batched-only", action="store_true",
                     help="run only the batched workload and print its object (profiling)")
@@ -160,7 +162,7 @@ def run_reference(args):
     value = N / sec
     sample = (f"oracle fit (kd-tree, scipy A^T A, Jacobi-PCG tol {args.tol:g}) + {pb.eval_n}^2 grid "
               f"evaluation on the terrain workload at N={N}, M={M} (same N/M and K as 1M x 100k)")
-    line = {"impl": "reference", "metric": "points fitted/s at 1e-6 rel. error", "value": value,
+    line = {"impl": "reference", "metric": "points fitted/s at 1e-6 rel. error, learned+FP32 vs plain FP64", "value": value,
             "unit": "points/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -219,6 +221,34 @@ def bench_batched(args, rank, dev, stream, flush, hbm, peak_source):
     ms, info, tinfo = timed(args.prec, args.tol, max(2, min(args.steps, 3)))
     launches = (ctx.launch_count() - launches0) // max(2, min(args.steps, 3))
     c_fast = cbuf.clone()
+    learned = None
+    if args.learned:
+        from paper_1806_07884_gb300 import warmstart
+        wp = warmstart.load_params(device=dev.index)
+        c0b = torch.empty(Mtot, dtype=torch.float64, device=dev)
+
+        def lstep():
+            ctx.bin_tiles(tiles, *d)
+            ctx.assemble("w31", args.prec)
+            c0 = ctx.warm_start(wp, out=c0b)
+            return ctx.solve_tiles(tol=args.tol, maxit=20000, c0=c0, out=cbuf)
+
+        lstep()
+        lms = []
+        for _ in range(2):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, linfo, ltinfo = lstep()
+            e1.record(stream)
+            e1.synchronize()
+            lms.append(e0.elapsed_time(e1))
+        learned = {"value": Ntot / (statistics.mean(lms) * 1e-3),
+                   "ms_per_step": round(statistics.mean(lms), 3),
+                   "iterations_max": linfo["iterations"],
+                   "iterations_mean": round(float(np.mean([t["iterations"] for t in ltinfo])), 1),
+                   "all_converged": all(t["status"] == 0 for t in ltinfo)}
     tune = ctx.tuning()
     # phases of one step
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
@@ -257,7 +287,7 @@ def bench_batched(args, rank, dev, stream, flush, hbm, peak_source):
            "iterations_max": info["iterations"], "refinements_max": info["refinements"],
            "iterations_mean": round(float(np.mean([t["iterations"] for t in tinfo])), 1),
            "all_converged": all(t["status"] == 0 for t in tinfo), "promoted": info["promoted"],
-           "phases_ms": phases, "tuning": tune, "roofline": roof}
+           "phases_ms": phases, "tuning": tune, "roofline": roof, "learned_start": learned}
     if not args.no_fp64_compare:
         ms64, info64, _ = timed("fp64", args.tol, 1)
         out["fp64_path"] = {"value": Ntot / (ms64 * 1e-3), "ms_per_step": round(ms64, 3),
@@ -330,10 +360,15 @@ def main():
     ctx = pkg.Context(local)
     stream = torch.cuda.current_stream(dev)
 
-    def step(inp, prec=args.prec, tol=args.tol):
+    from paper_1806_07884_gb300 import warmstart
+    wparams = warmstart.load_params(device=local) if args.learned else None
+    c0buf = torch.empty(M, dtype=torch.float64, device=dev)
+
+    def step(inp, prec=args.prec, tol=args.tol, learned=args.learned):
         ctx.bin(inp["cx"], inp["cy"], inp["px"], inp["py"], inp["h"], pb.R, pb.bbox)
         ctx.assemble(pb.kernel, prec)
-        c, info = ctx.solve(tol=tol, maxit=20000, out=cbuf)
+        c0 = ctx.warm_start(wparams, out=c0buf) if learned else None
+        c, info = ctx.solve(tol=tol, maxit=20000, c0=c0, out=cbuf)
         ctx.eval_grid(c, n, n, out=fbuf)
         return info
 
@@ -384,13 +419,18 @@ def main():
     ev[1].record(stream)
     ctx.assemble(pb.kernel, args.prec)
     ev[2].record(stream)
-    c, info = ctx.solve(tol=args.tol, maxit=20000, out=cbuf)
+    c0 = ctx.warm_start(wparams, out=c0buf) if args.learned else None
+    ev.append(torch.cuda.Event(enable_timing=True))
+    ev[5].record(stream)
+    c, info = ctx.solve(tol=args.tol, maxit=20000, c0=c0, out=cbuf)
     ev[3].record(stream)
     ctx.eval_grid(c, n, n, out=fbuf)
     ev[4].record(stream)
     torch.cuda.synchronize()
-    for k, name in enumerate(["bin", "assemble", "solve", "eval"]):
-        phases[name] = round(ev[k].elapsed_time(ev[k + 1]), 4)
+    phases = {"bin": ev[0].elapsed_time(ev[1]), "assemble": ev[1].elapsed_time(ev[2]),
+              "warm_start": ev[2].elapsed_time(ev[5]), "solve": ev[5].elapsed_time(ev[3]),
+              "eval": ev[3].elapsed_time(ev[4])}
+    phases = {k: round(v, 4) for k, v in phases.items()}
 
     # ---- roofline of the dominant kernel: the solver's SpMV, timed on its stream
     lay = ctx.layout()
@@ -425,6 +465,24 @@ def main():
     f_fast = fbuf.clone()
     acc = {}
     fp64 = None
+    other = None
+    if not args.no_fp64_compare:
+        # the same precision with the other start (cold if the timed step is learned)
+        o_ms = []
+        for _ in range(max(2, min(args.steps, 3))):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = torch.cuda.Event(enable_timing=True)
+            t1 = torch.cuda.Event(enable_timing=True)
+            t0.record(stream)
+            info_o = step(d, learned=not args.learned)
+            t1.record(stream)
+            torch.cuda.synchronize()
+            o_ms.append(t0.elapsed_time(t1))
+        oms = statistics.mean(o_ms)
+        other = {"start": "cold" if args.learned else "learned", "value": N / (oms * 1e-3),
+                 "ms_per_step": round(oms, 3), "iterations": info_o["iterations"],
+                 "refinements": info_o["refinements"]}
     if not args.no_fp64_compare:
         flush.zero_()
         torch.cuda.synchronize()
@@ -489,19 +547,23 @@ def main():
     if rank == 0:
         last = infos[-1]
         line = {
-            "metric": "points fitted/s at 1e-6 rel. error",
+            "metric": "points fitted/s at 1e-6 rel. error, learned+FP32 vs plain FP64",
             "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32+f64" if args.prec == "fp32_refine" else "f64",
+            "dtype": ("bf16/f32 net + " if args.learned else "") +
+                     ("f32+f64" if args.prec == "fp32_refine" else "f64"),
             "data": "synthetic",
             "config": {"workload": f"terrain {N} points x {M} Halton centres, Wendland phi_3,1, "
                                    f"K=30, {n}x{n} eval grid",
                        "N": N, "M": M, "kernel": pb.kernel, "prec": args.prec, "tol": args.tol,
-                       "warm_start": "none", "l2": "flushed before each step (512 MiB write)",
+                       "warm_start": "learned (32-64-64-1 network, paper_1806_07884_gb300/"
+                                     "warmstart_w31.npy)" if args.learned else "none",
+                       "l2": "flushed before each step (512 MiB write)",
                        "parallelism": f"replicas x{world}"},
             "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu,
-            "clocks": clocks, "accuracy": acc, "fp64_path": fp64, "phases_ms": phases,
+            "clocks": clocks, "accuracy": acc, "fp64_path": fp64, "other_start": other,
+            "phases_ms": phases,
             "batched": batched,
             "solver": {"iterations": last["iterations"], "refinements": last["refinements"],
                        "rel_residual": last["rel_residual"], "pinned": last["pinned"]},

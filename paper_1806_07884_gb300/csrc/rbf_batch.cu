@@ -1161,14 +1161,16 @@ rbf_status solve_tiles_run(rbf_ctx* ctx, double* c, int use_c0, double tol, int 
         std::vector<double> bn2, rn2;
         if ((s = tile_norms<float>(ctx, ctx->bvec.as<double>(), dinv32, &bn2, &npin, st)) != RBF_OK)
             return s;
+        // a start vector's first residual from the FP32 matrix (as in the single-system
+        // solver: accurate far below the inner tolerance, replaced by the FP64 residual of
+        // the next refinement step, never used to declare convergence)
+        bool approx_r = false;
         if (use_c0) {
             launch_gather_sorted(c, bd.cperm, x64, M, st);
             k_zero_masked<<<nb, 256, 0, st>>>(M, x64, dinv32);
             ctx->launches += 2;
-            RBF_CUDA_TRY(cudaMemsetAsync(r64, 0, sizeof(double) * M, st));
-            if ((s = residual_run(ctx, x64, r64, false, st)) != RBF_OK) return s;
-            k_zero_masked<<<nb, 256, 0, st>>>(M, r64, dinv32);
-            ctx->launches += 1;
+            launch_resid32(ctx, x64, r64, st);
+            approx_r = true;
         } else {
             RBF_CUDA_TRY(cudaMemsetAsync(x64, 0, sizeof(double) * M, st));
             RBF_CUDA_TRY(cudaMemcpyAsync(r64, ctx->bvec.p, sizeof(double) * M,
@@ -1191,7 +1193,7 @@ rbf_status solve_tiles_run(rbf_ctx* ctx, double* c, int use_c0, double tol, int 
             for (int t = 0; t < T; ++t) {
                 const double rl = bn[t] > 0.0 ? rn[t] / bn[t] : 0.0;
                 rel[t] = rl;
-                if (!conv[t] && (rl <= tol || rn[t] == 0.0)) conv[t] = 1;
+                if (!conv[t] && ((rl <= tol && !approx_r) || rn[t] == 0.0)) conv[t] = 1;
                 active[t] = !conv[t];
                 nact += active[t];
             }
@@ -1222,6 +1224,7 @@ rbf_status solve_tiles_run(rbf_ctx* ctx, double* c, int use_c0, double tol, int 
             k_zero_masked<<<nb, 256, 0, st>>>(M, r64, dinv32);
             ctx->launches += 2;
             if ((s = tile_norms<float>(ctx, r64, dinv32, &rn2, nullptr, st)) != RBF_OK) return s;
+            approx_r = false;
             for (int t = 0; t < T; ++t) {
                 if (!active[t]) continue;   // converged tiles keep their iterate and residual
                 const double rnew = sqrt(rn2[t]);
@@ -1236,7 +1239,7 @@ rbf_status solve_tiles_run(rbf_ctx* ctx, double* c, int use_c0, double tol, int 
         }
         for (int t = 0; t < T; ++t) {
             rel[t] = bn[t] > 0.0 ? rn[t] / bn[t] : 0.0;
-            if (!conv[t] && (rel[t] <= tol || rn[t] == 0.0)) conv[t] = 1;
+            if (!conv[t] && ((rel[t] <= tol && !approx_r) || rn[t] == 0.0)) conv[t] = 1;
             state[t] = conv[t] ? kConverged : kMaxIt;
         }
         bool all = true;

@@ -188,6 +188,8 @@ rbf_status export_upper_run(rbf_ctx* ctx, int64_t cap, int32_t* row, int32_t* co
 rbf_status prec_setup_run(rbf_ctx* ctx, int prec, int min_support, int* npin_d, cudaStream_t st);
 // y += B x over all cells (precision prec; x, y sorted order)
 void launch_spmv(rbf_ctx* ctx, int prec, const void* x, void* y, cudaStream_t st);
+// r64 = b - B32 x64 on unpinned rows (FP32 assembly; uses the FP32 CG workspace's u and w[0])
+void launch_resid32(rbf_ctx* ctx, const double* x64, double* r64, cudaStream_t st);
 
 rbf_status bench_spmv_run(rbf_ctx* ctx, int reps, cudaStream_t st);
 rbf_status bench_cg_run(rbf_ctx* ctx, int reps, cudaStream_t st);

@@ -57,64 +57,96 @@ __global__ void k_height_scale(const double* __restrict__ acc, int T, double* __
     if (t < T) sigma[t] = acc[2 * t + 1] > 0.0 ? sqrt(acc[2 * t] / acc[2 * t + 1]) : 1.0;
 }
 
-constexpr int kFeatThreads = 128;
+// Features, one warp per cell: the lanes take the candidate points of the cell's
+// 3x3 neighbourhood and test each against every centre of the cell (up to kFCent at a time),
+// accumulating per-centre bins with shared-memory atomics. Dense cells spread over the lanes
+// instead of serialising one thread per centre.
+constexpr int kFWarps = 4;
+constexpr int kFCent = 48;
 
-// One thread per sorted centre s; features written to row cperm[s] of feat (caller order).
-__global__ void __launch_bounds__(kFeatThreads)
-    k_features(Binned bd, const double* __restrict__ sigma, float* __restrict__ feat) {
-    __shared__ int cnt[NB][kFeatThreads];
-    __shared__ double hs[NB][kFeatThreads];
-    const int s = blockIdx.x * kFeatThreads + threadIdx.x;
-    const int tid = threadIdx.x;
-#pragma unroll
-    for (int k = 0; k < NB; ++k) {
-        cnt[k][tid] = 0;
-        hs[k][tid] = 0.0;
-    }
-    if (s >= bd.M) return;
+__global__ void __launch_bounds__(kFWarps * 32)
+    k_features_cell(Binned bd, const int* __restrict__ clist, int ncl,
+                    const double* __restrict__ sigma, float* __restrict__ feat) {
+    __shared__ int cnt[kFWarps][kFCent][NB];
+    __shared__ double hs[kFWarps][kFCent][NB];
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const int w = blockIdx.x * kFWarps + wl;
+    if (w >= ncl) return;
     const Grid& g = bd.g;
-    const int4 cm = bd.crow[s];
-    const int cell = cm.z, ix = cell % g.gx, iy = cell / g.gx;
-    const float cu = bd.cu[s], cv = bd.cv[s];
-    const double cx = bd.cx[s], cy = bd.cy[s];
-    int n = 0;
+    const int cell = clist ? clist[w] : w;
+    const int cs = bd.cstart[cell], m = bd.cstart[cell + 1] - cs;
+    if (m == 0) return;
+    const int ix = cell % g.gx, iy = cell / g.gx;
+    int (*C)[NB] = cnt[wl];
+    double (*H)[NB] = hs[wl];
+    // the three rows of candidate cells: contiguous point ranges
+    int r0[3], r1[3];
+    float roy[3];
+    int nrow = 0;
     for (int r = max(iy - 1, 0); r <= min(iy + 1, g.gy - 1); ++r) {
-        const float oy = float(r - iy);
-        for (int q = max(ix - 1, 0); q <= min(ix + 1, g.gx - 1); ++q) {
-            const float ox = float(q - ix);
-            const int c2 = r * g.gx + q;
-            const int p0 = bd.pstart[c2], p1 = bd.pstart[c2 + 1];
-            for (int p = p0; p < p1; ++p) {
-                const float du = (bd.pu[p] + ox) - cu, dv = (bd.pv[p] + oy) - cv;
-                const float r2 = du * du + dv * dv;
-                if (r2 >= kPrefilterR2) continue;
-                const float rf = sqrtf(r2) * float(NB);     // 16 r, error ~ 1e-5 at most
-                int k;
-                const float fr = rf - floorf(rf);
-                if (fr < 1e-4f || fr > 1.0f - 1e-4f || rf > float(NB) - 1e-3f) {
-                    const double dx = bd.px[p] - cx, dy = bd.py[p] - cy;
-                    const double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
-                    const double rr = __ddiv_rn(__dsqrt_rn(d2), g.R);
-                    if (!(rr < 1.0)) continue;
-                    k = int(floor(double(NB) * rr));
-                } else {
-                    if (rf >= float(NB)) continue;
-                    k = int(rf);
+        const int xa = max(ix - 1, 0), xb = min(ix + 1, g.gx - 1);
+        r0[nrow] = bd.pstart[r * g.gx + xa];
+        r1[nrow] = bd.pstart[r * g.gx + xb + 1];
+        roy[nrow] = float(r - iy);
+        ++nrow;
+    }
+    for (int a0 = 0; a0 < m; a0 += kFCent) {
+        const int ma = min(kFCent, m - a0);
+        for (int e = lane; e < ma * NB; e += 32) {
+            C[e / NB][e % NB] = 0;
+            H[e / NB][e % NB] = 0.0;
+        }
+        __syncwarp();
+        for (int rr = 0; rr < nrow; ++rr) {
+            for (int p = r0[rr] + lane; p < r1[rr]; p += 32) {
+                // the point's cell column (relative to the centre cell) from its position in
+                // the row range: find its cell by the cell starts of this row
+                const float pu = bd.pu[p], pv = bd.pv[p] + roy[rr];
+                const double px = bd.px[p], py = bd.py[p], ph = bd.ph[p];
+                const int row = iy + int(roy[rr]);
+                int q = max(ix - 1, 0);
+                while (q < min(ix + 1, g.gx - 1) && p >= bd.pstart[row * g.gx + q + 1]) ++q;
+                const float pux = pu + float(q - ix);
+                for (int a = 0; a < ma; ++a) {
+                    const int s = cs + a0 + a;
+                    const float du = pux - bd.cu[s], dv = pv - bd.cv[s];
+                    const float r2 = du * du + dv * dv;
+                    if (r2 >= kPrefilterR2) continue;
+                    const float rf = sqrtf(r2) * float(NB);
+                    const float fr = rf - floorf(rf);
+                    int k;
+                    if (fr < 1e-4f || fr > 1.0f - 1e-4f || rf > float(NB) - 1e-3f) {
+                        const double dx = px - bd.cx[s], dy = py - bd.cy[s];
+                        const double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+                        const double rr2 = __ddiv_rn(__dsqrt_rn(d2), g.R);
+                        if (!(rr2 < 1.0)) continue;
+                        k = int(floor(double(NB) * rr2));
+                    } else {
+                        if (rf >= float(NB)) continue;
+                        k = int(rf);
+                    }
+                    atomicAdd(&C[a][k], 1);
+                    atomicAdd(&H[a][k], ph);
                 }
-                cnt[k][tid] += 1;
-                hs[k][tid] += bd.ph[p];
-                ++n;
             }
         }
-    }
-    const double inv_n = 1.0 / double(max(n, 1));
-    const double inv_sig = 1.0 / sigma[cm.w];
-    float* out = feat + (long long)bd.cperm[s] * NF;
+        __syncwarp();
+        for (int a = lane; a < ma; a += 32) {
+            const int s = cs + a0 + a;
+            int n = 0;
 #pragma unroll
-    for (int k = 0; k < NB; ++k) {
-        const int ck = cnt[k][tid];
-        out[k] = float(double(ck) * inv_n);
-        out[NB + k] = ck > 0 ? float(hs[k][tid] / double(ck) * inv_sig) : 0.0f;
+            for (int k = 0; k < NB; ++k) n += C[a][k];
+            const double inv_n = 1.0 / double(max(n, 1));
+            const double inv_sig = 1.0 / sigma[bd.crow[s].w];
+            float* out = feat + (long long)bd.cperm[s] * NF;
+#pragma unroll
+            for (int k = 0; k < NB; ++k) {
+                const int ck = C[a][k];
+                out[k] = float(double(ck) * inv_n);
+                out[NB + k] = ck > 0 ? float(H[a][k] / double(ck) * inv_sig) : 0.0f;
+            }
+        }
+        __syncwarp();
     }
 }
 
@@ -353,7 +385,10 @@ static rbf_status height_scales(rbf_ctx* ctx, cudaStream_t st) {
 rbf_status features_run(rbf_ctx* ctx, float* feat, double* sigma_out, cudaStream_t st) {
     rbf_status s = height_scales(ctx, st);
     if (s != RBF_OK) return s;
-    k_features<<<div_up(ctx->M, kFeatThreads), kFeatThreads, 0, st>>>(view(ctx), ctx->sigma.as<double>(), feat);
+    // one warp per cell holding centres (the cell list of a batch, else every cell)
+    const int ncl = ctx->T > 0 ? ctx->ncl : ctx->g.ncell;
+    k_features_cell<<<div_up(ncl, kFWarps), kFWarps * 32, 0, st>>>(
+        view(ctx), ctx->T > 0 ? ctx->clist.as<int>() : nullptr, ncl, ctx->sigma.as<double>(), feat);
     ctx->launches += 1;
     if (sigma_out)
         RBF_CUDA_TRY(cudaMemcpyAsync(sigma_out, ctx->sigma.p, sizeof(double) * std::max(ctx->T, 1),

@@ -391,6 +391,17 @@ __global__ void k_mask_zero(int M, double* __restrict__ x, const float* __restri
     if (i < M && dinv32[i] == 0.0f) x[i] = 0.0;
 }
 
+__global__ void k_to_f32(int M, const double* __restrict__ x, float* __restrict__ u) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < M) u[i] = float(x[i]);
+}
+// r = b - w on unpinned rows, 0 on pinned rows (w = B32 x from the FP32 SpMV).
+__global__ void k_resid32(int M, const double* __restrict__ b, const float* __restrict__ w,
+                          const float* __restrict__ dinv32, double* __restrict__ r) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < M) r[i] = dinv32[i] == 0.0f ? 0.0 : b[i] - double(w[i]);
+}
+
 // ||v||^2 over unpinned rows into out[0] (single block, fixed order).
 __global__ void k_norm2(int M, const double* __restrict__ v, const float* __restrict__ dinv32,
                         double* __restrict__ out) {
@@ -613,6 +624,17 @@ rbf_status prec_setup_run(rbf_ctx* ctx, int prec, int min_support, int* npin_d, 
     return RBF_OK;
 }
 
+void launch_resid32(rbf_ctx* ctx, const double* x64, double* r64, cudaStream_t st) {
+    const int M = ctx->M;
+    const CgVec<float> v = cg_vectors<float>(ctx);
+    k_to_f32<<<div_up(M, 256), 256, 0, st>>>(M, x64, v.u);
+    cudaMemsetAsync(v.w[0], 0, sizeof(float) * M, st);
+    launch_spmv(ctx, RBF_FP32_REFINE, v.u, v.w[0], st);
+    k_resid32<<<div_up(M, 256), 256, 0, st>>>(M, ctx->bvec.as<double>(), v.w[0],
+                                              ctx->dinv32.as<float>(), r64);
+    ctx->launches += 2;
+}
+
 void launch_spmv(rbf_ctx* ctx, int prec, const void* x, void* y, cudaStream_t st) {
     const Binned bd = view(ctx);
     if (prec == RBF_FP64)
@@ -689,12 +711,20 @@ rbf_status solve_run(rbf_ctx* ctx, double* c, int use_c0, double tol, int maxit,
         k_norm2<<<1, 1024, 0, st>>>(M, ctx->bvec.as<double>(), dinv32, nrm_d);
         ctx->launches += 1;
         RBF_CUDA_TRY(cudaMemcpyAsync(nrm_h, nrm_d, sizeof(double), cudaMemcpyDeviceToHost, st));
+        // With a start vector the first residual comes from the FP32 matrix, r = b - B32 x
+        // (FP32 products and sums: relative error about 1e-6 of ||b||). It only has to be far
+        // more accurate than the inner tolerance, and the FP64 matrix-free residual of the
+        // next refinement step replaces it; no convergence is declared on it.
+        bool approx_r = false;
         if (use_c0) {
             launch_gather_sorted(c, bd.cperm, x64, M, st);
             k_mask_zero<<<div_up(M, 256), 256, 0, st>>>(M, x64, dinv32);
-            ctx->launches += 2;
-            RBF_CUDA_TRY(cudaMemsetAsync(r64, 0, sizeof(double) * M, st));
-            if ((s = residual_run(ctx, x64, r64, false, st)) != RBF_OK) return s;
+            k_to_f32<<<div_up(M, 256), 256, 0, st>>>(M, x64, v.u);
+            RBF_CUDA_TRY(cudaMemsetAsync(v.w[0], 0, sizeof(float) * M, st));
+            launch_spmv(ctx, RBF_FP32_REFINE, v.u, v.w[0], st);
+            k_resid32<<<div_up(M, 256), 256, 0, st>>>(M, ctx->bvec.as<double>(), v.w[0], dinv32, r64);
+            ctx->launches += 4;
+            approx_r = true;
         } else {
             RBF_CUDA_TRY(cudaMemsetAsync(x64, 0, sizeof(double) * M, st));
             RBF_CUDA_TRY(cudaMemcpyAsync(r64, ctx->bvec.p, sizeof(double) * M,
@@ -720,7 +750,7 @@ rbf_status solve_run(rbf_ctx* ctx, double* c, int use_c0, double tol, int maxit,
         const double inner_tol = ctx->inner_tol;
         for (outer = 0;; ++outer) {
             rel = bnorm > 0 ? rn / bnorm : 0.0;
-            if (rel <= tol || rn == 0.0) {
+            if ((rel <= tol && !approx_r) || rn == 0.0) {
                 state = kConverged;
                 break;
             }
@@ -743,6 +773,7 @@ rbf_status solve_run(rbf_ctx* ctx, double* c, int use_c0, double tol, int maxit,
             if ((s = residual_run(ctx, x64, r64, false, st)) != RBF_OK) return s;
             k_mask_zero<<<div_up(M, 256), 256, 0, st>>>(M, r64, dinv32);
             ctx->launches += 2;
+            approx_r = false;
             double rn_new = 0.0;
             if ((s = norm_r64(&rn_new)) != RBF_OK) return s;
             if (!(rn_new < 0.5 * rn)) {   // stalled: the FP32 matrix cannot resolve the system
