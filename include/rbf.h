@@ -168,6 +168,10 @@ rbf_status rbf_eval_grid(rbf_ctx* ctx, const double* c, int nx, int ny, const do
  *   "inner_tol"        relative tolerance of each FP32 inner solve of RBF_FP32_REFINE, in
  *                      (0, 1); default 1e-3
  *   "max_refinements"  FP64 refinement steps of RBF_FP32_REFINE, in [0, 1000]; default 30
+ *   "store_a"          1 (default): the FP32 assembly keeps the FP64 values of A (points x
+ *                      candidate centres of each cell's 3x3 block, ~8 x N x 9 x centres per cell
+ *                      bytes) so that the refinement's residual passes read them instead of
+ *                      recomputing them; 0 (or no room for them): matrix-free residual
  *   "autotune"         1 (default): rbf_solve_tiles times the candidate launch
  *                      configurations of its CG loop on the first solve of a system of a
  *                      new shape and keeps the fastest (see rbf_autotune); 0: it uses the

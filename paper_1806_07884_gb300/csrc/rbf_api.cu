@@ -151,7 +151,7 @@ rbf_status rbf_destroy(rbf_ctx* ctx) {
                        &ctx->support, &ctx->x, &ctx->r, &ctx->cgv[0], &ctx->cgv[1],
                        &ctx->dinv, &ctx->dinv32, &ctx->bjinv, &ctx->bjinv32, &ctx->crow, &ctx->cdesc,
                        &ctx->partial, &ctx->scal, &ctx->csort, &ctx->sigma, &ctx->feat,
-                       &ctx->mlp_part};
+                       &ctx->mlp_part, &ctx->astore, &ctx->woff, &ctx->wsize};
     for (rbf_buf* b : bufs) release(ctx, *b);
     if (ctx->hpinned) cudaFreeHost(ctx->hpinned);
     delete ctx;
@@ -197,6 +197,7 @@ rbf_status rbf_bin(rbf_ctx* ctx, const double* cx, const double* cy, int64_t M, 
     ctx->M = int(M);
     ctx->N = int(N);
     ctx->T = 0;
+    ctx->astore_ok = false;
     DeviceGuard dg(ctx->device);
     rbf_status s = bin_run(ctx, cx, cy, px, py, h, as_stream(stream));
     if (s == RBF_OK) ctx->binned = true;
@@ -396,6 +397,11 @@ rbf_status rbf_set_param(rbf_ctx* ctx, const char* name, double value) {
     if (!strcmp(name, "max_refinements")) {
         if (!(value >= 0.0 && value <= 1000.0)) return set_err(ctx, RBF_ERR_ARG, "max_refinements must be in [0, 1000]");
         ctx->max_refine = int(value);
+        return RBF_OK;
+    }
+    if (!strcmp(name, "store_a")) {
+        if (!(value == 0.0 || value == 1.0)) return set_err(ctx, RBF_ERR_ARG, "store_a must be 0 or 1");
+        ctx->store_a = int(value);
         return RBF_OK;
     }
     if (!strcmp(name, "autotune")) {

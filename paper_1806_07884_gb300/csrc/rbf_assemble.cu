@@ -323,7 +323,9 @@ template <int KIND>
 __global__ void __launch_bounds__(kThreads) k_residual(Binned bd, const int4* __restrict__ work,
                                                        int npad, const double* __restrict__ c,
                                                        double* __restrict__ r,
-                                                       int* __restrict__ support) {
+                                                       int* __restrict__ support,
+                                                       const long long* __restrict__ woff,
+                                                       double* __restrict__ astore) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ LocalCells lc;
     __shared__ double esm[kSubChunk];
@@ -367,6 +369,11 @@ __global__ void __launch_bounds__(kThreads) k_residual(Binned bd, const int4* __
         fill_phi<KIND, double>(bd, cs, n, npad, q0, p1, phi, hsm, support ? cnt : nullptr, wl);
         __syncthreads();
         const int np = min(kSubChunk, p1 - q0);
+        if (astore) {   // keep the rows of A for later residual passes: point p, candidate a
+            double* dst = astore + woff[blockIdx.x] + (long long)(q0 - p0) * n;
+            for (int e = threadIdx.x; e < np * n; e += blockDim.x)
+                dst[e] = phi[(e / n) * npad + (e % n)];
+        }
         // e_p = h_p - sum_a Phi[p][a] c_a  (one warp per point)
         for (int pp = warp; pp < np; pp += nw) {
             double s = 0.0;
@@ -393,6 +400,76 @@ __global__ void __launch_bounds__(kThreads) k_residual(Binned bd, const int4* __
         if (racc1 != 0.0) atomicAdd(&r[cs.s[a]], racc1);
         if (support && cnt[a]) atomicAdd(&support[cs.s[a]], cnt[a]);
     }
+}
+
+// The same residual from the stored rows of A (written by the FP64 pass of the FP32 assembly):
+// no distances, square roots or Wendland evaluations, only the two FP64 products per point.
+__global__ void __launch_bounds__(kThreads) k_residual_stored(Binned bd, const int4* __restrict__ work,
+                                                              int npad, const double* __restrict__ c,
+                                                              double* __restrict__ r,
+                                                              const long long* __restrict__ woff,
+                                                              const double* __restrict__ astore) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ LocalCells lc;
+    __shared__ double esm[kSubChunk];
+    __shared__ double hsm[kSubChunk];
+    const int4 wi = work[blockIdx.x];
+    const int cell = wi.x, p0 = wi.y, p1 = wi.z;
+    if (threadIdx.x == 0) describe_cells(bd, cell, lc);
+    __syncthreads();
+    const int n = lc.n;
+    double* phi = reinterpret_cast<double*>(smem);
+    double* cval = phi + kSubChunk * npad;
+    int* sidx = reinterpret_cast<int*>(cval + npad);
+    for (int a = threadIdx.x; a < n; a += blockDim.x) {
+        int k = 0;
+        while (a >= lc.off[k + 1]) ++k;
+        const int sa = lc.start[k] + (a - lc.off[k]);
+        sidx[a] = sa;
+        cval[a] = c ? c[sa] : 0.0;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const double* src0 = astore + woff[blockIdx.x];
+    double racc0 = 0.0, racc1 = 0.0;
+    for (int q0 = p0; q0 < p1; q0 += kSubChunk) {
+        const int np = min(kSubChunk, p1 - q0);
+        __syncthreads();
+        const double* src = src0 + (long long)(q0 - p0) * n;
+        for (int e = threadIdx.x; e < np * n; e += blockDim.x) phi[(e / n) * npad + (e % n)] = __ldcs(src + e);
+        if (threadIdx.x < np) hsm[threadIdx.x] = bd.ph[q0 + threadIdx.x];
+        __syncthreads();
+        for (int pp = warp; pp < np; pp += nw) {
+            double sacc = 0.0;
+            for (int a = lane; a < n; a += 32) sacc = fma(phi[pp * npad + a], cval[a], sacc);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+            if (lane == 0) esm[pp] = hsm[pp] - sacc;
+        }
+        __syncthreads();
+        for (int pp = 0; pp < np; ++pp) {
+            const double e = esm[pp];
+            if (threadIdx.x < n) racc0 = fma(phi[pp * npad + threadIdx.x], e, racc0);
+            if (threadIdx.x + kThreads < n) racc1 = fma(phi[pp * npad + threadIdx.x + kThreads], e, racc1);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < n && racc0 != 0.0) atomicAdd(&r[sidx[threadIdx.x]], racc0);
+    if (threadIdx.x + kThreads < n && racc1 != 0.0) atomicAdd(&r[sidx[threadIdx.x + kThreads]], racc1);
+}
+
+// Values of A stored per work item: its points x the candidates of its cell's 3x3 block.
+__global__ void k_work_sizes(Binned bd, const int4* __restrict__ work, int nwork,
+                             long long* __restrict__ size) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= nwork) return;
+    const int4 wi = work[w];
+    const Grid& g = bd.g;
+    const int ix = wi.x % g.gx, iy = wi.x / g.gx;
+    const int xa = max(ix - 1, 0), xb = min(ix + 1, g.gx - 1);
+    long long n = 0;
+    for (int r = max(iy - 1, 0); r <= min(iy + 1, g.gy - 1); ++r)
+        n += bd.cstart[r * g.gx + xb + 1] - bd.cstart[r * g.gx + xa];
+    size[w] = (long long)(wi.z - wi.y) * n;
 }
 
 template <typename T>
@@ -423,8 +500,11 @@ rbf_status launch_residual(rbf_ctx* ctx, const double* c, double* r, bool count,
     const size_t sm = asm_smem<double>(npad, true);
     auto kfn = k_residual<KIND>;
     RBF_CUDA_TRY(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
+    const bool store = count && ctx->astore_ok;
     kfn<<<ctx->nwork, kThreads, sm, st>>>(view(ctx), ctx->work.as<int4>(), npad, c, r,
-                                          count ? ctx->support.as<int>() : nullptr);
+                                          count ? ctx->support.as<int>() : nullptr,
+                                          store ? ctx->woff.as<long long>() : nullptr,
+                                          store ? ctx->astore.as<double>() : nullptr);
     RBF_CUDA_TRY(cudaGetLastError());
     ctx->launches += 1;
     return RBF_OK;
@@ -434,6 +514,7 @@ rbf_status launch_residual(rbf_ctx* ctx, const double* c, double* r, bool count,
 
 rbf_status assemble_run(rbf_ctx* ctx, int kernel, int prec, cudaStream_t st) {
     const int M = ctx->M;
+    ctx->astore_ok = false;   // rewritten below by an FP32 assembly
     const size_t vb = prec == RBF_FP64 ? sizeof(double) : sizeof(float);
     rbf_status s;
     if ((s = ensure(ctx, ctx->bvals, vb * std::max<int64_t>(ctx->nvals, 1), st)) != RBF_OK) return s;
@@ -460,6 +541,27 @@ rbf_status assemble_run(rbf_ctx* ctx, int kernel, int prec, cudaStream_t st) {
         default: s = launch_assemble<3, float>(ctx, st, npad); break;
     }
     if (s != RBF_OK) return s;
+    // Storage for the FP64 values of A, written by the pass below and read by every later
+    // residual pass (the refinement). Without room for it the residual stays matrix-free.
+    ctx->astore_ok = false;
+    if (ctx->store_a) {
+        if ((s = ensure(ctx, ctx->woff, sizeof(long long) * (ctx->nwork + 1), st)) != RBF_OK) return s;
+        if ((s = ensure(ctx, ctx->wsize, sizeof(long long) * ctx->nwork, st)) != RBF_OK) return s;
+        k_work_sizes<<<div_up(ctx->nwork, 256), 256, 0, st>>>(view(ctx), ctx->work.as<int4>(), ctx->nwork,
+                                                              ctx->wsize.as<long long>());
+        ctx->launches += 1;
+        if ((s = scan_i64(ctx, ctx->wsize.as<int64_t>(), ctx->woff.as<int64_t>(), ctx->nwork, st)) != RBF_OK)
+            return s;
+        long long* hp = static_cast<long long*>(ctx->hpinned) + 40;
+        RBF_CUDA_TRY(cudaMemcpyAsync(hp, ctx->woff.as<long long>() + ctx->nwork, sizeof(long long),
+                                     cudaMemcpyDeviceToHost, st));
+        RBF_CUDA_TRY(cudaStreamSynchronize(st));
+        const long long total = *hp;
+        if (ensure(ctx, ctx->astore, sizeof(double) * std::max<long long>(total, 1), st) == RBF_OK)
+            ctx->astore_ok = true;
+        else
+            ctx->err.clear();   // no room: matrix-free residual
+    }
     // b = A^T h and the support counts in FP64: the residual with c = 0
     RBF_CUDA_TRY(cudaMemsetAsync(ctx->bvec.p, 0, sizeof(double) * M, st));
     return residual_run(ctx, nullptr, ctx->bvec.as<double>(), true, st);
@@ -470,6 +572,17 @@ rbf_status residual_run(rbf_ctx* ctx, const double* c_sorted, double* r_sorted, 
     if (ctx->nwork == 0) return RBF_OK;
     const double* c = c_sorted;   // nullptr stands for c = 0, i.e. r = A^T h
     const int npad = std::max(4, (ctx->max_cand + 3) / 4 * 4);
+    if (!count && ctx->astore_ok) {
+        const size_t sm = sizeof(double) * (kSubChunk * npad + npad) + sizeof(int) * npad;
+        RBF_CUDA_TRY(cudaFuncSetAttribute(k_residual_stored, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          int(sm)));
+        k_residual_stored<<<ctx->nwork, kThreads, sm, st>>>(view(ctx), ctx->work.as<int4>(), npad, c,
+                                                            r_sorted, ctx->woff.as<long long>(),
+                                                            ctx->astore.as<double>());
+        RBF_CUDA_TRY(cudaGetLastError());
+        ctx->launches += 1;
+        return RBF_OK;
+    }
     switch (ctx->kernel) {
         case RBF_W30: return launch_residual<0>(ctx, c, r_sorted, count, st, npad);
         case RBF_W31: return launch_residual<1>(ctx, c, r_sorted, count, st, npad);

@@ -51,7 +51,8 @@ struct TSlot {
 };
 struct BatchScal {
     unsigned int ndone;        // tiles that have stopped (or take no part in this solve)
-    int T, maxit, pad;
+    int T, maxit;
+    int passes;                // loop passes of the solve graph so far
 };
 
 // Device view of the per-tile arrays (one allocation, layout in TileLayout).
@@ -589,8 +590,11 @@ __global__ void __launch_bounds__(256)
     tile_reduce<3, NT, double>(key, acc, t0, span, sred, dst);
 }
 
-__global__ void k_bcg_cond(const BatchScal* __restrict__ bs, cudaGraphConditionalHandle h) {
-    cudaGraphSetConditional(h, bs->ndone < unsigned(bs->T) ? 1u : 0u);
+__global__ void k_bcg_cond(BatchScal* __restrict__ bs, cudaGraphConditionalHandle h) {
+    // every running tile stops by maxit; the pass bound ends the loop whatever the states
+    const int passes = ++bs->passes;
+    const bool more = bs->ndone < unsigned(bs->T) && passes <= bs->maxit / kItersPerBody + 2;
+    cudaGraphSetConditional(h, more ? 1u : 0u);
 }
 
 // ---------------------------------------------------------------------------
@@ -1070,6 +1074,7 @@ rbf_status bin_tiles_run(rbf_ctx* ctx, const rbf_tile* tiles, int T, const doubl
         for (int r = 0; r < td[t].gy; ++r) rowtile[td[t].oy + r] = t;
 
     tiles_release(ctx);
+    ctx->astore_ok = false;
     ctx->T = T;
     ctx->tiles.assign(tiles, tiles + T);
     ctx->g = g;

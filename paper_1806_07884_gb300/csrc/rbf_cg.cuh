@@ -259,12 +259,6 @@ __device__ __forceinline__ T apply_prec(const Binned& bd, const T* __restrict__ 
     return ui;
 }
 
-// One thread per row i. Prologue (warp 0 of every block, identical results in all blocks):
-// gamma_k and (r_k, r_k) from the previous kernel's per-block partials, delta_k from the
-// SpMV's slots, the stopping test, then beta_k and alpha_k; block 0 writes the next slot.
-// Body: s, p, x, r updated; u = D^-1 r using the cell's updated residual (recomputed here
-// from the previous buffers); w of the other parity zeroed for the next SpMV; per-block
-
 template <typename T>
 CgVec<T> cg_vectors(rbf_ctx* ctx) {
     const int slot = sizeof(T) == 8 ? 0 : 1;

@@ -56,6 +56,11 @@ struct rbf_ctx {
     rbf_buf bvals;             // B values (double or float)
     rbf_buf bvec;              // [M] b = A^T h, sorted order (FP64)
     rbf_buf support;           // [M] points inside each support, sorted order
+    // FP64 values of A per work item (points x candidates of the cell's 3x3 block), kept by
+    // the FP32 assembly for the refinement's residual passes
+    rbf_buf astore, woff, wsize;
+    bool astore_ok = false;
+    int store_a = 1;           // rbf_set_param("store_a")
 
     // ---- solver workspace ----
     // FP64 refinement vectors (sorted order): the solution and the matrix-free residual

@@ -43,7 +43,7 @@ struct CgSlot {
 };
 struct CgScalars {
     double bb, tol2, bscale;     // (b, b); parameters written by the host before each solve
-    int maxit, pad;
+    int maxit, passes;           // passes: loop passes of the solve graph so far
     unsigned int ticket, pad2;   // last-block-done counter of the start kernel
     CgSlot sl[2];
     double out_rr, out_gamma;    // result, written when the solve stops
@@ -120,7 +120,13 @@ __global__ void __launch_bounds__(kSpmvWarps * 32, sizeof(T) == 4 ? 3 : 1)
     if (lane == 0 && d != T(0)) atomicAdd(&sc->acc_delta[P][gw & (kAccSlots - 1)], double(d));
 }
 
-// partials of gamma_{k+1} and (r_{k+1}, r_{k+1}). P is the parity k & 1.
+// One thread per row i. Prologue (warp 0 of every block, identical results in all blocks):
+// gamma_k and (r_k, r_k) from the previous kernel's per-block partials, delta_k from the
+// SpMV's slots, the stopping test, then beta_k and alpha_k; block 0 writes the next slot.
+// Body: s, p, x, r updated; u = D^-1 r with the cell's new residuals from shared memory (rows
+// of the cell outside the block's chunk recomputed with the same operations); w of the other
+// parity zeroed for the next SpMV; per-block partials of gamma_{k+1} and (r_{k+1}, r_{k+1}).
+// P is the parity k & 1.
 template <typename T>
 __global__ void __launch_bounds__(kVecThreads)
     k_cg_update(Binned bd, CgVec<T> v, int P, CgScalars* __restrict__ sc,
@@ -291,8 +297,12 @@ __global__ void __launch_bounds__(kVecThreads)
 
 // Loop condition of the solve graph (after an even number of iterations the next slot is
 // slot 0): keep iterating while the state is running.
-__global__ void k_cg_cond(const CgScalars* __restrict__ sc, cudaGraphConditionalHandle h) {
-    cudaGraphSetConditional(h, sc->sl[0].state == kRunning ? 1u : 0u);
+__global__ void k_cg_cond(CgScalars* __restrict__ sc, cudaGraphConditionalHandle h) {
+    // every running pass advances the iteration count, which stops at maxit; the pass bound
+    // ends the loop even if the state were never to leave "running"
+    const int passes = ++sc->passes;
+    const bool more = sc->sl[0].state == kRunning && passes <= sc->maxit / kItersPerBody + 2;
+    cudaGraphSetConditional(h, more ? 1u : 0u);
 }
 
 // Preconditioner set-up, one warp per cell: dinv[s] = 1 / B_ss for centres with at least

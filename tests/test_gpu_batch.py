@@ -86,13 +86,15 @@ def test_batched_fp64_matches_oracle_per_tile():
 
 
 def test_batched_fp32_refine_surface_matches_oracle():
+    # tol 1e-11: the clustered tile is ill-conditioned enough that a 1e-10 normal residual
+    # leaves its surface at ~1.6e-6 (the benchmark's workloads use 1e-11 for the same reason)
     pbs = _tiles_small()
-    cs, info, tinfo, ctx = pkg.fit_tiles(_problems(pbs), prec="fp32_refine", tol=1e-10)
+    cs, info, tinfo, ctx = pkg.fit_tiles(_problems(pbs), prec="fp32_refine", tol=1e-11)
     assert info["status"] == OK
     for k, pb in enumerate(pbs):
         c_ref, ref = _oracle(pb, ("small", k))
         c = cs[k].cpu().numpy()
-        assert tinfo[k]["status"] == OK and tinfo[k]["rel_residual"] <= 1e-10
+        assert tinfo[k]["status"] == OK and tinfo[k]["rel_residual"] <= 1e-11
         assert O.rel_err(ref["A"] @ c, ref["A"] @ c_ref) <= MIXED_BAR, k
         f = O.evaluate_grid(c, pb.centres, pb.R, pb.kernel, 33, pb.bbox)
         f_ref = O.evaluate_grid(c_ref, pb.centres, pb.R, pb.kernel, 33, pb.bbox)

@@ -295,3 +295,23 @@ def test_device_sqrt_against_cuda_sqrt():
     ulp = np.abs(o[ok, 0] - o[ok, 1]) / np.spacing(o[ok, 1])
     assert ulp.max() <= 4.0, ulp.max()
     assert o[0, 0] == 0.0
+
+
+@pytest.mark.parametrize("case", ["franke", "clustered", "dense_cell", "ragged"])
+def test_stored_a_residual_matches_matrix_free(case):
+    """FP32 + refinement with the stored FP64 values of A and with the matrix-free residual
+    reach the oracle's surface alike (the stored values are those the matrix-free pass
+    computes)."""
+    pb = _assembly_case(case)
+    c_ref, _ = O.fit(pb.points, pb.h, pb.centres, pb.R, pb.kernel, method="cholesky")
+    f_ref = O.evaluate_grid(c_ref, pb.centres, pb.R, pb.kernel, 65)
+    for store in (1, 0):
+        ctx = pkg.Context()
+        ctx.set_param("store_a", store)
+        C, P = pb.centres, pb.points
+        ctx.bin(_dev(C[:, 0]), _dev(C[:, 1]), _dev(P[:, 0]), _dev(P[:, 1]), _dev(pb.h), pb.R, pb.bbox)
+        ctx.assemble(pb.kernel, "fp32_refine")
+        c, info = ctx.solve(tol=1e-10)
+        assert info["refinements"] >= 1
+        assert O.rel_err(ctx.eval_grid(c, 65, 65).cpu().numpy(), f_ref) <= MIXED_BAR
+        ctx.close()
