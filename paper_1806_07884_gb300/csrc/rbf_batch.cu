@@ -449,23 +449,24 @@ __global__ void __launch_bounds__(NT)
     const int maxit = tc.bs->maxit;
     for (int j = threadIdx.x; j < span; j += NT) {
         const int t = t0 + j;
+        // the step in the solver's precision T (every block spanning the tile repeats it)
         const TSlot sl = slP[t];
         int state = sl.state;
-        double alpha = 0.0, beta = 0.0;
-        const double g = __ldcg(gP + t), rr = __ldcg(rrP + t);
+        T alpha = T(0), beta = T(0);
+        const T g = T(__ldcg(gP + t)), rr = T(__ldcg(rrP + t));
         if (state == kRunning) {
-            const double d = __ldcg(dlP + t);
+            const T d = T(__ldcg(dlP + t));
             if (!isfinite(g) || !isfinite(rr)) {
                 state = kBreakdown;
-            } else if (rr <= tc.tol2[t] * __ldcg(tc.bb + t)) {
+            } else if (rr <= T(tc.tol2[t]) * T(__ldcg(tc.bb + t))) {
                 state = kConverged;
             } else if (sl.it >= maxit) {
                 state = kMaxIt;
             } else {
-                beta = sl.it == 0 ? 0.0 : g / sl.gamma_prev;
-                const double den = sl.it == 0 ? d : d - beta * g / sl.alpha_prev;
+                beta = sl.it == 0 ? T(0) : g / T(sl.gamma_prev);
+                const T den = sl.it == 0 ? d : d - beta * g / T(sl.alpha_prev);
                 alpha = g / den;
-                if (!(den > 0.0) || !isfinite(alpha)) state = kBreakdown;
+                if (!(den > T(0)) || !isfinite(alpha)) state = kBreakdown;
             }
         }
         const bool owner = j > 0 || i0 == 0 || bd.crow[i0 - 1].w != t0;
@@ -473,21 +474,21 @@ __global__ void __launch_bounds__(NT)
             TSlot nx = sl;
             nx.state = state;
             if (state == kRunning) {
-                nx.gamma_prev = g;
-                nx.alpha_prev = alpha;
+                nx.gamma_prev = double(g);
+                nx.alpha_prev = double(alpha);
                 nx.it = sl.it + 1;
             }
             slQ[t] = nx;
             dlQ[t] = 0.0;
             if (sl.state == kRunning && state != kRunning) {
-                tc.out_rr[t] = rr;
+                tc.out_rr[t] = double(rr);
                 tc.out_it[t] = sl.it;
                 tc.out_state[t] = state;
                 atomicAdd(&tc.bs->ndone, 1u);
             }
         }
-        s_alpha[j] = T(alpha);
-        s_beta[j] = T(beta);
+        s_alpha[j] = alpha;
+        s_beta[j] = beta;
         s_go[j] = state == kRunning;
         sred[0][j] = 0.0;
         sred[1][j] = 0.0;

@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(kFWarps * 32)
     k_features_cell(Binned bd, const int* __restrict__ clist, int ncl,
                     const double* __restrict__ sigma, float* __restrict__ feat) {
     __shared__ int cnt[kFWarps][kFCent][NB];
-    __shared__ double hs[kFWarps][kFCent][NB];
+    __shared__ float hs[kFWarps][kFCent][NB];   // FP32 height sums: native shared atomics
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     const int w = blockIdx.x * kFWarps + wl;
     if (w >= ncl) return;
@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(kFWarps * 32)
     if (m == 0) return;
     const int ix = cell % g.gx, iy = cell / g.gx;
     int (*C)[NB] = cnt[wl];
-    double (*H)[NB] = hs[wl];
+    float (*H)[NB] = hs[wl];
     // the three rows of candidate cells: contiguous point ranges
     int r0[3], r1[3];
     float roy[3];
@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(kFWarps * 32)
         const int ma = min(kFCent, m - a0);
         for (int e = lane; e < ma * NB; e += 32) {
             C[e / NB][e % NB] = 0;
-            H[e / NB][e % NB] = 0.0;
+            H[e / NB][e % NB] = 0.0f;
         }
         __syncwarp();
         for (int rr = 0; rr < nrow; ++rr) {
@@ -102,7 +102,8 @@ __global__ void __launch_bounds__(kFWarps * 32)
                 // the point's cell column (relative to the centre cell) from its position in
                 // the row range: find its cell by the cell starts of this row
                 const float pu = bd.pu[p], pv = bd.pv[p] + roy[rr];
-                const double px = bd.px[p], py = bd.py[p], ph = bd.ph[p];
+                const double px = bd.px[p], py = bd.py[p];
+                const float ph = float(bd.ph[p]);
                 const int row = iy + int(roy[rr]);
                 int q = max(ix - 1, 0);
                 while (q < min(ix + 1, g.gx - 1) && p >= bd.pstart[row * g.gx + q + 1]) ++q;
@@ -143,7 +144,7 @@ __global__ void __launch_bounds__(kFWarps * 32)
             for (int k = 0; k < NB; ++k) {
                 const int ck = C[a][k];
                 out[k] = float(double(ck) * inv_n);
-                out[NB + k] = ck > 0 ? float(H[a][k] / double(ck) * inv_sig) : 0.0f;
+                out[NB + k] = ck > 0 ? float(double(H[a][k]) / double(ck) * inv_sig) : 0.0f;
             }
         }
         __syncwarp();

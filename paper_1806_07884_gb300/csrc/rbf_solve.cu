@@ -127,11 +127,14 @@ __global__ void __launch_bounds__(kSpmvWarps * 32, sizeof(T) == 4 ? 3 : 1)
 // of the cell outside the block's chunk recomputed with the same operations); w of the other
 // parity zeroed for the next SpMV; per-block partials of gamma_{k+1} and (r_{k+1}, r_{k+1}).
 // P is the parity k & 1.
+// The scalar step is taken in the solver's precision T (FP32 for the FP32 inner solver, whose
+// iterates the FP64 refinement corrects): every block repeats it, and FP64 issues at 1/64
+// of the FP32 rate on this GPU.
 template <typename T>
 __global__ void __launch_bounds__(kVecThreads)
     k_cg_update(Binned bd, CgVec<T> v, int P, CgScalars* __restrict__ sc,
-                double* __restrict__ pbuf) {
-    __shared__ double s_ab[2];
+                T* __restrict__ pbuf) {
+    __shared__ T s_ab[2];
     __shared__ int s_go;
     static_assert(kAccSlots == 64, "two slots per lane");
     const int nblk = gridDim.x;
@@ -139,33 +142,33 @@ __global__ void __launch_bounds__(kVecThreads)
         const int lane = threadIdx.x;
         const CgSlot sl = sc->sl[P];
         int state = sl.state;
-        double g = 0.0, rr = 0.0, d = 0.0;
+        T g = T(0), rr = T(0), d = T(0);
         if (state == kRunning) {
-            const double* pb = pbuf + size_t(P) * 2 * nblk;
+            const T* pb = pbuf + size_t(P) * 2 * nblk;
             for (int b = lane; b < nblk; b += 32) {
                 g += __ldcg(pb + 2 * b);
                 rr += __ldcg(pb + 2 * b + 1);
             }
-            d = __ldcg(&sc->acc_delta[P][lane]) + __ldcg(&sc->acc_delta[P][lane + 32]);
+            d = T(__ldcg(&sc->acc_delta[P][lane])) + T(__ldcg(&sc->acc_delta[P][lane + 32]));
         }
-        g = warp_sum_d(g);
-        rr = warp_sum_d(rr);
-        d = warp_sum_d(d);
+        g = warp_sum<T>(g);
+        rr = warp_sum<T>(rr);
+        d = warp_sum<T>(d);
         if (lane == 0) {
-            double alpha = 0.0, beta = 0.0;
+            T alpha = T(0), beta = T(0);
             const int was = state;
             if (state == kRunning) {
                 if (!isfinite(g) || !isfinite(rr)) {
                     state = kBreakdown;
-                } else if (rr <= sc->tol2 * sc->bb) {
+                } else if (rr <= T(sc->tol2) * T(sc->bb)) {
                     state = kConverged;
                 } else if (sl.it >= sc->maxit) {
                     state = kMaxIt;
                 } else {
-                    beta = sl.it == 0 ? 0.0 : g / sl.gamma_prev;
-                    const double den = sl.it == 0 ? d : d - beta * g / sl.alpha_prev;
+                    beta = sl.it == 0 ? T(0) : g / T(sl.gamma_prev);
+                    const T den = sl.it == 0 ? d : d - beta * g / T(sl.alpha_prev);
                     alpha = g / den;
-                    if (!(den > 0.0) || !isfinite(alpha)) state = kBreakdown;
+                    if (!(den > T(0)) || !isfinite(alpha)) state = kBreakdown;
                 }
             }
             s_ab[0] = alpha;
@@ -175,14 +178,14 @@ __global__ void __launch_bounds__(kVecThreads)
                 CgSlot nx = sl;
                 nx.state = state;
                 if (state == kRunning) {
-                    nx.gamma_prev = g;
-                    nx.alpha_prev = alpha;
+                    nx.gamma_prev = double(g);
+                    nx.alpha_prev = double(alpha);
                     nx.it = sl.it + 1;
                 }
                 sc->sl[P ^ 1] = nx;
                 if (was == kRunning && state != kRunning) {
-                    sc->out_rr = rr;
-                    sc->out_gamma = g;
+                    sc->out_rr = double(rr);
+                    sc->out_gamma = double(g);
                     sc->out_it = sl.it;
                     sc->out_state = state;
                 }
@@ -195,7 +198,7 @@ __global__ void __launch_bounds__(kVecThreads)
     }
     __syncthreads();
     if (!s_go) return;
-    const T ta = T(s_ab[0]), tb = T(s_ab[1]);
+    const T ta = s_ab[0], tb = s_ab[1];
     const T* __restrict__ rP = P ? v.r[1] : v.r[0];
     const T* __restrict__ sP = P ? v.s[1] : v.s[0];
     const T* __restrict__ wP = P ? v.w[1] : v.w[0];
@@ -241,9 +244,9 @@ __global__ void __launch_bounds__(kVecThreads)
     double tot[2];
     block_sum_t<2, T>(acc, tot);
     if (threadIdx.x == 0) {
-        double* pb = pbuf + size_t(P ^ 1) * 2 * nblk;
-        pb[2 * blockIdx.x] = tot[0];
-        pb[2 * blockIdx.x + 1] = tot[1];
+        T* pb = pbuf + size_t(P ^ 1) * 2 * nblk;
+        pb[2 * blockIdx.x] = T(tot[0]);
+        pb[2 * blockIdx.x + 1] = T(tot[1]);
     }
 }
 
@@ -253,14 +256,15 @@ __global__ void __launch_bounds__(kVecThreads)
 template <typename T, typename TB>
 __global__ void __launch_bounds__(kVecThreads)
     k_cg_init(Binned bd, CgVec<T> v, const TB* __restrict__ b, int use_x0,
-              CgScalars* __restrict__ sc, double* __restrict__ pbuf, double* __restrict__ partial) {
+              CgScalars* __restrict__ sc, T* __restrict__ pbuf, double* __restrict__ partial) {
     const double bscale = sc->bscale;
     const T* __restrict__ w1 = v.w[1];
     auto r0 = [&](int j) -> T {
         const T bj = T(double(b[j]) * bscale);
         return use_x0 ? bj - w1[j] : bj;
     };
-    double acc[2] = {0.0, 0.0}, bb[1] = {0.0}, tot[1];
+    T acc[2] = {T(0), T(0)};
+    double bb[1] = {0.0}, tot[1];
     const int M = bd.M;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) {
         const T di = v.dinv[i];
@@ -273,14 +277,15 @@ __global__ void __launch_bounds__(kVecThreads)
         v.p[i] = T(0);
         v.s[0][i] = T(0);
         v.w[0][i] = T(0);
-        acc[0] += double(ri) * double(ui);
-        acc[1] += double(ri) * double(ri);
+        acc[0] = fma(ri, ui, acc[0]);
+        acc[1] = fma(ri, ri, acc[1]);
         bb[0] += double(bi) * double(bi);
     }
-    block_sum<2>(acc);
+    double at[2];
+    block_sum_t<2, T>(acc, at);
     if (threadIdx.x == 0) {
-        pbuf[2 * blockIdx.x] = acc[0];
-        pbuf[2 * blockIdx.x + 1] = acc[1];
+        pbuf[2 * blockIdx.x] = T(at[0]);
+        pbuf[2 * blockIdx.x + 1] = T(at[1]);
     }
     if (last_block_total<1>(bb, partial, &sc->ticket, tot) && threadIdx.x == 0) {
         sc->bb = tot[0];
@@ -450,7 +455,7 @@ void launch_iteration(rbf_ctx* ctx, const CgVec<T>& v, int P, cudaStream_t cs) {
     CgScalars* sc = ctx->scal.as<CgScalars>();
     k_cg_spmv<T><<<spmv_grid_T<T>(ctx), kSpmvWarps * 32, 0, cs>>>(bd, ctx->bvals.as<T>(), v.u,
                                                                   v.w[P], P, sc);
-    k_cg_update<T><<<vec_grid(ctx), kVecThreads, 0, cs>>>(bd, v, P, sc, ctx->partial.as<double>());
+    k_cg_update<T><<<vec_grid(ctx), kVecThreads, 0, cs>>>(bd, v, P, sc, ctx->partial.as<T>());
 }
 
 // The solve graph of precision T: one conditional WHILE node whose body runs
@@ -531,7 +536,10 @@ rbf_status cg_start(rbf_ctx* ctx, const TB* b, double bscale, bool use_x0, doubl
         ctx->launches += 1;
     }
     double* part = ctx->partial.as<double>();
-    k_cg_init<T, TB><<<vec_grid(ctx), kVecThreads, 0, st>>>(bd, v, b, use_x0 ? 1 : 0, sc, part,
+    // per-block partials of the precision T in the first 4 vec_grid slots (both parities), the
+    // start kernel's (b, b) partials after them
+    k_cg_init<T, TB><<<vec_grid(ctx), kVecThreads, 0, st>>>(bd, v, b, use_x0 ? 1 : 0, sc,
+                                                            reinterpret_cast<T*>(part),
                                                             part + 4 * vec_grid(ctx));
     ctx->launches += 1;
     RBF_CUDA_TRY(cudaGetLastError());
