@@ -151,7 +151,7 @@ rbf_status rbf_destroy(rbf_ctx* ctx) {
                        &ctx->support, &ctx->x, &ctx->r, &ctx->cgv[0], &ctx->cgv[1],
                        &ctx->dinv, &ctx->dinv32, &ctx->bjinv, &ctx->bjinv32, &ctx->crow, &ctx->cdesc,
                        &ctx->partial, &ctx->scal, &ctx->csort, &ctx->sigma, &ctx->feat,
-                       &ctx->mlp_part, &ctx->astore, &ctx->woff, &ctx->wsize};
+                       &ctx->mlp_part, &ctx->astore, &ctx->amask, &ctx->woff, &ctx->wsize};
     for (rbf_buf* b : bufs) release(ctx, *b);
     if (ctx->hpinned) cudaFreeHost(ctx->hpinned);
     delete ctx;

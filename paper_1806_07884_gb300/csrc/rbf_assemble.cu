@@ -325,7 +325,9 @@ __global__ void __launch_bounds__(kThreads) k_residual(Binned bd, const int4* __
                                                        double* __restrict__ r,
                                                        int* __restrict__ support,
                                                        const long long* __restrict__ woff,
-                                                       double* __restrict__ astore) {
+                                                       double* __restrict__ astore,
+                                                       const long long* __restrict__ moff,
+                                                       unsigned int* __restrict__ amask) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ LocalCells lc;
     __shared__ double esm[kSubChunk];
@@ -369,10 +371,25 @@ __global__ void __launch_bounds__(kThreads) k_residual(Binned bd, const int4* __
         fill_phi<KIND, double>(bd, cs, n, npad, q0, p1, phi, hsm, support ? cnt : nullptr, wl);
         __syncthreads();
         const int np = min(kSubChunk, p1 - q0);
-        if (astore) {   // keep the rows of A for later residual passes: point p, candidate a
-            double* dst = astore + woff[blockIdx.x] + (long long)(q0 - p0) * n;
-            for (int e = threadIdx.x; e < np * n; e += blockDim.x)
-                dst[e] = phi[(e / n) * npad + (e % n)];
+        if (astore) {
+            // Keep the nonzeros of A for later residual passes, per sub-chunk and candidate a: a
+            // 32-bit mask of the sub-chunk's points in a's support, and their values in point
+            // order packed at the start of a's 32-slot column.
+            const long long q = (q0 - p0) / kSubChunk;
+            double* vals = astore + woff[blockIdx.x] + q * kSubChunk * n;
+            unsigned int* msk = amask + moff[blockIdx.x] + q * n;
+            for (int a = threadIdx.x; a < n; a += blockDim.x) {
+                unsigned int m = 0;
+                int j = 0;
+                for (int pp = 0; pp < np; ++pp) {
+                    const double v = phi[pp * npad + a];
+                    if (v != 0.0) {
+                        vals[(long long)a * kSubChunk + j++] = v;
+                        m |= 1u << pp;
+                    }
+                }
+                msk[a] = m;
+            }
         }
         // e_p = h_p - sum_a Phi[p][a] c_a  (one warp per point)
         for (int pp = warp; pp < np; pp += nw) {
@@ -402,13 +419,18 @@ __global__ void __launch_bounds__(kThreads) k_residual(Binned bd, const int4* __
     }
 }
 
-// The same residual from the stored rows of A (written by the FP64 pass of the FP32 assembly):
-// no distances, square roots or Wendland evaluations, only the two FP64 products per point.
+// The same residual from the stored nonzeros of A (written by the FP64 pass of the FP32
+// assembly): no distances, square roots or Wendland evaluations, and the two FP64 products
+// run over the nonzeros only. Per sub-chunk: e_p = h_p - sum_a A_pa c_a (one warp per point,
+// lanes over the candidates, a value found by the point's rank in the candidate's mask), then
+// r_a += sum_p A_pa e_p (one thread per candidate over its column).
 __global__ void __launch_bounds__(kThreads) k_residual_stored(Binned bd, const int4* __restrict__ work,
                                                               int npad, const double* __restrict__ c,
                                                               double* __restrict__ r,
                                                               const long long* __restrict__ woff,
-                                                              const double* __restrict__ astore) {
+                                                              const double* __restrict__ astore,
+                                                              const long long* __restrict__ moff,
+                                                              const unsigned int* __restrict__ amask) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ LocalCells lc;
     __shared__ double esm[kSubChunk];
@@ -418,9 +440,9 @@ __global__ void __launch_bounds__(kThreads) k_residual_stored(Binned bd, const i
     if (threadIdx.x == 0) describe_cells(bd, cell, lc);
     __syncthreads();
     const int n = lc.n;
-    double* phi = reinterpret_cast<double*>(smem);
-    double* cval = phi + kSubChunk * npad;
+    double* cval = reinterpret_cast<double*>(smem);
     int* sidx = reinterpret_cast<int*>(cval + npad);
+    unsigned int* smask = reinterpret_cast<unsigned int*>(sidx + npad);
     for (int a = threadIdx.x; a < n; a += blockDim.x) {
         int k = 0;
         while (a >= lc.off[k + 1]) ++k;
@@ -429,27 +451,36 @@ __global__ void __launch_bounds__(kThreads) k_residual_stored(Binned bd, const i
         cval[a] = c ? c[sa] : 0.0;
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const double* src0 = astore + woff[blockIdx.x];
     double racc0 = 0.0, racc1 = 0.0;
     for (int q0 = p0; q0 < p1; q0 += kSubChunk) {
         const int np = min(kSubChunk, p1 - q0);
+        const long long q = (q0 - p0) / kSubChunk;
+        const double* vals = astore + woff[blockIdx.x] + q * kSubChunk * n;
+        const unsigned int* msk = amask + moff[blockIdx.x] + q * n;
         __syncthreads();
-        const double* src = src0 + (long long)(q0 - p0) * n;
-        for (int e = threadIdx.x; e < np * n; e += blockDim.x) phi[(e / n) * npad + (e % n)] = __ldcs(src + e);
+        for (int a = threadIdx.x; a < n; a += blockDim.x) smask[a] = __ldcs(msk + a);
         if (threadIdx.x < np) hsm[threadIdx.x] = bd.ph[q0 + threadIdx.x];
         __syncthreads();
         for (int pp = warp; pp < np; pp += nw) {
+            const unsigned int below = (1u << pp) - 1u;
             double sacc = 0.0;
-            for (int a = lane; a < n; a += 32) sacc = fma(phi[pp * npad + a], cval[a], sacc);
+            for (int a = lane; a < n; a += 32) {
+                const unsigned int m = smask[a];
+                if ((m >> pp) & 1u)
+                    sacc = fma(__ldg(vals + (long long)a * kSubChunk + __popc(m & below)), cval[a], sacc);
+            }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
             if (lane == 0) esm[pp] = hsm[pp] - sacc;
         }
         __syncthreads();
-        for (int pp = 0; pp < np; ++pp) {
-            const double e = esm[pp];
-            if (threadIdx.x < n) racc0 = fma(phi[pp * npad + threadIdx.x], e, racc0);
-            if (threadIdx.x + kThreads < n) racc1 = fma(phi[pp * npad + threadIdx.x + kThreads], e, racc1);
+        for (int a = threadIdx.x; a < n; a += blockDim.x) {
+            unsigned int m = smask[a];
+            const double* col = vals + (long long)a * kSubChunk;
+            double acc = 0.0;
+            for (int j = 0; m; ++j, m &= m - 1u) acc = fma(__ldg(col + j), esm[__ffs(m) - 1], acc);
+            if (a == threadIdx.x) racc0 += acc;
+            else racc1 += acc;
         }
     }
     __syncthreads();
@@ -457,9 +488,10 @@ __global__ void __launch_bounds__(kThreads) k_residual_stored(Binned bd, const i
     if (threadIdx.x + kThreads < n && racc1 != 0.0) atomicAdd(&r[sidx[threadIdx.x + kThreads]], racc1);
 }
 
-// Values of A stored per work item: its points x the candidates of its cell's 3x3 block.
+// Storage of A per work item: its sub-chunks x the candidates of its cell's 3x3 block, 32
+// value slots (size) and one mask (msize) per sub-chunk and candidate.
 __global__ void k_work_sizes(Binned bd, const int4* __restrict__ work, int nwork,
-                             long long* __restrict__ size) {
+                             long long* __restrict__ size, long long* __restrict__ msize) {
     const int w = blockIdx.x * blockDim.x + threadIdx.x;
     if (w >= nwork) return;
     const int4 wi = work[w];
@@ -469,7 +501,9 @@ __global__ void k_work_sizes(Binned bd, const int4* __restrict__ work, int nwork
     long long n = 0;
     for (int r = max(iy - 1, 0); r <= min(iy + 1, g.gy - 1); ++r)
         n += bd.cstart[r * g.gx + xb + 1] - bd.cstart[r * g.gx + xa];
-    size[w] = (long long)(wi.z - wi.y) * n;
+    const long long nsub = (wi.z - wi.y + kSubChunk - 1) / kSubChunk;
+    size[w] = nsub * kSubChunk * n;
+    msize[w] = nsub * n;
 }
 
 template <typename T>
@@ -504,7 +538,9 @@ rbf_status launch_residual(rbf_ctx* ctx, const double* c, double* r, bool count,
     kfn<<<ctx->nwork, kThreads, sm, st>>>(view(ctx), ctx->work.as<int4>(), npad, c, r,
                                           count ? ctx->support.as<int>() : nullptr,
                                           store ? ctx->woff.as<long long>() : nullptr,
-                                          store ? ctx->astore.as<double>() : nullptr);
+                                          store ? ctx->astore.as<double>() : nullptr,
+                                          store ? ctx->moff_p : nullptr,
+                                          store ? ctx->amask.as<unsigned int>() : nullptr);
     RBF_CUDA_TRY(cudaGetLastError());
     ctx->launches += 1;
     return RBF_OK;
@@ -545,22 +581,30 @@ rbf_status assemble_run(rbf_ctx* ctx, int kernel, int prec, cudaStream_t st) {
     // residual pass (the refinement). Without room for it the residual stays matrix-free.
     ctx->astore_ok = false;
     if (ctx->store_a) {
-        if ((s = ensure(ctx, ctx->woff, sizeof(long long) * (ctx->nwork + 1), st)) != RBF_OK) return s;
-        if ((s = ensure(ctx, ctx->wsize, sizeof(long long) * ctx->nwork, st)) != RBF_OK) return s;
-        k_work_sizes<<<div_up(ctx->nwork, 256), 256, 0, st>>>(view(ctx), ctx->work.as<int4>(), ctx->nwork,
-                                                              ctx->wsize.as<long long>());
+        const int nw = ctx->nwork;
+        if ((s = ensure(ctx, ctx->woff, sizeof(long long) * 2 * (nw + 1), st)) != RBF_OK) return s;
+        if ((s = ensure(ctx, ctx->wsize, sizeof(long long) * 2 * nw, st)) != RBF_OK) return s;
+        long long* vsize = ctx->wsize.as<long long>();
+        long long* voff = ctx->woff.as<long long>();
+        k_work_sizes<<<div_up(nw, 256), 256, 0, st>>>(view(ctx), ctx->work.as<int4>(), nw, vsize,
+                                                      vsize + nw);
         ctx->launches += 1;
-        if ((s = scan_i64(ctx, ctx->wsize.as<int64_t>(), ctx->woff.as<int64_t>(), ctx->nwork, st)) != RBF_OK)
-            return s;
+        int64_t* vs64 = reinterpret_cast<int64_t*>(vsize);
+        int64_t* vo64 = reinterpret_cast<int64_t*>(voff);
+        if ((s = scan_i64(ctx, vs64, vo64, nw, st)) != RBF_OK) return s;
+        if ((s = scan_i64(ctx, vs64 + nw, vo64 + nw + 1, nw, st)) != RBF_OK) return s;
         long long* hp = static_cast<long long*>(ctx->hpinned) + 40;
-        RBF_CUDA_TRY(cudaMemcpyAsync(hp, ctx->woff.as<long long>() + ctx->nwork, sizeof(long long),
+        RBF_CUDA_TRY(cudaMemcpyAsync(hp, voff + nw, sizeof(long long), cudaMemcpyDeviceToHost, st));
+        RBF_CUDA_TRY(cudaMemcpyAsync(hp + 1, voff + 2 * nw + 1, sizeof(long long),
                                      cudaMemcpyDeviceToHost, st));
         RBF_CUDA_TRY(cudaStreamSynchronize(st));
-        const long long total = *hp;
-        if (ensure(ctx, ctx->astore, sizeof(double) * std::max<long long>(total, 1), st) == RBF_OK)
+        const long long nval = hp[0], nmask = hp[1];
+        if (ensure(ctx, ctx->astore, sizeof(double) * std::max<long long>(nval, 1), st) == RBF_OK &&
+            ensure(ctx, ctx->amask, sizeof(unsigned int) * std::max<long long>(nmask, 1), st) == RBF_OK)
             ctx->astore_ok = true;
         else
             ctx->err.clear();   // no room: matrix-free residual
+        ctx->moff_p = voff + nw + 1;
     }
     // b = A^T h and the support counts in FP64: the residual with c = 0
     RBF_CUDA_TRY(cudaMemsetAsync(ctx->bvec.p, 0, sizeof(double) * M, st));
@@ -573,12 +617,11 @@ rbf_status residual_run(rbf_ctx* ctx, const double* c_sorted, double* r_sorted, 
     const double* c = c_sorted;   // nullptr stands for c = 0, i.e. r = A^T h
     const int npad = std::max(4, (ctx->max_cand + 3) / 4 * 4);
     if (!count && ctx->astore_ok) {
-        const size_t sm = sizeof(double) * (kSubChunk * npad + npad) + sizeof(int) * npad;
-        RBF_CUDA_TRY(cudaFuncSetAttribute(k_residual_stored, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          int(sm)));
+        const size_t sm = sizeof(double) * npad + sizeof(int) * npad + sizeof(unsigned int) * npad;
         k_residual_stored<<<ctx->nwork, kThreads, sm, st>>>(view(ctx), ctx->work.as<int4>(), npad, c,
                                                             r_sorted, ctx->woff.as<long long>(),
-                                                            ctx->astore.as<double>());
+                                                            ctx->astore.as<double>(), ctx->moff_p,
+                                                            ctx->amask.as<unsigned int>());
         RBF_CUDA_TRY(cudaGetLastError());
         ctx->launches += 1;
         return RBF_OK;

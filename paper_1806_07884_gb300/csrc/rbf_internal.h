@@ -58,7 +58,8 @@ struct rbf_ctx {
     rbf_buf support;           // [M] points inside each support, sorted order
     // FP64 values of A per work item (points x candidates of the cell's 3x3 block), kept by
     // the FP32 assembly for the refinement's residual passes
-    rbf_buf astore, woff, wsize;
+    rbf_buf astore, amask, woff, wsize;   // values, masks, their offsets per work item
+    const long long* moff_p = nullptr;    // mask offsets (second half of woff)
     bool astore_ok = false;
     int store_a = 1;           // rbf_set_param("store_a")
 
