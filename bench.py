@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="fp32_refine", choices=["fp32_refine", "fp64"])
-    ap.add_argument("--tol", type=float, default=5e-12)
+    ap.add_argument("--tol", type=float, default=3e-12)
     ap.add_argument("--N", type=int, default=1_000_000)
     ap.add_argument("--M", type=int, default=100_000)
     ap.add_argument("--grid", type=int, default=1024)

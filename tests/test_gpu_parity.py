@@ -315,3 +315,39 @@ def test_stored_a_residual_matches_matrix_free(case):
         assert info["refinements"] >= 1
         assert O.rel_err(ctx.eval_grid(c, 65, 65).cpu().numpy(), f_ref) <= MIXED_BAR
         ctx.close()
+
+
+@pytest.mark.slow
+def test_bigdata_full_size_properties():
+    """The big-data workload at its full size (20 M points with 10:1 density variation, 2 M
+    Halton centres, phi_3,2, FP32 assembly and SpMV, FP64 residual and refinement): sampled
+    support counts (exact), b and FP32 B entries, the FP64 normal residual at sampled
+    centres, and sampled surface values against the oracle's one-by-one evaluation of the
+    same weights."""
+    pb = dg.config_bigdata()
+    so = O.SampledOracle(pb.points, pb.h, pb.centres, pb.R, pb.kernel)
+    rng = np.random.default_rng(1)
+    ctx = _binned(pb, prec="fp32_refine")
+    row, col, val, b, sup = [t.cpu().numpy() for t in ctx.export_upper()]
+    js = rng.choice(pb.M, 30, replace=False)
+    for j in js:
+        assert sup[j] == so.support(j)
+        assert abs(b[j] - so.b_entry(j)) <= 1e-12 * np.abs(b).max()
+    pick = rng.choice(len(val), 40, replace=False)
+    vmax = np.abs(val).max()
+    for t in pick:
+        assert abs(val[t] - so.B_entry(row[t], col[t])) <= 2e-6 * vmax     # FP32 entries
+    del row, col, val
+    c, info = ctx.solve(tol=1e-11)
+    assert info["rel_residual"] <= 1e-11
+    cn = c.cpu().numpy()
+    bmax = np.abs(b).max()
+    for j in js[:15]:
+        if sup[j] >= 3:
+            assert abs(so.normal_residual(cn, j)) <= 1e-8 * bmax
+    f = ctx.eval_grid(c, 4096, 4096).cpu().numpy()
+    gx = np.linspace(0, 1, 4096)
+    for _ in range(20):
+        i, j = rng.integers(0, 4096, 2)
+        assert abs(f[i, j] - so.f(cn, (gx[j], gx[i]))) <= 1e-12 * np.abs(f).max()
+    ctx.close()
