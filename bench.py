@@ -26,6 +26,7 @@ one system does not shard), weak scaling.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -38,17 +39,34 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 
-# DRAM bytes (read + write) per launch of the solver's SpMV from one ncu capture
-# (profiles/spmv_update_fp32_terrain_1M.md), valid while the solver source is unchanged.
-SPMV_TRAFFIC = {"src_sha256_16": "321c46b1a00541b1", "bytes": 76288 + 88064}
+# DRAM traffic of the SpMV kernels from ncu captures (profiles/spmv_update_fp32_terrain_1M.md,
+# profiles/batched_spmv_update_128tiles.md), valid while the captured kernel's source -- its
+# function text and the shared SpMV device code -- is unchanged.
+CSRC = os.path.join(ROOT, "paper_1806_07884_gb300", "csrc")
+SPMV_TRAFFIC = {"sha": "1e58bb809b2dfef6", "bytes": 194304 + 157184}
+BSPMV_TRAFFIC = {"sha": "0bd435b76eca1a27", "per_alg_byte": (303618304 + 11011840) / 302918784}
+
+
+def kernel_sha(fname, signature):
+    """sha256 (16 hex digits) of the kernel whose definition starts at `signature` in csrc/fname
+    (up to its closing brace at column 0) together with csrc/rbf_cg.cuh."""
+    with open(os.path.join(CSRC, fname)) as f:
+        text = f.read()
+    i = text.index(signature)
+    j = text.index("\n}\n", i)
+    with open(os.path.join(CSRC, "rbf_cg.cuh")) as f:
+        common = f.read()
+    return hashlib.sha256((text[i:j] + common).encode()).hexdigest()[:16]
 
 
 def spmv_traffic():
-    import hashlib
-    path = os.path.join(ROOT, "paper_1806_07884_gb300", "csrc", "rbf_solve.cu")
-    with open(path, "rb") as f:
-        sha = hashlib.sha256(f.read()).hexdigest()[:16]
-    return SPMV_TRAFFIC["bytes"] if sha == SPMV_TRAFFIC["src_sha256_16"] else None
+    ok = kernel_sha("rbf_solve.cu", "k_spmv(Binned bd") == SPMV_TRAFFIC["sha"]
+    return SPMV_TRAFFIC["bytes"] if ok else None
+
+
+def bspmv_traffic(alg_bytes):
+    ok = kernel_sha("rbf_batch.cu", "k_bcg_spmv(Binned bd") == BSPMV_TRAFFIC["sha"]
+    return int(BSPMV_TRAFFIC["per_alg_byte"] * alg_bytes) if ok else None
 
 
 def parse():
@@ -278,7 +296,8 @@ def bench_batched(args, rank, dev, stream, flush, hbm, peak_source):
     ach = spmv_bytes / (spmv_ms * 1e-3) / 1e9
     roof = {"bound": "hbm", "kernel": f"k_bcg_spmv<{'float' if vb == 4 else 'double'}>",
             "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s", "frac": round(ach / hbm, 4),
-            "traffic": None, "algorithmic_bytes": spmv_bytes, "launch_ms": round(spmv_ms, 5),
+            "traffic": bspmv_traffic(spmv_bytes), "traffic_note": "scaled from a 128-tile capture",
+            "algorithmic_bytes": spmv_bytes, "launch_ms": round(spmv_ms, 5),
             "peak_source": peak_source}
     out = {"workload": f"{args.tiles} tiles, N log-uniform in [2000, 200000], M = N/10, "
                        f"Wendland phi_3,1, K=30, sum N = {Ntot}, sum M = {Mtot}",
