@@ -98,6 +98,22 @@ def env_rank():
             int(os.environ.get("WORLD_SIZE", 1)))
 
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest of the ranks' values of x (the slowest rank sets the job's time)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: int, world: int, ms: float) -> float:
+    """Units per second of the whole job: every rank processes units_per_rank in ms."""
+    return world * units_per_rank / (ms * 1e-3)
+
+
 # ----------------------------------------------------------------------------------------
 # clocks sampled during the timed region
 # ----------------------------------------------------------------------------------------
@@ -423,11 +439,8 @@ def main():
     launches = ctx.launch_count() - launches0
     clocks = sampler.stop()
     ms = statistics.mean(step_ms)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * N / (ms * 1e-3)
+    ms = max_over_ranks(ms, world, dev)
+    value = whole_job_rate(N, world, ms)
 
     # ---- per-phase split of one step (not part of the timed number)
     phases = {}
@@ -541,11 +554,8 @@ def main():
             e1.synchronize()
             e_ms.append(e0.elapsed_time(e1))
         ems = statistics.mean(e_ms)
-        if world > 1:
-            t = torch.tensor([ems], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
-        e2e = {"value": world * N / (ems * 1e-3), "unit": "points/s", "h2d_bytes_per_step": h2d,
+        ems = max_over_ranks(ems, world, dev)
+        e2e = {"value": whole_job_rate(N, world, ems), "unit": "points/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": round(ems, 3)}
 
     # ---- the batched workload (its own sub-object of the line)
