@@ -444,6 +444,22 @@ __global__ void __launch_bounds__(NT)
     const int i0 = blockIdx.x * NT;
     if (i0 >= bd.M) return;
     const int i1 = min(i0 + NT, bd.M);
+    // the row's values, loaded before the per-tile prologue so that their latency overlaps it
+    const T* __restrict__ rP = P ? v.r[1] : v.r[0];
+    const T* __restrict__ sP = P ? v.s[1] : v.s[0];
+    const T* __restrict__ wP = P ? v.w[1] : v.w[0];
+    const int i = i0 + threadIdx.x;
+    int4 cm = make_int4(0, 0, 0, 0);
+    T f_d = T(0), f_w = T(0), f_s = T(0), f_p = T(0), f_u = T(0), f_r = T(0);
+    if (i < i1) {
+        cm = bd.crow[i];
+        f_d = v.dinv[i];
+        f_w = wP[i];
+        f_s = sP[i];
+        f_p = v.p[i];
+        f_u = v.u[i];
+        f_r = rP[i];
+    }
     int t0, span;
     block_tiles(bd, i0, i1, t0, span);
     const int maxit = tc.bs->maxit;
@@ -494,34 +510,28 @@ __global__ void __launch_bounds__(NT)
         sred[1][j] = 0.0;
     }
     __syncthreads();
-    const T* __restrict__ rP = P ? v.r[1] : v.r[0];
-    const T* __restrict__ sP = P ? v.s[1] : v.s[0];
-    const T* __restrict__ wP = P ? v.w[1] : v.w[0];
     T* __restrict__ rQ = P ? v.r[0] : v.r[1];
     T* __restrict__ sQ = P ? v.s[0] : v.s[1];
     T* __restrict__ wQ = P ? v.w[0] : v.w[1];
-    const int i = i0 + threadIdx.x;
     int key = INT_MAX;
     T acc[2] = {T(0), T(0)};
     // new residuals of the block's rows, for the block-Jacobi step (rows of a cell outside the
     // block are recomputed with the same operations)
     __shared__ T rsm[NT];
     bool go = false;
-    int4 cm = make_int4(0, 0, 0, 0);
     T ta = T(0), tb = T(0), di = T(0), ri = T(0);
     if (i < i1) {
-        cm = bd.crow[i];
         key = cm.w;
         const int j = cm.w - t0;
         go = s_go[j] != 0;
         if (go) {
             ta = s_alpha[j];
             tb = s_beta[j];
-            di = v.dinv[i];
-            const T wi = di == T(0) ? T(0) : wP[i];
-            const T si = fma(tb, sP[i], wi);
-            const T pi = fma(tb, v.p[i], v.u[i]);
-            ri = di == T(0) ? T(0) : fma(-ta, si, rP[i]);
+            di = f_d;
+            const T wi = di == T(0) ? T(0) : f_w;
+            const T si = fma(tb, f_s, wi);
+            const T pi = fma(tb, f_p, f_u);
+            ri = di == T(0) ? T(0) : fma(-ta, si, f_r);
             sQ[i] = si;
             v.p[i] = pi;
             v.x[i] = fma(ta, pi, v.x[i]);

@@ -138,6 +138,21 @@ __global__ void __launch_bounds__(kVecThreads)
     __shared__ int s_go;
     static_assert(kAccSlots == 64, "two slots per lane");
     const int nblk = gridDim.x;
+    const int M = bd.M;
+    const T* __restrict__ rP = P ? v.r[1] : v.r[0];
+    const T* __restrict__ sP = P ? v.s[1] : v.s[0];
+    const T* __restrict__ wP = P ? v.w[1] : v.w[0];
+    // the first chunk's row values, loaded before the prologue so that their latency overlaps it
+    const int i_first = blockIdx.x * kVecThreads + threadIdx.x;
+    T f_d = T(0), f_w = T(0), f_s = T(0), f_p = T(0), f_u = T(0), f_r = T(0);
+    if (i_first < M) {
+        f_d = v.dinv[i_first];
+        f_w = wP[i_first];
+        f_s = sP[i_first];
+        f_p = v.p[i_first];
+        f_u = v.u[i_first];
+        f_r = rP[i_first];
+    }
     if (threadIdx.x < 32) {
         const int lane = threadIdx.x;
         const CgSlot sl = sc->sl[P];
@@ -199,14 +214,10 @@ __global__ void __launch_bounds__(kVecThreads)
     __syncthreads();
     if (!s_go) return;
     const T ta = s_ab[0], tb = s_ab[1];
-    const T* __restrict__ rP = P ? v.r[1] : v.r[0];
-    const T* __restrict__ sP = P ? v.s[1] : v.s[0];
-    const T* __restrict__ wP = P ? v.w[1] : v.w[0];
     T* __restrict__ rQ = P ? v.r[0] : v.r[1];
     T* __restrict__ sQ = P ? v.s[0] : v.s[1];
     T* __restrict__ wQ = P ? v.w[0] : v.w[1];
     T acc[2] = {T(0), T(0)};
-    const int M = bd.M;
     // The new residual of each row of the chunk is kept in shared memory for the block-Jacobi
     // step; rows of a cell outside the chunk are recomputed with the same operations.
     __shared__ T rsm[kVecThreads];
@@ -215,11 +226,12 @@ __global__ void __launch_bounds__(kVecThreads)
         const bool valid = i < M;
         T di = T(0), ri = T(0);
         if (valid) {
-            di = v.dinv[i];
-            const T wi = di == T(0) ? T(0) : wP[i];
-            const T si = fma(tb, sP[i], wi);
-            const T pi = fma(tb, v.p[i], v.u[i]);
-            ri = di == T(0) ? T(0) : fma(-ta, si, rP[i]);
+            const bool first = i == i_first;
+            di = first ? f_d : v.dinv[i];
+            const T wi = di == T(0) ? T(0) : (first ? f_w : wP[i]);
+            const T si = fma(tb, first ? f_s : sP[i], wi);
+            const T pi = fma(tb, first ? f_p : v.p[i], first ? f_u : v.u[i]);
+            ri = di == T(0) ? T(0) : fma(-ta, si, first ? f_r : rP[i]);
             sQ[i] = si;
             v.p[i] = pi;
             v.x[i] = fma(ta, pi, v.x[i]);
