@@ -106,6 +106,9 @@ typedef struct {
     int64_t pinned;          /* centres of this tile with fewer than min_support points */
     int status;              /* rbf_status of this tile: RBF_OK, RBF_ERR_NOT_CONVERGED or
                                 RBF_ERR_BREAKDOWN */
+    int promoted;            /* 1 if this tile was finished by FP64 CG after its FP32
+                                refinement stalled or ran out of steps; tiles that converged
+                                in FP32 keep their refined iterate */
 } rbf_tile_info;
 
 /* Create / destroy a context bound to CUDA device `device`. */
@@ -237,7 +240,8 @@ rbf_status rbf_bin_tiles(rbf_ctx* ctx, const rbf_tile* tiles, int T, const doubl
  * maxit, min_support as for rbf_solve, applied per tile. tile_info: HOST array of T entries
  * (may be NULL); info: HOST totals (may be NULL): iterations = largest per-tile count,
  * refinements = most refinement steps, rel_residual = largest per-tile value, pinned = sum,
- * promoted as for rbf_solve (applies to the whole batch). Synchronises `stream`. Returns
+ * promoted = 1 if any tile was finished in FP64 (later solves on this context then run in
+ * FP64, as for rbf_solve). Synchronises `stream`. Returns
  * RBF_OK when every tile converged, else RBF_ERR_BREAKDOWN if some tile broke down, else
  * RBF_ERR_NOT_CONVERGED; c holds every tile's last iterate in all cases. */
 rbf_status rbf_solve_tiles(rbf_ctx* ctx, double* c, int use_c0, double tol, int maxit,

@@ -194,7 +194,8 @@ class Context:
                  rel_residual=info.rel_residual, pinned=info.pinned, promoted=info.promoted,
                  status=s)
         tl = [dict(iterations=t.iterations, refinements=t.refinements,
-                   rel_residual=t.rel_residual, pinned=t.pinned, status=t.status) for t in tinfo]
+                   rel_residual=t.rel_residual, pinned=t.pinned, status=t.status,
+                   promoted=t.promoted) for t in tinfo]
         if info.promoted:
             self.prec = "fp64"
         if s != 0 and raise_on_fail:

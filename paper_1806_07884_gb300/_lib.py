@@ -33,7 +33,8 @@ class Tile(C.Structure):
 
 class TileInfo(C.Structure):
     _fields_ = [("iterations", C.c_int), ("refinements", C.c_int),
-                ("rel_residual", C.c_double), ("pinned", C.c_int64), ("status", C.c_int)]
+                ("rel_residual", C.c_double), ("pinned", C.c_int64), ("status", C.c_int),
+                ("promoted", C.c_int)]
 
 
 _P = C.c_void_p

@@ -294,21 +294,16 @@ __global__ void k_zero_masked(int M, double* __restrict__ x, const float* __rest
 }
 
 template <typename T>
-__global__ void k_tile_to_sorted(const double* __restrict__ src, const int* __restrict__ perm,
-                                 const T* __restrict__ dinv, T* __restrict__ dst, int M) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s < M) dst[s] = dinv[s] == T(0) ? T(0) : T(src[perm[s]]);
-}
-template <typename T>
 __global__ void k_tile_from_sorted(const T* __restrict__ src, const int* __restrict__ perm,
                                    double* __restrict__ dst, int M) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s < M) dst[perm[s]] = double(src[s]);
 }
-__global__ void k_copy_masked(int M, const double* __restrict__ src, const double* __restrict__ dinv,
-                              double* __restrict__ dst) {
+template <typename T>
+__global__ void k_copy_masked(int M, const double* __restrict__ src, const T* __restrict__ dinv,
+                              T* __restrict__ dst) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < M) dst[i] = dinv[i] == 0.0 ? 0.0 : src[i];
+    if (i < M) dst[i] = dinv[i] == T(0) ? T(0) : T(src[i]);
 }
 
 // f(x) = sum_j c_j phi(||x - xi_j|| / R_t) for a query x of tile t: the centres of the 3x3
@@ -871,9 +866,12 @@ struct BcgOut {
     std::vector<double> rel;
 };
 
-// Batched CG on B (precision T) for B x_t = bscale_t b_t on the active tiles.
+// Batched CG on B (precision T) for B x_t = bscale_t b_t on the active tiles, from x0
+// (sorted order, FP64; null for x = 0). Every row of x0 is copied in, so tiles that take no
+// part keep the iterate x0 gives them. The copy follows the configuration choice: the
+// autotuner times its iterations on the solver's own vectors.
 template <typename T, typename TB>
-rbf_status run_bcg(rbf_ctx* ctx, const TB* b, bool use_x0, const std::vector<char>& active,
+rbf_status run_bcg(rbf_ctx* ctx, const TB* b, const double* x0, const std::vector<char>& active,
                    const std::vector<double>& bscale, const std::vector<double>& tol, int maxit,
                    BcgOut* out, cudaStream_t st) {
     rbf_status s;
@@ -882,7 +880,12 @@ rbf_status run_bcg(rbf_ctx* ctx, const TB* b, bool use_x0, const std::vector<cha
     cudaGraphExec_t ex;
     if ((s = bcg_graph<T>(ctx, cf, &ex)) != RBF_OK) return s;
     if ((s = write_tile_state(ctx, active, bscale, tol, maxit, st)) != RBF_OK) return s;
-    if ((s = bcg_start<T, TB>(ctx, b, use_x0, st)) != RBF_OK) return s;
+    if (x0) {
+        const CgVec<T> v = cg_vectors<T>(ctx);
+        k_copy_masked<T><<<std::max(1, div_up(ctx->M, 256)), 256, 0, st>>>(ctx->M, x0, v.dinv, v.x);
+        ctx->launches += 1;
+    }
+    if ((s = bcg_start<T, TB>(ctx, b, x0 != nullptr, st)) != RBF_OK) return s;
     RBF_CUDA_TRY(cudaGraphLaunch(ex, st));
     const TileLayout L(ctx->T);
     char* h = static_cast<char*>(ctx->hbt);
@@ -1127,23 +1130,24 @@ rbf_status solve_tiles_run(rbf_ctx* ctx, double* c, int use_c0, double tol, int 
     std::vector<int> iters(T, 0), refs(T, 0), state(T, kConverged);
     std::vector<double> rel(T, 0.0);
     std::vector<int64_t> npin(T, 0);
+    std::vector<char> tpro(T, 0);   // tiles finished in FP64 after their FP32 refinement
     int promoted = 0;
     const int nb = div_up(M, 256);
 
-    auto fp64_solve = [&](const std::vector<char>& active, bool x_ready) -> rbf_status {
-        // FP64 batched CG; x_ready: the FP64 CG's x already holds the start vector
+    auto fp64_solve = [&](const std::vector<char>& active, const double* x0) -> rbf_status {
+        // FP64 batched CG from x0 (sorted order), else from the caller's c0, else from 0
         ENS(cgv[0], sizeof(double) * kCgVecs * size_t(M));
         const CgVec<double> v = cg_vectors<double>(ctx);
-        bool use_x0 = x_ready;
-        if (!x_ready && use_c0) {
-            k_tile_to_sorted<double><<<nb, 256, 0, st>>>(c, bd.cperm, v.dinv, v.x, M);
+        if (!x0 && use_c0) {
+            double* c0s = ctx->r.as<double>();   // free in the FP64 path
+            launch_gather_sorted(c, bd.cperm, c0s, M, st);
             ctx->launches += 1;
-            use_x0 = true;
+            x0 = c0s;
         }
         std::vector<double> one(T, 1.0), tl(T, tol);
         BcgOut o;
-        rbf_status s2 = run_bcg<double, double>(ctx, ctx->bvec.as<double>(), use_x0, active, one,
-                                                tl, maxit, &o, st);
+        rbf_status s2 = run_bcg<double, double>(ctx, ctx->bvec.as<double>(), x0, active, one, tl,
+                                                maxit, &o, st);
         if (s2 != RBF_OK) return s2;
         for (int t = 0; t < T; ++t) {
             if (!active[t]) continue;
@@ -1164,7 +1168,7 @@ rbf_status solve_tiles_run(rbf_ctx* ctx, double* c, int use_c0, double tol, int 
         if ((s = tile_norms<double>(ctx, nullptr, ctx->dinv.as<double>(), nullptr, &npin, st)) != RBF_OK)
             return s;
         std::vector<char> all(T, 1);
-        if ((s = fp64_solve(all, false)) != RBF_OK) return s;
+        if ((s = fp64_solve(all, nullptr)) != RBF_OK) return s;
     } else {
         ENS(cgv[1], sizeof(float) * kCgVecs * size_t(M));
         ENS(dinv32, sizeof(float) * M);
@@ -1200,8 +1204,9 @@ rbf_status solve_tiles_run(rbf_ctx* ctx, double* c, int use_c0, double tol, int 
             bn[t] = sqrt(bn2[t]);
             rn[t] = sqrt(rn2[t]);
         }
-        std::vector<char> conv(T, 0), active(T, 0);
-        bool stalled = false;
+        // stall[t]: tile t's refinement stopped helping (or its FP32 CG broke down before a
+        // step); it leaves the FP32 loop and is finished in FP64, the other tiles go on
+        std::vector<char> conv(T, 0), active(T, 0), stall(T, 0);
         double* dscale = reinterpret_cast<double*>(ctx->tred.as<char>() + RedLayout(T).scale);
         std::vector<double> hscale(T);
         for (int outer = 0;; ++outer) {
@@ -1210,7 +1215,7 @@ rbf_status solve_tiles_run(rbf_ctx* ctx, double* c, int use_c0, double tol, int 
                 const double rl = bn[t] > 0.0 ? rn[t] / bn[t] : 0.0;
                 rel[t] = rl;
                 if (!conv[t] && ((rl <= tol && !approx_r) || rn[t] == 0.0)) conv[t] = 1;
-                active[t] = !conv[t];
+                active[t] = !conv[t] && !stall[t];
                 nact += active[t];
             }
             if (nact == 0 || outer == ctx->max_refine) break;
@@ -1221,7 +1226,7 @@ rbf_status solve_tiles_run(rbf_ctx* ctx, double* c, int use_c0, double tol, int 
                 itol[t] = std::max(ctx->inner_tol, 0.5 * tol / rel[t]);
             }
             BcgOut o;
-            if ((s = run_bcg<float, double>(ctx, r64, false, active, bsc, itol, maxit, &o, st)) != RBF_OK)
+            if ((s = run_bcg<float, double>(ctx, r64, nullptr, active, bsc, itol, maxit, &o, st)) != RBF_OK)
                 return s;
             for (int t = 0; t < T; ++t) {
                 hscale[t] = active[t] ? rn[t] : 0.0;
@@ -1230,7 +1235,7 @@ rbf_status solve_tiles_run(rbf_ctx* ctx, double* c, int use_c0, double tol, int 
                 refs[t] += 1;
                 // an inner breakdown before any step (FP32 rounding can make B32 indefinite on
                 // a very ill-conditioned tile) leaves nothing to apply: hand over to FP64
-                if (o.state[t] == kBreakdown && o.it[t] == 0) stalled = true;
+                if (o.state[t] == kBreakdown && o.it[t] == 0) stall[t] = 1;
             }
             RBF_CUDA_TRY(cudaMemcpyAsync(dscale, hscale.data(), sizeof(double) * T,
                                          cudaMemcpyHostToDevice, st));
@@ -1242,16 +1247,11 @@ rbf_status solve_tiles_run(rbf_ctx* ctx, double* c, int use_c0, double tol, int 
             if ((s = tile_norms<float>(ctx, r64, dinv32, &rn2, nullptr, st)) != RBF_OK) return s;
             approx_r = false;
             for (int t = 0; t < T; ++t) {
-                if (!active[t]) continue;   // converged tiles keep their iterate and residual
+                if (!active[t]) continue;   // other tiles keep their iterate and residual
                 const double rnew = sqrt(rn2[t]);
-                if (!(rnew < 0.5 * rn[t])) {
-                    stalled = true;
-                    rn[t] = std::min(rn[t], rnew);
-                } else {
-                    rn[t] = rnew;
-                }
+                if (!(rnew < 0.5 * rn[t])) stall[t] = 1;
+                rn[t] = rnew;
             }
-            if (stalled) break;
         }
         for (int t = 0; t < T; ++t) {
             rel[t] = bn[t] > 0.0 ? rn[t] / bn[t] : 0.0;
@@ -1273,13 +1273,8 @@ rbf_status solve_tiles_run(rbf_ctx* ctx, double* c, int use_c0, double tol, int 
             ENS(bjinv, sizeof(double) * std::max<int64_t>(ctx->nbj, 1));
             RBF_CUDA_TRY(cudaMemsetAsync(npin_d, 0, sizeof(int), st));
             if ((s = prec_setup_run(ctx, RBF_FP64, min_support, npin_d, st)) != RBF_OK) return s;
-            ENS(cgv[0], sizeof(double) * kCgVecs * size_t(M));
-            const CgVec<double> v64 = cg_vectors<double>(ctx);
-            k_copy_masked<<<nb, 256, 0, st>>>(M, x64, v64.dinv, v64.x);
-            ctx->launches += 1;
-            std::vector<char> todo(T);
-            for (int t = 0; t < T; ++t) todo[t] = !conv[t];
-            if ((s = fp64_solve(todo, true)) != RBF_OK) return s;
+            for (int t = 0; t < T; ++t) tpro[t] = !conv[t];
+            if ((s = fp64_solve(tpro, x64)) != RBF_OK) return s;
         }
     }
     RBF_CUDA_TRY(cudaGetLastError());
@@ -1300,6 +1295,7 @@ rbf_status solve_tiles_run(rbf_ctx* ctx, double* c, int use_c0, double tol, int 
             tinfo[t].rel_residual = rel[t];
             tinfo[t].pinned = npin[t];
             tinfo[t].status = ts;
+            tinfo[t].promoted = tpro[t];
         }
     }
     tot.promoted = promoted;

@@ -20,14 +20,14 @@ import numpy as np
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--tiles", type=int, default=2048)
+    ap.add_argument("--tiles", type=int, default=10000)
     ap.add_argument("--terrain", type=int, default=4, help="full-size terrains for training")
     ap.add_argument("--epochs", type=int, default=10)
     ap.add_argument("--batch", type=int, default=8192)
     ap.add_argument("--lr", type=float, default=3e-3)
     ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--eval-tiles", type=int, default=256)
-    ap.add_argument("--tol", type=float, default=1e-11)
+    ap.add_argument("--eval-tiles", type=int, default=512)
+    ap.add_argument("--tol", type=float, default=3e-12)
     ap.add_argument("--out", required=True)
     args = ap.parse_args()
 

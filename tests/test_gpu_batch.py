@@ -252,6 +252,62 @@ def test_batched_warm_start():
     ctx.close()
 
 
+def test_batched_start_vector_survives_the_autotuner():
+    """The first solve of a fresh context tunes its launch configuration by timing CG
+    iterations on the solver's own vectors; a start vector must reach the solve intact. From
+    a converged FP64 fit every tile starts below its tolerance and takes no step."""
+    pbs = _tiles_small()[:4]
+    tiles, cx, cy, px, py, hh = pkg.pack_tiles(_problems(pbs))
+    d = [_dev(a) for a in (cx, cy, px, py, hh)]
+    ctx = pkg.Context()
+    ctx.bin_tiles(tiles, *d)
+    ctx.assemble("w31", "fp64")
+    c1, i1, t1 = ctx.solve_tiles(tol=1e-13)
+    ctx.close()
+    ctx = pkg.Context()                             # untuned: the autotuner runs first
+    ctx.bin_tiles(tiles, *d)
+    ctx.assemble("w31", "fp64")
+    c2, i2, t2 = ctx.solve_tiles(tol=1e-12, c0=c1)
+    assert all(t["iterations"] <= 2 and t["status"] == OK for t in t2), t2
+    assert O.rel_err(c2.cpu().numpy(), c1.cpu().numpy()) <= 1e-12
+    ctx.close()
+
+
+def test_batched_promotion_finishes_only_the_unconverged_tiles():
+    """FP32 refinement cut short (3 steps to 1e-8): the tiles that converged keep their refined
+    iterates, the clustered tile is finished by FP64 CG -- on a fresh context, whose FP64
+    solve first tunes its launch configuration on the solver's own vectors. Every tile's
+    returned weights meet the tolerance in the oracle's FP64 normal residual (over unpinned
+    centres). FP32 rounding order varies from run to run, so up to four fresh contexts are
+    tried for a batch with both kinds of tile."""
+    pbs = _tiles_small()
+    tiles, cx, cy, px, py, hh = pkg.pack_tiles(_problems(pbs))
+    d = [_dev(a) for a in (cx, cy, px, py, hh)]
+    tol = 1e-8
+    mixed = False
+    for attempt in range(4):
+        ctx = pkg.Context()
+        ctx.bin_tiles(tiles, *d)
+        ctx.assemble("w31", "fp32_refine")
+        ctx.set_param("max_refinements", 3)
+        c, info, tinfo = ctx.solve_tiles(tol=tol)
+        ctx.close()
+        for k, pb in enumerate(pbs):
+            t = tiles[k]
+            _, ref = _oracle(pb, ("small", k))
+            ck = c[t["c0"]:t["c0"] + t["M"]].cpu().numpy()
+            A, free = ref["A"], ~ref["pinned"]
+            r = A.T @ (pb.h - A @ ck)
+            rel = np.linalg.norm(r[free]) / np.linalg.norm(ref["b"][free])
+            assert tinfo[k]["status"] == OK and rel <= 1.5 * tol, (k, rel, tinfo[k])
+        pro = [t["promoted"] for t in tinfo]
+        assert info["promoted"] == int(any(pro))
+        if any(pro) and not all(pro):
+            mixed = True
+            break
+    assert mixed, pro
+
+
 def test_autotuner_choice_and_forced_configs_agree():
     pbs = [dg.tile(1030 + k, N=n) for k, n in enumerate((3000, 9000, 5000, 12000))]
     tiles, cx, cy, px, py, hh = pkg.pack_tiles(_problems(pbs))
