@@ -460,16 +460,17 @@ __global__ void __launch_bounds__(NT)
     const int maxit = tc.bs->maxit;
     for (int j = threadIdx.x; j < span; j += NT) {
         const int t = t0 + j;
-        // the step in the solver's precision T (every block spanning the tile repeats it)
+        // the step in the solver's precision T (every block spanning the tile repeats it);
+        // the tile's values are all loaded before the state decides which are used
         const TSlot sl = slP[t];
+        const T g = T(__ldcg(gP + t)), rr = T(__ldcg(rrP + t)), d = T(__ldcg(dlP + t));
+        const T tol2 = T(tc.tol2[t]), bb = T(__ldcg(tc.bb + t));
         int state = sl.state;
         T alpha = T(0), beta = T(0);
-        const T g = T(__ldcg(gP + t)), rr = T(__ldcg(rrP + t));
         if (state == kRunning) {
-            const T d = T(__ldcg(dlP + t));
             if (!isfinite(g) || !isfinite(rr)) {
                 state = kBreakdown;
-            } else if (rr <= T(tc.tol2[t]) * T(__ldcg(tc.bb + t))) {
+            } else if (rr <= tol2 * bb) {
                 state = kConverged;
             } else if (sl.it >= maxit) {
                 state = kMaxIt;

@@ -29,6 +29,8 @@
 
 #include <algorithm>
 
+#include <type_traits>
+
 #include "rbf_cg.cuh"
 
 namespace rbf {
@@ -105,12 +107,13 @@ __global__ void __launch_bounds__(kSpmvWarps * 32, sizeof(T) == 4 ? 3 : 1)
 //   p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s, u = D^-1 r
 // It stops when (r, r) <= tol^2 (b, b).
 
-// w += B u (w zero on entry); delta = u^T B u into the slots of sc->acc_delta.
+// w += B u (w zero on entry); delta = u^T B u into the slots of sc->acc_delta. It does not
+// wait for the solver's state: after the solve stops (at most kItersPerBody - 1 SpMVs before
+// the loop condition is read) its w and delta go unused, and the next start resets the slots.
 template <typename T>
 __global__ void __launch_bounds__(kSpmvWarps * 32, sizeof(T) == 4 ? 3 : 1)
     k_cg_spmv(Binned bd, const T* __restrict__ B, const T* __restrict__ u, T* __restrict__ w,
               int P, CgScalars* __restrict__ sc) {
-    if (sc->sl[P].state != kRunning) return;
     const int lane = threadIdx.x & 31;
     const int gw = blockIdx.x * kSpmvWarps + (threadIdx.x >> 5);
     const int nw = gridDim.x * kSpmvWarps;
@@ -130,6 +133,7 @@ __global__ void __launch_bounds__(kSpmvWarps * 32, sizeof(T) == 4 ? 3 : 1)
 // The scalar step is taken in the solver's precision T (FP32 for the FP32 inner solver, whose
 // iterates the FP64 refinement corrects): every block repeats it, and FP64 issues at 1/64
 // of the FP32 rate on this GPU.
+constexpr int kPartBatch = 8;   // per-block partials loaded per lane before they are summed
 template <typename T>
 __global__ void __launch_bounds__(kVecThreads)
     k_cg_update(Binned bd, CgVec<T> v, int P, CgScalars* __restrict__ sc,
@@ -156,16 +160,27 @@ __global__ void __launch_bounds__(kVecThreads)
     if (threadIdx.x < 32) {
         const int lane = threadIdx.x;
         const CgSlot sl = sc->sl[P];
-        int state = sl.state;
-        T g = T(0), rr = T(0), d = T(0);
-        if (state == kRunning) {
-            const T* pb = pbuf + size_t(P) * 2 * nblk;
-            for (int b = lane; b < nblk; b += 32) {
-                g += __ldcg(pb + 2 * b);
-                rr += __ldcg(pb + 2 * b + 1);
+        // The partials (gamma, (r, r)) of block b are adjacent: one vector load each, up to
+        // kPartBatch per lane in flight before the first add (the sums keep block order).
+        using T2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
+        const T2* pb = reinterpret_cast<const T2*>(pbuf + size_t(P) * 2 * nblk);
+        T g = T(0), rr = T(0);
+        T d = T(__ldcg(&sc->acc_delta[P][lane])) + T(__ldcg(&sc->acc_delta[P][lane + 32]));
+        for (int b0 = lane; b0 < nblk; b0 += 32 * kPartBatch) {
+            T2 pv[kPartBatch];
+#pragma unroll
+            for (int k = 0; k < kPartBatch; ++k) {
+                const int b = b0 + 32 * k;
+                pv[k] = b < nblk ? __ldcg(pb + b) : T2{T(0), T(0)};
             }
-            d = T(__ldcg(&sc->acc_delta[P][lane])) + T(__ldcg(&sc->acc_delta[P][lane + 32]));
+#pragma unroll
+            for (int k = 0; k < kPartBatch; ++k) {
+                g += pv[k].x;
+                rr += pv[k].y;
+            }
         }
+        int state = sl.state;
+        if (state != kRunning) g = rr = d = T(0);
         g = warp_sum<T>(g);
         rr = warp_sum<T>(rr);
         d = warp_sum<T>(d);
