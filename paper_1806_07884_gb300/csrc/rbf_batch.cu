@@ -53,6 +53,9 @@ struct BatchScal {
     unsigned int ndone;        // tiles that have stopped (or take no part in this solve)
     int T, maxit;
     int passes;                // loop passes of the solve graph so far
+    int n_spmv, n_upd;         // items in the current work lists
+    unsigned int ndone_built;  // ndone when the work lists were built
+    int built;                 // the work lists belong to this solve
 };
 
 // Device view of the per-tile arrays (one allocation, layout in TileLayout).
@@ -114,6 +117,51 @@ struct TileLayout {
         v.out_it = reinterpret_cast<int*>(b + out_it);
         v.out_state = reinterpret_cast<int*>(b + out_state);
         return v;
+    }
+};
+
+// Per-tile ranges and the CG work lists (twork). A tile's non-empty cells are consecutive in
+// the cell list and its centres consecutive in the sorted order (bands follow tile order).
+// Work items cover one tile each: SpMV items {first, end} of `chunk` cells of the cell list,
+// update items {first, end} of `nt` rows; .z the tile, .w = 1 on a tile's first update item
+// (the tile's owner).
+struct TileWork {
+    int *clb, *cle;            // [T] tile t's cells: cell-list entries clb[t] .. cle[t]-1
+    int *rb, *re;              // [T] tile t's rows (sorted centres) rb[t] .. re[t]-1
+    int4* items_s;             // [cap_s] SpMV items
+    int4* items_u;             // [cap_u] update items
+};
+struct WorkLayout {
+    size_t clb, cle, rb, re, items_s, items_u, ranges_end, total;
+    int cap_s, cap_u;
+    // capacities for chunk >= 1 cells and nt >= 128 rows per item
+    WorkLayout(int T, int ncl, int M) {
+        cap_s = ncl + T;
+        cap_u = div_up(M, 128) + T;
+        size_t o = 0;
+        auto take = [&](size_t n) {
+            const size_t r = o;
+            o += (n + 15) / 16 * 16;
+            return r;
+        };
+        clb = take(4 * size_t(T));
+        cle = take(4 * size_t(T));
+        rb = take(4 * size_t(T));
+        re = take(4 * size_t(T));
+        ranges_end = o;
+        items_s = take(sizeof(int4) * size_t(cap_s));
+        items_u = take(sizeof(int4) * size_t(cap_u));
+        total = o;
+    }
+    TileWork view(char* b) const {
+        TileWork w;
+        w.clb = reinterpret_cast<int*>(b + clb);
+        w.cle = reinterpret_cast<int*>(b + cle);
+        w.rb = reinterpret_cast<int*>(b + rb);
+        w.re = reinterpret_cast<int*>(b + re);
+        w.items_s = reinterpret_cast<int4*>(b + items_s);
+        w.items_u = reinterpret_cast<int4*>(b + items_u);
+        return w;
     }
 };
 
@@ -201,6 +249,22 @@ __global__ void k_cell_compact(int ncell, const int* __restrict__ cstart,
                                const int* __restrict__ pos, int* __restrict__ list) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c < ncell && cstart[c + 1] > cstart[c]) list[pos[c]] = c;
+}
+
+// Each tile's range in the cell list and in the sorted rows, from the ends of its runs.
+__global__ void k_tile_ranges(const int* __restrict__ clist, int ncl, const int* __restrict__ rowtile,
+                              int gx, const int4* __restrict__ crow, int M, TileWork tw) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < ncl) {
+        const int t = rowtile[clist[i] / gx];
+        if (i == 0 || rowtile[clist[i - 1] / gx] != t) tw.clb[t] = i;
+        if (i == ncl - 1 || rowtile[clist[i + 1] / gx] != t) tw.cle[t] = i + 1;
+    }
+    if (i < M) {
+        const int t = crow[i].w;
+        if (i == 0 || crow[i - 1].w != t) tw.rb[t] = i;
+        if (i == M - 1 || crow[i + 1].w != t) tw.re[t] = i + 1;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -373,13 +437,107 @@ __global__ void k_eval_tiles_grid(Binned bd, const TileDev* __restrict__ td,
 // batched CG kernels
 // ---------------------------------------------------------------------------
 
-// w += B u over the non-empty cells of running tiles; delta_t = u^T B u per tile. Warps take
-// `chunk` consecutive cells of the list per step (consecutive cells are mostly of one tile,
-// so a warp adds its delta to the tile's total once per run of cells). Also zeroes the
-// per-tile sums the next update kernel accumulates (parity P ^ 1).
+// Work lists for the tiles running at the start of a solve-graph body (slot 0, on which every
+// body starts): tile order, each tile's SpMV items then its update items at offsets from
+// block-wide scans over the tiles, written by whole warps. Kept when no tile has stopped
+// since the last build. One block; tiles in rounds of kWlThreads.
+constexpr int kWlThreads = 1024;
+__global__ void __launch_bounds__(kWlThreads)
+    k_bcg_worklist(TileCg tc, TileWork tw, int ntile, int chunk, int nt) {
+    __shared__ int s_skip, s_base_s, s_base_u, s_tot_s, s_tot_u;
+    __shared__ int s_ws[kWlThreads / 32], s_wu[kWlThreads / 32];
+    BatchScal* bs = tc.bs;
+    const unsigned int nd = bs->ndone;
+    if (threadIdx.x == 0) {
+        s_skip = bs->built && bs->ndone_built == nd;
+        s_base_s = 0;
+        s_base_u = 0;
+    }
+    __syncthreads();
+    if (s_skip) return;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    for (int base = 0; base < ntile; base += kWlThreads) {
+        const int t = base + threadIdx.x;
+        int ns = 0, nu = 0, c0 = 0, c1 = 0, r0 = 0, r1 = 0;
+        if (t < ntile && tc.sl[0][t].state == kRunning) {
+            c0 = tw.clb[t];
+            c1 = tw.cle[t];
+            r0 = tw.rb[t];
+            r1 = tw.re[t];
+            ns = (c1 - c0 + chunk - 1) / chunk;
+            nu = (r1 - r0 + nt - 1) / nt;
+        }
+        int is = ns, iu = nu;   // inclusive scans within the warp
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int xs = __shfl_up_sync(kFull, is, o), xu = __shfl_up_sync(kFull, iu, o);
+            if (lane >= o) {
+                is += xs;
+                iu += xu;
+            }
+        }
+        if (lane == 31) {
+            s_ws[wp] = is;
+            s_wu[wp] = iu;
+        }
+        __syncthreads();
+        if (wp == 0) {
+            const int a0 = s_ws[lane], b0 = s_wu[lane];
+            int a = a0, b = b0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int xa = __shfl_up_sync(kFull, a, o), xb = __shfl_up_sync(kFull, b, o);
+                if (lane >= o) {
+                    a += xa;
+                    b += xb;
+                }
+            }
+            s_ws[lane] = a - a0;
+            s_wu[lane] = b - b0;
+            if (lane == 31) {
+                s_tot_s = a;
+                s_tot_u = b;
+            }
+        }
+        __syncthreads();
+        const int os = s_base_s + s_ws[wp] + is - ns, ou = s_base_u + s_wu[wp] + iu - nu;
+        // the warp writes its 32 tiles' items one tile at a time, lanes over the items
+        for (int l = 0; l < 32; ++l) {
+            const int tl = __shfl_sync(kFull, t, l);
+            const int nsl = __shfl_sync(kFull, ns, l), osl = __shfl_sync(kFull, os, l);
+            const int nul = __shfl_sync(kFull, nu, l), oul = __shfl_sync(kFull, ou, l);
+            const int c0l = __shfl_sync(kFull, c0, l), c1l = __shfl_sync(kFull, c1, l);
+            const int r0l = __shfl_sync(kFull, r0, l), r1l = __shfl_sync(kFull, r1, l);
+            for (int j = lane; j < nsl; j += 32) {
+                const int a = c0l + j * chunk;
+                tw.items_s[osl + j] = make_int4(a, min(a + chunk, c1l), tl, 0);
+            }
+            for (int j = lane; j < nul; j += 32) {
+                const int a = r0l + j * nt;
+                tw.items_u[oul + j] = make_int4(a, min(a + nt, r1l), tl, j == 0 ? 1 : 0);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            s_base_s += s_tot_s;
+            s_base_u += s_tot_u;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        bs->n_spmv = s_base_s;
+        bs->n_upd = s_base_u;
+        bs->ndone_built = nd;
+        bs->built = 1;
+    }
+}
+
+// w += B u over the SpMV items of running tiles; delta_t = u^T B u per tile (one atomic per
+// item). Persistent warps stride over the items. Also zeroes the per-tile sums the next
+// update kernel accumulates (parity P ^ 1).
 template <typename T>
 __global__ void __launch_bounds__(kSpmvWarps * 32, sizeof(T) == 4 ? 2 : 1)
-    k_bcg_spmv(Binned bd, const int* __restrict__ clist, int ncl, int chunk,
+    k_bcg_spmv(Binned bd, const int* __restrict__ clist, const int4* __restrict__ items,
                const T* __restrict__ B, const T* __restrict__ u, T* __restrict__ w, int P,
                int ntile, TileCg tc) {
     // parity selection by value (indexing the parameter's arrays with P would copy them to
@@ -392,162 +550,149 @@ __global__ void __launch_bounds__(kSpmvWarps * 32, sizeof(T) == 4 ? 2 : 1)
         gQ[t] = 0.0;
         rrQ[t] = 0.0;
     }
+    const int n = tc.bs->n_spmv;
     const int lane = threadIdx.x & 31;
-    const long long gw = blockIdx.x * (long long)kSpmvWarps + (threadIdx.x >> 5);
-    const long long step = (long long)gridDim.x * kSpmvWarps * chunk;
-    int cur = -1;
-    bool run = false;
-    T acc = T(0);        // this lane's share of the current tile's delta (warp sums in T)
-    for (long long base = gw * chunk; base < ncl; base += step) {
-        const int e = int(min(base + chunk, (long long)ncl));
-        for (int k = int(base); k < e; ++k) {
-            const CellDesc cd = load_desc(bd.cdesc + __ldg(clist + k));
-            if (cd.pad != cur) {            // warp-uniform
-                const T s = warp_sum<T>(acc);
-                if (lane == 0 && cur >= 0 && s != T(0)) atomicAdd(&dlP[cur], double(s));
-                acc = T(0);
-                cur = cd.pad;
-                run = slP[cur].state == kRunning;
-            }
-            if (run) acc += spmv_cell<T, (sizeof(T) == 4 ? kSpmvGroupHbm : kSpmvGroupL2)>(cd, B, u, w, lane);
-        }
+    const int nw = gridDim.x * kSpmvWarps;
+    for (int q = blockIdx.x * kSpmvWarps + (threadIdx.x >> 5); q < n; q += nw) {
+        const int4 it = items[q];
+        if (slP[it.z].state != kRunning) continue;   // stopped since the lists were built
+        T acc = T(0);   // this lane's share of the item's delta (warp sum in T)
+        for (int k = it.x; k < it.y; ++k)
+            acc += spmv_cell<T, (sizeof(T) == 4 ? kSpmvGroupHbm : kSpmvGroupL2)>(
+                load_desc(bd.cdesc + __ldg(clist + k)), B, u, w, lane);
+        const T sum = warp_sum<T>(acc);
+        if (lane == 0 && sum != T(0)) atomicAdd(&dlP[it.z], double(sum));
     }
-    const T s = warp_sum<T>(acc);
-    if (lane == 0 && cur >= 0 && s != T(0)) atomicAdd(&dlP[cur], double(s));
 }
 
-// One thread per row, one block per NT rows. Prologue: for each tile of the block's rows,
-// alpha_t and beta_t from the tile's sums (the same values in every block); the block holding
-// the tile's first row also writes the tile's next slot, clears its delta sum of the other
-// parity and, when the tile stops, records its result and counts it done. Body as the
-// single-system update with the row's tile scalars; per-tile sums of gamma and (r, r) for
-// the next iteration.
+// Persistent blocks stride over the update items (NT rows of one tile each). Per item:
+// the row values are loaded first, then thread 0 takes tile t's step (alpha_t, beta_t and
+// the stopping test from the tile's sums, in the solver's precision T; the same values in
+// every item of the tile); the owner item also writes the tile's next slot, clears its delta
+// sum of the other parity and, when the tile stops, records its result, counts it done and
+// marks the stop in both slots (another item reading the slot meanwhile takes the same
+// decision from the same sums). Body as the single-system update; per-tile sums of gamma and
+// (r, r) for the next iteration, one atomic per item.
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT)
-    k_bcg_update(Binned bd, CgVec<T> v, int P, TileCg tc) {
-    __shared__ T s_alpha[NT], s_beta[NT];
-    __shared__ double sred[2][NT];
-    __shared__ int s_go[NT];
-    const TSlot* __restrict__ slP = P ? tc.sl[1] : tc.sl[0];
-    TSlot* __restrict__ slQ = P ? tc.sl[0] : tc.sl[1];
+    k_bcg_update(Binned bd, CgVec<T> v, const int4* __restrict__ items, int P, TileCg tc) {
+    __shared__ T s_ab[2];
+    __shared__ int s_go;
+    // new residuals of the item's rows, for the block-Jacobi step (rows of a cell outside the
+    // item are recomputed with the same operations)
+    __shared__ T rsm[NT];
+    TSlot* slP = P ? tc.sl[1] : tc.sl[0];
+    TSlot* slQ = P ? tc.sl[0] : tc.sl[1];
     const double* __restrict__ gP = P ? tc.g[1] : tc.g[0];
     const double* __restrict__ rrP = P ? tc.rr[1] : tc.rr[0];
     const double* __restrict__ dlP = P ? tc.dl[1] : tc.dl[0];
     double* __restrict__ gQ = P ? tc.g[0] : tc.g[1];
     double* __restrict__ rrQ = P ? tc.rr[0] : tc.rr[1];
     double* __restrict__ dlQ = P ? tc.dl[0] : tc.dl[1];
-    const int i0 = blockIdx.x * NT;
-    if (i0 >= bd.M) return;
-    const int i1 = min(i0 + NT, bd.M);
-    // the row's values, loaded before the per-tile prologue so that their latency overlaps it
     const T* __restrict__ rP = P ? v.r[1] : v.r[0];
     const T* __restrict__ sP = P ? v.s[1] : v.s[0];
     const T* __restrict__ wP = P ? v.w[1] : v.w[0];
-    const int i = i0 + threadIdx.x;
-    int4 cm = make_int4(0, 0, 0, 0);
-    T f_d = T(0), f_w = T(0), f_s = T(0), f_p = T(0), f_u = T(0), f_r = T(0);
-    if (i < i1) {
-        cm = bd.crow[i];
-        f_d = v.dinv[i];
-        f_w = wP[i];
-        f_s = sP[i];
-        f_p = v.p[i];
-        f_u = v.u[i];
-        f_r = rP[i];
-    }
-    int t0, span;
-    block_tiles(bd, i0, i1, t0, span);
-    const int maxit = tc.bs->maxit;
-    for (int j = threadIdx.x; j < span; j += NT) {
-        const int t = t0 + j;
-        // the step in the solver's precision T (every block spanning the tile repeats it);
-        // the tile's values are all loaded before the state decides which are used
-        const TSlot sl = slP[t];
-        const T g = T(__ldcg(gP + t)), rr = T(__ldcg(rrP + t)), d = T(__ldcg(dlP + t));
-        const T tol2 = T(tc.tol2[t]), bb = T(__ldcg(tc.bb + t));
-        int state = sl.state;
-        T alpha = T(0), beta = T(0);
-        if (state == kRunning) {
-            if (!isfinite(g) || !isfinite(rr)) {
-                state = kBreakdown;
-            } else if (rr <= tol2 * bb) {
-                state = kConverged;
-            } else if (sl.it >= maxit) {
-                state = kMaxIt;
-            } else {
-                beta = sl.it == 0 ? T(0) : g / T(sl.gamma_prev);
-                const T den = sl.it == 0 ? d : d - beta * g / T(sl.alpha_prev);
-                alpha = g / den;
-                if (!(den > T(0)) || !isfinite(alpha)) state = kBreakdown;
-            }
-        }
-        const bool owner = j > 0 || i0 == 0 || bd.crow[i0 - 1].w != t0;
-        if (owner) {
-            TSlot nx = sl;
-            nx.state = state;
-            if (state == kRunning) {
-                nx.gamma_prev = double(g);
-                nx.alpha_prev = double(alpha);
-                nx.it = sl.it + 1;
-            }
-            slQ[t] = nx;
-            dlQ[t] = 0.0;
-            if (sl.state == kRunning && state != kRunning) {
-                tc.out_rr[t] = double(rr);
-                tc.out_it[t] = sl.it;
-                tc.out_state[t] = state;
-                atomicAdd(&tc.bs->ndone, 1u);
-            }
-        }
-        s_alpha[j] = alpha;
-        s_beta[j] = beta;
-        s_go[j] = state == kRunning;
-        sred[0][j] = 0.0;
-        sred[1][j] = 0.0;
-    }
-    __syncthreads();
     T* __restrict__ rQ = P ? v.r[0] : v.r[1];
     T* __restrict__ sQ = P ? v.s[0] : v.s[1];
     T* __restrict__ wQ = P ? v.w[0] : v.w[1];
-    int key = INT_MAX;
-    T acc[2] = {T(0), T(0)};
-    // new residuals of the block's rows, for the block-Jacobi step (rows of a cell outside the
-    // block are recomputed with the same operations)
-    __shared__ T rsm[NT];
-    bool go = false;
-    T ta = T(0), tb = T(0), di = T(0), ri = T(0);
-    if (i < i1) {
-        key = cm.w;
-        const int j = cm.w - t0;
-        go = s_go[j] != 0;
-        if (go) {
-            ta = s_alpha[j];
-            tb = s_beta[j];
-            di = f_d;
-            const T wi = di == T(0) ? T(0) : f_w;
-            const T si = fma(tb, f_s, wi);
-            const T pi = fma(tb, f_p, f_u);
-            ri = di == T(0) ? T(0) : fma(-ta, si, f_r);
-            sQ[i] = si;
-            v.p[i] = pi;
-            v.x[i] = fma(ta, pi, v.x[i]);
-            rQ[i] = ri;
-            wQ[i] = T(0);
+    const int n = tc.bs->n_upd;
+    const int maxit = tc.bs->maxit;
+    for (int b = blockIdx.x; b < n; b += gridDim.x) {
+        const int4 item = items[b];
+        const int r0 = item.x, r1 = item.y, t = item.z;
+        const int i = r0 + threadIdx.x;
+        const bool valid = i < r1;
+        // the row's values, loaded before the tile's step so that their latency overlaps it
+        int4 cm = make_int4(0, 0, 0, 0);
+        T f_d = T(0), f_w = T(0), f_s = T(0), f_p = T(0), f_u = T(0), f_r = T(0);
+        if (valid) {
+            cm = bd.crow[i];
+            f_d = v.dinv[i];
+            f_w = wP[i];
+            f_s = sP[i];
+            f_p = v.p[i];
+            f_u = v.u[i];
+            f_r = rP[i];
         }
+        if (threadIdx.x == 0) {
+            const TSlot sl = slP[t];
+            const T g = T(__ldcg(gP + t)), rr = T(__ldcg(rrP + t)), d = T(__ldcg(dlP + t));
+            const T tol2 = T(tc.tol2[t]), bb = T(__ldcg(tc.bb + t));
+            int state = sl.state;
+            T alpha = T(0), beta = T(0);
+            if (state == kRunning) {
+                if (!isfinite(g) || !isfinite(rr)) {
+                    state = kBreakdown;
+                } else if (rr <= tol2 * bb) {
+                    state = kConverged;
+                } else if (sl.it >= maxit) {
+                    state = kMaxIt;
+                } else {
+                    beta = sl.it == 0 ? T(0) : g / T(sl.gamma_prev);
+                    const T den = sl.it == 0 ? d : d - beta * g / T(sl.alpha_prev);
+                    alpha = g / den;
+                    if (!(den > T(0)) || !isfinite(alpha)) state = kBreakdown;
+                }
+            }
+            if (item.w) {
+                TSlot nx = sl;
+                nx.state = state;
+                if (state == kRunning) {
+                    nx.gamma_prev = double(g);
+                    nx.alpha_prev = double(alpha);
+                    nx.it = sl.it + 1;
+                }
+                slQ[t] = nx;
+                dlQ[t] = 0.0;
+                if (sl.state == kRunning && state != kRunning) {
+                    slP[t] = nx;
+                    tc.out_rr[t] = double(rr);
+                    tc.out_it[t] = sl.it;
+                    tc.out_state[t] = state;
+                    atomicAdd(&tc.bs->ndone, 1u);
+                }
+            }
+            s_ab[0] = alpha;
+            s_ab[1] = beta;
+            s_go = state == kRunning;
+        }
+        __syncthreads();
+        if (s_go) {   // uniform over the block
+            const T ta = s_ab[0], tb = s_ab[1];
+            T di = T(0), ri = T(0);
+            if (valid) {
+                di = f_d;
+                const T wi = di == T(0) ? T(0) : f_w;
+                const T si = fma(tb, f_s, wi);
+                const T pi = fma(tb, f_p, f_u);
+                ri = di == T(0) ? T(0) : fma(-ta, si, f_r);
+                sQ[i] = si;
+                v.p[i] = pi;
+                v.x[i] = fma(ta, pi, v.x[i]);
+                rQ[i] = ri;
+                wQ[i] = T(0);
+            }
+            rsm[threadIdx.x] = ri;
+            __syncthreads();
+            T acc[2] = {T(0), T(0)};
+            if (valid) {
+                const T ui = apply_prec<T>(bd, v.bjinv, cm, i, di, ri, [&](int jj) {
+                    const int o = jj - r0;
+                    return o >= 0 && o < NT ? rsm[o] : next_r(rP[jj], sP[jj], wP[jj], ta, tb);
+                });
+                v.u[i] = ui;
+                acc[0] = ri * ui;
+                acc[1] = ri * ri;
+            }
+            double tot[2];
+            block_sum_t<2, T>(acc, tot);
+            if (threadIdx.x == 0) {
+                if (tot[0] != 0.0) atomicAdd(gQ + t, tot[0]);
+                if (tot[1] != 0.0) atomicAdd(rrQ + t, tot[1]);
+            }
+        }
+        __syncthreads();   // s_ab, s_go and rsm are the next item's
     }
-    rsm[threadIdx.x] = ri;
-    __syncthreads();
-    if (go) {
-        const T ui = apply_prec<T>(bd, v.bjinv, cm, i, di, ri, [&](int jj) {
-            const int o = jj - i0;
-            return o >= 0 && o < NT ? rsm[o] : next_r(rP[jj], sP[jj], wP[jj], ta, tb);
-        });
-        v.u[i] = ui;
-        acc[0] = ri * ui;
-        acc[1] = ri * ri;
-    }
-    double* const dst[2] = {gQ, rrQ};
-    tile_reduce<2, NT, T>(key, acc, t0, span, sred, dst);
 }
 
 // Start of a batched solve of B x = bscale_t b per tile (tiles with bscale_t = 0 take no
@@ -626,21 +771,42 @@ int sm_count(const rbf_ctx* ctx) {
 }
 
 TileCg tile_view(rbf_ctx* ctx) { return TileLayout(ctx->T).view(ctx->tcg.as<char>()); }
+WorkLayout work_layout(const rbf_ctx* ctx) { return WorkLayout(ctx->T, ctx->ncl, ctx->M); }
+TileWork work_view(rbf_ctx* ctx) { return work_layout(ctx).view(ctx->twork.as<char>()); }
+
+// Persistent update grid: as many blocks of NT threads as can be resident, at most one per
+// item of the longest list.
+template <typename T>
+int update_grid(rbf_ctx* ctx, int nt) {
+    int a = 0;
+    switch (nt) {
+        case 128: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_bcg_update<T, 128>, 128, 0); break;
+        case 512: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_bcg_update<T, 512>, 512, 0); break;
+        default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_bcg_update<T, 256>, 256, 0); break;
+    }
+    const WorkLayout L = work_layout(ctx);
+    return std::max(1, std::min(std::max(a, 1) * sm_count(ctx), L.cap_u));
+}
+
+void launch_worklist(rbf_ctx* ctx, const TileCg& tc, const Cfg& cf, cudaStream_t cs) {
+    k_bcg_worklist<<<1, kWlThreads, 0, cs>>>(tc, work_view(ctx), ctx->T, cf.chunk, cf.nt);
+}
 
 // One batched CG iteration (two kernels) reading the buffers of parity P.
 template <typename T>
 void launch_bcg_iteration(rbf_ctx* ctx, const CgVec<T>& v, const TileCg& tc, const Cfg& cf,
                           int P, cudaStream_t cs) {
     const Binned bd = view(ctx);
-    const int grid = std::max(1, std::min(cf.bps * sm_count(ctx),
-                                          div_up(ctx->ncl, int64_t(kSpmvWarps) * cf.chunk)));
-    k_bcg_spmv<T><<<grid, kSpmvWarps * 32, 0, cs>>>(bd, ctx->clist.as<int>(), ctx->ncl, cf.chunk,
+    const TileWork tw = work_view(ctx);
+    const int items = div_up(ctx->ncl, cf.chunk) + ctx->T;   // most SpMV items
+    const int grid = std::max(1, std::min(cf.bps * sm_count(ctx), div_up(items, kSpmvWarps)));
+    k_bcg_spmv<T><<<grid, kSpmvWarps * 32, 0, cs>>>(bd, ctx->clist.as<int>(), tw.items_s,
                                                     ctx->bvals.as<T>(), v.u, v.w[P], P, ctx->T, tc);
-    const int nb = std::max(1, div_up(ctx->M, cf.nt));
+    const int nb = update_grid<T>(ctx, cf.nt);
     switch (cf.nt) {
-        case 128: k_bcg_update<T, 128><<<nb, 128, 0, cs>>>(bd, v, P, tc); break;
-        case 512: k_bcg_update<T, 512><<<nb, 512, 0, cs>>>(bd, v, P, tc); break;
-        default: k_bcg_update<T, 256><<<nb, 256, 0, cs>>>(bd, v, P, tc); break;
+        case 128: k_bcg_update<T, 128><<<nb, 128, 0, cs>>>(bd, v, tw.items_u, P, tc); break;
+        case 512: k_bcg_update<T, 512><<<nb, 512, 0, cs>>>(bd, v, tw.items_u, P, tc); break;
+        default: k_bcg_update<T, 256><<<nb, 256, 0, cs>>>(bd, v, tw.items_u, P, tc); break;
     }
 }
 
@@ -676,7 +842,7 @@ rbf_status write_tile_state(rbf_ctx* ctx, const std::vector<char>& active,
 }
 
 template <typename T, typename TB>
-rbf_status bcg_start(rbf_ctx* ctx, const TB* b, bool use_x0, cudaStream_t st) {
+rbf_status bcg_start(rbf_ctx* ctx, const TB* b, bool use_x0, const Cfg& cf, cudaStream_t st) {
     const Binned bd = view(ctx);
     const CgVec<T> v = cg_vectors<T>(ctx);
     if (use_x0) {
@@ -685,7 +851,8 @@ rbf_status bcg_start(rbf_ctx* ctx, const TB* b, bool use_x0, cudaStream_t st) {
     }
     k_bcg_init<T, TB><<<std::max(1, div_up(ctx->M, 256)), 256, 0, st>>>(bd, v, b, use_x0 ? 1 : 0,
                                                                        tile_view(ctx));
-    ctx->launches += 1;
+    launch_worklist(ctx, tile_view(ctx), cf, st);   // for iterations launched one by one
+    ctx->launches += 2;
     RBF_CUDA_TRY(cudaGetLastError());
     return RBF_OK;
 }
@@ -709,7 +876,7 @@ rbf_status time_cfg(rbf_ctx* ctx, const Cfg& cf, int iters, cudaEvent_t e0, cuda
     std::vector<double> one(T_, 1.0), zero(T_, 0.0);
     rbf_status s = write_tile_state(ctx, act, one, zero, 1 << 30, st);
     if (s != RBF_OK) return s;
-    if ((s = bcg_start<T, double>(ctx, ctx->bvec.as<double>(), false, st)) != RBF_OK) return s;
+    if ((s = bcg_start<T, double>(ctx, ctx->bvec.as<double>(), false, cf, st)) != RBF_OK) return s;
     const CgVec<T> v = cg_vectors<T>(ctx);
     const TileCg tc = tile_view(ctx);
     launch_bcg_iteration<T>(ctx, v, tc, cf, 0, st);
@@ -806,12 +973,12 @@ template <typename T>
 rbf_status bcg_graph(rbf_ctx* ctx, const Cfg& cf, cudaGraphExec_t* out) {
     rbf_ctx::TileGraph& sg = ctx->bt_graph[sizeof(T) == 8 ? 0 : 1];
     const CgVec<T> v = cg_vectors<T>(ctx);
-    const void* key[12] = {ctx->bvals.p, v.x, v.dinv, v.bjinv, ctx->tcg.p, ctx->clist.p,
+    const void* key[13] = {ctx->twork.p, ctx->bvals.p, v.x, v.dinv, v.bjinv, ctx->tcg.p, ctx->clist.p,
                            ctx->cdesc.p, ctx->crow.p, ctx->bjoff.p, ctx->cstart.p,
                            ctx->seg.p, ctx->rboff.p};
     bool hit = sg.exec && sg.T == ctx->T && sg.M == ctx->M && sg.ncl == ctx->ncl &&
                sg.bps == cf.bps && sg.chunk == cf.chunk && sg.nt == cf.nt;
-    for (int k = 0; k < 12 && hit; ++k) hit = sg.key[k] == key[k];
+    for (int k = 0; k < 13 && hit; ++k) hit = sg.key[k] == key[k];
     if (hit) {
         *out = sg.exec;
         return RBF_OK;
@@ -839,6 +1006,7 @@ rbf_status bcg_graph(rbf_ctx* ctx, const Cfg& cf, cudaGraphExec_t* out) {
         e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         const TileCg tc = tile_view(ctx);
+        launch_worklist(ctx, tc, cf, cs);   // kept unless some tile stopped
         for (int k = 0; k < kItersPerBody; ++k) launch_bcg_iteration<T>(ctx, v, tc, cf, k & 1, cs);
         k_bcg_cond<<<1, 1, 0, cs>>>(tc.bs, handle);
         cudaGraph_t captured = nullptr;
@@ -856,7 +1024,7 @@ rbf_status bcg_graph(rbf_ctx* ctx, const Cfg& cf, cudaGraphExec_t* out) {
     sg.bps = cf.bps;
     sg.chunk = cf.chunk;
     sg.nt = cf.nt;
-    for (int k = 0; k < 12; ++k) sg.key[k] = key[k];
+    for (int k = 0; k < 13; ++k) sg.key[k] = key[k];
     *out = sg.exec;
     return RBF_OK;
 }
@@ -886,7 +1054,7 @@ rbf_status run_bcg(rbf_ctx* ctx, const TB* b, const double* x0, const std::vecto
         k_copy_masked<T><<<std::max(1, div_up(ctx->M, 256)), 256, 0, st>>>(ctx->M, x0, v.dinv, v.x);
         ctx->launches += 1;
     }
-    if ((s = bcg_start<T, TB>(ctx, b, x0 != nullptr, st)) != RBF_OK) return s;
+    if ((s = bcg_start<T, TB>(ctx, b, x0 != nullptr, cf, st)) != RBF_OK) return s;
     RBF_CUDA_TRY(cudaGraphLaunch(ex, st));
     const TileLayout L(ctx->T);
     char* h = static_cast<char*>(ctx->hbt);
@@ -905,7 +1073,7 @@ rbf_status run_bcg(rbf_ctx* ctx, const TB* b, const double* x0, const std::vecto
         out->rel[t] = hv.bb[t] > 0.0 ? sqrt(hv.out_rr[t] / hv.bb[t]) : 0.0;
         max_it = std::max(max_it, hv.out_it[t]);
     }
-    ctx->launches += int64_t(max_it / kItersPerBody + 1) * (2 * kItersPerBody + 1);
+    ctx->launches += int64_t(max_it / kItersPerBody + 1) * (2 * kItersPerBody + 2);
     return RBF_OK;
 }
 
@@ -995,6 +1163,14 @@ rbf_status tiles_cell_list(rbf_ctx* ctx, cudaStream_t st) {
     RBF_CUDA_TRY(cudaMemcpyAsync(hp, pos + nc, sizeof(int), cudaMemcpyDeviceToHost, st));
     RBF_CUDA_TRY(cudaStreamSynchronize(st));
     ctx->ncl = *hp;
+    // each tile's cells in the list and rows in the sorted order, and room for the work lists
+    const WorkLayout L = work_layout(ctx);
+    if ((s = ensure(ctx, ctx->twork, L.total, st)) != RBF_OK) return s;
+    RBF_CUDA_TRY(cudaMemsetAsync(ctx->twork.p, 0, L.ranges_end, st));
+    k_tile_ranges<<<std::max(1, div_up(std::max(ctx->ncl, ctx->M), 256)), 256, 0, st>>>(
+        ctx->clist.as<int>(), ctx->ncl, ctx->rowtile.as<int>(), ctx->g.gx, ctx->crow.as<int4>(),
+        ctx->M, work_view(ctx));
+    ctx->launches += 1;
     RBF_CUDA_TRY(cudaGetLastError());
     return RBF_OK;
 }
@@ -1005,7 +1181,8 @@ void tiles_release(rbf_ctx* ctx) {
             cudaGraphExecDestroy(sg.exec);
             sg.exec = nullptr;
         }
-    rbf_buf* bufs[] = {&ctx->tdesc, &ctx->rowtile, &ctx->clist, &ctx->tcg, &ctx->tred, &ctx->qoff};
+    rbf_buf* bufs[] = {&ctx->tdesc, &ctx->rowtile, &ctx->clist, &ctx->tcg, &ctx->twork,
+                       &ctx->tred, &ctx->qoff};
     for (rbf_buf* b : bufs) release(ctx, *b);
     if (ctx->hbt) cudaFreeHost(ctx->hbt);
     ctx->hbt = nullptr;
@@ -1250,7 +1427,10 @@ rbf_status solve_tiles_run(rbf_ctx* ctx, double* c, int use_c0, double tol, int 
             for (int t = 0; t < T; ++t) {
                 if (!active[t]) continue;   // other tiles keep their iterate and residual
                 const double rnew = sqrt(rn2[t]);
-                if (!(rnew < 0.5 * rn[t])) stall[t] = 1;
+                // stalled: less than half the gain asked of the inner solve (and at most a
+                // halving), short of the tolerance
+                if (!(rnew <= tol * bn[t]) && !(rnew < std::max(0.5, 2.0 * itol[t]) * rn[t]))
+                    stall[t] = 1;
                 rn[t] = rnew;
             }
         }
@@ -1330,16 +1510,18 @@ rbf_status bench_tiles_impl(rbf_ctx* ctx, int reps, bool spmv_only, cudaStream_t
     if (spmv_only) {
         k_tile_fill<T><<<div_up(ctx->M, 256), 256, 0, st>>>(v.u, ctx->M, T(1));
         RBF_CUDA_TRY(cudaMemsetAsync(v.w[0], 0, sizeof(T) * ctx->M, st));
+        launch_worklist(ctx, tc, cf, st);
         const Binned bd = view(ctx);
-        const int grid = std::max(1, std::min(cf.bps * sm_count(ctx),
-                                              div_up(ctx->ncl, int64_t(kSpmvWarps) * cf.chunk)));
+        const int items = div_up(ctx->ncl, cf.chunk) + ctx->T;
+        const int grid = std::max(1, std::min(cf.bps * sm_count(ctx), div_up(items, kSpmvWarps)));
         for (int k = 0; k < reps; ++k)
-            k_bcg_spmv<T><<<grid, kSpmvWarps * 32, 0, st>>>(bd, ctx->clist.as<int>(), ctx->ncl,
-                                                            cf.chunk, ctx->bvals.as<T>(), v.u,
-                                                            v.w[0], 0, ctx->T, tc);
-        ctx->launches += reps + 1;
+            k_bcg_spmv<T><<<grid, kSpmvWarps * 32, 0, st>>>(bd, ctx->clist.as<int>(),
+                                                            work_view(ctx).items_s,
+                                                            ctx->bvals.as<T>(), v.u, v.w[0], 0,
+                                                            ctx->T, tc);
+        ctx->launches += reps + 2;
     } else {
-        if ((s = bcg_start<T, double>(ctx, ctx->bvec.as<double>(), false, st)) != RBF_OK) return s;
+        if ((s = bcg_start<T, double>(ctx, ctx->bvec.as<double>(), false, cf, st)) != RBF_OK) return s;
         for (int k = 0; k < reps; ++k) launch_bcg_iteration<T>(ctx, v, tc, cf, k & 1, st);
         ctx->launches += 2 * int64_t(reps);
     }

@@ -98,6 +98,7 @@ struct rbf_ctx {
     rbf_buf clist;                   // [ncl] cells holding at least one centre
     int ncl = 0;
     rbf_buf tcg;                     // per-tile CG scalars and results
+    rbf_buf twork;                   // per-tile cell and row ranges, CG work lists
     rbf_buf tred;                    // per-tile reductions (norms, pinned counts, scales)
     rbf_buf qoff;                    // [T+1] query offsets of rbf_eval_tiles
     void* hbt = nullptr;             // pinned host mirror of tcg / tred
@@ -115,7 +116,7 @@ struct rbf_ctx {
     int force_bps = 0, force_chunk = 0, force_nt = 0;   // fixed configuration (0: automatic)
     struct TileGraph {
         cudaGraphExec_t exec = nullptr;
-        const void* key[12] = {};
+        const void* key[13] = {};
         int T = 0, M = 0, ncl = 0, bps = 0, chunk = 0, nt = 0;
     };
     TileGraph bt_graph[2];

@@ -802,8 +802,8 @@ rbf_status solve_run(rbf_ctx* ctx, double* c, int use_c0, double tol, int maxit,
             if (outer == ctx->max_refine) break;
             int it = 0, ist = 0;
             double irel = 0.0;
-            s = run_cg<float, double>(ctx, r64, 1.0 / rn, false, std::max(inner_tol, 0.5 * tol / rel),
-                                      maxit, &it, &irel, &ist, st);
+            const double itol = std::max(inner_tol, 0.5 * tol / rel);
+            s = run_cg<float, double>(ctx, r64, 1.0 / rn, false, itol, maxit, &it, &irel, &ist, st);
             if (s != RBF_OK) return s;
             total_it += it;
             // An inner breakdown (FP32 rounding can make B32 indefinite when the system is
@@ -821,7 +821,11 @@ rbf_status solve_run(rbf_ctx* ctx, double* c, int use_c0, double tol, int maxit,
             approx_r = false;
             double rn_new = 0.0;
             if ((s = norm_r64(&rn_new)) != RBF_OK) return s;
-            if (!(rn_new < 0.5 * rn)) {   // stalled: the FP32 matrix cannot resolve the system
+            // Stalled: the step gained less than half of what the inner solve was asked for
+            // (and at most a halving), short of the tolerance -- the FP32 matrix cannot
+            // resolve the system.
+            const bool done = bnorm > 0 && rn_new / bnorm <= tol;
+            if (!done && !(rn_new < std::max(0.5, 2.0 * itol) * rn)) {
                 rn = std::min(rn, rn_new);
                 ++outer;
                 state = kMaxIt;

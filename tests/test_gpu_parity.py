@@ -269,10 +269,11 @@ def test_terrain_full_size_properties():
         i, j = rng.integers(0, 1024, 2)
         assert abs(f[i, j] - so.f(cn, (gx[j], gx[i]))) <= 1e-12 * np.abs(f).max()
     ctx.close()
-    # the clustered terrain is ill-conditioned (kappa ~ 6e6): a 1e-6 surface needs the
-    # normal residual at 1e-11, the tolerance the benchmark uses
+    # the clustered terrain is ill-conditioned (kappa ~ 6e6): at a 1e-11 normal residual the
+    # surface error varies around the 1e-6 bar from run to run (FP32 summation order), so the
+    # solve uses the benchmark's 3e-12
     ctx32 = _binned(pb, prec="fp32_refine")
-    c32, info32 = ctx32.solve(tol=1e-11)
+    c32, info32 = ctx32.solve(tol=3e-12)
     f32 = ctx32.eval_grid(c32, 1024, 1024).cpu().numpy()
     assert O.rel_err(f32, f) <= MIXED_BAR
     ctx32.close()
