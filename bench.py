@@ -26,6 +26,7 @@ one system does not shard), weak scaling.
 from __future__ import annotations
 
 import argparse
+import gc
 import hashlib
 import json
 import os
@@ -237,6 +238,8 @@ def bench_batched(args, rank, dev, stream, flush, hbm, peak_source):
 
     def timed(prec, tol, k):
         ms = []
+        gc.collect()
+        gc.disable()
         for _ in range(k):
             flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
@@ -246,6 +249,7 @@ def bench_batched(args, rank, dev, stream, flush, hbm, peak_source):
             e1.record(stream)
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
+        gc.enable()
         return statistics.mean(ms), info, tinfo
 
     for _ in range(2):                     # warm-up (the first one runs the autotuner)
@@ -421,6 +425,8 @@ def main():
     sampler = ClockSampler(local)
     sampler.start()
     launches0 = ctx.launch_count()
+    gc.collect()
+    gc.disable()     # no collector pauses inside the host side of the timed steps
     barrier()
     torch.cuda.synchronize()
     step_ms = []
@@ -436,6 +442,7 @@ def main():
         step_ms.append(e0.elapsed_time(e1))
     torch.cuda.synchronize()
     barrier()
+    gc.enable()
     launches = ctx.launch_count() - launches0
     clocks = sampler.stop()
     ms = statistics.mean(step_ms)
@@ -595,7 +602,9 @@ def main():
             "phases_ms": phases,
             "batched": batched,
             "solver": {"iterations": last["iterations"], "refinements": last["refinements"],
-                       "rel_residual": last["rel_residual"], "pinned": last["pinned"]},
+                       "rel_residual": last["rel_residual"], "pinned": last["pinned"],
+                       "promoted_steps": sum(int(i["promoted"]) for i in infos)},
+            "step_ms": [round(x, 3) for x in step_ms],
         }
         print(json.dumps(line), flush=True)
     ctx.close()

@@ -532,9 +532,12 @@ __global__ void __launch_bounds__(kWlThreads)
     }
 }
 
-// w += B u over the SpMV items of running tiles; delta_t = u^T B u per tile (one atomic per
-// item). Persistent warps stride over the items. Also zeroes the per-tile sums the next
-// update kernel accumulates (parity P ^ 1).
+// w += B u over the SpMV items of the running tiles; delta_t = u^T B u per tile (one atomic
+// per item). Persistent warps stride over the items, the next item's descriptor in flight
+// during the current one and an item's cell indices loaded one per lane. A tile that stops
+// inside a graph body keeps its items until the next body (at most kItersPerBody - 1 SpMVs
+// whose w and delta its stopped state leaves unused). Also zeroes the per-tile sums the
+// next update kernel accumulates (parity P ^ 1).
 template <typename T>
 __global__ void __launch_bounds__(kSpmvWarps * 32, sizeof(T) == 4 ? 2 : 1)
     k_bcg_spmv(Binned bd, const int* __restrict__ clist, const int4* __restrict__ items,
@@ -545,7 +548,6 @@ __global__ void __launch_bounds__(kSpmvWarps * 32, sizeof(T) == 4 ? 2 : 1)
     double* __restrict__ gQ = P ? tc.g[0] : tc.g[1];
     double* __restrict__ rrQ = P ? tc.rr[0] : tc.rr[1];
     double* __restrict__ dlP = P ? tc.dl[1] : tc.dl[0];
-    const TSlot* __restrict__ slP = P ? tc.sl[1] : tc.sl[0];
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntile; t += gridDim.x * blockDim.x) {
         gQ[t] = 0.0;
         rrQ[t] = 0.0;
@@ -553,13 +555,19 @@ __global__ void __launch_bounds__(kSpmvWarps * 32, sizeof(T) == 4 ? 2 : 1)
     const int n = tc.bs->n_spmv;
     const int lane = threadIdx.x & 31;
     const int nw = gridDim.x * kSpmvWarps;
-    for (int q = blockIdx.x * kSpmvWarps + (threadIdx.x >> 5); q < n; q += nw) {
-        const int4 it = items[q];
-        if (slP[it.z].state != kRunning) continue;   // stopped since the lists were built
+    int q = blockIdx.x * kSpmvWarps + (threadIdx.x >> 5);
+    int4 next = q < n ? items[q] : make_int4(0, 0, 0, 0);
+    for (; q < n; q += nw) {
+        const int4 it = next;
+        if (q + nw < n) next = items[q + nw];
         T acc = T(0);   // this lane's share of the item's delta (warp sum in T)
-        for (int k = it.x; k < it.y; ++k)
-            acc += spmv_cell<T, (sizeof(T) == 4 ? kSpmvGroupHbm : kSpmvGroupL2)>(
-                load_desc(bd.cdesc + __ldg(clist + k)), B, u, w, lane);
+        for (int k0 = it.x; k0 < it.y; k0 += 32) {
+            const int nc = min(32, it.y - k0);
+            const int mine = lane < nc ? __ldg(clist + k0 + lane) : 0;
+            for (int k = 0; k < nc; ++k)
+                acc += spmv_cell<T, (sizeof(T) == 4 ? kSpmvGroupHbm : kSpmvGroupL2)>(
+                    load_desc(bd.cdesc + __shfl_sync(kFull, mine, k)), B, u, w, lane);
+        }
         const T sum = warp_sum<T>(acc);
         if (lane == 0 && sum != T(0)) atomicAdd(&dlP[it.z], double(sum));
     }
