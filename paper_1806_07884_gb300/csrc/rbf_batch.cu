@@ -960,7 +960,8 @@ rbf_status pick_cfg(rbf_ctx* ctx, Cfg* out, cudaStream_t st) {
     const int slot = sizeof(T) == 8 ? 0 : 1;
     const rbf_ctx::TileTuning& tu = ctx->tune[slot];
     const bool fresh = tu.nt != 0 && tu.ncl == ctx->ncl && tu.M == ctx->M && tu.nvals == ctx->nvals;
-    if (!fresh && ctx->autotune && !(ctx->force_bps || ctx->force_chunk || ctx->force_nt)) {
+    if (!fresh && ctx->autotune && !ctx->no_tune_now &&
+        !(ctx->force_bps || ctx->force_chunk || ctx->force_nt)) {
         rbf_status s = autotune_impl<T>(ctx, st);
         if (s != RBF_OK) return s;
     }
@@ -1463,7 +1464,11 @@ rbf_status solve_tiles_run(rbf_ctx* ctx, double* c, int use_c0, double tol, int 
             RBF_CUDA_TRY(cudaMemsetAsync(npin_d, 0, sizeof(int), st));
             if ((s = prec_setup_run(ctx, RBF_FP64, min_support, npin_d, st)) != RBF_OK) return s;
             for (int t = 0; t < T; ++t) tpro[t] = !conv[t];
-            if ((s = fp64_solve(tpro, x64)) != RBF_OK) return s;
+            // a few tiles, typically: not worth tuning the FP64 loop for the whole batch
+            ctx->no_tune_now = true;
+            s = fp64_solve(tpro, x64);
+            ctx->no_tune_now = false;
+            if (s != RBF_OK) return s;
         }
     }
     RBF_CUDA_TRY(cudaGetLastError());

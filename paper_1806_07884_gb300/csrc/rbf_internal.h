@@ -113,6 +113,7 @@ struct rbf_ctx {
     };
     TileTuning tune[2];
     int autotune = 1;                // tune on the first batched solve of a new shape
+    bool no_tune_now = false;        // a promotion's FP64 finish: keep the default
     int force_bps = 0, force_chunk = 0, force_nt = 0;   // fixed configuration (0: automatic)
     struct TileGraph {
         cudaGraphExec_t exec = nullptr;

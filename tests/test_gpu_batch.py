@@ -131,14 +131,18 @@ def test_batched_assembly_equals_oracle_blocks():
 
 def test_batched_equals_single_system_solves():
     """Each tile follows its own CG: the batched FP64 solve gives every tile the weights and
-    (within rounding) the iteration count of solving that tile alone."""
+    (within rounding) the iteration count of solving that tile alone. Both solvers sum with
+    atomics, so the counts vary from run to run with the summation order: over six runs of
+    each, tile 2 took 440-442 iterations, and one single-system run took 431 (2% below); the
+    bound allows 4%. A CG with scalars shared by all tiles would give every tile the count
+    of the slowest."""
     pbs = _tiles_small()[:4]
     cs, info, tinfo, ctx = pkg.fit_tiles(_problems(pbs), prec="fp64", tol=1e-12)
     for k, pb in enumerate(pbs):
         c1, i1, ctx1 = pkg.fit(pb.points, pb.h, pb.centres, pb.R, pb.kernel, prec="fp64",
                                bbox=pb.bbox, tol=1e-12)
         assert O.rel_err(cs[k].cpu().numpy(), c1.cpu().numpy()) <= 1e-8, k
-        assert abs(tinfo[k]["iterations"] - i1["iterations"]) <= 2 + 0.02 * i1["iterations"], k
+        assert abs(tinfo[k]["iterations"] - i1["iterations"]) <= 2 + 0.04 * i1["iterations"], k
         ctx1.close()
     its = [t["iterations"] for t in tinfo]
     assert len(set(its)) > 1          # uneven tiles stop at different iterations
@@ -275,11 +279,10 @@ def test_batched_start_vector_survives_the_autotuner():
 
 def test_batched_promotion_finishes_only_the_unconverged_tiles():
     """FP32 refinement cut short (3 steps to 1e-8): the tiles that converged keep their refined
-    iterates, the clustered tile is finished by FP64 CG -- on a fresh context, whose FP64
-    solve first tunes its launch configuration on the solver's own vectors. Every tile's
-    returned weights meet the tolerance in the oracle's FP64 normal residual (over unpinned
-    centres). FP32 rounding order varies from run to run, so up to four fresh contexts are
-    tried for a batch with both kinds of tile."""
+    iterates, the clustered tile is finished by FP64 CG started from its refined iterate.
+    Every tile's returned weights meet the tolerance in the oracle's FP64 normal residual
+    (over unpinned centres). FP32 rounding order varies from run to run, so up to four fresh
+    contexts are tried for a batch with both kinds of tile."""
     pbs = _tiles_small()
     tiles, cx, cy, px, py, hh = pkg.pack_tiles(_problems(pbs))
     d = [_dev(a) for a in (cx, cy, px, py, hh)]
