@@ -65,6 +65,18 @@ def spmv_traffic():
     return SPMV_TRAFFIC["bytes"] if ok else None
 
 
+# The big-data SpMV is the single-system kernel on a B streamed from HBM; its DRAM traffic per
+# algorithmic byte comes from a capture of a smaller big-data system (B still far beyond L2).
+BIG_SPMV_TRAFFIC = {"sha": "1e58bb809b2dfef6", "per_alg_byte": (254799360 + 8496640) / 256737316,
+                    "note": "scaled from a 5M x 500k big-data capture"}
+
+
+def big_spmv_traffic(alg_bytes):
+    ok = BIG_SPMV_TRAFFIC["sha"] is not None and \
+        kernel_sha("rbf_solve.cu", "k_spmv(Binned bd") == BIG_SPMV_TRAFFIC["sha"]
+    return int(BIG_SPMV_TRAFFIC["per_alg_byte"] * alg_bytes) if ok else None
+
+
 def bspmv_traffic(alg_bytes):
     ok = kernel_sha("rbf_batch.cu", "k_bcg_spmv(Binned bd") == BSPMV_TRAFFIC["sha"]
     return int(BSPMV_TRAFFIC["per_alg_byte"] * alg_bytes) if ok else None
@@ -86,6 +98,12 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--quiet-extra", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-bigdata", action="store_true")
+    ap.add_argument("--bigdata-only", action="store_true",
+                    help="run only the big-data workload (its object is the line)")
+    ap.add_argument("--big-N", type=int, default=20_000_000)
+    ap.add_argument("--big-M", type=int, default=2_000_000)
+    ap.add_argument("--big-grid", type=int, default=4096)
     ap.add_argument("--no-learned", dest="learned", action="store_false",
                     help="cold start instead of the learned warm start in the timed step")
     ap.add_argument("--tiles", type=int, default=512)
@@ -351,6 +369,109 @@ def bench_batched(args, rank, dev, stream, flush, hbm, peak_source):
     return out
 
 
+def bench_bigdata(args, rank, dev, stream, flush, hbm, peak_source):
+    """The big-data workload: N = 20 M points with 10:1 density variation, 8-octave value-noise
+    heights, M = 2 M Halton centres, Wendland phi_3,2, FP32 assembly and SpMV with FP64
+    residual and refinement, 4096 x 4096 evaluation grid; N over the time of one step (bin,
+    assemble, solve, evaluate), device-resident inputs, L2 flushed before each step."""
+    import numpy as np
+    import torch
+
+    import datagen as dg
+    import paper_1806_07884_gb300 as pkg
+
+    pb = dg.config_bigdata(seed=rank, N=args.big_N, M=args.big_M, eval_n=args.big_grid)
+    N, M, n = pb.N, pb.M, args.big_grid
+    d = [torch.as_tensor(np.ascontiguousarray(a), device=dev) for a in
+         (pb.centres[:, 0], pb.centres[:, 1], pb.points[:, 0], pb.points[:, 1], pb.h)]
+    cbuf = torch.empty(M, dtype=torch.float64, device=dev)
+    fbuf = torch.empty((n, n), dtype=torch.float64, device=dev)
+    ctx = pkg.Context(dev.index)
+
+    def step(prec, tol):
+        ctx.bin(*d, pb.R, pb.bbox)
+        ctx.assemble(pb.kernel, prec)
+        c, info = ctx.solve(tol=tol, maxit=50000, out=cbuf)
+        ctx.eval_grid(c, n, n, out=fbuf)
+        return info
+
+    def timed(prec, tol, k):
+        ms, infos = [], []
+        gc.collect()
+        gc.disable()
+        for _ in range(k):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            infos.append(step(prec, tol))
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        gc.enable()
+        return statistics.mean(ms), ms, infos
+
+    step(args.prec, args.tol)                       # warm-up
+    torch.cuda.synchronize()
+    launches0 = ctx.launch_count()
+    k = max(2, min(args.steps, 3))
+    ms, step_ms, infos = timed(args.prec, args.tol, k)
+    launches = (ctx.launch_count() - launches0) // k
+    info = infos[-1]
+    f_fast = fbuf.clone()
+    # phases of one step
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    flush.zero_()
+    ev[0].record(stream)
+    ctx.bin(*d, pb.R, pb.bbox)
+    ev[1].record(stream)
+    ctx.assemble(pb.kernel, args.prec)
+    ev[2].record(stream)
+    c, _ = ctx.solve(tol=args.tol, maxit=50000, out=cbuf)
+    ev[3].record(stream)
+    ctx.eval_grid(c, n, n, out=fbuf)
+    ev[4].record(stream)
+    torch.cuda.synchronize()
+    phases = {nm: round(ev[i].elapsed_time(ev[i + 1]), 3)
+              for i, nm in enumerate(["bin", "assemble", "solve", "eval"])}
+    # roofline of the solver's SpMV (B streamed from HBM at this size), on its stream
+    lay = ctx.layout()
+    vb = lay["value_bytes"]
+    spmv_bytes = lay["nvals"] * vb + 3 * M * vb + lay["gx"] * lay["gy"] * 36
+    ctx.bench_spmv(5)
+    s0 = torch.cuda.Event(enable_timing=True)
+    s1 = torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    ctx.bench_spmv(50)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    spmv_ms = s0.elapsed_time(s1) / 50
+    ach = spmv_bytes / (spmv_ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "kernel": f"k_spmv<{'float' if vb == 4 else 'double'}>",
+            "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s", "frac": round(ach / hbm, 4),
+            "traffic": big_spmv_traffic(spmv_bytes), "traffic_note": BIG_SPMV_TRAFFIC["note"],
+            "algorithmic_bytes": spmv_bytes, "launch_ms": round(spmv_ms, 5),
+            "peak_source": peak_source}
+    out = {"workload": f"big data: {N} points (10:1 density), {M} Halton centres, Wendland "
+                       f"phi_3,2, K=30, {n}x{n} eval grid",
+           "value": N / (ms * 1e-3), "unit": "points/s", "ms_per_step": round(ms, 3),
+           "step_ms": [round(x, 3) for x in step_ms], "prec": args.prec, "tol": args.tol,
+           "gpu_launches_per_step": launches, "iterations": info["iterations"],
+           "refinements": info["refinements"],
+           "promoted_steps": sum(int(i["promoted"]) for i in infos),
+           "phases_ms": phases, "roofline": roof}
+    if not args.no_fp64_compare:
+        ms64, _, infos64 = timed("fp64", args.tol, 1)
+        out["fp64_path"] = {"value": N / (ms64 * 1e-3), "ms_per_step": round(ms64, 3),
+                            "iterations": infos64[-1]["iterations"]}
+        f_ref = fbuf.clone()
+        err = float((f_fast - f_ref).abs().max() / f_ref.abs().max())
+        out["accuracy"] = {"rel_err_f_vs_fp64": err, "reference": f"FP64 path at tol {args.tol}",
+                           "bar": 1e-6, "ok": err <= 1e-6}
+    ctx.close()
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -377,10 +498,11 @@ def main():
     except OSError:
         pass
     hbm = peaks.get("hbm_gbs", 6800.0)
-    if args.batched_only:
+    if args.batched_only or args.bigdata_only:
         flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
-        out = bench_batched(args, rank, dev, torch.cuda.current_stream(dev), flush, hbm,
-                            "measured" if "hbm_gbs" in peaks else "fallback")
+        run = bench_batched if args.batched_only else bench_bigdata
+        out = run(args, rank, dev, torch.cuda.current_stream(dev), flush, hbm,
+                  "measured" if "hbm_gbs" in peaks else "fallback")
         if rank == 0:
             print(json.dumps(out), flush=True)
         if world > 1:
@@ -571,6 +693,12 @@ def main():
         batched = bench_batched(args, rank, dev, stream, flush, hbm,
                                 "measured" if "hbm_gbs" in peaks else "fallback")
 
+    # ---- the big-data workload (its own sub-object of the line)
+    bigdata = None
+    if not args.no_bigdata:
+        bigdata = bench_bigdata(args, rank, dev, stream, flush, hbm,
+                                "measured" if "hbm_gbs" in peaks else "fallback")
+
     # ---- CPU baseline: the oracle on a bounded sample (rank 0, single GPU only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -601,6 +729,7 @@ def main():
             "clocks": clocks, "accuracy": acc, "fp64_path": fp64, "other_start": other,
             "phases_ms": phases,
             "batched": batched,
+            "bigdata": bigdata,
             "solver": {"iterations": last["iterations"], "refinements": last["refinements"],
                        "rel_residual": last["rel_residual"], "pinned": last["pinned"],
                        "promoted_steps": sum(int(i["promoted"]) for i in infos)},
