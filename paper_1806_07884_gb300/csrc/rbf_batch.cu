@@ -556,20 +556,37 @@ __global__ void __launch_bounds__(kSpmvWarps * 32, sizeof(T) == 4 ? 2 : 1)
     const int lane = threadIdx.x & 31;
     const int nw = gridDim.x * kSpmvWarps;
     int q = blockIdx.x * kSpmvWarps + (threadIdx.x >> 5);
-    int4 next = q < n ? items[q] : make_int4(0, 0, 0, 0);
+    // The warp's cells as one stream: an item's cell indices (one per lane, items hold at
+    // most 64 cells) are loaded an item ahead, and each cell's descriptor one cell ahead, so
+    // a cell's rows start streaming without waiting for either.
+    int4 it = q < n ? items[q] : make_int4(0, 0, 0, 0);
+    int4 next = q + nw < n ? items[q + nw] : make_int4(0, 0, 0, 0);
+    int mine = lane < it.y - it.x ? __ldg(clist + it.x + lane) : 0;
+    int mine2 = lane + 32 < it.y - it.x ? __ldg(clist + it.x + lane + 32) : 0;
+    CellDesc cd = load_desc(bd.cdesc + __shfl_sync(kFull, mine, 0));
     for (; q < n; q += nw) {
-        const int4 it = next;
-        if (q + nw < n) next = items[q + nw];
+        const int4 after = q + 2 * nw < n ? items[q + 2 * nw] : make_int4(0, 0, 0, 0);
+        const int nn = q + nw < n ? next.y - next.x : 0;
+        const int nmine = lane < nn ? __ldg(clist + next.x + lane) : 0;
+        const int nmine2 = lane + 32 < nn ? __ldg(clist + next.x + lane + 32) : 0;
+        const int nc = it.y - it.x;
         T acc = T(0);   // this lane's share of the item's delta (warp sum in T)
-        for (int k0 = it.x; k0 < it.y; k0 += 32) {
-            const int nc = min(32, it.y - k0);
-            const int mine = lane < nc ? __ldg(clist + k0 + lane) : 0;
-            for (int k = 0; k < nc; ++k)
-                acc += spmv_cell<T, (sizeof(T) == 4 ? kSpmvGroupHbm : kSpmvGroupL2)>(
-                    load_desc(bd.cdesc + __shfl_sync(kFull, mine, k)), B, u, w, lane);
+        for (int k = 0; k < nc; ++k) {
+            // descriptor of the following cell: this item's next, else the next item's first
+            const int kn = k + 1;
+            const int cn = kn < nc ? __shfl_sync(kFull, kn < 32 ? mine : mine2, kn & 31)
+                                   : __shfl_sync(kFull, nmine, 0);
+            const CellDesc nd = load_desc(bd.cdesc + cn);
+            acc += spmv_cell<T, (sizeof(T) == 4 ? kSpmvGroupHbm : kSpmvGroupL2)>(cd, B, u, w,
+                                                                                 lane);
+            cd = nd;
         }
         const T sum = warp_sum<T>(acc);
         if (lane == 0 && sum != T(0)) atomicAdd(&dlP[it.z], double(sum));
+        it = next;
+        next = after;
+        mine = nmine;
+        mine2 = nmine2;
     }
 }
 

@@ -219,6 +219,14 @@ __device__ T spmv_cell(const CellDesc& cd, const T* __restrict__ B, const T* x, 
     return dot;
 }
 
+// Start moving a cell descriptor (48 bytes, at most two cache lines) into L1 without holding
+// registers for it; a later load_desc of it then hits L1.
+__device__ __forceinline__ void prefetch_desc(const CellDesc* d) {
+    const char* p = reinterpret_cast<const char*>(d);
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p + sizeof(CellDesc) - 1));
+}
+
 __device__ __forceinline__ CellDesc load_desc(const CellDesc* d) {
     CellDesc v;
     const int4* p = reinterpret_cast<const int4*>(d);

@@ -95,8 +95,11 @@ __global__ void __launch_bounds__(kSpmvWarps * 32, sizeof(T) == 4 ? 3 : 1)
     k_spmv(Binned bd, const T* __restrict__ B, const T* __restrict__ x, T* __restrict__ y) {
     const int lane = threadIdx.x & 31;
     const int nw = gridDim.x * kSpmvWarps;
-    for (int c = blockIdx.x * kSpmvWarps + (threadIdx.x >> 5); c < bd.g.ncell; c += nw)
+    for (int c = blockIdx.x * kSpmvWarps + (threadIdx.x >> 5); c < bd.g.ncell; c += nw) {
+        // the next cell's descriptor moves into L1 while this cell's rows stream
+        if (c + nw < bd.g.ncell) prefetch_desc(bd.cdesc + c + nw);
         spmv_cell<T, kSpmvGroupL2>(load_desc(bd.cdesc + c), B, x, y, lane);
+    }
 }
 
 
@@ -118,7 +121,11 @@ __global__ void __launch_bounds__(kSpmvWarps * 32, sizeof(T) == 4 ? 3 : 1)
     const int gw = blockIdx.x * kSpmvWarps + (threadIdx.x >> 5);
     const int nw = gridDim.x * kSpmvWarps;
     T d = T(0);
-    for (int c = gw; c < bd.g.ncell; c += nw) d += spmv_cell<T, kSpmvGroupL2>(load_desc(bd.cdesc + c), B, u, w, lane);
+    for (int c = gw; c < bd.g.ncell; c += nw) {
+        // the next cell's descriptor moves into L1 while this cell's rows stream
+        if (c + nw < bd.g.ncell) prefetch_desc(bd.cdesc + c + nw);
+        d += spmv_cell<T, kSpmvGroupL2>(load_desc(bd.cdesc + c), B, u, w, lane);
+    }
     d = warp_sum<T>(d);
     if (lane == 0 && d != T(0)) atomicAdd(&sc->acc_delta[P][gw & (kAccSlots - 1)], double(d));
 }
