@@ -44,8 +44,8 @@ sys.path.insert(0, ROOT)
 # profiles/batched_spmv_update_128tiles.md), valid while the captured kernel's source -- its
 # function text and the shared SpMV device code -- is unchanged.
 CSRC = os.path.join(ROOT, "paper_1806_07884_gb300", "csrc")
-SPMV_TRAFFIC = {"sha": "ef43638bc248645f", "bytes": 309760 + 160000}
-BSPMV_TRAFFIC = {"sha": "42cd840c61089568", "per_alg_byte": (303692800 + 10511616) / 302918784}
+SPMV_TRAFFIC = {"sha": "7367e288530a83ff", "bytes": 170240 + 161024}
+BSPMV_TRAFFIC = {"sha": "9c9ea5673f28b93e", "per_alg_byte": (306878976 + 13672192) / 302918784}
 
 
 def kernel_sha(fname, signature):
@@ -67,7 +67,7 @@ def spmv_traffic():
 
 # The big-data SpMV is the single-system kernel on a B streamed from HBM; its DRAM traffic per
 # algorithmic byte comes from a capture of a smaller big-data system (B still far beyond L2).
-BIG_SPMV_TRAFFIC = {"sha": "ef43638bc248645f", "per_alg_byte": (254795520 + 8439808) / 256737316,
+BIG_SPMV_TRAFFIC = {"sha": "7367e288530a83ff", "per_alg_byte": (254805504 + 8428800) / 256737316,
                     "note": "scaled from a 5M x 500k big-data capture"}
 
 

@@ -3,6 +3,7 @@
 // block-Jacobi preconditioner application.
 #pragma once
 
+#include <type_traits>
 #include "rbf_internal.h"
 
 namespace rbf {
@@ -182,21 +183,35 @@ __device__ T spmv_cell(const CellDesc& cd, const T* __restrict__ B, const T* x, 
             // end (not active) read the row's start -- both valid addresses -- and contribute
             // nothing (x_i = 0 for i >= mm, x_t = 0 and no column update when not active).
             const T* rb = Bc + (long long)j0 * lp + (active ? kb : 0);
+            // With 8-row groups, a last group with at most 4 rows left loads only 4 rows (at
+            // about 9 rows per cell this saves a quarter of the loads; measured on the batched
+            // SpMV, while the 4-row shape is faster without the second code path).
+            auto rows = [&](int g0, auto ng) {
+                constexpr int NG = decltype(ng)::value;
+                T v[NG][4];
+#pragma unroll
+                for (int i = 0; i < NG; ++i)
+                    load4(rb + (long long)min(g0 + i, mm - 1) * lp, v[i]);
+#pragma unroll
+                for (int i = 0; i < NG; ++i) {
+                    const T xi = __shfl_sync(kFull, xs_lane, g0 + i);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        rp[g0 + i] = fma(v[i][q], xt[q], rp[g0 + i]);
+                        ca[q] = fma(v[i][q], xi, ca[q]);
+                    }
+                }
+            };
 #pragma unroll
             for (int g0 = 0; g0 < 16; g0 += G) {
                 if (g0 < mm) {                // warp-uniform
-                    T v[G][4];
-#pragma unroll
-                    for (int i = 0; i < G; ++i)
-                        load4(rb + (long long)min(g0 + i, mm - 1) * lp, v[i]);
-#pragma unroll
-                    for (int i = 0; i < G; ++i) {
-                        const T xi = __shfl_sync(kFull, xs_lane, g0 + i);
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            rp[g0 + i] = fma(v[i][q], xt[q], rp[g0 + i]);
-                            ca[q] = fma(v[i][q], xi, ca[q]);
-                        }
+                    if constexpr (G == 8) {
+                        if (mm - g0 <= 4)
+                            rows(g0, std::integral_constant<int, 4>());
+                        else
+                            rows(g0, std::integral_constant<int, 8>());
+                    } else {
+                        rows(g0, std::integral_constant<int, G>());
                     }
                 }
             }
