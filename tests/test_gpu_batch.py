@@ -311,6 +311,25 @@ def test_batched_promotion_finishes_only_the_unconverged_tiles():
     assert mixed, pro
 
 
+def test_batched_more_tiles_than_one_worklist_round():
+    """1,100 small tiles (more than the 1,024 the work-list build scans per round), FP32 +
+    refinement: every tile converges, and sampled tiles match the oracle's fit of that tile
+    alone. Tiles stop at different iterations, so the lists are rebuilt many times."""
+    rng = np.random.default_rng(11)
+    pbs = [dg.tile(70000 + k, N=int(rng.integers(300, 900))) for k in range(1100)]
+    cs, info, tinfo, ctx = pkg.fit_tiles(_problems(pbs), prec="fp32_refine", tol=1e-11)
+    assert info["status"] == OK
+    assert all(t["status"] == OK and t["rel_residual"] <= 1e-11 for t in tinfo)
+    its = [t["iterations"] for t in tinfo]
+    assert len(set(its)) > 10
+    for k in [0, 1, 511, 1023, 1024, 1025, 1099] + list(rng.choice(1100, 5, replace=False)):
+        pb = pbs[k]
+        c_ref, ref = O.fit(pb.points, pb.h, pb.centres, pb.R, pb.kernel)
+        c = cs[k].cpu().numpy()
+        assert O.rel_err(ref["A"] @ c, ref["A"] @ c_ref) <= MIXED_BAR, k
+    ctx.close()
+
+
 def test_autotuner_choice_and_forced_configs_agree():
     pbs = [dg.tile(1030 + k, N=n) for k, n in enumerate((3000, 9000, 5000, 12000))]
     tiles, cx, cy, px, py, hh = pkg.pack_tiles(_problems(pbs))
@@ -325,7 +344,8 @@ def test_autotuner_choice_and_forced_configs_agree():
     c_auto, info, _ = ctx.solve_tiles(tol=1e-10)
     assert ctx.tuning() == tu                       # the cached choice was used
     refs = [_oracle(pb, ("tune", k)) for k, pb in enumerate(pbs)]
-    for bps, chunk, nt in ((1, 1, 128), (2, 8, 512), (3, 16, 256)):
+    # chunk 40: SpMV items of more than 32 cells (their cell indices take two loads per lane)
+    for bps, chunk, nt in ((1, 1, 128), (2, 8, 512), (3, 16, 256), (2, 40, 256)):
         ctx.set_param("spmv_blocks_per_sm", bps)
         ctx.set_param("spmv_chunk", chunk)
         ctx.set_param("update_threads", nt)
