@@ -79,3 +79,36 @@ def test_null_arguments_rejected_without_gpu(libpath):
     assert lib.rbf_create(None, 0, nullf, nullfree, None) == _lib.RBF_ERR_ARG
     # bad device index: rejected without touching a GPU
     assert lib.rbf_create(ctypes.byref(out), 1 << 20, nullf, nullfree, None) != 0
+
+
+def test_struct_layouts_match_the_binding(tmp_path):
+    """Size and field offsets of every struct in include/rbf.h, as a C compiler lays them out,
+    equal those of the ctypes mirrors the binding passes to the library."""
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    from paper_1806_07884_gb300 import _lib
+    mirrors = {"rbf_solve_info": _lib.SolveInfo, "rbf_tile": _lib.Tile, "rbf_tile_info": _lib.TileInfo}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rbf.h"', "int main(void) {"]
+    for cname, py in mirrors.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for field, _ in py._fields_:
+            lines.append(f'printf("{cname} {field} %zu\\n", offsetof({cname}, {field}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    import subprocess
+    r = subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line:
+            name, key, val = line.split()
+            got[(name, key)] = int(val)
+    for cname, py in mirrors.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for field, _ in py._fields_:
+            assert got[(cname, field)] == getattr(py, field).offset, (cname, field)
