@@ -180,8 +180,9 @@ rbf_status rbf_eval_grid(rbf_ctx* ctx, const double* c, int nx, int ny, const do
  *                      new shape and keeps the fastest (see rbf_autotune); 0: it uses the
  *                      forced values below, else a fixed default
  *   "spmv_blocks_per_sm", "spmv_chunk", "update_threads"
- *                      force the batched CG's SpMV blocks per SM (1..8), cells per warp
- *                      step (1..64) and update block size (128, 256 or 512); 0 = automatic
+ *                      force the batched CG's SpMV blocks per SM (1..8), cells per SpMV
+ *                      work item (1..64) and update block size (128, 256 or 512); 0 =
+ *                      automatic
  * Returns RBF_ERR_ARG for an unknown name or a value out of range. */
 rbf_status rbf_set_param(rbf_ctx* ctx, const char* name, double value);
 
@@ -263,13 +264,13 @@ rbf_status rbf_eval_tiles_grid(rbf_ctx* ctx, const double* c, int nx, int ny, do
                                void* stream);
 
 /* Autotuner of the batched CG loop: on the assembled batched system, times CG iterations in
- * each candidate launch configuration (SpMV blocks per SM x cells per warp step, then the
+ * each candidate launch configuration (SpMV blocks per SM x cells per work item, then the
  * update block size) with CUDA events on `stream` and keeps the fastest for systems of this
  * shape. Overwrites the solver workspace. Synchronises `stream`. */
 rbf_status rbf_autotune(rbf_ctx* ctx, void* stream);
 
 /* The launch configuration of the batched CG loop for the precision of the last assembly
- * (HOST outputs, any may be NULL): SpMV blocks per SM, cells per warp step, update block
+ * (HOST outputs, any may be NULL): SpMV blocks per SM, cells per SpMV work item, update block
  * size, and the measured time of one iteration in microseconds (0 if not tuned). */
 rbf_status rbf_get_tuning(const rbf_ctx* ctx, int* spmv_blocks_per_sm, int* spmv_chunk,
                           int* update_threads, double* us_per_iteration);

@@ -15,15 +15,18 @@
 // Solve. The CG iteration is the Chronopoulos-Gear iteration of the single-system solver
 // with its scalars held per tile: alpha_t, beta_t, the stopping test and the iteration count
 // of tile t depend only on tile t's own reductions, so every tile follows the iterates of its
-// own CG and stops at its own tolerance; stopped tiles drop out of the SpMV and the update.
-// Reductions are segmented by tile (warp segmented sums, then shared-memory atomics per
-// tile, then one global atomic per tile and block). The iteration loop is one CUDA graph
-// (conditional WHILE node) that runs until every tile has stopped. FP32 refinement works per
-// tile: own scale, own inner tolerance, own FP64 residual norm and stopping test.
+// own CG and stops at its own tolerance. The iteration loop is one CUDA graph (conditional
+// WHILE node) that runs until every tile has stopped; each pass of its body first lists the
+// work of the tiles still running (SpMV items of consecutive cells of one tile, update items
+// of consecutive rows of one tile), so stopped tiles cost nothing, and the SpMV and update
+// kernels are persistent loops over those lists. Per-tile sums: one atomic per item and value
+// (the start kernel's segmented sums by tile: warp segmented sums, shared-memory atomics per
+// tile, one global atomic per tile and block). FP32 refinement works per tile: own scale, own
+// inner tolerance, own FP64 residual norm, stopping test and promotion to FP64.
 //
-// Launch configuration. The SpMV's blocks per SM, the number of consecutive cells a warp
-// takes per step and the update kernel's block size are picked by timing candidate
-// configurations on the assembled system and cached per system shape (rbf_autotune).
+// Launch configuration. The SpMV's blocks per SM, the number of cells per SpMV item and the
+// update kernel's block size are picked by timing candidate configurations on the assembled
+// system and cached per system shape (rbf_autotune).
 #include <limits.h>
 #include <math.h>
 #include <string.h>
@@ -918,7 +921,7 @@ rbf_status time_cfg(rbf_ctx* ctx, const Cfg& cf, int iters, cudaEvent_t e0, cuda
     return RBF_OK;
 }
 
-// The autotuner: SpMV blocks per SM x cells per warp step (update block size 256), then the
+// The autotuner: SpMV blocks per SM x cells per SpMV item (update block size 256), then the
 // update block size for the best SpMV choice; 8 timed iterations per candidate.
 template <typename T>
 rbf_status autotune_impl(rbf_ctx* ctx, cudaStream_t st) {

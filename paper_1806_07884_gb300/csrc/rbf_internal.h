@@ -105,7 +105,7 @@ struct rbf_ctx {
     size_t hbt_bytes = 0;
     // launch configuration of the batched CG loop, [0] FP64, [1] FP32
     struct TileTuning {
-        int spmv_bps = 0, chunk = 0, nt = 0;   // SpMV blocks per SM, cells per warp step,
+        int spmv_bps = 0, chunk = 0, nt = 0;   // SpMV blocks per SM, cells per SpMV item,
                                                // update block size (0: not chosen yet)
         double us_per_iter = 0.0;              // measured by the autotuner (0: not tuned)
         int ncl = 0, M = 0;                    // shape it was chosen for
