@@ -35,7 +35,8 @@ def _worker(rank, world, port, out):
 
 def test_two_replicas_take_the_slowest_rank():
     port = _free_port()
-    with mp.Manager() as man:
+    # spawn, not fork: in a full test run CUDA is already initialised in this process
+    with mp.get_context("spawn").Manager() as man:
         out = man.dict()
         mp.spawn(_worker, args=(2, port, out), nprocs=2, join=True)
         res = dict(out)
