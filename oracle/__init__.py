@@ -7,3 +7,4 @@ shares no code with the CUDA library (no kernels, headers, helpers or tables).
 """
 from .rbf_oracle import *  # noqa: F401,F403
 from . import mlp_oracle  # noqa: F401
+from . import poly_oracle  # noqa: F401
