@@ -28,3 +28,37 @@ def test_configs_deterministic_and_in_box():
     assert 2000 <= tl.N <= 200000 and tl.M == tl.N // 10
     big = dg.config_bigdata(N=20000, M=2000)
     assert big.points.shape == (20000, 2) and big.kernel == "w32"
+
+
+def test_support_radius_gives_k_centres_per_disc():
+    # reading: pi R^2 M = K on the unit square
+    for M, K in ((100_000, 30.0), (2_000_000, 30.0), (2_000, 20.0)):
+        R = dg.support_radius(M, K)
+        assert abs(np.pi * R * R * M - K) <= 1e-9 * K
+
+
+def test_bigdata_density_variation():
+    """Points are uniform draws kept with probability (1 + 9 s(x)) / 10 with s = (n(x) + 1) / 2
+    from a 3-octave value-noise field n in [-1, 1]: the density can vary at most 10:1, and
+    since n does not reach its bounds the realized contrast is smaller -- on a 32 x 32 grid
+    the densest cell holds about 3.4 times the points of the sparsest (seed 0)."""
+    big = dg.config_bigdata(N=400_000, M=4_000)
+    H, _, _ = np.histogram2d(big.points[:, 0], big.points[:, 1], bins=32, range=[[0, 1], [0, 1]])
+    ratio = H.max() / H.min()
+    assert 2.5 < ratio < 10.0, ratio
+    assert big.h.std() > 0 and np.isfinite(big.h).all()
+
+
+def test_tile_sizes_log_uniform_in_range():
+    """N_t = round(exp(U[ln 2e3, ln 2e5])), M_t = N_t // 10, independent seeds."""
+    ts = dg.tile_batch(1000, 200)
+    N = np.array([t.N for t in ts])
+    assert N.min() >= 2000 and N.max() <= 200000
+    assert all(t.M == t.N // 10 for t in ts)
+    ln = np.log(N)
+    mid = 0.5 * (np.log(2e3) + np.log(2e5))
+    half = 0.5 * (np.log(2e5) - np.log(2e3))
+    # uniform on [mid - half, mid + half]: mean at mid, standard deviation half / sqrt(3)
+    assert abs(ln.mean() - mid) < 0.25 * half
+    assert abs(ln.std() - half / np.sqrt(3)) < 0.2 * half
+    assert len({t.N for t in ts}) > 150
