@@ -235,14 +235,21 @@ def config_terrain(seed: int = 0, N: int = 1_000_000, M: int = 100_000, K: float
 
 def config_bigdata(seed: int = 0, N: int = 20_000_000, M: int = 2_000_000, K: float = 30.0,
                    kernel: str = "w32", eval_n: int = 4096) -> Problem:
-    """Big-data terrain: density 1 + 9 s(x) (10:1), 8-octave value-noise heights."""
+    """Big-data terrain: density 1 + 9 s(x) with s a 3-octave value-noise field scaled to
+    [0, 1] (10:1), 8-octave value-noise heights."""
     rng = np.random.default_rng(seed)
     dens = _noise_fn(rng, octaves=3, base=4)
     terr = _noise_fn(rng, octaves=8, base=4)
+    # s = the density field scaled to [0, 1] by its range on a 513^2 lattice (finer than its
+    # finest octave), so that the density 1 + 9 s varies 10:1
+    g = np.linspace(0.0, 1.0, 513)
+    GX, GY = np.meshgrid(g, g)
+    lat = dens(GX.ravel(), GY.ravel())
+    lo, hi = float(lat.min()), float(lat.max())
     chunks, have = [], 0
     while have < N:
         cand = rng.random((1 << 20, 2))
-        s = 0.5 * (dens(cand[:, 0], cand[:, 1]) + 1.0)          # in [0, 1]
+        s = np.clip((dens(cand[:, 0], cand[:, 1]) - lo) / (hi - lo), 0.0, 1.0)
         keep = rng.random(cand.shape[0]) < (1.0 + 9.0 * s) / 10.0
         chunks.append(cand[keep])
         have += int(keep.sum())

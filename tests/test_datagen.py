@@ -37,15 +37,15 @@ def test_support_radius_gives_k_centres_per_disc():
         assert abs(np.pi * R * R * M - K) <= 1e-9 * K
 
 
-def test_bigdata_density_variation():
-    """Points are uniform draws kept with probability (1 + 9 s(x)) / 10 with s = (n(x) + 1) / 2
-    from a 3-octave value-noise field n in [-1, 1]: the density can vary at most 10:1, and
-    since n does not reach its bounds the realized contrast is smaller -- on a 32 x 32 grid
-    the densest cell holds about 3.4 times the points of the sparsest (seed 0)."""
+def test_bigdata_density_varies_ten_to_one():
+    """Points are uniform draws kept with probability (1 + 9 s(x)) / 10, s a value-noise field
+    scaled to [0, 1] by its range: the density varies 10:1, so on a 16 x 16 grid the densest
+    cell holds several times the points of the sparsest, at most about ten times (up to
+    sampling noise)."""
     big = dg.config_bigdata(N=400_000, M=4_000)
-    H, _, _ = np.histogram2d(big.points[:, 0], big.points[:, 1], bins=32, range=[[0, 1], [0, 1]])
+    H, _, _ = np.histogram2d(big.points[:, 0], big.points[:, 1], bins=16, range=[[0, 1], [0, 1]])
     ratio = H.max() / H.min()
-    assert 2.5 < ratio < 10.0, ratio
+    assert 5.0 < ratio < 13.0, ratio
     assert big.h.std() > 0 and np.isfinite(big.h).all()
 
 
