@@ -112,3 +112,39 @@ def test_struct_layouts_match_the_binding(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(py), cname
         for field, _ in py._fields_:
             assert got[(cname, field)] == getattr(py, field).offset, (cname, field)
+
+
+def _ctx_functions():
+    """Header functions whose first parameter is the context."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*rbf_status\s+(rbf_\w+)\s*\(\s*(?:const\s+)?rbf_ctx\s*\*\s*ctx\b",
+                                 text, flags=re.M)))
+
+
+def test_every_context_call_rejects_a_null_context(libpath):
+    """Every entry point that takes a context returns RBF_ERR_ARG for a null one (other
+    pointers null, numbers zero) before touching a GPU."""
+    from paper_1806_07884_gb300 import _lib
+    lib = _lib.load(libpath)
+    names = _ctx_functions()
+    assert "rbf_solve_tiles" in names and "rbf_warm_start" in names and len(names) >= 20
+    for name in names:
+        args = []
+        for t in _lib.SIGNATURES[name][1]:
+            if t in (ctypes.c_double, ctypes.c_float):
+                args.append(0.0)
+            elif t in (ctypes.c_int, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint32):
+                args.append(0)
+            else:
+                args.append(None)
+        assert getattr(lib, name)(*args) == _lib.RBF_ERR_ARG, name
+    assert lib.rbf_last_error(None) is not None
+
+
+def test_context_free_calls_reject_bad_arguments(libpath):
+    from paper_1806_07884_gb300 import _lib
+    lib = _lib.load(libpath)
+    assert lib.rbf_selftest_sqrt(None, None, 5, None) == _lib.RBF_ERR_ARG
+    assert lib.rbf_eval_noalloc(None, None, None, 1, 0.1, None, 1, None, None, 0, None, None) \
+        == _lib.RBF_ERR_ARG
