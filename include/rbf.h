@@ -30,8 +30,9 @@
  *     to the host (rbf_bin, rbf_solve): those synchronise `stream` before return.
  *   - Errors are returned as rbf_status; no exception crosses this boundary.
  *     rbf_last_error(ctx) gives a message for the last failure on that context.
- *   - Device-side failures (CG breakdown, non-convergence, a grid barrier that waited
- *     longer than its limit) are reported through the status of rbf_solve; no kernel traps.
+ *   - Device-side failures (CG breakdown, non-convergence) are reported through the status
+ *     of rbf_solve / rbf_solve_tiles; no kernel traps, and no kernel spins on a flag set by
+ *     another block, so none can hang.
  *   - A context is not thread-safe; use one context per host thread.
  */
 #ifndef RBF_H_
@@ -52,8 +53,8 @@ typedef enum {
     RBF_ERR_NOT_CONVERGED = 4,  /* solver hit maxit before reaching tol */
     RBF_ERR_BREAKDOWN = 5,      /* CG breakdown: p^T B p <= 0 or a non-finite scalar */
     RBF_ERR_LIMIT = 6,          /* input exceeds a documented kernel limit */
-    RBF_ERR_TIMEOUT = 7         /* a grid-wide wait inside a kernel exceeded its time limit;
-                                   the kernel returned early and the context stays usable */
+    RBF_ERR_TIMEOUT = 7         /* reserved: no entry point of this version returns it (no
+                                   kernel waits on another block or on the host) */
 } rbf_status;
 
 /* Wendland functions phi_{3,s}(r), r = ||x - xi|| / R, zero for r >= 1 (Table 2, Eq. 18).
@@ -328,10 +329,14 @@ rbf_status rbf_warm_start(rbf_ctx* ctx, const float* params, double* c0, void* s
  * reserved when the library is loaded (each GPU that loads the library keeps it until the
  * process exits); nothing is allocated and no context is used.
  * Limits: M <= 65536 and at most 65536 cells of side R over bbox, else RBF_ERR_LIMIT (no
- * work queued). The first call on a device looks up the scratch address with that device
- * current (the device must be current when calling); make that first call before any stream
- * capture. Every call on a device shares the scratch: calls whose GPU work overlaps (other
- * streams or threads) race; calls ordered on one stream are safe. Asynchronous on `stream`. */
+ * work queued). The scratch address belongs to the CUDA context current on the calling
+ * thread: the first call in each context (the device's primary context unless the caller made
+ * another one current; a context created after a device reset counts as new) looks it up, so
+ * make that first call before any stream capture. Every call on a device shares the scratch:
+ * calls whose GPU work overlaps (other streams or threads) race; calls ordered on one stream
+ * are safe. The order in which a cell's centres are summed comes from atomic counters, so two
+ * identical calls can differ in the last bits; the value agrees with rbf_eval to rounding.
+ * Asynchronous on `stream`. */
 rbf_status rbf_eval_noalloc(const double* cx, const double* cy, const double* c, int64_t M,
                             double R, const double* bbox, rbf_kernel kernel, const double* qx,
                             const double* qy, int64_t Q, double* f, void* stream);

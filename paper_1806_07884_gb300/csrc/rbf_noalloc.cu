@@ -15,6 +15,17 @@
 // The scratch is shared by every call on a device: two calls whose work overlaps on the
 // GPU (different streams, or different host threads on the same device) race on it.
 // Calls on one stream are ordered and safe. The cell counters are cleared by each call.
+//
+// The host needs the scratch's device address, which belongs to the CUDA context that is
+// current. It is looked up with cudaGetSymbolAddress the first time a context is seen and
+// cached under that context's unique id (cuCtxGetId, never reused within a process), so a
+// context created after a device reset gets its own lookup instead of a stale address.
+//
+// Within a cell the centres are in the order their atomic counters handed out, which can
+// change from call to call: the sums of one query are then added in a different order and
+// two identical calls can differ in the last bits (the value agrees with rbf_eval to
+// rounding, not bit for bit).
+#include <cuda.h>
 #include <math.h>
 
 #include <algorithm>
@@ -153,22 +164,69 @@ __global__ void k_na_eval(unsigned char* base, Grid g, const double* __restrict_
     }
 }
 
-// Device address of g_na_scratch, looked up once per device (with that device current).
+// Device address of g_na_scratch per CUDA context. The driver's context functions are
+// reached through the runtime's entry-point query, so the library does not link libcuda.
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+constexpr int kNaCache = 64;
+struct NaEntry {
+    unsigned long long ctx_id;
+    void* ptr;
+};
 std::mutex g_na_mutex;
-void* g_na_ptr[256] = {};
+NaEntry g_na_cache[kNaCache] = {};
+int g_na_used = 0, g_na_next = 0;
+CtxGetCurrentFn g_get_current = nullptr;
+CtxGetIdFn g_get_id = nullptr;
 
+rbf_status na_driver_fns() {
+    if (g_get_current && g_get_id) return RBF_OK;
+    void* a = nullptr;
+    void* b = nullptr;
+    cudaDriverEntryPointQueryResult qa, qb;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa) !=
+            cudaSuccess ||
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb) !=
+            cudaSuccess ||
+        qa != cudaDriverEntryPointSuccess || qb != cudaDriverEntryPointSuccess || !a || !b) {
+        cudaGetLastError();
+        return RBF_ERR_CUDA;
+    }
+    g_get_current = reinterpret_cast<CtxGetCurrentFn>(a);
+    g_get_id = reinterpret_cast<CtxGetIdFn>(b);
+    return RBF_OK;
+}
+
+// The scratch address in the context current on device `dev` (made current first if the
+// runtime has not yet set one up on this thread).
 rbf_status na_scratch(int dev, unsigned char** out) {
-    if (dev < 0 || dev >= 256) return RBF_ERR_ARG;
     std::lock_guard<std::mutex> lock(g_na_mutex);
-    if (!g_na_ptr[dev]) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_na_scratch) != cudaSuccess || !p) {
+    rbf_status s = na_driver_fns();
+    if (s != RBF_OK) return s;
+    CUcontext cu = nullptr;
+    if (g_get_current(&cu) != CUDA_SUCCESS) return RBF_ERR_CUDA;
+    if (!cu) {
+        // no context on this thread yet: make the device's primary context current
+        if (cudaSetDevice(dev) != cudaSuccess || g_get_current(&cu) != CUDA_SUCCESS || !cu) {
             cudaGetLastError();
             return RBF_ERR_CUDA;
         }
-        g_na_ptr[dev] = p;
     }
-    *out = static_cast<unsigned char*>(g_na_ptr[dev]);
+    unsigned long long id = 0;
+    if (g_get_id(cu, &id) != CUDA_SUCCESS) return RBF_ERR_CUDA;
+    for (int k = 0; k < g_na_used; ++k)
+        if (g_na_cache[k].ctx_id == id) {
+            *out = static_cast<unsigned char*>(g_na_cache[k].ptr);
+            return RBF_OK;
+        }
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_na_scratch) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return RBF_ERR_CUDA;
+    }
+    const int slot = g_na_used < kNaCache ? g_na_used++ : (g_na_next++ % kNaCache);
+    g_na_cache[slot] = NaEntry{id, p};
+    *out = static_cast<unsigned char*>(p);
     return RBF_OK;
 }
 
