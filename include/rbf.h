@@ -121,12 +121,15 @@ const char* rbf_last_error(const rbf_ctx* ctx);
 /* Step (a): bin M centres (cx, cy) and N points (px, py) with heights h into a uniform
  * grid of cell side R (plus a 2^-30 relative margin) over bbox = {x0, y0, x1, y1}
  * (HOST array of 4 doubles). Items outside bbox are clamped to the edge cells, which
- * stays correct. The context keeps cell-sorted copies of the inputs and the permutation
- * back to the caller's centre order, and sizes the block-sparse B (Section 5: symmetric,
- * only the upper triangle stored, in cell-pair blocks). Requires M >= 1, N >= 1, R > 0,
- * finite coordinates and heights. Synchronises `stream`.
+ * stays correct. The context keeps cell-sorted copies of the inputs (within a cell, centres
+ * ordered by x) and the permutation back to the caller's centre order, and lays out the
+ * sparse B (Section 5: symmetric, only the upper triangle stored): row s keeps the columns
+ * t >= s of the centres within 2R of xi_s (a slightly wider superset), as three contiguous
+ * ranges of the sorted order, one per cell row. Requires M >= 1, N >= 1, R > 0, finite
+ * coordinates and heights. Synchronises `stream`.
  * Returns RBF_ERR_LIMIT if some 3x3 cell neighbourhood holds more than
- * rbf_max_candidates() centres. */
+ * rbf_max_candidates() centres, a cell more than 16384 centres, one cell row more than 2046
+ * centres within 2R of a centre, or the stored B more than 2^33 values. */
 rbf_status rbf_bin(rbf_ctx* ctx, const double* cx, const double* cy, int64_t M,
                    const double* px, const double* py, const double* h, int64_t N,
                    double R, const double* bbox, void* stream);
@@ -181,16 +184,30 @@ rbf_status rbf_eval_grid(rbf_ctx* ctx, const double* c, int nx, int ny, const do
  *                      new shape and keeps the fastest (see rbf_autotune); 0: it uses the
  *                      forced values below, else a fixed default
  *   "spmv_blocks_per_sm", "spmv_chunk", "update_threads"
- *                      force the batched CG's SpMV blocks per SM (1..8), cells per SpMV
- *                      work item (1..64) and update block size (128, 256 or 512); 0 =
+ *                      force the batched CG's SpMV blocks per SM (1..8), row groups per
+ *                      SpMV work item (1..64) and update block size (128, 256 or 512); 0 =
  *                      automatic
  * Returns RBF_ERR_ARG for an unknown name or a value out of range. */
 rbf_status rbf_set_param(rbf_ctx* ctx, const char* name, double value);
 
-/* Diagnostics: number of stored B values (upper cell-pair blocks) and bytes per value
- * of the last assembly; sizes of the cell grid. HOST outputs, any may be NULL. */
+/* Diagnostics: number of stored B values (the upper rows the SpMV streams) and bytes per
+ * value of the last assembly; sizes of the cell grid. HOST outputs, any may be NULL. */
 rbf_status rbf_get_layout(const rbf_ctx* ctx, int64_t* nvals, int* value_bytes, int* gx,
                           int* gy);
+
+/* Diagnostics of the stored B after an assembly. */
+typedef struct {
+    int64_t stored_values;   /* values the SpMV streams (as rbf_get_layout's nvals) */
+    int64_t nonzeros;        /* stored values that are not exactly zero: the nonzeros of the
+                                upper triangle of B, diagonal included (Eq. 11-12) */
+    int64_t row_groups;      /* row groups (up to 16 consecutive rows) the SpMV sweeps */
+    int64_t dropped;         /* Gram entries of the last assembly that found no slot in their
+                                row: 0 by construction (any other value is a library defect) */
+} rbf_layout_stats;
+
+/* Fill *out (HOST) for the last assembly; counts the nonzeros on the GPU. Requires a
+ * preceding rbf_assemble. Synchronises `stream`. */
+rbf_status rbf_get_layout_stats(rbf_ctx* ctx, rbf_layout_stats* out, void* stream);
 
 /* Diagnostics: copy the assembled B as COO triplets (upper triangle incl. diagonal,
  * caller's centre indices) into DEVICE arrays of capacity cap; *nnz gets the count.
@@ -265,13 +282,13 @@ rbf_status rbf_eval_tiles_grid(rbf_ctx* ctx, const double* c, int nx, int ny, do
                                void* stream);
 
 /* Autotuner of the batched CG loop: on the assembled batched system, times CG iterations in
- * each candidate launch configuration (SpMV blocks per SM x cells per work item, then the
+ * each candidate launch configuration (SpMV blocks per SM x row groups per work item, then the
  * update block size) with CUDA events on `stream` and keeps the fastest for systems of this
  * shape. Overwrites the solver workspace. Synchronises `stream`. */
 rbf_status rbf_autotune(rbf_ctx* ctx, void* stream);
 
 /* The launch configuration of the batched CG loop for the precision of the last assembly
- * (HOST outputs, any may be NULL): SpMV blocks per SM, cells per SpMV work item, update block
+ * (HOST outputs, any may be NULL): SpMV blocks per SM, row groups per SpMV work item, update block
  * size, and the measured time of one iteration in microseconds (0 if not tuned). */
 rbf_status rbf_get_tuning(const rbf_ctx* ctx, int* spmv_blocks_per_sm, int* spmv_chunk,
                           int* update_threads, double* us_per_iteration);

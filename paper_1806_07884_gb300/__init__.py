@@ -286,6 +286,15 @@ class Context:
                                             C.byref(gy)), "rbf_get_layout")
         return dict(nvals=nv.value, value_bytes=vb.value, gx=gx.value, gy=gy.value)
 
+    def layout_stats(self, stream=None):
+        """Stored values, nonzeros of the upper triangle (diagonal included), row groups and
+        dropped Gram entries (always 0) of the last assembly."""
+        st = _lib.LayoutStats()
+        self._check(self.lib.rbf_get_layout_stats(self._h, C.byref(st), self._stream(stream)),
+                    "rbf_get_layout_stats")
+        return dict(stored_values=st.stored_values, nonzeros=st.nonzeros,
+                    row_groups=st.row_groups, dropped=st.dropped)
+
     def set_param(self, name: str, value: float):
         """Solver parameters: "inner_tol", "max_refinements" (see include/rbf.h)."""
         self._check(self.lib.rbf_set_param(self._h, name.encode(), float(value)), "rbf_set_param")

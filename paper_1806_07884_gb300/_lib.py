@@ -37,6 +37,11 @@ class TileInfo(C.Structure):
                 ("promoted", C.c_int)]
 
 
+class LayoutStats(C.Structure):
+    _fields_ = [("stored_values", C.c_int64), ("nonzeros", C.c_int64),
+                ("row_groups", C.c_int64), ("dropped", C.c_int64)]
+
+
 _P = C.c_void_p
 _D = C.c_double
 _I = C.c_int
@@ -54,6 +59,7 @@ SIGNATURES = {
     "rbf_eval": (_I, [_P, _P, _P, _P, _I64, _P, _P]),
     "rbf_eval_grid": (_I, [_P, _P, _I, _I, C.POINTER(_D), _P, _P]),
     "rbf_get_layout": (_I, [_P, C.POINTER(_I64), C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)]),
+    "rbf_get_layout_stats": (_I, [_P, C.POINTER(LayoutStats), _P]),
     "rbf_export_upper": (_I, [_P, _I64, _P, _P, _P, _P, _P, C.POINTER(_I64), _P]),
     "rbf_get_launch_count": (_I, [_P, C.POINTER(_I64)]),
     "rbf_set_param": (_I, [_P, C.c_char_p, _D]),

@@ -76,11 +76,11 @@ Binned view(const rbf_ctx* ctx) {
     v.pu = ctx->pu.as<float>();
     v.pv = ctx->pv.as<float>();
     v.cperm = ctx->cperm.as<int>();
-    v.seg = ctx->seg.as<RowSeg>();
-    v.rboff = ctx->rboff.as<int64_t>();
+    v.rmeta = ctx->rmeta.as<RowMeta>();
+    v.gdesc = ctx->gdesc.as<GroupDesc>();
+    v.ngroup = ctx->ngroup;
     v.bjoff = ctx->bjoff.as<int64_t>();
     v.crow = ctx->crow.as<int4>();
-    v.cdesc = ctx->cdesc.as<CellDesc>();
     return v;
 }
 
@@ -146,10 +146,10 @@ rbf_status rbf_destroy(rbf_ctx* ctx) {
     rbf_buf* bufs[] = {&ctx->ccount, &ctx->pcount, &ctx->cstart, &ctx->pstart, &ctx->ckey,
                        &ctx->crank, &ctx->pkey, &ctx->prank, &ctx->cx, &ctx->cy, &ctx->cu,
                        &ctx->cv, &ctx->cperm, &ctx->px, &ctx->py, &ctx->ph, &ctx->pu, &ctx->pv,
-                       &ctx->seg, &ctx->rbsize, &ctx->rboff, &ctx->wcount, &ctx->wstart, &ctx->bjsize, &ctx->bjoff,
+                       &ctx->rmeta, &ctx->rsize, &ctx->roff, &ctx->gcount, &ctx->gstart, &ctx->gdesc, &ctx->wcount, &ctx->wstart, &ctx->bjsize, &ctx->bjoff,
                        &ctx->work, &ctx->scan_tmp, &ctx->stats, &ctx->bvals, &ctx->bvec,
                        &ctx->support, &ctx->x, &ctx->r, &ctx->cgv[0], &ctx->cgv[1],
-                       &ctx->dinv, &ctx->dinv32, &ctx->bjinv, &ctx->bjinv32, &ctx->crow, &ctx->cdesc,
+                       &ctx->dinv, &ctx->dinv32, &ctx->bjinv, &ctx->bjinv32, &ctx->crow,
                        &ctx->partial, &ctx->scal, &ctx->csort, &ctx->sigma, &ctx->feat,
                        &ctx->mlp_part, &ctx->astore, &ctx->amask, &ctx->woff, &ctx->wsize};
     for (rbf_buf* b : bufs) release(ctx, *b);
@@ -371,6 +371,14 @@ rbf_status rbf_get_layout(const rbf_ctx* ctx, int64_t* nvals, int* value_bytes, 
     if (gx) *gx = ctx->g.gx;
     if (gy) *gy = ctx->g.gy;
     return RBF_OK;
+}
+
+rbf_status rbf_get_layout_stats(rbf_ctx* ctx, rbf_layout_stats* out, void* stream) {
+    if (!ctx) return RBF_ERR_ARG;
+    if (!out) return set_err(ctx, RBF_ERR_ARG, "null out");
+    if (!ctx->assembled) return set_err(ctx, RBF_ERR_ARG, "rbf_get_layout_stats before rbf_assemble");
+    DeviceGuard dg(ctx->device);
+    return layout_stats_run(ctx, out, as_stream(stream));
 }
 
 rbf_status rbf_export_upper(rbf_ctx* ctx, int64_t cap, int32_t* row, int32_t* col, double* val,

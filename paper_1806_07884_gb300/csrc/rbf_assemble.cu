@@ -11,7 +11,9 @@
 // (Algorithm 1's triplets, never written to memory). The local Gram matrix
 // G = Phi^T Phi (upper triangle only, Section 5) is accumulated in registers, 4x4
 // entries per thread, and finally added into the stored upper triangle of B with
-// atomics; b and the support counts are reduced per candidate.
+// atomics (entry (a, b), a <= b in the candidate order, which is the sorted order, goes to row
+// s_a at the slot of column s_b; the diagonal halved, see RowMeta); b and the support counts
+// are reduced per candidate.
 #include <algorithm>
 
 #include "rbf_internal.h"
@@ -28,7 +30,7 @@ struct CandSmem {
     CT* y;
     int* s;             // [npad] sorted centre index
     int* a9;            // [npad] local cell 0..8 (row-major in the 3x3 block)
-    long long* rowbase; // [npad] offset of the candidate's row of B
+    RowMeta* rm;        // [npad] the candidate's stored row of B (assembly only)
     double* cval;       // [npad] coefficient (residual pass only)
     float* lu;          // [npad] FP32 coordinates in the point cell's frame, units of R
     float* lv;          //        (the same arrays as x, y in the FP32 path)
@@ -36,8 +38,6 @@ struct CandSmem {
 
 struct LocalCells {
     int start[9], len[9], off[10], cell[9];
-    int colshift[9][3];   // column offset of a centre t in the row block of local cell k,
-                          // for t in segment dy: segbase - segstart
     int n;
 };
 
@@ -53,10 +53,6 @@ __device__ void describe_cells(const Binned& bd, int cell, LocalCells& lc) {
             cc = cy * g.gx + cx;
             s = bd.cstart[cc];
             l = bd.cstart[cc + 1] - s;
-            const RowSeg sg = bd.seg[cc];
-            lc.colshift[k][0] = -sg.s0;
-            lc.colshift[k][1] = sg.l0 - sg.s1;
-            lc.colshift[k][2] = sg.l0 + sg.l1 - sg.s2;
         }
         lc.start[k] = s;
         lc.len[k] = l;
@@ -78,12 +74,9 @@ __device__ void stage_candidates(const Binned& bd, const LocalCells& lc, const C
             int k = 0;
             while (a >= lc.off[k + 1]) ++k;
             const int s = lc.start[k] + (a - lc.off[k]);
-            const int cc = lc.cell[k];
             cs.s[a] = s;
             cs.a9[a] = k;
-            const RowSeg sg = bd.seg[cc];
-            cs.rowbase[a] = (long long)bd.rboff[cc] +
-                            (long long)(s - bd.cstart[cc]) * (long long)sg.lp;
+            if (cs.rm) cs.rm[a] = bd.rmeta[s];
             cs.lu[a] = bd.cu[s] + float((k % 3) - 1);
             cs.lv[a] = bd.cv[s] + float((k / 3) - 1);
             if constexpr (sizeof(CT) == 8) {
@@ -94,7 +87,7 @@ __device__ void stage_candidates(const Binned& bd, const LocalCells& lc, const C
         } else {
             cs.s[a] = 0;
             cs.a9[a] = 0;
-            cs.rowbase[a] = 0;
+            if (cs.rm) cs.rm[a] = RowMeta{0, 0, 0, 0};
             cs.x[a] = CT(1e30);
             cs.y[a] = CT(1e30);
             cs.lu[a] = 1e30f;
@@ -169,7 +162,8 @@ template <int KIND, typename T>
 __global__ void __launch_bounds__(kThreads) k_assemble(Binned bd, const int4* __restrict__ work,
                                                        int npad, T* __restrict__ B,
                                                        double* __restrict__ bvec,
-                                                       int* __restrict__ support) {
+                                                       int* __restrict__ support,
+                                                       int* __restrict__ dropped) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ LocalCells lc;
     constexpr bool kFP64 = sizeof(T) == 8;
@@ -184,8 +178,8 @@ __global__ void __launch_bounds__(kThreads) k_assemble(Binned bd, const int4* __
     T* phi = reinterpret_cast<T*>(sp);
     sp += sizeof(T) * kSubChunk * npad;
     CandSmem<T> cs;
-    cs.rowbase = reinterpret_cast<long long*>(sp);
-    sp += sizeof(long long) * npad;
+    cs.rm = reinterpret_cast<RowMeta*>(sp);
+    sp += sizeof(RowMeta) * npad;
     cs.x = reinterpret_cast<T*>(sp);
     sp += sizeof(T) * npad;
     cs.y = reinterpret_cast<T*>(sp);
@@ -278,14 +272,15 @@ __global__ void __launch_bounds__(kThreads) k_assemble(Binned bd, const int4* __
                 }
             }
         }
-        // scatter the thread's 4x4 block of the local Gram matrix into B (upper triangle)
+        // scatter the thread's 4x4 block of the local Gram matrix into B (upper triangle):
+        // entry (a, b), a <= b, to row s_a, column s_b, whose cell row is dy above s_a's
         if (active) {
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int a = 4 * bi + u;
                 if (a >= n) continue;
                 const int ka = cs.a9[a];
-                const long long rba = cs.rowbase[a];
+                const RowMeta rma = cs.rm[a];
                 const int sa = cs.s[a];
 #pragma unroll
                 for (int v = 0; v < 4; ++v) {
@@ -293,11 +288,12 @@ __global__ void __launch_bounds__(kThreads) k_assemble(Binned bd, const int4* __
                     if (b >= n || b < a) continue;
                     const T val = acc[u][v];
                     if (val == T(0)) continue;
-                    const int kb = cs.a9[b];
-                    const int dy = kb / 3 - ka / 3;
-                    atomicAdd(&B[rba + lc.colshift[ka][dy] + cs.s[b]], val);
-                    if (b != a && kb == ka)
-                        atomicAdd(&B[cs.rowbase[b] + lc.colshift[kb][0] + sa], val);
+                    const int dy = cs.a9[b] / 3 - ka / 3;
+                    const long long slot = upper_slot(rma, sa, cs.s[b], dy);
+                    if (slot >= 0)
+                        atomicAdd(&B[slot], b == a ? T(0.5) * val : val);
+                    else
+                        atomicAdd(dropped, 1);
                 }
             }
         }
@@ -340,8 +336,7 @@ __global__ void __launch_bounds__(kThreads) k_residual(Binned bd, const int4* __
     double* phi = reinterpret_cast<double*>(sp);
     sp += sizeof(double) * kSubChunk * npad;
     CandSmem<double> cs;
-    cs.rowbase = reinterpret_cast<long long*>(sp);
-    sp += sizeof(long long) * npad;
+    cs.rm = nullptr;
     cs.x = reinterpret_cast<double*>(sp);
     sp += sizeof(double) * npad;
     cs.y = reinterpret_cast<double*>(sp);
@@ -508,9 +503,10 @@ __global__ void k_work_sizes(Binned bd, const int4* __restrict__ work, int nwork
 
 template <typename T>
 size_t asm_smem(int npad, bool resid) {
-    size_t b = sizeof(T) * kSubChunk * npad + sizeof(long long) * npad + 2 * sizeof(T) * npad +
-               3 * sizeof(int) * npad + sizeof(double) * kSubChunk;
+    size_t b = sizeof(T) * kSubChunk * npad + 2 * sizeof(T) * npad + 3 * sizeof(int) * npad +
+               sizeof(double) * kSubChunk;
     if (resid) b += sizeof(double) * npad;
+    else b += sizeof(RowMeta) * npad;
     if (sizeof(T) == 8)   // FP32 prefilter coordinates and the per-warp compacted lists
         b += 2 * sizeof(float) * npad + sizeof(int) * npad * (kThreads / 32);
     return b;
@@ -522,7 +518,8 @@ rbf_status launch_assemble(rbf_ctx* ctx, cudaStream_t st, int npad) {
     auto kfn = k_assemble<KIND, T>;
     RBF_CUDA_TRY(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
     kfn<<<ctx->nwork, kThreads, sm, st>>>(view(ctx), ctx->work.as<int4>(), npad, ctx->bvals.as<T>(),
-                                          ctx->bvec.as<double>(), ctx->support.as<int>());
+                                          ctx->bvec.as<double>(), ctx->support.as<int>(),
+                                          ctx->stats.as<int>() + 12);
     RBF_CUDA_TRY(cudaGetLastError());
     ctx->launches += 1;
     return RBF_OK;
@@ -559,6 +556,8 @@ rbf_status assemble_run(rbf_ctx* ctx, int kernel, int prec, cudaStream_t st) {
     RBF_CUDA_TRY(cudaMemsetAsync(ctx->bvals.p, 0, vb * ctx->nvals, st));
     RBF_CUDA_TRY(cudaMemsetAsync(ctx->bvec.p, 0, sizeof(double) * M, st));
     RBF_CUDA_TRY(cudaMemsetAsync(ctx->support.p, 0, sizeof(int) * M, st));
+    // stats[12]: Gram entries that found no slot in their row (none by construction)
+    RBF_CUDA_TRY(cudaMemsetAsync(ctx->stats.as<int>() + 12, 0, sizeof(int), st));
     if (ctx->nwork == 0) return RBF_OK;
     const int npad = std::max(4, (ctx->max_cand + 3) / 4 * 4);
     if (prec == RBF_FP64) {

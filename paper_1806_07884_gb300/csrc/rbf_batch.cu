@@ -17,14 +17,14 @@
 // of tile t depend only on tile t's own reductions, so every tile follows the iterates of its
 // own CG and stops at its own tolerance. The iteration loop is one CUDA graph (conditional
 // WHILE node) that runs until every tile has stopped; each pass of its body first lists the
-// work of the tiles still running (SpMV items of consecutive cells of one tile, update items
-// of consecutive rows of one tile), so stopped tiles cost nothing, and the SpMV and update
+// work of the tiles still running (SpMV items of consecutive row groups of one tile, update
+// items of consecutive rows of one tile), so stopped tiles cost nothing, and the SpMV and update
 // kernels are persistent loops over those lists. Per-tile sums: one atomic per item and value
 // (the start kernel's segmented sums by tile: warp segmented sums, shared-memory atomics per
 // tile, one global atomic per tile and block). FP32 refinement works per tile: own scale, own
 // inner tolerance, own FP64 residual norm, stopping test and promotion to FP64.
 //
-// Launch configuration. The SpMV's blocks per SM, the number of cells per SpMV item and the
+// Launch configuration. The SpMV's blocks per SM, the number of row groups per SpMV item and the
 // update kernel's block size are picked by timing candidate configurations on the assembled
 // system and cached per system shape (rbf_autotune).
 #include <limits.h>
@@ -123,13 +123,13 @@ struct TileLayout {
     }
 };
 
-// Per-tile ranges and the CG work lists (twork). A tile's non-empty cells are consecutive in
-// the cell list and its centres consecutive in the sorted order (bands follow tile order).
-// Work items cover one tile each: SpMV items {first, end} of `chunk` cells of the cell list,
-// update items {first, end} of `nt` rows; .z the tile, .w = 1 on a tile's first update item
-// (the tile's owner).
+// Per-tile ranges and the CG work lists (twork). A tile's row groups are consecutive in the
+// group list and its centres consecutive in the sorted order (bands follow tile order).
+// Work items cover one tile each: SpMV items {first, end} of `chunk` row groups, update items
+// {first, end} of `nt` rows; .z the tile, .w = 1 on a tile's first update item (the tile's
+// owner).
 struct TileWork {
-    int *clb, *cle;            // [T] tile t's cells: cell-list entries clb[t] .. cle[t]-1
+    int *clb, *cle;            // [T] tile t's row groups clb[t] .. cle[t]-1
     int *rb, *re;              // [T] tile t's rows (sorted centres) rb[t] .. re[t]-1
     int4* items_s;             // [cap_s] SpMV items
     int4* items_u;             // [cap_u] update items
@@ -137,9 +137,9 @@ struct TileWork {
 struct WorkLayout {
     size_t clb, cle, rb, re, items_s, items_u, ranges_end, total;
     int cap_s, cap_u;
-    // capacities for chunk >= 1 cells and nt >= 128 rows per item
-    WorkLayout(int T, int ncl, int M) {
-        cap_s = ncl + T;
+    // capacities for chunk >= 1 row groups and nt >= 128 rows per item
+    WorkLayout(int T, int ngroup, int M) {
+        cap_s = ngroup + T;
         cap_u = div_up(M, 128) + T;
         size_t o = 0;
         auto take = [&](size_t n) {
@@ -244,24 +244,14 @@ __global__ void k_tile_scatter(const TileDev* __restrict__ td, int which,
     }
 }
 
-__global__ void k_cell_flags(int ncell, const int* __restrict__ cstart, int* __restrict__ flag) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c < ncell) flag[c] = cstart[c + 1] > cstart[c] ? 1 : 0;
-}
-__global__ void k_cell_compact(int ncell, const int* __restrict__ cstart,
-                               const int* __restrict__ pos, int* __restrict__ list) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c < ncell && cstart[c + 1] > cstart[c]) list[pos[c]] = c;
-}
-
-// Each tile's range in the cell list and in the sorted rows, from the ends of its runs.
-__global__ void k_tile_ranges(const int* __restrict__ clist, int ncl, const int* __restrict__ rowtile,
-                              int gx, const int4* __restrict__ crow, int M, TileWork tw) {
+// Each tile's range in the group list and in the sorted rows, from the ends of its runs.
+__global__ void k_tile_ranges(const GroupDesc* __restrict__ gdesc, int ngroup,
+                              const int4* __restrict__ crow, int M, TileWork tw) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < ncl) {
-        const int t = rowtile[clist[i] / gx];
-        if (i == 0 || rowtile[clist[i - 1] / gx] != t) tw.clb[t] = i;
-        if (i == ncl - 1 || rowtile[clist[i + 1] / gx] != t) tw.cle[t] = i + 1;
+    if (i < ngroup) {
+        const int t = crow[gdesc[i].r0].w;
+        if (i == 0 || crow[gdesc[i - 1].r0].w != t) tw.clb[t] = i;
+        if (i == ngroup - 1 || crow[gdesc[i + 1].r0].w != t) tw.cle[t] = i + 1;
     }
     if (i < M) {
         const int t = crow[i].w;
@@ -536,16 +526,16 @@ __global__ void __launch_bounds__(kWlThreads)
 }
 
 // w += B u over the SpMV items of the running tiles; delta_t = u^T B u per tile (one atomic
-// per item). Persistent warps stride over the items, the next item's descriptor in flight
-// during the current one and an item's cell indices loaded one per lane. A tile that stops
-// inside a graph body keeps its items until the next body (at most kItersPerBody - 1 SpMVs
-// whose w and delta its stopped state leaves unused). Also zeroes the per-tile sums the
-// next update kernel accumulates (parity P ^ 1).
+// per item). Persistent warps stride over the items (runs of row groups of one tile), the next
+// group's descriptor moving into L1 while the current group streams. A tile that stops inside
+// a graph body keeps its items until the next body (at most kItersPerBody - 1 SpMVs whose w
+// and delta its stopped state leaves unused). Also zeroes the per-tile sums the next update
+// kernel accumulates (parity P ^ 1).
 template <typename T>
-__global__ void __launch_bounds__(kSpmvWarps * 32, sizeof(T) == 4 ? 2 : 1)
-    k_bcg_spmv(Binned bd, const int* __restrict__ clist, const int4* __restrict__ items,
-               const T* __restrict__ B, const T* __restrict__ u, T* __restrict__ w, int P,
-               int ntile, TileCg tc) {
+__global__ void __launch_bounds__(kSpmvWarps * 32, 2)
+    k_bcg_spmv(Binned bd, const int4* __restrict__ items, const T* __restrict__ B,
+               const T* __restrict__ u, T* __restrict__ w, int P, int ntile, TileCg tc) {
+    __shared__ GroupSmem gsm[kSpmvWarps];
     // parity selection by value (indexing the parameter's arrays with P would copy them to
     // local memory)
     double* __restrict__ gQ = P ? tc.g[0] : tc.g[1];
@@ -556,40 +546,22 @@ __global__ void __launch_bounds__(kSpmvWarps * 32, sizeof(T) == 4 ? 2 : 1)
         rrQ[t] = 0.0;
     }
     const int n = tc.bs->n_spmv;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int nw = gridDim.x * kSpmvWarps;
-    int q = blockIdx.x * kSpmvWarps + (threadIdx.x >> 5);
-    // The warp's cells as one stream: an item's cell indices (one per lane, items hold at
-    // most 64 cells) are loaded an item ahead, and each cell's descriptor one cell ahead, so
-    // a cell's rows start streaming without waiting for either.
+    int q = blockIdx.x * kSpmvWarps + wid;
     int4 it = q < n ? items[q] : make_int4(0, 0, 0, 0);
-    int4 next = q + nw < n ? items[q + nw] : make_int4(0, 0, 0, 0);
-    int mine = lane < it.y - it.x ? __ldg(clist + it.x + lane) : 0;
-    int mine2 = lane + 32 < it.y - it.x ? __ldg(clist + it.x + lane + 32) : 0;
-    CellDesc cd = load_desc(bd.cdesc + __shfl_sync(kFull, mine, 0));
     for (; q < n; q += nw) {
-        const int4 after = q + 2 * nw < n ? items[q + 2 * nw] : make_int4(0, 0, 0, 0);
-        const int nn = q + nw < n ? next.y - next.x : 0;
-        const int nmine = lane < nn ? __ldg(clist + next.x + lane) : 0;
-        const int nmine2 = lane + 32 < nn ? __ldg(clist + next.x + lane + 32) : 0;
-        const int nc = it.y - it.x;
+        const int4 next = q + nw < n ? items[q + nw] : make_int4(0, 0, 0, 0);
         T acc = T(0);   // this lane's share of the item's delta (warp sum in T)
-        for (int k = 0; k < nc; ++k) {
-            // descriptor of the following cell: this item's next, else the next item's first
-            const int kn = k + 1;
-            const int cn = kn < nc ? __shfl_sync(kFull, kn < 32 ? mine : mine2, kn & 31)
-                                   : __shfl_sync(kFull, nmine, 0);
-            const CellDesc nd = load_desc(bd.cdesc + cn);
-            acc += spmv_cell<T, (sizeof(T) == 4 ? kSpmvGroupHbm : kSpmvGroupL2)>(cd, B, u, w,
-                                                                                 lane);
-            cd = nd;
+        for (int g = it.x; g < it.y; ++g) {
+            // the following group's descriptor: this item's next, else the next item's first
+            const int gn = g + 1 < it.y ? g + 1 : (q + nw < n ? next.x : -1);
+            if (gn >= 0) prefetch_group(bd.gdesc + gn);
+            acc += spmv_group<T>(load_group(bd.gdesc + g), bd.rmeta, B, u, w, bd.M, lane, gsm[wid]);
         }
         const T sum = warp_sum<T>(acc);
         if (lane == 0 && sum != T(0)) atomicAdd(&dlP[it.z], double(sum));
         it = next;
-        next = after;
-        mine = nmine;
-        mine2 = nmine2;
     }
 }
 
@@ -799,7 +771,7 @@ int sm_count(const rbf_ctx* ctx) {
 }
 
 TileCg tile_view(rbf_ctx* ctx) { return TileLayout(ctx->T).view(ctx->tcg.as<char>()); }
-WorkLayout work_layout(const rbf_ctx* ctx) { return WorkLayout(ctx->T, ctx->ncl, ctx->M); }
+WorkLayout work_layout(const rbf_ctx* ctx) { return WorkLayout(ctx->T, ctx->ngroup, ctx->M); }
 TileWork work_view(rbf_ctx* ctx) { return work_layout(ctx).view(ctx->twork.as<char>()); }
 
 // Persistent update grid: as many blocks of NT threads as can be resident, at most one per
@@ -826,10 +798,10 @@ void launch_bcg_iteration(rbf_ctx* ctx, const CgVec<T>& v, const TileCg& tc, con
                           int P, cudaStream_t cs) {
     const Binned bd = view(ctx);
     const TileWork tw = work_view(ctx);
-    const int items = div_up(ctx->ncl, cf.chunk) + ctx->T;   // most SpMV items
+    const int items = div_up(ctx->ngroup, cf.chunk) + ctx->T;   // most SpMV items
     const int grid = std::max(1, std::min(cf.bps * sm_count(ctx), div_up(items, kSpmvWarps)));
-    k_bcg_spmv<T><<<grid, kSpmvWarps * 32, 0, cs>>>(bd, ctx->clist.as<int>(), tw.items_s,
-                                                    ctx->bvals.as<T>(), v.u, v.w[P], P, ctx->T, tc);
+    k_bcg_spmv<T><<<grid, kSpmvWarps * 32, 0, cs>>>(bd, tw.items_s, ctx->bvals.as<T>(), v.u,
+                                                    v.w[P], P, ctx->T, tc);
     const int nb = update_grid<T>(ctx, cf.nt);
     switch (cf.nt) {
         case 128: k_bcg_update<T, 128><<<nb, 128, 0, cs>>>(bd, v, tw.items_u, P, tc); break;
@@ -967,7 +939,7 @@ rbf_status autotune_impl(rbf_ctx* ctx, cudaStream_t st) {
     tu.chunk = best.chunk;
     tu.nt = best.nt;
     tu.us_per_iter = best_us;
-    tu.ncl = ctx->ncl;
+    tu.ngroup = ctx->ngroup;
     tu.M = ctx->M;
     tu.nvals = ctx->nvals;
     return RBF_OK;
@@ -979,14 +951,14 @@ template <typename T>
 rbf_status pick_cfg(rbf_ctx* ctx, Cfg* out, cudaStream_t st) {
     const int slot = sizeof(T) == 8 ? 0 : 1;
     const rbf_ctx::TileTuning& tu = ctx->tune[slot];
-    const bool fresh = tu.nt != 0 && tu.ncl == ctx->ncl && tu.M == ctx->M && tu.nvals == ctx->nvals;
+    const bool fresh = tu.nt != 0 && tu.ngroup == ctx->ngroup && tu.M == ctx->M && tu.nvals == ctx->nvals;
     if (!fresh && ctx->autotune && !ctx->no_tune_now &&
         !(ctx->force_bps || ctx->force_chunk || ctx->force_nt)) {
         rbf_status s = autotune_impl<T>(ctx, st);
         if (s != RBF_OK) return s;
     }
     Cfg c = default_cfg(ctx, slot);
-    if (ctx->tune[slot].nt != 0 && ctx->tune[slot].ncl == ctx->ncl && ctx->tune[slot].M == ctx->M &&
+    if (ctx->tune[slot].nt != 0 && ctx->tune[slot].ngroup == ctx->ngroup && ctx->tune[slot].M == ctx->M &&
         ctx->tune[slot].nvals == ctx->nvals) {
         if (!ctx->force_bps) c.bps = ctx->tune[slot].spmv_bps;
         if (!ctx->force_chunk) c.chunk = ctx->tune[slot].chunk;
@@ -1002,10 +974,10 @@ template <typename T>
 rbf_status bcg_graph(rbf_ctx* ctx, const Cfg& cf, cudaGraphExec_t* out) {
     rbf_ctx::TileGraph& sg = ctx->bt_graph[sizeof(T) == 8 ? 0 : 1];
     const CgVec<T> v = cg_vectors<T>(ctx);
-    const void* key[13] = {ctx->twork.p, ctx->bvals.p, v.x, v.dinv, v.bjinv, ctx->tcg.p, ctx->clist.p,
-                           ctx->cdesc.p, ctx->crow.p, ctx->bjoff.p, ctx->cstart.p,
-                           ctx->seg.p, ctx->rboff.p};
-    bool hit = sg.exec && sg.T == ctx->T && sg.M == ctx->M && sg.ncl == ctx->ncl &&
+    const void* key[13] = {ctx->twork.p, ctx->bvals.p, v.x, v.dinv, v.bjinv, ctx->tcg.p, ctx->gdesc.p,
+                           ctx->rmeta.p, ctx->crow.p, ctx->bjoff.p, ctx->cstart.p, nullptr,
+                           nullptr};
+    bool hit = sg.exec && sg.T == ctx->T && sg.M == ctx->M && sg.ngroup == ctx->ngroup &&
                sg.bps == cf.bps && sg.chunk == cf.chunk && sg.nt == cf.nt;
     for (int k = 0; k < 13 && hit; ++k) hit = sg.key[k] == key[k];
     if (hit) {
@@ -1049,7 +1021,7 @@ rbf_status bcg_graph(rbf_ctx* ctx, const Cfg& cf, cudaGraphExec_t* out) {
     }
     sg.T = ctx->T;
     sg.M = ctx->M;
-    sg.ncl = ctx->ncl;
+    sg.ngroup = ctx->ngroup;
     sg.bps = cf.bps;
     sg.chunk = cf.chunk;
     sg.nt = cf.nt;
@@ -1172,33 +1144,27 @@ rbf_status tiles_scatter(rbf_ctx* ctx, const double* cx, const double* cy, const
     return RBF_OK;
 }
 
-// List of the cells that hold at least one centre (the batched SpMV's work list); reads the
-// count back (the caller synchronises later).
-rbf_status tiles_cell_list(rbf_ctx* ctx, cudaStream_t st) {
-    const int nc = ctx->g.ncell;
+// Centres scattered again after their rank within the cell has changed (x order).
+rbf_status tiles_scatter_centres(rbf_ctx* ctx, const double* cx, const double* cy, cudaStream_t st) {
+    const dim3 grid(8, ctx->T);
+    k_tile_scatter<<<grid, 256, 0, st>>>(ctx->tdesc.as<TileDev>(), 0, cx, cy, nullptr, ctx->g,
+                                         ctx->ckey.as<int>(), ctx->crank.as<int>(),
+                                         ctx->cstart.as<int>(), ctx->cx.as<double>(),
+                                         ctx->cy.as<double>(), nullptr, ctx->cu.as<float>(),
+                                         ctx->cv.as<float>(), ctx->cperm.as<int>());
+    RBF_CUDA_TRY(cudaGetLastError());
+    return RBF_OK;
+}
+
+// Each tile's range of row groups (the batched SpMV's work) and of sorted rows, and room for
+// the work lists; the row groups must be described (gdesc) first.
+rbf_status tiles_group_ranges(rbf_ctx* ctx, cudaStream_t st) {
     rbf_status s;
-    // the centre counts and the row-block sizes are no longer needed: reuse them for the
-    // flags and their scan
-    int* flag = ctx->ccount.as<int>();
-    if ((s = ensure(ctx, ctx->clist, sizeof(int) * (nc + 1), st)) != RBF_OK) return s;
-    if ((s = ensure(ctx, ctx->rbsize, sizeof(int64_t) * (nc + 1), st)) != RBF_OK) return s;
-    int* pos = ctx->rbsize.as<int>();
-    k_cell_flags<<<div_up(nc, 256), 256, 0, st>>>(nc, ctx->cstart.as<int>(), flag);
-    if ((s = scan_i32(ctx, flag, pos, nc, st)) != RBF_OK) return s;
-    k_cell_compact<<<div_up(nc, 256), 256, 0, st>>>(nc, ctx->cstart.as<int>(), pos,
-                                                    ctx->clist.as<int>());
-    ctx->launches += 2;
-    int* hp = static_cast<int*>(ctx->hpinned) + 64;
-    RBF_CUDA_TRY(cudaMemcpyAsync(hp, pos + nc, sizeof(int), cudaMemcpyDeviceToHost, st));
-    RBF_CUDA_TRY(cudaStreamSynchronize(st));
-    ctx->ncl = *hp;
-    // each tile's cells in the list and rows in the sorted order, and room for the work lists
     const WorkLayout L = work_layout(ctx);
     if ((s = ensure(ctx, ctx->twork, L.total, st)) != RBF_OK) return s;
     RBF_CUDA_TRY(cudaMemsetAsync(ctx->twork.p, 0, L.ranges_end, st));
-    k_tile_ranges<<<std::max(1, div_up(std::max(ctx->ncl, ctx->M), 256)), 256, 0, st>>>(
-        ctx->clist.as<int>(), ctx->ncl, ctx->rowtile.as<int>(), ctx->g.gx, ctx->crow.as<int4>(),
-        ctx->M, work_view(ctx));
+    k_tile_ranges<<<std::max(1, div_up(std::max(ctx->ngroup, ctx->M), 256)), 256, 0, st>>>(
+        ctx->gdesc.as<GroupDesc>(), ctx->ngroup, ctx->crow.as<int4>(), ctx->M, work_view(ctx));
     ctx->launches += 1;
     RBF_CUDA_TRY(cudaGetLastError());
     return RBF_OK;
@@ -1210,7 +1176,7 @@ void tiles_release(rbf_ctx* ctx) {
             cudaGraphExecDestroy(sg.exec);
             sg.exec = nullptr;
         }
-    rbf_buf* bufs[] = {&ctx->tdesc, &ctx->rowtile, &ctx->clist, &ctx->tcg, &ctx->twork,
+    rbf_buf* bufs[] = {&ctx->tdesc, &ctx->rowtile, &ctx->tcg, &ctx->twork,
                        &ctx->tred, &ctx->qoff};
     for (rbf_buf* b : bufs) release(ctx, *b);
     if (ctx->hbt) cudaFreeHost(ctx->hbt);
@@ -1545,11 +1511,10 @@ rbf_status bench_tiles_impl(rbf_ctx* ctx, int reps, bool spmv_only, cudaStream_t
         RBF_CUDA_TRY(cudaMemsetAsync(v.w[0], 0, sizeof(T) * ctx->M, st));
         launch_worklist(ctx, tc, cf, st);
         const Binned bd = view(ctx);
-        const int items = div_up(ctx->ncl, cf.chunk) + ctx->T;
+        const int items = div_up(ctx->ngroup, cf.chunk) + ctx->T;
         const int grid = std::max(1, std::min(cf.bps * sm_count(ctx), div_up(items, kSpmvWarps)));
         for (int k = 0; k < reps; ++k)
-            k_bcg_spmv<T><<<grid, kSpmvWarps * 32, 0, st>>>(bd, ctx->clist.as<int>(),
-                                                            work_view(ctx).items_s,
+            k_bcg_spmv<T><<<grid, kSpmvWarps * 32, 0, st>>>(bd, work_view(ctx).items_s,
                                                             ctx->bvals.as<T>(), v.u, v.w[0], 0,
                                                             ctx->T, tc);
         ctx->launches += reps + 2;

@@ -5,11 +5,17 @@
 // nonzero entry of B = A^T A (Eq. 11-12) lies within 2R, i.e. in the 5x5 cells around
 // either one. The binning is a counting sort (histogram with atomics, device-wide
 // exclusive scan, scatter); afterwards each cell's items are contiguous, so any 1 x k
-// row of cells is one contiguous range of the sorted order.
+// row of cells is one contiguous range of the sorted order. The centres of each cell are
+// then ordered by x (ties by input index), so the centres of a cell row are ordered by x.
 //
-// The same pass sizes the stored upper triangle of B (Section 5 keeps only the
-// upper triangle): the rows of the centres of cell c form a dense m_c x L_c block
-// whose columns are the three contiguous ranges of RowSeg.
+// The same pass lays out the stored upper triangle of B (Section 5 keeps only the upper
+// triangle): for every centre s, the three column ranges of the sorted order its row keeps
+// (see RowMeta: the centres of its own and the next two cell rows that lie within 2R in x of
+// the chord of the 2R disc), found by binary search in x, the row's offset in the value array
+// (a scan of the row lengths), and the row groups the SpMV sweeps (up to kGroupRows
+// consecutive rows of one cell row with the union of their ranges).
+#include <limits.h>
+
 #include "rbf_internal.h"
 
 namespace rbf {
@@ -177,36 +183,69 @@ __global__ void k_scatter_points(const double* __restrict__ x, const double* __r
     }
 }
 
+// Rank of every centre within its cell in (x, input index) order, written to rank[] at the
+// centre's input index (the counting sort's scatter then places the cell's centres in that
+// order). One warp per cell, the cell's keys compared 32 at a time through shuffles. Cells of
+// more than kMaxCellCentres centres are not ranked and raise stats[3].
+constexpr int kMaxCellCentres = 16384;
+__global__ void k_cell_xrank(int ncell, const int* __restrict__ cstart, const double* __restrict__ sx,
+                             const int* __restrict__ perm, int* __restrict__ rank,
+                             int* __restrict__ stats) {
+    const int lane = threadIdx.x & 31;
+    const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (c >= ncell) return;
+    const int cs = cstart[c], m = cstart[c + 1] - cs;
+    if (m <= 1) {
+        if (m == 1 && lane == 0) rank[perm[cs]] = 0;
+        return;
+    }
+    if (m > kMaxCellCentres) {
+        if (lane == 0) atomicOr(&stats[3], 1);
+        return;
+    }
+    for (int d0 = 0; d0 < m; d0 += 32) {
+        const int d = d0 + lane;
+        const double xd = d < m ? sx[cs + d] : 0.0;
+        const int pd = d < m ? perm[cs + d] : 0;
+        int r = 0;
+        for (int e0 = 0; e0 < m; e0 += 32) {
+            const int e = e0 + lane;
+            const double xe = e < m ? sx[cs + e] : 0.0;
+            const int pe = e < m ? perm[cs + e] : 0;
+            const int ne = min(32, m - e0);
+            for (int j = 0; j < ne; ++j) {
+                const double xj = __shfl_sync(0xffffffffu, xe, j);
+                const int pj = __shfl_sync(0xffffffffu, pe, j);
+                r += (xj < xd || (xj == xd && pj < pd)) ? 1 : 0;
+            }
+        }
+        if (d < m) rank[pd] = r;
+    }
+}
+
 // Contiguous sorted-centre range of the cells (xa..xb, row), clipped to the grid.
 __device__ __forceinline__ void cell_row_range(const Grid& g, const int* cstart, int row, int xa,
-                                               int xb, int& s, int& l) {
+                                               int xb, int& s, int& e) {
     xa = max(xa, 0);
     xb = min(xb, g.gx - 1);
     if (row < 0 || row >= g.gy || xa > xb) {
-        s = 0;
-        l = 0;
+        s = e = 0;
         return;
     }
     s = cstart[row * g.gx + xa];
-    l = cstart[row * g.gx + xb + 1] - s;
+    e = cstart[row * g.gx + xb + 1];
 }
 
+// Per cell: the centres' cell records, the size of the cell's inverse diagonal block, the
+// assembly work items of its points, and the largest 3x3 candidate count of a point cell.
 __global__ void k_rows(Grid g, const int* __restrict__ cstart, const int* __restrict__ pstart,
-                       const int* __restrict__ rowtile, RowSeg* __restrict__ seg,
-                       int64_t* __restrict__ rbsize, int64_t* __restrict__ bjsize,
+                       const int* __restrict__ rowtile, int64_t* __restrict__ bjsize,
                        int* __restrict__ wcount, int4* __restrict__ crow, int* __restrict__ stats) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= g.ncell) return;
     const int ix = c % g.gx, iy = c / g.gx;
-    RowSeg sg;
-    cell_row_range(g, cstart, iy, ix, ix + 2, sg.s0, sg.l0);
-    cell_row_range(g, cstart, iy + 1, ix - 2, ix + 2, sg.s1, sg.l1);
-    cell_row_range(g, cstart, iy + 2, ix - 2, ix + 2, sg.s2, sg.l2);
-    sg.lp = (sg.l0 + sg.l1 + sg.l2 + kRowPad - 1) / kRowPad * kRowPad;
-    seg[c] = sg;
     const int cs = cstart[c];
     const int m = cstart[c + 1] - cs;
-    rbsize[c] = int64_t(m) * int64_t(sg.lp);
     const int tile = rowtile ? rowtile[iy] : 0;
     for (int i = 0; i < m; ++i) crow[cs + i] = make_int4(cs, m, c, tile);
     bjsize[c] = m <= kMaxBlock ? int64_t(m) * m : 0;
@@ -215,13 +254,135 @@ __global__ void k_rows(Grid g, const int* __restrict__ cstart, const int* __rest
     if (np > 0) {
         int ncand = 0;
         for (int d = -1; d <= 1; ++d) {
-            int s, l;
-            cell_row_range(g, cstart, iy + d, ix - 1, ix + 1, s, l);
-            ncand += l;
+            int s, e;
+            cell_row_range(g, cstart, iy + d, ix - 1, ix + 1, s, e);
+            ncand += e - s;
         }
         atomicMax(&stats[0], ncand);
         atomicMax(&stats[1], np);
     }
+}
+
+// First index t in [a, b) with x[t] > v (strict) or >= v, over x ordered ascending.
+__device__ __forceinline__ int upper_index(const double* x, int a, int b, double v, bool strict) {
+    while (a < b) {
+        const int mid = (a + b) >> 1;
+        const bool right = strict ? (x[mid] > v) : (x[mid] >= v);
+        if (right) b = mid;
+        else a = mid + 1;
+    }
+    return a;
+}
+
+// Column ranges of row s (RowMeta without its offset) and the row's stored length in pairs.
+// Coordinates are those of the sorted copies: the grid's frame for one system, the tile's
+// frame (units of R_t, R = 1) for a batch; the lower edge of the row's own cell row is taken
+// from the cell-local FP32 coordinate (error ~1e-7 R, far inside the disc margin).
+__global__ void k_row_ranges(Grid g, int M, const int* __restrict__ cstart,
+                             const double* __restrict__ sx, const double* __restrict__ sy,
+                             const float* __restrict__ sv, const int4* __restrict__ crow,
+                             RowMeta* __restrict__ rmeta, int64_t* __restrict__ rsize,
+                             int* __restrict__ stats) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= M) return;
+    const int c = crow[s].z;
+    const int ix = c % g.gx, iy = c / g.gx;
+    const double xs = sx[s], ys = sy[s];
+    const double W = 2.0 * g.R * kDiscMargin;
+    const double ybot = ys - double(sv[s]) * g.R;      // lower edge of the row's cell row
+    int lo[3], hi[3];
+    {   // own cell row: t >= s with x_t < x_s + W, within cells ix .. ix+2
+        int a, e;
+        cell_row_range(g, cstart, iy, ix, ix + 2, a, e);
+        lo[0] = s;
+        hi[0] = max(s + 1, upper_index(sx, s, e, xs + W, false));
+    }
+#pragma unroll
+    for (int k = 1; k <= 2; ++k) {
+        lo[k] = hi[k] = 0;
+        const double dy = fmax(0.0, ybot + k * g.h - ys);
+        if (iy + k >= g.gy || dy >= W) continue;
+        const double w = sqrt(W * W - dy * dy);
+        int a, e;
+        cell_row_range(g, cstart, iy + k, ix - 2, ix + 2, a, e);
+        lo[k] = upper_index(sx, a, e, xs - w, true);
+        hi[k] = upper_index(sx, lo[k], e, xs + w, false);
+    }
+    RowMeta rm;
+    unsigned int len = 0;
+    int tot = 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        int l = lo[k] & ~1, h = (hi[k] + 1) & ~1;
+        if (hi[k] <= lo[k]) l = h = lo[k] & ~1;
+        const int p = (h - l) >> 1;
+        if (p > kMaxSegPairs) atomicOr(&stats[4], 1);
+        len |= unsigned(min(p, kMaxSegPairs)) << (kLenBits * k);
+        tot += p;
+        if (k == 1) rm.lo1 = l;
+        if (k == 2) rm.lo2 = l;
+    }
+    rm.off = 0;
+    rm.len = len;
+    rmeta[s] = rm;
+    rsize[s] = tot;      // in pairs of values
+}
+
+// Offsets of the rows in the value array (in pairs), from the scan of the row lengths.
+__global__ void k_row_off(int M, const int64_t* __restrict__ roff, RowMeta* __restrict__ rmeta,
+                          int* __restrict__ stats) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= M) return;
+    const int64_t o = roff[s];
+    if (o + (1 << (3 * kLenBits)) > (int64_t(1) << 32)) atomicOr(&stats[5], 1);
+    rmeta[s].off = unsigned(o);
+}
+
+// Row groups per cell row: ceil(rows / kGroupRows) of the centres of cell row b.
+__global__ void k_group_count(Grid g, const int* __restrict__ cstart, int* __restrict__ gcount) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= g.gy) return;
+    const int n = cstart[(b + 1) * g.gx] - cstart[b * g.gx];
+    gcount[b] = (n + kGroupRows - 1) / kGroupRows;
+}
+
+// One thread per row group: its rows and the union of their column ranges per segment.
+__global__ void k_groups(Grid g, int ngroup, const int* __restrict__ cstart,
+                         const int* __restrict__ gstart, const RowMeta* __restrict__ rmeta,
+                         GroupDesc* __restrict__ gdesc) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= ngroup) return;
+    int a = 0, b = g.gy;            // cell row of the group: last b with gstart[b] <= q
+    while (b - a > 1) {
+        const int mid = (a + b) >> 1;
+        if (gstart[mid] <= q) a = mid;
+        else b = mid;
+    }
+    const int band = a;
+    const int r0 = cstart[band * g.gx] + (q - gstart[band]) * kGroupRows;
+    const int n = min(kGroupRows, cstart[(band + 1) * g.gx] - r0);
+    int lo[3] = {r0 & ~1, INT_MAX, INT_MAX}, hi[3] = {r0 & ~1, INT_MIN, INT_MIN};
+    for (int i = 0; i < n; ++i) {
+        const RowMeta rm = rmeta[r0 + i];
+        const int l[3] = {(r0 + i) & ~1, rm.lo1, rm.lo2};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const int p = seg_pairs(rm.len, k);
+            if (p == 0) continue;
+            lo[k] = min(lo[k], l[k]);
+            hi[k] = max(hi[k], l[k] + 2 * p);
+        }
+    }
+    GroupDesc d;
+    d.r0 = r0;
+    d.n = n;
+    d.lo0 = lo[0];
+    d.p0 = (hi[0] - lo[0]) >> 1;
+    d.lo1 = hi[1] > lo[1] ? lo[1] : 0;
+    d.p1 = hi[1] > lo[1] ? (hi[1] - lo[1]) >> 1 : 0;
+    d.lo2 = hi[2] > lo[2] ? lo[2] : 0;
+    d.p2 = hi[2] > lo[2] ? (hi[2] - lo[2]) >> 1 : 0;
+    gdesc[q] = d;
 }
 
 __global__ void k_work_fill(int ncell, const int* __restrict__ pstart,
@@ -233,36 +394,7 @@ __global__ void k_work_fill(int ncell, const int* __restrict__ pstart,
     for (int q = p0; q < p1; q += kWorkPoints, ++w) work[w] = make_int4(c, q, min(q + kWorkPoints, p1), 0);
 }
 
-__global__ void k_cell_desc(int ncell, int gx, const int* __restrict__ cstart,
-                            const RowSeg* __restrict__ seg, const int64_t* __restrict__ rboff,
-                            const int* __restrict__ rowtile, CellDesc* __restrict__ out) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= ncell) return;
-    const RowSeg sg = seg[c];
-    CellDesc d;
-    d.cs = cstart[c];
-    d.m = cstart[c + 1] - d.cs;
-    d.lp = sg.lp;
-    d.pad = rowtile ? rowtile[c / gx] : 0;   // tile of the cell (batched systems)
-    d.rboff = rboff[c];
-    d.s0 = sg.s0;
-    d.l0 = sg.l0;
-    d.s1 = sg.s1;
-    d.l1 = sg.l1;
-    d.s2 = sg.s2;
-    d.l2 = sg.l2;
-    out[c] = d;
-}
-
 }  // namespace
-
-void launch_cell_desc(rbf_ctx* ctx, cudaStream_t st) {
-    k_cell_desc<<<div_up(ctx->g.ncell, 256), 256, 0, st>>>(
-        ctx->g.ncell, ctx->g.gx, ctx->cstart.as<int>(), ctx->seg.as<RowSeg>(),
-        ctx->rboff.as<int64_t>(), ctx->T > 0 ? ctx->rowtile.as<int>() : nullptr,
-        ctx->cdesc.as<CellDesc>());
-    ctx->launches += 1;
-}
 
 rbf_status scan_i32(rbf_ctx* ctx, const int* in, int* out, int n, cudaStream_t st) {
     return scan_impl<int, int>(ctx, in, out, n, st);
@@ -296,13 +428,14 @@ rbf_status bin_run(rbf_ctx* ctx, const double* cx, const double* cy, const doubl
     ENS(ph, sizeof(double) * N);
     ENS(pu, sizeof(float) * N);
     ENS(pv, sizeof(float) * N);
-    ENS(seg, sizeof(RowSeg) * nc);
-    ENS(rbsize, sizeof(int64_t) * nc);
-    ENS(rboff, sizeof(int64_t) * (nc + 1));
+    ENS(rmeta, sizeof(RowMeta) * M);
+    ENS(rsize, sizeof(int64_t) * M);
+    ENS(roff, sizeof(int64_t) * (M + 1));
+    ENS(gcount, sizeof(int) * g.gy);
+    ENS(gstart, sizeof(int) * (g.gy + 1));
     ENS(wcount, sizeof(int) * nc);
     ENS(bjsize, sizeof(int64_t) * nc);
     ENS(crow, sizeof(int4) * M);
-    ENS(cdesc, sizeof(CellDesc) * nc);
     ENS(bjoff, sizeof(int64_t) * (nc + 1));
     ENS(wstart, sizeof(int) * (nc + 1));
     ENS(stats, sizeof(int64_t) * 8);
@@ -338,41 +471,72 @@ rbf_status bin_run(rbf_ctx* ctx, const double* cx, const double* cy, const doubl
                                             ctx->ph.as<double>(), ctx->pu.as<float>(),
                                             ctx->pv.as<float>());
     }
+    // order each cell's centres by x, then scatter them again in that order
+    k_cell_xrank<<<div_up(nc, 8), 256, 0, st>>>(nc, ctx->cstart.as<int>(), ctx->cx.as<double>(),
+                                                ctx->cperm.as<int>(), ctx->crank.as<int>(), stats);
+    if (ctx->T > 0) {
+        if ((s = tiles_scatter_centres(ctx, cx, cy, st)) != RBF_OK) return s;
+    } else {
+        k_scatter_centres<<<gbM, T, 0, st>>>(cx, cy, M, g, ctx->ckey.as<int>(),
+                                             ctx->crank.as<int>(), ctx->cstart.as<int>(),
+                                             ctx->cx.as<double>(), ctx->cy.as<double>(),
+                                             ctx->cu.as<float>(), ctx->cv.as<float>(),
+                                             ctx->cperm.as<int>());
+    }
     k_rows<<<div_up(nc, T), T, 0, st>>>(g, ctx->cstart.as<int>(), ctx->pstart.as<int>(),
                                         ctx->T > 0 ? ctx->rowtile.as<int>() : nullptr,
-                                        ctx->seg.as<RowSeg>(), ctx->rbsize.as<int64_t>(),
                                         ctx->bjsize.as<int64_t>(), ctx->wcount.as<int>(),
                                         ctx->crow.as<int4>(), stats);
+    // the stored rows of B: column ranges, offsets, row groups
+    k_row_ranges<<<div_up(M, T), T, 0, st>>>(g, M, ctx->cstart.as<int>(), ctx->cx.as<double>(),
+                                             ctx->cy.as<double>(), ctx->cv.as<float>(),
+                                             ctx->crow.as<int4>(), ctx->rmeta.as<RowMeta>(),
+                                             ctx->rsize.as<int64_t>(), stats);
     RBF_CUDA_TRY(cudaGetLastError());
-    ctx->launches += 5;
-    if ((s = scan_i64(ctx, ctx->rbsize.as<int64_t>(), ctx->rboff.as<int64_t>(), nc, st)) != RBF_OK)
+    ctx->launches += 7;
+    if ((s = scan_i64(ctx, ctx->rsize.as<int64_t>(), ctx->roff.as<int64_t>(), M, st)) != RBF_OK)
         return s;
-    launch_cell_desc(ctx, st);
+    k_row_off<<<div_up(M, T), T, 0, st>>>(M, ctx->roff.as<int64_t>(), ctx->rmeta.as<RowMeta>(), stats);
+    k_group_count<<<div_up(g.gy, T), T, 0, st>>>(g, ctx->cstart.as<int>(), ctx->gcount.as<int>());
+    ctx->launches += 2;
+    if ((s = scan_i32(ctx, ctx->gcount.as<int>(), ctx->gstart.as<int>(), g.gy, st)) != RBF_OK) return s;
     if ((s = scan_i32(ctx, ctx->wcount.as<int>(), ctx->wstart.as<int>(), nc, st)) != RBF_OK) return s;
     if ((s = scan_i64(ctx, ctx->bjsize.as<int64_t>(), ctx->bjoff.as<int64_t>(), nc, st)) != RBF_OK)
         return s;
 
     // read back the sizes the host needs to allocate B and launch the assembly
     int64_t* hp = static_cast<int64_t*>(ctx->hpinned);
-    RBF_CUDA_TRY(cudaMemcpyAsync(&hp[0], ctx->rboff.as<int64_t>() + nc, sizeof(int64_t),
+    RBF_CUDA_TRY(cudaMemcpyAsync(&hp[0], ctx->roff.as<int64_t>() + M, sizeof(int64_t),
                                  cudaMemcpyDeviceToHost, st));
     RBF_CUDA_TRY(cudaMemcpyAsync(&hp[1], ctx->wstart.as<int>() + nc, sizeof(int),
                                  cudaMemcpyDeviceToHost, st));
-    RBF_CUDA_TRY(cudaMemcpyAsync(&hp[2], stats, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
-    RBF_CUDA_TRY(cudaMemcpyAsync(&hp[4], ctx->bjoff.as<int64_t>() + nc, sizeof(int64_t),
+    RBF_CUDA_TRY(cudaMemcpyAsync(&hp[2], stats, 8 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    RBF_CUDA_TRY(cudaMemcpyAsync(&hp[6], ctx->bjoff.as<int64_t>() + nc, sizeof(int64_t),
+                                 cudaMemcpyDeviceToHost, st));
+    RBF_CUDA_TRY(cudaMemcpyAsync(&hp[7], ctx->gstart.as<int>() + g.gy, sizeof(int),
                                  cudaMemcpyDeviceToHost, st));
     RBF_CUDA_TRY(cudaStreamSynchronize(st));
     const int* hs = reinterpret_cast<const int*>(&hp[2]);
-    ctx->nvals = hp[0];
-    ctx->nbj = hp[4];
+    ctx->nvals = 2 * hp[0];
+    ctx->nbj = hp[6];
     ctx->nwork = *reinterpret_cast<const int*>(&hp[1]);
+    ctx->ngroup = *reinterpret_cast<const int*>(&hp[7]);
     ctx->max_cand = hs[0];
     ctx->max_cell_pts = hs[1];
     if (hs[2]) return set_err(ctx, RBF_ERR_ARG, "non-finite coordinate or height");
     if (ctx->max_cand > kMaxCand)
         return set_err(ctx, RBF_ERR_LIMIT,
                        "more than rbf_max_candidates() centres in one 3x3 cell neighbourhood");
-    if (ctx->T > 0 && (s = tiles_cell_list(ctx, st)) != RBF_OK) return s;
+    if (hs[3]) return set_err(ctx, RBF_ERR_LIMIT, "more than 16384 centres in one cell");
+    if (hs[4])
+        return set_err(ctx, RBF_ERR_LIMIT, "more than 2046 centres within 2R of a centre in one cell row");
+    if (hs[5]) return set_err(ctx, RBF_ERR_LIMIT, "stored B larger than 2^33 values");
+    ENS(gdesc, sizeof(GroupDesc) * std::max(ctx->ngroup, 1));
+    k_groups<<<div_up(std::max(ctx->ngroup, 1), T), T, 0, st>>>(
+        g, ctx->ngroup, ctx->cstart.as<int>(), ctx->gstart.as<int>(), ctx->rmeta.as<RowMeta>(),
+        ctx->gdesc.as<GroupDesc>());
+    ctx->launches += 1;
+    if (ctx->T > 0 && (s = tiles_group_ranges(ctx, st)) != RBF_OK) return s;
     ENS(work, sizeof(int4) * std::max(ctx->nwork, 1));
     k_work_fill<<<div_up(nc, T), T, 0, st>>>(nc, ctx->pstart.as<int>(), ctx->wstart.as<int>(),
                                              ctx->work.as<int4>());

@@ -1,6 +1,6 @@
 // Device building blocks of the conjugate-gradient solvers (single system and batched
-// tiles): warp and block reductions, the cell-blocked symmetric SpMV of one cell, and the
-// block-Jacobi preconditioner application.
+// tiles): warp and block reductions, the symmetric SpMV of one row group of the stored upper
+// triangle, and the block-Jacobi preconditioner application.
 #pragma once
 
 #include <type_traits>
@@ -17,11 +17,6 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kItersPerBody = 4;
 // Vectors of the CG workspace: x, u, p, r0, r1, s0, s1, w0, w1.
 constexpr int kCgVecs = 9;
-// Rows of a cell's block whose values one SpMV lane loads together (16-byte loads in flight):
-// 4 suits a B that stays in L2 at three CTAs per SM, 8 an HBM-resident B at two CTAs per SM
-// (measured).
-constexpr int kSpmvGroupL2 = 4;
-constexpr int kSpmvGroupHbm = 8;
 
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
@@ -77,26 +72,9 @@ __device__ __forceinline__ void block_sum_t(const T (&v)[NV], double (&out)[NV])
 template <typename T>
 __device__ __forceinline__ T ldcg(const T* p) { return __ldcg(p); }
 
-__device__ __forceinline__ int colmap(const RowSeg& sg, int k) {
-    return k < sg.l0 ? sg.s0 + k : (k < sg.l0 + sg.l1 ? sg.s1 + (k - sg.l0) : sg.s2 + (k - sg.l0 - sg.l1));
-}
-
-// Four consecutive values of a row (16-byte aligned: rows are padded to kRowPad values).
-__device__ __forceinline__ void load4(const float* p, float (&v)[4]) {
-    const float4 q = __ldg(reinterpret_cast<const float4*>(p));
-    v[0] = q.x;
-    v[1] = q.y;
-    v[2] = q.z;
-    v[3] = q.w;
-}
-__device__ __forceinline__ void load4(const double* p, double (&v)[4]) {
-    const double2 a = __ldg(reinterpret_cast<const double2*>(p));
-    const double2 b = __ldg(reinterpret_cast<const double2*>(p + 2));
-    v[0] = a.x;
-    v[1] = a.y;
-    v[2] = b.x;
-    v[3] = b.y;
-}
+template <typename T> struct Pair;
+template <> struct Pair<float> { using type = float2; };
+template <> struct Pair<double> { using type = double2; };
 
 // Sum v[0..15] over the 32 lanes of a warp so that lane l ends up holding the total of
 // row (l >> 1) & 15: four exchange-and-halve steps (xor 16, 8, 4, 2) and a final xor 1.
@@ -138,120 +116,132 @@ __device__ __forceinline__ T butterfly16(T (&v)[16], int lane) {
     return v[0] + __shfl_xor_sync(kFull, v[0], 1);
 }
 
-// y += B x restricted to the stored upper row block of cell c (warp-cooperative; all 32
-// lanes). Lane l streams columns 4l .. 4l+3 of each row with vector loads; every loaded
-// value B[s][t] feeds both products:
-//   row sums    y[s] += sum_t B[s][t] x[t]   (16 rows in registers, butterfly reduction)
-//   column sums y[t] += sum_s B[s][t] x[s]   for t outside the diagonal block c x c
-//   (the diagonal block is stored in full, so its transposed half is already in the rows)
-// and are added with atomics. Returns this lane's share (in T) of x^T B x over the cell's entries:
-// sum_s x[s] rowsum[s] + sum_t colsum[t] x[t].
-template <typename T, int G>
-__device__ T spmv_cell(const CellDesc& cd, const T* __restrict__ B, const T* x, T* y, int lane) {
-    const int cs = cd.cs, m = cd.m;
-    if (m == 0) return T(0);
-    RowSeg sg;
-    sg.s0 = cd.s0;
-    sg.l0 = cd.l0;
-    sg.s1 = cd.s1;
-    sg.l1 = cd.l1;
-    sg.s2 = cd.s2;
-    sg.l2 = cd.l2;
-    const int L = sg.l0 + sg.l1 + sg.l2, lp = cd.lp;
-    const T* Bc = B + cd.rboff;
-    T dot = T(0);
-    for (int j0 = 0; j0 < m; j0 += 16) {
-        const int mm = min(16, m - j0);
-        const T xs_lane = lane < mm ? ldcg(x + cs + j0 + lane) : T(0);
-        T rp[16];
-#pragma unroll
-        for (int i = 0; i < 16; ++i) rp[i] = T(0);
-        for (int k0 = 0; k0 < L; k0 += 128) {
-            const int kb = k0 + 4 * lane;
-            const bool active = kb < L;
-            int t[4];
-            T xt[4], ca[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                t[q] = kb + q < L ? colmap(sg, kb + q) : -1;
-                xt[q] = t[q] >= 0 ? ldcg(x + t[q]) : T(0);
-                ca[q] = T(0);
-            }
-            // Rows are streamed in groups of G whose loads are all issued before any of them
-            // is used, so each lane keeps G 16-byte loads in flight. Loads are unconditional:
-            // rows past the block's last (i >= mm) re-read row mm-1 and lanes past the row's
-            // end (not active) read the row's start -- both valid addresses -- and contribute
-            // nothing (x_i = 0 for i >= mm, x_t = 0 and no column update when not active).
-            const T* rb = Bc + (long long)j0 * lp + (active ? kb : 0);
-            // With 8-row groups, a last group with at most 4 rows left loads only 4 rows (at
-            // about 9 rows per cell this saves a quarter of the loads; measured on the batched
-            // SpMV, while the 4-row shape is faster without the second code path).
-            auto rows = [&](int g0, auto ng) {
-                constexpr int NG = decltype(ng)::value;
-                T v[NG][4];
-#pragma unroll
-                for (int i = 0; i < NG; ++i)
-                    load4(rb + (long long)min(g0 + i, mm - 1) * lp, v[i]);
-#pragma unroll
-                for (int i = 0; i < NG; ++i) {
-                    const T xi = __shfl_sync(kFull, xs_lane, g0 + i);
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        rp[g0 + i] = fma(v[i][q], xt[q], rp[g0 + i]);
-                        ca[q] = fma(v[i][q], xi, ca[q]);
-                    }
-                }
-            };
-#pragma unroll
-            for (int g0 = 0; g0 < 16; g0 += G) {
-                if (g0 < mm) {                // warp-uniform
-                    if constexpr (G == 8) {
-                        if (mm - g0 <= 4)
-                            rows(g0, std::integral_constant<int, 4>());
-                        else
-                            rows(g0, std::integral_constant<int, 8>());
-                    } else {
-                        rows(g0, std::integral_constant<int, G>());
-                    }
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                if (kb + q >= m && t[q] >= 0 && ca[q] != T(0)) {
-                    atomicAdd(y + t[q], ca[q]);
-                    dot = fma(ca[q], xt[q], dot);
-                }
-            }
-        }
-        const T tot = butterfly16(rp, lane);       // lanes 2r, 2r+1 hold row r
-        const int r = (lane >> 1) & 15;
-        const T xr = __shfl_sync(kFull, xs_lane, r);
-        if ((lane & 1) == 0 && r < mm) {
-            atomicAdd(y + cs + j0 + r, tot);
-            dot = fma(tot, xr, dot);
-        }
-    }
-    return dot;
-}
+static_assert(kGroupRows == 16, "the row reduction is a 16-row butterfly");
 
-// Start moving a cell descriptor (48 bytes, at most two cache lines) into L1 without holding
-// registers for it; a later load_desc of it then hits L1.
-__device__ __forceinline__ void prefetch_desc(const CellDesc* d) {
-    const char* p = reinterpret_cast<const char*>(d);
-    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
-    asm volatile("prefetch.global.L1 [%0];" ::"l"(p + sizeof(CellDesc) - 1));
-}
+// Per row of a group and segment, what a lane needs to find the value of its column t:
+// lo <= t < lo + len, value at B[base + t].
+struct __align__(16) SegSlot {
+    int lo, len;
+    long long base;
+};
+// Shared memory of one warp for spmv_group.
+struct GroupSmem {
+    SegSlot seg[kGroupRows][3];
+};
 
-__device__ __forceinline__ CellDesc load_desc(const CellDesc* d) {
-    CellDesc v;
+__device__ __forceinline__ GroupDesc load_group(const GroupDesc* d) {
+    GroupDesc v;
     const int4* p = reinterpret_cast<const int4*>(d);
     int4* q = reinterpret_cast<int4*>(&v);
     q[0] = __ldg(p);
     q[1] = __ldg(p + 1);
-    q[2] = __ldg(p + 2);
     return v;
 }
 
+// y += B x over the stored rows of one row group (warp-cooperative; all 32 lanes; see
+// RowMeta and GroupDesc). The warp sweeps the union of the rows' column ranges in column
+// pairs, lane l taking pair 32 q + l of the union in pass q; for each of the group's rows the
+// lane loads the row's two values at its columns (one aligned 2-vector load, skipped where
+// the columns are outside the row's own range), and every value B[s][t] feeds both products:
+//   row sums    y[s] += sum_t B[s][t] x[t]   (16 rows in registers, butterfly reduction)
+//   column sums y[t] += sum_s B[s][t] x[s]   (the lane's two columns, summed over the rows)
+// The halved diagonal makes the two sums count it once. Both are added with atomics.
+// Returns this lane's share (in T) of x^T B x: sum_s x[s] rowsum[s] + sum_t colsum[t] x[t].
+template <typename T>
+__device__ T spmv_group(const GroupDesc& gd, const RowMeta* __restrict__ rmeta,
+                        const T* __restrict__ B, const T* x, T* y, int M, int lane,
+                        GroupSmem& sm) {
+    using T2 = typename Pair<T>::type;
+    const int n = gd.n, r0 = gd.r0;
+    __syncwarp();
+    if (lane < kGroupRows) {
+        SegSlot e[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) e[k] = SegSlot{0, 0, 0};
+        if (lane < n) {
+            const int s = r0 + lane;
+            const int4 q = __ldg(reinterpret_cast<const int4*>(rmeta + s));
+            const unsigned int len = unsigned(q.w);
+            const long long off = 2LL * unsigned(q.x);
+            const int l0 = 2 * seg_pairs(len, 0), l1 = 2 * seg_pairs(len, 1);
+            const int l2 = 2 * seg_pairs(len, 2);
+            e[0] = SegSlot{s & ~1, l0, off - (s & ~1)};
+            e[1] = SegSlot{q.y, l1, off + l0 - q.y};
+            e[2] = SegSlot{q.z, l2, off + l0 + l1 - q.z};
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) sm.seg[lane][k] = e[k];
+    }
+    const T xrow = lane < n ? ldcg(x + r0 + lane) : T(0);
+    T xg[kGroupRows];
+#pragma unroll
+    for (int i = 0; i < kGroupRows; ++i) xg[i] = __shfl_sync(kFull, xrow, i);
+    __syncwarp();
+    const int P0 = gd.p0, P1 = gd.p1, PT = gd.p0 + gd.p1 + gd.p2;
+    T rp[kGroupRows];
+#pragma unroll
+    for (int i = 0; i < kGroupRows; ++i) rp[i] = T(0);
+    T dot = T(0);
+    for (int q0 = 0; q0 < PT; q0 += 32) {
+        const int q = q0 + lane;
+        const bool act = q < PT;
+        const int k = q < P0 ? 0 : (q < P0 + P1 ? 1 : 2);
+        const int col = k == 0 ? gd.lo0 + 2 * q
+                               : (k == 1 ? gd.lo1 + 2 * (q - P0) : gd.lo2 + 2 * (q - P0 - P1));
+        const T xt0 = act && col < M ? ldcg(x + col) : T(0);
+        const T xt1 = act && col + 1 < M ? ldcg(x + col + 1) : T(0);
+        // every row's two values first (kGroupRows loads in flight), then the products
+        T2 v[kGroupRows];
+#pragma unroll
+        for (int i = 0; i < kGroupRows; ++i) {
+            const SegSlot e = sm.seg[i][k];
+            const bool ok = act && unsigned(col - e.lo) < unsigned(e.len);
+            v[i] = ok ? __ldg(reinterpret_cast<const T2*>(B + e.base + col)) : T2{T(0), T(0)};
+        }
+        T ca0 = T(0), ca1 = T(0);
+#pragma unroll
+        for (int i = 0; i < kGroupRows; ++i) {
+            rp[i] = fma(v[i].x, xt0, fma(v[i].y, xt1, rp[i]));
+            ca0 = fma(v[i].x, xg[i], ca0);
+            ca1 = fma(v[i].y, xg[i], ca1);
+        }
+        // (a widening slot past the last column holds a zero, but 0 * x can be NaN when x
+        // is not finite: the bounds are tested, not inferred from the sums)
+        if (act && col < M && ca0 != T(0)) {
+            atomicAdd(y + col, ca0);
+            dot = fma(ca0, xt0, dot);
+        }
+        if (act && col + 1 < M && ca1 != T(0)) {
+            atomicAdd(y + col + 1, ca1);
+            dot = fma(ca1, xt1, dot);
+        }
+    }
+    const T tot = butterfly16(rp, lane);       // lanes 2r, 2r+1 hold row r
+    const int r = (lane >> 1) & 15;
+    const T xr = __shfl_sync(kFull, xrow, r);
+    if ((lane & 1) == 0 && r < n) {
+        atomicAdd(y + r0 + r, tot);
+        dot = fma(tot, xr, dot);
+    }
+    return dot;
+}
+
+// Start moving a group descriptor (32 bytes) into L1 without holding registers for it; a
+// later load_group of it then hits L1.
+__device__ __forceinline__ void prefetch_group(const GroupDesc* d) {
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(reinterpret_cast<const char*>(d)));
+}
+
+// Value of B[s][t] (s, t in the same cell; the preconditioner's diagonal blocks) from the
+// stored upper rows; the diagonal is stored halved.
+template <typename T>
+__device__ __forceinline__ T b_same_cell(const RowMeta* __restrict__ rmeta, const T* __restrict__ B,
+                                         int s, int t) {
+    const int a = min(s, t), b = max(s, t);
+    const long long o = 2LL * rmeta[a].off + (b - (a & ~1));
+    const T v = B[o];
+    return a == b ? T(2) * v : v;
+}
 
 template <typename T>
 struct CgVec {

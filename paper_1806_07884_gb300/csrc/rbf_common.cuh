@@ -101,29 +101,63 @@ __device__ __forceinline__ int cell_iy(const Grid& g, double y) {
     return int(f);
 }
 
-// Per-cell description of the stored upper part of B. The rows of B that belong to
-// the centres of cell c = (ix, iy) form one dense row-major block of m_c x L_c values:
-// columns are the centres of the 13 "upper" neighbour cells, i.e. three contiguous
-// ranges of the cell-sorted centre order:
-//   seg 0: cells (ix .. ix+2, iy)        seg 1: cells (ix-2 .. ix+2, iy+1)
-//   seg 2: cells (ix-2 .. ix+2, iy+2)    (clipped to the grid)
-// Any centre pair closer than 2R (the only pairs with B_st != 0) with cell(s) <= cell(t)
-// in key order has t inside one of these ranges of cell(s).
-// Rows are stored with a padded length lp (a multiple of kRowPad, zero-filled) so that every
-// row starts on a 16-byte boundary and can be streamed with vector loads.
-constexpr int kRowPad = 4;
-struct RowSeg {
-    int s0, l0, s1, l1, s2, l2;   // first centre and length of each segment
-    int lp;                       // padded row length (row stride of the block)
+// Stored upper triangle of B (Section 5 keeps only the upper triangle), row by row in the
+// cell-sorted centre order, where a cell's centres are ordered by x (then by input index), so
+// that the centres of one cell row ("band") are ordered by x. Row s keeps B[s][t] for the
+// t >= s that can be nonzero -- centres closer than 2R, i.e. inside the 2R disc around xi_s --
+// as three contiguous column ranges of the sorted order:
+//   seg 0: its own band, t in [s, e0): x_t < x_s + 2R
+//   seg 1: the band above, the centres whose x lies within the half-chord of the 2R disc at
+//          that band's lower edge
+//   seg 2: two bands above, likewise (empty when that edge is 2R or more above xi_s)
+// (a small relative margin widens each range, so FP32 rounding of the assembly's support
+// test can never place an entry outside it). Each range is widened to even column bounds
+// (lo rounded down, hi rounded up) and the three are stored back to back from an even offset,
+// so the value of column t always sits at an offset of the same parity as t: a lane reads
+// the values of a column pair (t, t+1) with one aligned 2-vector load. Slots whose column is
+// outside the row's own range (t < s in seg 0, the widening) hold exact zeros.
+// The diagonal value is stored halved: the SpMV adds every stored value once to the row sum
+// and once to the column sum, so a halved diagonal counts once in y = B x with no special
+// case. Readers of B itself (preconditioner set-up, export) double it.
+struct __align__(16) RowMeta {
+    unsigned int off;   // offset of the row's first stored value (column lo0 = s & ~1), in pairs
+    int lo1, lo2;       // first (even) column of seg 1 and seg 2
+    unsigned int len;   // stored pairs of seg 0 | seg 1 << 10 | seg 2 << 20 (10 bits each)
+};
+constexpr int kLenBits = 10;
+constexpr int kMaxSegPairs = (1 << kLenBits) - 1;
+__host__ __device__ __forceinline__ int seg_pairs(unsigned int len, int k) {
+    return int((len >> (kLenBits * k)) & unsigned(kMaxSegPairs));
+}
+
+// Relative widening of the 2R disc that bounds each row's column ranges.
+constexpr double kDiscMargin = 1.0 + 1e-5;
+
+// Rows of one row group: consecutive rows of one band whose column ranges one warp sweeps
+// together (lanes over the union of the rows' ranges, column sums kept in registers across
+// the rows).
+constexpr int kGroupRows = 16;
+
+// A row group and the union of its rows' column ranges per segment (even bounds, in column
+// pairs), which is what the SpMV's lanes sweep.
+struct __align__(16) GroupDesc {
+    int r0, n;          // first row and number of rows (1 .. kGroupRows)
+    int lo0, p0;        // seg 0 union: columns [lo0, lo0 + 2 p0)
+    int lo1, p1;        // seg 1 union
+    int lo2, p2;        // seg 2 union
 };
 
-// Everything a warp needs to stream the stored row block of one cell, in one 48-byte record
-// (three 16-byte loads) so the SpMV prologue is a single memory round trip.
-struct __align__(16) CellDesc {
-    int cs, m, lp, pad;          // first sorted centre, centre count, padded row length
-    long long rboff;             // offset of the row block in the value array
-    int s0, l0, s1, l1, s2, l2;  // column segments (see RowSeg)
-};
+// Offset of B[s][t] (s <= t, t in band(s) + k) in the value array, or -1 if the row keeps no
+// slot for t.
+__host__ __device__ __forceinline__ long long upper_slot(const RowMeta& rm, int s, int t, int k) {
+    const int lo = k == 0 ? (s & ~1) : (k == 1 ? rm.lo1 : rm.lo2);
+    const int n0 = 2 * seg_pairs(rm.len, 0), n1 = 2 * seg_pairs(rm.len, 1);
+    const int len = 2 * seg_pairs(rm.len, k);
+    const int base = k == 0 ? 0 : (k == 1 ? n0 : n0 + n1);
+    const int d = t - lo;
+    if (d < 0 || d >= len) return -1;
+    return 2LL * rm.off + base + d;
+}
 
 // Views of the context's device buffers passed by value to kernels.
 struct Binned {
@@ -141,11 +175,11 @@ struct Binned {
     const float* pu;        // [N] point coordinates local to its cell, units of R (FP32)
     const float* pv;
     const int* cperm;       // [M] sorted -> caller centre index
-    const RowSeg* seg;      // [ncell]
-    const int64_t* rboff;   // [ncell+1] offset of each cell's row block in the value array
+    const RowMeta* rmeta;   // [M] stored row of B of each sorted centre
+    const GroupDesc* gdesc; // [ngroup] row groups, in row order
+    int ngroup;
     const int64_t* bjoff;   // [ncell+1] offset of each cell's inverse diagonal block
-    const int4* crow;       // [M] {first sorted centre, centre count, cell, 0} of each centre's cell
-    const CellDesc* cdesc;  // [ncell]
+    const int4* crow;       // [M] {first sorted centre, centre count, cell, tile} of each centre's cell
 };
 
 // ---------------------------------------------------------------------------

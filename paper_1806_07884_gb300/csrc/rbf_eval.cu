@@ -70,34 +70,50 @@ __global__ void k_eval_grid(Binned bd, const double* __restrict__ c, int nx, int
     }
 }
 
+// One thread per stored row s: its nonzero values B[s][t], t >= s, as COO triplets in the
+// caller's centre order (the halved diagonal doubled), and b and the support counts.
 template <typename T>
 __global__ void k_export(Binned bd, const T* __restrict__ B, const double* __restrict__ bvec,
                          const int* __restrict__ support, int64_t cap, int32_t* __restrict__ row,
                          int32_t* __restrict__ col, double* __restrict__ val,
                          double* __restrict__ bout, int32_t* __restrict__ sout,
                          unsigned long long* __restrict__ counter) {
-    const int c = blockIdx.x;
-    const int cs = bd.cstart[c], m = bd.cstart[c + 1] - cs;
-    const RowSeg sg = bd.seg[c];
-    const int L = sg.l0 + sg.l1 + sg.l2;
-    const T* Bc = B + bd.rboff[c];
-    for (int e = threadIdx.x; e < m * L; e += blockDim.x) {
-        const int i = e / L, k = e % L;
-        const double v = double(Bc[int64_t(i) * sg.lp + k]);
-        const int t = k < sg.l0 ? sg.s0 + k : (k < sg.l0 + sg.l1 ? sg.s1 + k - sg.l0 : sg.s2 + k - sg.l0 - sg.l1);
-        const int s = cs + i;
-        if (t < s || v == 0.0) continue;   // diagonal block: keep the upper triangle only
-        const unsigned long long pos = atomicAdd(counter, 1ull);
-        if (pos < (unsigned long long)cap) {
-            row[pos] = bd.cperm[s];
-            col[pos] = bd.cperm[t];
-            val[pos] = v;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= bd.M) return;
+    const RowMeta rm = bd.rmeta[s];
+    const int lo[3] = {s & ~1, rm.lo1, rm.lo2};
+    long long o = 2LL * rm.off;
+    for (int k = 0; k < 3; ++k) {
+        const int len = 2 * seg_pairs(rm.len, k);
+        for (int j = 0; j < len; ++j) {
+            const int t = lo[k] + j;
+            double v = double(B[o + j]);
+            if (t < s || v == 0.0) continue;   // widening slots of the row hold zeros
+            if (t == s) v *= 2.0;
+            const unsigned long long pos = atomicAdd(counter, 1ull);
+            if (pos < (unsigned long long)cap) {
+                row[pos] = bd.cperm[s];
+                col[pos] = bd.cperm[t];
+                val[pos] = v;
+            }
         }
+        o += len;
     }
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
-        if (bout) bout[bd.cperm[cs + i]] = bvec[cs + i];
-        if (sout) sout[bd.cperm[cs + i]] = support[cs + i];
-    }
+    if (bout) bout[bd.cperm[s]] = bvec[s];
+    if (sout) sout[bd.cperm[s]] = support[s];
+}
+
+// Number of stored values that are not exactly zero (one warp-level ballot per 32 values).
+template <typename T>
+__global__ void k_count_nonzero(const T* __restrict__ B, int64_t n,
+                                unsigned long long* __restrict__ counter) {
+    unsigned long long c = 0;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n;
+         i += int64_t(gridDim.x) * blockDim.x)
+        c += B[i] != T(0) ? 1ull : 0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(counter, c);
 }
 
 int eval_grid_size(int64_t Q) { return int(std::min<int64_t>((Q + 255) / 256, 152 * 32)); }
@@ -158,14 +174,15 @@ rbf_status export_upper_run(rbf_ctx* ctx, int64_t cap, int32_t* row, int32_t* co
     const Binned bd = view(ctx);
     unsigned long long* counter = reinterpret_cast<unsigned long long*>(ctx->stats.as<char>() + 32);
     RBF_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st));
+    const int nb = div_up(ctx->M, 128);
     if (ctx->prec == RBF_FP64)
-        k_export<double><<<ctx->g.ncell, 256, 0, st>>>(bd, ctx->bvals.as<double>(), ctx->bvec.as<double>(),
-                                                        ctx->support.as<int>(), cap, row, col, val,
-                                                        bvec, support, counter);
+        k_export<double><<<nb, 128, 0, st>>>(bd, ctx->bvals.as<double>(), ctx->bvec.as<double>(),
+                                             ctx->support.as<int>(), cap, row, col, val, bvec,
+                                             support, counter);
     else
-        k_export<float><<<ctx->g.ncell, 256, 0, st>>>(bd, ctx->bvals.as<float>(), ctx->bvec.as<double>(),
-                                                       ctx->support.as<int>(), cap, row, col, val,
-                                                       bvec, support, counter);
+        k_export<float><<<nb, 128, 0, st>>>(bd, ctx->bvals.as<float>(), ctx->bvec.as<double>(),
+                                            ctx->support.as<int>(), cap, row, col, val, bvec,
+                                            support, counter);
     RBF_CUDA_TRY(cudaGetLastError());
     ctx->launches += 1;
     unsigned long long* h = static_cast<unsigned long long*>(ctx->hpinned);
@@ -173,6 +190,30 @@ rbf_status export_upper_run(rbf_ctx* ctx, int64_t cap, int32_t* row, int32_t* co
     RBF_CUDA_TRY(cudaStreamSynchronize(st));
     *nnz = int64_t(*h);
     if (*nnz > cap) return set_err(ctx, RBF_ERR_ARG, "export capacity too small");
+    return RBF_OK;
+}
+
+rbf_status layout_stats_run(rbf_ctx* ctx, rbf_layout_stats* out, cudaStream_t st) {
+    unsigned long long* counter = reinterpret_cast<unsigned long long*>(ctx->stats.as<char>() + 40);
+    RBF_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st));
+    const int nb = int(std::min<int64_t>((ctx->nvals + 255) / 256, 152 * 16));
+    if (ctx->nvals > 0) {
+        if (ctx->prec == RBF_FP64)
+            k_count_nonzero<double><<<nb, 256, 0, st>>>(ctx->bvals.as<double>(), ctx->nvals, counter);
+        else
+            k_count_nonzero<float><<<nb, 256, 0, st>>>(ctx->bvals.as<float>(), ctx->nvals, counter);
+        RBF_CUDA_TRY(cudaGetLastError());
+        ctx->launches += 1;
+    }
+    unsigned long long* h = static_cast<unsigned long long*>(ctx->hpinned);
+    RBF_CUDA_TRY(cudaMemcpyAsync(h, counter, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    RBF_CUDA_TRY(cudaMemcpyAsync(h + 1, ctx->stats.as<int>() + 12, sizeof(int),
+                                 cudaMemcpyDeviceToHost, st));
+    RBF_CUDA_TRY(cudaStreamSynchronize(st));
+    out->stored_values = ctx->nvals;
+    out->nonzeros = int64_t(h[0]);
+    out->row_groups = ctx->ngroup;
+    out->dropped = *reinterpret_cast<const int*>(h + 1);
     return RBF_OK;
 }
 

@@ -29,7 +29,7 @@ struct rbf_ctx {
     int max_cand = 0;          // largest 3x3 neighbourhood centre count
     int max_cell_pts = 0;      // largest points-per-cell count
     int nwork = 0;             // assembly work items
-    int64_t nvals = 0;         // stored B values (upper cell-pair blocks)
+    int64_t nvals = 0;         // stored B values (rows of the upper triangle, see RowMeta)
     bool binned = false;
 
     rbf_buf ccount, pcount;    // [ncell] counts, reused as scratch
@@ -38,12 +38,14 @@ struct rbf_ctx {
     rbf_buf pkey, prank;       // [N]
     rbf_buf cx, cy, cu, cv, cperm;      // [M]
     rbf_buf px, py, ph, pu, pv;         // [N]
-    rbf_buf seg;               // [ncell] RowSeg
-    rbf_buf rbsize, rboff;     // [ncell], [ncell+1] int64
+    rbf_buf rmeta;             // [M] RowMeta: the stored row of B of each sorted centre
+    rbf_buf rsize, roff;       // [M], [M+1] int64: row lengths and offsets (pairs of values)
+    rbf_buf gcount, gstart;    // [gy], [gy+1]: row groups per cell row and their first index
+    rbf_buf gdesc;             // [ngroup] GroupDesc
+    int ngroup = 0;            // row groups of the stored B
     rbf_buf wcount, wstart;    // [ncell], [ncell+1]
     rbf_buf bjsize, bjoff;     // [ncell], [ncell+1] int64: inverse diagonal blocks (m <= 32)
-    rbf_buf crow;              // [M] int4 {cell start, cell count, cell, 0} per sorted centre
-    rbf_buf cdesc;             // [ncell] CellDesc
+    rbf_buf crow;              // [M] int4 {cell start, cell count, cell, tile} per sorted centre
     int64_t nbj = 0;           // values of all inverse diagonal blocks
     rbf_buf work;              // [nwork] int4 {cell, p0, p1, 0}
     rbf_buf scan_tmp;          // block sums of the device scans
@@ -83,7 +85,7 @@ struct rbf_ctx {
     // CG solve graphs (conditional WHILE loop), [0] FP64, [1] FP32, and what they were built for
     struct SolveGraph {
         cudaGraphExec_t exec = nullptr;
-        int ncell = 0, M = 0, gx = 0;
+        int ncell = 0, M = 0, gx = 0, ngroup = 0;
         const void* crow = nullptr;
         const void* key[10] = {};
     };
@@ -95,8 +97,6 @@ struct rbf_ctx {
     std::vector<rbf_tile> tiles;     // the caller's tile descriptors
     rbf_buf tdesc;                   // [T] per-tile placement (device)
     rbf_buf rowtile;                 // [gy] tile owning each cell row, -1 between bands
-    rbf_buf clist;                   // [ncl] cells holding at least one centre
-    int ncl = 0;
     rbf_buf tcg;                     // per-tile CG scalars and results
     rbf_buf twork;                   // per-tile cell and row ranges, CG work lists
     rbf_buf tred;                    // per-tile reductions (norms, pinned counts, scales)
@@ -108,7 +108,7 @@ struct rbf_ctx {
         int spmv_bps = 0, chunk = 0, nt = 0;   // SpMV blocks per SM, cells per SpMV item,
                                                // update block size (0: not chosen yet)
         double us_per_iter = 0.0;              // measured by the autotuner (0: not tuned)
-        int ncl = 0, M = 0;                    // shape it was chosen for
+        int ngroup = 0, M = 0;                 // shape it was chosen for
         int64_t nvals = 0;
     };
     TileTuning tune[2];
@@ -118,7 +118,7 @@ struct rbf_ctx {
     struct TileGraph {
         cudaGraphExec_t exec = nullptr;
         const void* key[13] = {};
-        int T = 0, M = 0, ncl = 0, bps = 0, chunk = 0, nt = 0;
+        int T = 0, M = 0, ngroup = 0, bps = 0, chunk = 0, nt = 0;
     };
     TileGraph bt_graph[2];
 
@@ -147,7 +147,8 @@ rbf_status tiles_count(rbf_ctx* ctx, const double* cx, const double* cy, const d
                        const double* py, const double* h, cudaStream_t st);
 rbf_status tiles_scatter(rbf_ctx* ctx, const double* cx, const double* cy, const double* px,
                          const double* py, const double* h, cudaStream_t st);
-rbf_status tiles_cell_list(rbf_ctx* ctx, cudaStream_t st);
+rbf_status tiles_scatter_centres(rbf_ctx* ctx, const double* cx, const double* cy, cudaStream_t st);
+rbf_status tiles_group_ranges(rbf_ctx* ctx, cudaStream_t st);
 void tiles_release(rbf_ctx* ctx);
 rbf_status bin_tiles_run(rbf_ctx* ctx, const rbf_tile* tiles, int T, const double* cx,
                          const double* cy, int64_t Mtot, const double* px, const double* py,
@@ -188,6 +189,7 @@ rbf_status eval_points_run(rbf_ctx* ctx, const double* c, const double* qx, cons
 rbf_status eval_grid_run(rbf_ctx* ctx, const double* c, int nx, int ny, const double* box,
                          double* f, cudaStream_t st);
 rbf_status diag_sqrt_run(const double* a, double* out, int64_t n, cudaStream_t st);
+rbf_status layout_stats_run(rbf_ctx* ctx, rbf_layout_stats* out, cudaStream_t st);
 rbf_status export_upper_run(rbf_ctx* ctx, int64_t cap, int32_t* row, int32_t* col, double* val,
                             double* bvec, int32_t* support, int64_t* nnz, cudaStream_t st);
 
@@ -201,8 +203,6 @@ void launch_resid32(rbf_ctx* ctx, const double* x64, double* r64, cudaStream_t s
 
 rbf_status bench_spmv_run(rbf_ctx* ctx, int reps, cudaStream_t st);
 rbf_status bench_cg_run(rbf_ctx* ctx, int reps, cudaStream_t st);
-// per-cell SpMV descriptors (after the row-block offsets are known)
-void launch_cell_desc(rbf_ctx* ctx, cudaStream_t st);
 
 // permutation helpers (rbf_solve.cu)
 void launch_gather_sorted(const double* c_orig, const int* cperm, double* c_sorted, int M,

@@ -65,15 +65,14 @@ constexpr int kFWarps = 4;
 constexpr int kFCent = 48;
 
 __global__ void __launch_bounds__(kFWarps * 32)
-    k_features_cell(Binned bd, const int* __restrict__ clist, int ncl,
-                    const double* __restrict__ sigma, float* __restrict__ feat) {
+    k_features_cell(Binned bd, const double* __restrict__ sigma, float* __restrict__ feat) {
     __shared__ int cnt[kFWarps][kFCent][NB];
     __shared__ float hs[kFWarps][kFCent][NB];   // FP32 height sums: native shared atomics
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     const int w = blockIdx.x * kFWarps + wl;
-    if (w >= ncl) return;
     const Grid& g = bd.g;
-    const int cell = clist ? clist[w] : w;
+    if (w >= g.ncell) return;
+    const int cell = w;
     const int cs = bd.cstart[cell], m = bd.cstart[cell + 1] - cs;
     if (m == 0) return;
     const int ix = cell % g.gx, iy = cell / g.gx;
@@ -386,10 +385,9 @@ static rbf_status height_scales(rbf_ctx* ctx, cudaStream_t st) {
 rbf_status features_run(rbf_ctx* ctx, float* feat, double* sigma_out, cudaStream_t st) {
     rbf_status s = height_scales(ctx, st);
     if (s != RBF_OK) return s;
-    // one warp per cell holding centres (the cell list of a batch, else every cell)
-    const int ncl = ctx->T > 0 ? ctx->ncl : ctx->g.ncell;
-    k_features_cell<<<div_up(ncl, kFWarps), kFWarps * 32, 0, st>>>(
-        view(ctx), ctx->T > 0 ? ctx->clist.as<int>() : nullptr, ncl, ctx->sigma.as<double>(), feat);
+    // one warp per cell (cells without centres return at once)
+    k_features_cell<<<div_up(ctx->g.ncell, kFWarps), kFWarps * 32, 0, st>>>(
+        view(ctx), ctx->sigma.as<double>(), feat);
     ctx->launches += 1;
     if (sigma_out)
         RBF_CUDA_TRY(cudaMemcpyAsync(sigma_out, ctx->sigma.p, sizeof(double) * std::max(ctx->T, 1),

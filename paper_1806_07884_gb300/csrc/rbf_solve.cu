@@ -3,14 +3,16 @@
 // cells of the grid: the inverse of each cell's diagonal block B[c, c] (the centres of one
 // cell share most of their support and are the strongest couplings of B).
 //
-// SpMV y = B x over the cell-blocked upper storage (Section 5 keeps only the upper
-// triangle), one warp per cell (persistent warps striding over the cells): the cell's dense
-// m_c x lp_c row block, described by one 48-byte record, is streamed once with
-// 16-byte vector loads, and each value feeds both the row product (16 rows held in
+// SpMV y = B x over the stored upper triangle (Section 5 keeps only the upper triangle), one
+// warp per row group (persistent warps striding over the groups): the rows of a group are up
+// to 16 consecutive centres of one cell row, each storing the three column ranges of the
+// sorted order that can hold its nonzeros (about 1.3 times the true nonzeros, against about
+// twice for dense cell-pair blocks); the warp sweeps the union of the rows' ranges in column
+// pairs with aligned 2-vector loads, and each value feeds both the row product (16 rows held in
 // registers, summed across lanes by a butterfly transpose-reduction) and the transposed
-// product of the lower triangle (column sums added to y with atomics). HBM and L2 see each
-// stored value once per SpMV -- half the bytes of storing both triangles -- and no transposed
-// reads are needed. The same pass yields x^T B x locally.
+// product of the lower triangle (column sums over the group's rows, added to y with atomics).
+// HBM and L2 see each stored value once per SpMV and no transposed reads are needed. The same
+// pass yields x^T B x locally.
 //
 // The CG iteration uses the Chronopoulos-Gear recurrences: one SpMV and one fused pair of
 // reductions per iteration, as two kernels. The SpMV kernel accumulates delta = u^T B u
@@ -89,16 +91,18 @@ __device__ bool last_block_total(double (&v)[NV], double* partial, unsigned int*
     return true;
 }
 
-// Standalone SpMV y += B x (persistent warps striding over the cells; y zeroed by the caller).
+// Standalone SpMV y += B x (persistent warps striding over the row groups; y zeroed by the
+// caller).
 template <typename T>
-__global__ void __launch_bounds__(kSpmvWarps * 32, sizeof(T) == 4 ? 3 : 1)
+__global__ void __launch_bounds__(kSpmvWarps * 32, 2)
     k_spmv(Binned bd, const T* __restrict__ B, const T* __restrict__ x, T* __restrict__ y) {
-    const int lane = threadIdx.x & 31;
+    __shared__ GroupSmem gsm[kSpmvWarps];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int nw = gridDim.x * kSpmvWarps;
-    for (int c = blockIdx.x * kSpmvWarps + (threadIdx.x >> 5); c < bd.g.ncell; c += nw) {
-        // the next cell's descriptor moves into L1 while this cell's rows stream
-        if (c + nw < bd.g.ncell) prefetch_desc(bd.cdesc + c + nw);
-        spmv_cell<T, kSpmvGroupL2>(load_desc(bd.cdesc + c), B, x, y, lane);
+    for (int q = blockIdx.x * kSpmvWarps + wid; q < bd.ngroup; q += nw) {
+        // the next group's descriptor moves into L1 while this group's rows stream
+        if (q + nw < bd.ngroup) prefetch_group(bd.gdesc + q + nw);
+        spmv_group<T>(load_group(bd.gdesc + q), bd.rmeta, B, x, y, bd.M, lane, gsm[wid]);
     }
 }
 
@@ -114,17 +118,18 @@ __global__ void __launch_bounds__(kSpmvWarps * 32, sizeof(T) == 4 ? 3 : 1)
 // wait for the solver's state: after the solve stops (at most kItersPerBody - 1 SpMVs before
 // the loop condition is read) its w and delta go unused, and the next start resets the slots.
 template <typename T>
-__global__ void __launch_bounds__(kSpmvWarps * 32, sizeof(T) == 4 ? 3 : 1)
+__global__ void __launch_bounds__(kSpmvWarps * 32, 2)
     k_cg_spmv(Binned bd, const T* __restrict__ B, const T* __restrict__ u, T* __restrict__ w,
               int P, CgScalars* __restrict__ sc) {
-    const int lane = threadIdx.x & 31;
-    const int gw = blockIdx.x * kSpmvWarps + (threadIdx.x >> 5);
+    __shared__ GroupSmem gsm[kSpmvWarps];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int gw = blockIdx.x * kSpmvWarps + wid;
     const int nw = gridDim.x * kSpmvWarps;
     T d = T(0);
-    for (int c = gw; c < bd.g.ncell; c += nw) {
-        // the next cell's descriptor moves into L1 while this cell's rows stream
-        if (c + nw < bd.g.ncell) prefetch_desc(bd.cdesc + c + nw);
-        d += spmv_cell<T, kSpmvGroupL2>(load_desc(bd.cdesc + c), B, u, w, lane);
+    for (int q = gw; q < bd.ngroup; q += nw) {
+        // the next group's descriptor moves into L1 while this group's rows stream
+        if (q + nw < bd.ngroup) prefetch_group(bd.gdesc + q + nw);
+        d += spmv_group<T>(load_group(bd.gdesc + q), bd.rmeta, B, u, w, bd.M, lane, gsm[wid]);
     }
     d = warp_sum<T>(d);
     if (lane == 0 && d != T(0)) atomicAdd(&sc->acc_delta[P][gw & (kAccSlots - 1)], double(d));
@@ -362,11 +367,9 @@ __global__ void __launch_bounds__(kBjWarps * 32)
     if (c >= bd.g.ncell) return;
     const int cs = bd.cstart[c], m = bd.cstart[c + 1] - cs;
     if (m == 0) return;
-    const int lp = bd.seg[c].lp;
-    const T* Bc = B + bd.rboff[c];
     int np = 0;
     for (int i = lane; i < m; i += 32) {
-        const T d = Bc[int64_t(i) * lp + i];
+        const T d = b_same_cell<T>(bd.rmeta, B, cs + i, cs + i);
         const bool pin = support[cs + i] < min_support || !(d > T(0));
         dinv[cs + i] = pin ? T(0) : T(1) / d;
         np += pin;
@@ -380,7 +383,7 @@ __global__ void __launch_bounds__(kBjWarps * 32)
     for (int e = lane; e < m * m; e += 32) {
         const int i = e / m, j = e - (e / m) * m;
         const bool pin = dinv[cs + i] == T(0) || dinv[cs + j] == T(0);
-        a[i][j] = pin ? (i == j ? 1.0 : 0.0) : double(Bc[int64_t(i) * lp + j]);
+        a[i][j] = pin ? (i == j ? 1.0 : 0.0) : double(b_same_cell<T>(bd.rmeta, B, cs + i, cs + j));
     }
     __syncwarp();
     for (int k = 0; k < m; ++k) {
@@ -476,7 +479,7 @@ int spmv_grid_T(rbf_ctx* ctx) {
     }
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
-    return std::max(1, std::min(per_sm * std::max(sms, 1), div_up(ctx->g.ncell, kSpmvWarps)));
+    return std::max(1, std::min(per_sm * std::max(sms, 1), div_up(ctx->ngroup, kSpmvWarps)));
 }
 int vec_grid(const rbf_ctx* ctx) {
     return std::max(1, std::min(div_up(ctx->M, kVecThreads), 152 * 8));
@@ -501,9 +504,9 @@ rbf_status cg_graph(rbf_ctx* ctx, cudaGraphExec_t* out) {
     rbf_ctx::SolveGraph& sg = ctx->cg_graph[sizeof(T) == 8 ? 0 : 1];
     const CgVec<T> v = cg_vectors<T>(ctx);
     const void* key[10] = {ctx->bvals.p, v.x, v.dinv, v.bjinv, ctx->scal.p, ctx->partial.p,
-                           ctx->cstart.p, ctx->seg.p, ctx->rboff.p, ctx->bjoff.p};
+                           ctx->cstart.p, ctx->rmeta.p, ctx->gdesc.p, ctx->bjoff.p};
     bool hit = sg.exec && sg.ncell == ctx->g.ncell && sg.M == ctx->M && sg.gx == ctx->g.gx &&
-               sg.crow == ctx->crow.p;
+               sg.crow == ctx->crow.p && sg.ngroup == ctx->ngroup;
     for (int k = 0; k < 10 && hit; ++k) hit = sg.key[k] == key[k];
     if (hit) {
         *out = sg.exec;
@@ -546,6 +549,7 @@ rbf_status cg_graph(rbf_ctx* ctx, cudaGraphExec_t* out) {
     sg.M = ctx->M;
     sg.gx = ctx->g.gx;
     sg.crow = ctx->crow.p;
+    sg.ngroup = ctx->ngroup;
     for (int k = 0; k < 10; ++k) sg.key[k] = key[k];
     *out = sg.exec;
     return RBF_OK;

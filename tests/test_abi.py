@@ -88,7 +88,8 @@ def test_struct_layouts_match_the_binding(tmp_path):
     if cc is None:
         pytest.skip("no C compiler")
     from paper_1806_07884_gb300 import _lib
-    mirrors = {"rbf_solve_info": _lib.SolveInfo, "rbf_tile": _lib.Tile, "rbf_tile_info": _lib.TileInfo}
+    mirrors = {"rbf_solve_info": _lib.SolveInfo, "rbf_tile": _lib.Tile, "rbf_tile_info": _lib.TileInfo,
+               "rbf_layout_stats": _lib.LayoutStats}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rbf.h"', "int main(void) {"]
     for cname, py in mirrors.items():
         lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')

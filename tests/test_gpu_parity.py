@@ -87,6 +87,12 @@ def test_assembly_fp64_matches_oracle(case, kind):
     assert err <= 1e-12, err
     assert O.rel_err(b, bref) <= 1e-12
     np.testing.assert_array_equal(sup, O.support_counts(A))   # integer: exact
+    # the stored rows hold every nonzero once (no Gram entry without a slot) and the
+    # nonzero count of the stored values is the oracle's count of the upper triangle
+    st = ctx.layout_stats()
+    assert st["dropped"] == 0
+    assert st["nonzeros"] == len(ref)
+    assert st["stored_values"] >= st["nonzeros"]
     ctx.close()
 
 
