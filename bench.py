@@ -82,6 +82,17 @@ def bspmv_traffic(alg_bytes):
     return int(BSPMV_TRAFFIC["per_alg_byte"] * alg_bytes) if ok else None
 
 
+def spmv_bytes(ctx, M: int, vb: int):
+    """Bytes of one SpMV y = B x: the algorithmic bytes of the method (each nonzero of the
+    upper triangle of B once, plus three vectors of length M: x read, y read and written) and
+    the bytes the library's layout streams (every stored value, 16 B of row description per
+    row, 32 B per row group, the same vectors)."""
+    st = ctx.layout_stats()
+    alg = st["nonzeros"] * vb + 3 * M * vb
+    stored = st["stored_values"] * vb + 16 * M + 32 * st["row_groups"] + 3 * M * vb
+    return alg, stored, st
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -411,13 +422,15 @@ def bench_batched(args, rank, dev, stream, flush, hbm, peak_source):
     s1.record(stream)
     torch.cuda.synchronize()
     spmv_ms = s0.elapsed_time(s1) / 30
-    spmv_bytes = lay["nvals"] * vb + 3 * Mtot * vb
-    ach = spmv_bytes / (spmv_ms * 1e-3) / 1e9
+    alg, stored, lst = spmv_bytes(ctx, Mtot, vb)
+    ach = alg / (spmv_ms * 1e-3) / 1e9
     roof = {"bound": "hbm", "kernel": f"k_bcg_spmv<{'float' if vb == 4 else 'double'}>",
             "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s", "frac": round(ach / hbm, 4),
-            "traffic": bspmv_traffic(spmv_bytes), "traffic_note": "scaled from a 128-tile capture",
-            "algorithmic_bytes": spmv_bytes, "launch_ms": round(spmv_ms, 5),
-            "peak_source": peak_source}
+            "traffic": bspmv_traffic(alg), "traffic_note": "scaled from a 128-tile capture",
+            "algorithmic_bytes": alg, "stored_bytes": stored,
+            "stored_over_algorithmic": round(stored / alg, 4),
+            "upper_nonzeros": lst["nonzeros"], "stored_values": lst["stored_values"],
+            "launch_ms": round(spmv_ms, 5), "peak_source": peak_source}
     out = {"workload": f"{args.tiles} tiles, N log-uniform in [2000, 200000], M = N/10, "
                        f"Wendland phi_3,1, K=30, sum N = {Ntot}, sum M = {Mtot}",
            "value": Ntot / (ms * 1e-3), "unit": "points/s", "ms_per_step": round(ms, 3),
@@ -518,7 +531,7 @@ def bench_bigdata(args, rank, dev, stream, flush, hbm, peak_source):
     # roofline of the solver's SpMV (B streamed from HBM at this size), on its stream
     lay = ctx.layout()
     vb = lay["value_bytes"]
-    spmv_bytes = lay["nvals"] * vb + 3 * M * vb + lay["gx"] * lay["gy"] * 36
+    alg, stored, lst = spmv_bytes(ctx, M, vb)
     ctx.bench_spmv(5)
     s0 = torch.cuda.Event(enable_timing=True)
     s1 = torch.cuda.Event(enable_timing=True)
@@ -527,12 +540,14 @@ def bench_bigdata(args, rank, dev, stream, flush, hbm, peak_source):
     s1.record(stream)
     torch.cuda.synchronize()
     spmv_ms = s0.elapsed_time(s1) / 50
-    ach = spmv_bytes / (spmv_ms * 1e-3) / 1e9
+    ach = alg / (spmv_ms * 1e-3) / 1e9
     roof = {"bound": "hbm", "kernel": f"k_spmv<{'float' if vb == 4 else 'double'}>",
             "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s", "frac": round(ach / hbm, 4),
-            "traffic": big_spmv_traffic(spmv_bytes), "traffic_note": BIG_SPMV_TRAFFIC["note"],
-            "algorithmic_bytes": spmv_bytes, "launch_ms": round(spmv_ms, 5),
-            "peak_source": peak_source}
+            "traffic": big_spmv_traffic(alg), "traffic_note": BIG_SPMV_TRAFFIC["note"],
+            "algorithmic_bytes": alg, "stored_bytes": stored,
+            "stored_over_algorithmic": round(stored / alg, 4),
+            "upper_nonzeros": lst["nonzeros"], "stored_values": lst["stored_values"],
+            "launch_ms": round(spmv_ms, 5), "peak_source": peak_source}
     out = {"workload": f"big data: {N} points (10:1 density), {M} Halton centres, Wendland "
                        f"phi_3,2, K=30, {n}x{n} eval grid",
            "value": N / (ms * 1e-3), "unit": "points/s", "ms_per_step": round(ms, 3),
@@ -677,8 +692,7 @@ def main():
     # ---- roofline of the dominant kernel: the solver's SpMV, timed on its stream
     lay = ctx.layout()
     vb = lay["value_bytes"]
-    ncell = lay["gx"] * lay["gy"]
-    spmv_bytes = lay["nvals"] * vb + 3 * M * vb + ncell * (4 + 24 + 8)
+    alg, stored, lst = spmv_bytes(ctx, M, vb)
     reps = 200
     ctx.bench_spmv(10)
     s0 = torch.cuda.Event(enable_timing=True)
@@ -695,13 +709,34 @@ def main():
     s1.record(stream)
     torch.cuda.synchronize()
     cg_iter_us = s0.elapsed_time(s1) * 1e3 / 100
-    achieved = spmv_bytes / (spmv_ms * 1e-3) / 1e9
+    achieved = alg / (spmv_ms * 1e-3) / 1e9
+    # L2 ceiling: the terrain's stored B fits in the 126 MB L2, so its SpMV streams from L2;
+    # a plain device copy of a 24 MiB buffer (read + write 48 MiB, resident in L2), timed
+    # like the SpMV, gives the rate L2 sustains for a stream
+    l2a = torch.empty(24 << 20, dtype=torch.uint8, device=dev)
+    l2b = torch.empty_like(l2a)
+    for _ in range(20):
+        l2b.copy_(l2a)
+    s0.record(stream)
+    for _ in range(200):
+        l2b.copy_(l2a)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    l2_gbs = 2 * l2a.numel() / (s0.elapsed_time(s1) * 1e-3 / 200) / 1e9
+    del l2a, l2b
     roofline = {"bound": "hbm", "kernel": f"k_spmv<{'float' if vb == 4 else 'double'}>",
                 "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                 "frac": round(achieved / hbm, 4), "traffic": spmv_traffic(),
-                "algorithmic_bytes": spmv_bytes, "launch_ms": round(spmv_ms, 5),
+                "algorithmic_bytes": alg, "stored_bytes": stored,
+                "stored_over_algorithmic": round(stored / alg, 4),
+                "upper_nonzeros": lst["nonzeros"], "stored_values": lst["stored_values"],
+                "launch_ms": round(spmv_ms, 5),
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
-                "cg_iteration_us_plain_launches": round(cg_iter_us, 2)}
+                "cg_iteration_us_plain_launches": round(cg_iter_us, 2),
+                "l2": {"peak": round(l2_gbs, 1), "unit": "GB/s",
+                       "frac": round(achieved / l2_gbs, 4),
+                       "peak_source": "measured in this run: device copy of 24 MiB, read + write",
+                       "b_fits_in_l2": stored < 100e6}}
 
     # ---- accuracy: this path's surface against a tight FP64 solve of the same workload
     f_fast = fbuf.clone()
