@@ -128,8 +128,8 @@ const char* rbf_last_error(const rbf_ctx* ctx);
  * ranges of the sorted order, one per cell row. Requires M >= 1, N >= 1, R > 0, finite
  * coordinates and heights. Synchronises `stream`.
  * Returns RBF_ERR_LIMIT if some 3x3 cell neighbourhood holds more than
- * rbf_max_candidates() centres, a cell more than 16384 centres, one cell row more than 2046
- * centres within 2R of a centre, or the stored B more than 2^33 values. */
+ * rbf_max_candidates() centres, a cell more than 16384 centres, one cell row more than 4092
+ * centres within 2R of a centre, or the stored B more than 2^34 values. */
 rbf_status rbf_bin(rbf_ctx* ctx, const double* cx, const double* cy, int64_t M,
                    const double* px, const double* py, const double* h, int64_t N,
                    double R, const double* bbox, void* stream);
@@ -171,6 +171,43 @@ rbf_status rbf_eval(rbf_ctx* ctx, const double* c, const double* qx, const doubl
 rbf_status rbf_eval_grid(rbf_ctx* ctx, const double* c, int nx, int ny, const double* box,
                          double* f, void* stream);
 
+/* ---- linear polynomial reproduction (Section 3, Eq. 6-10) ----
+ * The approximant gains a linear polynomial, f(x) = sum_j c_j phi(||x - xi_j|| / R)
+ * + a_x x + a_y y + a_0 (Eq. 6-7), and (c, a_x, a_y, a_0) minimise ||A c + P k - h||_2, row i
+ * of P being (x_i, y_i, 1) (Eq. 8-9): the bordered normal system of Eq. 10,
+ *     [A^T A  A^T P] [c]   [A^T h]
+ *     [P^T A  P^T P] [k] = [P^T h],
+ * solved as one SPD system (least squares: no orthogonality constraint rows). Centres with
+ * fewer than min_support points in their support leave the system (c_j = 0) as in rbf_solve;
+ * the three polynomial unknowns always stay. Single systems only (a batched context returns
+ * RBF_ERR_ARG). */
+
+/* As rbf_assemble, and also A^T P (M x 3), P^T P and P^T h in FP64 (the polynomial handled in
+ * the bounding box's centred, scaled frame, which spans the same functions). Asynchronous. */
+rbf_status rbf_assemble_poly(rbf_ctx* ctx, rbf_kernel kernel, rbf_prec prec, void* stream);
+
+/* Solve Eq. 10 after rbf_assemble_poly: iterative refinement from c = 0, k = 0 whose every
+ * step takes the FP64 residual (A^T e, P^T e), e = h - A c - P k, from the points, and solves
+ * the correction by CG on the bordered matrix in the assembly's precision (FP32 B and
+ * A^T P with FP32 inner tolerance "inner_tol", or FP64), preconditioned by the cells' inverse
+ * diagonal blocks and (P^T P)^-1. A stalled FP32 refinement is finished with an FP64 assembly
+ * (info->promoted). c: DEVICE, M doubles in the caller's centre order (output); k: DEVICE, 3
+ * doubles (a_x, a_y, a_0) in the caller's coordinates (output). tol: on
+ * ||(A^T e, P^T e)||_2 / ||(A^T h, P^T h)||_2 (info->rel_residual). maxit: per inner solve.
+ * Synchronises `stream`. Returns RBF_ERR_ARG if P^T P is singular (collinear points),
+ * RBF_ERR_NOT_CONVERGED / RBF_ERR_BREAKDOWN with c, k holding the last iterate. */
+rbf_status rbf_solve_poly(rbf_ctx* ctx, double* c, double* k, double tol, int maxit,
+                          int min_support, rbf_solve_info* info, void* stream);
+
+/* f(q) = sum_j c_j phi(||q - xi_j|| / R) + a_x q_x + a_y q_y + a_0 (Eq. 6-7) at Q query
+ * points (as rbf_eval); k: DEVICE, 3 doubles. Asynchronous. */
+rbf_status rbf_eval_poly(rbf_ctx* ctx, const double* c, const double* k, const double* qx,
+                         const double* qy, int64_t Q, double* f, void* stream);
+
+/* The same on the node-centred nx x ny grid over box (as rbf_eval_grid). Asynchronous. */
+rbf_status rbf_eval_grid_poly(rbf_ctx* ctx, const double* c, const double* k, int nx, int ny,
+                              const double* box, double* f, void* stream);
+
 /* Solver parameters (HOST call, takes effect at the next rbf_solve):
  *   "inner_tol"        relative tolerance of each FP32 inner solve of RBF_FP32_REFINE, in
  *                      (0, 1); default 1e-3
@@ -200,7 +237,7 @@ typedef struct {
     int64_t stored_values;   /* values the SpMV streams (as rbf_get_layout's nvals) */
     int64_t nonzeros;        /* stored values that are not exactly zero: the nonzeros of the
                                 upper triangle of B, diagonal included (Eq. 11-12) */
-    int64_t row_groups;      /* row groups (up to 16 consecutive rows) the SpMV sweeps */
+    int64_t row_groups;      /* row groups (up to 8 consecutive rows) the SpMV sweeps */
     int64_t dropped;         /* Gram entries of the last assembly that found no slot in their
                                 row: 0 by construction (any other value is a library defect) */
 } rbf_layout_stats;

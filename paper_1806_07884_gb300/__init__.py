@@ -19,8 +19,8 @@ import ctypes as C
 from . import _lib
 from ._lib import KERNELS, PRECS, RBFError
 
-__all__ = ["Context", "fit", "fit_tiles", "pack_tiles", "RBFError", "KERNELS", "PRECS",
-           "max_candidates"]
+__all__ = ["Context", "fit", "fit_poly", "fit_tiles", "pack_tiles", "RBFError", "KERNELS",
+           "PRECS", "max_candidates"]
 
 
 def _torch():
@@ -154,6 +154,54 @@ class Context:
         s = self.lib.rbf_eval_grid(self._h, _dptr(c, "c"), int(nx), int(ny), b, _dptr(f, "f"),
                                    self._stream(stream))
         self._check(s, "rbf_eval_grid")
+        return f
+
+    # -- linear polynomial reproduction (Section 3, Eq. 6-10) ------------------------------
+    def assemble_poly(self, kernel: str = "w31", prec: str = "fp64", stream=None):
+        """Steps (b)+(c) with the polynomial blocks of Eq. 10 (A^T P, P^T P, P^T h)."""
+        s = self.lib.rbf_assemble_poly(self._h, KERNELS[kernel], PRECS[prec], self._stream(stream))
+        self._check(s, "rbf_assemble_poly")
+        self.kernel, self.prec = kernel, prec
+
+    def solve_poly(self, tol: float = 1e-10, maxit: int = 100000, min_support: int = 3,
+                   out=None, kout=None, stream=None, raise_on_fail: bool = True):
+        """Step (d) on the bordered system of Eq. 10: returns (c, k, info), k = (a_x, a_y, a_0)
+        in the caller's coordinates (CUDA float64, length 3)."""
+        torch = _torch()
+        dev = f"cuda:{self.device}"
+        c = out if out is not None else torch.empty(self.M, dtype=torch.float64, device=dev)
+        k = kout if kout is not None else torch.empty(3, dtype=torch.float64, device=dev)
+        info = _lib.SolveInfo()
+        s = self.lib.rbf_solve_poly(self._h, _dptr(c, "c"), _dptr(k, "k"), float(tol), int(maxit),
+                                    int(min_support), C.byref(info), self._stream(stream))
+        d = dict(iterations=info.iterations, refinements=info.refinements,
+                 rel_residual=info.rel_residual, pinned=info.pinned, promoted=info.promoted,
+                 status=s)
+        if info.promoted:
+            self.prec = "fp64"
+        if s != 0 and raise_on_fail:
+            self._check(s, "rbf_solve_poly")
+        return c, k, d
+
+    def eval_poly(self, c, k, qx, qy, out=None, stream=None):
+        """Step (e) with the polynomial at query points."""
+        torch = _torch()
+        Q = int(qx.numel())
+        f = out if out is not None else torch.empty(Q, dtype=torch.float64, device=qx.device)
+        s = self.lib.rbf_eval_poly(self._h, _dptr(c, "c"), _dptr(k, "k"), _dptr(qx, "qx"),
+                                   _dptr(qy, "qy"), Q, _dptr(f, "f"), self._stream(stream))
+        self._check(s, "rbf_eval_poly")
+        return f
+
+    def eval_grid_poly(self, c, k, nx: int, ny: int, box=(0.0, 0.0, 1.0, 1.0), out=None,
+                       stream=None):
+        """Step (e) with the polynomial on the node-centred nx x ny grid; shape (ny, nx)."""
+        torch = _torch()
+        f = out if out is not None else torch.empty((ny, nx), dtype=torch.float64, device=c.device)
+        b = (C.c_double * 4)(*[float(v) for v in box])
+        s = self.lib.rbf_eval_grid_poly(self._h, _dptr(c, "c"), _dptr(k, "k"), int(nx), int(ny),
+                                        b, _dptr(f, "f"), self._stream(stream))
+        self._check(s, "rbf_eval_grid_poly")
         return f
 
     # -- batched tiles --------------------------------------------------------------------
@@ -391,3 +439,24 @@ def fit(points, h, centres, R: float, kernel: str = "w31", prec: str = "fp64",
     c, info = ctx.solve(tol=tol, maxit=maxit, min_support=min_support,
                         c0=None if c0 is None else dev64(c0))
     return c, info, ctx
+
+
+def fit_poly(points, h, centres, R: float, kernel: str = "w31", prec: str = "fp64",
+             bbox=(0.0, 0.0, 1.0, 1.0), tol: float = 1e-10, maxit: int = 200000,
+             min_support: int = 3, ctx: Context | None = None, device: int = 0):
+    """Whole fit with linear polynomial reproduction (Eq. 10). Returns (c, k, info, ctx) with
+    c and k = (a_x, a_y, a_0) on the device."""
+    torch = _torch()
+    dev = f"cuda:{device}"
+
+    def dev64(a):
+        t = a if isinstance(a, torch.Tensor) else torch.as_tensor(a)
+        return t.to(device=dev, dtype=torch.float64, non_blocking=True)
+
+    P, H, Cc = dev64(points), dev64(h), dev64(centres)
+    ctx = ctx or Context(device)
+    ctx.bin(Cc[:, 0].contiguous(), Cc[:, 1].contiguous(), P[:, 0].contiguous(),
+            P[:, 1].contiguous(), H.contiguous(), R, bbox)
+    ctx.assemble_poly(kernel, prec)
+    c, k, info = ctx.solve_poly(tol=tol, maxit=maxit, min_support=min_support)
+    return c, k, info, ctx

@@ -60,6 +60,10 @@ SIGNATURES = {
     "rbf_eval_grid": (_I, [_P, _P, _I, _I, C.POINTER(_D), _P, _P]),
     "rbf_get_layout": (_I, [_P, C.POINTER(_I64), C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)]),
     "rbf_get_layout_stats": (_I, [_P, C.POINTER(LayoutStats), _P]),
+    "rbf_assemble_poly": (_I, [_P, _I, _I, _P]),
+    "rbf_solve_poly": (_I, [_P, _P, _P, _D, _I, _I, C.POINTER(SolveInfo), _P]),
+    "rbf_eval_poly": (_I, [_P, _P, _P, _P, _P, _I64, _P, _P]),
+    "rbf_eval_grid_poly": (_I, [_P, _P, _P, _I, _I, C.POINTER(_D), _P, _P]),
     "rbf_export_upper": (_I, [_P, _I64, _P, _P, _P, _P, _P, C.POINTER(_I64), _P]),
     "rbf_get_launch_count": (_I, [_P, C.POINTER(_I64)]),
     "rbf_set_param": (_I, [_P, C.c_char_p, _D]),

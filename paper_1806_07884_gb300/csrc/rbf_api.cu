@@ -151,7 +151,8 @@ rbf_status rbf_destroy(rbf_ctx* ctx) {
                        &ctx->support, &ctx->x, &ctx->r, &ctx->cgv[0], &ctx->cgv[1],
                        &ctx->dinv, &ctx->dinv32, &ctx->bjinv, &ctx->bjinv32, &ctx->crow,
                        &ctx->partial, &ctx->scal, &ctx->csort, &ctx->sigma, &ctx->feat,
-                       &ctx->mlp_part, &ctx->astore, &ctx->amask, &ctx->woff, &ctx->wsize};
+                       &ctx->mlp_part, &ctx->astore, &ctx->amask, &ctx->woff, &ctx->wsize,
+                       &ctx->pE, &ctx->pE32, &ctx->pdev, &ctx->pepart};
     for (rbf_buf* b : bufs) release(ctx, *b);
     if (ctx->hpinned) cudaFreeHost(ctx->hpinned);
     delete ctx;
@@ -227,6 +228,56 @@ rbf_status rbf_solve(rbf_ctx* ctx, double* c, int use_c0, double tol, int maxit,
     if (ctx->T > 0) return set_err(ctx, RBF_ERR_ARG, "batched context: use rbf_solve_tiles");
     DeviceGuard dg(ctx->device);
     return solve_run(ctx, c, use_c0, tol, maxit, min_support, info, as_stream(stream));
+}
+
+rbf_status rbf_assemble_poly(rbf_ctx* ctx, rbf_kernel kernel, rbf_prec prec, void* stream) {
+    if (!ctx) return RBF_ERR_ARG;
+    if (!ctx->binned) return set_err(ctx, RBF_ERR_ARG, "rbf_assemble_poly before rbf_bin");
+    if (ctx->T > 0) return set_err(ctx, RBF_ERR_ARG, "rbf_assemble_poly on a batched context");
+    if (kernel < RBF_W30 || kernel > RBF_W33) return set_err(ctx, RBF_ERR_ARG, "unknown kernel");
+    if (prec != RBF_FP64 && prec != RBF_FP32_REFINE) return set_err(ctx, RBF_ERR_ARG, "unknown precision");
+    DeviceGuard dg(ctx->device);
+    ctx->kernel = kernel;
+    ctx->prec = prec;
+    ctx->solved = false;
+    rbf_status s = assemble_run(ctx, kernel, prec, as_stream(stream), true);
+    ctx->assembled = s == RBF_OK;
+    return s;
+}
+
+rbf_status rbf_solve_poly(rbf_ctx* ctx, double* c, double* k, double tol, int maxit,
+                          int min_support, rbf_solve_info* info, void* stream) {
+    if (!ctx) return RBF_ERR_ARG;
+    if (!ctx->assembled || !ctx->poly)
+        return set_err(ctx, RBF_ERR_ARG, "rbf_solve_poly before rbf_assemble_poly");
+    if (!c || !k) return set_err(ctx, RBF_ERR_ARG, "null c or k");
+    if (!(tol >= 0.0) || maxit < 0) return set_err(ctx, RBF_ERR_ARG, "need tol >= 0, maxit >= 0");
+    DeviceGuard dg(ctx->device);
+    return solve_poly_run(ctx, c, k, tol, maxit, min_support, info, as_stream(stream));
+}
+
+rbf_status rbf_eval_poly(rbf_ctx* ctx, const double* c, const double* k, const double* qx,
+                         const double* qy, int64_t Q, double* f, void* stream) {
+    if (!ctx) return RBF_ERR_ARG;
+    if (!ctx->binned || ctx->kernel < 0) return set_err(ctx, RBF_ERR_ARG, "rbf_eval_poly before rbf_assemble");
+    if (ctx->T > 0) return set_err(ctx, RBF_ERR_ARG, "rbf_eval_poly on a batched context");
+    if (Q < 0 || (Q > 0 && (!c || !k || !qx || !qy || !f)))
+        return set_err(ctx, RBF_ERR_ARG, "bad arguments");
+    DeviceGuard dg(ctx->device);
+    return eval_points_poly_run(ctx, c, k, qx, qy, Q, f, as_stream(stream));
+}
+
+rbf_status rbf_eval_grid_poly(rbf_ctx* ctx, const double* c, const double* k, int nx, int ny,
+                              const double* box, double* f, void* stream) {
+    if (!ctx) return RBF_ERR_ARG;
+    if (!ctx->binned || ctx->kernel < 0)
+        return set_err(ctx, RBF_ERR_ARG, "rbf_eval_grid_poly before rbf_assemble");
+    if (ctx->T > 0) return set_err(ctx, RBF_ERR_ARG, "rbf_eval_grid_poly on a batched context");
+    if (nx < 1 || ny < 1 || !c || !k || !box || !f) return set_err(ctx, RBF_ERR_ARG, "bad arguments");
+    for (int j = 0; j < 4; ++j)
+        if (!isfinite(box[j])) return set_err(ctx, RBF_ERR_ARG, "non-finite box");
+    DeviceGuard dg(ctx->device);
+    return eval_grid_run(ctx, c, nx, ny, box, f, as_stream(stream), k);
 }
 
 rbf_status rbf_bin_tiles(rbf_ctx* ctx, const rbf_tile* tiles, int T, const double* cx,

@@ -23,6 +23,26 @@ namespace {
 
 constexpr int kThreads = 256;
 
+// Adds the block-wide sums of v[0..NV-1] into out[] (one FP64 atomic per value, by thread 0).
+template <int NV>
+__device__ __forceinline__ void block_atomic_sum(double (&v)[NV], double* out) {
+    __shared__ double red[NV][kThreads / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        double x = v[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) red[k][w] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        double t = 0.0;
+        for (int j = 0; j < kThreads / 32; ++j) t += red[threadIdx.x][j];
+        if (t != 0.0) atomicAdd(out + threadIdx.x, t);
+    }
+}
+
 // Shared-memory layout of the candidate staging area.
 template <typename CT>
 struct CandSmem {
@@ -315,6 +335,9 @@ __global__ void __launch_bounds__(kThreads) k_assemble(Binned bd, const int4* __
 // ---------------------------------------------------------------------------
 // Matrix-free FP64 normal residual r = A^T (h - A c), optionally with support counts.
 // ---------------------------------------------------------------------------
+// With the polynomial (pa): e_p also subtracts k . (u_p, v_p, 1), r_k = sum_p e_p (u_p, v_p, 1)
+// is added into pa.rk, and (assembly) A^T P into pa.E, P^T P and P^T h into pa.gp. r may be
+// null (only the polynomial sums of the FP64 assembly are wanted).
 template <int KIND>
 __global__ void __launch_bounds__(kThreads) k_residual(Binned bd, const int4* __restrict__ work,
                                                        int npad, const double* __restrict__ c,
@@ -323,10 +346,17 @@ __global__ void __launch_bounds__(kThreads) k_residual(Binned bd, const int4* __
                                                        const long long* __restrict__ woff,
                                                        double* __restrict__ astore,
                                                        const long long* __restrict__ moff,
-                                                       unsigned int* __restrict__ amask) {
+                                                       unsigned int* __restrict__ amask,
+                                                       PolyArgs pa) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ LocalCells lc;
     __shared__ double esm[kSubChunk];
+    __shared__ double usm[kSubChunk], vsm[kSubChunk];
+    const bool poly = pa.k || pa.E || pa.gp || pa.rk;
+    const double pk0 = pa.k ? pa.k[0] : 0.0, pk1 = pa.k ? pa.k[1] : 0.0, pk2 = pa.k ? pa.k[2] : 0.0;
+    double eacc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};   // A^T P of candidates tid, tid + kThreads
+    double gacc[9] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};   // P^T P (6), P^T h (3)
+    double rkacc[3] = {0.0, 0.0, 0.0};
     const int4 wi = work[blockIdx.x];
     const int cell = wi.x, p0 = wi.y, p1 = wi.z;
     if (threadIdx.x == 0) describe_cells(bd, cell, lc);
@@ -364,8 +394,13 @@ __global__ void __launch_bounds__(kThreads) k_residual(Binned bd, const int4* __
     for (int q0 = p0; q0 < p1; q0 += kSubChunk) {
         __syncthreads();
         fill_phi<KIND, double>(bd, cs, n, npad, q0, p1, phi, hsm, support ? cnt : nullptr, wl);
-        __syncthreads();
         const int np = min(kSubChunk, p1 - q0);
+        if (poly && threadIdx.x < kSubChunk) {
+            const int p = q0 + threadIdx.x;
+            usm[threadIdx.x] = threadIdx.x < np ? (bd.px[p] - pa.xc) * pa.sx : 0.0;
+            vsm[threadIdx.x] = threadIdx.x < np ? (bd.py[p] - pa.yc) * pa.sy : 0.0;
+        }
+        __syncthreads();
         if (astore) {
             // Keep the nonzeros of A for later residual passes, per sub-chunk and candidate a: a
             // 32-bit mask of the sub-chunk's points in a's support, and their values in point
@@ -386,31 +421,85 @@ __global__ void __launch_bounds__(kThreads) k_residual(Binned bd, const int4* __
                 msk[a] = m;
             }
         }
-        // e_p = h_p - sum_a Phi[p][a] c_a  (one warp per point)
+        // e_p = h_p - sum_a Phi[p][a] c_a - k . (u_p, v_p, 1)  (one warp per point)
         for (int pp = warp; pp < np; pp += nw) {
             double s = 0.0;
             for (int a = lane; a < n; a += 32) s = fma(phi[pp * npad + a], cs.cval[a], s);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) esm[pp] = hsm[pp] - s;
+            if (lane == 0)
+                esm[pp] = hsm[pp] - s - (pa.k ? fma(pk0, usm[pp], fma(pk1, vsm[pp], pk2)) : 0.0);
         }
         __syncthreads();
-        // r_a += sum_p Phi[p][a] e_p
+        if (poly && threadIdx.x < np) {
+            const double u = usm[threadIdx.x], v = vsm[threadIdx.x], e = esm[threadIdx.x];
+            if (pa.rk) {
+                rkacc[0] = fma(e, u, rkacc[0]);
+                rkacc[1] = fma(e, v, rkacc[1]);
+                rkacc[2] += e;
+            }
+            if (pa.gp) {
+                const double hp = hsm[threadIdx.x];
+                gacc[0] = fma(u, u, gacc[0]);
+                gacc[1] = fma(u, v, gacc[1]);
+                gacc[2] += u;
+                gacc[3] = fma(v, v, gacc[3]);
+                gacc[4] += v;
+                gacc[5] += 1.0;
+                gacc[6] = fma(hp, u, gacc[6]);
+                gacc[7] = fma(hp, v, gacc[7]);
+                gacc[8] += hp;
+            }
+        }
+        // r_a += sum_p Phi[p][a] e_p (and A^T P: E_a += sum_p Phi[p][a] (u_p, v_p, 1))
         for (int pp = 0; pp < np; ++pp) {
             const double e = esm[pp];
-            if (threadIdx.x < n) racc0 = fma(phi[pp * npad + threadIdx.x], e, racc0);
-            if (threadIdx.x + kThreads < n) racc1 = fma(phi[pp * npad + threadIdx.x + kThreads], e, racc1);
+            if (threadIdx.x < n) {
+                const double f = phi[pp * npad + threadIdx.x];
+                racc0 = fma(f, e, racc0);
+                if (pa.E) {
+                    eacc[0] = fma(f, usm[pp], eacc[0]);
+                    eacc[1] = fma(f, vsm[pp], eacc[1]);
+                    eacc[2] += f;
+                }
+            }
+            if (threadIdx.x + kThreads < n) {
+                const double f = phi[pp * npad + threadIdx.x + kThreads];
+                racc1 = fma(f, e, racc1);
+                if (pa.E) {
+                    eacc[3] = fma(f, usm[pp], eacc[3]);
+                    eacc[4] = fma(f, vsm[pp], eacc[4]);
+                    eacc[5] += f;
+                }
+            }
         }
     }
     __syncthreads();
+    const int64_t M = bd.M;
     if (threadIdx.x < n) {
-        if (racc0 != 0.0) atomicAdd(&r[cs.s[threadIdx.x]], racc0);
-        if (support && cnt[threadIdx.x]) atomicAdd(&support[cs.s[threadIdx.x]], cnt[threadIdx.x]);
+        const int sa = cs.s[threadIdx.x];
+        if (r && racc0 != 0.0) atomicAdd(&r[sa], racc0);
+        if (support && cnt[threadIdx.x]) atomicAdd(&support[sa], cnt[threadIdx.x]);
+        if (pa.E)
+            for (int j = 0; j < 3; ++j)
+                if (eacc[j] != 0.0) atomicAdd(&pa.E[j * M + sa], eacc[j]);
     }
     if (threadIdx.x + kThreads < n) {
         const int a = threadIdx.x + kThreads;
-        if (racc1 != 0.0) atomicAdd(&r[cs.s[a]], racc1);
-        if (support && cnt[a]) atomicAdd(&support[cs.s[a]], cnt[a]);
+        const int sa = cs.s[a];
+        if (r && racc1 != 0.0) atomicAdd(&r[sa], racc1);
+        if (support && cnt[a]) atomicAdd(&support[sa], cnt[a]);
+        if (pa.E)
+            for (int j = 0; j < 3; ++j)
+                if (eacc[3 + j] != 0.0) atomicAdd(&pa.E[j * M + sa], eacc[3 + j]);
+    }
+    if (pa.rk) block_atomic_sum<3>(rkacc, pa.rk);
+    if (pa.gp) {
+        __syncthreads();
+        // P^T P is symmetric: the six sums fill the 3 x 3 block, then P^T h
+        double full[12] = {gacc[0], gacc[1], gacc[2], gacc[1], gacc[3], gacc[4],
+                           gacc[2], gacc[4], gacc[5], gacc[6], gacc[7], gacc[8]};
+        block_atomic_sum<12>(full, pa.gp);
     }
 }
 
@@ -425,11 +514,15 @@ __global__ void __launch_bounds__(kThreads) k_residual_stored(Binned bd, const i
                                                               const long long* __restrict__ woff,
                                                               const double* __restrict__ astore,
                                                               const long long* __restrict__ moff,
-                                                              const unsigned int* __restrict__ amask) {
+                                                              const unsigned int* __restrict__ amask,
+                                                              PolyArgs pa) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ LocalCells lc;
     __shared__ double esm[kSubChunk];
     __shared__ double hsm[kSubChunk];
+    __shared__ double usm[kSubChunk], vsm[kSubChunk];
+    const double pk0 = pa.k ? pa.k[0] : 0.0, pk1 = pa.k ? pa.k[1] : 0.0, pk2 = pa.k ? pa.k[2] : 0.0;
+    double rkacc[3] = {0.0, 0.0, 0.0};
     const int4 wi = work[blockIdx.x];
     const int cell = wi.x, p0 = wi.y, p1 = wi.z;
     if (threadIdx.x == 0) describe_cells(bd, cell, lc);
@@ -454,7 +547,13 @@ __global__ void __launch_bounds__(kThreads) k_residual_stored(Binned bd, const i
         const unsigned int* msk = amask + moff[blockIdx.x] + q * n;
         __syncthreads();
         for (int a = threadIdx.x; a < n; a += blockDim.x) smask[a] = __ldcs(msk + a);
-        if (threadIdx.x < np) hsm[threadIdx.x] = bd.ph[q0 + threadIdx.x];
+        if (threadIdx.x < np) {
+            hsm[threadIdx.x] = bd.ph[q0 + threadIdx.x];
+            if (pa.k) {
+                usm[threadIdx.x] = (bd.px[q0 + threadIdx.x] - pa.xc) * pa.sx;
+                vsm[threadIdx.x] = (bd.py[q0 + threadIdx.x] - pa.yc) * pa.sy;
+            }
+        }
         __syncthreads();
         for (int pp = warp; pp < np; pp += nw) {
             const unsigned int below = (1u << pp) - 1u;
@@ -466,9 +565,16 @@ __global__ void __launch_bounds__(kThreads) k_residual_stored(Binned bd, const i
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
-            if (lane == 0) esm[pp] = hsm[pp] - sacc;
+            if (lane == 0)
+                esm[pp] = hsm[pp] - sacc - (pa.k ? fma(pk0, usm[pp], fma(pk1, vsm[pp], pk2)) : 0.0);
         }
         __syncthreads();
+        if (pa.rk && threadIdx.x < np) {
+            const double e = esm[threadIdx.x];
+            rkacc[0] = fma(e, usm[threadIdx.x], rkacc[0]);
+            rkacc[1] = fma(e, vsm[threadIdx.x], rkacc[1]);
+            rkacc[2] += e;
+        }
         for (int a = threadIdx.x; a < n; a += blockDim.x) {
             unsigned int m = smask[a];
             const double* col = vals + (long long)a * kSubChunk;
@@ -481,6 +587,7 @@ __global__ void __launch_bounds__(kThreads) k_residual_stored(Binned bd, const i
     __syncthreads();
     if (threadIdx.x < n && racc0 != 0.0) atomicAdd(&r[sidx[threadIdx.x]], racc0);
     if (threadIdx.x + kThreads < n && racc1 != 0.0) atomicAdd(&r[sidx[threadIdx.x + kThreads]], racc1);
+    if (pa.rk) block_atomic_sum<3>(rkacc, pa.rk);
 }
 
 // Storage of A per work item: its sub-chunks x the candidates of its cell's 3x3 block, 32
@@ -527,7 +634,7 @@ rbf_status launch_assemble(rbf_ctx* ctx, cudaStream_t st, int npad) {
 
 template <int KIND>
 rbf_status launch_residual(rbf_ctx* ctx, const double* c, double* r, bool count, cudaStream_t st,
-                           int npad) {
+                           int npad, const PolyArgs& pa) {
     const size_t sm = asm_smem<double>(npad, true);
     auto kfn = k_residual<KIND>;
     RBF_CUDA_TRY(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
@@ -537,7 +644,7 @@ rbf_status launch_residual(rbf_ctx* ctx, const double* c, double* r, bool count,
                                           store ? ctx->woff.as<long long>() : nullptr,
                                           store ? ctx->astore.as<double>() : nullptr,
                                           store ? ctx->moff_p : nullptr,
-                                          store ? ctx->amask.as<unsigned int>() : nullptr);
+                                          store ? ctx->amask.as<unsigned int>() : nullptr, pa);
     RBF_CUDA_TRY(cudaGetLastError());
     ctx->launches += 1;
     return RBF_OK;
@@ -545,9 +652,52 @@ rbf_status launch_residual(rbf_ctx* ctx, const double* c, double* r, bool count,
 
 }  // namespace
 
-rbf_status assemble_run(rbf_ctx* ctx, int kernel, int prec, cudaStream_t st) {
+PolyArgs poly_args(rbf_ctx* ctx) {
+    PolyArgs pa{};
+    pa.xc = ctx->pxc;
+    pa.yc = ctx->pyc;
+    pa.sx = ctx->psx;
+    pa.sy = ctx->psy;
+    return pa;
+}
+
+namespace {
+// A^T P into E, P^T P and P^T h into gp (zeroed first) with the FP64 pass over the points.
+rbf_status poly_sums(rbf_ctx* ctx, cudaStream_t st, bool also_b) {
+    const int M = ctx->M;
+    rbf_status s;
+    if ((s = ensure(ctx, ctx->pE, sizeof(double) * 3 * size_t(M), st)) != RBF_OK) return s;
+    if ((s = ensure(ctx, ctx->pE32, sizeof(float) * 3 * size_t(M), st)) != RBF_OK) return s;
+    if ((s = ensure(ctx, ctx->pdev, sizeof(PolyDev), st)) != RBF_OK) return s;
+    RBF_CUDA_TRY(cudaMemsetAsync(ctx->pE.p, 0, sizeof(double) * 3 * size_t(M), st));
+    RBF_CUDA_TRY(cudaMemsetAsync(ctx->pdev.p, 0, sizeof(PolyDev), st));
+    PolyArgs pa = poly_args(ctx);
+    pa.E = ctx->pE.as<double>();
+    pa.gp = ctx->pdev.as<PolyDev>()->gp;
+    if (ctx->nwork == 0) return RBF_OK;
+    const int npad = std::max(4, (ctx->max_cand + 3) / 4 * 4);
+    // with also_b the pass is the FP32 assembly's FP64 pass (b, supports, stored A); else only
+    // the polynomial sums (the FP64 assembly has b and the supports already)
+    double* r = also_b ? ctx->bvec.as<double>() : nullptr;
+    switch (ctx->kernel) {
+        case RBF_W30: return launch_residual<0>(ctx, nullptr, r, also_b, st, npad, pa);
+        case RBF_W31: return launch_residual<1>(ctx, nullptr, r, also_b, st, npad, pa);
+        case RBF_W32: return launch_residual<2>(ctx, nullptr, r, also_b, st, npad, pa);
+        default: return launch_residual<3>(ctx, nullptr, r, also_b, st, npad, pa);
+    }
+}
+
+__global__ void k_to_float(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n;
+         i += int64_t(gridDim.x) * blockDim.x)
+        b[i] = float(a[i]);
+}
+}  // namespace
+
+rbf_status assemble_run(rbf_ctx* ctx, int kernel, int prec, cudaStream_t st, bool with_poly) {
     const int M = ctx->M;
     ctx->astore_ok = false;   // rewritten below by an FP32 assembly
+    ctx->poly = false;
     const size_t vb = prec == RBF_FP64 ? sizeof(double) : sizeof(float);
     rbf_status s;
     if ((s = ensure(ctx, ctx->bvals, vb * std::max<int64_t>(ctx->nvals, 1), st)) != RBF_OK) return s;
@@ -558,7 +708,27 @@ rbf_status assemble_run(rbf_ctx* ctx, int kernel, int prec, cudaStream_t st) {
     RBF_CUDA_TRY(cudaMemsetAsync(ctx->support.p, 0, sizeof(int) * M, st));
     // stats[12]: Gram entries that found no slot in their row (none by construction)
     RBF_CUDA_TRY(cudaMemsetAsync(ctx->stats.as<int>() + 12, 0, sizeof(int), st));
-    if (ctx->nwork == 0) return RBF_OK;
+    if (with_poly) {
+        // the polynomial's frame: the bounding box centred and scaled to [-1, 1]
+        const Grid& g = ctx->g;
+        const double w = g.gx * g.h, hh = g.gy * g.h;
+        ctx->pxc = g.x0 + 0.5 * w;
+        ctx->pyc = g.y0 + 0.5 * hh;
+        ctx->psx = 2.0 / w;
+        ctx->psy = 2.0 / hh;
+    }
+    auto finish_poly = [&](bool also_b) -> rbf_status {
+        if (!with_poly) return RBF_OK;
+        rbf_status ps = poly_sums(ctx, st, also_b);
+        if (ps != RBF_OK) return ps;
+        k_to_float<<<std::min(div_up(3 * int64_t(M), 256), 4096), 256, 0, st>>>(
+            ctx->pE.as<double>(), ctx->pE32.as<float>(), 3 * int64_t(M));
+        ctx->launches += 1;
+        RBF_CUDA_TRY(cudaGetLastError());
+        ctx->poly = true;
+        return RBF_OK;
+    };
+    if (ctx->nwork == 0) return finish_poly(false);
     const int npad = std::max(4, (ctx->max_cand + 3) / 4 * 4);
     if (prec == RBF_FP64) {
         switch (kernel) {
@@ -567,7 +737,8 @@ rbf_status assemble_run(rbf_ctx* ctx, int kernel, int prec, cudaStream_t st) {
             case RBF_W32: s = launch_assemble<2, double>(ctx, st, npad); break;
             default: s = launch_assemble<3, double>(ctx, st, npad); break;
         }
-        return s;
+        if (s != RBF_OK) return s;
+        return finish_poly(false);
     }
     switch (kernel) {
         case RBF_W30: s = launch_assemble<0, float>(ctx, st, npad); break;
@@ -605,13 +776,22 @@ rbf_status assemble_run(rbf_ctx* ctx, int kernel, int prec, cudaStream_t st) {
             ctx->err.clear();   // no room: matrix-free residual
         ctx->moff_p = voff + nw + 1;
     }
-    // b = A^T h and the support counts in FP64: the residual with c = 0
+    // b = A^T h and the support counts in FP64: the residual with c = 0 (with the polynomial,
+    // the same pass also sums A^T P, P^T P and P^T h)
     RBF_CUDA_TRY(cudaMemsetAsync(ctx->bvec.p, 0, sizeof(double) * M, st));
+    if (with_poly) return finish_poly(true);
     return residual_run(ctx, nullptr, ctx->bvec.as<double>(), true, st);
 }
 
 rbf_status residual_run(rbf_ctx* ctx, const double* c_sorted, double* r_sorted, bool count,
-                        cudaStream_t st) {
+                        cudaStream_t st, bool poly) {
+    PolyArgs pa = poly_args(ctx);
+    if (poly) {
+        PolyDev* pd = ctx->pdev.as<PolyDev>();
+        pa.k = pd->k64;
+        pa.rk = pd->rk;
+        RBF_CUDA_TRY(cudaMemsetAsync(pd->rk, 0, 3 * sizeof(double), st));
+    }
     if (ctx->nwork == 0) return RBF_OK;
     const double* c = c_sorted;   // nullptr stands for c = 0, i.e. r = A^T h
     const int npad = std::max(4, (ctx->max_cand + 3) / 4 * 4);
@@ -620,16 +800,16 @@ rbf_status residual_run(rbf_ctx* ctx, const double* c_sorted, double* r_sorted, 
         k_residual_stored<<<ctx->nwork, kThreads, sm, st>>>(view(ctx), ctx->work.as<int4>(), npad, c,
                                                             r_sorted, ctx->woff.as<long long>(),
                                                             ctx->astore.as<double>(), ctx->moff_p,
-                                                            ctx->amask.as<unsigned int>());
+                                                            ctx->amask.as<unsigned int>(), pa);
         RBF_CUDA_TRY(cudaGetLastError());
         ctx->launches += 1;
         return RBF_OK;
     }
     switch (ctx->kernel) {
-        case RBF_W30: return launch_residual<0>(ctx, c, r_sorted, count, st, npad);
-        case RBF_W31: return launch_residual<1>(ctx, c, r_sorted, count, st, npad);
-        case RBF_W32: return launch_residual<2>(ctx, c, r_sorted, count, st, npad);
-        default: return launch_residual<3>(ctx, c, r_sorted, count, st, npad);
+        case RBF_W30: return launch_residual<0>(ctx, c, r_sorted, count, st, npad, pa);
+        case RBF_W31: return launch_residual<1>(ctx, c, r_sorted, count, st, npad, pa);
+        case RBF_W32: return launch_residual<2>(ctx, c, r_sorted, count, st, npad, pa);
+        default: return launch_residual<3>(ctx, c, r_sorted, count, st, npad, pa);
     }
 }
 

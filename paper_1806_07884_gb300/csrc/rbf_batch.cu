@@ -532,7 +532,7 @@ __global__ void __launch_bounds__(kWlThreads)
 // and delta its stopped state leaves unused). Also zeroes the per-tile sums the next update
 // kernel accumulates (parity P ^ 1).
 template <typename T>
-__global__ void __launch_bounds__(kSpmvWarps * 32, 2)
+__global__ void __launch_bounds__(kSpmvWarps * 32, sizeof(T) == 4 ? 3 : 2)
     k_bcg_spmv(Binned bd, const int4* __restrict__ items, const T* __restrict__ B,
                const T* __restrict__ u, T* __restrict__ w, int P, int ntile, TileCg tc) {
     __shared__ GroupSmem gsm[kSpmvWarps];
@@ -549,15 +549,19 @@ __global__ void __launch_bounds__(kSpmvWarps * 32, 2)
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int nw = gridDim.x * kSpmvWarps;
     int q = blockIdx.x * kSpmvWarps + wid;
-    int4 it = q < n ? items[q] : make_int4(0, 0, 0, 0);
+    if (q >= n) return;
+    int4 it = items[q];
+    // the next group's description is loaded while this group's rows stream: this item's
+    // next group, else the next item's first
+    GroupStage<T> cur = stage_group<T>(bd.gdesc, bd.rmeta, u, it.x, lane);
     for (; q < n; q += nw) {
         const int4 next = q + nw < n ? items[q + nw] : make_int4(0, 0, 0, 0);
         T acc = T(0);   // this lane's share of the item's delta (warp sum in T)
         for (int g = it.x; g < it.y; ++g) {
-            // the following group's descriptor: this item's next, else the next item's first
             const int gn = g + 1 < it.y ? g + 1 : (q + nw < n ? next.x : -1);
-            if (gn >= 0) prefetch_group(bd.gdesc + gn);
-            acc += spmv_group<T>(load_group(bd.gdesc + g), bd.rmeta, B, u, w, bd.M, lane, gsm[wid]);
+            const GroupStage<T> nxt = gn >= 0 ? stage_group<T>(bd.gdesc, bd.rmeta, u, gn, lane) : cur;
+            acc += spmv_group<T>(cur, B, u, w, bd.M, lane, gsm[wid]);
+            cur = nxt;
         }
         const T sum = warp_sum<T>(acc);
         if (lane == 0 && sum != T(0)) atomicAdd(&dlP[it.z], double(sum));
@@ -1309,7 +1313,7 @@ rbf_status solve_tiles_run(rbf_ctx* ctx, double* c, int use_c0, double tol, int 
 
     auto fp64_solve = [&](const std::vector<char>& active, const double* x0) -> rbf_status {
         // FP64 batched CG from x0 (sorted order), else from the caller's c0, else from 0
-        ENS(cgv[0], sizeof(double) * kCgVecs * size_t(M));
+        ENS(cgv[0], sizeof(double) * kCgVecs * cg_stride(M));
         const CgVec<double> v = cg_vectors<double>(ctx);
         if (!x0 && use_c0) {
             double* c0s = ctx->r.as<double>();   // free in the FP64 path
@@ -1343,7 +1347,7 @@ rbf_status solve_tiles_run(rbf_ctx* ctx, double* c, int use_c0, double tol, int 
         std::vector<char> all(T, 1);
         if ((s = fp64_solve(all, nullptr)) != RBF_OK) return s;
     } else {
-        ENS(cgv[1], sizeof(float) * kCgVecs * size_t(M));
+        ENS(cgv[1], sizeof(float) * kCgVecs * cg_stride(M));
         ENS(dinv32, sizeof(float) * M);
         ENS(bjinv32, sizeof(float) * std::max<int64_t>(ctx->nbj, 1));
         if ((s = prec_setup_run(ctx, RBF_FP32_REFINE, min_support, npin_d, st)) != RBF_OK) return s;
@@ -1578,14 +1582,14 @@ rbf_status autotune_run(rbf_ctx* ctx, cudaStream_t st) {
     if ((s = ensure(ctx, ctx->scal, 256, st)) != RBF_OK) return s;
     int* npin_d = ctx->scal.as<int>();
     if (ctx->prec == RBF_FP64) {
-        if ((s = ensure(ctx, ctx->cgv[0], sizeof(double) * kCgVecs * size_t(M), st)) != RBF_OK) return s;
+        if ((s = ensure(ctx, ctx->cgv[0], sizeof(double) * kCgVecs * cg_stride(M), st)) != RBF_OK) return s;
         if ((s = ensure(ctx, ctx->dinv, sizeof(double) * M, st)) != RBF_OK) return s;
         if ((s = ensure(ctx, ctx->bjinv, sizeof(double) * std::max<int64_t>(ctx->nbj, 1), st)) != RBF_OK)
             return s;
         if ((s = prec_setup_run(ctx, RBF_FP64, 3, npin_d, st)) != RBF_OK) return s;
         return autotune_impl<double>(ctx, st);
     }
-    if ((s = ensure(ctx, ctx->cgv[1], sizeof(float) * kCgVecs * size_t(M), st)) != RBF_OK) return s;
+    if ((s = ensure(ctx, ctx->cgv[1], sizeof(float) * kCgVecs * cg_stride(M), st)) != RBF_OK) return s;
     if ((s = ensure(ctx, ctx->dinv32, sizeof(float) * M, st)) != RBF_OK) return s;
     if ((s = ensure(ctx, ctx->bjinv32, sizeof(float) * std::max<int64_t>(ctx->nbj, 1), st)) != RBF_OK)
         return s;

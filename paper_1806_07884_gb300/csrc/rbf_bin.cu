@@ -313,22 +313,22 @@ __global__ void k_row_ranges(Grid g, int M, const int* __restrict__ cstart,
     int tot = 0;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        int l = lo[k] & ~1, h = (hi[k] + 1) & ~1;
-        if (hi[k] <= lo[k]) l = h = lo[k] & ~1;
-        const int p = (h - l) >> 1;
-        if (p > kMaxSegPairs) atomicOr(&stats[4], 1);
-        len |= unsigned(min(p, kMaxSegPairs)) << (kLenBits * k);
-        tot += p;
+        int l = lo[k] & ~3, h = (hi[k] + 3) & ~3;
+        if (hi[k] <= lo[k]) l = h = lo[k] & ~3;
+        const int q = (h - l) >> 2;
+        if (q > kMaxSegQuads) atomicOr(&stats[4], 1);
+        len |= unsigned(min(q, kMaxSegQuads)) << (kLenBits * k);
+        tot += q;
         if (k == 1) rm.lo1 = l;
         if (k == 2) rm.lo2 = l;
     }
     rm.off = 0;
     rm.len = len;
     rmeta[s] = rm;
-    rsize[s] = tot;      // in pairs of values
+    rsize[s] = tot;      // in quads of values
 }
 
-// Offsets of the rows in the value array (in pairs), from the scan of the row lengths.
+// Offsets of the rows in the value array (in quads), from the scan of the row lengths.
 __global__ void k_row_off(int M, const int64_t* __restrict__ roff, RowMeta* __restrict__ rmeta,
                           int* __restrict__ stats) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -361,27 +361,27 @@ __global__ void k_groups(Grid g, int ngroup, const int* __restrict__ cstart,
     const int band = a;
     const int r0 = cstart[band * g.gx] + (q - gstart[band]) * kGroupRows;
     const int n = min(kGroupRows, cstart[(band + 1) * g.gx] - r0);
-    int lo[3] = {r0 & ~1, INT_MAX, INT_MAX}, hi[3] = {r0 & ~1, INT_MIN, INT_MIN};
+    int lo[3] = {r0 & ~3, INT_MAX, INT_MAX}, hi[3] = {r0 & ~3, INT_MIN, INT_MIN};
     for (int i = 0; i < n; ++i) {
         const RowMeta rm = rmeta[r0 + i];
-        const int l[3] = {(r0 + i) & ~1, rm.lo1, rm.lo2};
+        const int l[3] = {(r0 + i) & ~3, rm.lo1, rm.lo2};
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            const int p = seg_pairs(rm.len, k);
+            const int p = seg_quads(rm.len, k);
             if (p == 0) continue;
             lo[k] = min(lo[k], l[k]);
-            hi[k] = max(hi[k], l[k] + 2 * p);
+            hi[k] = max(hi[k], l[k] + 4 * p);
         }
     }
     GroupDesc d;
     d.r0 = r0;
     d.n = n;
     d.lo0 = lo[0];
-    d.p0 = (hi[0] - lo[0]) >> 1;
+    d.q0 = (hi[0] - lo[0]) >> 2;
     d.lo1 = hi[1] > lo[1] ? lo[1] : 0;
-    d.p1 = hi[1] > lo[1] ? (hi[1] - lo[1]) >> 1 : 0;
+    d.q1 = hi[1] > lo[1] ? (hi[1] - lo[1]) >> 2 : 0;
     d.lo2 = hi[2] > lo[2] ? lo[2] : 0;
-    d.p2 = hi[2] > lo[2] ? (hi[2] - lo[2]) >> 1 : 0;
+    d.q2 = hi[2] > lo[2] ? (hi[2] - lo[2]) >> 2 : 0;
     gdesc[q] = d;
 }
 
@@ -517,7 +517,7 @@ rbf_status bin_run(rbf_ctx* ctx, const double* cx, const double* cy, const doubl
                                  cudaMemcpyDeviceToHost, st));
     RBF_CUDA_TRY(cudaStreamSynchronize(st));
     const int* hs = reinterpret_cast<const int*>(&hp[2]);
-    ctx->nvals = 2 * hp[0];
+    ctx->nvals = 4 * hp[0];
     ctx->nbj = hp[6];
     ctx->nwork = *reinterpret_cast<const int*>(&hp[1]);
     ctx->ngroup = *reinterpret_cast<const int*>(&hp[7]);
@@ -529,8 +529,8 @@ rbf_status bin_run(rbf_ctx* ctx, const double* cx, const double* cy, const doubl
                        "more than rbf_max_candidates() centres in one 3x3 cell neighbourhood");
     if (hs[3]) return set_err(ctx, RBF_ERR_LIMIT, "more than 16384 centres in one cell");
     if (hs[4])
-        return set_err(ctx, RBF_ERR_LIMIT, "more than 2046 centres within 2R of a centre in one cell row");
-    if (hs[5]) return set_err(ctx, RBF_ERR_LIMIT, "stored B larger than 2^33 values");
+        return set_err(ctx, RBF_ERR_LIMIT, "more than 4092 centres within 2R of a centre in one cell row");
+    if (hs[5]) return set_err(ctx, RBF_ERR_LIMIT, "stored B larger than 2^34 values");
     ENS(gdesc, sizeof(GroupDesc) * std::max(ctx->ngroup, 1));
     k_groups<<<div_up(std::max(ctx->ngroup, 1), T), T, 0, st>>>(
         g, ctx->ngroup, ctx->cstart.as<int>(), ctx->gstart.as<int>(), ctx->rmeta.as<RowMeta>(),

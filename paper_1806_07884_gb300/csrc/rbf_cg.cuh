@@ -17,6 +17,9 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kItersPerBody = 4;
 // Vectors of the CG workspace: x, u, p, r0, r1, s0, s1, w0, w1.
 constexpr int kCgVecs = 9;
+// Stride of the CG workspace vectors: M rounded up to a multiple of 4, so every vector starts
+// on a 16-byte boundary (the SpMV reads x and adds into y four values at a time).
+inline size_t cg_stride(int M) { return (size_t(M) + 3) & ~size_t(3); }
 
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
@@ -72,61 +75,96 @@ __device__ __forceinline__ void block_sum_t(const T (&v)[NV], double (&out)[NV])
 template <typename T>
 __device__ __forceinline__ T ldcg(const T* p) { return __ldcg(p); }
 
-template <typename T> struct Pair;
-template <> struct Pair<float> { using type = float2; };
-template <> struct Pair<double> { using type = double2; };
-
-// Sum v[0..15] over the 32 lanes of a warp so that lane l ends up holding the total of
-// row (l >> 1) & 15: four exchange-and-halve steps (xor 16, 8, 4, 2) and a final xor 1.
+// Sum v[0..7] over the 32 lanes of a warp so that lane l ends up holding the total of
+// row (l >> 2) & 7: three exchange-and-halve steps (xor 16, 8, 4), then xor 2 and xor 1.
 template <typename T>
-__device__ __forceinline__ T butterfly16(T (&v)[16], int lane) {
+__device__ __forceinline__ T butterfly8(T (&v)[8], int lane) {
     {
         const bool hi = lane & 16;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const T send = hi ? v[j] : v[j + 8];
-            const T keep = hi ? v[j + 8] : v[j];
+        for (int j = 0; j < 4; ++j) {
+            const T send = hi ? v[j] : v[j + 4];
+            const T keep = hi ? v[j + 4] : v[j];
             v[j] = keep + __shfl_xor_sync(kFull, send, 16);
         }
     }
     {
         const bool hi = lane & 8;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const T send = hi ? v[j] : v[j + 4];
-            const T keep = hi ? v[j + 4] : v[j];
+        for (int j = 0; j < 2; ++j) {
+            const T send = hi ? v[j] : v[j + 2];
+            const T keep = hi ? v[j + 2] : v[j];
             v[j] = keep + __shfl_xor_sync(kFull, send, 8);
         }
     }
     {
         const bool hi = lane & 4;
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            const T send = hi ? v[j] : v[j + 2];
-            const T keep = hi ? v[j + 2] : v[j];
-            v[j] = keep + __shfl_xor_sync(kFull, send, 4);
-        }
-    }
-    {
-        const bool hi = lane & 2;
         const T send = hi ? v[0] : v[1];
         const T keep = hi ? v[1] : v[0];
-        v[0] = keep + __shfl_xor_sync(kFull, send, 2);
+        v[0] = keep + __shfl_xor_sync(kFull, send, 4);
     }
+    v[0] += __shfl_xor_sync(kFull, v[0], 2);
     return v[0] + __shfl_xor_sync(kFull, v[0], 1);
 }
 
-static_assert(kGroupRows == 16, "the row reduction is a 16-row butterfly");
+static_assert(kGroupRows == 8, "the row reduction is an 8-row butterfly");
 
-// Per row of a group and segment, what a lane needs to find the value of its column t:
-// lo <= t < lo + len, value at B[base + t].
-struct __align__(16) SegSlot {
-    int lo, len;
-    long long base;
-};
-// Shared memory of one warp for spmv_group.
-struct GroupSmem {
-    SegSlot seg[kGroupRows][3];
+// Four consecutive values (16-byte aligned for FP32, 32-byte for FP64).
+struct V4f { float x, y, z, w; };
+struct V4d { double x, y, z, w; };
+template <typename T> struct V4;
+template <> struct V4<float> { using type = V4f; };
+template <> struct V4<double> { using type = V4d; };
+__device__ __forceinline__ V4f ld4(const float* p) {
+    const float4 q = __ldg(reinterpret_cast<const float4*>(p));
+    return V4f{q.x, q.y, q.z, q.w};
+}
+__device__ __forceinline__ V4d ld4(const double* p) {
+    const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+    const double2 b = __ldg(reinterpret_cast<const double2*>(p + 2));
+    return V4d{a.x, a.y, b.x, b.y};
+}
+// x[t..t+3] (t a multiple of 4; the vector is 16-byte aligned), zero past M
+template <typename T>
+__device__ __forceinline__ typename V4<T>::type ldx4(const T* x, int t, int M) {
+    using R = typename V4<T>::type;
+    if (t + 3 < M) {
+        if constexpr (sizeof(T) == 4) {
+            const float4 q = __ldcg(reinterpret_cast<const float4*>(x + t));
+            return R{q.x, q.y, q.z, q.w};
+        } else {
+            const double2 a = __ldcg(reinterpret_cast<const double2*>(x + t));
+            const double2 b = __ldcg(reinterpret_cast<const double2*>(x + t + 2));
+            return R{a.x, a.y, b.x, b.y};
+        }
+    }
+    return R{t < M ? ldcg(x + t) : T(0), t + 1 < M ? ldcg(x + t + 1) : T(0),
+             t + 2 < M ? ldcg(x + t + 2) : T(0), t + 3 < M ? ldcg(x + t + 3) : T(0)};
+}
+// y[t..t+3] += v (t a multiple of 4), nothing past M or for zero parts
+template <typename T>
+__device__ __forceinline__ void atomic_add4(T* y, int t, int M, const typename V4<T>::type& v) {
+    if constexpr (sizeof(T) == 4) {
+        if (t + 3 < M) {
+            if (v.x != 0.0f || v.y != 0.0f || v.z != 0.0f || v.w != 0.0f)
+                atomicAdd(reinterpret_cast<float4*>(y + t), make_float4(v.x, v.y, v.z, v.w));
+            return;
+        }
+    }
+    if (t < M && v.x != T(0)) atomicAdd(y + t, v.x);
+    if (t + 1 < M && v.y != T(0)) atomicAdd(y + t + 1, v.y);
+    if (t + 2 < M && v.z != T(0)) atomicAdd(y + t + 2, v.z);
+    if (t + 3 < M && v.w != T(0)) atomicAdd(y + t + 3, v.w);
+}
+
+// What a warp needs of a row group before its values stream: the group's description, the
+// RowMeta of row lane (lanes < kGroupRows) and x of that row. Loaded one group ahead so the
+// round trip overlaps the previous group.
+template <typename T>
+struct GroupStage {
+    GroupDesc gd;
+    int4 meta;
+    T xrow;
 };
 
 __device__ __forceinline__ GroupDesc load_group(const GroupDesc* d) {
@@ -138,98 +176,115 @@ __device__ __forceinline__ GroupDesc load_group(const GroupDesc* d) {
     return v;
 }
 
+template <typename T>
+__device__ __forceinline__ GroupStage<T> stage_group(const GroupDesc* __restrict__ gdesc,
+                                                     const RowMeta* __restrict__ rmeta,
+                                                     const T* x, int g, int lane) {
+    GroupStage<T> st;
+    st.gd = load_group(gdesc + g);
+    const bool mine = lane < st.gd.n;
+    st.meta = mine ? __ldg(reinterpret_cast<const int4*>(rmeta + st.gd.r0 + lane))
+                   : make_int4(0, 0, 0, 0);
+    st.xrow = mine ? ldcg(x + st.gd.r0 + lane) : T(0);
+    return st;
+}
+
+// Per row of a group and segment, what a lane needs to find the value of its column t:
+// lo <= t < lo + len, value at Bg[rel + t] with Bg the group's first stored value.
+struct SegSlot {
+    int lo, len, rel, pad;
+};
+// Shared memory of one warp for spmv_group.
+struct GroupSmem {
+    SegSlot seg[kGroupRows][3];
+};
+
 // y += B x over the stored rows of one row group (warp-cooperative; all 32 lanes; see
 // RowMeta and GroupDesc). The warp sweeps the union of the rows' column ranges in column
-// pairs, lane l taking pair 32 q + l of the union in pass q; for each of the group's rows the
-// lane loads the row's two values at its columns (one aligned 2-vector load, skipped where
-// the columns are outside the row's own range), and every value B[s][t] feeds both products:
-//   row sums    y[s] += sum_t B[s][t] x[t]   (16 rows in registers, butterfly reduction)
-//   column sums y[t] += sum_s B[s][t] x[s]   (the lane's two columns, summed over the rows)
-// The halved diagonal makes the two sums count it once. Both are added with atomics.
+// quads, lane l taking quad 32 q + l of the union in pass q (one pass for unions up to 128
+// columns); for each of the group's rows the lane loads the row's four values at its columns
+// (one aligned 4-vector load, skipped where the columns are outside the row's own range), and
+// every value B[s][t] feeds both products:
+//   row sums    y[s] += sum_t B[s][t] x[t]   (8 rows in registers, butterfly reduction)
+//   column sums y[t] += sum_s B[s][t] x[s]   (the lane's four columns, summed over the rows,
+//                                             added with one 4-vector atomic)
+// The halved diagonal makes the two sums count it once.
 // Returns this lane's share (in T) of x^T B x: sum_s x[s] rowsum[s] + sum_t colsum[t] x[t].
 template <typename T>
-__device__ T spmv_group(const GroupDesc& gd, const RowMeta* __restrict__ rmeta,
-                        const T* __restrict__ B, const T* x, T* y, int M, int lane,
-                        GroupSmem& sm) {
-    using T2 = typename Pair<T>::type;
+__device__ T spmv_group(const GroupStage<T>& st, const T* __restrict__ B, const T* x, T* y,
+                        int M, int lane, GroupSmem& sm) {
+    using R4 = typename V4<T>::type;
+    const GroupDesc& gd = st.gd;
     const int n = gd.n, r0 = gd.r0;
+    // the group's first stored value (row r0, column r0 & ~3)
+    const long long gbase = 4LL * unsigned(__shfl_sync(kFull, st.meta.x, 0));
     __syncwarp();
     if (lane < kGroupRows) {
         SegSlot e[3];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) e[k] = SegSlot{0, 0, 0};
+        for (int k = 0; k < 3; ++k) e[k] = SegSlot{0, 0, 0, 0};
         if (lane < n) {
             const int s = r0 + lane;
-            const int4 q = __ldg(reinterpret_cast<const int4*>(rmeta + s));
-            const unsigned int len = unsigned(q.w);
-            const long long off = 2LL * unsigned(q.x);
-            const int l0 = 2 * seg_pairs(len, 0), l1 = 2 * seg_pairs(len, 1);
-            const int l2 = 2 * seg_pairs(len, 2);
-            e[0] = SegSlot{s & ~1, l0, off - (s & ~1)};
-            e[1] = SegSlot{q.y, l1, off + l0 - q.y};
-            e[2] = SegSlot{q.z, l2, off + l0 + l1 - q.z};
+            const unsigned int len = unsigned(st.meta.w);
+            const int rel = int(4LL * unsigned(st.meta.x) - gbase);
+            const int l0 = 4 * seg_quads(len, 0), l1 = 4 * seg_quads(len, 1);
+            const int l2 = 4 * seg_quads(len, 2);
+            e[0] = SegSlot{s & ~3, l0, rel - (s & ~3), 0};
+            e[1] = SegSlot{st.meta.y, l1, rel + l0 - st.meta.y, 0};
+            e[2] = SegSlot{st.meta.z, l2, rel + l0 + l1 - st.meta.z, 0};
         }
 #pragma unroll
         for (int k = 0; k < 3; ++k) sm.seg[lane][k] = e[k];
     }
-    const T xrow = lane < n ? ldcg(x + r0 + lane) : T(0);
     T xg[kGroupRows];
 #pragma unroll
-    for (int i = 0; i < kGroupRows; ++i) xg[i] = __shfl_sync(kFull, xrow, i);
+    for (int i = 0; i < kGroupRows; ++i) xg[i] = __shfl_sync(kFull, st.xrow, i);
     __syncwarp();
-    const int P0 = gd.p0, P1 = gd.p1, PT = gd.p0 + gd.p1 + gd.p2;
+    const T* Bg = B + gbase;
+    const int Q0 = gd.q0, Q1 = gd.q1, QT = gd.q0 + gd.q1 + gd.q2;
     T rp[kGroupRows];
 #pragma unroll
     for (int i = 0; i < kGroupRows; ++i) rp[i] = T(0);
     T dot = T(0);
-    for (int q0 = 0; q0 < PT; q0 += 32) {
-        const int q = q0 + lane;
-        const bool act = q < PT;
-        const int k = q < P0 ? 0 : (q < P0 + P1 ? 1 : 2);
-        const int col = k == 0 ? gd.lo0 + 2 * q
-                               : (k == 1 ? gd.lo1 + 2 * (q - P0) : gd.lo2 + 2 * (q - P0 - P1));
-        const T xt0 = act && col < M ? ldcg(x + col) : T(0);
-        const T xt1 = act && col + 1 < M ? ldcg(x + col + 1) : T(0);
-        // every row's two values first (kGroupRows loads in flight), then the products
-        T2 v[kGroupRows];
+    for (int qq = 0; qq < QT; qq += 32) {
+        const int q = qq + lane;
+        const bool act = q < QT;
+        const int k = q < Q0 ? 0 : (q < Q0 + Q1 ? 1 : 2);
+        const int col = k == 0 ? gd.lo0 + 4 * q
+                               : (k == 1 ? gd.lo1 + 4 * (q - Q0) : gd.lo2 + 4 * (q - Q0 - Q1));
+        const R4 xt = act ? ldx4<T>(x, col, M) : R4{T(0), T(0), T(0), T(0)};
+        // every row's four values first (kGroupRows loads in flight), then the products
+        R4 v[kGroupRows];
 #pragma unroll
         for (int i = 0; i < kGroupRows; ++i) {
             const SegSlot e = sm.seg[i][k];
             const bool ok = act && unsigned(col - e.lo) < unsigned(e.len);
-            v[i] = ok ? __ldg(reinterpret_cast<const T2*>(B + e.base + col)) : T2{T(0), T(0)};
+            v[i] = ok ? ld4(Bg + (e.rel + col)) : R4{T(0), T(0), T(0), T(0)};
         }
-        T ca0 = T(0), ca1 = T(0);
+        R4 ca{T(0), T(0), T(0), T(0)};
 #pragma unroll
         for (int i = 0; i < kGroupRows; ++i) {
-            rp[i] = fma(v[i].x, xt0, fma(v[i].y, xt1, rp[i]));
-            ca0 = fma(v[i].x, xg[i], ca0);
-            ca1 = fma(v[i].y, xg[i], ca1);
+            rp[i] = fma(v[i].x, xt.x, fma(v[i].y, xt.y, fma(v[i].z, xt.z, fma(v[i].w, xt.w, rp[i]))));
+            ca.x = fma(v[i].x, xg[i], ca.x);
+            ca.y = fma(v[i].y, xg[i], ca.y);
+            ca.z = fma(v[i].z, xg[i], ca.z);
+            ca.w = fma(v[i].w, xg[i], ca.w);
         }
-        // (a widening slot past the last column holds a zero, but 0 * x can be NaN when x
-        // is not finite: the bounds are tested, not inferred from the sums)
-        if (act && col < M && ca0 != T(0)) {
-            atomicAdd(y + col, ca0);
-            dot = fma(ca0, xt0, dot);
-        }
-        if (act && col + 1 < M && ca1 != T(0)) {
-            atomicAdd(y + col + 1, ca1);
-            dot = fma(ca1, xt1, dot);
+        if (act) {
+            // (a widening slot past the last column holds a zero, but 0 * x can be NaN when x
+            // is not finite: atomic_add4 tests the bounds itself)
+            atomic_add4<T>(y, col, M, ca);
+            dot = fma(ca.x, xt.x, fma(ca.y, xt.y, fma(ca.z, xt.z, fma(ca.w, xt.w, dot))));
         }
     }
-    const T tot = butterfly16(rp, lane);       // lanes 2r, 2r+1 hold row r
-    const int r = (lane >> 1) & 15;
-    const T xr = __shfl_sync(kFull, xrow, r);
-    if ((lane & 1) == 0 && r < n) {
+    const T tot = butterfly8(rp, lane);        // lanes 4r .. 4r+3 hold row r
+    const int r = (lane >> 2) & 7;
+    const T xr = __shfl_sync(kFull, st.xrow, r);
+    if ((lane & 3) == 0 && r < n) {
         atomicAdd(y + r0 + r, tot);
         dot = fma(tot, xr, dot);
     }
     return dot;
-}
-
-// Start moving a group descriptor (32 bytes) into L1 without holding registers for it; a
-// later load_group of it then hits L1.
-__device__ __forceinline__ void prefetch_group(const GroupDesc* d) {
-    asm volatile("prefetch.global.L1 [%0];" ::"l"(reinterpret_cast<const char*>(d)));
 }
 
 // Value of B[s][t] (s, t in the same cell; the preconditioner's diagonal blocks) from the
@@ -238,7 +293,7 @@ template <typename T>
 __device__ __forceinline__ T b_same_cell(const RowMeta* __restrict__ rmeta, const T* __restrict__ B,
                                          int s, int t) {
     const int a = min(s, t), b = max(s, t);
-    const long long o = 2LL * rmeta[a].off + (b - (a & ~1));
+    const long long o = 4LL * rmeta[a].off + (b - (a & ~3));
     const T v = B[o];
     return a == b ? T(2) * v : v;
 }
@@ -276,7 +331,7 @@ template <typename T>
 CgVec<T> cg_vectors(rbf_ctx* ctx) {
     const int slot = sizeof(T) == 8 ? 0 : 1;
     T* base = ctx->cgv[slot].as<T>();
-    const size_t M = size_t(ctx->M);
+    const size_t M = cg_stride(ctx->M);
     CgVec<T> v;
     v.x = base;
     v.u = base + M;

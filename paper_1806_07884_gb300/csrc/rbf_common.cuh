@@ -111,23 +111,24 @@ __device__ __forceinline__ int cell_iy(const Grid& g, double y) {
 //          that band's lower edge
 //   seg 2: two bands above, likewise (empty when that edge is 2R or more above xi_s)
 // (a small relative margin widens each range, so FP32 rounding of the assembly's support
-// test can never place an entry outside it). Each range is widened to even column bounds
-// (lo rounded down, hi rounded up) and the three are stored back to back from an even offset,
-// so the value of column t always sits at an offset of the same parity as t: a lane reads
-// the values of a column pair (t, t+1) with one aligned 2-vector load. Slots whose column is
-// outside the row's own range (t < s in seg 0, the widening) hold exact zeros.
+// test can never place an entry outside it). Each range is widened to column bounds that are
+// multiples of 4 (lo rounded down, hi rounded up) and the three are stored back to back from
+// an offset that is a multiple of 4, so the value of column t always sits at an offset equal
+// to t modulo 4: a lane reads the values of a column quad (t..t+3, t a multiple of 4) with one
+// aligned 4-vector load. Slots whose column is outside the row's own range (t < s in seg 0,
+// the widening) hold exact zeros.
 // The diagonal value is stored halved: the SpMV adds every stored value once to the row sum
 // and once to the column sum, so a halved diagonal counts once in y = B x with no special
 // case. Readers of B itself (preconditioner set-up, export) double it.
 struct __align__(16) RowMeta {
-    unsigned int off;   // offset of the row's first stored value (column lo0 = s & ~1), in pairs
-    int lo1, lo2;       // first (even) column of seg 1 and seg 2
-    unsigned int len;   // stored pairs of seg 0 | seg 1 << 10 | seg 2 << 20 (10 bits each)
+    unsigned int off;   // offset of the row's first stored value (column s & ~3), in quads
+    int lo1, lo2;       // first column (a multiple of 4) of seg 1 and seg 2
+    unsigned int len;   // stored quads of seg 0 | seg 1 << 10 | seg 2 << 20 (10 bits each)
 };
 constexpr int kLenBits = 10;
-constexpr int kMaxSegPairs = (1 << kLenBits) - 1;
-__host__ __device__ __forceinline__ int seg_pairs(unsigned int len, int k) {
-    return int((len >> (kLenBits * k)) & unsigned(kMaxSegPairs));
+constexpr int kMaxSegQuads = (1 << kLenBits) - 1;
+__host__ __device__ __forceinline__ int seg_quads(unsigned int len, int k) {
+    return int((len >> (kLenBits * k)) & unsigned(kMaxSegQuads));
 }
 
 // Relative widening of the 2R disc that bounds each row's column ranges.
@@ -136,28 +137,40 @@ constexpr double kDiscMargin = 1.0 + 1e-5;
 // Rows of one row group: consecutive rows of one band whose column ranges one warp sweeps
 // together (lanes over the union of the rows' ranges, column sums kept in registers across
 // the rows).
-constexpr int kGroupRows = 16;
+constexpr int kGroupRows = 8;
 
-// A row group and the union of its rows' column ranges per segment (even bounds, in column
-// pairs), which is what the SpMV's lanes sweep.
+// A row group and the union of its rows' column ranges per segment (bounds multiples of 4,
+// in column quads), which is what the SpMV's lanes sweep.
 struct __align__(16) GroupDesc {
     int r0, n;          // first row and number of rows (1 .. kGroupRows)
-    int lo0, p0;        // seg 0 union: columns [lo0, lo0 + 2 p0)
-    int lo1, p1;        // seg 1 union
-    int lo2, p2;        // seg 2 union
+    int lo0, q0;        // seg 0 union: columns [lo0, lo0 + 4 q0)
+    int lo1, q1;        // seg 1 union
+    int lo2, q2;        // seg 2 union
 };
 
 // Offset of B[s][t] (s <= t, t in band(s) + k) in the value array, or -1 if the row keeps no
 // slot for t.
 __host__ __device__ __forceinline__ long long upper_slot(const RowMeta& rm, int s, int t, int k) {
-    const int lo = k == 0 ? (s & ~1) : (k == 1 ? rm.lo1 : rm.lo2);
-    const int n0 = 2 * seg_pairs(rm.len, 0), n1 = 2 * seg_pairs(rm.len, 1);
-    const int len = 2 * seg_pairs(rm.len, k);
+    const int lo = k == 0 ? (s & ~3) : (k == 1 ? rm.lo1 : rm.lo2);
+    const int n0 = 4 * seg_quads(rm.len, 0), n1 = 4 * seg_quads(rm.len, 1);
+    const int len = 4 * seg_quads(rm.len, k);
     const int base = k == 0 ? 0 : (k == 1 ? n0 : n0 + n1);
     const int d = t - lo;
     if (d < 0 || d >= len) return -1;
-    return 2LL * rm.off + base + d;
+    return 4LL * rm.off + base + d;
 }
+
+// Linear polynomial of Section 3 (Eq. 6-10), P_i = (x_i, y_i, 1), handled in a centred and
+// scaled frame u = (x - xc) sx, v = (y - yc) sy (|u|, |v| <= 1 over the bounding box), which
+// spans the same functions and keeps the polynomial block of Eq. 10 well scaled. Arguments of
+// the FP64 passes over the points; null pointers switch the parts off.
+struct PolyArgs {
+    double xc, yc, sx, sy;   // the frame
+    const double* k;         // [3] coefficients (of u, v, 1) of the current iterate (residual)
+    double* E;               // [3 * M] A^T P, column-major (u, v, 1), sorted order (assembly)
+    double* gp;              // [12] P^T P (row-major 3 x 3) then P^T h (assembly)
+    double* rk;              // [3] P^T (h - A c - P k) (residual)
+};
 
 // Views of the context's device buffers passed by value to kernels.
 struct Binned {

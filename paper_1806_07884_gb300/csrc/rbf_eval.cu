@@ -46,12 +46,21 @@ __global__ void k_diag_sqrt(const double* __restrict__ a, double* __restrict__ o
     }
 }
 
+// The linear polynomial of Section 3 (Eq. 6-7), coefficients (a_x, a_y, a_0) in the caller's
+// coordinates; 0 without one.
+__device__ __forceinline__ double poly_at(const double* __restrict__ k, double x, double y) {
+    return k ? fma(k[0], x, fma(k[1], y, k[2])) : 0.0;
+}
+
 template <int KIND>
 __global__ void k_eval_points(Binned bd, const double* __restrict__ c, const double* __restrict__ qx,
-                              const double* __restrict__ qy, int64_t Q, double* __restrict__ f) {
+                              const double* __restrict__ qy, int64_t Q, double* __restrict__ f,
+                              const double* __restrict__ k) {
     for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < Q;
-         i += int64_t(gridDim.x) * blockDim.x)
-        f[i] = eval_at<KIND>(bd, c, qx[i], qy[i]);
+         i += int64_t(gridDim.x) * blockDim.x) {
+        const double x = qx[i], y = qy[i];
+        f[i] = eval_at<KIND>(bd, c, x, y) + poly_at(k, x, y);
+    }
 }
 
 // Grid node coordinates follow an inclusive linspace: start + j * step (separately
@@ -59,14 +68,14 @@ __global__ void k_eval_points(Binned bd, const double* __restrict__ c, const dou
 template <int KIND>
 __global__ void k_eval_grid(Binned bd, const double* __restrict__ c, int nx, int ny, double x0,
                             double y0, double x1, double y1, double sx, double sy,
-                            double* __restrict__ f) {
+                            double* __restrict__ f, const double* __restrict__ k) {
     const int64_t Q = int64_t(nx) * ny;
     for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < Q;
          q += int64_t(gridDim.x) * blockDim.x) {
         const int i = int(q / nx), j = int(q % nx);
         const double x = (j == nx - 1 && nx > 1) ? x1 : __dadd_rn(__dmul_rn(double(j), sx), x0);
         const double y = (i == ny - 1 && ny > 1) ? y1 : __dadd_rn(__dmul_rn(double(i), sy), y0);
-        f[q] = eval_at<KIND>(bd, c, x, y);
+        f[q] = eval_at<KIND>(bd, c, x, y) + poly_at(k, x, y);
     }
 }
 
@@ -81,10 +90,10 @@ __global__ void k_export(Binned bd, const T* __restrict__ B, const double* __res
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= bd.M) return;
     const RowMeta rm = bd.rmeta[s];
-    const int lo[3] = {s & ~1, rm.lo1, rm.lo2};
-    long long o = 2LL * rm.off;
+    const int lo[3] = {s & ~3, rm.lo1, rm.lo2};
+    long long o = 4LL * rm.off;
     for (int k = 0; k < 3; ++k) {
-        const int len = 2 * seg_pairs(rm.len, k);
+        const int len = 4 * seg_quads(rm.len, k);
         for (int j = 0; j < len; ++j) {
             const int t = lo[k] + j;
             double v = double(B[o + j]);
@@ -128,6 +137,11 @@ rbf_status diag_sqrt_run(const double* a, double* out, int64_t n, cudaStream_t s
 
 rbf_status eval_points_run(rbf_ctx* ctx, const double* c, const double* qx, const double* qy,
                            int64_t Q, double* f, cudaStream_t st) {
+    return eval_points_poly_run(ctx, c, nullptr, qx, qy, Q, f, st);
+}
+
+rbf_status eval_points_poly_run(rbf_ctx* ctx, const double* c, const double* k, const double* qx,
+                                const double* qy, int64_t Q, double* f, cudaStream_t st) {
     rbf_status s = ensure(ctx, ctx->csort, sizeof(double) * ctx->M, st);
     if (s != RBF_OK) return s;
     const Binned bd = view(ctx);
@@ -137,10 +151,10 @@ rbf_status eval_points_run(rbf_ctx* ctx, const double* c, const double* qx, cons
     const double* cs = ctx->csort.as<double>();
     const int gb = eval_grid_size(Q);
     switch (ctx->kernel) {
-        case RBF_W30: k_eval_points<0><<<gb, 256, 0, st>>>(bd, cs, qx, qy, Q, f); break;
-        case RBF_W31: k_eval_points<1><<<gb, 256, 0, st>>>(bd, cs, qx, qy, Q, f); break;
-        case RBF_W32: k_eval_points<2><<<gb, 256, 0, st>>>(bd, cs, qx, qy, Q, f); break;
-        default: k_eval_points<3><<<gb, 256, 0, st>>>(bd, cs, qx, qy, Q, f); break;
+        case RBF_W30: k_eval_points<0><<<gb, 256, 0, st>>>(bd, cs, qx, qy, Q, f, k); break;
+        case RBF_W31: k_eval_points<1><<<gb, 256, 0, st>>>(bd, cs, qx, qy, Q, f, k); break;
+        case RBF_W32: k_eval_points<2><<<gb, 256, 0, st>>>(bd, cs, qx, qy, Q, f, k); break;
+        default: k_eval_points<3><<<gb, 256, 0, st>>>(bd, cs, qx, qy, Q, f, k); break;
     }
     RBF_CUDA_TRY(cudaGetLastError());
     ctx->launches += 1;
@@ -148,7 +162,7 @@ rbf_status eval_points_run(rbf_ctx* ctx, const double* c, const double* qx, cons
 }
 
 rbf_status eval_grid_run(rbf_ctx* ctx, const double* c, int nx, int ny, const double* box,
-                         double* f, cudaStream_t st) {
+                         double* f, cudaStream_t st, const double* k) {
     rbf_status s = ensure(ctx, ctx->csort, sizeof(double) * ctx->M, st);
     if (s != RBF_OK) return s;
     const Binned bd = view(ctx);
@@ -159,10 +173,10 @@ rbf_status eval_grid_run(rbf_ctx* ctx, const double* c, int nx, int ny, const do
     const double sy = ny > 1 ? (y1 - y0) / double(ny - 1) : 0.0;
     const int gb = eval_grid_size(int64_t(nx) * ny);
     switch (ctx->kernel) {
-        case RBF_W30: k_eval_grid<0><<<gb, 256, 0, st>>>(bd, cs, nx, ny, x0, y0, x1, y1, sx, sy, f); break;
-        case RBF_W31: k_eval_grid<1><<<gb, 256, 0, st>>>(bd, cs, nx, ny, x0, y0, x1, y1, sx, sy, f); break;
-        case RBF_W32: k_eval_grid<2><<<gb, 256, 0, st>>>(bd, cs, nx, ny, x0, y0, x1, y1, sx, sy, f); break;
-        default: k_eval_grid<3><<<gb, 256, 0, st>>>(bd, cs, nx, ny, x0, y0, x1, y1, sx, sy, f); break;
+        case RBF_W30: k_eval_grid<0><<<gb, 256, 0, st>>>(bd, cs, nx, ny, x0, y0, x1, y1, sx, sy, f, k); break;
+        case RBF_W31: k_eval_grid<1><<<gb, 256, 0, st>>>(bd, cs, nx, ny, x0, y0, x1, y1, sx, sy, f, k); break;
+        case RBF_W32: k_eval_grid<2><<<gb, 256, 0, st>>>(bd, cs, nx, ny, x0, y0, x1, y1, sx, sy, f, k); break;
+        default: k_eval_grid<3><<<gb, 256, 0, st>>>(bd, cs, nx, ny, x0, y0, x1, y1, sx, sy, f, k); break;
     }
     RBF_CUDA_TRY(cudaGetLastError());
     ctx->launches += 2;

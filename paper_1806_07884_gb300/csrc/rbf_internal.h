@@ -9,6 +9,21 @@
 
 #include "rbf_common.cuh"
 
+// Device state of the linear polynomial of Section 3 (Eq. 10): the assembly's P^T P and P^T h,
+// the inverse of P^T P (the preconditioner's block of the three polynomial rows), the FP64
+// iterate and residual of the polynomial unknowns, and the CG recurrences of the three rows
+// (kept in FP64 whatever the solver's precision: one thread updates them per iteration).
+struct PolyDev {
+    double gp[12];       // P^T P (row-major 3 x 3), then P^T h
+    double ginv[9];      // (P^T P)^-1
+    double k64[3];       // FP64 iterate (coefficients of u, v, 1)
+    double rk[3];        // FP64 residual P^T (h - A c - P k)
+    double uk[2][3];     // CG: preconditioned residual u of the three rows, by iteration parity
+    double xk[3], pk[3], sk[3], rkc[3];   // CG: solution, direction, s = K p, residual
+    double bk[3];        // right-hand side of the three rows in the current CG solve
+    double tmp[4];
+};
+
 // A device buffer obtained from the context's allocator.
 struct rbf_buf {
     void* p = nullptr;
@@ -65,6 +80,13 @@ struct rbf_ctx {
     bool astore_ok = false;
     int store_a = 1;           // rbf_set_param("store_a")
 
+    // ---- linear polynomial (Section 3, Eq. 6-10): rbf_assemble_poly / rbf_solve_poly ----
+    bool poly = false;         // the last assembly added the polynomial blocks of Eq. 10
+    double pxc = 0.0, pyc = 0.0, psx = 1.0, psy = 1.0;   // frame u = (x - xc) sx, v = (y - yc) sy
+    rbf_buf pE, pE32;          // [3 M] A^T P (FP64), and its FP32 copy for the FP32 solver
+    rbf_buf pdev;              // PolyDev
+    rbf_buf pepart;            // per-block partial sums of E^T u (both parities)
+
     // ---- solver workspace ----
     // FP64 refinement vectors (sorted order): the solution and the matrix-free residual
     rbf_buf x, r;
@@ -87,7 +109,7 @@ struct rbf_ctx {
         cudaGraphExec_t exec = nullptr;
         int ncell = 0, M = 0, gx = 0, ngroup = 0;
         const void* crow = nullptr;
-        const void* key[10] = {};
+        const void* key[12] = {};
     };
     SolveGraph cg_graph[2];
     bool solved = false;       // solver workspace exists
@@ -171,23 +193,33 @@ rbf_status mlp_step_run(rbf_ctx* ctx, float* params, float* m, float* v, int ste
                         const float* feat, const float* target, const int* idx, int64_t n,
                         float* grad, double* loss, cudaStream_t st);
 
-// rbf_assemble.cu
-rbf_status assemble_run(rbf_ctx* ctx, int kernel, int prec, cudaStream_t st);
+// rbf_assemble.cu (with_poly: also A^T P, P^T P and P^T h of Eq. 10)
+rbf_status assemble_run(rbf_ctx* ctx, int kernel, int prec, cudaStream_t st, bool with_poly = false);
 
-// rbf_resid.cu : r = A^T (h - A c) in FP64, matrix-free (c in sorted order). With
-// count_support the support counts are recomputed.
+// r = A^T (h - A c) in FP64 (c in sorted order), from the stored A or matrix-free. With
+// count_support the support counts are recomputed. With the polynomial of the last assembly,
+// poly = true also subtracts P k (k = PolyDev::k64) and writes P^T (h - A c - P k) to
+// PolyDev::rk.
 rbf_status residual_run(rbf_ctx* ctx, const double* c_sorted, double* r_sorted,
-                        bool count_support, cudaStream_t st);
+                        bool count_support, cudaStream_t st, bool poly = false);
+// the frame of the polynomial and the device pointers of PolyDev for the FP64 passes
+PolyArgs poly_args(rbf_ctx* ctx);
 
 // rbf_solve.cu
 rbf_status solve_run(rbf_ctx* ctx, double* c, int use_c0, double tol, int maxit,
                      int min_support, rbf_solve_info* info, cudaStream_t st);
+// the bordered system of Eq. 10 (after an assembly with the polynomial); k: DEVICE, 3 doubles
+// (a_x, a_y, a_0) in the caller's coordinates
+rbf_status solve_poly_run(rbf_ctx* ctx, double* c, double* k, double tol, int maxit,
+                          int min_support, rbf_solve_info* info, cudaStream_t st);
 
 // rbf_eval.cu
 rbf_status eval_points_run(rbf_ctx* ctx, const double* c, const double* qx, const double* qy,
                            int64_t Q, double* f, cudaStream_t st);
 rbf_status eval_grid_run(rbf_ctx* ctx, const double* c, int nx, int ny, const double* box,
-                         double* f, cudaStream_t st);
+                         double* f, cudaStream_t st, const double* k = nullptr);
+rbf_status eval_points_poly_run(rbf_ctx* ctx, const double* c, const double* k, const double* qx,
+                                const double* qy, int64_t Q, double* f, cudaStream_t st);
 rbf_status diag_sqrt_run(const double* a, double* out, int64_t n, cudaStream_t st);
 rbf_status layout_stats_run(rbf_ctx* ctx, rbf_layout_stats* out, cudaStream_t st);
 rbf_status export_upper_run(rbf_ctx* ctx, int64_t cap, int32_t* row, int32_t* col, double* val,

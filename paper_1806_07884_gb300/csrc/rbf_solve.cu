@@ -94,15 +94,19 @@ __device__ bool last_block_total(double (&v)[NV], double* partial, unsigned int*
 // Standalone SpMV y += B x (persistent warps striding over the row groups; y zeroed by the
 // caller).
 template <typename T>
-__global__ void __launch_bounds__(kSpmvWarps * 32, 2)
+__global__ void __launch_bounds__(kSpmvWarps * 32, sizeof(T) == 4 ? 3 : 2)
     k_spmv(Binned bd, const T* __restrict__ B, const T* __restrict__ x, T* __restrict__ y) {
     __shared__ GroupSmem gsm[kSpmvWarps];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int nw = gridDim.x * kSpmvWarps;
-    for (int q = blockIdx.x * kSpmvWarps + wid; q < bd.ngroup; q += nw) {
-        // the next group's descriptor moves into L1 while this group's rows stream
-        if (q + nw < bd.ngroup) prefetch_group(bd.gdesc + q + nw);
-        spmv_group<T>(load_group(bd.gdesc + q), bd.rmeta, B, x, y, bd.M, lane, gsm[wid]);
+    int q = blockIdx.x * kSpmvWarps + wid;
+    if (q >= bd.ngroup) return;
+    // the next group's description is loaded while this group's rows stream
+    GroupStage<T> cur = stage_group<T>(bd.gdesc, bd.rmeta, x, q, lane);
+    for (; q < bd.ngroup; q += nw) {
+        const GroupStage<T> nxt = q + nw < bd.ngroup ? stage_group<T>(bd.gdesc, bd.rmeta, x, q + nw, lane) : cur;
+        spmv_group<T>(cur, B, x, y, bd.M, lane, gsm[wid]);
+        cur = nxt;
     }
 }
 
@@ -118,7 +122,7 @@ __global__ void __launch_bounds__(kSpmvWarps * 32, 2)
 // wait for the solver's state: after the solve stops (at most kItersPerBody - 1 SpMVs before
 // the loop condition is read) its w and delta go unused, and the next start resets the slots.
 template <typename T>
-__global__ void __launch_bounds__(kSpmvWarps * 32, 2)
+__global__ void __launch_bounds__(kSpmvWarps * 32, sizeof(T) == 4 ? 3 : 2)
     k_cg_spmv(Binned bd, const T* __restrict__ B, const T* __restrict__ u, T* __restrict__ w,
               int P, CgScalars* __restrict__ sc) {
     __shared__ GroupSmem gsm[kSpmvWarps];
@@ -126,10 +130,15 @@ __global__ void __launch_bounds__(kSpmvWarps * 32, 2)
     const int gw = blockIdx.x * kSpmvWarps + wid;
     const int nw = gridDim.x * kSpmvWarps;
     T d = T(0);
-    for (int q = gw; q < bd.ngroup; q += nw) {
-        // the next group's descriptor moves into L1 while this group's rows stream
-        if (q + nw < bd.ngroup) prefetch_group(bd.gdesc + q + nw);
-        d += spmv_group<T>(load_group(bd.gdesc + q), bd.rmeta, B, u, w, bd.M, lane, gsm[wid]);
+    if (gw < bd.ngroup) {
+        // the next group's description is loaded while this group's rows stream
+        GroupStage<T> cur = stage_group<T>(bd.gdesc, bd.rmeta, u, gw, lane);
+        for (int q = gw; q < bd.ngroup; q += nw) {
+            const GroupStage<T> nxt =
+                q + nw < bd.ngroup ? stage_group<T>(bd.gdesc, bd.rmeta, u, q + nw, lane) : cur;
+            d += spmv_group<T>(cur, B, u, w, bd.M, lane, gsm[wid]);
+            cur = nxt;
+        }
     }
     d = warp_sum<T>(d);
     if (lane == 0 && d != T(0)) atomicAdd(&sc->acc_delta[P][gw & (kAccSlots - 1)], double(d));
@@ -146,12 +155,20 @@ __global__ void __launch_bounds__(kSpmvWarps * 32, 2)
 // iterates the FP64 refinement corrects): every block repeats it, and FP64 issues at 1/64
 // of the FP32 rate on this GPU.
 constexpr int kPartBatch = 8;   // per-block partials loaded per lane before they are summed
+// With the linear polynomial of Eq. 10 (pd non-null) the system is bordered by the three
+// polynomial rows: the w of row i gains E_i . u_k (E = A^T P in the solver's precision, u_k the
+// polynomial part of u), the polynomial rows' w_k = E^T u + G u_k (G = P^T P; E^T u from the
+// previous kernel's per-block partials pe), and delta gains 2 (E^T u) . u_k + u_k^T G u_k.
+// Block 0's thread 0 advances the three rows' recurrences (FP64) with u_k = G^-1 r_k.
 template <typename T>
 __global__ void __launch_bounds__(kVecThreads)
     k_cg_update(Binned bd, CgVec<T> v, int P, CgScalars* __restrict__ sc,
-                T* __restrict__ pbuf) {
+                T* __restrict__ pbuf, const T* __restrict__ E, T* __restrict__ pe,
+                PolyDev* __restrict__ pd) {
     __shared__ T s_ab[2];
     __shared__ int s_go;
+    __shared__ T s_uk[3];
+    __shared__ double s_pg[2];   // block 0: the polynomial rows' share of gamma and (r, r)
     static_assert(kAccSlots == 64, "two slots per lane");
     const int nblk = gridDim.x;
     const int M = bd.M;
@@ -191,11 +208,36 @@ __global__ void __launch_bounds__(kVecThreads)
                 rr += pv[k].y;
             }
         }
+        T et[3] = {T(0), T(0), T(0)};
+        if (pd) {
+            const T* pp = pe + size_t(P) * 4 * nblk;
+            for (int b = lane; b < nblk; b += 32)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) et[j] += __ldcg(pp + 4 * b + j);
+#pragma unroll
+            for (int j = 0; j < 3; ++j) et[j] = warp_sum<T>(et[j]);
+        }
         int state = sl.state;
         if (state != kRunning) g = rr = d = T(0);
         g = warp_sum<T>(g);
         rr = warp_sum<T>(rr);
         d = warp_sum<T>(d);
+        double wk[3] = {0.0, 0.0, 0.0};
+        if (pd && lane == 0) {
+            // w_k = E^T u + G u_k; delta += 2 (E^T u) . u_k + u_k^T G u_k
+            double dp = 0.0;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const double ui = __ldcg(&pd->uk[P][i]);
+                double gu = 0.0;
+#pragma unroll
+                for (int j = 0; j < 3; ++j) gu = fma(pd->gp[3 * i + j], __ldcg(&pd->uk[P][j]), gu);
+                wk[i] = double(et[i]) + gu;
+                dp += ui * (2.0 * double(et[i]) + gu);
+                s_uk[i] = T(ui);
+            }
+            if (state == kRunning) d += T(dp);
+        }
         if (lane == 0) {
             T alpha = T(0), beta = T(0);
             const int was = state;
@@ -216,6 +258,33 @@ __global__ void __launch_bounds__(kVecThreads)
             s_ab[0] = alpha;
             s_ab[1] = beta;
             s_go = state == kRunning;
+            if (pd && blockIdx.x == 0 && state == kRunning) {
+                // the three polynomial rows: s = w + beta s, p = u + beta p, x += alpha p,
+                // r -= alpha s, u = G^-1 r (FP64)
+                double rn[3];
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    const double sk = fma(double(beta), pd->sk[i], wk[i]);
+                    const double pk = fma(double(beta), pd->pk[i], __ldcg(&pd->uk[P][i]));
+                    pd->sk[i] = sk;
+                    pd->pk[i] = pk;
+                    pd->xk[i] = fma(double(alpha), pk, pd->xk[i]);
+                    rn[i] = fma(-double(alpha), sk, pd->rkc[i]);
+                    pd->rkc[i] = rn[i];
+                }
+                double pg = 0.0, prr = 0.0;
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    double un = 0.0;
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) un = fma(pd->ginv[3 * i + j], rn[j], un);
+                    pd->uk[P ^ 1][i] = un;
+                    pg = fma(rn[i], un, pg);
+                    prr = fma(rn[i], rn[i], prr);
+                }
+                s_pg[0] = pg;
+                s_pg[1] = prr;
+            }
             if (blockIdx.x == 0) {
                 CgSlot nx = sl;
                 nx.state = state;
@@ -245,6 +314,12 @@ __global__ void __launch_bounds__(kVecThreads)
     T* __restrict__ sQ = P ? v.s[0] : v.s[1];
     T* __restrict__ wQ = P ? v.w[0] : v.w[1];
     T acc[2] = {T(0), T(0)};
+    T eacc[3] = {T(0), T(0), T(0)};
+    const T uk0 = pd ? s_uk[0] : T(0), uk1 = pd ? s_uk[1] : T(0), uk2 = pd ? s_uk[2] : T(0);
+    // w_j of the bordered system: B u + E_j . u_k
+    auto wfull = [&](int j, T wj) -> T {
+        return pd ? fma(E[j], uk0, fma(E[M + j], uk1, fma(E[2 * M + j], uk2, wj))) : wj;
+    };
     // The new residual of each row of the chunk is kept in shared memory for the block-Jacobi
     // step; rows of a cell outside the chunk are recomputed with the same operations.
     __shared__ T rsm[kVecThreads];
@@ -255,7 +330,7 @@ __global__ void __launch_bounds__(kVecThreads)
         if (valid) {
             const bool first = i == i_first;
             di = first ? f_d : v.dinv[i];
-            const T wi = di == T(0) ? T(0) : (first ? f_w : wP[i]);
+            const T wi = di == T(0) ? T(0) : wfull(i, first ? f_w : wP[i]);
             const T si = fma(tb, first ? f_s : sP[i], wi);
             const T pi = fma(tb, first ? f_p : v.p[i], first ? f_u : v.u[i]);
             ri = di == T(0) ? T(0) : fma(-ta, si, first ? f_r : rP[i]);
@@ -272,30 +347,53 @@ __global__ void __launch_bounds__(kVecThreads)
             // rows of pinned centres carry zeros in the inverse block, so r_j need no mask
             const T ui = apply_prec<T>(bd, v.bjinv, cm, i, di, ri, [&](int j) {
                 const int o = j - base;
-                return o >= 0 && o < kVecThreads ? rsm[o] : next_r(rP[j], sP[j], wP[j], ta, tb);
+                return o >= 0 && o < kVecThreads ? rsm[o]
+                                                 : next_r(rP[j], sP[j], wfull(j, wP[j]), ta, tb);
             });
             v.u[i] = ui;
             acc[0] = fma(ri, ui, acc[0]);
             acc[1] = fma(ri, ri, acc[1]);
+            if (pd) {
+                eacc[0] = fma(E[i], ui, eacc[0]);
+                eacc[1] = fma(E[M + i], ui, eacc[1]);
+                eacc[2] = fma(E[2 * M + i], ui, eacc[2]);
+            }
         }
         __syncthreads();
     }
     double tot[2];
     block_sum_t<2, T>(acc, tot);
     if (threadIdx.x == 0) {
+        if (pd && blockIdx.x == 0) {
+            tot[0] += s_pg[0];
+            tot[1] += s_pg[1];
+        }
         T* pb = pbuf + size_t(P ^ 1) * 2 * nblk;
         pb[2 * blockIdx.x] = T(tot[0]);
         pb[2 * blockIdx.x + 1] = T(tot[1]);
+    }
+    if (pd) {
+        double et[3];
+        block_sum_t<3, T>(eacc, et);
+        if (threadIdx.x == 0) {
+            T* pp = pe + size_t(P ^ 1) * 4 * nblk + 4 * blockIdx.x;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) pp[j] = T(et[j]);
+        }
     }
 }
 
 // Start: r = bscale b - B x0 (B x0 in w[1] when use_x0), u = D^-1 r, p = s[0] = w[0] = 0
 // (x = 0 without a start vector); per-block partials of gamma_0 and (r_0, r_0) for the first
 // update, and (b, b) reduced by the last block, which also sets the parity-0 slot.
+// With the polynomial (pd): its three rows start from r_k = bscale * pd->bk (x_k = 0, no start
+// vector), u_k = G^-1 r_k; block 0 adds their shares of gamma, (r, r) and (b, b); the
+// per-block partials of E^T u of parity 0 are written for the first update.
 template <typename T, typename TB>
 __global__ void __launch_bounds__(kVecThreads)
     k_cg_init(Binned bd, CgVec<T> v, const TB* __restrict__ b, int use_x0,
-              CgScalars* __restrict__ sc, T* __restrict__ pbuf, double* __restrict__ partial) {
+              CgScalars* __restrict__ sc, T* __restrict__ pbuf, double* __restrict__ partial,
+              const T* __restrict__ E, T* __restrict__ pe, PolyDev* __restrict__ pd) {
     const double bscale = sc->bscale;
     const T* __restrict__ w1 = v.w[1];
     auto r0 = [&](int j) -> T {
@@ -303,6 +401,7 @@ __global__ void __launch_bounds__(kVecThreads)
         return use_x0 ? bj - w1[j] : bj;
     };
     T acc[2] = {T(0), T(0)};
+    T eacc[3] = {T(0), T(0), T(0)};
     double bb[1] = {0.0}, tot[1];
     const int M = bd.M;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) {
@@ -319,12 +418,40 @@ __global__ void __launch_bounds__(kVecThreads)
         acc[0] = fma(ri, ui, acc[0]);
         acc[1] = fma(ri, ri, acc[1]);
         bb[0] += double(bi) * double(bi);
+        if (pd) {
+            eacc[0] = fma(E[i], ui, eacc[0]);
+            eacc[1] = fma(E[M + i], ui, eacc[1]);
+            eacc[2] = fma(E[2 * M + i], ui, eacc[2]);
+        }
+    }
+    if (pd && blockIdx.x == 0 && threadIdx.x == 0) {
+        double rk[3];
+        for (int i = 0; i < 3; ++i) {
+            rk[i] = pd->bk[i] * bscale;
+            pd->rkc[i] = rk[i];
+            pd->xk[i] = pd->pk[i] = pd->sk[i] = 0.0;
+            bb[0] += rk[i] * rk[i];
+        }
+        for (int i = 0; i < 3; ++i) {
+            double un = 0.0;
+            for (int j = 0; j < 3; ++j) un = fma(pd->ginv[3 * i + j], rk[j], un);
+            pd->uk[0][i] = un;
+            pd->uk[1][i] = 0.0;
+            acc[0] += T(rk[i] * un);
+            acc[1] += T(rk[i] * rk[i]);
+        }
     }
     double at[2];
     block_sum_t<2, T>(acc, at);
     if (threadIdx.x == 0) {
         pbuf[2 * blockIdx.x] = T(at[0]);
         pbuf[2 * blockIdx.x + 1] = T(at[1]);
+    }
+    if (pd) {
+        double et[3];
+        block_sum_t<3, T>(eacc, et);
+        if (threadIdx.x == 0)
+            for (int j = 0; j < 3; ++j) pe[4 * blockIdx.x + j] = T(et[j]);
     }
     if (last_block_total<1>(bb, partial, &sc->ticket, tot) && threadIdx.x == 0) {
         sc->bb = tot[0];
@@ -431,16 +558,60 @@ __global__ void k_from_sorted_T(const T* __restrict__ src, const int* __restrict
     if (s < M) dst[perm[s]] = double(src[s]);
 }
 
-// x64 = (x64 + scale * d32) on unpinned rows; x64 pinned rows forced to 0.
-__global__ void k_axpy_mixed(int M, double* __restrict__ x, const float* __restrict__ d,
-                             double scale, const float* __restrict__ dinv) {
+// x64 = (x64 + scale * d) on unpinned rows; x64 pinned rows forced to 0.
+template <typename T>
+__global__ void k_axpy_mixed(int M, double* __restrict__ x, const T* __restrict__ d,
+                             double scale, const T* __restrict__ dinv) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < M) x[i] = dinv[i] == 0.0f ? 0.0 : fma(scale, double(d[i]), x[i]);
+    if (i < M) x[i] = dinv[i] == T(0) ? 0.0 : fma(scale, double(d[i]), x[i]);
 }
 
-__global__ void k_mask_zero(int M, double* __restrict__ x, const float* __restrict__ dinv32) {
+// ---- the three polynomial rows of Eq. 10 (one thread each) ----
+
+// G^-1 = adj(G) / det(G) for the SPD 3 x 3 block G = P^T P (FP64); tmp[0] = 1 when G is
+// numerically singular (the points are collinear: a linear polynomial is not determined).
+// Also clears the FP64 iterate of the polynomial unknowns.
+__global__ void k_poly_setup(PolyDev* pd) {
+    const double* g = pd->gp;
+    const double c00 = g[4] * g[8] - g[5] * g[7], c01 = g[5] * g[6] - g[3] * g[8],
+                 c02 = g[3] * g[7] - g[4] * g[6];
+    const double det = g[0] * c00 + g[1] * c01 + g[2] * c02;
+    const double tr = (g[0] + g[4] + g[8]) / 3.0;
+    const bool bad = !(det > 1e-12 * tr * tr * tr) || !isfinite(det);
+    const double id = bad ? 0.0 : 1.0 / det;
+    double a[9] = {c00, g[2] * g[7] - g[1] * g[8], g[1] * g[5] - g[2] * g[4],
+                   c01, g[0] * g[8] - g[2] * g[6], g[2] * g[3] - g[0] * g[5],
+                   c02, g[1] * g[6] - g[0] * g[7], g[0] * g[4] - g[1] * g[3]};
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) pd->ginv[3 * i + j] = 0.5 * (a[3 * i + j] + a[3 * j + i]) * id;
+    for (int i = 0; i < 3; ++i) pd->k64[i] = 0.0;
+    pd->tmp[0] = bad ? 1.0 : 0.0;
+}
+
+// k64 += scale * x_k (the correction of the last CG solve)
+__global__ void k_poly_axpy(PolyDev* pd, double scale) {
+    for (int i = 0; i < 3; ++i) pd->k64[i] = fma(scale, pd->xk[i], pd->k64[i]);
+}
+
+// out[0] += ||v||^2 (three values)
+__global__ void k_poly_norm_add(const double* __restrict__ v, double* __restrict__ out) {
+    out[0] += v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+}
+
+// The coefficients in the caller's coordinates: u = (x - xc) sx, v = (y - yc) sy, so
+// k0 u + k1 v + k2 = (k0 sx) x + (k1 sy) y + (k2 - k0 sx xc - k1 sy yc).
+__global__ void k_poly_export(const PolyDev* __restrict__ pd, double xc, double yc, double sx,
+                              double sy, double* __restrict__ out) {
+    const double ax = pd->k64[0] * sx, ay = pd->k64[1] * sy;
+    out[0] = ax;
+    out[1] = ay;
+    out[2] = pd->k64[2] - ax * xc - ay * yc;
+}
+
+template <typename TM>
+__global__ void k_mask_zero(int M, double* __restrict__ x, const TM* __restrict__ dinv) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < M && dinv32[i] == 0.0f) x[i] = 0.0;
+    if (i < M && dinv[i] == TM(0)) x[i] = 0.0;
 }
 
 __global__ void k_to_f32(int M, const double* __restrict__ x, float* __restrict__ u) {
@@ -485,14 +656,33 @@ int vec_grid(const rbf_ctx* ctx) {
     return std::max(1, std::min(div_up(ctx->M, kVecThreads), 152 * 8));
 }
 
+// The polynomial rows of Eq. 10 in a CG solve of precision T (all null without them).
+template <typename T>
+struct PolyCg {
+    const T* E = nullptr;   // A^T P in T
+    T* pe = nullptr;        // per-block partials of E^T u
+    PolyDev* pd = nullptr;
+};
+template <typename T>
+PolyCg<T> poly_cg(rbf_ctx* ctx, bool on) {
+    PolyCg<T> q;
+    if (!on) return q;
+    q.E = sizeof(T) == 8 ? reinterpret_cast<const T*>(ctx->pE.p) : reinterpret_cast<const T*>(ctx->pE32.p);
+    q.pe = ctx->pepart.as<T>();
+    q.pd = ctx->pdev.as<PolyDev>();
+    return q;
+}
+
 // One CG iteration (two kernels) reading the buffers of parity P, on stream cs.
 template <typename T>
-void launch_iteration(rbf_ctx* ctx, const CgVec<T>& v, int P, cudaStream_t cs) {
+void launch_iteration(rbf_ctx* ctx, const CgVec<T>& v, int P, cudaStream_t cs,
+                      const PolyCg<T>& pq = PolyCg<T>()) {
     const Binned bd = view(ctx);
     CgScalars* sc = ctx->scal.as<CgScalars>();
     k_cg_spmv<T><<<spmv_grid_T<T>(ctx), kSpmvWarps * 32, 0, cs>>>(bd, ctx->bvals.as<T>(), v.u,
                                                                   v.w[P], P, sc);
-    k_cg_update<T><<<vec_grid(ctx), kVecThreads, 0, cs>>>(bd, v, P, sc, ctx->partial.as<T>());
+    k_cg_update<T><<<vec_grid(ctx), kVecThreads, 0, cs>>>(bd, v, P, sc, ctx->partial.as<T>(),
+                                                          pq.E, pq.pe, pq.pd);
 }
 
 // The solve graph of precision T: one conditional WHILE node whose body runs
@@ -500,14 +690,15 @@ void launch_iteration(rbf_ctx* ctx, const CgVec<T>& v, int P, cudaStream_t cs) {
 // device-side state, so the whole iteration runs on the GPU without host round trips.
 // Instantiated once per context, precision and workspace layout, then replayed.
 template <typename T>
-rbf_status cg_graph(rbf_ctx* ctx, cudaGraphExec_t* out) {
+rbf_status cg_graph(rbf_ctx* ctx, cudaGraphExec_t* out, bool poly) {
     rbf_ctx::SolveGraph& sg = ctx->cg_graph[sizeof(T) == 8 ? 0 : 1];
     const CgVec<T> v = cg_vectors<T>(ctx);
-    const void* key[10] = {ctx->bvals.p, v.x, v.dinv, v.bjinv, ctx->scal.p, ctx->partial.p,
-                           ctx->cstart.p, ctx->rmeta.p, ctx->gdesc.p, ctx->bjoff.p};
+    const PolyCg<T> pq = poly_cg<T>(ctx, poly);
+    const void* key[12] = {ctx->bvals.p, v.x, v.dinv, v.bjinv, ctx->scal.p, ctx->partial.p,
+                           ctx->cstart.p, ctx->rmeta.p, ctx->gdesc.p, ctx->bjoff.p, pq.E, pq.pe};
     bool hit = sg.exec && sg.ncell == ctx->g.ncell && sg.M == ctx->M && sg.gx == ctx->g.gx &&
                sg.crow == ctx->crow.p && sg.ngroup == ctx->ngroup;
-    for (int k = 0; k < 10 && hit; ++k) hit = sg.key[k] == key[k];
+    for (int k = 0; k < 12 && hit; ++k) hit = sg.key[k] == key[k];
     if (hit) {
         *out = sg.exec;
         return RBF_OK;
@@ -534,7 +725,7 @@ rbf_status cg_graph(rbf_ctx* ctx, cudaGraphExec_t* out) {
     if (e == cudaSuccess)
         e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        for (int k = 0; k < kItersPerBody; ++k) launch_iteration<T>(ctx, v, k & 1, cs);
+        for (int k = 0; k < kItersPerBody; ++k) launch_iteration<T>(ctx, v, k & 1, cs, pq);
         k_cg_cond<<<1, 1, 0, cs>>>(ctx->scal.as<CgScalars>(), handle);
         cudaGraph_t captured = nullptr;
         e = cudaStreamEndCapture(cs, &captured);
@@ -550,7 +741,7 @@ rbf_status cg_graph(rbf_ctx* ctx, cudaGraphExec_t* out) {
     sg.gx = ctx->g.gx;
     sg.crow = ctx->crow.p;
     sg.ngroup = ctx->ngroup;
-    for (int k = 0; k < 10; ++k) sg.key[k] = key[k];
+    for (int k = 0; k < 12; ++k) sg.key[k] = key[k];
     *out = sg.exec;
     return RBF_OK;
 }
@@ -559,10 +750,13 @@ rbf_status cg_graph(rbf_ctx* ctx, cudaGraphExec_t* out) {
 // when use_x0).
 template <typename T, typename TB>
 rbf_status cg_start(rbf_ctx* ctx, const TB* b, double bscale, bool use_x0, double tol, int maxit,
-                    cudaStream_t st) {
+                    cudaStream_t st, bool poly = false, const double* bk = nullptr) {
     const Binned bd = view(ctx);
     const CgVec<T> v = cg_vectors<T>(ctx);
     CgScalars* sc = ctx->scal.as<CgScalars>();
+    const PolyCg<T> pq = poly_cg<T>(ctx, poly);
+    if (poly)
+        RBF_CUDA_TRY(cudaMemcpyAsync(pq.pd->bk, bk, 3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
     CgScalars h{};
     h.tol2 = tol * tol;
     h.bscale = bscale;
@@ -578,7 +772,8 @@ rbf_status cg_start(rbf_ctx* ctx, const TB* b, double bscale, bool use_x0, doubl
     // start kernel's (b, b) partials after them
     k_cg_init<T, TB><<<vec_grid(ctx), kVecThreads, 0, st>>>(bd, v, b, use_x0 ? 1 : 0, sc,
                                                             reinterpret_cast<T*>(part),
-                                                            part + 4 * vec_grid(ctx));
+                                                            part + 4 * vec_grid(ctx), pq.E, pq.pe,
+                                                            pq.pd);
     ctx->launches += 1;
     RBF_CUDA_TRY(cudaGetLastError());
     return RBF_OK;
@@ -588,11 +783,12 @@ rbf_status cg_start(rbf_ctx* ctx, const TB* b, double bscale, bool use_x0, doubl
 // `st`, then one launch of the solve graph.
 template <typename T, typename TB>
 rbf_status run_cg(rbf_ctx* ctx, const TB* b, double bscale, bool use_x0, double tol, int maxit,
-                  int* iters, double* relres, int* state, cudaStream_t st) {
+                  int* iters, double* relres, int* state, cudaStream_t st, bool poly = false,
+                  const double* bk = nullptr) {
     rbf_status s;
     cudaGraphExec_t ex;
-    if ((s = cg_graph<T>(ctx, &ex)) != RBF_OK) return s;
-    if ((s = cg_start<T, TB>(ctx, b, bscale, use_x0, tol, maxit, st)) != RBF_OK) return s;
+    if ((s = cg_graph<T>(ctx, &ex, poly)) != RBF_OK) return s;
+    if ((s = cg_start<T, TB>(ctx, b, bscale, use_x0, tol, maxit, st, poly, bk)) != RBF_OK) return s;
     RBF_CUDA_TRY(cudaGraphLaunch(ex, st));
     CgScalars* hs = static_cast<CgScalars*>(ctx->hpinned);
     RBF_CUDA_TRY(cudaMemcpyAsync(hs, ctx->scal.p, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
@@ -644,7 +840,7 @@ __global__ void k_fill(T* __restrict__ v, int n, T value) {
 
 template <typename T>
 rbf_status bench_spmv_impl(rbf_ctx* ctx, int reps, cudaStream_t st) {
-    rbf_status s = ensure(ctx, ctx->cgv[sizeof(T) == 8 ? 0 : 1], sizeof(T) * kCgVecs * size_t(ctx->M), st);
+    rbf_status s = ensure(ctx, ctx->cgv[sizeof(T) == 8 ? 0 : 1], sizeof(T) * kCgVecs * cg_stride(ctx->M), st);
     if (s != RBF_OK) return s;
     const Binned bd = view(ctx);
     const CgVec<T> v = cg_vectors<T>(ctx);
@@ -727,7 +923,7 @@ rbf_status solve_run(rbf_ctx* ctx, double* c, int use_c0, double tol, int maxit,
     int state = kConverged;
 
     if (ctx->prec == RBF_FP64) {
-        ENS(cgv[0], sizeof(double) * kCgVecs * size_t(M));
+        ENS(cgv[0], sizeof(double) * kCgVecs * cg_stride(M));
         ENS(dinv, sizeof(double) * M);
         ENS(bjinv, sizeof(double) * std::max<int64_t>(ctx->nbj, 1));
         k_prec_setup<double><<<div_up(ctx->g.ncell, kBjWarps), kBjWarps * 32, 0, st>>>(
@@ -750,7 +946,7 @@ rbf_status solve_run(rbf_ctx* ctx, double* c, int use_c0, double tol, int maxit,
         inf.iterations = it;
         inf.rel_residual = rel;
     } else {
-        ENS(cgv[1], sizeof(float) * kCgVecs * size_t(M));
+        ENS(cgv[1], sizeof(float) * kCgVecs * cg_stride(M));
         ENS(dinv32, sizeof(float) * M);
         ENS(bjinv32, sizeof(float) * std::max<int64_t>(ctx->nbj, 1));
         k_prec_setup<float><<<div_up(ctx->g.ncell, kBjWarps), kBjWarps * 32, 0, st>>>(
@@ -774,7 +970,7 @@ rbf_status solve_run(rbf_ctx* ctx, double* c, int use_c0, double tol, int maxit,
         bool approx_r = false;
         if (use_c0) {
             launch_gather_sorted(c, bd.cperm, x64, M, st);
-            k_mask_zero<<<div_up(M, 256), 256, 0, st>>>(M, x64, dinv32);
+            k_mask_zero<float><<<div_up(M, 256), 256, 0, st>>>(M, x64, dinv32);
             k_to_f32<<<div_up(M, 256), 256, 0, st>>>(M, x64, v.u);
             RBF_CUDA_TRY(cudaMemsetAsync(v.w[0], 0, sizeof(float) * M, st));
             launch_spmv(ctx, RBF_FP32_REFINE, v.u, v.w[0], st);
@@ -824,10 +1020,10 @@ rbf_status solve_run(rbf_ctx* ctx, double* c, int use_c0, double tol, int maxit,
                 state = kBreakdown;
                 break;
             }
-            k_axpy_mixed<<<div_up(M, 256), 256, 0, st>>>(M, x64, v.x, rn, dinv32);
+            k_axpy_mixed<float><<<div_up(M, 256), 256, 0, st>>>(M, x64, v.x, rn, dinv32);
             RBF_CUDA_TRY(cudaMemsetAsync(r64, 0, sizeof(double) * M, st));
             if ((s = residual_run(ctx, x64, r64, false, st)) != RBF_OK) return s;
-            k_mask_zero<<<div_up(M, 256), 256, 0, st>>>(M, r64, dinv32);
+            k_mask_zero<float><<<div_up(M, 256), 256, 0, st>>>(M, r64, dinv32);
             ctx->launches += 2;
             approx_r = false;
             double rn_new = 0.0;
@@ -865,6 +1061,173 @@ rbf_status solve_run(rbf_ctx* ctx, double* c, int use_c0, double tol, int maxit,
         launch_scatter_orig(x64, bd.cperm, c, M, st);
         ctx->launches += 1;
     }
+    RBF_CUDA_TRY(cudaGetLastError());
+    ctx->solved = true;
+    RBF_CUDA_TRY(cudaMemcpyAsync(npin_h, npin_d, sizeof(int), cudaMemcpyDeviceToHost, st));
+    RBF_CUDA_TRY(cudaStreamSynchronize(st));
+    inf.pinned = *reinterpret_cast<int*>(npin_h);
+    if (info) *info = inf;
+#undef ENS
+    return finish_status(ctx, state);
+}
+
+// The bordered system of Eq. 10 by iterative refinement from c = 0, k = 0: every step computes
+// the FP64 residual (A^T e, P^T e) of e = h - A c - P k from the points (or the stored A),
+// solves the correction with preconditioned CG on the bordered matrix in the assembly's
+// precision (FP32 inner tolerance inner_tol, or FP64 to what the outer tolerance needs), and
+// adds it in FP64. A stalled FP32 refinement promotes the solve to an FP64 assembly and goes on
+// with FP64 inner solves from the refined iterate.
+rbf_status solve_poly_run(rbf_ctx* ctx, double* c, double* kout, double tol, int maxit,
+                          int min_support, rbf_solve_info* info, cudaStream_t st) {
+    const int M = ctx->M;
+    const Binned bd = view(ctx);
+    rbf_status s;
+#define ENS(buf, bytes) \
+    if ((s = ensure(ctx, ctx->buf, (bytes), st)) != RBF_OK) return s;
+    ENS(x, sizeof(double) * M);
+    ENS(r, sizeof(double) * M);
+    ENS(scal, sizeof(CgScalars) + 64);
+    ENS(partial, sizeof(double) * 5 * std::max(vec_grid(ctx), 1));
+    ENS(pepart, sizeof(double) * 8 * std::max(vec_grid(ctx), 1));
+    int64_t* npin_h = static_cast<int64_t*>(ctx->hpinned) + 256;
+    int* npin_d = reinterpret_cast<int*>(ctx->scal.as<char>() + sizeof(CgScalars));
+    double* nrm_d = reinterpret_cast<double*>(ctx->scal.as<char>() + sizeof(CgScalars) + 8);
+    double* nrm_h = reinterpret_cast<double*>(static_cast<char*>(ctx->hpinned) + 3072);
+    PolyDev* pd = ctx->pdev.as<PolyDev>();
+    double* x64 = ctx->x.as<double>();
+    double* r64 = ctx->r.as<double>();
+    // the row mask of the current precision (0 on pinned rows)
+    auto setup = [&](int prec) -> rbf_status {
+        RBF_CUDA_TRY(cudaMemsetAsync(npin_d, 0, sizeof(int), st));
+        if (prec == RBF_FP64) {
+            ENS(cgv[0], sizeof(double) * kCgVecs * cg_stride(M));
+            ENS(dinv, sizeof(double) * M);
+            ENS(bjinv, sizeof(double) * std::max<int64_t>(ctx->nbj, 1));
+        } else {
+            ENS(cgv[1], sizeof(float) * kCgVecs * cg_stride(M));
+            ENS(dinv32, sizeof(float) * M);
+            ENS(bjinv32, sizeof(float) * std::max<int64_t>(ctx->nbj, 1));
+        }
+        return prec_setup_run(ctx, prec, min_support, npin_d, st);
+    };
+    if ((s = setup(ctx->prec)) != RBF_OK) return s;
+    k_poly_setup<<<1, 1, 0, st>>>(pd);
+    ctx->launches += 1;
+    // the mask in both precisions agrees (the support counts decide it), FP64 iterate 0
+    auto mask_zero = [&](double* vv) {
+        if (ctx->prec == RBF_FP64)
+            k_mask_zero<double><<<div_up(M, 256), 256, 0, st>>>(M, vv, ctx->dinv.as<double>());
+        else
+            k_mask_zero<float><<<div_up(M, 256), 256, 0, st>>>(M, vv, ctx->dinv32.as<float>());
+        ctx->launches += 1;
+    };
+    // ||r||^2 over unpinned rows plus the three polynomial rows
+    auto norm = [&](const double* vv, const double* vk, double* out) -> rbf_status {
+        if (ctx->prec == RBF_FP64) {
+            // k_norm2 masks with an FP32 row mask; with FP64 the pinned rows are zero already
+            k_norm2<<<1, 1024, 0, st>>>(M, vv, nullptr, nrm_d);
+        } else {
+            k_norm2<<<1, 1024, 0, st>>>(M, vv, ctx->dinv32.as<float>(), nrm_d);
+        }
+        k_poly_norm_add<<<1, 1, 0, st>>>(vk, nrm_d);
+        ctx->launches += 2;
+        RBF_CUDA_TRY(cudaMemcpyAsync(nrm_h, nrm_d, sizeof(double), cudaMemcpyDeviceToHost, st));
+        RBF_CUDA_TRY(cudaStreamSynchronize(st));
+        *out = sqrt(nrm_h[0]);
+        return RBF_OK;
+    };
+    RBF_CUDA_TRY(cudaMemsetAsync(x64, 0, sizeof(double) * M, st));
+    RBF_CUDA_TRY(cudaMemcpyAsync(r64, ctx->bvec.p, sizeof(double) * M, cudaMemcpyDeviceToDevice, st));
+    RBF_CUDA_TRY(cudaMemcpyAsync(pd->rk, pd->gp + 9, 3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    mask_zero(r64);
+    RBF_CUDA_TRY(cudaGetLastError());
+    double bnorm = 0.0;
+    if ((s = norm(r64, pd->rk, &bnorm)) != RBF_OK) return s;
+    {
+        double* flag = static_cast<double*>(ctx->hpinned) + 300;
+        RBF_CUDA_TRY(cudaMemcpyAsync(flag, pd->tmp, sizeof(double), cudaMemcpyDeviceToHost, st));
+        RBF_CUDA_TRY(cudaStreamSynchronize(st));
+        if (*flag != 0.0)
+            return set_err(ctx, RBF_ERR_ARG, "P^T P is singular: the points do not determine a linear polynomial");
+    }
+    double rn = bnorm;
+    rbf_solve_info inf{};
+    int state = kMaxIt, total_it = 0, outer = 0;
+    const int max_outer = std::max(ctx->max_refine, 1) + 8;
+    for (outer = 0;; ++outer) {
+        const double rel = bnorm > 0 ? rn / bnorm : 0.0;
+        if (rel <= tol || rn == 0.0) {
+            state = kConverged;
+            break;
+        }
+        if (outer >= max_outer) break;
+        const bool fp64 = ctx->prec == RBF_FP64;
+        const double itol = fp64 ? 0.5 * tol / rel : std::max(ctx->inner_tol, 0.5 * tol / rel);
+        int it = 0, ist = 0;
+        double irel = 0.0;
+        if (fp64)
+            s = run_cg<double, double>(ctx, r64, 1.0 / rn, false, itol, maxit, &it, &irel, &ist, st,
+                                       true, pd->rk);
+        else
+            s = run_cg<float, double>(ctx, r64, 1.0 / rn, false, itol, maxit, &it, &irel, &ist, st,
+                                      true, pd->rk);
+        if (s != RBF_OK) return s;
+        total_it += it;
+        if (ist == kBreakdown && it == 0) {
+            state = kBreakdown;
+            break;
+        }
+        if (fp64) {
+            const CgVec<double> v = cg_vectors<double>(ctx);
+            k_axpy_mixed<double><<<div_up(M, 256), 256, 0, st>>>(M, x64, v.x, rn, v.dinv);
+        } else {
+            const CgVec<float> v = cg_vectors<float>(ctx);
+            k_axpy_mixed<float><<<div_up(M, 256), 256, 0, st>>>(M, x64, v.x, rn, v.dinv);
+        }
+        k_poly_axpy<<<1, 1, 0, st>>>(pd, rn);
+        RBF_CUDA_TRY(cudaMemsetAsync(r64, 0, sizeof(double) * M, st));
+        if ((s = residual_run(ctx, x64, r64, false, st, true)) != RBF_OK) return s;
+        mask_zero(r64);
+        ctx->launches += 2;
+        double rn_new = 0.0;
+        if ((s = norm(r64, pd->rk, &rn_new)) != RBF_OK) return s;
+        const bool done = bnorm > 0 && rn_new / bnorm <= tol;
+        if (!done && !(rn_new < std::max(0.5, 2.0 * itol) * rn)) {
+            if (fp64) {   // no progress in FP64 either
+                rn = std::min(rn, rn_new);
+                ++outer;
+                break;
+            }
+            // promote: FP64 assembly (B, b, and again A^T P, P^T P, P^T h), FP64 inner solves
+            // from the refined iterate (kept across the assembly, which clears PolyDev)
+            double* kh = static_cast<double*>(ctx->hpinned) + 310;
+            RBF_CUDA_TRY(cudaMemcpyAsync(kh, pd->k64, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+            RBF_CUDA_TRY(cudaStreamSynchronize(st));
+            const double k0[3] = {kh[0], kh[1], kh[2]};
+            if ((s = assemble_run(ctx, ctx->kernel, RBF_FP64, st, true)) != RBF_OK) return s;
+            ctx->prec = RBF_FP64;
+            inf.promoted = 1;
+            if ((s = setup(RBF_FP64)) != RBF_OK) return s;
+            k_poly_setup<<<1, 1, 0, st>>>(pd);
+            ctx->launches += 1;
+            RBF_CUDA_TRY(cudaStreamSynchronize(st));
+            kh[0] = k0[0];
+            kh[1] = k0[1];
+            kh[2] = k0[2];
+            RBF_CUDA_TRY(cudaMemcpyAsync(pd->k64, kh, 3 * sizeof(double), cudaMemcpyHostToDevice, st));
+            RBF_CUDA_TRY(cudaMemsetAsync(r64, 0, sizeof(double) * M, st));
+            if ((s = residual_run(ctx, x64, r64, false, st, true)) != RBF_OK) return s;
+            mask_zero(r64);
+            if ((s = norm(r64, pd->rk, &rn_new)) != RBF_OK) return s;
+        }
+        rn = rn_new;
+    }
+    inf.iterations = total_it;
+    inf.refinements = outer;
+    inf.rel_residual = bnorm > 0 ? rn / bnorm : 0.0;
+    launch_scatter_orig(x64, bd.cperm, c, M, st);
+    k_poly_export<<<1, 1, 0, st>>>(pd, ctx->pxc, ctx->pyc, ctx->psx, ctx->psy, kout);
+    ctx->launches += 2;
     RBF_CUDA_TRY(cudaGetLastError());
     ctx->solved = true;
     RBF_CUDA_TRY(cudaMemcpyAsync(npin_h, npin_d, sizeof(int), cudaMemcpyDeviceToHost, st));
