@@ -625,17 +625,38 @@ __global__ void k_resid32(int M, const double* __restrict__ b, const float* __re
     if (i < M) r[i] = dinv32[i] == 0.0f ? 0.0 : b[i] - double(w[i]);
 }
 
-// ||v||^2 over unpinned rows into out[0] (single block, fixed order).
-__global__ void k_norm2(int M, const double* __restrict__ v, const float* __restrict__ dinv32,
-                        double* __restrict__ out) {
+// ||v||^2 over unpinned rows into out[0], in a fixed order: per-block partial sums (blocks of
+// kVecThreads rows strided over the vector) into part[], then one block adds them in block
+// order.
+constexpr int kNormBlocks = 304;
+__global__ void __launch_bounds__(kVecThreads)
+    k_norm2_part(int M, const double* __restrict__ v, const float* __restrict__ dinv32,
+                 double* __restrict__ part) {
     double s = 0.0;
-    for (int i = threadIdx.x; i < M; i += blockDim.x) {
+    for (int i = blockIdx.x * kVecThreads + threadIdx.x; i < M; i += gridDim.x * kVecThreads) {
         if (dinv32 && dinv32[i] == 0.0f) continue;
-        s += v[i] * v[i];
+        s = fma(v[i], v[i], s);
     }
     double a[1] = {s};
     block_sum<1>(a);
+    if (threadIdx.x == 0) part[blockIdx.x] = a[0];
+}
+__global__ void __launch_bounds__(kVecThreads)
+    k_norm2_total(int nb, const double* __restrict__ part, double* __restrict__ out) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nb; b += kVecThreads) s += part[b];
+    double a[1] = {s};
+    block_sum<1>(a);
     if (threadIdx.x == 0) out[0] = a[0];
+}
+
+// ||v||^2 (unpinned rows when dinv32 is given) into out (device), two launches.
+void launch_norm2(rbf_ctx* ctx, const double* v, const float* dinv32, double* out, cudaStream_t st) {
+    const int nb = std::max(1, std::min(kNormBlocks, div_up(ctx->M, kVecThreads)));
+    double* part = ctx->partial.as<double>();   // free between CG solves
+    k_norm2_part<<<nb, kVecThreads, 0, st>>>(ctx->M, v, dinv32, part);
+    k_norm2_total<<<1, kVecThreads, 0, st>>>(nb, part, out);
+    ctx->launches += 2;
 }
 
 // Persistent SpMV grid: as many blocks as can be resident (never more than the cells need).
@@ -960,8 +981,7 @@ rbf_status solve_run(rbf_ctx* ctx, double* c, int use_c0, double tol, int maxit,
         double* nrm_h = reinterpret_cast<double*>(static_cast<char*>(ctx->hpinned) + 3072);
         const float* dinv32 = ctx->dinv32.as<float>();
         // ||b|| over unpinned rows
-        k_norm2<<<1, 1024, 0, st>>>(M, ctx->bvec.as<double>(), dinv32, nrm_d);
-        ctx->launches += 1;
+        launch_norm2(ctx, ctx->bvec.as<double>(), dinv32, nrm_d, st);
         RBF_CUDA_TRY(cudaMemcpyAsync(nrm_h, nrm_d, sizeof(double), cudaMemcpyDeviceToHost, st));
         // With a start vector the first residual comes from the FP32 matrix, r = b - B32 x
         // (FP32 products and sums: relative error about 1e-6 of ||b||). It only has to be far
@@ -985,8 +1005,7 @@ rbf_status solve_run(rbf_ctx* ctx, double* c, int use_c0, double tol, int maxit,
         RBF_CUDA_TRY(cudaStreamSynchronize(st));
         const double bnorm = sqrt(nrm_h[0]);
         auto norm_r64 = [&](double* out) -> rbf_status {
-            k_norm2<<<1, 1024, 0, st>>>(M, r64, dinv32, nrm_d);
-            ctx->launches += 1;
+            launch_norm2(ctx, r64, dinv32, nrm_d, st);
             RBF_CUDA_TRY(cudaMemcpyAsync(nrm_h, nrm_d, sizeof(double), cudaMemcpyDeviceToHost, st));
             RBF_CUDA_TRY(cudaStreamSynchronize(st));
             *out = sqrt(nrm_h[0]);
@@ -1123,14 +1142,10 @@ rbf_status solve_poly_run(rbf_ctx* ctx, double* c, double* kout, double tol, int
     };
     // ||r||^2 over unpinned rows plus the three polynomial rows
     auto norm = [&](const double* vv, const double* vk, double* out) -> rbf_status {
-        if (ctx->prec == RBF_FP64) {
-            // k_norm2 masks with an FP32 row mask; with FP64 the pinned rows are zero already
-            k_norm2<<<1, 1024, 0, st>>>(M, vv, nullptr, nrm_d);
-        } else {
-            k_norm2<<<1, 1024, 0, st>>>(M, vv, ctx->dinv32.as<float>(), nrm_d);
-        }
+        // the FP32 row mask, or none: with FP64 the pinned rows are zero already
+        launch_norm2(ctx, vv, ctx->prec == RBF_FP64 ? nullptr : ctx->dinv32.as<float>(), nrm_d, st);
         k_poly_norm_add<<<1, 1, 0, st>>>(vk, nrm_d);
-        ctx->launches += 2;
+        ctx->launches += 1;
         RBF_CUDA_TRY(cudaMemcpyAsync(nrm_h, nrm_d, sizeof(double), cudaMemcpyDeviceToHost, st));
         RBF_CUDA_TRY(cudaStreamSynchronize(st));
         *out = sqrt(nrm_h[0]);
