@@ -44,8 +44,8 @@ sys.path.insert(0, ROOT)
 # while the captured kernel's source -- its function text and the shared SpMV device code --
 # is unchanged.
 CSRC = os.path.join(ROOT, "paper_1806_07884_gb300", "csrc")
-SPMV_TRAFFIC = {"sha": "7367e288530a83ff", "bytes": 170240 + 161024}
-BSPMV_TRAFFIC = {"sha": "9c9ea5673f28b93e", "per_alg_byte": (306878976 + 13672192) / 302918784}
+SPMV_TRAFFIC = {"sha": None, "bytes": None}
+BSPMV_TRAFFIC = {"sha": "5a6fa94a64c6ed56", "per_alg_byte": (229475840 + 15457536) / 148343644}
 
 
 def kernel_sha(fname, signature):
@@ -61,13 +61,14 @@ def kernel_sha(fname, signature):
 
 
 def spmv_traffic():
-    ok = kernel_sha("rbf_solve.cu", "k_spmv(Binned bd") == SPMV_TRAFFIC["sha"]
+    ok = SPMV_TRAFFIC["sha"] is not None and \
+        kernel_sha("rbf_solve.cu", "k_spmv(Binned bd") == SPMV_TRAFFIC["sha"]
     return SPMV_TRAFFIC["bytes"] if ok else None
 
 
 # The big-data SpMV is the single-system kernel on a B streamed from HBM; its DRAM traffic per
 # algorithmic byte comes from a capture of a smaller big-data system (B still far beyond L2).
-BIG_SPMV_TRAFFIC = {"sha": "7367e288530a83ff", "per_alg_byte": (254805504 + 8428800) / 256737316,
+BIG_SPMV_TRAFFIC = {"sha": "e830f8a7a1cd60e2", "per_alg_byte": (187650304 + 7747072) / 121659036,
                     "note": "scaled from a 5M x 500k big-data capture"}
 
 
@@ -369,6 +370,29 @@ def bench_batched(args, rank, dev, stream, flush, hbm, peak_source):
     ms, info, tinfo = timed(args.prec, args.tol, max(2, min(args.steps, 3)))
     launches = (ctx.launch_count() - launches0) // max(2, min(args.steps, 3))
     c_fast = cbuf.clone()
+    # roofline of the batched SpMV (every tile running), timed on its stream, on the
+    # precision of the timed path (a step that promoted tiles leaves an FP64 B: assemble again)
+    if ctx.prec != args.prec:
+        step(args.prec, args.tol)
+    lay = ctx.layout()
+    vb = lay["value_bytes"]
+    ctx.bench_spmv(5)
+    s0 = torch.cuda.Event(enable_timing=True)
+    s1 = torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    ctx.bench_spmv(30)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    spmv_ms = s0.elapsed_time(s1) / 30
+    alg, stored, lst = spmv_bytes(ctx, Mtot, vb)
+    ach = alg / (spmv_ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "kernel": f"k_bcg_spmv<{'float' if vb == 4 else 'double'}>",
+            "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s", "frac": round(ach / hbm, 4),
+            "traffic": bspmv_traffic(alg), "traffic_note": "scaled from a 128-tile capture",
+            "algorithmic_bytes": alg, "stored_bytes": stored,
+            "stored_over_algorithmic": round(stored / alg, 4),
+            "upper_nonzeros": lst["nonzeros"], "stored_values": lst["stored_values"],
+            "launch_ms": round(spmv_ms, 5), "peak_source": peak_source}
     learned = None
     if args.learned:
         from paper_1806_07884_gb300 import warmstart
@@ -411,26 +435,6 @@ def bench_batched(args, rank, dev, stream, flush, hbm, peak_source):
     torch.cuda.synchronize()
     phases = {n: round(ev[k].elapsed_time(ev[k + 1]), 3)
               for k, n in enumerate(["bin", "assemble", "solve"])}
-    # roofline of the batched SpMV (FP32 B, every tile running), timed on its stream
-    lay = ctx.layout()
-    vb = lay["value_bytes"]
-    ctx.bench_spmv(5)
-    s0 = torch.cuda.Event(enable_timing=True)
-    s1 = torch.cuda.Event(enable_timing=True)
-    s0.record(stream)
-    ctx.bench_spmv(30)
-    s1.record(stream)
-    torch.cuda.synchronize()
-    spmv_ms = s0.elapsed_time(s1) / 30
-    alg, stored, lst = spmv_bytes(ctx, Mtot, vb)
-    ach = alg / (spmv_ms * 1e-3) / 1e9
-    roof = {"bound": "hbm", "kernel": f"k_bcg_spmv<{'float' if vb == 4 else 'double'}>",
-            "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s", "frac": round(ach / hbm, 4),
-            "traffic": bspmv_traffic(alg), "traffic_note": "scaled from a 128-tile capture",
-            "algorithmic_bytes": alg, "stored_bytes": stored,
-            "stored_over_algorithmic": round(stored / alg, 4),
-            "upper_nonzeros": lst["nonzeros"], "stored_values": lst["stored_values"],
-            "launch_ms": round(spmv_ms, 5), "peak_source": peak_source}
     out = {"workload": f"{args.tiles} tiles, N log-uniform in [2000, 200000], M = N/10, "
                        f"Wendland phi_3,1, K=30, sum N = {Ntot}, sum M = {Mtot}",
            "value": Ntot / (ms * 1e-3), "unit": "points/s", "ms_per_step": round(ms, 3),
@@ -528,7 +532,10 @@ def bench_bigdata(args, rank, dev, stream, flush, hbm, peak_source):
     torch.cuda.synchronize()
     phases = {nm: round(ev[i].elapsed_time(ev[i + 1]), 3)
               for i, nm in enumerate(["bin", "assemble", "solve", "eval"])}
-    # roofline of the solver's SpMV (B streamed from HBM at this size), on its stream
+    # roofline of the solver's SpMV (B streamed from HBM at this size), on its stream, on the
+    # precision of the timed path (a promoted step leaves an FP64 B: assemble again)
+    if ctx.prec != args.prec:
+        step(args.prec, args.tol)
     lay = ctx.layout()
     vb = lay["value_bytes"]
     alg, stored, lst = spmv_bytes(ctx, M, vb)

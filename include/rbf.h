@@ -372,6 +372,12 @@ rbf_status rbf_mlp_train_step(rbf_ctx* ctx, float* params, float* m, float* v, i
  * c0_j = sigma * network(features of centre j), sigma per tile for a batch. Asynchronous. */
 rbf_status rbf_warm_start(rbf_ctx* ctx, const float* params, double* c0, void* stream);
 
+/* Training targets of the network for the binned system and weights c (DEVICE, M doubles,
+ * caller's order): target[j] = c_j / sigma, sigma as for rbf_features (per tile for a batch);
+ * target: DEVICE, M floats, caller's order. The inverse of rbf_warm_start's scaling.
+ * Asynchronous. */
+rbf_status rbf_mlp_targets(rbf_ctx* ctx, const double* c, float* target, void* stream);
+
 /* Evaluation with no allocation at all (the paper has no counterpart; this is a service to
  * callers that cannot allocate device memory where they need the surface -- e.g. code that
  * runs while its own memory pool is locked or inside a fixed device-memory budget, or a

@@ -315,6 +315,15 @@ class Context:
         self._check(s, "rbf_warm_start")
         return c0
 
+    def mlp_targets(self, c, out=None, stream=None):
+        """The network's training targets t_j = c_j / sigma (caller order, float32)."""
+        torch = _torch()
+        t = out if out is not None else torch.empty(self.M, dtype=torch.float32, device=c.device)
+        s = self.lib.rbf_mlp_targets(self._h, _dptr(c, "c"), C.c_void_p(t.data_ptr()),
+                                     self._stream(stream))
+        self._check(s, "rbf_mlp_targets")
+        return t
+
     def autotune(self, stream=None):
         """Time the batched CG loop's launch configurations and keep the fastest."""
         self._check(self.lib.rbf_autotune(self._h, self._stream(stream)), "rbf_autotune")

@@ -80,6 +80,7 @@ SIGNATURES = {
     "rbf_mlp_forward": (_I, [_P, _P, _P, _I64, _P, _P]),
     "rbf_mlp_train_step": (_I, [_P, _P, _P, _P, _I, _D, _P, _P, _P, _I64, _P, _P, _P]),
     "rbf_warm_start": (_I, [_P, _P, _P, _P]),
+    "rbf_mlp_targets": (_I, [_P, _P, _P, _P]),
     "rbf_get_tuning": (_I, [_P, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I), C.POINTER(_D)]),
 }
 

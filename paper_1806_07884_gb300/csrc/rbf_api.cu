@@ -77,7 +77,7 @@ Binned view(const rbf_ctx* ctx) {
     v.pv = ctx->pv.as<float>();
     v.cperm = ctx->cperm.as<int>();
     v.rmeta = ctx->rmeta.as<RowMeta>();
-    v.gdesc = ctx->gdesc.as<GroupDesc>();
+    v.gdesc = ctx->gdesc.as<GroupRec>();
     v.ngroup = ctx->ngroup;
     v.bjoff = ctx->bjoff.as<int64_t>();
     v.crow = ctx->crow.as<int4>();
@@ -370,6 +370,14 @@ rbf_status rbf_warm_start(rbf_ctx* ctx, const float* params, double* c0, void* s
     if (!params || !c0) return set_err(ctx, RBF_ERR_ARG, "null pointer argument");
     DeviceGuard dg(ctx->device);
     return warm_start_run(ctx, params, c0, as_stream(stream));
+}
+
+rbf_status rbf_mlp_targets(rbf_ctx* ctx, const double* c, float* target, void* stream) {
+    if (!ctx) return RBF_ERR_ARG;
+    if (!ctx->binned) return set_err(ctx, RBF_ERR_ARG, "rbf_mlp_targets before rbf_bin / rbf_bin_tiles");
+    if (!c || !target) return set_err(ctx, RBF_ERR_ARG, "null pointer argument");
+    DeviceGuard dg(ctx->device);
+    return mlp_targets_run(ctx, c, target, as_stream(stream));
 }
 
 rbf_status rbf_autotune(rbf_ctx* ctx, void* stream) {

@@ -245,13 +245,13 @@ __global__ void k_tile_scatter(const TileDev* __restrict__ td, int which,
 }
 
 // Each tile's range in the group list and in the sorted rows, from the ends of its runs.
-__global__ void k_tile_ranges(const GroupDesc* __restrict__ gdesc, int ngroup,
+__global__ void k_tile_ranges(const GroupRec* __restrict__ gdesc, int ngroup,
                               const int4* __restrict__ crow, int M, TileWork tw) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < ngroup) {
-        const int t = crow[gdesc[i].r0].w;
-        if (i == 0 || crow[gdesc[i - 1].r0].w != t) tw.clb[t] = i;
-        if (i == ngroup - 1 || crow[gdesc[i + 1].r0].w != t) tw.cle[t] = i + 1;
+        const int t = crow[gdesc[i].d.r0].w;
+        if (i == 0 || crow[gdesc[i - 1].d.r0].w != t) tw.clb[t] = i;
+        if (i == ngroup - 1 || crow[gdesc[i + 1].d.r0].w != t) tw.cle[t] = i + 1;
     }
     if (i < M) {
         const int t = crow[i].w;
@@ -551,17 +551,22 @@ __global__ void __launch_bounds__(kSpmvWarps * 32, sizeof(T) == 4 ? 3 : 2)
     int q = blockIdx.x * kSpmvWarps + wid;
     if (q >= n) return;
     int4 it = items[q];
-    // the next group's description is loaded while this group's rows stream: this item's
-    // next group, else the next item's first
-    GroupStage<T> cur = stage_group<T>(bd.gdesc, bd.rmeta, u, it.x, lane);
+    // the next group's record is loaded while this group's rows stream: this item's next
+    // group, else the next item's first
+    stage_group(bd.gdesc, it.x, gsm[wid], 0, lane);
+    int b = 0;
     for (; q < n; q += nw) {
         const int4 next = q + nw < n ? items[q + nw] : make_int4(0, 0, 0, 0);
         T acc = T(0);   // this lane's share of the item's delta (warp sum in T)
-        for (int g = it.x; g < it.y; ++g) {
+        for (int g = it.x; g < it.y; ++g, b ^= 1) {
             const int gn = g + 1 < it.y ? g + 1 : (q + nw < n ? next.x : -1);
-            const GroupStage<T> nxt = gn >= 0 ? stage_group<T>(bd.gdesc, bd.rmeta, u, gn, lane) : cur;
-            acc += spmv_group<T>(cur, B, u, w, bd.M, lane, gsm[wid]);
-            cur = nxt;
+            if (gn >= 0) {
+                stage_group(bd.gdesc, gn, gsm[wid], b ^ 1, lane);
+                group_wait<1>();
+            } else {
+                group_wait<0>();
+            }
+            acc += spmv_group<T>(b, B, u, w, bd.M, lane, gsm[wid]);
         }
         const T sum = warp_sum<T>(acc);
         if (lane == 0 && sum != T(0)) atomicAdd(&dlP[it.z], double(sum));
@@ -1168,7 +1173,7 @@ rbf_status tiles_group_ranges(rbf_ctx* ctx, cudaStream_t st) {
     if ((s = ensure(ctx, ctx->twork, L.total, st)) != RBF_OK) return s;
     RBF_CUDA_TRY(cudaMemsetAsync(ctx->twork.p, 0, L.ranges_end, st));
     k_tile_ranges<<<std::max(1, div_up(std::max(ctx->ngroup, ctx->M), 256)), 256, 0, st>>>(
-        ctx->gdesc.as<GroupDesc>(), ctx->ngroup, ctx->crow.as<int4>(), ctx->M, work_view(ctx));
+        ctx->gdesc.as<GroupRec>(), ctx->ngroup, ctx->crow.as<int4>(), ctx->M, work_view(ctx));
     ctx->launches += 1;
     RBF_CUDA_TRY(cudaGetLastError());
     return RBF_OK;

@@ -349,7 +349,7 @@ __global__ void k_group_count(Grid g, const int* __restrict__ cstart, int* __res
 // One thread per row group: its rows and the union of their column ranges per segment.
 __global__ void k_groups(Grid g, int ngroup, const int* __restrict__ cstart,
                          const int* __restrict__ gstart, const RowMeta* __restrict__ rmeta,
-                         GroupDesc* __restrict__ gdesc) {
+                         GroupRec* __restrict__ gdesc) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= ngroup) return;
     int a = 0, b = g.gy;            // cell row of the group: last b with gstart[b] <= q
@@ -382,7 +382,9 @@ __global__ void k_groups(Grid g, int ngroup, const int* __restrict__ cstart,
     d.q1 = hi[1] > lo[1] ? (hi[1] - lo[1]) >> 2 : 0;
     d.lo2 = hi[2] > lo[2] ? lo[2] : 0;
     d.q2 = hi[2] > lo[2] ? (hi[2] - lo[2]) >> 2 : 0;
-    gdesc[q] = d;
+    GroupRec& rec = gdesc[q];
+    rec.d = d;
+    for (int i = 0; i < kGroupRows; ++i) rec.rows[i] = i < n ? rmeta[r0 + i] : RowMeta{0, 0, 0, 0};
 }
 
 __global__ void k_work_fill(int ncell, const int* __restrict__ pstart,
@@ -531,10 +533,10 @@ rbf_status bin_run(rbf_ctx* ctx, const double* cx, const double* cy, const doubl
     if (hs[4])
         return set_err(ctx, RBF_ERR_LIMIT, "more than 4092 centres within 2R of a centre in one cell row");
     if (hs[5]) return set_err(ctx, RBF_ERR_LIMIT, "stored B larger than 2^34 values");
-    ENS(gdesc, sizeof(GroupDesc) * std::max(ctx->ngroup, 1));
+    ENS(gdesc, sizeof(GroupRec) * std::max(ctx->ngroup, 1));
     k_groups<<<div_up(std::max(ctx->ngroup, 1), T), T, 0, st>>>(
         g, ctx->ngroup, ctx->cstart.as<int>(), ctx->gstart.as<int>(), ctx->rmeta.as<RowMeta>(),
-        ctx->gdesc.as<GroupDesc>());
+        ctx->gdesc.as<GroupRec>());
     ctx->launches += 1;
     if (ctx->T > 0 && (s = tiles_group_ranges(ctx, st)) != RBF_OK) return s;
     ENS(work, sizeof(int4) * std::max(ctx->nwork, 1));

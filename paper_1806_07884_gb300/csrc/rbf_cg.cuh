@@ -157,91 +157,80 @@ __device__ __forceinline__ void atomic_add4(T* y, int t, int M, const typename V
     if (t + 3 < M && v.w != T(0)) atomicAdd(y + t + 3, v.w);
 }
 
-// What a warp needs of a row group before its values stream: the group's description, the
-// RowMeta of row lane (lanes < kGroupRows) and x of that row. Loaded one group ahead so the
-// round trip overlaps the previous group.
-template <typename T>
-struct GroupStage {
-    GroupDesc gd;
-    int4 meta;
-    T xrow;
-};
-
-__device__ __forceinline__ GroupDesc load_group(const GroupDesc* d) {
-    GroupDesc v;
-    const int4* p = reinterpret_cast<const int4*>(d);
-    int4* q = reinterpret_cast<int4*>(&v);
-    q[0] = __ldg(p);
-    q[1] = __ldg(p + 1);
-    return v;
-}
-
-template <typename T>
-__device__ __forceinline__ GroupStage<T> stage_group(const GroupDesc* __restrict__ gdesc,
-                                                     const RowMeta* __restrict__ rmeta,
-                                                     const T* x, int g, int lane) {
-    GroupStage<T> st;
-    st.gd = load_group(gdesc + g);
-    const bool mine = lane < st.gd.n;
-    st.meta = mine ? __ldg(reinterpret_cast<const int4*>(rmeta + st.gd.r0 + lane))
-                   : make_int4(0, 0, 0, 0);
-    st.xrow = mine ? ldcg(x + st.gd.r0 + lane) : T(0);
-    return st;
-}
-
 // Per row of a group and segment, what a lane needs to find the value of its column t:
 // lo <= t < lo + len, value at Bg[rel + t] with Bg the group's first stored value.
 struct SegSlot {
     int lo, len, rel, pad;
 };
-// Shared memory of one warp for spmv_group.
+// Shared memory of one warp for spmv_group: two record slots (the current group's, and the
+// next group's arriving) and the current group's segment slots.
 struct GroupSmem {
+    int4 rec[2][kGroupRecInt4];
     SegSlot seg[kGroupRows][3];
 };
 
+// Start copying group g's record (GroupRec: description and the rows' RowMeta) into record
+// slot b of the warp's shared memory, one 16-byte asynchronous copy per lane for lanes <
+// kGroupRecInt4, as one commit group of every lane; group_wait makes it visible.
+__device__ __forceinline__ void stage_group(const GroupRec* __restrict__ gdesc, int g,
+                                            GroupSmem& sm, int b, int lane) {
+    if (lane < kGroupRecInt4) {
+        const unsigned dst = unsigned(__cvta_generic_to_shared(&sm.rec[b][lane]));
+        const int4* src = reinterpret_cast<const int4*>(gdesc + g) + lane;
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+// Wait for all but the `pending` most recent commit groups of this lane, then make the warp's
+// copies visible to every lane.
+template <int pending>
+__device__ __forceinline__ void group_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(pending) : "memory");
+    __syncwarp();
+}
+
 // y += B x over the stored rows of one row group (warp-cooperative; all 32 lanes; see
-// RowMeta and GroupDesc). The warp sweeps the union of the rows' column ranges in column
-// quads, lane l taking quad 32 q + l of the union in pass q (one pass for unions up to 128
-// columns); for each of the group's rows the lane loads the row's four values at its columns
-// (one aligned 4-vector load, skipped where the columns are outside the row's own range), and
-// every value B[s][t] feeds both products:
+// RowMeta and GroupDesc), given its record staged by stage_group. The warp sweeps the union of
+// the rows' column ranges in column quads, lane l taking quad 32 q + l of the union in pass q
+// (one pass for unions up to 128 columns); for each of the group's rows the lane loads the
+// row's four values at its columns (one aligned 4-vector load, skipped where the columns are
+// outside the row's own range), and every value B[s][t] feeds both products:
 //   row sums    y[s] += sum_t B[s][t] x[t]   (8 rows in registers, butterfly reduction)
 //   column sums y[t] += sum_s B[s][t] x[s]   (the lane's four columns, summed over the rows,
 //                                             added with one 4-vector atomic)
 // The halved diagonal makes the two sums count it once.
 // Returns this lane's share (in T) of x^T B x: sum_s x[s] rowsum[s] + sum_t colsum[t] x[t].
 template <typename T>
-__device__ T spmv_group(const GroupStage<T>& st, const T* __restrict__ B, const T* x, T* y,
-                        int M, int lane, GroupSmem& sm) {
+__device__ T spmv_group(int b, const T* __restrict__ B, const T* x, T* y, int M, int lane,
+                        GroupSmem& sm) {
     using R4 = typename V4<T>::type;
-    const GroupDesc& gd = st.gd;
-    const int n = gd.n, r0 = gd.r0;
+    const int4 h0 = sm.rec[b][0], h1 = sm.rec[b][1];
+    const int r0 = h0.x, n = h0.y;
+    const int lo0 = h0.z, Q0 = h0.w, lo1 = h1.x, Q1 = h1.y, lo2 = h1.z, QT = h0.w + h1.y + h1.w;
     // the group's first stored value (row r0, column r0 & ~3)
-    const long long gbase = 4LL * unsigned(__shfl_sync(kFull, st.meta.x, 0));
-    __syncwarp();
+    const long long gbase = 4LL * unsigned(sm.rec[b][2].x);
+    // x of row lane, in flight with the values below
+    const T xrow = lane < n ? ldcg(x + r0 + lane) : T(0);
     if (lane < kGroupRows) {
         SegSlot e[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) e[k] = SegSlot{0, 0, 0, 0};
         if (lane < n) {
+            const int4 meta = sm.rec[b][2 + lane];
             const int s = r0 + lane;
-            const unsigned int len = unsigned(st.meta.w);
-            const int rel = int(4LL * unsigned(st.meta.x) - gbase);
+            const unsigned int len = unsigned(meta.w);
+            const int rel = int(4LL * unsigned(meta.x) - gbase);
             const int l0 = 4 * seg_quads(len, 0), l1 = 4 * seg_quads(len, 1);
             const int l2 = 4 * seg_quads(len, 2);
             e[0] = SegSlot{s & ~3, l0, rel - (s & ~3), 0};
-            e[1] = SegSlot{st.meta.y, l1, rel + l0 - st.meta.y, 0};
-            e[2] = SegSlot{st.meta.z, l2, rel + l0 + l1 - st.meta.z, 0};
+            e[1] = SegSlot{meta.y, l1, rel + l0 - meta.y, 0};
+            e[2] = SegSlot{meta.z, l2, rel + l0 + l1 - meta.z, 0};
         }
 #pragma unroll
         for (int k = 0; k < 3; ++k) sm.seg[lane][k] = e[k];
     }
-    T xg[kGroupRows];
-#pragma unroll
-    for (int i = 0; i < kGroupRows; ++i) xg[i] = __shfl_sync(kFull, st.xrow, i);
     __syncwarp();
     const T* Bg = B + gbase;
-    const int Q0 = gd.q0, Q1 = gd.q1, QT = gd.q0 + gd.q1 + gd.q2;
     T rp[kGroupRows];
 #pragma unroll
     for (int i = 0; i < kGroupRows; ++i) rp[i] = T(0);
@@ -250,8 +239,7 @@ __device__ T spmv_group(const GroupStage<T>& st, const T* __restrict__ B, const 
         const int q = qq + lane;
         const bool act = q < QT;
         const int k = q < Q0 ? 0 : (q < Q0 + Q1 ? 1 : 2);
-        const int col = k == 0 ? gd.lo0 + 4 * q
-                               : (k == 1 ? gd.lo1 + 4 * (q - Q0) : gd.lo2 + 4 * (q - Q0 - Q1));
+        const int col = k == 0 ? lo0 + 4 * q : (k == 1 ? lo1 + 4 * (q - Q0) : lo2 + 4 * (q - Q0 - Q1));
         const R4 xt = act ? ldx4<T>(x, col, M) : R4{T(0), T(0), T(0), T(0)};
         // every row's four values first (kGroupRows loads in flight), then the products
         R4 v[kGroupRows];
@@ -264,11 +252,12 @@ __device__ T spmv_group(const GroupStage<T>& st, const T* __restrict__ B, const 
         R4 ca{T(0), T(0), T(0), T(0)};
 #pragma unroll
         for (int i = 0; i < kGroupRows; ++i) {
+            const T xi = __shfl_sync(kFull, xrow, i);   // x of row i
             rp[i] = fma(v[i].x, xt.x, fma(v[i].y, xt.y, fma(v[i].z, xt.z, fma(v[i].w, xt.w, rp[i]))));
-            ca.x = fma(v[i].x, xg[i], ca.x);
-            ca.y = fma(v[i].y, xg[i], ca.y);
-            ca.z = fma(v[i].z, xg[i], ca.z);
-            ca.w = fma(v[i].w, xg[i], ca.w);
+            ca.x = fma(v[i].x, xi, ca.x);
+            ca.y = fma(v[i].y, xi, ca.y);
+            ca.z = fma(v[i].z, xi, ca.z);
+            ca.w = fma(v[i].w, xi, ca.w);
         }
         if (act) {
             // (a widening slot past the last column holds a zero, but 0 * x can be NaN when x
@@ -279,11 +268,12 @@ __device__ T spmv_group(const GroupStage<T>& st, const T* __restrict__ B, const 
     }
     const T tot = butterfly8(rp, lane);        // lanes 4r .. 4r+3 hold row r
     const int r = (lane >> 2) & 7;
-    const T xr = __shfl_sync(kFull, st.xrow, r);
+    const T xr = __shfl_sync(kFull, xrow, r);
     if ((lane & 3) == 0 && r < n) {
         atomicAdd(y + r0 + r, tot);
         dot = fma(tot, xr, dot);
     }
+    __syncwarp();   // the segment slots and this record slot are free for the next group
     return dot;
 }
 

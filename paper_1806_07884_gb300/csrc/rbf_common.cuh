@@ -148,6 +148,14 @@ struct __align__(16) GroupDesc {
     int lo2, q2;        // seg 2 union
 };
 
+// What the SpMV reads of a row group before its values: the GroupDesc and the RowMeta of its
+// rows (zeros past n) in one 160-byte record, fetched by ten lanes in one round trip.
+constexpr int kGroupRecInt4 = 2 + kGroupRows;
+struct __align__(16) GroupRec {
+    GroupDesc d;
+    RowMeta rows[kGroupRows];
+};
+
 // Offset of B[s][t] (s <= t, t in band(s) + k) in the value array, or -1 if the row keeps no
 // slot for t.
 __host__ __device__ __forceinline__ long long upper_slot(const RowMeta& rm, int s, int t, int k) {
@@ -189,7 +197,7 @@ struct Binned {
     const float* pv;
     const int* cperm;       // [M] sorted -> caller centre index
     const RowMeta* rmeta;   // [M] stored row of B of each sorted centre
-    const GroupDesc* gdesc; // [ngroup] row groups, in row order
+    const GroupRec* gdesc;  // [ngroup] row groups (description and rows' RowMeta), row order
     int ngroup;
     const int64_t* bjoff;   // [ncell+1] offset of each cell's inverse diagonal block
     const int4* crow;       // [M] {first sorted centre, centre count, cell, tile} of each centre's cell

@@ -189,6 +189,7 @@ rbf_status features_run(rbf_ctx* ctx, float* feat, double* sigma_out, cudaStream
 rbf_status mlp_forward_run(rbf_ctx* ctx, const float* params, const float* feat, int64_t n, float* y,
                            cudaStream_t st);
 rbf_status warm_start_run(rbf_ctx* ctx, const float* params, double* c0, cudaStream_t st);
+rbf_status mlp_targets_run(rbf_ctx* ctx, const double* c, float* target, cudaStream_t st);
 rbf_status mlp_step_run(rbf_ctx* ctx, float* params, float* m, float* v, int step, double lr,
                         const float* feat, const float* target, const int* idx, int64_t n,
                         float* grad, double* loss, cudaStream_t st);

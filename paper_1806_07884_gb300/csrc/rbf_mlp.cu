@@ -233,6 +233,16 @@ __global__ void k_warm_scale(Binned bd, const double* __restrict__ sigma, const 
     c0[j] = sigma[bd.crow[s].w] * double(y[j]);
 }
 
+// The network's training target of every centre: t[cperm[s]] = c[cperm[s]] / sigma_tile
+// (c in the caller's order), the inverse of k_warm_scale.
+__global__ void k_mlp_targets(Binned bd, const double* __restrict__ sigma,
+                              const double* __restrict__ c, float* __restrict__ t) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= bd.M) return;
+    const int j = bd.cperm[s];
+    t[j] = float(c[j] / sigma[bd.crow[s].w]);
+}
+
 constexpr int kGS = 64;           // samples per gradient block
 constexpr int kGT = 4 * kGS;      // threads: four per sample
 constexpr int kPad = NH + 1;      // padded activation rows
@@ -400,6 +410,16 @@ rbf_status mlp_forward_run(rbf_ctx* ctx, const float* params, const float* feat,
                            cudaStream_t st) {
     if (n <= 0) return RBF_OK;
     k_mlp_forward<<<div_up(n, kFwdThreads), kFwdThreads, 0, st>>>(params, feat, n, y);
+    ctx->launches += 1;
+    RBF_CUDA_TRY(cudaGetLastError());
+    return RBF_OK;
+}
+
+rbf_status mlp_targets_run(rbf_ctx* ctx, const double* c, float* target, cudaStream_t st) {
+    // the height scales of the binned system (tiles)
+    rbf_status s = height_scales(ctx, st);
+    if (s != RBF_OK) return s;
+    k_mlp_targets<<<div_up(ctx->M, 256), 256, 0, st>>>(view(ctx), ctx->sigma.as<double>(), c, target);
     ctx->launches += 1;
     RBF_CUDA_TRY(cudaGetLastError());
     return RBF_OK;

@@ -58,7 +58,9 @@ struct CgScalars {
 
 namespace {
 
-constexpr int kVecThreads = 256;
+// Threads per block of the CG vector kernels: 512, so a solve of 100 k rows runs ~200 blocks,
+// whose per-block partial sums every update block's prologue adds in one batch of loads.
+constexpr int kVecThreads = 512;
 
 // Stores this block's NV partial sums; returns true in the single last block to finish,
 // whose thread 0 then holds the totals, summed in block order, in tot[].
@@ -101,12 +103,16 @@ __global__ void __launch_bounds__(kSpmvWarps * 32, sizeof(T) == 4 ? 3 : 2)
     const int nw = gridDim.x * kSpmvWarps;
     int q = blockIdx.x * kSpmvWarps + wid;
     if (q >= bd.ngroup) return;
-    // the next group's description is loaded while this group's rows stream
-    GroupStage<T> cur = stage_group<T>(bd.gdesc, bd.rmeta, x, q, lane);
-    for (; q < bd.ngroup; q += nw) {
-        const GroupStage<T> nxt = q + nw < bd.ngroup ? stage_group<T>(bd.gdesc, bd.rmeta, x, q + nw, lane) : cur;
-        spmv_group<T>(cur, B, x, y, bd.M, lane, gsm[wid]);
-        cur = nxt;
+    // the next group's record is copied while this group's rows stream
+    stage_group(bd.gdesc, q, gsm[wid], 0, lane);
+    for (int b = 0; q < bd.ngroup; q += nw, b ^= 1) {
+        if (q + nw < bd.ngroup) {
+            stage_group(bd.gdesc, q + nw, gsm[wid], b ^ 1, lane);
+            group_wait<1>();
+        } else {
+            group_wait<0>();
+        }
+        spmv_group<T>(b, B, x, y, bd.M, lane, gsm[wid]);
     }
 }
 
@@ -131,13 +137,17 @@ __global__ void __launch_bounds__(kSpmvWarps * 32, sizeof(T) == 4 ? 3 : 2)
     const int nw = gridDim.x * kSpmvWarps;
     T d = T(0);
     if (gw < bd.ngroup) {
-        // the next group's description is loaded while this group's rows stream
-        GroupStage<T> cur = stage_group<T>(bd.gdesc, bd.rmeta, u, gw, lane);
-        for (int q = gw; q < bd.ngroup; q += nw) {
-            const GroupStage<T> nxt =
-                q + nw < bd.ngroup ? stage_group<T>(bd.gdesc, bd.rmeta, u, q + nw, lane) : cur;
-            d += spmv_group<T>(cur, B, u, w, bd.M, lane, gsm[wid]);
-            cur = nxt;
+        // the next group's record is copied while this group's rows stream
+        stage_group(bd.gdesc, gw, gsm[wid], 0, lane);
+        int b = 0;
+        for (int q = gw; q < bd.ngroup; q += nw, b ^= 1) {
+            if (q + nw < bd.ngroup) {
+                stage_group(bd.gdesc, q + nw, gsm[wid], b ^ 1, lane);
+                group_wait<1>();
+            } else {
+                group_wait<0>();
+            }
+            d += spmv_group<T>(b, B, u, w, bd.M, lane, gsm[wid]);
         }
     }
     d = warp_sum<T>(d);
@@ -177,7 +187,8 @@ __global__ void __launch_bounds__(kVecThreads)
     const T* __restrict__ wP = P ? v.w[1] : v.w[0];
     // the first chunk's row values, loaded before the prologue so that their latency overlaps it
     const int i_first = blockIdx.x * kVecThreads + threadIdx.x;
-    T f_d = T(0), f_w = T(0), f_s = T(0), f_p = T(0), f_u = T(0), f_r = T(0);
+    T f_d = T(0), f_w = T(0), f_s = T(0), f_p = T(0), f_u = T(0), f_r = T(0), f_x = T(0);
+    int4 f_cm = make_int4(0, 0, 0, 0);
     if (i_first < M) {
         f_d = v.dinv[i_first];
         f_w = wP[i_first];
@@ -185,6 +196,8 @@ __global__ void __launch_bounds__(kVecThreads)
         f_p = v.p[i_first];
         f_u = v.u[i_first];
         f_r = rP[i_first];
+        f_x = v.x[i_first];
+        f_cm = bd.crow[i_first];
     }
     if (threadIdx.x < 32) {
         const int lane = threadIdx.x;
@@ -336,14 +349,14 @@ __global__ void __launch_bounds__(kVecThreads)
             ri = di == T(0) ? T(0) : fma(-ta, si, first ? f_r : rP[i]);
             sQ[i] = si;
             v.p[i] = pi;
-            v.x[i] = fma(ta, pi, v.x[i]);
+            v.x[i] = fma(ta, pi, first ? f_x : v.x[i]);
             rQ[i] = ri;
             wQ[i] = T(0);
         }
         rsm[threadIdx.x] = ri;
         __syncthreads();
         if (valid) {
-            const int4 cm = bd.crow[i];
+            const int4 cm = i == i_first ? f_cm : bd.crow[i];
             // rows of pinned centres carry zeros in the inverse block, so r_j need no mask
             const T ui = apply_prec<T>(bd, v.bjinv, cm, i, di, ri, [&](int j) {
                 const int o = j - base;
@@ -674,7 +687,7 @@ int spmv_grid_T(rbf_ctx* ctx) {
     return std::max(1, std::min(per_sm * std::max(sms, 1), div_up(ctx->ngroup, kSpmvWarps)));
 }
 int vec_grid(const rbf_ctx* ctx) {
-    return std::max(1, std::min(div_up(ctx->M, kVecThreads), 152 * 8));
+    return std::max(1, std::min(div_up(ctx->M, kVecThreads), 152 * 4));
 }
 
 // The polynomial rows of Eq. 10 in a CG solve of precision T (all null without them).

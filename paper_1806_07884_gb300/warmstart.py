@@ -34,10 +34,8 @@ def training_set(problems, kernel="w31", tol=1e-10, ctx=None, device=0):
     ctx.bin_tiles(tiles, *[torch.as_tensor(a).to(dev) for a in (cx, cy, px, py, hh)])
     ctx.assemble(kernel, "fp64")
     c, info, tinfo = ctx.solve_tiles(tol=tol)
-    feat, sig = ctx.features()
-    owner = np.concatenate([np.full(t["M"], k) for k, t in enumerate(tiles)])   # tile of centre
-    sig_c = sig[torch.as_tensor(owner, device=dev)]
-    target = (c / sig_c).float()
+    feat, _ = ctx.features()
+    target = ctx.mlp_targets(c)
     return feat, target, ctx
 
 
