@@ -61,6 +61,45 @@ struct LocalCells {
     int n;
 };
 
+// off[a] = cnt[0] + ... + cnt[a-1] for a < n and off[n] = the total (shared arrays), by the
+// whole block; n may exceed the block size.
+__device__ void block_scan_counts(const int* cnt, int n, int* off) {
+    __shared__ int wtot[kThreads / 32];
+    __shared__ int carry;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < n; base += kThreads) {
+        const int a = base + threadIdx.x;
+        const int v = a < n ? cnt[a] : 0;
+        int x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wtot[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            int t = lane < kThreads / 32 ? wtot[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < kThreads / 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, t, o);
+                if (lane >= o) t += y;
+            }
+            if (lane < kThreads / 32) wtot[lane] = t;
+        }
+        __syncthreads();
+        const int excl = carry + (w > 0 ? wtot[w - 1] : 0) + x - v;
+        if (a < n) off[a] = excl;
+        __syncthreads();
+        if (threadIdx.x == kThreads - 1) carry = excl + v;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) off[n] = carry;
+    __syncthreads();
+}
+
 // Thread 0 describes the 3x3 block of cells around point cell `cell`.
 __device__ void describe_cells(const Binned& bd, int cell, LocalCells& lc) {
     const Grid& g = bd.g;
@@ -338,7 +377,7 @@ __global__ void __launch_bounds__(kThreads) k_assemble(Binned bd, const int4* __
 // With the polynomial (pa): e_p also subtracts k . (u_p, v_p, 1), r_k = sum_p e_p (u_p, v_p, 1)
 // is added into pa.rk, and (assembly) A^T P into pa.E, P^T P and P^T h into pa.gp. r may be
 // null (only the polynomial sums of the FP64 assembly are wanted).
-template <int KIND>
+template <int KIND, bool POLY>
 __global__ void __launch_bounds__(kThreads) k_residual(Binned bd, const int4* __restrict__ work,
                                                        int npad, const double* __restrict__ c,
                                                        double* __restrict__ r,
@@ -352,7 +391,8 @@ __global__ void __launch_bounds__(kThreads) k_residual(Binned bd, const int4* __
     __shared__ LocalCells lc;
     __shared__ double esm[kSubChunk];
     __shared__ double usm[kSubChunk], vsm[kSubChunk];
-    const bool poly = pa.k || pa.E || pa.gp || pa.rk;
+    constexpr bool poly = POLY;   // the polynomial's parts are compiled only into its instance
+    if constexpr (!POLY) pa = PolyArgs{};
     const double pk0 = pa.k ? pa.k[0] : 0.0, pk1 = pa.k ? pa.k[1] : 0.0, pk2 = pa.k ? pa.k[2] : 0.0;
     double eacc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};   // A^T P of candidates tid, tid + kThreads
     double gacc[9] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};   // P^T P (6), P^T h (3)
@@ -386,6 +426,13 @@ __global__ void __launch_bounds__(kThreads) k_residual(Binned bd, const int4* __
     cs.lv = reinterpret_cast<float*>(sp);
     sp += sizeof(float) * npad;
     int* wl = reinterpret_cast<int*>(sp);
+    sp += sizeof(int) * npad * (kThreads / 32);
+    // stored A: per candidate its mask, nonzero count and offset in the sub-chunk's values
+    unsigned int* amsk = reinterpret_cast<unsigned int*>(sp);
+    sp += sizeof(unsigned int) * npad;
+    int* acnt = reinterpret_cast<int*>(sp);
+    sp += sizeof(int) * npad;
+    int* aoff = reinterpret_cast<int*>(sp);
 
     stage_candidates<double>(bd, lc, cs, npad, c);
     for (int a = threadIdx.x; a < npad; a += blockDim.x) cnt[a] = 0;
@@ -402,31 +449,38 @@ __global__ void __launch_bounds__(kThreads) k_residual(Binned bd, const int4* __
         }
         __syncthreads();
         if (astore) {
-            // Keep the nonzeros of A for later residual passes, per sub-chunk and candidate a: a
-            // 32-bit mask of the sub-chunk's points in a's support, and their values in point
-            // order packed at the start of a's 32-slot column.
+            // Keep the nonzeros of A for later residual passes, per sub-chunk: per candidate a
+            // a 32-bit mask of the sub-chunk's points in a's support, and the values packed
+            // candidate after candidate (each candidate's in point order) from the start of the
+            // sub-chunk's region, so a later pass reads them with coalesced loads.
             const long long q = (q0 - p0) / kSubChunk;
             double* vals = astore + woff[blockIdx.x] + q * kSubChunk * n;
             unsigned int* msk = amask + moff[blockIdx.x] + q * n;
             for (int a = threadIdx.x; a < n; a += blockDim.x) {
                 unsigned int m = 0;
-                int j = 0;
-                for (int pp = 0; pp < np; ++pp) {
-                    const double v = phi[pp * npad + a];
-                    if (v != 0.0) {
-                        vals[(long long)a * kSubChunk + j++] = v;
-                        m |= 1u << pp;
-                    }
-                }
+                for (int pp = 0; pp < np; ++pp)
+                    if (phi[pp * npad + a] != 0.0) m |= 1u << pp;
+                amsk[a] = m;
+                acnt[a] = __popc(m);
                 msk[a] = m;
             }
+            __syncthreads();
+            block_scan_counts(acnt, n, aoff);
+            for (int a = threadIdx.x; a < n; a += blockDim.x) {
+                unsigned int m = amsk[a];
+                double* dst = vals + aoff[a];
+                for (int j = 0; m; ++j, m &= m - 1u) dst[j] = phi[(__ffs(m) - 1) * npad + a];
+            }
         }
-        // e_p = h_p - sum_a Phi[p][a] c_a - k . (u_p, v_p, 1)  (one warp per point)
+        // e_p = h_p - sum_a Phi[p][a] c_a - k . (u_p, v_p, 1)  (one warp per point; the sum
+        // is skipped for c = 0, the assembly's pass)
         for (int pp = warp; pp < np; pp += nw) {
             double s = 0.0;
-            for (int a = lane; a < n; a += 32) s = fma(phi[pp * npad + a], cs.cval[a], s);
+            if (c) {
+                for (int a = lane; a < n; a += 32) s = fma(phi[pp * npad + a], cs.cval[a], s);
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+                for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            }
             if (lane == 0)
                 esm[pp] = hsm[pp] - s - (pa.k ? fma(pk0, usm[pp], fma(pk1, vsm[pp], pk2)) : 0.0);
         }
@@ -505,9 +559,11 @@ __global__ void __launch_bounds__(kThreads) k_residual(Binned bd, const int4* __
 
 // The same residual from the stored nonzeros of A (written by the FP64 pass of the FP32
 // assembly): no distances, square roots or Wendland evaluations, and the two FP64 products
-// run over the nonzeros only. Per sub-chunk: e_p = h_p - sum_a A_pa c_a (one warp per point,
-// lanes over the candidates, a value found by the point's rank in the candidate's mask), then
-// r_a += sum_p A_pa e_p (one thread per candidate over its column).
+// run over the nonzeros only. Per sub-chunk: the packed values are copied into shared memory
+// with coalesced loads (their per-candidate offsets from a scan of the masks' popcounts), then
+// e_p = h_p - sum_a A_pa c_a (one warp per point, lanes over the candidates, a value found by
+// the point's rank in the candidate's mask) and r_a += sum_p A_pa e_p (one thread per candidate
+// over its values).
 __global__ void __launch_bounds__(kThreads) k_residual_stored(Binned bd, const int4* __restrict__ work,
                                                               int npad, const double* __restrict__ c,
                                                               double* __restrict__ r,
@@ -528,9 +584,12 @@ __global__ void __launch_bounds__(kThreads) k_residual_stored(Binned bd, const i
     if (threadIdx.x == 0) describe_cells(bd, cell, lc);
     __syncthreads();
     const int n = lc.n;
-    double* cval = reinterpret_cast<double*>(smem);
+    double* sval = reinterpret_cast<double*>(smem);         // [kSubChunk * npad] the sub-chunk's values
+    double* cval = sval + kSubChunk * npad;
     int* sidx = reinterpret_cast<int*>(cval + npad);
     unsigned int* smask = reinterpret_cast<unsigned int*>(sidx + npad);
+    int* acnt = reinterpret_cast<int*>(smask + npad);
+    int* aoff = acnt + npad;
     for (int a = threadIdx.x; a < n; a += blockDim.x) {
         int k = 0;
         while (a >= lc.off[k + 1]) ++k;
@@ -546,7 +605,16 @@ __global__ void __launch_bounds__(kThreads) k_residual_stored(Binned bd, const i
         const double* vals = astore + woff[blockIdx.x] + q * kSubChunk * n;
         const unsigned int* msk = amask + moff[blockIdx.x] + q * n;
         __syncthreads();
-        for (int a = threadIdx.x; a < n; a += blockDim.x) smask[a] = __ldcs(msk + a);
+        for (int a = threadIdx.x; a < n; a += blockDim.x) {
+            const unsigned int m = __ldcs(msk + a);
+            smask[a] = m;
+            acnt[a] = __popc(m);
+        }
+        __syncthreads();
+        block_scan_counts(acnt, n, aoff);
+        // the sub-chunk's packed values, coalesced
+        const int nnz = aoff[n];
+        for (int i = threadIdx.x; i < nnz; i += blockDim.x) sval[i] = __ldcs(vals + i);
         if (threadIdx.x < np) {
             hsm[threadIdx.x] = bd.ph[q0 + threadIdx.x];
             if (pa.k) {
@@ -560,8 +628,7 @@ __global__ void __launch_bounds__(kThreads) k_residual_stored(Binned bd, const i
             double sacc = 0.0;
             for (int a = lane; a < n; a += 32) {
                 const unsigned int m = smask[a];
-                if ((m >> pp) & 1u)
-                    sacc = fma(__ldg(vals + (long long)a * kSubChunk + __popc(m & below)), cval[a], sacc);
+                if ((m >> pp) & 1u) sacc = fma(sval[aoff[a] + __popc(m & below)], cval[a], sacc);
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
@@ -577,9 +644,9 @@ __global__ void __launch_bounds__(kThreads) k_residual_stored(Binned bd, const i
         }
         for (int a = threadIdx.x; a < n; a += blockDim.x) {
             unsigned int m = smask[a];
-            const double* col = vals + (long long)a * kSubChunk;
+            const double* col = sval + aoff[a];
             double acc = 0.0;
-            for (int j = 0; m; ++j, m &= m - 1u) acc = fma(__ldg(col + j), esm[__ffs(m) - 1], acc);
+            for (int j = 0; m; ++j, m &= m - 1u) acc = fma(col[j], esm[__ffs(m) - 1], acc);
             if (a == threadIdx.x) racc0 += acc;
             else racc1 += acc;
         }
@@ -612,7 +679,7 @@ template <typename T>
 size_t asm_smem(int npad, bool resid) {
     size_t b = sizeof(T) * kSubChunk * npad + 2 * sizeof(T) * npad + 3 * sizeof(int) * npad +
                sizeof(double) * kSubChunk;
-    if (resid) b += sizeof(double) * npad;
+    if (resid) b += sizeof(double) * npad + 3 * sizeof(int) * npad + 16;
     else b += sizeof(RowMeta) * npad;
     if (sizeof(T) == 8)   // FP32 prefilter coordinates and the per-warp compacted lists
         b += 2 * sizeof(float) * npad + sizeof(int) * npad * (kThreads / 32);
@@ -636,7 +703,8 @@ template <int KIND>
 rbf_status launch_residual(rbf_ctx* ctx, const double* c, double* r, bool count, cudaStream_t st,
                            int npad, const PolyArgs& pa) {
     const size_t sm = asm_smem<double>(npad, true);
-    auto kfn = k_residual<KIND>;
+    const bool poly = pa.k || pa.E || pa.gp || pa.rk;
+    auto kfn = poly ? k_residual<KIND, true> : k_residual<KIND, false>;
     RBF_CUDA_TRY(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
     const bool store = count && ctx->astore_ok;
     kfn<<<ctx->nwork, kThreads, sm, st>>>(view(ctx), ctx->work.as<int4>(), npad, c, r,
@@ -796,7 +864,9 @@ rbf_status residual_run(rbf_ctx* ctx, const double* c_sorted, double* r_sorted, 
     const double* c = c_sorted;   // nullptr stands for c = 0, i.e. r = A^T h
     const int npad = std::max(4, (ctx->max_cand + 3) / 4 * 4);
     if (!count && ctx->astore_ok) {
-        const size_t sm = sizeof(double) * npad + sizeof(int) * npad + sizeof(unsigned int) * npad;
+        const size_t sm = sizeof(double) * (kSubChunk + 1) * npad + 4 * sizeof(int) * npad + 16;
+        RBF_CUDA_TRY(cudaFuncSetAttribute(k_residual_stored, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          int(sm)));
         k_residual_stored<<<ctx->nwork, kThreads, sm, st>>>(view(ctx), ctx->work.as<int4>(), npad, c,
                                                             r_sorted, ctx->woff.as<long long>(),
                                                             ctx->astore.as<double>(), ctx->moff_p,
