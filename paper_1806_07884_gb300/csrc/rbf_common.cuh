@@ -59,15 +59,15 @@ __device__ __forceinline__ bool inside_exact(double dx, double dy, double R, dou
 
 // Square root of a >= 0 in FP64 by Newton-Raphson iteration for the reciprocal square root,
 // y <- y (3 - a y^2) / 2, seeded with the FP32 hardware estimate rsqrtf (about 23 correct
-// bits; each step doubles them), followed by one Newton step on sqrt itself,
-// s <- s + y (a - s^2) / 2. About ten FP64 operations instead of a full IEEE square root;
-// the result is within a few units in the last place of sqrt(a) (checked against sqrt by
-// the library's self-test entry point).
+// bits; the step doubles them to about 46), followed by one Newton step on sqrt itself,
+// s <- s + y (a - s^2) / 2, which squares the remaining relative error (below FP64 rounding).
+// About seven FP64 operations instead of a full IEEE square root; the result is within a few
+// units in the last place of sqrt(a) (checked against sqrt by the library's self-test entry
+// point).
 __device__ __forceinline__ double sqrt_nr(double a) {
     if (!(a > 0.0)) return 0.0;
     if (a < 1e-30 || a > 1e30) return sqrt(a);   // outside the FP32 seed's normal range
     double y = double(rsqrtf(float(a)));
-    y = y * fma(-0.5 * a, y * y, 1.5);
     y = y * fma(-0.5 * a, y * y, 1.5);
     const double s = a * y;
     return fma(0.5 * y, fma(-s, s, a), s);

@@ -1,42 +1,14 @@
 // Step (e): evaluate the approximant f(x) = sum_j c_j phi(||x - xi_j|| / R) (Eq. 3) at
-// query points or on a node-centred grid. Only the centres of the 3x3 cells around the
-// query's cell can contribute (compact support, Eq. 18); they are three contiguous ranges
-// of the cell-sorted centre order. Also: export of the assembled B for diagnostics.
+// query points or on a node-centred grid, one warp per query. Only the centres of the 3x3
+// cells around the query's cell can contribute (compact support, Eq. 18); they are three
+// contiguous ranges of the cell-sorted centre order. Also: export of the assembled B for
+// diagnostics.
 #include <algorithm>
 
 #include "rbf_internal.h"
 
 namespace rbf {
 namespace {
-
-template <int KIND>
-__device__ __forceinline__ double eval_at(const Binned& bd, const double* __restrict__ c,
-                                          double x, double y) {
-    const Grid& g = bd.g;
-    const int ix = cell_ix(g, x), iy = cell_iy(g, y);
-    // the query in its cell's frame (units of R) for the FP32 prefilter
-    const float uq = float((x - (g.x0 + ix * g.h)) * g.invR);
-    const float vq = float((y - (g.y0 + iy * g.h)) * g.invR);
-    double f = 0.0;
-    for (int row = max(iy - 1, 0); row <= min(iy + 1, g.gy - 1); ++row) {
-        const float oy = float(row - iy);
-        for (int cx = max(ix - 1, 0); cx <= min(ix + 1, g.gx - 1); ++cx) {
-            const float ox = float(cx - ix);
-            const int cell = row * g.gx + cx;
-            const int s0 = bd.cstart[cell], s1 = bd.cstart[cell + 1];
-            for (int s = s0; s < s1; ++s) {
-                const float du = uq - (bd.cu[s] + ox), dv = vq - (bd.cv[s] + oy);
-                if (du * du + dv * dv >= kPrefilterR2) continue;
-                const double dx = x - bd.cx[s], dy = y - bd.cy[s];
-                if (inside_exact(dx, dy, g.R, g.R2)) {
-                    const double r = sqrt_nr(fma(dx, dx, dy * dy)) * g.invR;
-                    f = fma(c[s], wendland<KIND, double>(r), f);
-                }
-            }
-        }
-    }
-    return f;
-}
 
 __global__ void k_diag_sqrt(const double* __restrict__ a, double* __restrict__ out, int64_t n) {
     for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n;
@@ -52,30 +24,108 @@ __device__ __forceinline__ double poly_at(const double* __restrict__ k, double x
     return k ? fma(k[0], x, fma(k[1], y, k[2])) : 0.0;
 }
 
+// f at (x, y) by one warp (all 32 lanes; the result in every lane): the lanes sweep the
+// centres of the query's 3x3 cells (three contiguous ranges) with the FP32 prefilter, the
+// centres that pass are compacted into the warp's list (ballot + prefix count), and the FP64
+// distance, exact support test and Wendland value run on them a full warp at a time, so the
+// FP64 pipe sees the ~K pairs inside the support rather than every candidate of 32 queries.
 template <int KIND>
-__global__ void k_eval_points(Binned bd, const double* __restrict__ c, const double* __restrict__ qx,
-                              const double* __restrict__ qy, int64_t Q, double* __restrict__ f,
-                              const double* __restrict__ k) {
-    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < Q;
-         i += int64_t(gridDim.x) * blockDim.x) {
+__device__ __forceinline__ double eval_warp(const Binned& bd, const double* __restrict__ c,
+                                            double x, double y, int* list, int lane) {
+    const Grid& g = bd.g;
+    const int ix = cell_ix(g, x), iy = cell_iy(g, y);
+    const float uq = float((x - (g.x0 + ix * g.h)) * g.invR);
+    const float vq = float((y - (g.y0 + iy * g.h)) * g.invR);
+    const int xa = max(ix - 1, 0), xb = min(ix + 1, g.gx - 1);
+    int rs[3], rl[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const int row = iy - 1 + d;
+        if (row < 0 || row >= g.gy) {
+            rs[d] = rl[d] = 0;
+        } else {
+            rs[d] = bd.cstart[row * g.gx + xa];
+            rl[d] = bd.cstart[row * g.gx + xb + 1] - rs[d];
+        }
+    }
+    const int n = rl[0] + rl[1] + rl[2];
+    double f = 0.0;
+    int nl = 0;
+    // the listed centres' FP64 terms, a full warp at a time; the list then starts again (it
+    // holds kMaxCand entries: a query away from the data can see more candidates than the
+    // binning's limit, which counts only cells with points)
+    auto flush = [&]() {
+        __syncwarp();
+        for (int k = lane; k < nl; k += 32) {
+            const int s = list[k];
+            const double dx = x - bd.cx[s], dy = y - bd.cy[s];
+            if (inside_exact(dx, dy, g.R, g.R2)) {
+                const double r = sqrt_nr(fma(dx, dx, dy * dy)) * g.invR;
+                f = fma(c[s], wendland<KIND, double>(r), f);
+            }
+        }
+        __syncwarp();
+        nl = 0;
+    };
+    for (int a0 = 0; a0 < n; a0 += 32) {
+        const int a = a0 + lane;
+        bool pass = false;
+        int s = 0;
+        if (a < n) {
+            const int d = a < rl[0] ? 0 : (a < rl[0] + rl[1] ? 1 : 2);
+            s = rs[d] + (d == 0 ? a : (d == 1 ? a - rl[0] : a - rl[0] - rl[1]));
+            // the candidate in the query cell's frame (its cell is ox, oy cells away)
+            const int cc = bd.crow[s].z;
+            const float ox = float(cc % g.gx - ix), oy = float(cc / g.gx - iy);
+            const float du = uq - (bd.cu[s] + ox), dv = vq - (bd.cv[s] + oy);
+            pass = du * du + dv * dv < kPrefilterR2;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, pass);
+        if (pass) list[nl + __popc(bal & ((1u << lane) - 1u))] = s;
+        nl += __popc(bal);
+        if (nl > kMaxCand - 32) flush();
+    }
+    flush();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+    return f;
+}
+
+constexpr int kEvalWarps = 8;
+
+// One warp per query point (persistent warps striding over the queries).
+template <int KIND>
+__global__ void __launch_bounds__(kEvalWarps * 32)
+    k_eval_points(Binned bd, const double* __restrict__ c, const double* __restrict__ qx,
+                  const double* __restrict__ qy, int64_t Q, double* __restrict__ f,
+                  const double* __restrict__ k) {
+    __shared__ int list[kEvalWarps][kMaxCand];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int64_t i = blockIdx.x * int64_t(kEvalWarps) + w; i < Q; i += int64_t(gridDim.x) * kEvalWarps) {
         const double x = qx[i], y = qy[i];
-        f[i] = eval_at<KIND>(bd, c, x, y) + poly_at(k, x, y);
+        const double v = eval_warp<KIND>(bd, c, x, y, list[w], lane);
+        if (lane == 0) f[i] = v + poly_at(k, x, y);
     }
 }
 
 // Grid node coordinates follow an inclusive linspace: start + j * step (separately
 // rounded), the last node exactly at the end of the box.
+// One warp per grid node (persistent warps striding over the nodes, consecutive warps on
+// neighbouring nodes so their candidates stay in L1).
 template <int KIND>
-__global__ void k_eval_grid(Binned bd, const double* __restrict__ c, int nx, int ny, double x0,
-                            double y0, double x1, double y1, double sx, double sy,
-                            double* __restrict__ f, const double* __restrict__ k) {
+__global__ void __launch_bounds__(kEvalWarps * 32)
+    k_eval_grid(Binned bd, const double* __restrict__ c, int nx, int ny, double x0, double y0,
+                double x1, double y1, double sx, double sy, double* __restrict__ f,
+                const double* __restrict__ k) {
+    __shared__ int list[kEvalWarps][kMaxCand];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t Q = int64_t(nx) * ny;
-    for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < Q;
-         q += int64_t(gridDim.x) * blockDim.x) {
+    for (int64_t q = blockIdx.x * int64_t(kEvalWarps) + w; q < Q; q += int64_t(gridDim.x) * kEvalWarps) {
         const int i = int(q / nx), j = int(q % nx);
         const double x = (j == nx - 1 && nx > 1) ? x1 : __dadd_rn(__dmul_rn(double(j), sx), x0);
         const double y = (i == ny - 1 && ny > 1) ? y1 : __dadd_rn(__dmul_rn(double(i), sy), y0);
-        f[q] = eval_at<KIND>(bd, c, x, y) + poly_at(k, x, y);
+        const double v = eval_warp<KIND>(bd, c, x, y, list[w], lane);
+        if (lane == 0) f[q] = v + poly_at(k, x, y);
     }
 }
 
@@ -126,6 +176,8 @@ __global__ void k_count_nonzero(const T* __restrict__ B, int64_t n,
 }
 
 int eval_grid_size(int64_t Q) { return int(std::min<int64_t>((Q + 255) / 256, 152 * 32)); }
+// warps of kEvalWarps per block, one query each, persistent over the queries
+int eval_warp_grid(int64_t Q) { return int(std::min<int64_t>((Q + kEvalWarps - 1) / kEvalWarps, 152 * 8)); }
 
 }  // namespace
 
@@ -149,12 +201,13 @@ rbf_status eval_points_poly_run(rbf_ctx* ctx, const double* c, const double* k, 
     ctx->launches += 1;
     if (Q <= 0) return RBF_OK;
     const double* cs = ctx->csort.as<double>();
-    const int gb = eval_grid_size(Q);
+    const int gb = eval_warp_grid(Q);
+    constexpr int T = kEvalWarps * 32;
     switch (ctx->kernel) {
-        case RBF_W30: k_eval_points<0><<<gb, 256, 0, st>>>(bd, cs, qx, qy, Q, f, k); break;
-        case RBF_W31: k_eval_points<1><<<gb, 256, 0, st>>>(bd, cs, qx, qy, Q, f, k); break;
-        case RBF_W32: k_eval_points<2><<<gb, 256, 0, st>>>(bd, cs, qx, qy, Q, f, k); break;
-        default: k_eval_points<3><<<gb, 256, 0, st>>>(bd, cs, qx, qy, Q, f, k); break;
+        case RBF_W30: k_eval_points<0><<<gb, T, 0, st>>>(bd, cs, qx, qy, Q, f, k); break;
+        case RBF_W31: k_eval_points<1><<<gb, T, 0, st>>>(bd, cs, qx, qy, Q, f, k); break;
+        case RBF_W32: k_eval_points<2><<<gb, T, 0, st>>>(bd, cs, qx, qy, Q, f, k); break;
+        default: k_eval_points<3><<<gb, T, 0, st>>>(bd, cs, qx, qy, Q, f, k); break;
     }
     RBF_CUDA_TRY(cudaGetLastError());
     ctx->launches += 1;
@@ -171,12 +224,13 @@ rbf_status eval_grid_run(rbf_ctx* ctx, const double* c, int nx, int ny, const do
     const double x0 = box[0], y0 = box[1], x1 = box[2], y1 = box[3];
     const double sx = nx > 1 ? (x1 - x0) / double(nx - 1) : 0.0;
     const double sy = ny > 1 ? (y1 - y0) / double(ny - 1) : 0.0;
-    const int gb = eval_grid_size(int64_t(nx) * ny);
+    const int gb = eval_warp_grid(int64_t(nx) * ny);
+    constexpr int T = kEvalWarps * 32;
     switch (ctx->kernel) {
-        case RBF_W30: k_eval_grid<0><<<gb, 256, 0, st>>>(bd, cs, nx, ny, x0, y0, x1, y1, sx, sy, f, k); break;
-        case RBF_W31: k_eval_grid<1><<<gb, 256, 0, st>>>(bd, cs, nx, ny, x0, y0, x1, y1, sx, sy, f, k); break;
-        case RBF_W32: k_eval_grid<2><<<gb, 256, 0, st>>>(bd, cs, nx, ny, x0, y0, x1, y1, sx, sy, f, k); break;
-        default: k_eval_grid<3><<<gb, 256, 0, st>>>(bd, cs, nx, ny, x0, y0, x1, y1, sx, sy, f, k); break;
+        case RBF_W30: k_eval_grid<0><<<gb, T, 0, st>>>(bd, cs, nx, ny, x0, y0, x1, y1, sx, sy, f, k); break;
+        case RBF_W31: k_eval_grid<1><<<gb, T, 0, st>>>(bd, cs, nx, ny, x0, y0, x1, y1, sx, sy, f, k); break;
+        case RBF_W32: k_eval_grid<2><<<gb, T, 0, st>>>(bd, cs, nx, ny, x0, y0, x1, y1, sx, sy, f, k); break;
+        default: k_eval_grid<3><<<gb, T, 0, st>>>(bd, cs, nx, ny, x0, y0, x1, y1, sx, sy, f, k); break;
     }
     RBF_CUDA_TRY(cudaGetLastError());
     ctx->launches += 2;
