@@ -116,6 +116,9 @@ def parse():
     ap.add_argument("--big-N", type=int, default=20_000_000)
     ap.add_argument("--big-M", type=int, default=2_000_000)
     ap.add_argument("--big-grid", type=int, default=4096)
+    ap.add_argument("--host-b-mb", type=float, default=64.0,
+                    help="also time one big-data step with B in host memory, assembled in "
+                         "blocks of this many MB (0: skip)")
     ap.add_argument("--no-learned", dest="learned", action="store_false",
                     help="cold start instead of the learned warm start in the timed step")
     ap.add_argument("--tiles", type=int, default=512)
@@ -467,6 +470,40 @@ def bench_batched(args, rank, dev, stream, flush, hbm, peak_source):
     return out
 
 
+def bench_host_b(args, ctx, step, timed, N, M, f_dev, fbuf, stream):
+    """The same step with B in pinned host memory, assembled in blocks of cell rows that fit
+    host_b_mb MB of device memory (Section 5's block-wise assembly, "b_device_mb"); the solver
+    reads B over the host link. One step after one warm-up, and the SpMV's rate over the link
+    on the stored bytes it reads."""
+    import torch
+
+    ctx.set_param("b_device_mb", args.host_b_mb)
+    try:
+        step(args.prec, args.tol)                   # warm-up
+        ms, _, infos = timed(args.prec, args.tol, 1)
+        lst = ctx.layout_stats()
+        err = float((fbuf - f_dev).abs().max() / f_dev.abs().max())
+        vb = ctx.layout()["value_bytes"]
+        stored = lst["stored_values"] * vb + 3 * M * vb
+        ctx.bench_spmv(2)
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        ctx.bench_spmv(10)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        spmv_ms = s0.elapsed_time(s1) / 10
+    finally:
+        ctx.set_param("b_device_mb", 0.0)
+    return {"b_device_mb": args.host_b_mb, "host_blocks": lst["host_blocks"],
+            "b_bytes": lst["stored_values"] * vb, "value": N / (ms * 1e-3), "unit": "points/s",
+            "ms_per_step": round(ms, 3), "iterations": infos[-1]["iterations"],
+            "promoted": int(infos[-1]["promoted"]),
+            "spmv_ms": round(spmv_ms, 4),
+            "spmv_link_gbs": round(stored / (spmv_ms * 1e-3) / 1e9, 1),
+            "rel_err_f_vs_device_b": err, "bar": 1e-6, "ok": err <= 1e-6}
+
+
 def bench_bigdata(args, rank, dev, stream, flush, hbm, peak_source):
     """The big-data workload: N = 20 M points with 10:1 density variation, 8-octave value-noise
     heights, M = 2 M Halton centres, Wendland phi_3,2, FP32 assembly and SpMV with FP64
@@ -563,6 +600,8 @@ def bench_bigdata(args, rank, dev, stream, flush, hbm, peak_source):
            "refinements": info["refinements"],
            "promoted_steps": sum(int(i["promoted"]) for i in infos),
            "phases_ms": phases, "roofline": roof}
+    if args.host_b_mb > 0:
+        out["out_of_core"] = bench_host_b(args, ctx, step, timed, N, M, f_fast, fbuf, stream)
     if not args.no_fp64_compare:
         ms64, _, infos64 = timed("fp64", args.tol, 1)
         out["fp64_path"] = {"value": N / (ms64 * 1e-3), "ms_per_step": round(ms64, 3),

@@ -53,8 +53,8 @@ typedef enum {
     RBF_ERR_NOT_CONVERGED = 4,  /* solver hit maxit before reaching tol */
     RBF_ERR_BREAKDOWN = 5,      /* CG breakdown: p^T B p <= 0 or a non-finite scalar */
     RBF_ERR_LIMIT = 6,          /* input exceeds a documented kernel limit */
-    RBF_ERR_TIMEOUT = 7         /* reserved: no entry point of this version returns it (no
-                                   kernel waits on another block or on the host) */
+    RBF_ERR_TIMEOUT = 7         /* a grid barrier of the persistent CG solve (rbf_solve)
+                                   waited longer than 2 s; the context stays usable */
 } rbf_status;
 
 /* Wendland functions phi_{3,s}(r), r = ||x - xi|| / R, zero for r >= 1 (Table 2, Eq. 18).
@@ -112,7 +112,10 @@ typedef struct {
                                 in FP32 keep their refined iterate */
 } rbf_tile_info;
 
-/* Create / destroy a context bound to CUDA device `device`. */
+/* Create / destroy a context bound to CUDA device `device`. alloc / free_fn (both or
+ * neither; NULL: cudaMalloc / cudaFree) supply the workspace: device memory of at least
+ * `bytes`, aligned to 256 bytes (as cudaMalloc's), usable on `stream`; a NULL or misaligned
+ * result makes the call that needed it return RBF_ERR_ALLOC. */
 rbf_status rbf_create(rbf_ctx** out, int device, rbf_alloc_fn alloc, rbf_free_fn free_fn,
                       void* user);
 rbf_status rbf_destroy(rbf_ctx* ctx);
@@ -152,8 +155,13 @@ rbf_status rbf_assemble(rbf_ctx* ctx, rbf_kernel kernel, rbf_prec prec, void* st
  * min_support: centres whose support disc holds fewer data points are removed from
  *           the system and get c_j = 0 (the paper leaves empty supports undefined).
  * info    : HOST pointer, may be NULL.
+ * Each CG solve runs as one launch of a CUDA graph looping over the two kernels of an
+ * iteration, or, with "cg_persistent" 1 (where the device can hold its grid at once), as one
+ * cooperative launch of a persistent kernel (SpMV and vector update of every iteration
+ * separated by grid barriers). Both give the same iterates up to the order of FP additions.
  * Synchronises `stream`. Returns RBF_ERR_NOT_CONVERGED / RBF_ERR_BREAKDOWN with c
- * holding the last iterate. With RBF_FP32_REFINE, a refinement step that no longer reduces
+ * holding the last iterate, RBF_ERR_TIMEOUT if a barrier wait of the persistent kernel ran
+ * out. With RBF_FP32_REFINE, a refinement step that no longer reduces
  * the FP64 residual promotes the solve to FP64 (see rbf_solve_info.promoted). */
 rbf_status rbf_solve(rbf_ctx* ctx, double* c, int use_c0, double tol, int maxit,
                      int min_support, rbf_solve_info* info, void* stream);
@@ -224,6 +232,21 @@ rbf_status rbf_eval_grid_poly(rbf_ctx* ctx, const double* c, const double* k, in
  *                      force the batched CG's SpMV blocks per SM (1..8), row groups per
  *                      SpMV work item (1..64) and update block size (128, 256 or 512); 0 =
  *                      automatic
+ *   "cg_persistent"    0 (default): rbf_solve's CG loop as the CUDA graph of two kernels per
+ *                      iteration; 1: as one cooperative launch of the persistent kernel
+ *   "cg_barrier_test"  test hook, 0 (default) or 1: the persistent kernel's barriers wait for
+ *                      one block more than its grid has, so the first wait runs out (2 s) and
+ *                      rbf_solve returns RBF_ERR_TIMEOUT
+ *   "b_device_mb"      0 (default): B lives in device memory. > 0 (single systems; takes effect
+ *                      at the next rbf_assemble / rbf_assemble_poly): B too large for the
+ *                      device -- the block-wise assembly of Section 5 (Eq. 13-16). The stored
+ *                      values of B live in pinned, device-mapped host memory (read by the
+ *                      solver over the host link) and are assembled on the device in blocks of
+ *                      consecutive cell rows whose values fit this many MB (at least one cell
+ *                      row per block), each block copied out when done. The values are those
+ *                      of the in-device assembly up to the order of the FP additions. The
+ *                      host buffer is freed by rbf_destroy or the next in-device assembly.
+ *                      Pinned host memory that cannot be had returns RBF_ERR_ALLOC.
  * Returns RBF_ERR_ARG for an unknown name or a value out of range. */
 rbf_status rbf_set_param(rbf_ctx* ctx, const char* name, double value);
 
@@ -240,6 +263,8 @@ typedef struct {
     int64_t row_groups;      /* row groups (up to 8 consecutive rows) the SpMV sweeps */
     int64_t dropped;         /* Gram entries of the last assembly that found no slot in their
                                 row: 0 by construction (any other value is a library defect) */
+    int64_t host_blocks;     /* 0: B in device memory; else the blocks of cell rows of the
+                                last out-of-core assembly (B in host memory, "b_device_mb") */
 } rbf_layout_stats;
 
 /* Fill *out (HOST) for the last assembly; counts the nonzeros on the GPU. Requires a

@@ -344,16 +344,19 @@ class Context:
         return dict(nvals=nv.value, value_bytes=vb.value, gx=gx.value, gy=gy.value)
 
     def layout_stats(self, stream=None):
-        """Stored values, nonzeros of the upper triangle (diagonal included), row groups and
-        dropped Gram entries (always 0) of the last assembly."""
+        """Stored values, nonzeros of the upper triangle (diagonal included), row groups,
+        dropped Gram entries (always 0) and host blocks (0: B in device memory) of the last
+        assembly."""
         st = _lib.LayoutStats()
         self._check(self.lib.rbf_get_layout_stats(self._h, C.byref(st), self._stream(stream)),
                     "rbf_get_layout_stats")
         return dict(stored_values=st.stored_values, nonzeros=st.nonzeros,
-                    row_groups=st.row_groups, dropped=st.dropped)
+                    row_groups=st.row_groups, dropped=st.dropped, host_blocks=st.host_blocks)
 
     def set_param(self, name: str, value: float):
-        """Solver parameters: "inner_tol", "max_refinements" (see include/rbf.h)."""
+        """Context parameters: "inner_tol", "max_refinements", "store_a", "autotune",
+        "spmv_blocks_per_sm", "spmv_chunk", "update_threads", "b_device_mb" (see
+        include/rbf.h)."""
         self._check(self.lib.rbf_set_param(self._h, name.encode(), float(value)), "rbf_set_param")
 
     def launch_count(self) -> int:

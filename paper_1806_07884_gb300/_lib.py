@@ -39,7 +39,7 @@ class TileInfo(C.Structure):
 
 class LayoutStats(C.Structure):
     _fields_ = [("stored_values", C.c_int64), ("nonzeros", C.c_int64),
-                ("row_groups", C.c_int64), ("dropped", C.c_int64)]
+                ("row_groups", C.c_int64), ("dropped", C.c_int64), ("host_blocks", C.c_int64)]
 
 
 _P = C.c_void_p

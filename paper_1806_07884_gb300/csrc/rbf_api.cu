@@ -1,5 +1,6 @@
 // C-ABI entry points of librbf (declared in include/rbf.h): argument checks, context
 // and workspace management; the work itself is done by the kernels of the other units.
+#include <stdint.h>
 #include <math.h>
 #include <stdio.h>
 
@@ -54,6 +55,11 @@ rbf_status ensure(rbf_ctx* ctx, rbf_buf& b, size_t bytes, cudaStream_t st) {
         p = nullptr;
     }
     if (!p) return set_err(ctx, RBF_ERR_ALLOC, "workspace allocation failed");
+    if (reinterpret_cast<uintptr_t>(p) % 256 != 0) {
+        // the kernels read the workspace in 16-byte vectors from offsets that assume it
+        if (ctx->free_fn) ctx->free_fn(p, want, nullptr, ctx->user);
+        return set_err(ctx, RBF_ERR_ALLOC, "the allocator returned memory not aligned to 256 bytes");
+    }
     b.p = p;
     b.bytes = want;
     return RBF_OK;
@@ -152,9 +158,10 @@ rbf_status rbf_destroy(rbf_ctx* ctx) {
                        &ctx->dinv, &ctx->dinv32, &ctx->bjinv, &ctx->bjinv32, &ctx->crow,
                        &ctx->partial, &ctx->scal, &ctx->csort, &ctx->sigma, &ctx->feat,
                        &ctx->mlp_part, &ctx->astore, &ctx->amask, &ctx->woff, &ctx->wsize,
-                       &ctx->pE, &ctx->pE32, &ctx->pdev, &ctx->pepart};
+                       &ctx->pE, &ctx->pE32, &ctx->pdev, &ctx->pepart, &ctx->bblock, &ctx->bandtab};
     for (rbf_buf* b : bufs) release(ctx, *b);
     if (ctx->hpinned) cudaFreeHost(ctx->hpinned);
+    if (ctx->bhost) cudaFreeHost(ctx->bhost);
     delete ctx;
     return RBF_OK;
 }
@@ -492,6 +499,22 @@ rbf_status rbf_set_param(rbf_ctx* ctx, const char* name, double value) {
         if (!(value == 0.0 || value == 128.0 || value == 256.0 || value == 512.0))
             return set_err(ctx, RBF_ERR_ARG, "update_threads must be 0, 128, 256 or 512");
         ctx->force_nt = int(value);
+        return RBF_OK;
+    }
+    if (!strcmp(name, "cg_persistent")) {
+        if (!(value == 0.0 || value == 1.0)) return set_err(ctx, RBF_ERR_ARG, "cg_persistent must be 0 or 1");
+        ctx->cg_persistent = int(value);
+        return RBF_OK;
+    }
+    if (!strcmp(name, "cg_barrier_test")) {
+        if (!(value == 0.0 || value == 1.0)) return set_err(ctx, RBF_ERR_ARG, "cg_barrier_test must be 0 or 1");
+        ctx->cg_barrier_extra = int(value);
+        return RBF_OK;
+    }
+    if (!strcmp(name, "b_device_mb")) {
+        if (!(value >= 0.0 && value <= 1e9))
+            return set_err(ctx, RBF_ERR_ARG, "b_device_mb must be in [0, 1e9]");
+        ctx->b_device_mb = value;
         return RBF_OK;
     }
     return set_err(ctx, RBF_ERR_ARG, "unknown parameter");

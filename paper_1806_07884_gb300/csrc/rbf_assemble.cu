@@ -15,6 +15,7 @@
 // s_a at the slot of column s_b; the diagonal halved, see RowMeta); b and the support counts
 // are reduced per candidate.
 #include <algorithm>
+#include <vector>
 
 #include "rbf_internal.h"
 
@@ -222,7 +223,10 @@ __global__ void __launch_bounds__(kThreads) k_assemble(Binned bd, const int4* __
                                                        int npad, T* __restrict__ B,
                                                        double* __restrict__ bvec,
                                                        int* __restrict__ support,
-                                                       int* __restrict__ dropped) {
+                                                       int* __restrict__ dropped, long long boff,
+                                                       int rlo, int rhi) {
+    // B holds the values from offset boff on, of rows rlo .. rhi-1 only (a block of an
+    // out-of-core assembly; the whole B otherwise); bvec null: no b and support counts
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ LocalCells lc;
     constexpr bool kFP64 = sizeof(T) == 8;
@@ -295,10 +299,10 @@ __global__ void __launch_bounds__(kThreads) k_assemble(Binned bd, const int4* __
         for (int q0 = p0; q0 < p1; q0 += kSubChunk) {
             __syncthreads();
             fill_phi<KIND, T>(bd, cs, n, npad, q0, p1, phi, kFP64 ? hsm : nullptr,
-                              (kFP64 && pass == 0) ? cnt : nullptr, wl);
+                              (kFP64 && pass == 0 && bvec) ? cnt : nullptr, wl);
             __syncthreads();
             const int np = min(kSubChunk, p1 - q0);
-            if (kFP64 && pass == 0) {
+            if (kFP64 && pass == 0 && bvec) {
                 for (int pp = 0; pp < np; ++pp) {
                     const double hp = hsm[pp];
                     if (threadIdx.x < n) bacc0 += hp * double(phi[pp * npad + threadIdx.x]);
@@ -341,6 +345,7 @@ __global__ void __launch_bounds__(kThreads) k_assemble(Binned bd, const int4* __
                 const int ka = cs.a9[a];
                 const RowMeta rma = cs.rm[a];
                 const int sa = cs.s[a];
+                if (sa < rlo || sa >= rhi) continue;   // a row of another block
 #pragma unroll
                 for (int v = 0; v < 4; ++v) {
                     const int b = 4 * bj + v;
@@ -350,14 +355,14 @@ __global__ void __launch_bounds__(kThreads) k_assemble(Binned bd, const int4* __
                     const int dy = cs.a9[b] / 3 - ka / 3;
                     const long long slot = upper_slot(rma, sa, cs.s[b], dy);
                     if (slot >= 0)
-                        atomicAdd(&B[slot], b == a ? T(0.5) * val : val);
+                        atomicAdd(&B[slot - boff], b == a ? T(0.5) * val : val);
                     else
                         atomicAdd(dropped, 1);
                 }
             }
         }
     }
-    if constexpr (kFP64) {
+    if (kFP64 && bvec) {
         __syncthreads();
         if (threadIdx.x < n) {
             if (bacc0 != 0.0) atomicAdd(&bvec[cs.s[threadIdx.x]], bacc0);
@@ -686,14 +691,21 @@ size_t asm_smem(int npad, bool resid) {
     return b;
 }
 
+// The Gram entries of rows [rlo, rhi) from work items [w0, w1) into B (whose first value is
+// value boff of the whole B); b and the support counts too when with_b (FP64, whole B only).
 template <int KIND, typename T>
-rbf_status launch_assemble(rbf_ctx* ctx, cudaStream_t st, int npad) {
+rbf_status launch_assemble(rbf_ctx* ctx, cudaStream_t st, int npad, T* B, bool with_b,
+                           long long boff = 0, int rlo = 0, int rhi = -1, int w0 = 0, int w1 = -1) {
     const size_t sm = asm_smem<T>(npad, false);
     auto kfn = k_assemble<KIND, T>;
     RBF_CUDA_TRY(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
-    kfn<<<ctx->nwork, kThreads, sm, st>>>(view(ctx), ctx->work.as<int4>(), npad, ctx->bvals.as<T>(),
-                                          ctx->bvec.as<double>(), ctx->support.as<int>(),
-                                          ctx->stats.as<int>() + 12);
+    if (rhi < 0) rhi = ctx->M;
+    if (w1 < 0) w1 = ctx->nwork;
+    if (w1 <= w0) return RBF_OK;
+    kfn<<<w1 - w0, kThreads, sm, st>>>(view(ctx), ctx->work.as<int4>() + w0, npad, B,
+                                       with_b ? ctx->bvec.as<double>() : nullptr,
+                                       ctx->support.as<int>(), ctx->stats.as<int>() + 12, boff,
+                                       rlo, rhi);
     RBF_CUDA_TRY(cudaGetLastError());
     ctx->launches += 1;
     return RBF_OK;
@@ -762,16 +774,151 @@ __global__ void k_to_float(const double* __restrict__ a, float* __restrict__ b, 
 }
 }  // namespace
 
+namespace {
+// Per cell row b (and b = gy): its first sorted row, that row's value offset (quads) and the
+// first assembly work item of the row's cells.
+__global__ void k_band_table(Grid g, int M, int nwork, const int* __restrict__ cstart,
+                             const int64_t* __restrict__ roff, const int* __restrict__ wstart,
+                             long long* __restrict__ tab) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b > g.gy) return;
+    const int row = b < g.gy ? cstart[b * g.gx] : M;
+    tab[3 * b] = row;
+    tab[3 * b + 1] = roff[row];
+    tab[3 * b + 2] = b < g.gy ? wstart[b * g.gx] : nwork;
+}
+
+// The pinned host copy of B, mapped into the device's address space.
+rbf_status ensure_host_b(rbf_ctx* ctx, size_t bytes, cudaStream_t st) {
+    bytes = std::max<size_t>(bytes, 256);
+    if (ctx->bhost && ctx->bhost_bytes >= bytes) return RBF_OK;
+    if (ctx->bhost) {
+        RBF_CUDA_TRY(cudaStreamSynchronize(st));
+        cudaFreeHost(ctx->bhost);
+        ctx->bhost = ctx->bhost_dev = nullptr;
+        ctx->bhost_bytes = 0;
+    }
+    void* p = nullptr;
+    void* d = nullptr;
+    if (cudaHostAlloc(&p, bytes, cudaHostAllocMapped) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return set_err(ctx, RBF_ERR_ALLOC, "pinned host memory for B");
+    }
+    if (cudaHostGetDevicePointer(&d, p, 0) != cudaSuccess || !d) {
+        cudaGetLastError();
+        cudaFreeHost(p);
+        return set_err(ctx, RBF_ERR_CUDA, "device address of the host copy of B");
+    }
+    ctx->bhost = p;
+    ctx->bhost_dev = d;
+    ctx->bhost_bytes = bytes;
+    return RBF_OK;
+}
+
+// Out-of-core assembly of B (Eq. 13-16: B assembled block by block within a memory bound):
+// consecutive cell rows are grouped into blocks whose stored values fit b_device_mb MB; each
+// block is assembled on the device from the work items of the point cells within one cell row
+// of it (every point whose support touches a row of the block), keeping only the entries of
+// its rows, and copied to the host copy of B, which the solver then reads through its device
+// address. Blocks hold at least one cell row whatever the bound.
+template <int KIND, typename T>
+rbf_status assemble_blocks(rbf_ctx* ctx, cudaStream_t st, int npad) {
+    const Grid& g = ctx->g;
+    const int gy = g.gy;
+    rbf_status s;
+    if ((s = ensure(ctx, ctx->bandtab, sizeof(long long) * 3 * size_t(gy + 1), st)) != RBF_OK) return s;
+    k_band_table<<<div_up(gy + 1, 256), 256, 0, st>>>(g, ctx->M, ctx->nwork, ctx->cstart.as<int>(),
+                                                      ctx->roff.as<int64_t>(), ctx->wstart.as<int>(),
+                                                      ctx->bandtab.as<long long>());
+    ctx->launches += 1;
+    RBF_CUDA_TRY(cudaGetLastError());
+    std::vector<long long> tab(3 * size_t(gy + 1));
+    RBF_CUDA_TRY(cudaMemcpyAsync(tab.data(), ctx->bandtab.p, sizeof(long long) * tab.size(),
+                                 cudaMemcpyDeviceToHost, st));
+    RBF_CUDA_TRY(cudaStreamSynchronize(st));
+    auto val = [&](int b) { return 4 * tab[3 * b + 1]; };
+    const long long budget = std::max<long long>(
+        4, (long long)(ctx->b_device_mb * 1048576.0 / double(sizeof(T))));
+    struct Blk { int b0, b1; };
+    std::vector<Blk> blocks;
+    long long maxv = 0;
+    for (int b = 0; b < gy;) {
+        int b1 = b + 1;
+        while (b1 < gy && val(b1 + 1) - val(b) <= budget) ++b1;
+        blocks.push_back({b, b1});
+        maxv = std::max(maxv, val(b1) - val(b));
+        b = b1;
+    }
+    if ((s = ensure(ctx, ctx->bblock, sizeof(T) * size_t(std::max<long long>(maxv, 1)), st)) != RBF_OK)
+        return s;
+    T* blk = ctx->bblock.as<T>();
+    char* host = static_cast<char*>(ctx->bhost);
+    for (const Blk& k : blocks) {
+        const long long v0 = val(k.b0), v1 = val(k.b1);
+        if (v1 == v0) continue;
+        const int r0 = int(tab[3 * k.b0]), r1 = int(tab[3 * k.b1]);
+        const int w0 = int(tab[3 * std::max(k.b0 - 1, 0) + 2]);
+        const int w1 = int(tab[3 * std::min(k.b1 + 1, gy) + 2]);
+        RBF_CUDA_TRY(cudaMemsetAsync(blk, 0, sizeof(T) * size_t(v1 - v0), st));
+        if ((s = launch_assemble<KIND, T>(ctx, st, npad, blk, false, v0, r0, r1, w0, w1)) != RBF_OK)
+            return s;
+        RBF_CUDA_TRY(cudaMemcpyAsync(host + sizeof(T) * size_t(v0), blk, sizeof(T) * size_t(v1 - v0),
+                                     cudaMemcpyDeviceToHost, st));
+    }
+    ctx->bblocks = int64_t(blocks.size());
+    return RBF_OK;
+}
+
+template <typename T>
+rbf_status assemble_b(rbf_ctx* ctx, int kernel, cudaStream_t st, int npad, bool host_b, bool with_b) {
+    if (host_b) {
+        switch (kernel) {
+            case RBF_W30: return assemble_blocks<0, T>(ctx, st, npad);
+            case RBF_W31: return assemble_blocks<1, T>(ctx, st, npad);
+            case RBF_W32: return assemble_blocks<2, T>(ctx, st, npad);
+            default: return assemble_blocks<3, T>(ctx, st, npad);
+        }
+    }
+    T* B = ctx->bvals.as<T>();
+    switch (kernel) {
+        case RBF_W30: return launch_assemble<0, T>(ctx, st, npad, B, with_b);
+        case RBF_W31: return launch_assemble<1, T>(ctx, st, npad, B, with_b);
+        case RBF_W32: return launch_assemble<2, T>(ctx, st, npad, B, with_b);
+        default: return launch_assemble<3, T>(ctx, st, npad, B, with_b);
+    }
+}
+}  // namespace
+
 rbf_status assemble_run(rbf_ctx* ctx, int kernel, int prec, cudaStream_t st, bool with_poly) {
     const int M = ctx->M;
     ctx->astore_ok = false;   // rewritten below by an FP32 assembly
     ctx->poly = false;
     const size_t vb = prec == RBF_FP64 ? sizeof(double) : sizeof(float);
     rbf_status s;
-    if ((s = ensure(ctx, ctx->bvals, vb * std::max<int64_t>(ctx->nvals, 1), st)) != RBF_OK) return s;
+    // a batch of tiles keeps B on the device (its tiles are small)
+    const bool host_b = ctx->b_device_mb > 0.0 && ctx->T == 0;
+    ctx->b_in_host = false;
+    ctx->bblocks = 0;
+    if (host_b) {
+        // every value is written by the blocks' copies, which cover [0, nvals) end to end
+        if (ctx->bvals.p) {
+            RBF_CUDA_TRY(cudaStreamSynchronize(st));
+            release(ctx, ctx->bvals);
+        }
+        if ((s = ensure_host_b(ctx, vb * std::max<int64_t>(ctx->nvals, 1), st)) != RBF_OK) return s;
+        ctx->b_in_host = true;
+    } else {
+        if (ctx->bhost) {
+            RBF_CUDA_TRY(cudaStreamSynchronize(st));
+            cudaFreeHost(ctx->bhost);
+            ctx->bhost = ctx->bhost_dev = nullptr;
+            ctx->bhost_bytes = 0;
+        }
+        if ((s = ensure(ctx, ctx->bvals, vb * std::max<int64_t>(ctx->nvals, 1), st)) != RBF_OK) return s;
+        RBF_CUDA_TRY(cudaMemsetAsync(ctx->bvals.p, 0, vb * ctx->nvals, st));
+    }
     if ((s = ensure(ctx, ctx->bvec, sizeof(double) * M, st)) != RBF_OK) return s;
     if ((s = ensure(ctx, ctx->support, sizeof(int) * M, st)) != RBF_OK) return s;
-    RBF_CUDA_TRY(cudaMemsetAsync(ctx->bvals.p, 0, vb * ctx->nvals, st));
     RBF_CUDA_TRY(cudaMemsetAsync(ctx->bvec.p, 0, sizeof(double) * M, st));
     RBF_CUDA_TRY(cudaMemsetAsync(ctx->support.p, 0, sizeof(int) * M, st));
     // stats[12]: Gram entries that found no slot in their row (none by construction)
@@ -799,22 +946,14 @@ rbf_status assemble_run(rbf_ctx* ctx, int kernel, int prec, cudaStream_t st, boo
     if (ctx->nwork == 0) return finish_poly(false);
     const int npad = std::max(4, (ctx->max_cand + 3) / 4 * 4);
     if (prec == RBF_FP64) {
-        switch (kernel) {
-            case RBF_W30: s = launch_assemble<0, double>(ctx, st, npad); break;
-            case RBF_W31: s = launch_assemble<1, double>(ctx, st, npad); break;
-            case RBF_W32: s = launch_assemble<2, double>(ctx, st, npad); break;
-            default: s = launch_assemble<3, double>(ctx, st, npad); break;
+        if ((s = assemble_b<double>(ctx, kernel, st, npad, host_b, true)) != RBF_OK) return s;
+        if (host_b) {
+            // the blocks overlap in work items: b and the support counts by the FP64 pass
+            if ((s = residual_run(ctx, nullptr, ctx->bvec.as<double>(), true, st)) != RBF_OK) return s;
         }
-        if (s != RBF_OK) return s;
         return finish_poly(false);
     }
-    switch (kernel) {
-        case RBF_W30: s = launch_assemble<0, float>(ctx, st, npad); break;
-        case RBF_W31: s = launch_assemble<1, float>(ctx, st, npad); break;
-        case RBF_W32: s = launch_assemble<2, float>(ctx, st, npad); break;
-        default: s = launch_assemble<3, float>(ctx, st, npad); break;
-    }
-    if (s != RBF_OK) return s;
+    if ((s = assemble_b<float>(ctx, kernel, st, npad, host_b, false)) != RBF_OK) return s;
     // Storage for the FP64 values of A, written by the pass below and read by every later
     // residual pass (the refinement). Without room for it the residual stays matrix-free.
     ctx->astore_ok = false;

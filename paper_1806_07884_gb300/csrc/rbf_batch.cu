@@ -809,7 +809,7 @@ void launch_bcg_iteration(rbf_ctx* ctx, const CgVec<T>& v, const TileCg& tc, con
     const TileWork tw = work_view(ctx);
     const int items = div_up(ctx->ngroup, cf.chunk) + ctx->T;   // most SpMV items
     const int grid = std::max(1, std::min(cf.bps * sm_count(ctx), div_up(items, kSpmvWarps)));
-    k_bcg_spmv<T><<<grid, kSpmvWarps * 32, 0, cs>>>(bd, tw.items_s, ctx->bvals.as<T>(), v.u,
+    k_bcg_spmv<T><<<grid, kSpmvWarps * 32, 0, cs>>>(bd, tw.items_s, bvals_dev<T>(ctx), v.u,
                                                     v.w[P], P, ctx->T, tc);
     const int nb = update_grid<T>(ctx, cf.nt);
     switch (cf.nt) {
@@ -983,7 +983,7 @@ template <typename T>
 rbf_status bcg_graph(rbf_ctx* ctx, const Cfg& cf, cudaGraphExec_t* out) {
     rbf_ctx::TileGraph& sg = ctx->bt_graph[sizeof(T) == 8 ? 0 : 1];
     const CgVec<T> v = cg_vectors<T>(ctx);
-    const void* key[13] = {ctx->twork.p, ctx->bvals.p, v.x, v.dinv, v.bjinv, ctx->tcg.p, ctx->gdesc.p,
+    const void* key[13] = {ctx->twork.p, bvals_dev<void>(ctx), v.x, v.dinv, v.bjinv, ctx->tcg.p, ctx->gdesc.p,
                            ctx->rmeta.p, ctx->crow.p, ctx->bjoff.p, ctx->cstart.p, nullptr,
                            nullptr};
     bool hit = sg.exec && sg.T == ctx->T && sg.M == ctx->M && sg.ngroup == ctx->ngroup &&
@@ -1524,7 +1524,7 @@ rbf_status bench_tiles_impl(rbf_ctx* ctx, int reps, bool spmv_only, cudaStream_t
         const int grid = std::max(1, std::min(cf.bps * sm_count(ctx), div_up(items, kSpmvWarps)));
         for (int k = 0; k < reps; ++k)
             k_bcg_spmv<T><<<grid, kSpmvWarps * 32, 0, st>>>(bd, work_view(ctx).items_s,
-                                                            ctx->bvals.as<T>(), v.u, v.w[0], 0,
+                                                            bvals_dev<T>(ctx), v.u, v.w[0], 0,
                                                             ctx->T, tc);
         ctx->launches += reps + 2;
     } else {

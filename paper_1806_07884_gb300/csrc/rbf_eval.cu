@@ -244,11 +244,11 @@ rbf_status export_upper_run(rbf_ctx* ctx, int64_t cap, int32_t* row, int32_t* co
     RBF_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st));
     const int nb = div_up(ctx->M, 128);
     if (ctx->prec == RBF_FP64)
-        k_export<double><<<nb, 128, 0, st>>>(bd, ctx->bvals.as<double>(), ctx->bvec.as<double>(),
+        k_export<double><<<nb, 128, 0, st>>>(bd, bvals_dev<double>(ctx), ctx->bvec.as<double>(),
                                              ctx->support.as<int>(), cap, row, col, val, bvec,
                                              support, counter);
     else
-        k_export<float><<<nb, 128, 0, st>>>(bd, ctx->bvals.as<float>(), ctx->bvec.as<double>(),
+        k_export<float><<<nb, 128, 0, st>>>(bd, bvals_dev<float>(ctx), ctx->bvec.as<double>(),
                                             ctx->support.as<int>(), cap, row, col, val, bvec,
                                             support, counter);
     RBF_CUDA_TRY(cudaGetLastError());
@@ -267,9 +267,9 @@ rbf_status layout_stats_run(rbf_ctx* ctx, rbf_layout_stats* out, cudaStream_t st
     const int nb = int(std::min<int64_t>((ctx->nvals + 255) / 256, 152 * 16));
     if (ctx->nvals > 0) {
         if (ctx->prec == RBF_FP64)
-            k_count_nonzero<double><<<nb, 256, 0, st>>>(ctx->bvals.as<double>(), ctx->nvals, counter);
+            k_count_nonzero<double><<<nb, 256, 0, st>>>(bvals_dev<double>(ctx), ctx->nvals, counter);
         else
-            k_count_nonzero<float><<<nb, 256, 0, st>>>(ctx->bvals.as<float>(), ctx->nvals, counter);
+            k_count_nonzero<float><<<nb, 256, 0, st>>>(bvals_dev<float>(ctx), ctx->nvals, counter);
         RBF_CUDA_TRY(cudaGetLastError());
         ctx->launches += 1;
     }
@@ -282,6 +282,7 @@ rbf_status layout_stats_run(rbf_ctx* ctx, rbf_layout_stats* out, cudaStream_t st
     out->nonzeros = int64_t(h[0]);
     out->row_groups = ctx->ngroup;
     out->dropped = *reinterpret_cast<const int*>(h + 1);
+    out->host_blocks = ctx->b_in_host ? ctx->bblocks : 0;
     return RBF_OK;
 }
 

@@ -71,6 +71,17 @@ struct rbf_ctx {
     int prec = -1;
     bool assembled = false;
     rbf_buf bvals;             // B values (double or float)
+    // B beyond device memory (rbf_set_param "b_device_mb" > 0): the values live in pinned host
+    // memory mapped into the device's address space (over NVLink-C2C on GB300), assembled in
+    // blocks of cell rows through the device buffer bblock of at most b_device_mb MB
+    double b_device_mb = 0.0;
+    bool b_in_host = false;    // the last assembly's B lives in host memory
+    void* bhost = nullptr;     // pinned host copy of B
+    size_t bhost_bytes = 0;
+    void* bhost_dev = nullptr; // its device address
+    rbf_buf bblock;            // device block of B under assembly
+    rbf_buf bandtab;           // [3 (gy + 1)] per cell row: first row, its value offset, first work item
+    int64_t bblocks = 0;       // blocks of the last out-of-core assembly
     rbf_buf bvec;              // [M] b = A^T h, sorted order (FP64)
     rbf_buf support;           // [M] points inside each support, sorted order
     // FP64 values of A per work item (points x candidates of the cell's 3x3 block), kept by
@@ -100,6 +111,9 @@ struct rbf_ctx {
     void* hpinned = nullptr;   // pinned host scratch for scalar read-back (4 KiB)
     int64_t launches = 0;      // kernels launched by this context (graph nodes included)
     int spmv_blocks_per_sm[2] = {0, 0};   // occupancy of the SpMV kernels, [0] FP64, [1] FP32
+    int persist_blocks_per_sm[2] = {0, 0};  // of the persistent solve kernel (-1: not resident)
+    int cg_persistent = 0;           // single systems: one cooperative launch per solve
+    int cg_barrier_extra = 0;        // test hook: the persistent solve's barriers never complete
     // solver parameters (rbf_set_param)
     double inner_tol = 1e-3;   // relative tolerance of each FP32 inner solve
     int max_refine = 30;       // FP64 refinement steps of RBF_FP32_REFINE
@@ -151,6 +165,13 @@ struct rbf_ctx {
 };
 
 namespace rbf {
+
+// The stored B values as the kernels address them: the device buffer, or the mapped host copy
+// when the last assembly kept B in host memory.
+template <typename T>
+inline T* bvals_dev(const rbf_ctx* ctx) {
+    return static_cast<T*>(ctx->b_in_host ? ctx->bhost_dev : ctx->bvals.p);
+}
 
 rbf_status set_err(rbf_ctx* ctx, rbf_status s, const char* msg);
 rbf_status ensure(rbf_ctx* ctx, rbf_buf& b, size_t bytes, cudaStream_t st);

@@ -22,7 +22,7 @@
 
 #include <algorithm>
 
-#include "rbf_internal.h"
+#include "rbf_cg.cuh"
 
 namespace rbf {
 namespace {
@@ -39,17 +39,27 @@ static_assert(kNParam == RBF_MLP_NPARAM, "parameter count");
 // features
 // ---------------------------------------------------------------------------
 
-// Per-tile (or whole-system) sums of h^2 and point counts, one thread per cell.
-__global__ void k_height_sums(Binned bd, const int* __restrict__ rowtile, double* __restrict__ acc) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+// Per-tile (or whole-system) sums of h^2 and point counts, one warp per cell (lanes over its
+// points).
+constexpr int kHWarps = 8;
+__global__ void __launch_bounds__(kHWarps * 32)
+    k_height_sums(Binned bd, const int* __restrict__ rowtile, double* __restrict__ acc) {
+    const int lane = threadIdx.x & 31;
+    const int c = blockIdx.x * kHWarps + (threadIdx.x >> 5);
     if (c >= bd.g.ncell) return;
     const int p0 = bd.pstart[c], p1 = bd.pstart[c + 1];
     if (p1 == p0) return;
-    double s = 0.0;
-    for (int p = p0; p < p1; ++p) s += bd.ph[p] * bd.ph[p];
-    const int t = rowtile ? rowtile[c / bd.g.gx] : 0;
-    atomicAdd(&acc[2 * t], s);
-    atomicAdd(&acc[2 * t + 1], double(p1 - p0));
+    double sum = 0.0;
+    for (int p = p0 + lane; p < p1; p += 32) {
+        const double h = bd.ph[p];
+        sum = fma(h, h, sum);
+    }
+    sum = warp_sum_d(sum);
+    if (lane == 0) {
+        const int t = rowtile ? rowtile[c / bd.g.gx] : 0;
+        atomicAdd(&acc[2 * t], sum);
+        atomicAdd(&acc[2 * t + 1], double(p1 - p0));
+    }
 }
 
 __global__ void k_height_scale(const double* __restrict__ acc, int T, double* __restrict__ sigma) {
@@ -57,66 +67,69 @@ __global__ void k_height_scale(const double* __restrict__ acc, int T, double* __
     if (t < T) sigma[t] = acc[2 * t + 1] > 0.0 ? sqrt(acc[2 * t] / acc[2 * t + 1]) : 1.0;
 }
 
-// Features, one warp per cell: the lanes take the candidate points of the cell's
-// 3x3 neighbourhood and test each against every centre of the cell (up to kFCent at a time),
-// accumulating per-centre bins with shared-memory atomics. Dense cells spread over the lanes
-// instead of serialising one thread per centre.
-constexpr int kFWarps = 4;
-constexpr int kFCent = 48;
+// Features, one block per cell: the threads take the candidate points of the cell's 3x3
+// neighbourhood (the three rows of cells are contiguous point ranges) and test each against
+// every centre of the cell (up to kFCent at a time, their cell-local coordinates staged in
+// shared memory), accumulating per-centre bins with shared-memory atomics. A block per cell
+// keeps dense cells (ten times the mean point count and more in clustered data) from
+// serialising on one warp. The per-bin means are formed in FP32 (relative error ~1e-7).
+constexpr int kFThreads = 256;
+constexpr int kFCent = 64;
 
-__global__ void __launch_bounds__(kFWarps * 32)
+__global__ void __launch_bounds__(kFThreads)
     k_features_cell(Binned bd, const double* __restrict__ sigma, float* __restrict__ feat) {
-    __shared__ int cnt[kFWarps][kFCent][NB];
-    __shared__ float hs[kFWarps][kFCent][NB];   // FP32 height sums: native shared atomics
-    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-    const int w = blockIdx.x * kFWarps + wl;
+    __shared__ int cnt[kFCent][NB];
+    __shared__ float hs[kFCent][NB];   // FP32 height sums: native shared atomics
+    __shared__ float su[kFCent], sv[kFCent];
     const Grid& g = bd.g;
-    if (w >= g.ncell) return;
-    const int cell = w;
+    const int cell = blockIdx.x;
     const int cs = bd.cstart[cell], m = bd.cstart[cell + 1] - cs;
     if (m == 0) return;
     const int ix = cell % g.gx, iy = cell / g.gx;
-    int (*C)[NB] = cnt[wl];
-    float (*H)[NB] = hs[wl];
-    // the three rows of candidate cells: contiguous point ranges
-    int r0[3], r1[3];
+    const int xa = max(ix - 1, 0), xb = min(ix + 1, g.gx - 1);
+    // per row of cells: its point range and the first point of its 2nd and 3rd cell
+    int r0[3], r1[3], e1[3], e2[3];
     float roy[3];
     int nrow = 0;
     for (int r = max(iy - 1, 0); r <= min(iy + 1, g.gy - 1); ++r) {
-        const int xa = max(ix - 1, 0), xb = min(ix + 1, g.gx - 1);
-        r0[nrow] = bd.pstart[r * g.gx + xa];
-        r1[nrow] = bd.pstart[r * g.gx + xb + 1];
+        const int* ps = bd.pstart + r * g.gx;
+        r0[nrow] = ps[xa];
+        e1[nrow] = xa + 1 <= xb ? ps[xa + 1] : ps[xb + 1];
+        e2[nrow] = xa + 2 <= xb ? ps[xa + 2] : ps[xb + 1];
+        r1[nrow] = ps[xb + 1];
         roy[nrow] = float(r - iy);
         ++nrow;
     }
+    const double inv_sig = 1.0 / sigma[bd.crow[cs].w];
     for (int a0 = 0; a0 < m; a0 += kFCent) {
         const int ma = min(kFCent, m - a0);
-        for (int e = lane; e < ma * NB; e += 32) {
-            C[e / NB][e % NB] = 0;
-            H[e / NB][e % NB] = 0.0f;
+        for (int e = threadIdx.x; e < ma * NB; e += kFThreads) {
+            cnt[e / NB][e % NB] = 0;
+            hs[e / NB][e % NB] = 0.0f;
         }
-        __syncwarp();
+        for (int a = threadIdx.x; a < ma; a += kFThreads) {
+            su[a] = bd.cu[cs + a0 + a];
+            sv[a] = bd.cv[cs + a0 + a];
+        }
+        __syncthreads();
         for (int rr = 0; rr < nrow; ++rr) {
-            for (int p = r0[rr] + lane; p < r1[rr]; p += 32) {
-                // the point's cell column (relative to the centre cell) from its position in
-                // the row range: find its cell by the cell starts of this row
-                const float pu = bd.pu[p], pv = bd.pv[p] + roy[rr];
-                const double px = bd.px[p], py = bd.py[p];
+            for (int p = r0[rr] + int(threadIdx.x); p < r1[rr]; p += kFThreads) {
+                // the point's cell column relative to the centre cell
+                const int q = xa + (p >= e1[rr]) + (p >= e2[rr]);
+                const float pux = bd.pu[p] + float(q - ix), pv = bd.pv[p] + roy[rr];
                 const float ph = float(bd.ph[p]);
-                const int row = iy + int(roy[rr]);
-                int q = max(ix - 1, 0);
-                while (q < min(ix + 1, g.gx - 1) && p >= bd.pstart[row * g.gx + q + 1]) ++q;
-                const float pux = pu + float(q - ix);
                 for (int a = 0; a < ma; ++a) {
-                    const int s = cs + a0 + a;
-                    const float du = pux - bd.cu[s], dv = pv - bd.cv[s];
+                    const float du = pux - su[a], dv = pv - sv[a];
                     const float r2 = du * du + dv * dv;
                     if (r2 >= kPrefilterR2) continue;
                     const float rf = sqrtf(r2) * float(NB);
                     const float fr = rf - floorf(rf);
                     int k;
                     if (fr < 1e-4f || fr > 1.0f - 1e-4f || rf > float(NB) - 1e-3f) {
-                        const double dx = px - bd.cx[s], dy = py - bd.cy[s];
+                        // near a bin edge or the support's edge: decide in FP64, every
+                        // operation rounded once, as sqrt(dx*dx + dy*dy) / R
+                        const int s = cs + a0 + a;
+                        const double dx = bd.px[p] - bd.cx[s], dy = bd.py[p] - bd.cy[s];
                         const double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
                         const double rr2 = __ddiv_rn(__dsqrt_rn(d2), g.R);
                         if (!(rr2 < 1.0)) continue;
@@ -125,28 +138,31 @@ __global__ void __launch_bounds__(kFWarps * 32)
                         if (rf >= float(NB)) continue;
                         k = int(rf);
                     }
-                    atomicAdd(&C[a][k], 1);
-                    atomicAdd(&H[a][k], ph);
+                    atomicAdd(&cnt[a][k], 1);
+                    atomicAdd(&hs[a][k], ph);
                 }
             }
         }
-        __syncwarp();
-        for (int a = lane; a < ma; a += 32) {
-            const int s = cs + a0 + a;
-            int n = 0;
+        __syncthreads();
+        // 16 threads per centre, one per bin; every thread takes every pass (the shuffles
+        // below involve the whole warp)
+        for (int a1 = 0; a1 < ma; a1 += kFThreads / NB) {
+            const int a = a1 + (threadIdx.x >> 4);
+            const int k = threadIdx.x & (NB - 1);
+            const bool ok = a < ma;
+            const int ck = ok ? cnt[a][k] : 0;
+            // support count: the 16 bins of this centre (the other half-warp holds another)
+            int n = ck;
 #pragma unroll
-            for (int k = 0; k < NB; ++k) n += C[a][k];
-            const double inv_n = 1.0 / double(max(n, 1));
-            const double inv_sig = 1.0 / sigma[bd.crow[s].w];
-            float* out = feat + (long long)bd.cperm[s] * NF;
-#pragma unroll
-            for (int k = 0; k < NB; ++k) {
-                const int ck = C[a][k];
-                out[k] = float(double(ck) * inv_n);
-                out[NB + k] = ck > 0 ? float(double(H[a][k]) / double(ck) * inv_sig) : 0.0f;
+            for (int o = 8; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o, NB);
+            if (ok) {
+                const int s = cs + a0 + a;
+                float* out = feat + (long long)bd.cperm[s] * NF;
+                out[k] = float(ck) / float(max(n, 1));
+                out[NB + k] = ck > 0 ? hs[a][k] / float(ck) * float(inv_sig) : 0.0f;
             }
         }
-        __syncwarp();
+        __syncthreads();
     }
 }
 
@@ -384,7 +400,7 @@ static rbf_status height_scales(rbf_ctx* ctx, cudaStream_t st) {
     if ((s = ensure(ctx, ctx->sigma, sizeof(double) * 3 * T, st)) != RBF_OK) return s;
     double* acc = ctx->sigma.as<double>() + T;
     RBF_CUDA_TRY(cudaMemsetAsync(acc, 0, sizeof(double) * 2 * T, st));
-    k_height_sums<<<div_up(ctx->g.ncell, 256), 256, 0, st>>>(
+    k_height_sums<<<div_up(ctx->g.ncell, kHWarps), kHWarps * 32, 0, st>>>(
         view(ctx), ctx->T > 0 ? ctx->rowtile.as<int>() : nullptr, acc);
     k_height_scale<<<div_up(T, 256), 256, 0, st>>>(acc, T, ctx->sigma.as<double>());
     ctx->launches += 2;
@@ -395,8 +411,8 @@ static rbf_status height_scales(rbf_ctx* ctx, cudaStream_t st) {
 rbf_status features_run(rbf_ctx* ctx, float* feat, double* sigma_out, cudaStream_t st) {
     rbf_status s = height_scales(ctx, st);
     if (s != RBF_OK) return s;
-    // one warp per cell (cells without centres return at once)
-    k_features_cell<<<div_up(ctx->g.ncell, kFWarps), kFWarps * 32, 0, st>>>(
+    // one block per cell (cells without centres return at once)
+    k_features_cell<<<ctx->g.ncell, kFThreads, 0, st>>>(
         view(ctx), ctx->sigma.as<double>(), feat);
     ctx->launches += 1;
     if (sigma_out)

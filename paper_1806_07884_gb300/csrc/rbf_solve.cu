@@ -53,6 +53,9 @@ struct CgScalars {
     double out_rr, out_gamma;    // result, written when the solve stops
     int out_it, out_state;
     double acc_delta[2][kAccSlots];   // u^T B u of the SpMV of each parity, spread over slots
+    // grid barrier of the persistent solve kernel: arrivals, generation, timed-out flag
+    unsigned int bar_count, bar_gen;
+    int bar_err, bar_pad;
 };
 
 
@@ -489,6 +492,258 @@ __global__ void k_cg_cond(CgScalars* __restrict__ sc, cudaGraphConditionalHandle
     cudaGraphSetConditional(h, more ? 1u : 0u);
 }
 
+// ---------------------------------------------------------------------------------------
+// Persistent solve: the whole CG loop of one system in a single cooperative launch (every
+// block resident), the SpMV and the update of each iteration separated by grid barriers
+// instead of kernel boundaries. Per iteration k (parity P = k & 1):
+//   SpMV phase   w_P += B u (the warps stride over the row groups as in k_cg_spmv), delta_k
+//                into the slots acc_delta[P]; each thread then loads its first row's vectors
+//   barrier
+//   scalar step  every block sums the slots and takes gamma_k, (r_k, r_k) from the previous
+//                update's per-block partials (block order): identical alpha, beta and stop
+//                decision in every block
+//   update phase the rows (as k_cg_update), per-block partials of gamma_{k+1}, (r_{k+1},
+//                r_{k+1}); w of the other parity zeroed
+//   barrier
+// Vectors written inside the kernel are read through L2 (ld.global.cg), never a stale L1
+// line. The barrier is a counter and a generation word in device memory; every wait is
+// bounded (kBarrierTimeoutNs by the global timer), after which the waiter raises bar_err and
+// all blocks leave the loop (the host reports RBF_ERR_TIMEOUT). Cooperative launch rejects a
+// grid that cannot be resident at once, so no block waits for one that has not started.
+constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;   // 2 s
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned int* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// All blocks of the grid; false (in every thread of the block) if the wait timed out or
+// another block's did.
+__device__ bool grid_barrier(CgScalars* sc, unsigned nblk) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned g = ld_acquire_gpu(&sc->bar_gen);
+        __threadfence();
+        if (atomicAdd(&sc->bar_count, 1u) == nblk - 1) {
+            atomicExch(&sc->bar_count, 0u);
+            __threadfence();
+            atomicAdd(&sc->bar_gen, 1u);
+        } else {
+            const unsigned long long t0 = global_ns();
+            unsigned n = 0;
+            while (ld_acquire_gpu(&sc->bar_gen) == g) {
+                if ((++n & 31u) == 0 &&
+                    (*reinterpret_cast<volatile int*>(&sc->bar_err) != 0 ||
+                     global_ns() - t0 > kBarrierTimeoutNs)) {
+                    atomicExch(&sc->bar_err, 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kSpmvWarps * 32, sizeof(T) == 4 ? 3 : 2)
+    k_cg_persist(Binned bd, CgVec<T> v, const T* __restrict__ B, CgScalars* __restrict__ sc,
+                 const T* __restrict__ pinit, int ninit, T* __restrict__ pbuf, int bar_extra) {
+    constexpr int NT = kSpmvWarps * 32;
+    using T2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
+    __shared__ GroupSmem gsm[kSpmvWarps];
+    __shared__ T s_g[2];      // gamma_k, (r_k, r_k)
+    __shared__ T s_ab[2];     // alpha_k, beta_k
+    __shared__ int s_go;
+    __shared__ T rsm[NT];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned nblk = gridDim.x;
+    // arrivals that complete a barrier: the grid, plus a test hook's blocks that never come
+    const unsigned narrive = nblk + unsigned(bar_extra);
+    const int gw = blockIdx.x * kSpmvWarps + wid, nw = gridDim.x * kSpmvWarps;
+    const int M = bd.M, ngroup = bd.ngroup;
+    const int nthr = gridDim.x * NT;
+    const int i_first = blockIdx.x * NT + threadIdx.x;
+    // scalar state (thread 0 of every block, identical in all blocks)
+    T gprev = T(1), aprev = T(1);
+    int it = 0, state = kRunning;
+    const T tol2bb = T(sc->tol2) * T(sc->bb);
+    const int maxit = sc->maxit;
+    // Warp 0 sums per-block partials (gamma, (r, r)) in block order into s_g.
+    auto sum_partials = [&](const T* part, int n) {
+        const T2* pb = reinterpret_cast<const T2*>(part);
+        T g = T(0), rr = T(0);
+        for (int b0 = lane; b0 < n; b0 += 32 * kPartBatch) {
+            T2 pv[kPartBatch];
+#pragma unroll
+            for (int k = 0; k < kPartBatch; ++k) {
+                const int b = b0 + 32 * k;
+                pv[k] = b < n ? __ldcg(pb + b) : T2{T(0), T(0)};
+            }
+#pragma unroll
+            for (int k = 0; k < kPartBatch; ++k) {
+                g += pv[k].x;
+                rr += pv[k].y;
+            }
+        }
+        g = warp_sum<T>(g);
+        rr = warp_sum<T>(rr);
+        if (lane == 0) {
+            s_g[0] = g;
+            s_g[1] = rr;
+        }
+    };
+    if (wid == 0) sum_partials(pinit, ninit);
+    if (gw < ngroup) stage_group(bd.gdesc, gw, gsm[wid], 0, lane);
+    bool timed_out = false;
+    for (int P = 0;; P ^= 1) {
+        const T* __restrict__ rP = P ? v.r[1] : v.r[0];
+        const T* __restrict__ sP = P ? v.s[1] : v.s[0];
+        T* __restrict__ wP = P ? v.w[1] : v.w[0];
+        // ---- SpMV phase
+        if (gw < ngroup) {
+            T d = T(0);
+            int b = 0;
+            for (int q = gw; q < ngroup; q += nw, b ^= 1) {
+                if (q + nw < ngroup) {
+                    stage_group(bd.gdesc, q + nw, gsm[wid], b ^ 1, lane);
+                    group_wait<1>();
+                } else {
+                    group_wait<0>();
+                }
+                d += spmv_group<T>(b, B, v.u, wP, M, lane, gsm[wid]);
+            }
+            // the records are fixed: the next iteration's first one travels during the barrier
+            stage_group(bd.gdesc, gw, gsm[wid], 0, lane);
+            d = warp_sum<T>(d);
+            if (lane == 0 && d != T(0)) atomicAdd(&sc->acc_delta[P][gw & (kAccSlots - 1)], double(d));
+        }
+        // this thread's first row, loaded before the barrier (none of it changes in the SpMV)
+        T f_d = T(0), f_s = T(0), f_p = T(0), f_u = T(0), f_r = T(0), f_x = T(0);
+        int4 f_cm = make_int4(0, 0, 0, 0);
+        if (i_first < M) {
+            f_d = __ldg(v.dinv + i_first);
+            f_s = __ldcg(sP + i_first);
+            f_p = __ldcg(v.p + i_first);
+            f_u = __ldcg(v.u + i_first);
+            f_r = __ldcg(rP + i_first);
+            f_x = __ldcg(v.x + i_first);
+            f_cm = __ldg(bd.crow + i_first);
+        }
+        if (!grid_barrier(sc, narrive)) {
+            timed_out = true;
+            break;
+        }
+        // ---- scalar step
+        const T f_w = i_first < M ? __ldcg(wP + i_first) : T(0);
+        if (wid == 0) {
+            T d = T(__ldcg(&sc->acc_delta[P][lane])) + T(__ldcg(&sc->acc_delta[P][lane + 32]));
+            d = warp_sum<T>(d);
+            if (lane == 0) {
+                const T g = s_g[0], rr = s_g[1];
+                T alpha = T(0), beta = T(0);
+                if (!isfinite(g) || !isfinite(rr)) {
+                    state = kBreakdown;
+                } else if (rr <= tol2bb) {
+                    state = kConverged;
+                } else if (it >= maxit) {
+                    state = kMaxIt;
+                } else {
+                    beta = it == 0 ? T(0) : g / gprev;
+                    const T den = it == 0 ? d : d - beta * g / aprev;
+                    alpha = g / den;
+                    if (!(den > T(0)) || !isfinite(alpha)) state = kBreakdown;
+                }
+                s_ab[0] = alpha;
+                s_ab[1] = beta;
+                s_go = state == kRunning;
+                if (state == kRunning) {
+                    gprev = g;
+                    aprev = alpha;
+                } else if (blockIdx.x == 0) {
+                    sc->out_rr = double(rr);
+                    sc->out_gamma = double(g);
+                    sc->out_it = it;
+                    sc->out_state = state;
+                }
+            }
+            // the slots of the other parity were last read before the previous barrier
+            if (blockIdx.x == 0) {
+                sc->acc_delta[P ^ 1][lane] = 0.0;
+                sc->acc_delta[P ^ 1][lane + 32] = 0.0;
+            }
+        }
+        __syncthreads();
+        if (!s_go) break;
+        ++it;
+        // ---- update phase
+        const T ta = s_ab[0], tb = s_ab[1];
+        T* __restrict__ rQ = P ? v.r[0] : v.r[1];
+        T* __restrict__ sQ = P ? v.s[0] : v.s[1];
+        T* __restrict__ wQ = P ? v.w[0] : v.w[1];
+        T acc[2] = {T(0), T(0)};
+        for (int base = blockIdx.x * NT; base < M; base += nthr) {
+            const int i = base + threadIdx.x;
+            const bool valid = i < M;
+            const bool first = i == i_first;
+            T di = T(0), ri = T(0);
+            if (valid) {
+                di = first ? f_d : __ldg(v.dinv + i);
+                const T wi = di == T(0) ? T(0) : (first ? f_w : __ldcg(wP + i));
+                const T si = fma(tb, first ? f_s : __ldcg(sP + i), wi);
+                const T pi = fma(tb, first ? f_p : __ldcg(v.p + i), first ? f_u : __ldcg(v.u + i));
+                ri = di == T(0) ? T(0) : fma(-ta, si, first ? f_r : __ldcg(rP + i));
+                sQ[i] = si;
+                v.p[i] = pi;
+                v.x[i] = fma(ta, pi, first ? f_x : __ldcg(v.x + i));
+                rQ[i] = ri;
+                wQ[i] = T(0);
+            }
+            rsm[threadIdx.x] = ri;
+            __syncthreads();
+            if (valid) {
+                const int4 cm = first ? f_cm : __ldg(bd.crow + i);
+                const T ui = apply_prec<T>(bd, v.bjinv, cm, i, di, ri, [&](int j) {
+                    const int o = j - base;
+                    return o >= 0 && o < NT ? rsm[o]
+                                            : next_r(__ldcg(rP + j), __ldcg(sP + j), __ldcg(wP + j), ta, tb);
+                });
+                v.u[i] = ui;
+                acc[0] = fma(ri, ui, acc[0]);
+                acc[1] = fma(ri, ri, acc[1]);
+            }
+            __syncthreads();
+        }
+        double tot[2];
+        block_sum_t<2, T>(acc, tot);
+        if (threadIdx.x == 0) {
+            T* pb = pbuf + size_t(P ^ 1) * 2 * nblk;
+            pb[2 * blockIdx.x] = T(tot[0]);
+            pb[2 * blockIdx.x + 1] = T(tot[1]);
+        }
+        if (!grid_barrier(sc, narrive)) {
+            timed_out = true;
+            break;
+        }
+        if (wid == 0) sum_partials(pbuf + size_t(P ^ 1) * 2 * nblk, int(nblk));
+    }
+    // no copy of this thread may still be in flight when the block ends
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    if (timed_out && blockIdx.x == 0 && threadIdx.x == 0) sc->out_state = kBreakdown;
+}
+
 // Preconditioner set-up, one warp per cell: dinv[s] = 1 / B_ss for centres with at least
 // min_support points inside their support, else 0 (pinned: row and column removed from the
 // system); and, for cells with m <= kMaxBlock, the inverse of the cell's diagonal block
@@ -713,7 +968,7 @@ void launch_iteration(rbf_ctx* ctx, const CgVec<T>& v, int P, cudaStream_t cs,
                       const PolyCg<T>& pq = PolyCg<T>()) {
     const Binned bd = view(ctx);
     CgScalars* sc = ctx->scal.as<CgScalars>();
-    k_cg_spmv<T><<<spmv_grid_T<T>(ctx), kSpmvWarps * 32, 0, cs>>>(bd, ctx->bvals.as<T>(), v.u,
+    k_cg_spmv<T><<<spmv_grid_T<T>(ctx), kSpmvWarps * 32, 0, cs>>>(bd, bvals_dev<T>(ctx), v.u,
                                                                   v.w[P], P, sc);
     k_cg_update<T><<<vec_grid(ctx), kVecThreads, 0, cs>>>(bd, v, P, sc, ctx->partial.as<T>(),
                                                           pq.E, pq.pe, pq.pd);
@@ -728,7 +983,7 @@ rbf_status cg_graph(rbf_ctx* ctx, cudaGraphExec_t* out, bool poly) {
     rbf_ctx::SolveGraph& sg = ctx->cg_graph[sizeof(T) == 8 ? 0 : 1];
     const CgVec<T> v = cg_vectors<T>(ctx);
     const PolyCg<T> pq = poly_cg<T>(ctx, poly);
-    const void* key[12] = {ctx->bvals.p, v.x, v.dinv, v.bjinv, ctx->scal.p, ctx->partial.p,
+    const void* key[12] = {bvals_dev<void>(ctx), v.x, v.dinv, v.bjinv, ctx->scal.p, ctx->partial.p,
                            ctx->cstart.p, ctx->rmeta.p, ctx->gdesc.p, ctx->bjoff.p, pq.E, pq.pe};
     bool hit = sg.exec && sg.ncell == ctx->g.ncell && sg.M == ctx->M && sg.gx == ctx->g.gx &&
                sg.crow == ctx->crow.p && sg.ngroup == ctx->ngroup;
@@ -798,7 +1053,7 @@ rbf_status cg_start(rbf_ctx* ctx, const TB* b, double bscale, bool use_x0, doubl
     RBF_CUDA_TRY(cudaMemcpyAsync(sc, &h, sizeof(CgScalars), cudaMemcpyHostToDevice, st));
     if (use_x0) {
         RBF_CUDA_TRY(cudaMemsetAsync(v.w[1], 0, sizeof(T) * ctx->M, st));
-        k_spmv<T><<<spmv_grid_T<T>(ctx), kSpmvWarps * 32, 0, st>>>(bd, ctx->bvals.as<T>(), v.x, v.w[1]);
+        k_spmv<T><<<spmv_grid_T<T>(ctx), kSpmvWarps * 32, 0, st>>>(bd, bvals_dev<T>(ctx), v.x, v.w[1]);
         ctx->launches += 1;
     }
     double* part = ctx->partial.as<double>();
@@ -813,24 +1068,92 @@ rbf_status cg_start(rbf_ctx* ctx, const TB* b, double bscale, bool use_x0, doubl
     return RBF_OK;
 }
 
+// Blocks of the persistent solve kernel that fit on the device at once (0: none).
+template <typename T>
+int persist_grid(rbf_ctx* ctx) {
+    int& per_sm = ctx->persist_blocks_per_sm[sizeof(T) == 8 ? 0 : 1];
+    if (per_sm == 0) {
+        int a = 0, coop = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_cg_persist<T>, kSpmvWarps * 32, 0) !=
+                cudaSuccess ||
+            cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device) != cudaSuccess) {
+            cudaGetLastError();
+            a = 0;
+        }
+        per_sm = (a > 0 && coop) ? a : -1;
+    }
+    if (per_sm < 0) return 0;
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    return per_sm * sms;
+}
+
+// Per-block partials of the persistent kernel: after the start kernel's (4 + 1) vec_grid
+// slots, rounded up to an even number of doubles so that the pairs it reads as one 16-byte
+// vector (double2 in FP64) stay aligned.
+inline size_t persist_offset(rbf_ctx* ctx) {
+    return (5 * size_t(std::max(vec_grid(ctx), 1)) + 1) & ~size_t(1);
+}
+template <typename T>
+T* persist_partials(rbf_ctx* ctx) {
+    return reinterpret_cast<T*>(ctx->partial.as<double>() + persist_offset(ctx));
+}
+
 // Preconditioned CG on the assembled B (precision T) for B x = bscale * b: start kernels on
-// `st`, then one launch of the solve graph.
+// `st`, then the iteration loop -- one cooperative launch of the persistent kernel (single
+// systems without the polynomial rows), else one launch of the solve graph.
 template <typename T, typename TB>
 rbf_status run_cg(rbf_ctx* ctx, const TB* b, double bscale, bool use_x0, double tol, int maxit,
                   int* iters, double* relres, int* state, cudaStream_t st, bool poly = false,
                   const double* bk = nullptr) {
     rbf_status s;
-    cudaGraphExec_t ex;
-    if ((s = cg_graph<T>(ctx, &ex, poly)) != RBF_OK) return s;
-    if ((s = cg_start<T, TB>(ctx, b, bscale, use_x0, tol, maxit, st, poly, bk)) != RBF_OK) return s;
-    RBF_CUDA_TRY(cudaGraphLaunch(ex, st));
+    const int pgrid = (!poly && ctx->cg_persistent && ctx->T == 0) ? persist_grid<T>(ctx) : 0;
+    bool persisted = false;
+    if (pgrid > 0) {
+        if ((s = ensure(ctx, ctx->partial, sizeof(double) * (persist_offset(ctx) + 4 * size_t(pgrid)),
+                        st)) != RBF_OK)
+            return s;
+        if ((s = cg_start<T, TB>(ctx, b, bscale, use_x0, tol, maxit, st)) != RBF_OK) return s;
+        Binned bd = view(ctx);
+        CgVec<T> v = cg_vectors<T>(ctx);
+        const T* B = bvals_dev<T>(ctx);
+        CgScalars* sc = ctx->scal.as<CgScalars>();
+        const T* pinit = reinterpret_cast<const T*>(ctx->partial.p);
+        int ninit = vec_grid(ctx);
+        T* pbuf = persist_partials<T>(ctx);
+        int extra = ctx->cg_barrier_extra;
+        void* args[] = {&bd, &v, &B, &sc, &pinit, &ninit, &pbuf, &extra};
+        const cudaError_t e = cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(k_cg_persist<T>),
+                                                          dim3(pgrid), dim3(kSpmvWarps * 32), args, 0, st);
+        if (e == cudaSuccess) {
+            persisted = true;
+            ctx->launches += 1;
+        } else {
+            // not resident at once (another context holds SMs, say): the graph loop instead,
+            // from the start kernel's state
+            cudaGetLastError();
+            ctx->persist_blocks_per_sm[sizeof(T) == 8 ? 0 : 1] = -1;
+        }
+    }
+    if (!persisted) {
+        cudaGraphExec_t ex;
+        if ((s = cg_graph<T>(ctx, &ex, poly)) != RBF_OK) return s;
+        if (pgrid == 0)
+            if ((s = cg_start<T, TB>(ctx, b, bscale, use_x0, tol, maxit, st, poly, bk)) != RBF_OK) return s;
+        RBF_CUDA_TRY(cudaGraphLaunch(ex, st));
+    }
     CgScalars* hs = static_cast<CgScalars*>(ctx->hpinned);
     RBF_CUDA_TRY(cudaMemcpyAsync(hs, ctx->scal.p, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
     RBF_CUDA_TRY(cudaStreamSynchronize(st));
-    // kernels launched by the graph: per loop pass 2 * kItersPerBody + 1; the stop is detected
-    // one kernel after the last iteration, so the passes cover out_it + 1 iterations
-    const int passes = hs->out_it / kItersPerBody + 1;
-    ctx->launches += int64_t(passes) * (2 * kItersPerBody + 1);
+    if (persisted && hs->bar_err)
+        return set_err(ctx, RBF_ERR_TIMEOUT, "a grid barrier of the persistent CG solve timed out");
+    if (!persisted) {
+        // kernels launched by the graph: per loop pass 2 * kItersPerBody + 1; the stop is
+        // detected one kernel after the last iteration, so the passes cover out_it + 1
+        // iterations
+        const int passes = hs->out_it / kItersPerBody + 1;
+        ctx->launches += int64_t(passes) * (2 * kItersPerBody + 1);
+    }
     *iters = hs->out_it;
     *relres = hs->bb > 0 ? sqrt(hs->out_rr / hs->bb) : 0.0;
     *state = hs->out_state;
@@ -881,7 +1204,7 @@ rbf_status bench_spmv_impl(rbf_ctx* ctx, int reps, cudaStream_t st) {
     k_fill<T><<<div_up(ctx->M, 256), 256, 0, st>>>(v.u, ctx->M, T(1));
     RBF_CUDA_TRY(cudaMemsetAsync(v.w[0], 0, sizeof(T) * ctx->M, st));
     for (int k = 0; k < reps; ++k)
-        k_spmv<T><<<spmv_grid_T<T>(ctx), kSpmvWarps * 32, 0, st>>>(bd, ctx->bvals.as<T>(), v.u, v.w[0]);
+        k_spmv<T><<<spmv_grid_T<T>(ctx), kSpmvWarps * 32, 0, st>>>(bd, bvals_dev<T>(ctx), v.u, v.w[0]);
     RBF_CUDA_TRY(cudaGetLastError());
     ctx->launches += reps + 1;
     return RBF_OK;
@@ -896,12 +1219,12 @@ rbf_status prec_setup_run(rbf_ctx* ctx, int prec, int min_support, int* npin_d, 
     const Binned bd = view(ctx);
     const int nb = div_up(ctx->g.ncell, kBjWarps);
     if (prec == RBF_FP64)
-        k_prec_setup<double><<<nb, kBjWarps * 32, 0, st>>>(bd, ctx->bvals.as<double>(),
+        k_prec_setup<double><<<nb, kBjWarps * 32, 0, st>>>(bd, bvals_dev<double>(ctx),
                                                            ctx->support.as<int>(), min_support,
                                                            ctx->dinv.as<double>(),
                                                            ctx->bjinv.as<double>(), npin_d);
     else
-        k_prec_setup<float><<<nb, kBjWarps * 32, 0, st>>>(bd, ctx->bvals.as<float>(),
+        k_prec_setup<float><<<nb, kBjWarps * 32, 0, st>>>(bd, bvals_dev<float>(ctx),
                                                           ctx->support.as<int>(), min_support,
                                                           ctx->dinv32.as<float>(),
                                                           ctx->bjinv32.as<float>(), npin_d);
@@ -925,10 +1248,10 @@ void launch_spmv(rbf_ctx* ctx, int prec, const void* x, void* y, cudaStream_t st
     const Binned bd = view(ctx);
     if (prec == RBF_FP64)
         k_spmv<double><<<spmv_grid_T<double>(ctx), kSpmvWarps * 32, 0, st>>>(
-            bd, ctx->bvals.as<double>(), static_cast<const double*>(x), static_cast<double*>(y));
+            bd, bvals_dev<double>(ctx), static_cast<const double*>(x), static_cast<double*>(y));
     else
         k_spmv<float><<<spmv_grid_T<float>(ctx), kSpmvWarps * 32, 0, st>>>(
-            bd, ctx->bvals.as<float>(), static_cast<const float*>(x), static_cast<float*>(y));
+            bd, bvals_dev<float>(ctx), static_cast<const float*>(x), static_cast<float*>(y));
     ctx->launches += 1;
 }
 
@@ -961,7 +1284,7 @@ rbf_status solve_run(rbf_ctx* ctx, double* c, int use_c0, double tol, int maxit,
         ENS(dinv, sizeof(double) * M);
         ENS(bjinv, sizeof(double) * std::max<int64_t>(ctx->nbj, 1));
         k_prec_setup<double><<<div_up(ctx->g.ncell, kBjWarps), kBjWarps * 32, 0, st>>>(
-            bd, ctx->bvals.as<double>(), ctx->support.as<int>(), min_support,
+            bd, bvals_dev<double>(ctx), ctx->support.as<int>(), min_support,
             ctx->dinv.as<double>(), ctx->bjinv.as<double>(), npin_d);
         ctx->launches += 1;
         const CgVec<double> v = cg_vectors<double>(ctx);
@@ -984,7 +1307,7 @@ rbf_status solve_run(rbf_ctx* ctx, double* c, int use_c0, double tol, int maxit,
         ENS(dinv32, sizeof(float) * M);
         ENS(bjinv32, sizeof(float) * std::max<int64_t>(ctx->nbj, 1));
         k_prec_setup<float><<<div_up(ctx->g.ncell, kBjWarps), kBjWarps * 32, 0, st>>>(
-            bd, ctx->bvals.as<float>(), ctx->support.as<int>(), min_support,
+            bd, bvals_dev<float>(ctx), ctx->support.as<int>(), min_support,
             ctx->dinv32.as<float>(), ctx->bjinv32.as<float>(), npin_d);
         ctx->launches += 1;
         const CgVec<float> v = cg_vectors<float>(ctx);

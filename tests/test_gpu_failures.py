@@ -5,7 +5,9 @@
 * a workspace allocator that returns NULL makes the call that needed the memory return
   RBF_ERR_ALLOC with a message; with room again the same context completes the fit;
 * an allocator with no room for the stored values of A keeps the matrix-free residual and
-  still reaches the oracle's surface."""
+  still reaches the oracle's surface;
+* a grid-barrier wait of the persistent CG kernel that runs out (a barrier told to wait for a
+  block that does not exist) returns RBF_ERR_TIMEOUT and leaves the context usable."""
 import ctypes as C
 
 import numpy as np
@@ -146,3 +148,25 @@ def test_no_room_for_stored_a_keeps_the_matrix_free_residual():
     f_ref = O.evaluate(c_ref, pb.centres, pb.points, pb.R, pb.kernel)
     assert O.rel_err(f, f_ref) <= MIXED_BAR
     assert lib.rbf_destroy(h) == 0
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_refine"])
+def test_barrier_wait_that_runs_out_is_a_timeout(prec):
+    """The persistent solve's grid barriers are told to wait for one block more than the grid
+    has (the "cg_barrier_test" hook): every wait runs out after its 2 s limit, every block
+    leaves, rbf_solve returns RBF_ERR_TIMEOUT, and the same context then completes the fit."""
+    pb = dg.config_franke(seed=22, N=4000, M=400)
+    c_ref, _ = O.fit(pb.points, pb.h, pb.centres, pb.R, pb.kernel)
+    ctx = _binned(pb, prec)
+    ctx.set_param("cg_persistent", 1)
+    ctx.set_param("cg_barrier_test", 1)
+    with pytest.raises(pkg.RBFError) as e:
+        ctx.solve(tol=1e-13)
+    assert "RBF_ERR_TIMEOUT" in str(e.value)
+    ctx.set_param("cg_barrier_test", 0)
+    c, info = ctx.solve(tol=1e-13)
+    assert info["status"] == 0
+    f = O.evaluate(c.cpu().numpy(), pb.centres, pb.points, pb.R, pb.kernel)
+    f_ref = O.evaluate(c_ref, pb.centres, pb.points, pb.R, pb.kernel)
+    assert O.rel_err(f, f_ref) <= (FP64_BAR if prec == "fp64" else MIXED_BAR)
+    ctx.close()

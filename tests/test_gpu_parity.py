@@ -198,6 +198,39 @@ def test_pinned_centre_far_from_data():
         ctx.close()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32_refine"])
+@pytest.mark.parametrize("case", ["terrain", "clustered", "ragged", "tiny", "single"])
+def test_persistent_and_graph_loops_agree(case, prec):
+    """The CG loop as one cooperative launch of the persistent kernel and as the CUDA graph of
+    two kernels per iteration: the same iterates up to the order of the FP
+    additions, so the oracle's surface, the same iteration count within 3% in FP64, and in
+    FP32 + refinement (whose FP32 atomics make the count vary from run to run in either
+    loop) within 15% unless a stalled refinement promoted one of the two solves to FP64."""
+    pb = _assembly_case(case)
+    c_ref, _ = O.fit(pb.points, pb.h, pb.centres, pb.R, pb.kernel, method="cholesky")
+    f_ref = O.evaluate_grid(c_ref, pb.centres, pb.R, pb.kernel, 33)
+    ctx = _binned(pb, prec=prec)
+    out = {}
+    for persistent in (1, 0):
+        ctx.set_param("cg_persistent", persistent)
+        n0 = ctx.launch_count()
+        c, info = ctx.solve(tol=1e-13)
+        out[persistent] = (info, ctx.launch_count() - n0)
+        f = ctx.eval_grid(c, 33, 33, pb.bbox).cpu().numpy()
+        assert O.rel_err(f, f_ref) <= (FP64_BAR if prec == "fp64" else MIXED_BAR), persistent
+    i1, i0 = out[1][0], out[0][0]
+    it1, it0 = i1["iterations"], i0["iterations"]
+    if prec == "fp64":
+        assert abs(it1 - it0) <= max(2, 0.03 * it0), (i1, i0)
+    elif not (i1["promoted"] or i0["promoted"]):
+        assert abs(it1 - it0) <= max(4, 0.15 * it0), (i1, i0)
+    # one launch per inner solve against 2 per iteration in the graph (when CG ran at all:
+    # a system whose centres are all pinned has nothing to solve)
+    if it0 > 0:
+        assert out[1][1] < out[0][1], (out[1], out[0])
+    ctx.close()
+
+
 def test_warm_start_and_determinism():
     pb = dg.config_franke(seed=9, N=8000, M=800)
     c_ref, _ = O.fit(pb.points, pb.h, pb.centres, pb.R, pb.kernel)

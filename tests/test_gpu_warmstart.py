@@ -131,6 +131,13 @@ def _problems(pbs):
     return [(p.points, p.h, p.centres, p.R, p.bbox) for p in pbs]
 
 
+# The learned start's measured iteration ratio on the held-out tiles below (FP32 + FP64
+# refinement to 1e-10): about 1 -- what the start vector gains is its residual and surface
+# error, not CG iterations (tests/test_warmstart_bound.py: a start must be within ~3% of the
+# answer in every mode to save 15%).
+RATIO_BAND = (0.93, 1.03)
+
+
 def test_training_reduces_loss_and_what_the_warm_start_gains():
     """Train on 48 solved tiles with the library's own kernels, then start the solver of 8
     held-out tiles from the network's prediction. What it gains: the start vector's normal
@@ -167,7 +174,10 @@ def test_training_reduces_loss_and_what_the_warm_start_gains():
     c_warm, i_warm, t_warm = ctx.solve_tiles(tol=1e-10, c0=c0)
     it_cold = sum(t["iterations"] for t in t_cold)
     it_warm = sum(t["iterations"] for t in t_warm)
-    assert it_warm <= 1.05 * it_cold, (it_warm, it_cold)
+    ratio = it_warm / it_cold
+    print(f"learned start / cold start CG iterations on 8 held-out tiles: {it_warm} / {it_cold}"
+          f" = {ratio:.4f}")
+    assert RATIO_BAND[0] <= ratio <= RATIO_BAND[1], (it_warm, it_cold)
     assert all(t["status"] == 0 for t in t_warm)
     for k, pb in enumerate(test_pbs):
         t = tiles[k]
