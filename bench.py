@@ -364,6 +364,7 @@ def bench_batched(args, rank, dev, stream, flush, hbm, peak_source):
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
         gc.enable()
+        timed.step_ms = [round(x, 3) for x in ms]
         return statistics.mean(ms), info, tinfo
 
     for _ in range(2):                     # warm-up (the first one runs the autotuner)
@@ -441,6 +442,7 @@ def bench_batched(args, rank, dev, stream, flush, hbm, peak_source):
     out = {"workload": f"{args.tiles} tiles, N log-uniform in [2000, 200000], M = N/10, "
                        f"Wendland phi_3,1, K=30, sum N = {Ntot}, sum M = {Mtot}",
            "value": Ntot / (ms * 1e-3), "unit": "points/s", "ms_per_step": round(ms, 3),
+           "step_ms": timed.step_ms,
            "prec": args.prec, "tol": args.tol, "gpu_launches_per_step": launches,
            "iterations_max": info["iterations"], "refinements_max": info["refinements"],
            "iterations_mean": round(float(np.mean([t["iterations"] for t in tinfo])), 1),
@@ -755,6 +757,13 @@ def main():
     s1.record(stream)
     torch.cuda.synchronize()
     cg_iter_us = s0.elapsed_time(s1) * 1e3 / 100
+    # the solver's own loop (one cooperative launch of the persistent kernel here)
+    ctx.bench_cg_loop(50)
+    s0.record(stream)
+    ctx.bench_cg_loop(500)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    cg_loop_us = s0.elapsed_time(s1) * 1e3 / 500
     achieved = alg / (spmv_ms * 1e-3) / 1e9
     # L2 ceiling: the terrain's stored B fits in the 126 MB L2, so its SpMV streams from L2;
     # a plain device copy of a 24 MiB buffer (read + write 48 MiB, resident in L2), timed
@@ -779,10 +788,56 @@ def main():
                 "launch_ms": round(spmv_ms, 5),
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
                 "cg_iteration_us_plain_launches": round(cg_iter_us, 2),
+                "cg_iteration_us_solver_loop": round(cg_loop_us, 2),
                 "l2": {"peak": round(l2_gbs, 1), "unit": "GB/s",
                        "frac": round(achieved / l2_gbs, 4),
                        "peak_source": "measured in this run: device copy of 24 MiB, read + write",
                        "b_fits_in_l2": stored < 100e6}}
+
+    # ---- FMA peaks of this GPU, measured in this run, and the FP64 refinement residual
+    def fma_tflops(prec, reps):
+        ctx.bench_fma(prec, max(1, reps // 8))
+        s0.record(stream)
+        fl = ctx.bench_fma(prec, reps)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        return fl / (s0.elapsed_time(s1) * 1e-3) / 1e12
+    fma = {"fp32_tflops": round(fma_tflops("fp32_refine", 1 << 16), 2),
+           "fp64_tflops": round(fma_tflops("fp64", 1 << 12), 3),
+           "source": "measured in this run: 8 independent FMA chains per thread, 8 blocks of "
+                     "256 threads per SM (rbf_bench_fma)"}
+    alu = []
+    if args.prec == "fp32_refine":
+        # A's nonzeros = the support counts summed (pairs with ||x_i - xi_j|| < R)
+        sup = ctx.export_upper()[4]
+        nnz_a = int(sup.sum().item())
+        del sup
+        ctx.bench_residual(2)
+        s0.record(stream)
+        ctx.bench_residual(10)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        res_ms = s0.elapsed_time(s1) / 10
+        fl = 4.0 * nnz_a          # A c and A^T e: one FMA per nonzero each
+        ach = fl / (res_ms * 1e-3) / 1e12
+        alu.append({"kernel": "k_residual_stored (FP64 refinement residual r = A^T (h - A x))",
+                    "bound": "fp64", "achieved": round(ach, 3), "peak": fma["fp64_tflops"],
+                    "unit": "TFLOP/s", "frac": round(ach / fma["fp64_tflops"], 4),
+                    "flops_per_launch": fl, "model": "4 flops per nonzero of A (A c, A^T e)",
+                    "a_nonzeros": nnz_a, "launch_ms": round(res_ms, 4),
+                    "stored_a_bytes_per_launch": 8 * nnz_a})
+    # the evaluation grid: pairs (node, centre within R) ~ nodes x M pi R^2 / area
+    area = (pb.bbox[2] - pb.bbox[0]) * (pb.bbox[3] - pb.bbox[1])
+    pairs = n * n * M * np.pi * pb.R ** 2 / area
+    fl = 19.0 * pairs
+    ach = fl / (phases["eval"] * 1e-3) / 1e12
+    alu.append({"kernel": f"k_eval_grid ({n}^2 nodes, FP64 Wendland sums)", "bound": "fp64",
+                "achieved": round(ach, 3), "peak": fma["fp64_tflops"], "unit": "TFLOP/s",
+                "frac": round(ach / fma["fp64_tflops"], 4), "flops_per_launch": round(fl),
+                "model": "19 FP64 flops per node-centre pair in support (difference, r^2, "
+                         "square root, Wendland polynomial, accumulation); pairs estimated as "
+                         "nodes x M pi R^2 / area", "pairs": round(pairs),
+                "launch_ms": phases["eval"]})
 
     # ---- accuracy: this path's surface against a tight FP64 solve of the same workload
     f_fast = fbuf.clone()
@@ -818,6 +873,23 @@ def main():
         fp64_ms = t0.elapsed_time(t1)
         fp64 = {"value": N / (fp64_ms * 1e-3), "ms_per_step": round(fp64_ms, 3),
                 "iterations": info64["iterations"], "tol": args.tol}
+        # the FP64 path's SpMV, on the FP64 B this step assembled: 2 FMA per off-diagonal
+        # stored nonzero (row and column products), 1 per diagonal one
+        if ctx.prec == "fp64":
+            ctx.bench_spmv(5)
+            s0.record(stream)
+            ctx.bench_spmv(50)
+            s1.record(stream)
+            torch.cuda.synchronize()
+            sp64_ms = s0.elapsed_time(s1) / 50
+            fl = 4.0 * (lst["nonzeros"] - M) + 2.0 * M
+            ach = fl / (sp64_ms * 1e-3) / 1e12
+            alu.append({"kernel": "k_spmv<double> (FP64 path)", "bound": "fp64",
+                        "achieved": round(ach, 3), "peak": fma["fp64_tflops"], "unit": "TFLOP/s",
+                        "frac": round(ach / fma["fp64_tflops"], 4), "flops_per_launch": fl,
+                        "model": "4 flops per off-diagonal upper nonzero, 2 per diagonal",
+                        "launch_ms": round(sp64_ms, 4),
+                        "bytes_per_launch": 8 * lst["stored_values"] + 3 * 8 * M})
         step(d, prec="fp64", tol=1e-13)
         f_ref = fbuf.clone()
         err = float((f_fast - f_ref).abs().max() / f_ref.abs().max())
@@ -901,6 +973,7 @@ def main():
                        "l2": "flushed before each step (512 MiB write)",
                        "parallelism": f"replicas x{world}"},
             "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu,
+            "fma_peaks": fma, "alu_rooflines": alu,
             "clocks": clocks, "accuracy": acc, "fp64_path": fp64, "other_start": other,
             "phases_ms": phases,
             "batched": batched,

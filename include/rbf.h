@@ -155,10 +155,11 @@ rbf_status rbf_assemble(rbf_ctx* ctx, rbf_kernel kernel, rbf_prec prec, void* st
  * min_support: centres whose support disc holds fewer data points are removed from
  *           the system and get c_j = 0 (the paper leaves empty supports undefined).
  * info    : HOST pointer, may be NULL.
- * Each CG solve runs as one launch of a CUDA graph looping over the two kernels of an
- * iteration, or, with "cg_persistent" 1 (where the device can hold its grid at once), as one
- * cooperative launch of a persistent kernel (SpMV and vector update of every iteration
- * separated by grid barriers). Both give the same iterates up to the order of FP additions.
+ * Each CG solve runs as one cooperative launch of a persistent kernel (SpMV and vector update
+ * of every iteration separated by grid barriers) or as one launch of a CUDA graph looping over
+ * the two kernels of an iteration ("cg_persistent"; the graph also where the device cannot
+ * hold the persistent grid at once). Both give the same iterates up to the order of FP
+ * additions.
  * Synchronises `stream`. Returns RBF_ERR_NOT_CONVERGED / RBF_ERR_BREAKDOWN with c
  * holding the last iterate, RBF_ERR_TIMEOUT if a barrier wait of the persistent kernel ran
  * out. With RBF_FP32_REFINE, a refinement step that no longer reduces
@@ -232,8 +233,11 @@ rbf_status rbf_eval_grid_poly(rbf_ctx* ctx, const double* c, const double* k, in
  *                      force the batched CG's SpMV blocks per SM (1..8), row groups per
  *                      SpMV work item (1..64) and update block size (128, 256 or 512); 0 =
  *                      automatic
- *   "cg_persistent"    0 (default): rbf_solve's CG loop as the CUDA graph of two kernels per
- *                      iteration; 1: as one cooperative launch of the persistent kernel
+ *   "cg_persistent"    how rbf_solve runs its CG loop: 1 as one cooperative launch of the
+ *                      persistent kernel, 0 as the CUDA graph of two kernels per iteration,
+ *                      -1 (default) the persistent kernel for FP64 and for FP32 systems of at
+ *                      most 4 x (SMs) x 768 centres, else the graph (the faster of the two on
+ *                      GB300 at each size)
  *   "cg_barrier_test"  test hook, 0 (default) or 1: the persistent kernel's barriers wait for
  *                      one block more than its grid has, so the first wait runs out (2 s) and
  *                      rbf_solve returns RBF_ERR_TIMEOUT
@@ -296,6 +300,25 @@ rbf_status rbf_bench_spmv(rbf_ctx* ctx, int reps, void* stream);
  * batched context, where the iterations are batched ones with every tile running).
  * Asynchronous. */
 rbf_status rbf_bench_cg(rbf_ctx* ctx, int reps, void* stream);
+
+/* Diagnostics / timing: run `reps` (>= 1) preconditioned CG iterations on B c = b from c = 0
+ * (tolerance 0) in the solver's own loop -- the persistent kernel or the graph, as rbf_solve
+ * chooses ("cg_persistent") -- so that time / reps is the loop's cost per iteration. Uses and
+ * overwrites the solver's workspace; requires a preceding rbf_solve on a single system.
+ * Synchronises `stream`. */
+rbf_status rbf_bench_cg_loop(rbf_ctx* ctx, int reps, void* stream);
+
+/* Diagnostics / timing: the device's FMA throughput in precision `prec` (RBF_FP64: FP64;
+ * RBF_FP32_REFINE: FP32): one kernel in which every thread of 8 blocks per SM runs 8
+ * independent FMA chains of `reps` (1 .. 2^32) steps; *flops (HOST) gets the floating-point
+ * operations it performs (2 per FMA). Time it with events on `stream`. Asynchronous. */
+rbf_status rbf_bench_fma(rbf_ctx* ctx, int prec, int64_t reps, double* flops, void* stream);
+
+/* Diagnostics / timing: `reps` FP64 residual passes r = A^T (h - A x) of the FP32 refinement
+ * at the current iterate (reading the stored A when the FP32 assembly kept it), as every
+ * refinement step runs them. Requires a preceding rbf_solve on a single system without the
+ * polynomial. Asynchronous. */
+rbf_status rbf_bench_residual(rbf_ctx* ctx, int reps, void* stream);
 
 /* Batched step (a): bin T independent tiles (HOST array `tiles`) into one packed system.
  * cx, cy: DEVICE arrays of Mtot centre coordinates; px, py, h: DEVICE arrays of Ntot point

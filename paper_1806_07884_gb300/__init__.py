@@ -374,6 +374,25 @@ class Context:
         solve; overwrites the solver workspace)."""
         self._check(self.lib.rbf_bench_cg(self._h, int(reps), self._stream(stream)), "rbf_bench_cg")
 
+    def bench_fma(self, prec: str, reps: int, stream=None) -> float:
+        """Launch the FMA throughput probe in `prec` ("fp64" or "fp32_refine" for FP32);
+        returns the flops it performs (timing hook)."""
+        fl = C.c_double()
+        self._check(self.lib.rbf_bench_fma(self._h, _lib.PRECS[prec], int(reps), C.byref(fl),
+                                           self._stream(stream)), "rbf_bench_fma")
+        return fl.value
+
+    def bench_residual(self, reps: int, stream=None):
+        """Run reps FP64 refinement residual passes at the current iterate (timing hook)."""
+        self._check(self.lib.rbf_bench_residual(self._h, int(reps), self._stream(stream)),
+                    "rbf_bench_residual")
+
+    def bench_cg_loop(self, reps: int, stream=None):
+        """Run reps CG iterations in the solver's own loop (persistent kernel or graph; timing
+        hook; needs a prior solve; overwrites the solver workspace; synchronises)."""
+        self._check(self.lib.rbf_bench_cg_loop(self._h, int(reps), self._stream(stream)),
+                    "rbf_bench_cg_loop")
+
     def export_upper(self, stream=None):
         """The assembled upper triangle of B as COO (caller's centre indices), plus b and the
         support counts, as CUDA tensors."""

@@ -71,6 +71,9 @@ SIGNATURES = {
     "rbf_eval_noalloc": (_I, [_P, _P, _P, _I64, _D, C.POINTER(_D), _I, _P, _P, _I64, _P, _P]),
     "rbf_bench_spmv": (_I, [_P, _I, _P]),
     "rbf_bench_cg": (_I, [_P, _I, _P]),
+    "rbf_bench_cg_loop": (_I, [_P, _I, _P]),
+    "rbf_bench_fma": (_I, [_P, _I, _I64, C.POINTER(_D), _P]),
+    "rbf_bench_residual": (_I, [_P, _I, _P]),
     "rbf_bin_tiles": (_I, [_P, C.POINTER(Tile), _I, _P, _P, _I64, _P, _P, _P, _I64, _P]),
     "rbf_solve_tiles": (_I, [_P, _P, _I, _D, _I, _I, C.POINTER(TileInfo), C.POINTER(SolveInfo), _P]),
     "rbf_autotune": (_I, [_P, _P]),

@@ -502,7 +502,8 @@ rbf_status rbf_set_param(rbf_ctx* ctx, const char* name, double value) {
         return RBF_OK;
     }
     if (!strcmp(name, "cg_persistent")) {
-        if (!(value == 0.0 || value == 1.0)) return set_err(ctx, RBF_ERR_ARG, "cg_persistent must be 0 or 1");
+        if (!(value == 0.0 || value == 1.0 || value == -1.0))
+            return set_err(ctx, RBF_ERR_ARG, "cg_persistent must be -1, 0 or 1");
         ctx->cg_persistent = int(value);
         return RBF_OK;
     }
@@ -545,6 +546,32 @@ rbf_status rbf_bench_cg(rbf_ctx* ctx, int reps, void* stream) {
     DeviceGuard dg(ctx->device);
     if (ctx->T > 0) return bench_tiles_run(ctx, reps, false, as_stream(stream));
     return bench_cg_run(ctx, reps, as_stream(stream));
+}
+
+rbf_status rbf_bench_fma(rbf_ctx* ctx, int prec, int64_t reps, double* flops, void* stream) {
+    if (!ctx || !flops) return RBF_ERR_ARG;
+    if (prec != RBF_FP64 && prec != RBF_FP32_REFINE) return set_err(ctx, RBF_ERR_ARG, "unknown precision");
+    if (reps < 1 || reps > (int64_t(1) << 32)) return set_err(ctx, RBF_ERR_ARG, "reps must be in [1, 2^32]");
+    DeviceGuard dg(ctx->device);
+    return bench_fma_run(ctx, prec, (long long)reps, flops, as_stream(stream));
+}
+
+rbf_status rbf_bench_residual(rbf_ctx* ctx, int reps, void* stream) {
+    if (!ctx) return RBF_ERR_ARG;
+    if (!ctx->solved || !ctx->assembled) return set_err(ctx, RBF_ERR_ARG, "rbf_bench_residual before rbf_solve");
+    if (reps < 0) return set_err(ctx, RBF_ERR_ARG, "reps < 0");
+    if (ctx->T > 0 || ctx->poly) return set_err(ctx, RBF_ERR_ARG, "rbf_bench_residual on a batched or polynomial context");
+    DeviceGuard dg(ctx->device);
+    return bench_residual_run(ctx, reps, as_stream(stream));
+}
+
+rbf_status rbf_bench_cg_loop(rbf_ctx* ctx, int reps, void* stream) {
+    if (!ctx) return RBF_ERR_ARG;
+    if (!ctx->solved || !ctx->assembled) return set_err(ctx, RBF_ERR_ARG, "rbf_bench_cg_loop before rbf_solve");
+    if (reps < 1) return set_err(ctx, RBF_ERR_ARG, "reps < 1");
+    if (ctx->T > 0) return set_err(ctx, RBF_ERR_ARG, "rbf_bench_cg_loop on a batched context");
+    DeviceGuard dg(ctx->device);
+    return bench_cg_loop_run(ctx, reps, as_stream(stream));
 }
 
 }  // extern "C"

@@ -1388,7 +1388,7 @@ rbf_status solve_tiles_run(rbf_ctx* ctx, double* c, int use_c0, double tol, int 
         }
         // stall[t]: tile t's refinement stopped helping (or its FP32 CG broke down before a
         // step); it leaves the FP32 loop and is finished in FP64, the other tiles go on
-        std::vector<char> conv(T, 0), active(T, 0), stall(T, 0);
+        std::vector<char> conv(T, 0), active(T, 0), stall(T, 0), weak(T, 0);
         double* dscale = reinterpret_cast<double*>(ctx->tred.as<char>() + RedLayout(T).scale);
         std::vector<double> hscale(T);
         for (int outer = 0;; ++outer) {
@@ -1431,10 +1431,15 @@ rbf_status solve_tiles_run(rbf_ctx* ctx, double* c, int use_c0, double tol, int 
             for (int t = 0; t < T; ++t) {
                 if (!active[t]) continue;   // other tiles keep their iterate and residual
                 const double rnew = sqrt(rn2[t]);
-                // stalled: less than half the gain asked of the inner solve (and at most a
-                // halving), short of the tolerance
-                if (!(rnew <= tol * bn[t]) && !(rnew < std::max(0.5, 2.0 * itol[t]) * rn[t]))
-                    stall[t] = 1;
+                // stalled: two steps in a row each gained less than half of what the inner
+                // solve was asked for (and at most a halving), short of the tolerance; one weak
+                // step alone is retried (the FP32 iterates vary from run to run, and a retry
+                // costs a few hundred iterations of one tile against an FP64 finish)
+                if (!(rnew <= tol * bn[t]) && !(rnew < std::max(0.5, 2.0 * itol[t]) * rn[t])) {
+                    if (++weak[t] >= 2) stall[t] = 1;
+                } else {
+                    weak[t] = 0;
+                }
                 rn[t] = rnew;
             }
         }

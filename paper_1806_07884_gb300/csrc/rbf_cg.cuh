@@ -52,22 +52,23 @@ __device__ __forceinline__ T warp_sum(T v) {
     return v;
 }
 
-// Block-wide sums of NV values of type T: each warp sums in T (FP32 for the FP32 solver,
-// keeping the slow FP64 pipe out of the per-row work), the warp totals are added in FP64.
-// The result is valid in thread 0.
+// Block-wide sums of NV values of type T, entirely in T (FP32 for the FP32 solver: FP64 on
+// this GPU issues at a small fraction of the FP32 rate with a long latency, and the sums of
+// the block's few dozen warp totals need no more than the precision of their terms). The
+// result, in thread 0, is handed out as double.
 template <int NV, typename T>
 __device__ __forceinline__ void block_sum_t(const T (&v)[NV], double (&out)[NV]) {
-    __shared__ double red[NV][32];
+    __shared__ T red[NV][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
         const T s = warp_sum<T>(v[k]);
-        if (lane == 0) red[k][w] = double(s);
+        if (lane == 0) red[k][w] = s;
     }
     __syncthreads();
     if (w == 0) {
 #pragma unroll
-        for (int k = 0; k < NV; ++k) out[k] = warp_sum_d(lane < nw ? red[k][lane] : 0.0);
+        for (int k = 0; k < NV; ++k) out[k] = double(warp_sum<T>(lane < nw ? red[k][lane] : T(0)));
     }
     __syncthreads();
 }
@@ -115,6 +116,7 @@ struct V4d { double x, y, z, w; };
 template <typename T> struct V4;
 template <> struct V4<float> { using type = V4f; };
 template <> struct V4<double> { using type = V4d; };
+// Values of B, through the read-only data path.
 __device__ __forceinline__ V4f ld4(const float* p) {
     const float4 q = __ldg(reinterpret_cast<const float4*>(p));
     return V4f{q.x, q.y, q.z, q.w};
@@ -304,16 +306,27 @@ __device__ __forceinline__ T next_r(T r, T s, T w, T ta, T tb) {
 }
 
 // u_i = sum_j Dinv[i][j] r_j over the rows j of row i's cell (row a of the cell's inverse
-// block), r_j produced by rj(j) for the cell's rows; or dinv_i r_i for large cells.
-template <typename T, typename F>
+// block), r_j produced by rj(j) for the cell's rows; or dinv_i r_i for large cells. kB columns
+// at a time: every load of a batch is in flight before its products, which are then summed in
+// column order (zeros past the block add nothing), so every kB gives the same bits.
+template <typename T, int kB = 4, typename F>
 __device__ __forceinline__ T apply_prec(const Binned& bd, const T* __restrict__ bjinv, int4 cm,
                                         int i, T di, T ri, F rj) {
     if (cm.y > kMaxBlock) return di * ri;
     const int a = i - cm.x;
-    const T* drow = bjinv + bd.bjoff[cm.z] + (long long)a * cm.y;
+    // the inverse block is stored exactly symmetric: row a is read as column a, so that the
+    // cell's threads (consecutive a) read consecutive words
+    const T* dcol = bjinv + bd.bjoff[cm.z] + a;
     T ui = T(0);
-#pragma unroll 4
-    for (int j = 0; j < cm.y; ++j) ui = fma(__ldg(drow + j), rj(cm.x + j), ui);
+    for (int j0 = 0; j0 < cm.y; j0 += kB) {
+        T dv[kB], rv[kB];
+#pragma unroll
+        for (int k = 0; k < kB; ++k) dv[k] = j0 + k < cm.y ? __ldg(dcol + (long long)(j0 + k) * cm.y) : T(0);
+#pragma unroll
+        for (int k = 0; k < kB; ++k) rv[k] = j0 + k < cm.y ? rj(cm.x + j0 + k) : T(0);
+#pragma unroll
+        for (int k = 0; k < kB; ++k) ui = fma(dv[k], rv[k], ui);
+    }
     return ui;
 }
 

@@ -112,7 +112,8 @@ struct rbf_ctx {
     int64_t launches = 0;      // kernels launched by this context (graph nodes included)
     int spmv_blocks_per_sm[2] = {0, 0};   // occupancy of the SpMV kernels, [0] FP64, [1] FP32
     int persist_blocks_per_sm[2] = {0, 0};  // of the persistent solve kernel (-1: not resident)
-    int cg_persistent = 0;           // single systems: one cooperative launch per solve
+    int cg_persistent = -1;          // single systems' CG loop: 1 persistent kernel, 0 graph,
+                                     // -1 chosen by size and precision
     int cg_barrier_extra = 0;        // test hook: the persistent solve's barriers never complete
     // solver parameters (rbf_set_param)
     double inner_tol = 1e-3;   // relative tolerance of each FP32 inner solve
@@ -257,6 +258,9 @@ void launch_resid32(rbf_ctx* ctx, const double* x64, double* r64, cudaStream_t s
 
 rbf_status bench_spmv_run(rbf_ctx* ctx, int reps, cudaStream_t st);
 rbf_status bench_cg_run(rbf_ctx* ctx, int reps, cudaStream_t st);
+rbf_status bench_cg_loop_run(rbf_ctx* ctx, int reps, cudaStream_t st);
+rbf_status bench_fma_run(rbf_ctx* ctx, int prec, long long reps, double* flops, cudaStream_t st);
+rbf_status bench_residual_run(rbf_ctx* ctx, int reps, cudaStream_t st);
 
 // permutation helpers (rbf_solve.cu)
 void launch_gather_sorted(const double* c_orig, const int* cperm, double* c_sorted, int M,

@@ -53,8 +53,9 @@ struct CgScalars {
     double out_rr, out_gamma;    // result, written when the solve stops
     int out_it, out_state;
     double acc_delta[2][kAccSlots];   // u^T B u of the SpMV of each parity, spread over slots
-    // grid barrier of the persistent solve kernel: arrivals, generation, timed-out flag
-    unsigned int bar_count, bar_gen;
+    // grid barrier of the persistent solve kernel: arrivals so far (never reset within a
+    // solve: barrier n completes at n times the grid's blocks), timed-out flag
+    unsigned long long bar_count;
     int bar_err, bar_pad;
 };
 
@@ -493,64 +494,74 @@ __global__ void k_cg_cond(CgScalars* __restrict__ sc, cudaGraphConditionalHandle
 }
 
 // ---------------------------------------------------------------------------------------
-// Persistent solve: the whole CG loop of one system in a single cooperative launch (every
-// block resident), the SpMV and the update of each iteration separated by grid barriers
-// instead of kernel boundaries. Per iteration k (parity P = k & 1):
-//   SpMV phase   w_P += B u (the warps stride over the row groups as in k_cg_spmv), delta_k
-//                into the slots acc_delta[P]; each thread then loads its first row's vectors
+// Persistent solve: the whole CG loop of one system in a single cooperative launch (one block
+// per SM, every block resident), the SpMV and the update of each iteration separated by grid
+// barriers instead of kernel boundaries. Per iteration k (parity P = k & 1):
+//   SpMV phase   w_P += B u over the block's contiguous range of row groups (each warp's
+//                first group fixed and staged during the previous barrier, the rest taken
+//                from a shared-memory counter, so the warps of a block finish together);
+//                the block's share of delta_k = u^T B u summed warp by warp into one
+//                per-block partial; each thread then loads its first row's vectors
 //   barrier
-//   scalar step  every block sums the slots and takes gamma_k, (r_k, r_k) from the previous
-//                update's per-block partials (block order): identical alpha, beta and stop
-//                decision in every block
+//   scalar step  every block sums the per-block delta partials, and has gamma_k, (r_k, r_k)
+//                from the previous update's partials, both in block order: identical alpha,
+//                beta and stop decision in every block
 //   update phase the rows (as k_cg_update), per-block partials of gamma_{k+1}, (r_{k+1},
 //                r_{k+1}); w of the other parity zeroed
 //   barrier
-// Vectors written inside the kernel are read through L2 (ld.global.cg), never a stale L1
-// line. The barrier is a counter and a generation word in device memory; every wait is
-// bounded (kBarrierTimeoutNs by the global timer), after which the waiter raises bar_err and
-// all blocks leave the loop (the host reports RBF_ERR_TIMEOUT). Cooperative launch rejects a
-// grid that cannot be resident at once, so no block waits for one that has not started.
+// Vectors written inside the kernel are read through L2 (ld.global.cg), never from a stale L1
+// line. The barrier is one 64-bit arrival counter in device memory: thread 0 of each block adds
+// 1 with release semantics (the block's writes, ordered before it by __syncthreads, become
+// visible with it) and polls with acquire loads until the count reaches the barrier's target.
+// Every wait is bounded (kBarrierTimeoutNs by the global timer); a waiter that runs out raises
+// bar_err, on which every other waiter gives up too, and all blocks leave the loop (the host
+// reports RBF_ERR_TIMEOUT). Cooperative launch rejects a grid that cannot be resident at once,
+// so no block waits for one that has not started.
 constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;   // 2 s
+
+template <typename T>
+struct PersistCfg {
+    // FP32: 24 warps per SM at <= 85 registers; FP64: 16 warps at <= 128
+    static constexpr int threads = sizeof(T) == 4 ? 768 : 512;
+    static constexpr int warps = threads / 32;
+};
 
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
-__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned int* p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
+__device__ __forceinline__ void red_release_add_u64(unsigned long long* p, unsigned long long v) {
+    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
 
-// All blocks of the grid; false (in every thread of the block) if the wait timed out or
-// another block's did.
-__device__ bool grid_barrier(CgScalars* sc, unsigned nblk) {
+// All blocks of the grid; `target` = the arrivals that complete this barrier. False (in every
+// thread of the block) if the wait ran out or another block's did.
+__device__ bool grid_barrier(CgScalars* sc, unsigned long long target) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        const unsigned g = ld_acquire_gpu(&sc->bar_gen);
-        __threadfence();
-        if (atomicAdd(&sc->bar_count, 1u) == nblk - 1) {
-            atomicExch(&sc->bar_count, 0u);
-            __threadfence();
-            atomicAdd(&sc->bar_gen, 1u);
-        } else {
+        red_release_add_u64(&sc->bar_count, 1ull);
+        if (ld_acquire_u64(&sc->bar_count) < target) {
             const unsigned long long t0 = global_ns();
             unsigned n = 0;
-            while (ld_acquire_gpu(&sc->bar_gen) == g) {
-                if ((++n & 31u) == 0 &&
+            while (ld_acquire_u64(&sc->bar_count) < target) {
+                if ((++n & 15u) == 0 &&
                     (*reinterpret_cast<volatile int*>(&sc->bar_err) != 0 ||
                      global_ns() - t0 > kBarrierTimeoutNs)) {
                     atomicExch(&sc->bar_err, 1);
                     ok = 0;
                     break;
                 }
-                __nanosleep(32);
+                __nanosleep(20);
             }
         }
-        __threadfence();
         s_ok = ok;
     }
     __syncthreads();
@@ -558,78 +569,87 @@ __device__ bool grid_barrier(CgScalars* sc, unsigned nblk) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kSpmvWarps * 32, sizeof(T) == 4 ? 3 : 2)
+__global__ void __launch_bounds__(PersistCfg<T>::threads, 1)
     k_cg_persist(Binned bd, CgVec<T> v, const T* __restrict__ B, CgScalars* __restrict__ sc,
                  const T* __restrict__ pinit, int ninit, T* __restrict__ pbuf, int bar_extra) {
-    constexpr int NT = kSpmvWarps * 32;
+    constexpr int NT = PersistCfg<T>::threads, NW = PersistCfg<T>::warps;
     using T2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
-    __shared__ GroupSmem gsm[kSpmvWarps];
-    __shared__ T s_g[2];      // gamma_k, (r_k, r_k)
+    __shared__ GroupSmem gsm[NW];
+    __shared__ T s_dw[NW];    // per-warp delta partials
+    __shared__ int s_next[2]; // next group of the block's range to take, per parity
     __shared__ T s_ab[2];     // alpha_k, beta_k
     __shared__ int s_go;
     __shared__ T rsm[NT];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const unsigned nblk = gridDim.x;
-    // arrivals that complete a barrier: the grid, plus a test hook's blocks that never come
-    const unsigned narrive = nblk + unsigned(bar_extra);
-    const int gw = blockIdx.x * kSpmvWarps + wid, nw = gridDim.x * kSpmvWarps;
+    const int nblk = int(gridDim.x);
+    // arrivals per barrier: the grid, plus a test hook's blocks that never come
+    const unsigned long long narrive = unsigned(nblk) + unsigned(bar_extra);
+    unsigned long long target = 0;
     const int M = bd.M, ngroup = bd.ngroup;
-    const int nthr = gridDim.x * NT;
-    const int i_first = blockIdx.x * NT + threadIdx.x;
+
+    // This block's row groups [g0, g1), equal shares by count (a group's time is mostly its
+    // fixed latency, not its bytes); warp wid starts at g0 + wid, the others are taken from a
+    // shared-memory counter. Its rows [rb0, rb1): equal shares moved back to the start of
+    // their cell, so that every cell's rows (the preconditioner's blocks) lie in one block and
+    // one chunk of it.
+    const int g0 = int((long long)ngroup * blockIdx.x / nblk);
+    const int g1 = int((long long)ngroup * (blockIdx.x + 1) / nblk);
+    auto cell_start = [&](int r) -> int {
+        if (r >= M) return M;
+        const int4 cm = __ldg(bd.crow + r);
+        return cm.y <= kMaxBlock ? cm.x : r;   // rows of larger cells need no neighbours
+    };
+    const int rb0 = blockIdx.x == 0 ? 0 : cell_start(int((long long)M * blockIdx.x / nblk));
+    const int rb1 = cell_start(int((long long)M * (blockIdx.x + 1) / nblk));
+    // end of the chunk of at most NT rows that starts at row c
+    auto chunk_end = [&](int c) -> int {
+        const int e = min(c + NT, rb1);
+        return e < rb1 ? cell_start(e) : e;
+    };
+    const int ce_first = chunk_end(rb0);
+    const int gfirst = g0 + wid;
+    const int i_first = rb0 + threadIdx.x < ce_first ? rb0 + threadIdx.x : M;
+    T* __restrict__ pgr = pbuf;              // [2 parities][nblk] x (gamma, (r, r))
+    T* __restrict__ pdl = pbuf + 4 * nblk;   // [nblk] delta
     // scalar state (thread 0 of every block, identical in all blocks)
     T gprev = T(1), aprev = T(1);
     int it = 0, state = kRunning;
     const T tol2bb = T(sc->tol2) * T(sc->bb);
     const int maxit = sc->maxit;
-    // Warp 0 sums per-block partials (gamma, (r, r)) in block order into s_g.
-    auto sum_partials = [&](const T* part, int n) {
-        const T2* pb = reinterpret_cast<const T2*>(part);
-        T g = T(0), rr = T(0);
-        for (int b0 = lane; b0 < n; b0 += 32 * kPartBatch) {
-            T2 pv[kPartBatch];
-#pragma unroll
-            for (int k = 0; k < kPartBatch; ++k) {
-                const int b = b0 + 32 * k;
-                pv[k] = b < n ? __ldcg(pb + b) : T2{T(0), T(0)};
-            }
-#pragma unroll
-            for (int k = 0; k < kPartBatch; ++k) {
-                g += pv[k].x;
-                rr += pv[k].y;
-            }
-        }
-        g = warp_sum<T>(g);
-        rr = warp_sum<T>(rr);
-        if (lane == 0) {
-            s_g[0] = g;
-            s_g[1] = rr;
-        }
-    };
-    if (wid == 0) sum_partials(pinit, ninit);
-    if (gw < ngroup) stage_group(bd.gdesc, gw, gsm[wid], 0, lane);
+    if (threadIdx.x == 0) {
+        s_next[0] = g0 + NW;
+        s_next[1] = g0 + NW;
+    }
+    if (gfirst < g1) stage_group(bd.gdesc, gfirst, gsm[wid], 0, lane);
+    __syncthreads();
     bool timed_out = false;
     for (int P = 0;; P ^= 1) {
         const T* __restrict__ rP = P ? v.r[1] : v.r[0];
         const T* __restrict__ sP = P ? v.s[1] : v.s[0];
         T* __restrict__ wP = P ? v.w[1] : v.w[0];
         // ---- SpMV phase
-        if (gw < ngroup) {
-            T d = T(0);
+        T d = T(0);
+        if (gfirst < g1) {
             int b = 0;
-            for (int q = gw; q < ngroup; q += nw, b ^= 1) {
-                if (q + nw < ngroup) {
-                    stage_group(bd.gdesc, q + nw, gsm[wid], b ^ 1, lane);
+            for (;;) {
+                int qn = 0;
+                if (lane == 0) qn = atomicAdd(&s_next[P], 1);
+                qn = __shfl_sync(kFull, qn, 0);
+                if (qn < g1) {
+                    stage_group(bd.gdesc, qn, gsm[wid], b ^ 1, lane);
                     group_wait<1>();
                 } else {
                     group_wait<0>();
                 }
                 d += spmv_group<T>(b, B, v.u, wP, M, lane, gsm[wid]);
+                if (qn >= g1) break;
+                b ^= 1;
             }
             // the records are fixed: the next iteration's first one travels during the barrier
-            stage_group(bd.gdesc, gw, gsm[wid], 0, lane);
+            stage_group(bd.gdesc, gfirst, gsm[wid], 0, lane);
             d = warp_sum<T>(d);
-            if (lane == 0 && d != T(0)) atomicAdd(&sc->acc_delta[P][gw & (kAccSlots - 1)], double(d));
         }
+        if (lane == 0) s_dw[wid] = d;
         // this thread's first row, loaded before the barrier (none of it changes in the SpMV)
         T f_d = T(0), f_s = T(0), f_p = T(0), f_u = T(0), f_r = T(0), f_x = T(0);
         int4 f_cm = make_int4(0, 0, 0, 0);
@@ -642,17 +662,46 @@ __global__ void __launch_bounds__(kSpmvWarps * 32, sizeof(T) == 4 ? 3 : 2)
             f_x = __ldcg(v.x + i_first);
             f_cm = __ldg(bd.crow + i_first);
         }
-        if (!grid_barrier(sc, narrive)) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            T db = T(0);
+            for (int w = 0; w < NW; ++w) db += s_dw[w];
+            pdl[blockIdx.x] = db;
+        }
+        target += narrive;
+        if (!grid_barrier(sc, target)) {
             timed_out = true;
             break;
         }
         // ---- scalar step
         const T f_w = i_first < M ? __ldcg(wP + i_first) : T(0);
         if (wid == 0) {
-            T d = T(__ldcg(&sc->acc_delta[P][lane])) + T(__ldcg(&sc->acc_delta[P][lane + 32]));
-            d = warp_sum<T>(d);
+            // delta_k from this iteration's per-block partials; gamma_k and (r_k, r_k) from the
+            // previous update's (the start kernel's at k = 0), all loads in one batch, each sum
+            // in block order
+            const T2* pp = reinterpret_cast<const T2*>(it == 0 ? pinit : pgr + size_t(P ^ 1) * 2 * nblk);
+            const int npp = it == 0 ? ninit : nblk;
+            T dd = T(0), g = T(0), rr = T(0);
+            for (int b0 = lane; b0 < max(nblk, npp); b0 += 32 * kPartBatch) {
+                T pv[kPartBatch];
+                T2 qv[kPartBatch];
+#pragma unroll
+                for (int k = 0; k < kPartBatch; ++k) {
+                    const int b = b0 + 32 * k;
+                    pv[k] = b < nblk ? __ldcg(pdl + b) : T(0);
+                    qv[k] = b < npp ? __ldcg(pp + b) : T2{T(0), T(0)};
+                }
+#pragma unroll
+                for (int k = 0; k < kPartBatch; ++k) {
+                    dd += pv[k];
+                    g += qv[k].x;
+                    rr += qv[k].y;
+                }
+            }
+            dd = warp_sum<T>(dd);
+            g = warp_sum<T>(g);
+            rr = warp_sum<T>(rr);
             if (lane == 0) {
-                const T g = s_g[0], rr = s_g[1];
                 T alpha = T(0), beta = T(0);
                 if (!isfinite(g) || !isfinite(rr)) {
                     state = kBreakdown;
@@ -662,7 +711,7 @@ __global__ void __launch_bounds__(kSpmvWarps * 32, sizeof(T) == 4 ? 3 : 2)
                     state = kMaxIt;
                 } else {
                     beta = it == 0 ? T(0) : g / gprev;
-                    const T den = it == 0 ? d : d - beta * g / aprev;
+                    const T den = it == 0 ? dd : dd - beta * g / aprev;
                     alpha = g / den;
                     if (!(den > T(0)) || !isfinite(alpha)) state = kBreakdown;
                 }
@@ -678,11 +727,8 @@ __global__ void __launch_bounds__(kSpmvWarps * 32, sizeof(T) == 4 ? 3 : 2)
                     sc->out_it = it;
                     sc->out_state = state;
                 }
-            }
-            // the slots of the other parity were last read before the previous barrier
-            if (blockIdx.x == 0) {
-                sc->acc_delta[P ^ 1][lane] = 0.0;
-                sc->acc_delta[P ^ 1][lane + 32] = 0.0;
+                // the other parity's counter, next used after the coming barrier
+                s_next[P ^ 1] = g0 + NW;
             }
         }
         __syncthreads();
@@ -694,9 +740,9 @@ __global__ void __launch_bounds__(kSpmvWarps * 32, sizeof(T) == 4 ? 3 : 2)
         T* __restrict__ sQ = P ? v.s[0] : v.s[1];
         T* __restrict__ wQ = P ? v.w[0] : v.w[1];
         T acc[2] = {T(0), T(0)};
-        for (int base = blockIdx.x * NT; base < M; base += nthr) {
+        for (int base = rb0, cend = ce_first; base < rb1; base = cend, cend = chunk_end(cend)) {
             const int i = base + threadIdx.x;
-            const bool valid = i < M;
+            const bool valid = i < cend;
             const bool first = i == i_first;
             T di = T(0), ri = T(0);
             if (valid) {
@@ -715,11 +761,8 @@ __global__ void __launch_bounds__(kSpmvWarps * 32, sizeof(T) == 4 ? 3 : 2)
             __syncthreads();
             if (valid) {
                 const int4 cm = first ? f_cm : __ldg(bd.crow + i);
-                const T ui = apply_prec<T>(bd, v.bjinv, cm, i, di, ri, [&](int j) {
-                    const int o = j - base;
-                    return o >= 0 && o < NT ? rsm[o]
-                                            : next_r(__ldcg(rP + j), __ldcg(sP + j), __ldcg(wP + j), ta, tb);
-                });
+                // the cell's rows are all in this chunk
+                const T ui = apply_prec<T, 16>(bd, v.bjinv, cm, i, di, ri, [&](int j) { return rsm[j - base]; });
                 v.u[i] = ui;
                 acc[0] = fma(ri, ui, acc[0]);
                 acc[1] = fma(ri, ri, acc[1]);
@@ -729,15 +772,15 @@ __global__ void __launch_bounds__(kSpmvWarps * 32, sizeof(T) == 4 ? 3 : 2)
         double tot[2];
         block_sum_t<2, T>(acc, tot);
         if (threadIdx.x == 0) {
-            T* pb = pbuf + size_t(P ^ 1) * 2 * nblk;
-            pb[2 * blockIdx.x] = T(tot[0]);
-            pb[2 * blockIdx.x + 1] = T(tot[1]);
+            T* pq = pgr + size_t(P) * 2 * nblk;
+            pq[2 * blockIdx.x] = T(tot[0]);
+            pq[2 * blockIdx.x + 1] = T(tot[1]);
         }
-        if (!grid_barrier(sc, narrive)) {
+        target += narrive;
+        if (!grid_barrier(sc, target)) {
             timed_out = true;
             break;
         }
-        if (wid == 0) sum_partials(pbuf + size_t(P ^ 1) * 2 * nblk, int(nblk));
     }
     // no copy of this thread may still be in flight when the block ends
     asm volatile("cp.async.wait_all;" ::: "memory");
@@ -1074,18 +1117,18 @@ int persist_grid(rbf_ctx* ctx) {
     int& per_sm = ctx->persist_blocks_per_sm[sizeof(T) == 8 ? 0 : 1];
     if (per_sm == 0) {
         int a = 0, coop = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_cg_persist<T>, kSpmvWarps * 32, 0) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_cg_persist<T>, PersistCfg<T>::threads, 0) !=
                 cudaSuccess ||
             cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device) != cudaSuccess) {
             cudaGetLastError();
             a = 0;
         }
-        per_sm = (a > 0 && coop) ? a : -1;
+        per_sm = (a > 0 && coop) ? 1 : -1;   // one block per SM
     }
     if (per_sm < 0) return 0;
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
-    return per_sm * sms;
+    return sms;
 }
 
 // Per-block partials of the persistent kernel: after the start kernel's (4 + 1) vec_grid
@@ -1107,13 +1150,23 @@ rbf_status run_cg(rbf_ctx* ctx, const TB* b, double bscale, bool use_x0, double 
                   int* iters, double* relres, int* state, cudaStream_t st, bool poly = false,
                   const double* bk = nullptr) {
     rbf_status s;
-    const int pgrid = (!poly && ctx->cg_persistent && ctx->T == 0) ? persist_grid<T>(ctx) : 0;
-    bool persisted = false;
+    int pgrid = (!poly && ctx->cg_persistent != 0 && ctx->T == 0) ? persist_grid<T>(ctx) : 0;
+    // Automatic choice (measured on GB300): the persistent kernel wins while each block's rows
+    // take at most four chunks of its update phase (FP32 terrain 1M x 100k: 15.8 against 16.5
+    // us per iteration); beyond that the graph's update kernel, with more warps per SM in
+    // flight, is faster in FP32 (big data 20M x 2M: 252 against 285 us), while FP64 iterations
+    // are bound by the SpMV's FP64 arithmetic and keep the persistent kernel (79 against 90 us
+    // at 1M x 100k, 1341 against 1382 us at 20M x 2M).
+    if (pgrid > 0 && ctx->cg_persistent < 0 && sizeof(T) == 4 &&
+        ctx->M > 4LL * pgrid * PersistCfg<T>::threads)
+        pgrid = 0;
+    bool persisted = false, started = false;
     if (pgrid > 0) {
-        if ((s = ensure(ctx, ctx->partial, sizeof(double) * (persist_offset(ctx) + 4 * size_t(pgrid)),
+        if ((s = ensure(ctx, ctx->partial, sizeof(double) * (persist_offset(ctx) + 5 * size_t(pgrid)),
                         st)) != RBF_OK)
             return s;
         if ((s = cg_start<T, TB>(ctx, b, bscale, use_x0, tol, maxit, st)) != RBF_OK) return s;
+        started = true;
         Binned bd = view(ctx);
         CgVec<T> v = cg_vectors<T>(ctx);
         const T* B = bvals_dev<T>(ctx);
@@ -1124,7 +1177,7 @@ rbf_status run_cg(rbf_ctx* ctx, const TB* b, double bscale, bool use_x0, double 
         int extra = ctx->cg_barrier_extra;
         void* args[] = {&bd, &v, &B, &sc, &pinit, &ninit, &pbuf, &extra};
         const cudaError_t e = cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(k_cg_persist<T>),
-                                                          dim3(pgrid), dim3(kSpmvWarps * 32), args, 0, st);
+                                                          dim3(pgrid), dim3(PersistCfg<T>::threads), args, 0, st);
         if (e == cudaSuccess) {
             persisted = true;
             ctx->launches += 1;
@@ -1138,7 +1191,7 @@ rbf_status run_cg(rbf_ctx* ctx, const TB* b, double bscale, bool use_x0, double 
     if (!persisted) {
         cudaGraphExec_t ex;
         if ((s = cg_graph<T>(ctx, &ex, poly)) != RBF_OK) return s;
-        if (pgrid == 0)
+        if (!started)
             if ((s = cg_start<T, TB>(ctx, b, bscale, use_x0, tol, maxit, st, poly, bk)) != RBF_OK) return s;
         RBF_CUDA_TRY(cudaGraphLaunch(ex, st));
     }
@@ -1184,6 +1237,20 @@ void launch_scatter_orig(const double* c_sorted, const int* cperm, double* c_ori
     k_scatter<<<div_up(M, 256), 256, 0, st>>>(c_sorted, cperm, c_orig, M);
 }
 
+// Timing hook: `reps` CG iterations on B x = b from x = 0 (tolerance 0) in the solver's own
+// loop, persistent kernel or graph as rbf_solve would choose. Synchronises `st`.
+template <typename T>
+rbf_status bench_cg_loop_impl(rbf_ctx* ctx, int reps, cudaStream_t st) {
+    int it = 0, state = 0;
+    double rel = 0.0;
+    return run_cg<T, double>(ctx, ctx->bvec.as<double>(), 1.0, false, 0.0, reps, &it, &rel, &state, st);
+}
+
+rbf_status bench_cg_loop_run(rbf_ctx* ctx, int reps, cudaStream_t st) {
+    return ctx->prec == RBF_FP64 ? bench_cg_loop_impl<double>(ctx, reps, st)
+                                 : bench_cg_loop_impl<float>(ctx, reps, st);
+}
+
 rbf_status bench_cg_run(rbf_ctx* ctx, int reps, cudaStream_t st) {
     return ctx->prec == RBF_FP64 ? bench_cg_impl<double>(ctx, reps, st)
                                  : bench_cg_impl<float>(ctx, reps, st);
@@ -1213,6 +1280,55 @@ rbf_status bench_spmv_impl(rbf_ctx* ctx, int reps, cudaStream_t st) {
 rbf_status bench_spmv_run(rbf_ctx* ctx, int reps, cudaStream_t st) {
     return ctx->prec == RBF_FP64 ? bench_spmv_impl<double>(ctx, reps, st)
                                  : bench_spmv_impl<float>(ctx, reps, st);
+}
+
+// FMA throughput probe: every thread runs kFmaChains independent FMA chains of `reps` steps
+// (2 kFmaChains reps flops per thread); the result is stored only if it equals a value it
+// cannot reach, which keeps the chains live.
+constexpr int kFmaChains = 8;
+template <typename T>
+__global__ void __launch_bounds__(256) k_fma_peak(T* __restrict__ sink, long long reps, T a, T b) {
+    T x[kFmaChains];
+#pragma unroll
+    for (int k = 0; k < kFmaChains; ++k) x[k] = T(threadIdx.x + k) * T(1e-3);
+    for (long long i = 0; i < reps; ++i) {
+#pragma unroll
+        for (int k = 0; k < kFmaChains; ++k) x[k] = fma(x[k], a, b);
+    }
+    T sum = T(0);
+#pragma unroll
+    for (int k = 0; k < kFmaChains; ++k) sum += x[k];
+    if (sum == T(-12345.678)) sink[blockIdx.x] = sum;
+}
+
+rbf_status bench_fma_run(rbf_ctx* ctx, int prec, long long reps, double* flops, cudaStream_t st) {
+    int sms = 0;
+    RBF_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+    const int blocks = sms * 8;
+    rbf_status s = ensure(ctx, ctx->scan_tmp, sizeof(double) * blocks, st);
+    if (s != RBF_OK) return s;
+    // a contraction toward a fixed point: the values stay finite for any reps
+    if (prec == RBF_FP64)
+        k_fma_peak<double><<<blocks, 256, 0, st>>>(ctx->scan_tmp.as<double>(), reps, 0.999, 1e-3);
+    else
+        k_fma_peak<float><<<blocks, 256, 0, st>>>(ctx->scan_tmp.as<float>(), reps, 0.999f, 1e-3f);
+    RBF_CUDA_TRY(cudaGetLastError());
+    ctx->launches += 1;
+    *flops = 2.0 * kFmaChains * double(reps) * double(blocks) * 256.0;
+    return RBF_OK;
+}
+
+// Timing hook: `reps` FP64 residual passes r = A^T (h - A x) of the refinement at the current
+// FP64 iterate (stored A when the FP32 assembly kept it, else matrix-free).
+rbf_status bench_residual_run(rbf_ctx* ctx, int reps, cudaStream_t st) {
+    double* x64 = ctx->x.as<double>();
+    double* r64 = ctx->r.as<double>();
+    for (int k = 0; k < reps; ++k) {
+        RBF_CUDA_TRY(cudaMemsetAsync(r64, 0, sizeof(double) * ctx->M, st));
+        rbf_status s = residual_run(ctx, x64, r64, false, st);
+        if (s != RBF_OK) return s;
+    }
+    return RBF_OK;
 }
 
 rbf_status prec_setup_run(rbf_ctx* ctx, int prec, int min_support, int* npin_d, cudaStream_t st) {
@@ -1349,7 +1465,7 @@ rbf_status solve_run(rbf_ctx* ctx, double* c, int use_c0, double tol, int maxit,
         };
         double rn = 0.0;
         if ((s = norm_r64(&rn)) != RBF_OK) return s;
-        int total_it = 0, outer = 0;
+        int total_it = 0, outer = 0, weak = 0;
         double rel = 0.0;
         state = kMaxIt;
         // Inner tolerance: each refinement step gains about -log10(inner_tol) digits; FP32
@@ -1383,15 +1499,20 @@ rbf_status solve_run(rbf_ctx* ctx, double* c, int use_c0, double tol, int maxit,
             approx_r = false;
             double rn_new = 0.0;
             if ((s = norm_r64(&rn_new)) != RBF_OK) return s;
-            // Stalled: the step gained less than half of what the inner solve was asked for
-            // (and at most a halving), short of the tolerance -- the FP32 matrix cannot
-            // resolve the system.
+            // Stalled: two steps in a row each gained less than half of what the inner solve
+            // was asked for (and at most a halving), short of the tolerance -- the FP32
+            // matrix cannot resolve the system. One weak step alone is retried: the FP32
+            // iterates vary from run to run, and a retry is far cheaper than an FP64 finish.
             const bool done = bnorm > 0 && rn_new / bnorm <= tol;
             if (!done && !(rn_new < std::max(0.5, 2.0 * itol) * rn)) {
-                rn = std::min(rn, rn_new);
-                ++outer;
-                state = kMaxIt;
-                break;
+                if (++weak >= 2) {
+                    rn = std::min(rn, rn_new);
+                    ++outer;
+                    state = kMaxIt;
+                    break;
+                }
+            } else {
+                weak = 0;
             }
             rn = rn_new;
         }
@@ -1503,7 +1624,7 @@ rbf_status solve_poly_run(rbf_ctx* ctx, double* c, double* kout, double tol, int
     }
     double rn = bnorm;
     rbf_solve_info inf{};
-    int state = kMaxIt, total_it = 0, outer = 0;
+    int state = kMaxIt, total_it = 0, outer = 0, weak = 0;
     const int max_outer = std::max(ctx->max_refine, 1) + 8;
     for (outer = 0;; ++outer) {
         const double rel = bnorm > 0 ? rn / bnorm : 0.0;
@@ -1543,7 +1664,14 @@ rbf_status solve_poly_run(rbf_ctx* ctx, double* c, double* kout, double tol, int
         double rn_new = 0.0;
         if ((s = norm(r64, pd->rk, &rn_new)) != RBF_OK) return s;
         const bool done = bnorm > 0 && rn_new / bnorm <= tol;
-        if (!done && !(rn_new < std::max(0.5, 2.0 * itol) * rn)) {
+        const bool weak_step = !done && !(rn_new < std::max(0.5, 2.0 * itol) * rn);
+        // one weak FP32 step alone is retried (as in rbf_solve); two in a row promote
+        if (weak_step && !fp64 && ++weak < 2) {
+            rn = rn_new;
+            continue;
+        }
+        if (!weak_step) weak = 0;
+        if (weak_step) {
             if (fp64) {   // no progress in FP64 either
                 rn = std::min(rn, rn_new);
                 ++outer;
