@@ -562,11 +562,13 @@ __global__ void __launch_bounds__(kThreads) k_residual(Binned bd, const int4* __
     }
 }
 
+constexpr int kPointLanes = 8;   // lanes per point in the stored residual's A c products
+
 // The same residual from the stored nonzeros of A (written by the FP64 pass of the FP32
 // assembly): no distances, square roots or Wendland evaluations, and the two FP64 products
 // run over the nonzeros only. Per sub-chunk: the packed values are copied into shared memory
 // with coalesced loads (their per-candidate offsets from a scan of the masks' popcounts), then
-// e_p = h_p - sum_a A_pa c_a (one warp per point, lanes over the candidates, a value found by
+// e_p = h_p - sum_a A_pa c_a (eight lanes per point over the candidates, a value found by
 // the point's rank in the candidate's mask) and r_a += sum_p A_pa e_p (one thread per candidate
 // over its values).
 __global__ void __launch_bounds__(kThreads) k_residual_stored(Binned bd, const int4* __restrict__ work,
@@ -628,17 +630,28 @@ __global__ void __launch_bounds__(kThreads) k_residual_stored(Binned bd, const i
             }
         }
         __syncthreads();
-        for (int pp = warp; pp < np; pp += nw) {
-            const unsigned int below = (1u << pp) - 1u;
-            double sacc = 0.0;
-            for (int a = lane; a < n; a += 32) {
-                const unsigned int m = smask[a];
-                if ((m >> pp) & 1u) sacc = fma(sval[aoff[a] + __popc(m & below)], cval[a], sacc);
-            }
+        // kPointLanes lanes per point (a warp takes 32 / kPointLanes points), so that the
+        // FP64 sum over each point's lanes takes log2(kPointLanes) steps: with a whole warp per
+        // point the reduction's FP64 adds, not the products, dominated the pass
+        {
+            const int sub = lane / kPointLanes, sl = lane % kPointLanes;
+            constexpr int kPerWarp = 32 / kPointLanes;
+            for (int base = warp * kPerWarp; base < np; base += nw * kPerWarp) {
+                const int pp = base + sub;
+                const bool ok = pp < np;
+                const unsigned int below = (1u << (pp & 31)) - 1u;
+                double sacc = 0.0;
+                if (ok) {
+                    for (int a = sl; a < n; a += kPointLanes) {
+                        const unsigned int m = smask[a];
+                        if ((m >> pp) & 1u) sacc = fma(sval[aoff[a] + __popc(m & below)], cval[a], sacc);
+                    }
+                }
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
-            if (lane == 0)
-                esm[pp] = hsm[pp] - sacc - (pa.k ? fma(pk0, usm[pp], fma(pk1, vsm[pp], pk2)) : 0.0);
+                for (int o = kPointLanes / 2; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+                if (ok && sl == 0)
+                    esm[pp] = hsm[pp] - sacc - (pa.k ? fma(pk0, usm[pp], fma(pk1, vsm[pp], pk2)) : 0.0);
+            }
         }
         __syncthreads();
         if (pa.rk && threadIdx.x < np) {
