@@ -449,10 +449,11 @@ rbf_status rbf_eval_noalloc(const double* cx, const double* cy, const double* c,
                             double R, const double* bbox, rbf_kernel kernel, const double* qx,
                             const double* qy, int64_t Q, double* f, void* stream);
 
-/* Self-test of the device square root used for distances (Newton-Raphson iteration for the
- * reciprocal square root seeded by the FP32 hardware estimate): for each a[i] >= 0 (DEVICE,
- * n values) writes out[2i] = that square root and out[2i+1] = CUDA's sqrt(a[i]) (DEVICE,
- * 2n values). Asynchronous. */
+/* Self-test of the device square roots used for distances, both seeded by the FP32 hardware
+ * estimate of 1/sqrt: for each a[i] >= 0 (DEVICE, n values) writes out[3i] = the two-step
+ * Newton-Raphson root (within a few units in the last place), out[3i+1] = the one-step root of
+ * the evaluation and the FP64 assembly pass (relative error ~3e-14) and out[3i+2] = CUDA's
+ * sqrt(a[i]) (DEVICE, 3n values). Asynchronous. */
 rbf_status rbf_selftest_sqrt(const double* a, double* out, int64_t n, void* stream);
 
 #ifdef __cplusplus

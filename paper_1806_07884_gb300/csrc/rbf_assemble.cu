@@ -194,8 +194,9 @@ __device__ void fill_phi(const Binned& bd, const CandSmem<T>& cs, int n, int npa
             for (int k = lane; k < nl; k += 32) {
                 const int a = list[k];
                 const double dx = xp - cs.x[a], dy = yp - cs.y[a];
-                if (inside_exact(dx, dy, bd.g.R, bd.g.R2)) {
-                    const double r = sqrt_nr(fma(dx, dx, dy * dy)) * bd.g.invR;
+                double d2;
+                if (inside_exact_d2(dx, dy, bd.g.R, bd.g.R2, d2)) {
+                    const double r = sqrt_fast(d2) * bd.g.invR;
                     row[a] = wendland<KIND, double>(r);
                     if (cnt) atomicAdd(&cnt[a], 1);
                 }

@@ -384,8 +384,9 @@ __device__ __forceinline__ double eval_tile_at(const Binned& bd, const TileDev& 
                 const float du = uq - (bd.cu[s] + ox), dv = vq - (bd.cv[s] + oy);
                 if (du * du + dv * dv >= kPrefilterR2) continue;
                 const double dx = xl - bd.cx[s], dy = yl - bd.cy[s];
-                if (inside_exact(dx, dy, 1.0, 1.0)) {
-                    const double rr = sqrt_nr(fma(dx, dx, dy * dy));
+                double d2;
+                if (inside_exact_d2(dx, dy, 1.0, 1.0, d2)) {
+                    const double rr = sqrt_fast(d2);
                     f = fma(c[s], wendland<KIND, double>(rr), f);
                 }
             }

@@ -57,6 +57,29 @@ __device__ __forceinline__ bool inside_exact(double dx, double dy, double R, dou
     return __ddiv_rn(__dsqrt_rn(d2), R) < 1.0;
 }
 
+// The same test, also handing out the separately rounded squared distance it computed.
+__device__ __forceinline__ bool inside_exact_d2(double dx, double dy, double R, double R2, double& d2) {
+    d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+    if (d2 < R2 * (1.0 - 1e-9)) return true;
+    if (d2 > R2 * (1.0 + 1e-9)) return false;
+    return __ddiv_rn(__dsqrt_rn(d2), R) < 1.0;
+}
+
+// Square root of a >= 0 for distances whose Wendland values feed sums checked to far above
+// FP64 rounding (surfaces, B, b): the FP32 hardware estimate y of 1/sqrt(a) (relative error e,
+// about 2^-22) and one Newton step on the square root itself, s <- s + y (a - s^2) / 2 from
+// s = a y, which leaves a relative error of about e^2 (~3e-14). Four FP64 operations besides
+// the two conversions -- this GPU's FP64 pipe is what the evaluation and the assembly's FP64
+// pass are bound by -- against eight for sqrt_nr. The range test runs in FP32; outside FP32's
+// normal range (and at 0) it falls back to sqrt.
+__device__ __forceinline__ double sqrt_fast(double a) {
+    const float af = float(a);
+    if (!(af > 1e-30f && af < 1e30f)) return sqrt(a);
+    const double y = double(rsqrtf(af));
+    const double s = a * y;
+    return fma(0.5 * y, fma(-s, s, a), s);
+}
+
 // Square root of a >= 0 in FP64 by Newton-Raphson iteration for the reciprocal square root,
 // y <- y (3 - a y^2) / 2, seeded with the FP32 hardware estimate rsqrtf (about 23 correct
 // bits; the step doubles them to about 46), followed by one Newton step on sqrt itself,

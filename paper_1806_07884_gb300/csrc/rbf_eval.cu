@@ -13,8 +13,9 @@ namespace {
 __global__ void k_diag_sqrt(const double* __restrict__ a, double* __restrict__ out, int64_t n) {
     for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n;
          i += int64_t(gridDim.x) * blockDim.x) {
-        out[2 * i] = sqrt_nr(a[i]);
-        out[2 * i + 1] = sqrt(a[i]);
+        out[3 * i] = sqrt_nr(a[i]);
+        out[3 * i + 1] = sqrt_fast(a[i]);
+        out[3 * i + 2] = sqrt(a[i]);
     }
 }
 
@@ -59,8 +60,9 @@ __device__ __forceinline__ double eval_warp(const Binned& bd, const double* __re
         for (int k = lane; k < nl; k += 32) {
             const int s = list[k];
             const double dx = x - bd.cx[s], dy = y - bd.cy[s];
-            if (inside_exact(dx, dy, g.R, g.R2)) {
-                const double r = sqrt_nr(fma(dx, dx, dy * dy)) * g.invR;
+            double d2;
+            if (inside_exact_d2(dx, dy, g.R, g.R2, d2)) {
+                const double r = sqrt_fast(d2) * g.invR;
                 f = fma(c[s], wendland<KIND, double>(r), f);
             }
         }

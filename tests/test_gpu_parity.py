@@ -319,22 +319,26 @@ def test_terrain_full_size_properties():
 
 
 def test_device_sqrt_against_cuda_sqrt():
-    """The Newton-Raphson square root used for distances stays within 4 ulp of CUDA's sqrt
-    over the range of squared distances (and exact at 0)."""
+    """The device square roots used for distances against CUDA's sqrt over the range of
+    squared distances: the two-step Newton-Raphson root within 4 ulp, the one-step root of the
+    evaluation and the FP64 assembly pass within 1e-13 relative (its error is the square of
+    the FP32 seed's, ~2^-44), both exact at 0."""
     from paper_1806_07884_gb300 import _lib
     lib = _lib.load()
     rng = np.random.default_rng(0)
-    a = np.concatenate([[0.0, 1.0, 4.0, 1e-300, 1e-30], 10.0 ** rng.uniform(-30, 10, 200000),
+    a = np.concatenate([[0.0, 1.0, 4.0, 1e-300, 1e-30, 1e35], 10.0 ** rng.uniform(-30, 10, 200000),
                         rng.random(100000)])
     ad = _dev(a)
-    out = torch.empty(2 * a.size, dtype=torch.float64, device="cuda")
+    out = torch.empty(3 * a.size, dtype=torch.float64, device="cuda")
     assert lib.rbf_selftest_sqrt(ad.data_ptr(), out.data_ptr(), a.size, None) == 0
     torch.cuda.synchronize()
-    o = out.cpu().numpy().reshape(-1, 2)
-    ok = o[:, 1] > 0
-    ulp = np.abs(o[ok, 0] - o[ok, 1]) / np.spacing(o[ok, 1])
+    o = out.cpu().numpy().reshape(-1, 3)
+    ok = o[:, 2] > 0
+    ulp = np.abs(o[ok, 0] - o[ok, 2]) / np.spacing(o[ok, 2])
     assert ulp.max() <= 4.0, ulp.max()
-    assert o[0, 0] == 0.0
+    rel = np.abs(o[ok, 1] - o[ok, 2]) / o[ok, 2]
+    assert rel.max() <= 1e-13, rel.max()
+    assert o[0, 0] == 0.0 and o[0, 1] == 0.0
 
 
 @pytest.mark.parametrize("case", ["franke", "clustered", "dense_cell", "ragged"])
