@@ -614,7 +614,7 @@ __global__ void __launch_bounds__(NT)
         const bool valid = i < r1;
         // the row's values, loaded before the tile's step so that their latency overlaps it
         int4 cm = make_int4(0, 0, 0, 0);
-        T f_d = T(0), f_w = T(0), f_s = T(0), f_p = T(0), f_u = T(0), f_r = T(0);
+        T f_d = T(0), f_w = T(0), f_s = T(0), f_p = T(0), f_u = T(0), f_r = T(0), f_x = T(0);
         if (valid) {
             cm = bd.crow[i];
             f_d = v.dinv[i];
@@ -623,6 +623,7 @@ __global__ void __launch_bounds__(NT)
             f_p = v.p[i];
             f_u = v.u[i];
             f_r = rP[i];
+            f_x = v.x[i];
         }
         if (threadIdx.x == 0) {
             const TSlot sl = slP[t];
@@ -678,7 +679,7 @@ __global__ void __launch_bounds__(NT)
                 ri = di == T(0) ? T(0) : fma(-ta, si, f_r);
                 sQ[i] = si;
                 v.p[i] = pi;
-                v.x[i] = fma(ta, pi, v.x[i]);
+                v.x[i] = fma(ta, pi, f_x);
                 rQ[i] = ri;
                 wQ[i] = T(0);
             }
