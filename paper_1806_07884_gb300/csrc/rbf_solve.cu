@@ -340,29 +340,46 @@ __global__ void __launch_bounds__(kVecThreads)
     // The new residual of each row of the chunk is kept in shared memory for the block-Jacobi
     // step; rows of a cell outside the chunk are recomputed with the same operations.
     __shared__ T rsm[kVecThreads];
-    for (int base = blockIdx.x * kVecThreads; base < M; base += gridDim.x * kVecThreads) {
+    // The row values of the block's next chunk are loaded at the start of the current one, so
+    // that their latency overlaps this chunk's work (with M far beyond the grid, each block
+    // takes several chunks and the update is bound by these round trips).
+    T c_d = f_d, c_w = f_w, c_s = f_s, c_p = f_p, c_u = f_u, c_r = f_r, c_x = f_x;
+    int4 c_cm = f_cm;
+    const int stride = gridDim.x * kVecThreads;
+    for (int base = blockIdx.x * kVecThreads; base < M; base += stride) {
         const int i = base + threadIdx.x;
         const bool valid = i < M;
+        const int in = i + stride;
+        T n_d = T(0), n_w = T(0), n_s = T(0), n_p = T(0), n_u = T(0), n_r = T(0), n_x = T(0);
+        int4 n_cm = make_int4(0, 0, 0, 0);
+        if (in < M) {
+            n_d = v.dinv[in];
+            n_w = wP[in];
+            n_s = sP[in];
+            n_p = v.p[in];
+            n_u = v.u[in];
+            n_r = rP[in];
+            n_x = v.x[in];
+            n_cm = bd.crow[in];
+        }
         T di = T(0), ri = T(0);
         if (valid) {
-            const bool first = i == i_first;
-            di = first ? f_d : v.dinv[i];
-            const T wi = di == T(0) ? T(0) : wfull(i, first ? f_w : wP[i]);
-            const T si = fma(tb, first ? f_s : sP[i], wi);
-            const T pi = fma(tb, first ? f_p : v.p[i], first ? f_u : v.u[i]);
-            ri = di == T(0) ? T(0) : fma(-ta, si, first ? f_r : rP[i]);
+            di = c_d;
+            const T wi = di == T(0) ? T(0) : wfull(i, c_w);
+            const T si = fma(tb, c_s, wi);
+            const T pi = fma(tb, c_p, c_u);
+            ri = di == T(0) ? T(0) : fma(-ta, si, c_r);
             sQ[i] = si;
             v.p[i] = pi;
-            v.x[i] = fma(ta, pi, first ? f_x : v.x[i]);
+            v.x[i] = fma(ta, pi, c_x);
             rQ[i] = ri;
             wQ[i] = T(0);
         }
         rsm[threadIdx.x] = ri;
         __syncthreads();
         if (valid) {
-            const int4 cm = i == i_first ? f_cm : bd.crow[i];
             // rows of pinned centres carry zeros in the inverse block, so r_j need no mask
-            const T ui = apply_prec<T>(bd, v.bjinv, cm, i, di, ri, [&](int j) {
+            const T ui = apply_prec<T>(bd, v.bjinv, c_cm, i, di, ri, [&](int j) {
                 const int o = j - base;
                 return o >= 0 && o < kVecThreads ? rsm[o]
                                                  : next_r(rP[j], sP[j], wfull(j, wP[j]), ta, tb);
@@ -376,6 +393,14 @@ __global__ void __launch_bounds__(kVecThreads)
                 eacc[2] = fma(E[2 * M + i], ui, eacc[2]);
             }
         }
+        c_d = n_d;
+        c_w = n_w;
+        c_s = n_s;
+        c_p = n_p;
+        c_u = n_u;
+        c_r = n_r;
+        c_x = n_x;
+        c_cm = n_cm;
         __syncthreads();
     }
     double tot[2];
