@@ -765,27 +765,48 @@ __global__ void __launch_bounds__(PersistCfg<T>::threads, 1)
         T* __restrict__ sQ = P ? v.s[0] : v.s[1];
         T* __restrict__ wQ = P ? v.w[0] : v.w[1];
         T acc[2] = {T(0), T(0)};
-        for (int base = rb0, cend = ce_first; base < rb1; base = cend, cend = chunk_end(cend)) {
+        // With several chunks per block (large systems), row cend + tid of the next chunk is
+        // loaded at the start of the current one (and the next chunk's end with it), so that
+        // those round trips overlap this chunk's work; a row the chunk's cut moves to a later
+        // chunk is simply loaded again there.
+        T c_d = f_d, c_w = f_w, c_s = f_s, c_p = f_p, c_u = f_u, c_r = f_r, c_x = f_x;
+        int4 c_cm = f_cm;
+        int i_c = i_first;
+        for (int base = rb0, cend = ce_first; base < rb1;) {
+            const int nend = cend < rb1 ? chunk_end(cend) : rb1;
+            const int in = cend + threadIdx.x;
+            T n_d = T(0), n_w = T(0), n_s = T(0), n_p = T(0), n_u = T(0), n_r = T(0), n_x = T(0);
+            int4 n_cm = make_int4(0, 0, 0, 0);
+            if (in < rb1) {
+                n_d = __ldg(v.dinv + in);
+                n_w = __ldcg(wP + in);
+                n_s = __ldcg(sP + in);
+                n_p = __ldcg(v.p + in);
+                n_u = __ldcg(v.u + in);
+                n_r = __ldcg(rP + in);
+                n_x = __ldcg(v.x + in);
+                n_cm = __ldg(bd.crow + in);
+            }
             const int i = base + threadIdx.x;
             const bool valid = i < cend;
-            const bool first = i == i_first;
+            const bool have = i == i_c;
             T di = T(0), ri = T(0);
             if (valid) {
-                di = first ? f_d : __ldg(v.dinv + i);
-                const T wi = di == T(0) ? T(0) : (first ? f_w : __ldcg(wP + i));
-                const T si = fma(tb, first ? f_s : __ldcg(sP + i), wi);
-                const T pi = fma(tb, first ? f_p : __ldcg(v.p + i), first ? f_u : __ldcg(v.u + i));
-                ri = di == T(0) ? T(0) : fma(-ta, si, first ? f_r : __ldcg(rP + i));
+                di = have ? c_d : __ldg(v.dinv + i);
+                const T wi = di == T(0) ? T(0) : (have ? c_w : __ldcg(wP + i));
+                const T si = fma(tb, have ? c_s : __ldcg(sP + i), wi);
+                const T pi = fma(tb, have ? c_p : __ldcg(v.p + i), have ? c_u : __ldcg(v.u + i));
+                ri = di == T(0) ? T(0) : fma(-ta, si, have ? c_r : __ldcg(rP + i));
                 sQ[i] = si;
                 v.p[i] = pi;
-                v.x[i] = fma(ta, pi, first ? f_x : __ldcg(v.x + i));
+                v.x[i] = fma(ta, pi, have ? c_x : __ldcg(v.x + i));
                 rQ[i] = ri;
                 wQ[i] = T(0);
             }
             rsm[threadIdx.x] = ri;
             __syncthreads();
             if (valid) {
-                const int4 cm = first ? f_cm : __ldg(bd.crow + i);
+                const int4 cm = have ? c_cm : __ldg(bd.crow + i);
                 // the cell's rows are all in this chunk
                 const T ui = apply_prec<T, 16>(bd, v.bjinv, cm, i, di, ri, [&](int j) { return rsm[j - base]; });
                 v.u[i] = ui;
@@ -793,6 +814,17 @@ __global__ void __launch_bounds__(PersistCfg<T>::threads, 1)
                 acc[1] = fma(ri, ri, acc[1]);
             }
             __syncthreads();
+            c_d = n_d;
+            c_w = n_w;
+            c_s = n_s;
+            c_p = n_p;
+            c_u = n_u;
+            c_r = n_r;
+            c_x = n_x;
+            c_cm = n_cm;
+            i_c = in;
+            base = cend;
+            cend = nend;
         }
         double tot[2];
         block_sum_t<2, T>(acc, tot);
@@ -1177,9 +1209,9 @@ rbf_status run_cg(rbf_ctx* ctx, const TB* b, double bscale, bool use_x0, double 
     rbf_status s;
     int pgrid = (!poly && ctx->cg_persistent != 0 && ctx->T == 0) ? persist_grid<T>(ctx) : 0;
     // Automatic choice (measured on GB300): the persistent kernel wins while each block's rows
-    // take at most four chunks of its update phase (FP32 terrain 1M x 100k: 15.8 against 16.5
+    // take at most four chunks of its update phase (FP32 terrain 1M x 100k: 14.9 against 16.2
     // us per iteration); beyond that the graph's update kernel, with more warps per SM in
-    // flight, is faster in FP32 (big data 20M x 2M: 252 against 285 us), while FP64 iterations
+    // flight, is faster in FP32 (big data 20M x 2M: 208 against 232 us), while FP64 iterations
     // are bound by the SpMV's FP64 arithmetic and keep the persistent kernel (79 against 90 us
     // at 1M x 100k, 1341 against 1382 us at 20M x 2M).
     if (pgrid > 0 && ctx->cg_persistent < 0 && sizeof(T) == 4 &&
