@@ -511,7 +511,31 @@ __global__ void __launch_bounds__(kThreads) k_residual(Binned bd, const int4* __
                 gacc[8] += hp;
             }
         }
-        // r_a += sum_p Phi[p][a] e_p (and A^T P: E_a += sum_p Phi[p][a] (u_p, v_p, 1))
+        // r_a += sum_p Phi[p][a] e_p (and A^T P: E_a += sum_p Phi[p][a] (u_p, v_p, 1)). With
+        // the masks of the stored A at hand, only the points in a's support are visited (in
+        // the same order: the zero terms add nothing); the FP64 pipe bounds this pass.
+        if (astore) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int a = threadIdx.x + h * kThreads;
+                if (a >= n) continue;
+                double acc = h ? racc1 : racc0;
+                double* ea = eacc + 3 * h;
+                for (unsigned int m = amsk[a]; m; m &= m - 1u) {
+                    const int pp = __ffs(m) - 1;
+                    const double f = phi[pp * npad + a];
+                    acc = fma(f, esm[pp], acc);
+                    if (pa.E) {
+                        ea[0] = fma(f, usm[pp], ea[0]);
+                        ea[1] = fma(f, vsm[pp], ea[1]);
+                        ea[2] += f;
+                    }
+                }
+                if (h) racc1 = acc;
+                else racc0 = acc;
+            }
+            continue;
+        }
         for (int pp = 0; pp < np; ++pp) {
             const double e = esm[pp];
             if (threadIdx.x < n) {
