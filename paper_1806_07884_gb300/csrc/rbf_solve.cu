@@ -1041,8 +1041,12 @@ int spmv_grid_T(rbf_ctx* ctx) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
     return std::max(1, std::min(per_sm * std::max(sms, 1), div_up(ctx->ngroup, kSpmvWarps)));
 }
+// Vector-kernel grid: one block per kVecThreads rows, at most the two blocks per SM of
+// 512 threads that stay resident (152 SMs): no second wave, and the blocks of a large system
+// take several chunks each, whose row loads the update kernel overlaps (20M x 2M: 204 against
+// 208 us per iteration with four blocks per SM).
 int vec_grid(const rbf_ctx* ctx) {
-    return std::max(1, std::min(div_up(ctx->M, kVecThreads), 152 * 4));
+    return std::max(1, std::min(div_up(ctx->M, kVecThreads), 152 * 2));
 }
 
 // The polynomial rows of Eq. 10 in a CG solve of precision T (all null without them).
