@@ -8,3 +8,4 @@ shares no code with the CUDA library (no kernels, headers, helpers or tables).
 from .rbf_oracle import *  # noqa: F401,F403
 from . import mlp_oracle  # noqa: F401
 from . import poly_oracle  # noqa: F401
+from . import window_oracle  # noqa: F401
