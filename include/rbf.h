@@ -366,6 +366,56 @@ rbf_status rbf_eval_tiles(rbf_ctx* ctx, const double* c, const double* qx, const
 rbf_status rbf_eval_tiles_grid(rbf_ctx* ctx, const double* c, int nx, int ny, double* f,
                                void* stream);
 
+/* ---- Moving window (the "moving window" the paper names as future work, Section 7) ----
+ * A large domain is cut into wx x wy overlapping windows fitted independently -- each window
+ * is one tile of the batched fit -- and the surface blends the windows' local surfaces with a
+ * partition of unity. Window (i, j) (row-major, j slow; tile j wx + i):
+ *   core box        [a_i, a_{i+1}] x [b_j, b_{j+1}], a_i = x0 + (x1 - x0) i / wx, likewise b_j
+ *   extended box    the core box grown by `overlap` on its inner sides, closed; a side on the
+ *                   domain's boundary is open to infinity (items outside bbox belong to the
+ *                   edge windows)
+ *   points          those in the extended box
+ *   centres         those in the extended box grown by R (every centre whose support reaches
+ *                   one of the window's points), so a centre can belong to several windows
+ *   weight          the product over the inner sides of s((q - (a_i - overlap)) / (2 overlap))
+ *                   and s(((a_{i+1} + overlap) - q) / (2 overlap)), s(t) = t^2 (3 - 2t) on
+ *                   [0, 1] (0 below, 1 above): neighbours' weights sum to one across their
+ *                   common band; with overlap 0, steps (q >= a_i, q < a_{i+1})
+ *   surface         f(q) = sum_w weight_w(q) f_w(q) / sum_w weight_w(q) over the windows whose
+ *                   extended box holds q, f_w the window's own fit (Eq. 3 on its centres)
+ * Use: rbf_bin_windows, then rbf_assemble and rbf_solve_tiles (c: DEVICE, the Mtot weights of
+ * rbf_window_sizes, window after window; rbf_window_centres maps them to input centres), then
+ * rbf_eval_windows / rbf_eval_windows_grid. The windows' centre and point order within a window
+ * comes from atomics: results agree from run to run up to the order of FP additions. */
+
+/* Lay the windows out over bbox = {x0, y0, x1, y1} (HOST; x1 > x0, y1 > y0) and bin them as
+ * a batch: cx, cy (M centres), px, py, h (N points) DEVICE arrays in the caller's order; R > 0
+ * the support radius of every window; 1 <= wx, wy, wx wy <= 65536; overlap >= 0.
+ * Synchronises `stream`. Returns RBF_ERR_ARG for a window without centres (fewer windows or a
+ * larger overlap), RBF_ERR_LIMIT as rbf_bin_tiles. */
+rbf_status rbf_bin_windows(rbf_ctx* ctx, const double* cx, const double* cy, int64_t M,
+                           const double* px, const double* py, const double* h, int64_t N,
+                           double R, const double* bbox, int wx, int wy, double overlap,
+                           void* stream);
+
+/* Centres (Mtot) and points (Ntot) summed over the windows of the last rbf_bin_windows (HOST
+ * outputs): the length of rbf_solve_tiles' c. */
+rbf_status rbf_window_sizes(const rbf_ctx* ctx, int64_t* Mtot, int64_t* Ntot);
+
+/* idx[k] (DEVICE, capacity cap >= Mtot) = the input index of the centre behind weight k.
+ * Asynchronous. */
+rbf_status rbf_window_centres(rbf_ctx* ctx, int64_t* idx, int64_t cap, void* stream);
+
+/* The blended surface at Q query points (qx, qy, f DEVICE) from the windows' weights c (DEVICE,
+ * Mtot values as rbf_solve_tiles returns them). Asynchronous. */
+rbf_status rbf_eval_windows(rbf_ctx* ctx, const double* c, const double* qx, const double* qy,
+                            int64_t Q, double* f, void* stream);
+
+/* The same on the node-centred nx x ny grid over box (HOST {x0, y0, x1, y1}); f[i nx + j]
+ * (DEVICE, nx ny values). Asynchronous. */
+rbf_status rbf_eval_windows_grid(rbf_ctx* ctx, const double* c, int nx, int ny, const double* box,
+                                 double* f, void* stream);
+
 /* Autotuner of the batched CG loop: on the assembled batched system, times CG iterations in
  * each candidate launch configuration (SpMV blocks per SM x row groups per work item, then the
  * update block size) with CUDA events on `stream` and keeps the fastest for systems of this

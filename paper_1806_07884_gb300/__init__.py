@@ -272,6 +272,50 @@ class Context:
         self._check(s, "rbf_eval_tiles_grid")
         return f
 
+    # -- moving window ----------------------------------------------------------------------
+    def bin_windows(self, cx, cy, px, py, h, R: float, bbox, wx: int, wy: int, overlap: float,
+                    stream=None):
+        """Lay out wx x wy overlapping windows over bbox and bin them as a batch (see
+        rbf_bin_windows); then assemble and solve_tiles fit every window."""
+        M, N = int(cx.numel()), int(px.numel())
+        box = (C.c_double * 4)(*[float(v) for v in bbox])
+        s = self.lib.rbf_bin_windows(self._h, _dptr(cx, "cx"), _dptr(cy, "cy"), M, _dptr(px, "px"),
+                                     _dptr(py, "py"), _dptr(h, "h"), N, float(R), box, int(wx),
+                                     int(wy), float(overlap), self._stream(stream))
+        self._check(s, "rbf_bin_windows")
+        mt, nt = C.c_int64(), C.c_int64()
+        self._check(self.lib.rbf_window_sizes(self._h, C.byref(mt), C.byref(nt)), "rbf_window_sizes")
+        self.M, self.N, self.T = mt.value, nt.value, int(wx) * int(wy)
+
+    def window_centres(self, stream=None):
+        """Input index of the centre behind each of the windows' Mtot weights (CUDA int64)."""
+        torch = _torch()
+        idx = torch.empty(self.M, dtype=torch.int64, device=f"cuda:{self.device}")
+        self._check(self.lib.rbf_window_centres(self._h, C.c_void_p(idx.data_ptr()), self.M,
+                                                self._stream(stream)), "rbf_window_centres")
+        return idx
+
+    def eval_windows(self, c, qx, qy, out=None, stream=None):
+        """The blended moving-window surface at query points."""
+        torch = _torch()
+        Q = int(qx.numel())
+        f = out if out is not None else torch.empty(Q, dtype=torch.float64, device=qx.device)
+        self._check(self.lib.rbf_eval_windows(self._h, _dptr(c, "c"), _dptr(qx, "qx"),
+                                              _dptr(qy, "qy"), Q, _dptr(f, "f"),
+                                              self._stream(stream)), "rbf_eval_windows")
+        return f
+
+    def eval_windows_grid(self, c, nx: int, ny: int, box=(0.0, 0.0, 1.0, 1.0), out=None,
+                          stream=None):
+        """The blended moving-window surface on the nx x ny node grid over box, shape (ny, nx)."""
+        torch = _torch()
+        f = out if out is not None else torch.empty((ny, nx), dtype=torch.float64, device=c.device)
+        b = (C.c_double * 4)(*[float(v) for v in box])
+        self._check(self.lib.rbf_eval_windows_grid(self._h, _dptr(c, "c"), int(nx), int(ny), b,
+                                                   _dptr(f, "f"), self._stream(stream)),
+                    "rbf_eval_windows_grid")
+        return f
+
     # -- learned warm start ----------------------------------------------------------------
     def features(self, out=None, stream=None):
         """Radial features of every centre (caller order, (M, 32) float32 CUDA tensor) and the
@@ -448,6 +492,29 @@ def fit_tiles(problems, kernel: str = "w31", prec: str = "fp32_refine", tol: flo
     c, info, tinfo = ctx.solve_tiles(tol=tol, maxit=maxit, min_support=min_support)
     cs = [c[d["c0"]:d["c0"] + d["M"]] for d in tiles]
     return cs, info, tinfo, ctx
+
+
+def fit_windows(points, h, centres, R: float, wx: int, wy: int, overlap: float,
+                kernel: str = "w31", prec: str = "fp32_refine", bbox=(0.0, 0.0, 1.0, 1.0),
+                tol: float = 1e-10, maxit: int = 200000, min_support: int = 3,
+                ctx: Context | None = None, device: int = 0):
+    """Moving-window fit: wx x wy overlapping windows fitted as one batch. Returns (c, info,
+    per-window info, ctx); c holds the windows' weights one window after another
+    (ctx.window_centres() maps them to input centres), ctx.eval_windows(_grid) blends them."""
+    torch = _torch()
+    dev = f"cuda:{device}"
+
+    def dev64(a):
+        t = a if isinstance(a, torch.Tensor) else torch.as_tensor(a)
+        return t.to(device=dev, dtype=torch.float64)
+
+    P, H, Cc = dev64(points), dev64(h), dev64(centres)
+    ctx = ctx or Context(device)
+    ctx.bin_windows(Cc[:, 0].contiguous(), Cc[:, 1].contiguous(), P[:, 0].contiguous(),
+                    P[:, 1].contiguous(), H.contiguous(), R, bbox, wx, wy, overlap)
+    ctx.assemble(kernel, prec)
+    c, info, tinfo = ctx.solve_tiles(tol=tol, maxit=maxit, min_support=min_support)
+    return c, info, tinfo, ctx
 
 
 def fit(points, h, centres, R: float, kernel: str = "w31", prec: str = "fp64",

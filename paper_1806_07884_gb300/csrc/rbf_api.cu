@@ -158,7 +158,8 @@ rbf_status rbf_destroy(rbf_ctx* ctx) {
                        &ctx->dinv, &ctx->dinv32, &ctx->bjinv, &ctx->bjinv32, &ctx->crow,
                        &ctx->partial, &ctx->scal, &ctx->csort, &ctx->sigma, &ctx->feat,
                        &ctx->mlp_part, &ctx->astore, &ctx->amask, &ctx->woff, &ctx->wsize,
-                       &ctx->pE, &ctx->pE32, &ctx->pdev, &ctx->pepart, &ctx->bblock, &ctx->bandtab};
+                       &ctx->pE, &ctx->pE32, &ctx->pdev, &ctx->pepart, &ctx->bblock, &ctx->bandtab,
+                       &ctx->win_count, &ctx->win_off, &ctx->win_c, &ctx->win_cidx, &ctx->win_p};
     for (rbf_buf* b : bufs) release(ctx, *b);
     if (ctx->hpinned) cudaFreeHost(ctx->hpinned);
     if (ctx->bhost) cudaFreeHost(ctx->bhost);
@@ -174,6 +175,7 @@ rbf_status rbf_bin(rbf_ctx* ctx, const double* cx, const double* cy, int64_t M, 
                    const double* py, const double* h, int64_t N, double R, const double* bbox,
                    void* stream) {
     if (!ctx) return RBF_ERR_ARG;
+    ctx->win_on = false;
     ctx->binned = false;
     ctx->assembled = false;
     ctx->solved = false;
@@ -294,6 +296,7 @@ rbf_status rbf_bin_tiles(rbf_ctx* ctx, const rbf_tile* tiles, int T, const doubl
     ctx->binned = false;
     ctx->assembled = false;
     ctx->solved = false;
+    ctx->win_on = false;
     if (!tiles || T < 1) return set_err(ctx, RBF_ERR_ARG, "need T >= 1 tiles");
     if (!cx || !cy || (Ntot > 0 && (!px || !py || !h)))
         return set_err(ctx, RBF_ERR_ARG, "null pointer argument");
@@ -303,6 +306,71 @@ rbf_status rbf_bin_tiles(rbf_ctx* ctx, const rbf_tile* tiles, int T, const doubl
     rbf_status s = bin_tiles_run(ctx, tiles, T, cx, cy, Mtot, px, py, h, Ntot, as_stream(stream));
     if (s == RBF_OK) ctx->binned = true;
     return s;
+}
+
+rbf_status rbf_bin_windows(rbf_ctx* ctx, const double* cx, const double* cy, int64_t M,
+                           const double* px, const double* py, const double* h, int64_t N,
+                           double R, const double* bbox, int wx, int wy, double overlap,
+                           void* stream) {
+    if (!ctx) return RBF_ERR_ARG;
+    ctx->binned = false;
+    ctx->assembled = false;
+    ctx->solved = false;
+    ctx->win_on = false;
+    if (!cx || !cy || !px || !py || !h || !bbox) return set_err(ctx, RBF_ERR_ARG, "null pointer argument");
+    if (M < 1 || N < 1 || M > (int64_t(1) << 30) || N > (int64_t(1) << 30))
+        return set_err(ctx, RBF_ERR_ARG, "need 1 <= M, N <= 2^30");
+    if (!(R > 0.0) || !isfinite(R)) return set_err(ctx, RBF_ERR_ARG, "R must be finite and > 0");
+    for (int k = 0; k < 4; ++k)
+        if (!isfinite(bbox[k])) return set_err(ctx, RBF_ERR_ARG, "non-finite bbox");
+    if (!(bbox[2] > bbox[0]) || !(bbox[3] > bbox[1]))
+        return set_err(ctx, RBF_ERR_ARG, "bbox must be {x0, y0, x1, y1} with x1 > x0, y1 > y0");
+    if (wx < 1 || wy < 1 || int64_t(wx) * wy > 65536)
+        return set_err(ctx, RBF_ERR_ARG, "need wx, wy >= 1 and wx * wy <= 65536 windows");
+    if (!(overlap >= 0.0) || !isfinite(overlap)) return set_err(ctx, RBF_ERR_ARG, "overlap must be finite and >= 0");
+    DeviceGuard dg(ctx->device);
+    rbf_status s = window_bin_run(ctx, cx, cy, M, px, py, h, N, R, bbox, wx, wy, overlap, as_stream(stream));
+    if (s == RBF_OK) ctx->binned = true;
+    return s;
+}
+
+rbf_status rbf_window_sizes(const rbf_ctx* ctx, int64_t* Mtot, int64_t* Ntot) {
+    if (!ctx || !Mtot || !Ntot || !ctx->win_on) return RBF_ERR_ARG;
+    *Mtot = ctx->win_M;
+    *Ntot = ctx->win_N;
+    return RBF_OK;
+}
+
+rbf_status rbf_window_centres(rbf_ctx* ctx, int64_t* idx, int64_t cap, void* stream) {
+    if (!ctx) return RBF_ERR_ARG;
+    if (!ctx->win_on) return set_err(ctx, RBF_ERR_ARG, "rbf_window_centres before rbf_bin_windows");
+    if (!idx || cap < ctx->win_M) return set_err(ctx, RBF_ERR_ARG, "idx must hold rbf_window_sizes' Mtot values");
+    DeviceGuard dg(ctx->device);
+    RBF_CUDA_TRY(cudaMemcpyAsync(idx, ctx->win_cidx.p, sizeof(int64_t) * size_t(ctx->win_M),
+                                 cudaMemcpyDeviceToDevice, as_stream(stream)));
+    return RBF_OK;
+}
+
+rbf_status rbf_eval_windows(rbf_ctx* ctx, const double* c, const double* qx, const double* qy,
+                            int64_t Q, double* f, void* stream) {
+    if (!ctx) return RBF_ERR_ARG;
+    if (!ctx->win_on || !ctx->assembled)
+        return set_err(ctx, RBF_ERR_ARG, "rbf_eval_windows before rbf_bin_windows + rbf_assemble");
+    if (Q < 0 || (Q > 0 && (!c || !qx || !qy || !f))) return set_err(ctx, RBF_ERR_ARG, "null pointer argument");
+    DeviceGuard dg(ctx->device);
+    return window_eval_run(ctx, c, qx, qy, Q, 0, 0, nullptr, f, as_stream(stream));
+}
+
+rbf_status rbf_eval_windows_grid(rbf_ctx* ctx, const double* c, int nx, int ny, const double* box,
+                                 double* f, void* stream) {
+    if (!ctx) return RBF_ERR_ARG;
+    if (!ctx->win_on || !ctx->assembled)
+        return set_err(ctx, RBF_ERR_ARG, "rbf_eval_windows_grid before rbf_bin_windows + rbf_assemble");
+    if (!c || !box || !f || nx < 1 || ny < 1) return set_err(ctx, RBF_ERR_ARG, "bad grid arguments");
+    for (int k = 0; k < 4; ++k)
+        if (!isfinite(box[k])) return set_err(ctx, RBF_ERR_ARG, "non-finite box");
+    DeviceGuard dg(ctx->device);
+    return window_eval_run(ctx, c, nullptr, nullptr, 0, nx, ny, box, f, as_stream(stream));
 }
 
 rbf_status rbf_solve_tiles(rbf_ctx* ctx, double* c, int use_c0, double tol, int maxit,

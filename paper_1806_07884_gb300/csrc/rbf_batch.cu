@@ -1609,4 +1609,285 @@ rbf_status autotune_run(rbf_ctx* ctx, cudaStream_t st) {
     return autotune_impl<float>(ctx, st);
 }
 
+// ---------------------------------------------------------------------------------------
+// Moving window (the "moving window" technique of the paper's future work, Section 7): the
+// domain is cut into wx x wy overlapping windows; each is one tile of the batched fit over its
+// own points and the centres whose support reaches them, and the surface blends the windows'
+// local surfaces with a smooth-step partition of unity. Window geometry:
+//   core edges  a_i = x0 + (x1 - x0) i / wx  (likewise along y)
+//   extended    [a_i - d, a_{i+1} + d], closed; a side on the domain's boundary is open to
+//               infinity (items outside the box belong to the edge windows)
+//   points      in the extended box; centres in the extended box grown by R
+//   weight      product over the inner sides of s((q - (a_i - d)) / 2d), s(((a_{i+1} + d) - q)
+//               / 2d), s(t) = t^2 (3 - 2t) clamped to [0, 1]; with d = 0 the steps q >= a_i,
+//               q < a_{i+1}
+// ---------------------------------------------------------------------------------------
+namespace {
+
+struct WinGeom {
+    double x0, y0, x1, y1, d, R;
+    int wx, wy;
+};
+
+__host__ __device__ __forceinline__ double win_edge(double lo, double hi, int i, int n) {
+    return lo + (hi - lo) * double(i) / double(n);
+}
+
+// Is coordinate v inside window i's extended interval (grown by `grow`) along one axis?
+__host__ __device__ __forceinline__ bool win_member(double v, double lo, double hi, int i, int n,
+                                                   double d, double grow) {
+    const bool lo_ok = i == 0 || v >= (win_edge(lo, hi, i, n) - d) - grow;
+    const bool hi_ok = i == n - 1 || v <= (win_edge(lo, hi, i + 1, n) + d) + grow;
+    return lo_ok && hi_ok;
+}
+
+// The windows along one axis that may hold v (a superset; callers test each exactly).
+__device__ __forceinline__ int2 win_range(double v, double lo, double hi, int n, double reach) {
+    const double w = (hi - lo) / double(n);
+    const double a = floor((v - reach - lo) / w) - 1.0, b = floor((v + reach - lo) / w) + 1.0;
+    const int i0 = int(fmin(fmax(a, 0.0), double(n - 1)));
+    const int i1 = int(fmin(fmax(b, 0.0), double(n - 1)));
+    return make_int2(i0, i1);
+}
+
+__device__ __forceinline__ double smooth_step01(double t) {
+    t = fmin(fmax(t, 0.0), 1.0);
+    return t * t * (3.0 - 2.0 * t);
+}
+
+__device__ __forceinline__ double win_axis_weight(double v, double lo, double hi, int i, int n, double d) {
+    double w = 1.0;
+    if (d > 0.0) {
+        if (i > 0) w *= smooth_step01((v - (win_edge(lo, hi, i, n) - d)) / (2.0 * d));
+        if (i < n - 1) w *= smooth_step01(((win_edge(lo, hi, i + 1, n) + d) - v) / (2.0 * d));
+    } else {
+        if (i > 0 && !(v >= win_edge(lo, hi, i, n))) w = 0.0;
+        if (i < n - 1 && !(v < win_edge(lo, hi, i + 1, n))) w = 0.0;
+    }
+    return w;
+}
+
+// Count (cursor == nullptr) or scatter the items into the windows that hold them: each item
+// of window w goes to off[w] + (a slot taken with an atomic), with its input index.
+__global__ void k_win_items(const double* __restrict__ x, const double* __restrict__ y,
+                            const double* __restrict__ h, int64_t n, WinGeom g, double grow,
+                            int* __restrict__ count, const long long* __restrict__ off,
+                            int* __restrict__ cursor, double* __restrict__ ox,
+                            double* __restrict__ oy, double* __restrict__ oh,
+                            long long* __restrict__ oidx) {
+    const double reach = g.d + grow;
+    for (int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; k < n;
+         k += int64_t(gridDim.x) * blockDim.x) {
+        const double xv = x[k], yv = y[k];
+        const int2 rx = win_range(xv, g.x0, g.x1, g.wx, reach);
+        const int2 ry = win_range(yv, g.y0, g.y1, g.wy, reach);
+        for (int j = ry.x; j <= ry.y; ++j) {
+            if (!win_member(yv, g.y0, g.y1, j, g.wy, g.d, grow)) continue;
+            for (int i = rx.x; i <= rx.y; ++i) {
+                if (!win_member(xv, g.x0, g.x1, i, g.wx, g.d, grow)) continue;
+                const int w = j * g.wx + i;
+                if (!cursor) {
+                    atomicAdd(&count[w], 1);
+                    continue;
+                }
+                const long long slot = off[w] + atomicAdd(&cursor[w], 1);
+                ox[slot] = xv;
+                oy[slot] = yv;
+                if (oh) oh[slot] = h[k];
+                if (oidx) oidx[slot] = k;
+            }
+        }
+    }
+}
+
+// The blended surface at (x, y): sum_w weight_w f_w / sum_w weight_w over the windows whose
+// extended box holds the query (f_w: the window's own surface, as the batched evaluation).
+template <int KIND>
+__device__ __forceinline__ double eval_windows_at(const Binned& bd, const TileDev* __restrict__ td,
+                                                  const double* __restrict__ c, const WinGeom& g,
+                                                  double x, double y) {
+    const int2 rx = win_range(x, g.x0, g.x1, g.wx, g.d);
+    const int2 ry = win_range(y, g.y0, g.y1, g.wy, g.d);
+    double num = 0.0, den = 0.0;
+    for (int j = ry.x; j <= ry.y; ++j) {
+        if (!win_member(y, g.y0, g.y1, j, g.wy, g.d, 0.0)) continue;
+        const double wy = win_axis_weight(y, g.y0, g.y1, j, g.wy, g.d);
+        if (wy == 0.0) continue;
+        for (int i = rx.x; i <= rx.y; ++i) {
+            if (!win_member(x, g.x0, g.x1, i, g.wx, g.d, 0.0)) continue;
+            const double wt = wy * win_axis_weight(x, g.x0, g.x1, i, g.wx, g.d);
+            if (wt == 0.0) continue;
+            num = fma(wt, eval_tile_at<KIND>(bd, td[j * g.wx + i], c, x, y), num);
+            den += wt;
+        }
+    }
+    return den > 0.0 ? num / den : 0.0;
+}
+
+template <int KIND>
+__global__ void k_eval_windows(Binned bd, const TileDev* __restrict__ td, const double* __restrict__ c,
+                               WinGeom g, const double* __restrict__ qx, const double* __restrict__ qy,
+                               int64_t Q, double* __restrict__ f) {
+    for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < Q;
+         q += int64_t(gridDim.x) * blockDim.x)
+        f[q] = eval_windows_at<KIND>(bd, td, c, g, qx[q], qy[q]);
+}
+
+// The node-centred nx x ny grid over box (inclusive linspace, the last node exactly at the
+// box's end), f[i nx + j].
+template <int KIND>
+__global__ void k_eval_windows_grid(Binned bd, const TileDev* __restrict__ td,
+                                    const double* __restrict__ c, WinGeom g, int nx, int ny,
+                                    double bx0, double by0, double bx1, double by1,
+                                    double* __restrict__ f) {
+    const int64_t Q = int64_t(nx) * ny;
+    const double sx = nx > 1 ? (bx1 - bx0) / (nx - 1) : 0.0;
+    const double sy = ny > 1 ? (by1 - by0) / (ny - 1) : 0.0;
+    for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < Q;
+         q += int64_t(gridDim.x) * blockDim.x) {
+        const int i = int(q / nx), j = int(q % nx);
+        const double x = (j == nx - 1 && nx > 1) ? bx1 : __dadd_rn(__dmul_rn(double(j), sx), bx0);
+        const double y = (i == ny - 1 && ny > 1) ? by1 : __dadd_rn(__dmul_rn(double(i), sy), by0);
+        f[q] = eval_windows_at<KIND>(bd, td, c, g, x, y);
+    }
+}
+
+WinGeom win_geom(const rbf_ctx* ctx) {
+    WinGeom g;
+    g.x0 = ctx->win_bbox[0];
+    g.y0 = ctx->win_bbox[1];
+    g.x1 = ctx->win_bbox[2];
+    g.y1 = ctx->win_bbox[3];
+    g.d = ctx->win_overlap;
+    g.R = ctx->win_R;
+    g.wx = ctx->win_wx;
+    g.wy = ctx->win_wy;
+    return g;
+}
+
+}  // namespace
+
+rbf_status window_bin_run(rbf_ctx* ctx, const double* cx, const double* cy, int64_t M,
+                          const double* px, const double* py, const double* h, int64_t N,
+                          double R, const double* bbox, int wx, int wy, double overlap,
+                          cudaStream_t st) {
+    ctx->win_on = false;
+    const int T = wx * wy;
+    WinGeom g;
+    g.x0 = bbox[0];
+    g.y0 = bbox[1];
+    g.x1 = bbox[2];
+    g.y1 = bbox[3];
+    g.d = overlap;
+    g.R = R;
+    g.wx = wx;
+    g.wy = wy;
+    rbf_status s;
+    if ((s = ensure(ctx, ctx->win_count, sizeof(int) * 4 * size_t(T), st)) != RBF_OK) return s;
+    int* ccount = ctx->win_count.as<int>();
+    int* pcount = ccount + T;
+    int* ccur = ccount + 2 * T;
+    int* pcur = ccount + 3 * T;
+    RBF_CUDA_TRY(cudaMemsetAsync(ccount, 0, sizeof(int) * 4 * size_t(T), st));
+    const int gb = 152 * 8;
+    k_win_items<<<gb, 256, 0, st>>>(cx, cy, nullptr, M, g, R, ccount, nullptr, nullptr, nullptr,
+                                    nullptr, nullptr, nullptr);
+    k_win_items<<<gb, 256, 0, st>>>(px, py, nullptr, N, g, 0.0, pcount, nullptr, nullptr, nullptr,
+                                    nullptr, nullptr, nullptr);
+    ctx->launches += 2;
+    RBF_CUDA_TRY(cudaGetLastError());
+    std::vector<int> cnt(2 * size_t(T));
+    RBF_CUDA_TRY(cudaMemcpyAsync(cnt.data(), ccount, sizeof(int) * 2 * size_t(T),
+                                 cudaMemcpyDeviceToHost, st));
+    RBF_CUDA_TRY(cudaStreamSynchronize(st));
+    // each window's range of the concatenated centres and points, and its tile
+    std::vector<long long> off(2 * (size_t(T) + 1), 0);
+    std::vector<rbf_tile> tiles(T);
+    long long Mtot = 0, Ntot = 0;
+    for (int w = 0; w < T; ++w) {
+        if (cnt[w] < 1)
+            return set_err(ctx, RBF_ERR_ARG, "a window holds no centre: use fewer windows or more overlap");
+        off[w] = Mtot;
+        off[T + 1 + w] = Ntot;
+        const int i = w % wx, j = w / wx;
+        rbf_tile& t = tiles[w];
+        t.c0 = Mtot;
+        t.M = cnt[w];
+        t.p0 = Ntot;
+        t.N = cnt[T + w];
+        t.R = R;
+        // the tile's box: the window's extended box grown by R (the domain's box on its
+        // sides; items beyond it go to the edge cells)
+        t.bbox[0] = i == 0 ? g.x0 : (win_edge(g.x0, g.x1, i, wx) - overlap) - R;
+        t.bbox[2] = i == wx - 1 ? g.x1 : (win_edge(g.x0, g.x1, i + 1, wx) + overlap) + R;
+        t.bbox[1] = j == 0 ? g.y0 : (win_edge(g.y0, g.y1, j, wy) - overlap) - R;
+        t.bbox[3] = j == wy - 1 ? g.y1 : (win_edge(g.y0, g.y1, j + 1, wy) + overlap) + R;
+        Mtot += cnt[w];
+        Ntot += cnt[T + w];
+    }
+    off[T] = Mtot;
+    off[2 * size_t(T) + 1] = Ntot;
+    if (Mtot > (int64_t(1) << 30) || Ntot > (int64_t(1) << 30))
+        return set_err(ctx, RBF_ERR_LIMIT, "the windows hold more than 2^30 centres or points");
+    if ((s = ensure(ctx, ctx->win_off, sizeof(long long) * off.size(), st)) != RBF_OK) return s;
+    if ((s = ensure(ctx, ctx->win_c, sizeof(double) * 2 * size_t(std::max(Mtot, 1LL)), st)) != RBF_OK) return s;
+    if ((s = ensure(ctx, ctx->win_cidx, sizeof(long long) * size_t(std::max(Mtot, 1LL)), st)) != RBF_OK) return s;
+    if ((s = ensure(ctx, ctx->win_p, sizeof(double) * 3 * size_t(std::max(Ntot, 1LL)), st)) != RBF_OK) return s;
+    RBF_CUDA_TRY(cudaMemcpyAsync(ctx->win_off.p, off.data(), sizeof(long long) * off.size(),
+                                 cudaMemcpyHostToDevice, st));
+    double* wc = ctx->win_c.as<double>();
+    double* wp = ctx->win_p.as<double>();
+    const long long* doff = ctx->win_off.as<long long>();
+    k_win_items<<<gb, 256, 0, st>>>(cx, cy, nullptr, M, g, R, nullptr, doff, ccur, wc, wc + Mtot,
+                                    nullptr, ctx->win_cidx.as<long long>());
+    if (N > 0)
+        k_win_items<<<gb, 256, 0, st>>>(px, py, h, N, g, 0.0, nullptr, doff + T + 1, pcur, wp,
+                                        wp + Ntot, wp + 2 * Ntot, nullptr);
+    ctx->launches += 2;
+    RBF_CUDA_TRY(cudaGetLastError());
+    // `off` is pageable host memory: the copy has read it by the time cudaMemcpyAsync returns
+    if ((s = bin_tiles_run(ctx, tiles.data(), T, wc, wc + Mtot, Mtot, wp, wp + Ntot, wp + 2 * Ntot,
+                           Ntot, st)) != RBF_OK)
+        return s;
+    ctx->win_on = true;
+    ctx->win_wx = wx;
+    ctx->win_wy = wy;
+    ctx->win_overlap = overlap;
+    ctx->win_R = R;
+    for (int k = 0; k < 4; ++k) ctx->win_bbox[k] = bbox[k];
+    ctx->win_M = Mtot;
+    ctx->win_N = Ntot;
+    return RBF_OK;
+}
+
+// The blended surface: at queries (qx non-null) or on the nx x ny grid over box.
+rbf_status window_eval_run(rbf_ctx* ctx, const double* c, const double* qx, const double* qy,
+                           int64_t Q, int nx, int ny, const double* box, double* f, cudaStream_t st) {
+    rbf_status s = ensure(ctx, ctx->csort, sizeof(double) * ctx->M, st);
+    if (s != RBF_OK) return s;
+    const Binned bd = view(ctx);
+    launch_gather_sorted(c, bd.cperm, ctx->csort.as<double>(), ctx->M, st);
+    ctx->launches += 1;
+    const TileDev* td = ctx->tdesc.as<TileDev>();
+    const double* cs = ctx->csort.as<double>();
+    const WinGeom g = win_geom(ctx);
+    const int64_t n = qx ? Q : int64_t(nx) * ny;
+    if (n == 0) return RBF_OK;
+    const int grid = int(std::min<int64_t>(div_up(n, 256), 152 * 16));
+#define EVAL_WIN(K)                                                                          \
+    if (qx) k_eval_windows<K><<<grid, 256, 0, st>>>(bd, td, cs, g, qx, qy, Q, f);             \
+    else k_eval_windows_grid<K><<<grid, 256, 0, st>>>(bd, td, cs, g, nx, ny, box[0], box[1],  \
+                                                       box[2], box[3], f);
+    switch (ctx->kernel) {
+        case RBF_W30: EVAL_WIN(0) break;
+        case RBF_W31: EVAL_WIN(1) break;
+        case RBF_W32: EVAL_WIN(2) break;
+        default: EVAL_WIN(3) break;
+    }
+#undef EVAL_WIN
+    ctx->launches += 1;
+    RBF_CUDA_TRY(cudaGetLastError());
+    return RBF_OK;
+}
+
 }  // namespace rbf

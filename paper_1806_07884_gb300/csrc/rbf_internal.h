@@ -159,6 +159,17 @@ struct rbf_ctx {
     };
     TileGraph bt_graph[2];
 
+    // ---- moving window (rbf_bin_windows): the windows are the tiles of a batch ----
+    bool win_on = false;             // the batch was laid out by rbf_bin_windows
+    int win_wx = 0, win_wy = 0;
+    double win_overlap = 0.0, win_R = 0.0, win_bbox[4] = {0.0, 0.0, 1.0, 1.0};
+    int64_t win_M = 0, win_N = 0;    // centres and points summed over the windows
+    rbf_buf win_count;               // per window: centre and point counts, scatter cursors
+    rbf_buf win_off;                 // per window: first centre, first point (and the totals)
+    rbf_buf win_c;                   // the windows' centres (x then y), window after window
+    rbf_buf win_cidx;                // input index of each of them
+    rbf_buf win_p;                   // the windows' points (x, y, h), window after window
+
     // ---- learned warm start (rbf_features / rbf_warm_start / rbf_mlp_*) ----
     rbf_buf sigma;                   // [T or 1] height scales, then 2 T sums
     rbf_buf feat;                    // [M x 32] features and [M] network outputs
@@ -203,6 +214,12 @@ rbf_status solve_tiles_run(rbf_ctx* ctx, double* c, int use_c0, double tol, int 
 rbf_status autotune_run(rbf_ctx* ctx, cudaStream_t st);
 // timing hooks of a batched system: the batched SpMV alone, or whole batched CG iterations
 rbf_status bench_tiles_run(rbf_ctx* ctx, int reps, bool spmv_only, cudaStream_t st);
+rbf_status window_bin_run(rbf_ctx* ctx, const double* cx, const double* cy, int64_t M,
+                          const double* px, const double* py, const double* h, int64_t N,
+                          double R, const double* bbox, int wx, int wy, double overlap,
+                          cudaStream_t st);
+rbf_status window_eval_run(rbf_ctx* ctx, const double* c, const double* qx, const double* qy,
+                           int64_t Q, int nx, int ny, const double* box, double* f, cudaStream_t st);
 rbf_status eval_tiles_run(rbf_ctx* ctx, const double* c, const double* qx, const double* qy,
                           const int64_t* qoff, int nx, int ny, double* f, cudaStream_t st);
 
