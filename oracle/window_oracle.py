@@ -12,9 +12,14 @@ Definitions (the paper gives the technique's name only; these are the library's 
 * window (i, j)'s extended box: [a_i - d, a_{i+1} + d] x [b_j - d, b_{j+1} + d] (closed),
   d the overlap; a side on the boundary of bbox extends to infinity, so that items outside
   bbox belong to the edge windows;
-* its points: the points in its extended box; its centres: the centres in the extended box
-  grown by R on every side (every centre whose support reaches one of its points);
-* its fit: the least-squares weights of those points and centres (oracle.fit);
+* its data box: the extended box grown by a margin m >= 0 on its inner sides (the library's
+  default m = R); its points and its centres: those in the data box. A centre at the data
+  box's edge keeps at least about half of its support's points, so a window's system is
+  about as well conditioned as the global one; taking the centres of a box grown by R around
+  the points instead leaves centres whose support holds a sliver of the window's points
+  (condition numbers up to ~1e14 on clustered terrain against ~1e5 globally);
+* its fit: the least-squares weights of those points and centres (oracle.fit); the window's
+  surface is used inside its extended box only;
 * the surface at q: sum_w w_w(q) f_w(q) / sum_w w_w(q) over the windows whose extended box
   holds q, with w_w = rho_x(q_x) rho_y(q_y) and rho along x for window i the product of
   s((q_x - (a_i - d)) / (2 d)) (when i > 0) and s(((a_{i+1} + d) - q_x) / (2 d)) (when
@@ -75,26 +80,27 @@ def axis_weight(v, edges, i, d):
     return w
 
 
-def windows(P, C, R, bbox, wx, wy, d):
-    """Per window (i, j) in row-major order (j slow): (point indices, centre indices)."""
+def windows(P, C, bbox, wx, wy, d, m):
+    """Per window (i, j) in row-major order (j slow): (point indices, centre indices) of the
+    items in its data box (extended box grown by the margin m)."""
     ex = core_edges(bbox[0], bbox[2], wx)
     ey = core_edges(bbox[1], bbox[3], wy)
     out = []
     for j in range(wy):
         for i in range(wx):
-            pm = members(P[:, 0], ex, i, d) & members(P[:, 1], ey, j, d)
-            cm = members(C[:, 0], ex, i, d, R) & members(C[:, 1], ey, j, d, R)
+            pm = members(P[:, 0], ex, i, d, m) & members(P[:, 1], ey, j, d, m)
+            cm = members(C[:, 0], ex, i, d, m) & members(C[:, 1], ey, j, d, m)
             out.append((np.nonzero(pm)[0], np.nonzero(cm)[0]))
     return out
 
 
-def fit_windows(P, h, C, R, bbox, wx, wy, d, kind="w31", min_support=3, method="cholesky"):
+def fit_windows(P, h, C, R, bbox, wx, wy, d, m, kind="w31", min_support=3, method="cholesky"):
     """Each window's weights: a list of (centre indices, c) in window order."""
     P = np.asarray(P, np.float64)
     C = np.asarray(C, np.float64)
     h = np.asarray(h, np.float64)
     res = []
-    for pi, ci in windows(P, C, R, bbox, wx, wy, d):
+    for pi, ci in windows(P, C, bbox, wx, wy, d, m):
         if ci.size == 0:
             res.append((ci, np.zeros(0)))
             continue
