@@ -136,6 +136,12 @@ def parse():
     ap.add_argument("--host-b-mb", type=float, default=64.0,
                     help="also time one big-data step with B in host memory, assembled in "
                          "blocks of this many MB (0: skip)")
+    ap.add_argument("--windows", type=int, default=4,
+                    help="also time the big-data fit as W x W moving windows (0: skip)")
+    ap.add_argument("--window-overlap", type=float, default=2.0,
+                    help="the windows' overlap in units of R")
+    ap.add_argument("--window-margin", type=float, default=2.0,
+                    help="the windows' data margin in units of R")
     ap.add_argument("--no-learned", dest="learned", action="store_false",
                     help="cold start instead of the learned warm start in the timed step")
     ap.add_argument("--tiles", type=int, default=512)
@@ -523,6 +529,75 @@ def bench_host_b(args, ctx, step, timed, N, M, f_dev, fbuf, stream):
             "rel_err_f_vs_device_b": err, "bar": 1e-6, "ok": err <= 1e-6}
 
 
+def bench_windows(args, dev, d, pb, f_global, stream, flush):
+    """The big-data fit as W x W overlapping windows (the moving window of Section 7): one
+    step = bin the windows, assemble and solve them as one batch, evaluate the blended surface
+    on the same grid; N over its device time (one warm-up, two timed steps). The blended
+    surface is another approximation than the global fit: its difference from it is reported,
+    not held to a parity bar (the GPU tests tie both to their oracles)."""
+    import torch
+
+    import paper_1806_07884_gb300 as pkg
+
+    W, n = args.windows, args.big_grid
+    ov, mg = args.window_overlap * pb.R, args.window_margin * pb.R
+    ctx = pkg.Context(dev.index)
+    fbuf = torch.empty((n, n), dtype=torch.float64, device=dev)
+    box = (0.0, 0.0, 1.0, 1.0)
+
+    def step():
+        ctx.bin_windows(*d, pb.R, pb.bbox, W, W, ov, mg)
+        ctx.assemble(pb.kernel, args.prec)
+        c, info, tinfo = ctx.solve_tiles(tol=args.tol, maxit=50000)
+        ctx.eval_windows_grid(c, n, n, box, out=fbuf)
+        return c, info, tinfo
+
+    try:
+        step()
+        torch.cuda.synchronize()
+        ms, infos = [], []
+        for _ in range(2):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, info, tinfo = step()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            infos.append((info, tinfo))
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        flush.zero_()
+        ev[0].record(stream)
+        ctx.bin_windows(*d, pb.R, pb.bbox, W, W, ov, mg)
+        ev[1].record(stream)
+        ctx.assemble(pb.kernel, args.prec)
+        ev[2].record(stream)
+        c, _, _ = ctx.solve_tiles(tol=args.tol, maxit=50000)
+        ev[3].record(stream)
+        ctx.eval_windows_grid(c, n, n, box, out=fbuf)
+        ev[4].record(stream)
+        torch.cuda.synchronize()
+        phases = {nm: round(ev[i].elapsed_time(ev[i + 1]), 3)
+                  for i, nm in enumerate(["bin", "assemble", "solve", "eval"])}
+        dif = fbuf - f_global
+        diff = float(dif.abs().max() / f_global.abs().max())
+        rms = float(dif.square().mean().sqrt() / f_global.square().mean().sqrt())
+        info, tinfo = infos[-1]
+        its = [t["iterations"] for t in tinfo]
+        out = {"windows": f"{W}x{W}", "overlap_in_R": args.window_overlap,
+               "value": pb.N / (statistics.mean(ms) * 1e-3), "unit": "points/s",
+               "ms_per_step": round(statistics.mean(ms), 3), "step_ms": [round(x, 3) for x in ms],
+               "margin_in_R": args.window_margin, "phases_ms": phases, "centres_over_M": round(ctx.M / pb.M, 4),
+               "points_over_N": round(ctx.N / pb.N, 4),
+               "iterations_max": max(its), "iterations_mean": round(sum(its) / len(its), 1),
+               "promoted_windows": sum(int(t["promoted"]) for t in tinfo),
+               "rel_diff_f_vs_global_fit": diff, "rms_diff_f_vs_global_fit": rms}
+    finally:
+        ctx.close()
+    return out
+
+
 def bench_bigdata(args, rank, dev, stream, flush, hbm, peak_source):
     """The big-data workload: N = 20 M points with 10:1 density variation, 8-octave value-noise
     heights, M = 2 M Halton centres, Wendland phi_3,2, FP32 assembly and SpMV with FP64
@@ -621,6 +696,8 @@ def bench_bigdata(args, rank, dev, stream, flush, hbm, peak_source):
            "phases_ms": phases, "roofline": roof}
     if args.host_b_mb > 0:
         out["out_of_core"] = bench_host_b(args, ctx, step, timed, N, M, f_fast, fbuf, stream)
+    if args.windows > 0:
+        out["moving_window"] = bench_windows(args, dev, d, pb, f_fast, stream, flush)
     if not args.no_fp64_compare:
         ms64, _, infos64 = timed("fp64", args.tol, 1)
         out["fp64_path"] = {"value": N / (ms64 * 1e-3), "ms_per_step": round(ms64, 3),

@@ -374,9 +374,12 @@ rbf_status rbf_eval_tiles_grid(rbf_ctx* ctx, const double* c, int nx, int ny, do
  *   extended box    the core box grown by `overlap` on its inner sides, closed; a side on the
  *                   domain's boundary is open to infinity (items outside bbox belong to the
  *                   edge windows)
- *   points          those in the extended box
- *   centres         those in the extended box grown by R (every centre whose support reaches
- *                   one of the window's points), so a centre can belong to several windows
+ *   data box        the extended box grown by `margin` on its inner sides
+ *   points, centres those in the data box (an item can belong to several windows); a centre
+ *                   at the data box's edge keeps about half of its support's points, so with
+ *                   margin >= R a window's system is about as well conditioned as the whole
+ *                   domain's, and the window's surface inside its extended box has every
+ *                   centre within R
  *   weight          the product over the inner sides of s((q - (a_i - overlap)) / (2 overlap))
  *                   and s(((a_{i+1} + overlap) - q) / (2 overlap)), s(t) = t^2 (3 - 2t) on
  *                   [0, 1] (0 below, 1 above): neighbours' weights sum to one across their
@@ -390,13 +393,13 @@ rbf_status rbf_eval_tiles_grid(rbf_ctx* ctx, const double* c, int nx, int ny, do
 
 /* Lay the windows out over bbox = {x0, y0, x1, y1} (HOST; x1 > x0, y1 > y0) and bin them as
  * a batch: cx, cy (M centres), px, py, h (N points) DEVICE arrays in the caller's order; R > 0
- * the support radius of every window; 1 <= wx, wy, wx wy <= 65536; overlap >= 0.
- * Synchronises `stream`. Returns RBF_ERR_ARG for a window without centres (fewer windows or a
+ * the support radius of every window; 1 <= wx, wy, wx wy <= 65536; overlap >= 0; margin >= 0
+ * (R is the usual choice). Synchronises `stream`. Returns RBF_ERR_ARG for a window without centres (fewer windows or a
  * larger overlap), RBF_ERR_LIMIT as rbf_bin_tiles. */
 rbf_status rbf_bin_windows(rbf_ctx* ctx, const double* cx, const double* cy, int64_t M,
                            const double* px, const double* py, const double* h, int64_t N,
                            double R, const double* bbox, int wx, int wy, double overlap,
-                           void* stream);
+                           double margin, void* stream);
 
 /* Centres (Mtot) and points (Ntot) summed over the windows of the last rbf_bin_windows (HOST
  * outputs): the length of rbf_solve_tiles' c. */

@@ -274,14 +274,16 @@ class Context:
 
     # -- moving window ----------------------------------------------------------------------
     def bin_windows(self, cx, cy, px, py, h, R: float, bbox, wx: int, wy: int, overlap: float,
-                    stream=None):
+                    margin: float | None = None, stream=None):
         """Lay out wx x wy overlapping windows over bbox and bin them as a batch (see
-        rbf_bin_windows); then assemble and solve_tiles fit every window."""
+        rbf_bin_windows; margin defaults to R); then assemble and solve_tiles fit every
+        window."""
         M, N = int(cx.numel()), int(px.numel())
         box = (C.c_double * 4)(*[float(v) for v in bbox])
+        m = float(R if margin is None else margin)
         s = self.lib.rbf_bin_windows(self._h, _dptr(cx, "cx"), _dptr(cy, "cy"), M, _dptr(px, "px"),
                                      _dptr(py, "py"), _dptr(h, "h"), N, float(R), box, int(wx),
-                                     int(wy), float(overlap), self._stream(stream))
+                                     int(wy), float(overlap), m, self._stream(stream))
         self._check(s, "rbf_bin_windows")
         mt, nt = C.c_int64(), C.c_int64()
         self._check(self.lib.rbf_window_sizes(self._h, C.byref(mt), C.byref(nt)), "rbf_window_sizes")
@@ -497,7 +499,7 @@ def fit_tiles(problems, kernel: str = "w31", prec: str = "fp32_refine", tol: flo
 def fit_windows(points, h, centres, R: float, wx: int, wy: int, overlap: float,
                 kernel: str = "w31", prec: str = "fp32_refine", bbox=(0.0, 0.0, 1.0, 1.0),
                 tol: float = 1e-10, maxit: int = 200000, min_support: int = 3,
-                ctx: Context | None = None, device: int = 0):
+                margin: float | None = None, ctx: Context | None = None, device: int = 0):
     """Moving-window fit: wx x wy overlapping windows fitted as one batch. Returns (c, info,
     per-window info, ctx); c holds the windows' weights one window after another
     (ctx.window_centres() maps them to input centres), ctx.eval_windows(_grid) blends them."""
@@ -511,7 +513,7 @@ def fit_windows(points, h, centres, R: float, wx: int, wy: int, overlap: float,
     P, H, Cc = dev64(points), dev64(h), dev64(centres)
     ctx = ctx or Context(device)
     ctx.bin_windows(Cc[:, 0].contiguous(), Cc[:, 1].contiguous(), P[:, 0].contiguous(),
-                    P[:, 1].contiguous(), H.contiguous(), R, bbox, wx, wy, overlap)
+                    P[:, 1].contiguous(), H.contiguous(), R, bbox, wx, wy, overlap, margin)
     ctx.assemble(kernel, prec)
     c, info, tinfo = ctx.solve_tiles(tol=tol, maxit=maxit, min_support=min_support)
     return c, info, tinfo, ctx

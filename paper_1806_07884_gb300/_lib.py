@@ -79,7 +79,8 @@ SIGNATURES = {
     "rbf_autotune": (_I, [_P, _P]),
     "rbf_eval_tiles": (_I, [_P, _P, _P, _P, C.POINTER(_I64), _P, _P]),
     "rbf_eval_tiles_grid": (_I, [_P, _P, _I, _I, _P, _P]),
-    "rbf_bin_windows": (_I, [_P, _P, _P, _I64, _P, _P, _P, _I64, _D, C.POINTER(_D), _I, _I, _D, _P]),
+    "rbf_bin_windows": (_I, [_P, _P, _P, _I64, _P, _P, _P, _I64, _D, C.POINTER(_D), _I, _I, _D, _D,
+                             _P]),
     "rbf_window_sizes": (_I, [_P, C.POINTER(_I64), C.POINTER(_I64)]),
     "rbf_window_centres": (_I, [_P, _P, _I64, _P]),
     "rbf_eval_windows": (_I, [_P, _P, _P, _P, _I64, _P, _P]),

@@ -159,7 +159,7 @@ rbf_status rbf_destroy(rbf_ctx* ctx) {
                        &ctx->partial, &ctx->scal, &ctx->csort, &ctx->sigma, &ctx->feat,
                        &ctx->mlp_part, &ctx->astore, &ctx->amask, &ctx->woff, &ctx->wsize,
                        &ctx->pE, &ctx->pE32, &ctx->pdev, &ctx->pepart, &ctx->bblock, &ctx->bandtab,
-                       &ctx->win_count, &ctx->win_off, &ctx->win_c, &ctx->win_cidx, &ctx->win_p};
+                       &ctx->win_edges, &ctx->win_count, &ctx->win_off, &ctx->win_c, &ctx->win_cidx, &ctx->win_p};
     for (rbf_buf* b : bufs) release(ctx, *b);
     if (ctx->hpinned) cudaFreeHost(ctx->hpinned);
     if (ctx->bhost) cudaFreeHost(ctx->bhost);
@@ -311,7 +311,7 @@ rbf_status rbf_bin_tiles(rbf_ctx* ctx, const rbf_tile* tiles, int T, const doubl
 rbf_status rbf_bin_windows(rbf_ctx* ctx, const double* cx, const double* cy, int64_t M,
                            const double* px, const double* py, const double* h, int64_t N,
                            double R, const double* bbox, int wx, int wy, double overlap,
-                           void* stream) {
+                           double margin, void* stream) {
     if (!ctx) return RBF_ERR_ARG;
     ctx->binned = false;
     ctx->assembled = false;
@@ -327,9 +327,13 @@ rbf_status rbf_bin_windows(rbf_ctx* ctx, const double* cx, const double* cy, int
         return set_err(ctx, RBF_ERR_ARG, "bbox must be {x0, y0, x1, y1} with x1 > x0, y1 > y0");
     if (wx < 1 || wy < 1 || int64_t(wx) * wy > 65536)
         return set_err(ctx, RBF_ERR_ARG, "need wx, wy >= 1 and wx * wy <= 65536 windows");
+    if (!(double(wx) / (bbox[2] - bbox[0]) < 1e30) || !(double(wy) / (bbox[3] - bbox[1]) < 1e30))
+        return set_err(ctx, RBF_ERR_ARG, "windows narrower than 1e-30");
     if (!(overlap >= 0.0) || !isfinite(overlap)) return set_err(ctx, RBF_ERR_ARG, "overlap must be finite and >= 0");
+    if (!(margin >= 0.0) || !isfinite(margin)) return set_err(ctx, RBF_ERR_ARG, "margin must be finite and >= 0");
     DeviceGuard dg(ctx->device);
-    rbf_status s = window_bin_run(ctx, cx, cy, M, px, py, h, N, R, bbox, wx, wy, overlap, as_stream(stream));
+    rbf_status s = window_bin_run(ctx, cx, cy, M, px, py, h, N, R, bbox, wx, wy, overlap, margin,
+                                  as_stream(stream));
     if (s == RBF_OK) ctx->binned = true;
     return s;
 }

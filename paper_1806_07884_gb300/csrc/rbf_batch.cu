@@ -1617,36 +1617,48 @@ rbf_status autotune_run(rbf_ctx* ctx, cudaStream_t st) {
 //   core edges  a_i = x0 + (x1 - x0) i / wx  (likewise along y)
 //   extended    [a_i - d, a_{i+1} + d], closed; a side on the domain's boundary is open to
 //               infinity (items outside the box belong to the edge windows)
-//   points      in the extended box; centres in the extended box grown by R
+//   data box    the extended box grown by the margin m on its inner sides; the window's
+//               points and centres are those in it (a centre at its edge keeps about half of
+//               its support's points, so the window's system stays well conditioned)
 //   weight      product over the inner sides of s((q - (a_i - d)) / 2d), s(((a_{i+1} + d) - q)
 //               / 2d), s(t) = t^2 (3 - 2t) clamped to [0, 1]; with d = 0 the steps q >= a_i,
 //               q < a_{i+1}
 // ---------------------------------------------------------------------------------------
 namespace {
 
+// The layout's bounds, computed once on the host in the operation order of the definition
+// (membership decisions are exact comparisons against these values), DEVICE table:
+//   x: data_lo[wx], data_hi[wx], ext_lo[wx], ext_hi[wx]; then y likewise (wy each)
+// data = extended box grown by the margin; sides on the domain's boundary are -inf / +inf.
 struct WinGeom {
-    double x0, y0, x1, y1, d, R;
+    double x0, y0, d;
+    float inv_cx, inv_cy;        // wx / (x1 - x0), wy / (y1 - y0): candidate lookup only
+    float reach_data, reach_ext; // d + margin, d
+    const double* tx;            // x bounds (4 wx values)
+    const double* ty;            // y bounds (4 wy values)
     int wx, wy;
 };
 
-__host__ __device__ __forceinline__ double win_edge(double lo, double hi, int i, int n) {
+// Core edge i of n over [lo, hi] (host).
+inline double win_edge(double lo, double hi, int i, int n) {
     return lo + (hi - lo) * double(i) / double(n);
 }
 
-// Is coordinate v inside window i's extended interval (grown by `grow`) along one axis?
-__host__ __device__ __forceinline__ bool win_member(double v, double lo, double hi, int i, int n,
-                                                   double d, double grow) {
-    const bool lo_ok = i == 0 || v >= (win_edge(lo, hi, i, n) - d) - grow;
-    const bool hi_ok = i == n - 1 || v <= (win_edge(lo, hi, i + 1, n) + d) + grow;
-    return lo_ok && hi_ok;
+// Is v inside window i's interval along one axis? t: that axis' bounds, data or extended.
+__device__ __forceinline__ bool win_member(double v, const double* __restrict__ t, int i, int n,
+                                           bool data) {
+    const double* b = t + (data ? 0 : 2 * n);
+    return v >= b[i] && v <= b[n + i];
 }
 
-// The windows along one axis that may hold v (a superset; callers test each exactly).
-__device__ __forceinline__ int2 win_range(double v, double lo, double hi, int n, double reach) {
-    const double w = (hi - lo) / double(n);
-    const double a = floor((v - reach - lo) / w) - 1.0, b = floor((v + reach - lo) / w) + 1.0;
-    const int i0 = int(fmin(fmax(a, 0.0), double(n - 1)));
-    const int i1 = int(fmin(fmax(b, 0.0), double(n - 1)));
+// The windows along one axis that may hold v: a superset (one window of slack on each side
+// absorbs the FP32 rounding); callers test each exactly. v - lo is taken in FP64 so that the
+// rounding is relative to the offset into the domain, not to the coordinates.
+__device__ __forceinline__ int2 win_range(double v, double lo, float inv_c, int n, float reach) {
+    const float dv = float(v - lo);
+    const float a = floorf((dv - reach) * inv_c) - 1.0f, b = floorf((dv + reach) * inv_c) + 1.0f;
+    const int i0 = int(fminf(fmaxf(a, 0.0f), float(n - 1)));
+    const int i1 = int(fminf(fmaxf(b, 0.0f), float(n - 1)));
     return make_int2(i0, i1);
 }
 
@@ -1655,48 +1667,126 @@ __device__ __forceinline__ double smooth_step01(double t) {
     return t * t * (3.0 - 2.0 * t);
 }
 
-__device__ __forceinline__ double win_axis_weight(double v, double lo, double hi, int i, int n, double d) {
+// Window i's partition-of-unity factor along one axis (t: that axis' bounds).
+__device__ __forceinline__ double win_axis_weight(double v, const double* __restrict__ t, int i,
+                                                  int n, double d) {
+    const double lo = t[2 * n + i], hi = t[3 * n + i];
     double w = 1.0;
     if (d > 0.0) {
-        if (i > 0) w *= smooth_step01((v - (win_edge(lo, hi, i, n) - d)) / (2.0 * d));
-        if (i < n - 1) w *= smooth_step01(((win_edge(lo, hi, i + 1, n) + d) - v) / (2.0 * d));
+        if (i > 0) w *= smooth_step01((v - lo) / (2.0 * d));
+        if (i < n - 1) w *= smooth_step01((hi - v) / (2.0 * d));
     } else {
-        if (i > 0 && !(v >= win_edge(lo, hi, i, n))) w = 0.0;
-        if (i < n - 1 && !(v < win_edge(lo, hi, i + 1, n))) w = 0.0;
+        if (i > 0 && !(v >= lo)) w = 0.0;
+        if (i < n - 1 && !(v < hi)) w = 0.0;
     }
     return w;
 }
 
+// Calls f(w) for every window w whose data box holds (xv, yv).
+template <class F>
+__device__ __forceinline__ void for_each_window(double xv, double yv, const WinGeom& g, F&& f) {
+    const int2 rx = win_range(xv, g.x0, g.inv_cx, g.wx, g.reach_data);
+    const int2 ry = win_range(yv, g.y0, g.inv_cy, g.wy, g.reach_data);
+    for (int j = ry.x; j <= ry.y; ++j) {
+        if (!win_member(yv, g.ty, j, g.wy, true)) continue;
+        for (int i = rx.x; i <= rx.y; ++i)
+            if (win_member(xv, g.tx, i, g.wx, true)) f(j * g.wx + i);
+    }
+}
+
 // Count (cursor == nullptr) or scatter the items into the windows that hold them: each item
-// of window w goes to off[w] + (a slot taken with an atomic), with its input index.
+// of window w goes to off[w] + (a slot taken with an atomic), with its input index. One
+// global atomic per (item, window): for many windows, where few items share a counter.
 __global__ void k_win_items(const double* __restrict__ x, const double* __restrict__ y,
-                            const double* __restrict__ h, int64_t n, WinGeom g, double grow,
+                            const double* __restrict__ h, int64_t n, WinGeom g,
                             int* __restrict__ count, const long long* __restrict__ off,
                             int* __restrict__ cursor, double* __restrict__ ox,
                             double* __restrict__ oy, double* __restrict__ oh,
                             long long* __restrict__ oidx) {
-    const double reach = g.d + grow;
     for (int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; k < n;
          k += int64_t(gridDim.x) * blockDim.x) {
         const double xv = x[k], yv = y[k];
-        const int2 rx = win_range(xv, g.x0, g.x1, g.wx, reach);
-        const int2 ry = win_range(yv, g.y0, g.y1, g.wy, reach);
-        for (int j = ry.x; j <= ry.y; ++j) {
-            if (!win_member(yv, g.y0, g.y1, j, g.wy, g.d, grow)) continue;
-            for (int i = rx.x; i <= rx.y; ++i) {
-                if (!win_member(xv, g.x0, g.x1, i, g.wx, g.d, grow)) continue;
-                const int w = j * g.wx + i;
-                if (!cursor) {
-                    atomicAdd(&count[w], 1);
-                    continue;
-                }
-                const long long slot = off[w] + atomicAdd(&cursor[w], 1);
-                ox[slot] = xv;
-                oy[slot] = yv;
-                if (oh) oh[slot] = h[k];
-                if (oidx) oidx[slot] = k;
+        for_each_window(xv, yv, g, [&](int w) {
+            if (!cursor) {
+                atomicAdd(&count[w], 1);
+                return;
+            }
+            const long long slot = off[w] + atomicAdd(&cursor[w], 1);
+            ox[slot] = xv;
+            oy[slot] = yv;
+            if (oh) oh[slot] = h[k];
+            if (oidx) oidx[slot] = k;
+        });
+    }
+}
+
+// The same for few windows (T <= kWinBlockMax), where every item of a window would hit one
+// counter: per chunk of kWinItems items the block counts its items per window in shared
+// memory, takes one range per window with one global atomic, then scatters into its ranges.
+constexpr int kWinBlockMax = 4096;
+constexpr int kWinThreads = 512;
+constexpr int kWinPerThread = 4;
+
+__global__ void __launch_bounds__(kWinThreads)
+k_win_items_block(const double* __restrict__ x, const double* __restrict__ y,
+                  const double* __restrict__ h, int64_t n, WinGeom g,
+                  int* __restrict__ count, const long long* __restrict__ off,
+                  int* __restrict__ cursor, double* __restrict__ ox, double* __restrict__ oy,
+                  double* __restrict__ oh, long long* __restrict__ oidx) {
+    extern __shared__ int win_sm[];
+    const int T = g.wx * g.wy;
+    int* scnt = win_sm;          // per window: this chunk's items, then the scatter cursor
+    int* sbase = win_sm + T;     // per window: the chunk's first slot in the window's range
+    constexpr int64_t kChunk = int64_t(kWinThreads) * kWinPerThread;
+    for (int64_t k0 = blockIdx.x * kChunk; k0 < n; k0 += int64_t(gridDim.x) * kChunk) {
+        for (int w = threadIdx.x; w < T; w += kWinThreads) scnt[w] = 0;
+        __syncthreads();
+        for (int r = 0; r < kWinPerThread; ++r) {
+            const int64_t k = k0 + r * kWinThreads + threadIdx.x;
+            if (k < n) for_each_window(x[k], y[k], g, [&](int w) { atomicAdd(&scnt[w], 1); });
+        }
+        __syncthreads();
+        for (int w = threadIdx.x; w < T; w += kWinThreads) {
+            const int c = scnt[w];
+            if (c > 0) {
+                if (!cursor) atomicAdd(&count[w], c);
+                else sbase[w] = atomicAdd(&cursor[w], c);
+            }
+            scnt[w] = 0;
+        }
+        __syncthreads();
+        if (cursor) {
+            for (int r = 0; r < kWinPerThread; ++r) {
+                const int64_t k = k0 + r * kWinThreads + threadIdx.x;
+                if (k >= n) continue;
+                const double xv = x[k], yv = y[k];
+                for_each_window(xv, yv, g, [&](int w) {
+                    const long long slot = off[w] + sbase[w] + atomicAdd(&scnt[w], 1);
+                    ox[slot] = xv;
+                    oy[slot] = yv;
+                    if (oh) oh[slot] = h[k];
+                    if (oidx) oidx[slot] = k;
+                });
             }
         }
+        __syncthreads();
+    }
+}
+
+// Counts or scatters the items into their windows (the block kernel for few windows).
+void launch_win_items(const double* x, const double* y, const double* h, int64_t n,
+                      const WinGeom& g, int* count, const long long* off,
+                      int* cursor, double* ox, double* oy, double* oh, long long* oidx,
+                      cudaStream_t st) {
+    if (n <= 0) return;
+    const int T = g.wx * g.wy;
+    if (T <= kWinBlockMax) {
+        const int64_t chunks = div_up(n, int64_t(kWinThreads) * kWinPerThread);
+        const int grid = int(std::min<int64_t>(chunks, 152 * 4));
+        k_win_items_block<<<grid, kWinThreads, sizeof(int) * 2 * size_t(T), st>>>(
+            x, y, h, n, g, count, off, cursor, ox, oy, oh, oidx);
+    } else {
+        k_win_items<<<152 * 8, 256, 0, st>>>(x, y, h, n, g, count, off, cursor, ox, oy, oh, oidx);
     }
 }
 
@@ -1706,16 +1796,16 @@ template <int KIND>
 __device__ __forceinline__ double eval_windows_at(const Binned& bd, const TileDev* __restrict__ td,
                                                   const double* __restrict__ c, const WinGeom& g,
                                                   double x, double y) {
-    const int2 rx = win_range(x, g.x0, g.x1, g.wx, g.d);
-    const int2 ry = win_range(y, g.y0, g.y1, g.wy, g.d);
+    const int2 rx = win_range(x, g.x0, g.inv_cx, g.wx, g.reach_ext);
+    const int2 ry = win_range(y, g.y0, g.inv_cy, g.wy, g.reach_ext);
     double num = 0.0, den = 0.0;
     for (int j = ry.x; j <= ry.y; ++j) {
-        if (!win_member(y, g.y0, g.y1, j, g.wy, g.d, 0.0)) continue;
-        const double wy = win_axis_weight(y, g.y0, g.y1, j, g.wy, g.d);
+        if (!win_member(y, g.ty, j, g.wy, false)) continue;
+        const double wy = win_axis_weight(y, g.ty, j, g.wy, g.d);
         if (wy == 0.0) continue;
         for (int i = rx.x; i <= rx.y; ++i) {
-            if (!win_member(x, g.x0, g.x1, i, g.wx, g.d, 0.0)) continue;
-            const double wt = wy * win_axis_weight(x, g.x0, g.x1, i, g.wx, g.d);
+            if (!win_member(x, g.tx, i, g.wx, false)) continue;
+            const double wt = wy * win_axis_weight(x, g.tx, i, g.wx, g.d);
             if (wt == 0.0) continue;
             num = fma(wt, eval_tile_at<KIND>(bd, td[j * g.wx + i], c, x, y), num);
             den += wt;
@@ -1752,17 +1842,44 @@ __global__ void k_eval_windows_grid(Binned bd, const TileDev* __restrict__ td,
     }
 }
 
-WinGeom win_geom(const rbf_ctx* ctx) {
+// The layout's geometry over its bounds table (DEVICE, 4 (wx + wy) values).
+WinGeom make_win_geom(const double* bbox, int wx, int wy, double overlap, double margin,
+                      const double* table) {
     WinGeom g;
-    g.x0 = ctx->win_bbox[0];
-    g.y0 = ctx->win_bbox[1];
-    g.x1 = ctx->win_bbox[2];
-    g.y1 = ctx->win_bbox[3];
-    g.d = ctx->win_overlap;
-    g.R = ctx->win_R;
-    g.wx = ctx->win_wx;
-    g.wy = ctx->win_wy;
+    g.x0 = bbox[0];
+    g.y0 = bbox[1];
+    g.d = overlap;
+    g.inv_cx = float(double(wx) / (bbox[2] - bbox[0]));
+    g.inv_cy = float(double(wy) / (bbox[3] - bbox[1]));
+    g.reach_data = float(overlap + margin);
+    g.reach_ext = float(overlap);
+    g.tx = table;
+    g.ty = table + 4 * size_t(wx);
+    g.wx = wx;
+    g.wy = wy;
     return g;
+}
+
+// The bounds table on the host: per axis data_lo, data_hi, ext_lo, ext_hi (n values each).
+std::vector<double> win_table(const double* bbox, int wx, int wy, double d, double m) {
+    std::vector<double> t(4 * (size_t(wx) + wy));
+    auto axis = [&](double* b, double lo, double hi, int n) {
+        for (int i = 0; i < n; ++i) {
+            const double elo = win_edge(lo, hi, i, n) - d, ehi = win_edge(lo, hi, i + 1, n) + d;
+            b[i] = i == 0 ? -INFINITY : elo - m;
+            b[n + i] = i == n - 1 ? INFINITY : ehi + m;
+            b[2 * n + i] = i == 0 ? -INFINITY : elo;
+            b[3 * n + i] = i == n - 1 ? INFINITY : ehi;
+        }
+    };
+    axis(t.data(), bbox[0], bbox[2], wx);
+    axis(t.data() + 4 * size_t(wx), bbox[1], bbox[3], wy);
+    return t;
+}
+
+WinGeom win_geom(const rbf_ctx* ctx) {
+    return make_win_geom(ctx->win_bbox, ctx->win_wx, ctx->win_wy, ctx->win_overlap,
+                         ctx->win_margin, ctx->win_edges.as<double>());
 }
 
 }  // namespace
@@ -1770,30 +1887,26 @@ WinGeom win_geom(const rbf_ctx* ctx) {
 rbf_status window_bin_run(rbf_ctx* ctx, const double* cx, const double* cy, int64_t M,
                           const double* px, const double* py, const double* h, int64_t N,
                           double R, const double* bbox, int wx, int wy, double overlap,
-                          cudaStream_t st) {
+                          double margin, cudaStream_t st) {
     ctx->win_on = false;
     const int T = wx * wy;
-    WinGeom g;
-    g.x0 = bbox[0];
-    g.y0 = bbox[1];
-    g.x1 = bbox[2];
-    g.y1 = bbox[3];
-    g.d = overlap;
-    g.R = R;
-    g.wx = wx;
-    g.wy = wy;
     rbf_status s;
+    const std::vector<double> tab = win_table(bbox, wx, wy, overlap, margin);
+    if ((s = ensure(ctx, ctx->win_edges, sizeof(double) * tab.size(), st)) != RBF_OK) return s;
+    // `tab` is pageable host memory: the copy has read it when cudaMemcpyAsync returns
+    RBF_CUDA_TRY(cudaMemcpyAsync(ctx->win_edges.p, tab.data(), sizeof(double) * tab.size(),
+                                 cudaMemcpyHostToDevice, st));
+    const WinGeom g = make_win_geom(bbox, wx, wy, overlap, margin, ctx->win_edges.as<double>());
     if ((s = ensure(ctx, ctx->win_count, sizeof(int) * 4 * size_t(T), st)) != RBF_OK) return s;
     int* ccount = ctx->win_count.as<int>();
     int* pcount = ccount + T;
     int* ccur = ccount + 2 * T;
     int* pcur = ccount + 3 * T;
     RBF_CUDA_TRY(cudaMemsetAsync(ccount, 0, sizeof(int) * 4 * size_t(T), st));
-    const int gb = 152 * 8;
-    k_win_items<<<gb, 256, 0, st>>>(cx, cy, nullptr, M, g, R, ccount, nullptr, nullptr, nullptr,
-                                    nullptr, nullptr, nullptr);
-    k_win_items<<<gb, 256, 0, st>>>(px, py, nullptr, N, g, 0.0, pcount, nullptr, nullptr, nullptr,
-                                    nullptr, nullptr, nullptr);
+    launch_win_items(cx, cy, nullptr, M, g, ccount, nullptr, nullptr, nullptr, nullptr, nullptr,
+                     nullptr, st);
+    launch_win_items(px, py, nullptr, N, g, pcount, nullptr, nullptr, nullptr, nullptr, nullptr,
+                     nullptr, st);
     ctx->launches += 2;
     RBF_CUDA_TRY(cudaGetLastError());
     std::vector<int> cnt(2 * size_t(T));
@@ -1816,12 +1929,14 @@ rbf_status window_bin_run(rbf_ctx* ctx, const double* cx, const double* cy, int6
         t.p0 = Ntot;
         t.N = cnt[T + w];
         t.R = R;
-        // the tile's box: the window's extended box grown by R (the domain's box on its
-        // sides; items beyond it go to the edge cells)
-        t.bbox[0] = i == 0 ? g.x0 : (win_edge(g.x0, g.x1, i, wx) - overlap) - R;
-        t.bbox[2] = i == wx - 1 ? g.x1 : (win_edge(g.x0, g.x1, i + 1, wx) + overlap) + R;
-        t.bbox[1] = j == 0 ? g.y0 : (win_edge(g.y0, g.y1, j, wy) - overlap) - R;
-        t.bbox[3] = j == wy - 1 ? g.y1 : (win_edge(g.y0, g.y1, j + 1, wy) + overlap) + R;
+        // the tile's box: the window's data box (the domain's box on its sides; items beyond
+        // it go to the edge cells)
+        const double* bx = tab.data();
+        const double* by = tab.data() + 4 * size_t(wx);
+        t.bbox[0] = i == 0 ? bbox[0] : bx[i];
+        t.bbox[2] = i == wx - 1 ? bbox[2] : bx[wx + i];
+        t.bbox[1] = j == 0 ? bbox[1] : by[j];
+        t.bbox[3] = j == wy - 1 ? bbox[3] : by[wy + j];
         Mtot += cnt[w];
         Ntot += cnt[T + w];
     }
@@ -1838,12 +1953,11 @@ rbf_status window_bin_run(rbf_ctx* ctx, const double* cx, const double* cy, int6
     double* wc = ctx->win_c.as<double>();
     double* wp = ctx->win_p.as<double>();
     const long long* doff = ctx->win_off.as<long long>();
-    k_win_items<<<gb, 256, 0, st>>>(cx, cy, nullptr, M, g, R, nullptr, doff, ccur, wc, wc + Mtot,
-                                    nullptr, ctx->win_cidx.as<long long>());
-    if (N > 0)
-        k_win_items<<<gb, 256, 0, st>>>(px, py, h, N, g, 0.0, nullptr, doff + T + 1, pcur, wp,
-                                        wp + Ntot, wp + 2 * Ntot, nullptr);
-    ctx->launches += 2;
+    launch_win_items(cx, cy, nullptr, M, g, nullptr, doff, ccur, wc, wc + Mtot, nullptr,
+                     ctx->win_cidx.as<long long>(), st);
+    launch_win_items(px, py, h, N, g, nullptr, doff + T + 1, pcur, wp, wp + Ntot, wp + 2 * Ntot,
+                     nullptr, st);
+    ctx->launches += N > 0 ? 2 : 1;
     RBF_CUDA_TRY(cudaGetLastError());
     // `off` is pageable host memory: the copy has read it by the time cudaMemcpyAsync returns
     if ((s = bin_tiles_run(ctx, tiles.data(), T, wc, wc + Mtot, Mtot, wp, wp + Ntot, wp + 2 * Ntot,
@@ -1853,7 +1967,7 @@ rbf_status window_bin_run(rbf_ctx* ctx, const double* cx, const double* cy, int6
     ctx->win_wx = wx;
     ctx->win_wy = wy;
     ctx->win_overlap = overlap;
-    ctx->win_R = R;
+    ctx->win_margin = margin;
     for (int k = 0; k < 4; ++k) ctx->win_bbox[k] = bbox[k];
     ctx->win_M = Mtot;
     ctx->win_N = Ntot;

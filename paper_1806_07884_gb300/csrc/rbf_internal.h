@@ -162,8 +162,9 @@ struct rbf_ctx {
     // ---- moving window (rbf_bin_windows): the windows are the tiles of a batch ----
     bool win_on = false;             // the batch was laid out by rbf_bin_windows
     int win_wx = 0, win_wy = 0;
-    double win_overlap = 0.0, win_R = 0.0, win_bbox[4] = {0.0, 0.0, 1.0, 1.0};
+    double win_overlap = 0.0, win_margin = 0.0, win_bbox[4] = {0.0, 0.0, 1.0, 1.0};
     int64_t win_M = 0, win_N = 0;    // centres and points summed over the windows
+    rbf_buf win_edges;               // window bounds: per axis data lo / hi, extended lo / hi
     rbf_buf win_count;               // per window: centre and point counts, scatter cursors
     rbf_buf win_off;                 // per window: first centre, first point (and the totals)
     rbf_buf win_c;                   // the windows' centres (x then y), window after window
@@ -217,7 +218,7 @@ rbf_status bench_tiles_run(rbf_ctx* ctx, int reps, bool spmv_only, cudaStream_t 
 rbf_status window_bin_run(rbf_ctx* ctx, const double* cx, const double* cy, int64_t M,
                           const double* px, const double* py, const double* h, int64_t N,
                           double R, const double* bbox, int wx, int wy, double overlap,
-                          cudaStream_t st);
+                          double margin, cudaStream_t st);
 rbf_status window_eval_run(rbf_ctx* ctx, const double* c, const double* qx, const double* qy,
                            int64_t Q, int nx, int ny, const double* box, double* f, cudaStream_t st);
 rbf_status eval_tiles_run(rbf_ctx* ctx, const double* c, const double* qx, const double* qy,

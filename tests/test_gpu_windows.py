@@ -4,10 +4,10 @@ rbf_eval_windows(_grid)) against oracle/window_oracle.py on the same seeded inpu
 Bars: window membership exact (each window's centres are the oracle's, integer); the weights
 of each window to max(1e-9, 1e-14 kappa_w) relative (kappa_w: condition number of the window's
 Jacobi-scaled B) in FP64; the blended surface at the data points and on a grid to 1e-9 (FP64)
-and 1e-6 (FP32 + FP64 refinement), or 1e-14 max_w kappa_w where that is larger: a window's
-halo holds centres whose supports reach only a sliver of its points, and on clustered data
-such windows are ill-conditioned, their surface no better determined than their weights; one
-window equals the single-system fit."""
+and 1e-6 (FP32 + FP64 refinement), or 1e-14 max_w kappa_w where that is larger (a window's
+surface is no better determined than its weights; with a margin of 0 on clustered data a
+window can be much worse conditioned than the whole domain); one window equals the
+single-system fit."""
 import numpy as np
 import pytest
 
@@ -43,24 +43,28 @@ def _kappa(P, h, C, R, kind, min_support=3):
     return float(ev[-1] / ev[0])
 
 
+# name: (problem, wx, wy, overlap / R, margin / R)
 CASES = {
-    "franke_3x2": (lambda: dg.config_franke(seed=81, N=6000, M=600), 3, 2, 2.0),
-    "terrain_2x2": (lambda: dg.config_terrain(seed=82, N=20000, M=2000), 2, 2, 4.0),
-    "uniform_3x3": (lambda: dg.config_small(83, 8000, 600), 3, 3, 1.0),
+    "franke_3x2": (lambda: dg.config_franke(seed=81, N=6000, M=600), 3, 2, 2.0, 1.0),
+    "terrain_2x3": (lambda: dg.config_terrain(seed=82, N=20000, M=2000), 2, 3, 3.0, 1.0),
+    "terrain_4x3_margin2": (lambda: dg.config_terrain(seed=86, N=20000, M=2000), 4, 3, 1.0, 2.0),
+    "uniform_3x3_no_overlap": (lambda: dg.config_small(83, 8000, 600), 3, 3, 0.0, 1.0),
+    "franke_2x2_no_margin": (lambda: dg.config_franke(seed=87, N=6000, M=600), 2, 2, 1.0, 0.0),
 }
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32_refine"])
 @pytest.mark.parametrize("case", list(CASES))
 def test_windows_match_the_oracle(case, prec):
-    make, wx, wy, d_in_R = CASES[case]
+    make, wx, wy, d_in_R, m_in_R = CASES[case]
     pb = make()
-    d = d_in_R * pb.R
+    d, m = d_in_R * pb.R, m_in_R * pb.R
     c, info, tinfo, ctx = pkg.fit_windows(pb.points, pb.h, pb.centres, pb.R, wx, wy, d,
-                                          pb.kernel, prec=prec, bbox=pb.bbox, tol=1e-14 if prec == "fp64" else 1e-12)
+                                          pb.kernel, prec=prec, bbox=pb.bbox, margin=m,
+                                          tol=1e-14 if prec == "fp64" else 1e-12)
     assert info["status"] == 0, info
-    fits = W.fit_windows(pb.points, pb.h, pb.centres, pb.R, pb.bbox, wx, wy, d, pb.kernel)
-    wins = W.windows(pb.points, pb.centres, pb.R, pb.bbox, wx, wy, d)
+    fits = W.fit_windows(pb.points, pb.h, pb.centres, pb.R, pb.bbox, wx, wy, d, m, pb.kernel)
+    wins = W.windows(pb.points, pb.centres, pb.bbox, wx, wy, d, m)
     idx = ctx.window_centres().cpu().numpy()
     cg = c.cpu().numpy()
     assert len(idx) == sum(len(ci) for ci, _ in fits)
@@ -111,10 +115,11 @@ def test_window_errors():
     args = [_dev(pb.centres[:, 0]), _dev(pb.centres[:, 1]), _dev(pb.points[:, 0]),
             _dev(pb.points[:, 1]), _dev(pb.h), pb.R]
     with pytest.raises(pkg.RBFError) as e:       # many of 100 x 100 windows hold no centre
-        ctx.bin_windows(*args, (0.0, 0.0, 1.0, 1.0), 100, 100, 0.0)
+        ctx.bin_windows(*args, (0.0, 0.0, 1.0, 1.0), 100, 100, 0.0, 0.0)
     assert "RBF_ERR_ARG" in str(e.value)
     for bad in [((0.0, 0.0, 0.0, 1.0), 2, 2, 0.1), ((0.0, 0.0, 1.0, 1.0), 0, 2, 0.1),
-                ((0.0, 0.0, 1.0, 1.0), 2, 2, -0.1), ((0.0, 0.0, 1.0, 1.0), 300, 300, 0.1)]:
+                ((0.0, 0.0, 1.0, 1.0), 2, 2, -0.1), ((0.0, 0.0, 1.0, 1.0), 300, 300, 0.1),
+                ((0.0, 0.0, 1.0, 1.0), 2, 2, 0.1, -1e-3), ((0.0, 0.0, 1.0, 1.0), 2, 2, 0.1, float("inf"))]:
         with pytest.raises(pkg.RBFError) as e:
             ctx.bin_windows(*args, *bad)
         assert "RBF_ERR_ARG" in str(e.value)
