@@ -1,5 +1,5 @@
 // Step (e): evaluate the approximant f(x) = sum_j c_j phi(||x - xi_j|| / R) (Eq. 3) at
-// query points or on a node-centred grid, one warp per query. Only the centres of the 3x3
+// query points or on a node-centred grid, a warp per 32 queries. Only the centres of the 3x3
 // cells around the query's cell can contribute (compact support, Eq. 18); they are three
 // contiguous ranges of the cell-sorted centre order. Also: export of the assembled B for
 // diagnostics.
@@ -25,109 +25,160 @@ __device__ __forceinline__ double poly_at(const double* __restrict__ k, double x
     return k ? fma(k[0], x, fma(k[1], y, k[2])) : 0.0;
 }
 
-// f at (x, y) by one warp (all 32 lanes; the result in every lane): the lanes sweep the
-// centres of the query's 3x3 cells (three contiguous ranges) with the FP32 prefilter, the
-// centres that pass are compacted into the warp's list (ballot + prefix count), and the FP64
-// distance, exact support test and Wendland value run on them a full warp at a time, so the
-// FP64 pipe sees the ~K pairs inside the support rather than every candidate of 32 queries.
+// f at 32 queries by one warp, lane l owning query l (x, y; `valid` false for a lane without
+// one): the result in the owner lane. Each lane first locates its own query (cell, cell-frame
+// FP32 coordinates), so that per-query FP64 work runs once per 32 queries. Then, query after
+// query, the lanes sweep the centres of its 3x3 cells (three contiguous ranges) with the FP32
+// prefilter and append the passing (centre, query) pairs to the warp's ring; whenever 32 pairs
+// wait, the lanes take one pair each through the FP64 distance, exact support test and
+// Wendland value, and a segmented shuffle reduction (pairs of one query are contiguous) gives
+// each query's part of the round to one lane, which adds it to the query's sum in shared
+// memory. The FP64 pipe thus sees full rounds of pairs inside the support instead of one
+// query's ~K pairs spread over two rounds, and no per-query reduction.
+constexpr int kEvalRing = 64;        // pending pairs: < 32 before an append of <= 32
+constexpr int kEvalWarps = 8;
+
+struct EvalWarpSmem {
+    int s[kEvalRing];                // centre (sorted index)
+    int q[kEvalRing];                // query lane
+    double f[32];                    // per query: the sum so far
+};
+
 template <int KIND>
-__device__ __forceinline__ double eval_warp(const Binned& bd, const double* __restrict__ c,
-                                            double x, double y, int* list, int lane) {
+__device__ __forceinline__ double eval_warp32(const Binned& bd, const double* __restrict__ c,
+                                              double x, double y, bool valid, int lane,
+                                              EvalWarpSmem& sm) {
     const Grid& g = bd.g;
-    const int ix = cell_ix(g, x), iy = cell_iy(g, y);
-    const float uq = float((x - (g.x0 + ix * g.h)) * g.invR);
-    const float vq = float((y - (g.y0 + iy * g.h)) * g.invR);
-    const int xa = max(ix - 1, 0), xb = min(ix + 1, g.gx - 1);
-    int rs[3], rl[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        const int row = iy - 1 + d;
-        if (row < 0 || row >= g.gy) {
-            rs[d] = rl[d] = 0;
-        } else {
-            rs[d] = bd.cstart[row * g.gx + xa];
-            rl[d] = bd.cstart[row * g.gx + xb + 1] - rs[d];
-        }
+    int ix = 0, iy = 0;
+    float uq = 0.0f, vq = 0.0f;
+    if (valid) {
+        ix = cell_ix(g, x);
+        iy = cell_iy(g, y);
+        uq = float((x - (g.x0 + ix * g.h)) * g.invR);
+        vq = float((y - (g.y0 + iy * g.h)) * g.invR);
+    } else {
+        x = y = 0.0;
     }
-    const int n = rl[0] + rl[1] + rl[2];
-    double f = 0.0;
-    int nl = 0;
-    // the listed centres' FP64 terms, a full warp at a time; the list then starts again (it
-    // holds kMaxCand entries: a query away from the data can see more candidates than the
-    // binning's limit, which counts only cells with points)
-    auto flush = [&]() {
+    sm.f[lane] = 0.0;
+    __syncwarp();
+    const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+    int head = 0, tail = 0;          // pending pairs [head, tail) of the ring (warp-uniform)
+
+    // one round: lane k takes pending pair head + k (k < cnt)
+    auto round = [&](int cnt) {
         __syncwarp();
-        for (int k = lane; k < nl; k += 32) {
-            const int s = list[k];
-            const double dx = x - bd.cx[s], dy = y - bd.cy[s];
+        const bool act = lane < cnt;
+        const int slot = (head + lane) & (kEvalRing - 1);
+        const int sidx = act ? sm.s[slot] : 0;
+        const int key = act ? sm.q[slot] : -1;
+        const double xq = __shfl_sync(0xffffffffu, x, key & 31);
+        const double yq = __shfl_sync(0xffffffffu, y, key & 31);
+        double t = 0.0;
+        if (act) {
+            const double dx = xq - bd.cx[sidx], dy = yq - bd.cy[sidx];
             double d2;
             if (inside_exact_d2(dx, dy, g.R, g.R2, d2)) {
                 const double r = sqrt_fast(d2) * g.invR;
-                f = fma(c[s], wendland<KIND, double>(r), f);
+                t = c[sidx] * wendland<KIND, double>(r);
             }
         }
-        __syncwarp();
-        nl = 0;
-    };
-    for (int a0 = 0; a0 < n; a0 += 32) {
-        const int a = a0 + lane;
-        bool pass = false;
-        int s = 0;
-        if (a < n) {
-            const int d = a < rl[0] ? 0 : (a < rl[0] + rl[1] ? 1 : 2);
-            s = rs[d] + (d == 0 ? a : (d == 1 ? a - rl[0] : a - rl[0] - rl[1]));
-            // the candidate in the query cell's frame (its cell is ox, oy cells away)
-            const int cc = bd.crow[s].z;
-            const float ox = float(cc % g.gx - ix), oy = float(cc / g.gx - iy);
-            const float du = uq - (bd.cu[s] + ox), dv = vq - (bd.cv[s] + oy);
-            pass = du * du + dv * dv < kPrefilterR2;
-        }
-        const unsigned bal = __ballot_sync(0xffffffffu, pass);
-        if (pass) list[nl + __popc(bal & ((1u << lane) - 1u))] = s;
-        nl += __popc(bal);
-        if (nl > kMaxCand - 32) flush();
-    }
-    flush();
+        // segmented sum towards the first lane of each query's run
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
-    return f;
+        for (int o = 1; o < 32; o <<= 1) {
+            const double tv = __shfl_down_sync(0xffffffffu, t, o);
+            const int kv = __shfl_down_sync(0xffffffffu, key, o);
+            if (lane + o < 32 && kv == key) t += tv;
+        }
+        const int kp = __shfl_up_sync(0xffffffffu, key, 1);
+        if (act && (lane == 0 || kp != key)) sm.f[key] += t;
+        head += cnt;
+        __syncwarp();
+    };
+
+    for (unsigned pend = vmask; pend; pend &= pend - 1) {
+        const int qn = __ffs(pend) - 1;
+        const int qix = __shfl_sync(0xffffffffu, ix, qn), qiy = __shfl_sync(0xffffffffu, iy, qn);
+        const float quq = __shfl_sync(0xffffffffu, uq, qn), qvq = __shfl_sync(0xffffffffu, vq, qn);
+        const int xa = max(qix - 1, 0), xb = min(qix + 1, g.gx - 1);
+        int rs[3], rl[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const int row = qiy - 1 + d;
+            if (row < 0 || row >= g.gy) {
+                rs[d] = rl[d] = 0;
+            } else {
+                rs[d] = bd.cstart[row * g.gx + xa];
+                rl[d] = bd.cstart[row * g.gx + xb + 1] - rs[d];
+            }
+        }
+        const int n = rl[0] + rl[1] + rl[2];
+        for (int a0 = 0; a0 < n; a0 += 32) {
+            const int a = a0 + lane;
+            bool pass = false;
+            int s = 0;
+            if (a < n) {
+                const int d = a < rl[0] ? 0 : (a < rl[0] + rl[1] ? 1 : 2);
+                s = rs[d] + (d == 0 ? a : (d == 1 ? a - rl[0] : a - rl[0] - rl[1]));
+                // the candidate in the query cell's frame (its cell is ox, oy cells away)
+                const int cc = bd.crow[s].z;
+                const float ox = float(cc % g.gx - qix), oy = float(cc / g.gx - qiy);
+                const float du = quq - (bd.cu[s] + ox), dv = qvq - (bd.cv[s] + oy);
+                pass = du * du + dv * dv < kPrefilterR2;
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, pass);
+            if (pass) {
+                const int slot = (tail + __popc(bal & ((1u << lane) - 1u))) & (kEvalRing - 1);
+                sm.s[slot] = s;
+                sm.q[slot] = qn;
+            }
+            tail += __popc(bal);
+            if (tail - head >= 32) round(32);
+        }
+    }
+    if (tail > head) round(tail - head);
+    return sm.f[lane];
 }
 
-constexpr int kEvalWarps = 8;
-
-// One warp per query point (persistent warps striding over the queries).
+// Persistent warps over groups of 32 query points.
 template <int KIND>
 __global__ void __launch_bounds__(kEvalWarps * 32)
     k_eval_points(Binned bd, const double* __restrict__ c, const double* __restrict__ qx,
                   const double* __restrict__ qy, int64_t Q, double* __restrict__ f,
                   const double* __restrict__ k) {
-    __shared__ int list[kEvalWarps][kMaxCand];
+    __shared__ EvalWarpSmem sm[kEvalWarps];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int64_t i = blockIdx.x * int64_t(kEvalWarps) + w; i < Q; i += int64_t(gridDim.x) * kEvalWarps) {
-        const double x = qx[i], y = qy[i];
-        const double v = eval_warp<KIND>(bd, c, x, y, list[w], lane);
-        if (lane == 0) f[i] = v + poly_at(k, x, y);
+    const int64_t groups = (Q + 31) / 32;
+    for (int64_t gi = blockIdx.x * int64_t(kEvalWarps) + w; gi < groups;
+         gi += int64_t(gridDim.x) * kEvalWarps) {
+        const int64_t i = gi * 32 + lane;
+        const bool valid = i < Q;
+        const double x = valid ? qx[i] : 0.0, y = valid ? qy[i] : 0.0;
+        const double v = eval_warp32<KIND>(bd, c, x, y, valid, lane, sm[w]);
+        if (valid) f[i] = v + poly_at(k, x, y);
     }
 }
 
 // Grid node coordinates follow an inclusive linspace: start + j * step (separately
-// rounded), the last node exactly at the end of the box.
-// One warp per grid node (persistent warps striding over the nodes, consecutive warps on
-// neighbouring nodes so their candidates stay in L1).
+// rounded), the last node exactly at the end of the box. Persistent warps over segments of
+// 32 consecutive nodes of a row (consecutive warps on neighbouring segments, so that their
+// candidates stay in L1).
 template <int KIND>
 __global__ void __launch_bounds__(kEvalWarps * 32)
     k_eval_grid(Binned bd, const double* __restrict__ c, int nx, int ny, double x0, double y0,
                 double x1, double y1, double sx, double sy, double* __restrict__ f,
                 const double* __restrict__ k) {
-    __shared__ int list[kEvalWarps][kMaxCand];
+    __shared__ EvalWarpSmem sm[kEvalWarps];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t Q = int64_t(nx) * ny;
-    for (int64_t q = blockIdx.x * int64_t(kEvalWarps) + w; q < Q; q += int64_t(gridDim.x) * kEvalWarps) {
-        const int i = int(q / nx), j = int(q % nx);
+    const int segs = (nx + 31) / 32;
+    const int64_t groups = int64_t(segs) * ny;
+    for (int64_t gi = blockIdx.x * int64_t(kEvalWarps) + w; gi < groups;
+         gi += int64_t(gridDim.x) * kEvalWarps) {
+        const int i = int(gi / segs), j = int(gi % segs) * 32 + lane;
+        const bool valid = j < nx;
         const double x = (j == nx - 1 && nx > 1) ? x1 : __dadd_rn(__dmul_rn(double(j), sx), x0);
         const double y = (i == ny - 1 && ny > 1) ? y1 : __dadd_rn(__dmul_rn(double(i), sy), y0);
-        const double v = eval_warp<KIND>(bd, c, x, y, list[w], lane);
-        if (lane == 0) f[q] = v + poly_at(k, x, y);
+        const double v = eval_warp32<KIND>(bd, c, x, y, valid, lane, sm[w]);
+        if (valid) f[int64_t(i) * nx + j] = v + poly_at(k, x, y);
     }
 }
 
@@ -179,7 +230,11 @@ __global__ void k_count_nonzero(const T* __restrict__ B, int64_t n,
 
 int eval_grid_size(int64_t Q) { return int(std::min<int64_t>((Q + 255) / 256, 152 * 32)); }
 // warps of kEvalWarps per block, one query each, persistent over the queries
-int eval_warp_grid(int64_t Q) { return int(std::min<int64_t>((Q + kEvalWarps - 1) / kEvalWarps, 152 * 8)); }
+// Blocks for Q queries: a warp per 32 of them, persistent beyond 8 blocks per SM.
+int eval_warp_grid(int64_t Q) {
+    const int64_t groups = (Q + 31) / 32;
+    return int(std::max<int64_t>(1, std::min<int64_t>((groups + kEvalWarps - 1) / kEvalWarps, 152 * 8)));
+}
 
 }  // namespace
 
