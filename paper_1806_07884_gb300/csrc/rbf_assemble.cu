@@ -157,27 +157,46 @@ __device__ void stage_candidates(const Binned& bd, const LocalCells& lc, const C
     }
 }
 
+constexpr int kFillRing = 64;   // pending (point, candidate) pairs per warp: < 32 + 32
+
 // Fill Phi[pp][a] for the points q0 .. q0+kSubChunk-1 (rows beyond p1 are zero).
 // FP64: global coordinates, support decided by the exact test; counts supports if asked.
+// ring: kFillRing ints per warp (FP64 only).
 template <int KIND, typename T>
 __device__ void fill_phi(const Binned& bd, const CandSmem<T>& cs, int n, int npad, int q0, int p1,
-                         T* phi, double* hsm, int* cnt, int* wl) {
+                         T* phi, double* hsm, int* cnt, int* ring_all) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int pp = warp; pp < kSubChunk; pp += nw) {
-        const int p = q0 + pp;
-        const bool valid = p < p1;
-        T* row = phi + pp * npad;
-        if constexpr (sizeof(T) == 8) {
-            // FP64: candidates passing the FP32 prefilter are compacted into this warp's list
-            // (ballot + prefix count) and evaluated 32 at a time, so the FP64 pipe only sees
-            // near-full warps of pairs that can lie inside the support.
-            const double xp = valid ? bd.px[p] : 1e300;
-            const double yp = valid ? bd.py[p] : 1e300;
+    if constexpr (sizeof(T) == 8) {
+        // FP64: the warp sweeps its points' candidates with the FP32 prefilter and appends the
+        // passing (point, candidate) pairs to its ring; every 32 pending pairs make one round of
+        // FP64 distances, exact tests and Wendland values, one pair per lane, so the FP64 pipe
+        // sees full warps of pairs that can lie inside the support, across the warp's points.
+        int* ring = ring_all + warp * kFillRing;
+        int head = 0, tail = 0;     // pending pairs [head, tail) (warp-uniform)
+        auto round = [&](int cntp) {
+            __syncwarp();
+            if (lane < cntp) {
+                const int e = ring[(head + lane) & (kFillRing - 1)];
+                const int pp = e >> 16, a = e & 0xffff;
+                const int p = q0 + pp;
+                const double dx = bd.px[p] - cs.x[a], dy = bd.py[p] - cs.y[a];
+                double d2;
+                if (inside_exact_d2(dx, dy, bd.g.R, bd.g.R2, d2)) {
+                    const double r = sqrt_fast(d2) * bd.g.invR;
+                    phi[pp * npad + a] = wendland<KIND, double>(r);
+                    if (cnt) atomicAdd(&cnt[a], 1);
+                }
+            }
+            head += cntp;
+            __syncwarp();
+        };
+        for (int pp = warp; pp < kSubChunk; pp += nw) {
+            const int p = q0 + pp;
+            const bool valid = p < p1;
+            T* row = phi + pp * npad;
             const float up = valid ? bd.pu[p] : 1e30f;
             const float vp = valid ? bd.pv[p] : 1e30f;
             if (lane == 0 && hsm) hsm[pp] = valid ? bd.ph[p] : 0.0;
-            int* list = wl + warp * npad;
-            int nl = 0;
             for (int a0 = 0; a0 < npad; a0 += 32) {
                 const int a = a0 + lane;
                 bool pass = false;
@@ -187,22 +206,18 @@ __device__ void fill_phi(const Binned& bd, const CandSmem<T>& cs, int n, int npa
                     pass = du * du + dv * dv < kPrefilterR2;
                 }
                 const unsigned bal = __ballot_sync(0xffffffffu, pass);
-                if (pass) list[nl + __popc(bal & ((1u << lane) - 1u))] = a;
-                nl += __popc(bal);
+                if (pass)
+                    ring[(tail + __popc(bal & ((1u << lane) - 1u))) & (kFillRing - 1)] = (pp << 16) | a;
+                tail += __popc(bal);
+                if (tail - head >= 32) round(32);
             }
-            __syncwarp();
-            for (int k = lane; k < nl; k += 32) {
-                const int a = list[k];
-                const double dx = xp - cs.x[a], dy = yp - cs.y[a];
-                double d2;
-                if (inside_exact_d2(dx, dy, bd.g.R, bd.g.R2, d2)) {
-                    const double r = sqrt_fast(d2) * bd.g.invR;
-                    row[a] = wendland<KIND, double>(r);
-                    if (cnt) atomicAdd(&cnt[a], 1);
-                }
-            }
-            __syncwarp();
-        } else {
+        }
+        if (tail > head) round(tail - head);
+    } else {
+        for (int pp = warp; pp < kSubChunk; pp += nw) {
+            const int p = q0 + pp;
+            const bool valid = p < p1;
+            T* row = phi + pp * npad;
             const float up = valid ? bd.pu[p] : 1e30f;
             const float vp = valid ? bd.pv[p] : 1e30f;
             for (int a = lane; a < npad; a += 32) {
@@ -264,7 +279,7 @@ __global__ void __launch_bounds__(kThreads) k_assemble(Binned bd, const int4* __
         cs.lv = reinterpret_cast<float*>(sp);
         sp += sizeof(float) * npad;
         wl = reinterpret_cast<int*>(sp);
-        sp += sizeof(int) * npad * (kThreads / 32);
+        sp += sizeof(int) * kFillRing * (kThreads / 32);
     } else {
         cs.lu = reinterpret_cast<float*>(cs.x);
         cs.lv = reinterpret_cast<float*>(cs.y);
@@ -432,7 +447,7 @@ __global__ void __launch_bounds__(kThreads) k_residual(Binned bd, const int4* __
     cs.lv = reinterpret_cast<float*>(sp);
     sp += sizeof(float) * npad;
     int* wl = reinterpret_cast<int*>(sp);
-    sp += sizeof(int) * npad * (kThreads / 32);
+    sp += sizeof(int) * kFillRing * (kThreads / 32);
     // stored A: per candidate its mask, nonzero count and offset in the sub-chunk's values
     unsigned int* amsk = reinterpret_cast<unsigned int*>(sp);
     sp += sizeof(unsigned int) * npad;
@@ -724,8 +739,8 @@ size_t asm_smem(int npad, bool resid) {
                sizeof(double) * kSubChunk;
     if (resid) b += sizeof(double) * npad + 3 * sizeof(int) * npad + 16;
     else b += sizeof(RowMeta) * npad;
-    if (sizeof(T) == 8)   // FP32 prefilter coordinates and the per-warp compacted lists
-        b += 2 * sizeof(float) * npad + sizeof(int) * npad * (kThreads / 32);
+    if (sizeof(T) == 8)   // FP32 prefilter coordinates and the per-warp pair rings
+        b += 2 * sizeof(float) * npad + sizeof(int) * kFillRing * (kThreads / 32);
     return b;
 }
 
