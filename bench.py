@@ -136,6 +136,9 @@ def parse():
     ap.add_argument("--host-b-mb", type=float, default=64.0,
                     help="also time one big-data step with B in host memory, assembled in "
                          "blocks of this many MB (0: skip)")
+    ap.add_argument("--inner-tol", type=float, default=1e-2,
+                    help="relative tolerance of each FP32 inner solve of the terrain fit (the "
+                         "library's default, 1e-3, suits the big-data and batched systems)")
     ap.add_argument("--windows", type=int, default=4,
                     help="also time the big-data fit as W x W moving windows (0: skip)")
     ap.add_argument("--window-overlap", type=float, default=2.0,
@@ -757,6 +760,8 @@ def main():
     fbuf = torch.empty((n, n), dtype=torch.float64, device=dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     ctx = pkg.Context(local)
+    if args.inner_tol is not None:
+        ctx.set_param("inner_tol", args.inner_tol)
     stream = torch.cuda.current_stream(dev)
 
     from paper_1806_07884_gb300 import warmstart
@@ -1063,6 +1068,7 @@ def main():
             "config": {"workload": f"terrain {N} points x {M} Halton centres, Wendland phi_3,1, "
                                    f"K=30, {n}x{n} eval grid",
                        "N": N, "M": M, "kernel": pb.kernel, "prec": args.prec, "tol": args.tol,
+                       "inner_tol": args.inner_tol if args.inner_tol is not None else 1e-3,
                        "warm_start": "learned (32-64-64-1 network, paper_1806_07884_gb300/"
                                      "warmstart_w31.npy)" if args.learned else "none",
                        "l2": "flushed before each step (512 MiB write)",
