@@ -478,9 +478,11 @@ __global__ void __launch_bounds__(kThreads) k_residual(Binned bd, const int4* __
             double* vals = astore + woff[blockIdx.x] + q * kSubChunk * n;
             unsigned int* msk = amask + moff[blockIdx.x] + q * n;
             for (int a = threadIdx.x; a < n; a += blockDim.x) {
+                // Phi is +0.0 outside the support and positive inside: an integer test of
+                // its bits keeps the mask off the FP64 pipe
                 unsigned int m = 0;
                 for (int pp = 0; pp < np; ++pp)
-                    if (phi[pp * npad + a] != 0.0) m |= 1u << pp;
+                    if (__double_as_longlong(phi[pp * npad + a]) != 0) m |= 1u << pp;
                 amsk[a] = m;
                 acnt[a] = __popc(m);
                 msk[a] = m;
