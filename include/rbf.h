@@ -21,6 +21,9 @@
  *   rbf_bin_tiles, rbf_solve_tiles
  *                  many independent tiles of uneven size binned, assembled (rbf_assemble)
  *                  and solved together, each kernel launched once for the whole batch
+ *   rbf_bin_windows, rbf_eval_windows
+ *                  the moving window (Section 7): overlapping windows of one domain fitted
+ *                  as a batch of tiles and blended by a partition of unity
  *
  * Conventions (all entry points):
  *   - Array arguments are DEVICE pointers owned by the caller unless stated
