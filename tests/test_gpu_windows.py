@@ -109,6 +109,31 @@ def test_one_window_is_the_single_system_fit():
     ctx1.close()
 
 
+def test_many_windows_use_the_per_item_atomic_path():
+    """More than 4096 windows: the items are counted and scattered with one global atomic per
+    (item, window) instead of the block-aggregated counts; membership and the surface at the
+    data points as in the parity cases (FP64)."""
+    pb = dg.config_small(88, 200000, 20000)
+    wx = wy = 65
+    d, m = 0.5 * pb.R, pb.R
+    c, info, _, ctx = pkg.fit_windows(pb.points, pb.h, pb.centres, pb.R, wx, wy, d, pb.kernel,
+                                      prec="fp64", bbox=pb.bbox, margin=m, tol=1e-13)
+    assert info["status"] == 0, info
+    wins = W.windows(pb.points, pb.centres, pb.bbox, wx, wy, d, m)
+    idx = ctx.window_centres().cpu().numpy()
+    at = 0
+    for _, ci in wins:
+        np.testing.assert_array_equal(np.sort(idx[at:at + len(ci)]), ci)
+        at += len(ci)
+    assert at == len(idx)
+    fits = W.fit_windows(pb.points, pb.h, pb.centres, pb.R, pb.bbox, wx, wy, d, m, pb.kernel)
+    Q = pb.points[::10]
+    f = ctx.eval_windows(c, _dev(Q[:, 0]), _dev(Q[:, 1])).cpu().numpy()
+    f_ref = W.evaluate_windows(fits, pb.centres, Q, pb.R, pb.bbox, wx, wy, d, pb.kernel)
+    assert O.rel_err(f, f_ref) <= 1e-8
+    ctx.close()
+
+
 def test_window_errors():
     pb = dg.config_small(85, 2000, 60, K=1.0)
     ctx = pkg.Context()
