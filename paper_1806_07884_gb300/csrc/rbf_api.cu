@@ -159,7 +159,7 @@ rbf_status rbf_destroy(rbf_ctx* ctx) {
                        &ctx->partial, &ctx->scal, &ctx->csort, &ctx->sigma, &ctx->feat,
                        &ctx->mlp_part, &ctx->astore, &ctx->amask, &ctx->woff, &ctx->wsize,
                        &ctx->pE, &ctx->pE32, &ctx->pdev, &ctx->pepart, &ctx->bblock, &ctx->bandtab,
-                       &ctx->win_edges, &ctx->win_count, &ctx->win_off, &ctx->win_c, &ctx->win_cidx, &ctx->win_p};
+                       &ctx->win_eval, &ctx->win_edges, &ctx->win_count, &ctx->win_off, &ctx->win_c, &ctx->win_cidx, &ctx->win_p};
     for (rbf_buf* b : bufs) release(ctx, *b);
     if (ctx->hpinned) cudaFreeHost(ctx->hpinned);
     if (ctx->bhost) cudaFreeHost(ctx->bhost);

@@ -35,6 +35,7 @@
 #include <vector>
 
 #include "rbf_cg.cuh"
+#include "rbf_evalpairs.cuh"
 
 namespace rbf {
 namespace {
@@ -1824,22 +1825,118 @@ __global__ void k_eval_windows(Binned bd, const TileDev* __restrict__ td, const 
 }
 
 // The node-centred nx x ny grid over box (inclusive linspace, the last node exactly at the
-// box's end), f[i nx + j].
+// box's end), f[i nx + j], window by window: a work item is a segment of 32 consecutive nodes
+// of one grid row inside one window's node range (host-computed, one node of slack; each lane
+// tests its node against the window's extended box exactly), evaluated by the pair-stream
+// engine in the window's tile frame; the weighted values are added into f with FP64 atomics
+// (f zeroed first) and k_eval_windows_finish divides by the sum of the weights.
+struct WinNodes {
+    int j0, j1, i0, i1;          // node columns [j0, j1] and rows [i0, i1] of the window
+};
+constexpr int kWinEvalWarps = 8;
+
+__device__ __forceinline__ double grid_node(int j, int n, double lo, double hi, double step) {
+    return (j == n - 1 && n > 1) ? hi : __dadd_rn(__dmul_rn(double(j), step), lo);
+}
+
 template <int KIND>
-__global__ void k_eval_windows_grid(Binned bd, const TileDev* __restrict__ td,
-                                    const double* __restrict__ c, WinGeom g, int nx, int ny,
-                                    double bx0, double by0, double bx1, double by1,
-                                    double* __restrict__ f) {
+__global__ void __launch_bounds__(kWinEvalWarps * 32)
+k_eval_windows_grid(Binned bd, const TileDev* __restrict__ td, const double* __restrict__ c,
+                    WinGeom g, const WinNodes* __restrict__ wn, const long long* __restrict__ woff,
+                    int T, int nx, int ny, double bx0, double by0, double bx1, double by1,
+                    double sx, double sy, double* __restrict__ f) {
+    __shared__ EvalWarpSmem sm[kWinEvalWarps];
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const long long total = woff[T];
+    for (long long gi = blockIdx.x * (long long)kWinEvalWarps + wp; gi < total;
+         gi += (long long)gridDim.x * kWinEvalWarps) {
+        int lo = 0, hi = T - 1;      // the window: the last with woff[win] <= gi
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (woff[mid] <= gi) lo = mid;
+            else hi = mid - 1;
+        }
+        const int win = lo;
+        const WinNodes r = wn[win];
+        const int spr = (r.j1 - r.j0 + 32) / 32;
+        const long long loc = gi - woff[win];
+        const int i = r.i0 + int(loc / spr);
+        const int j = r.j0 + int(loc % spr) * 32 + lane;
+        const int wi = win % g.wx, wj = win / g.wx;
+        bool valid = j <= r.j1;
+        double x = 0.0, y = 0.0, wt = 0.0;
+        if (valid) {
+            x = grid_node(j, nx, bx0, bx1, sx);
+            y = grid_node(i, ny, by0, by1, sy);
+            valid = win_member(x, g.tx, wi, g.wx, false) && win_member(y, g.ty, wj, g.wy, false);
+            if (valid) {
+                wt = win_axis_weight(y, g.ty, wj, g.wy, g.d) * win_axis_weight(x, g.tx, wi, g.wx, g.d);
+                valid = wt != 0.0;
+            }
+        }
+        const TileDev t = td[win];
+        EvalQuery q;
+        q.valid = valid;
+        q.x = q.y = 0.0;
+        q.ix = q.iy = 0;
+        q.uq = q.vq = 0.0f;
+        if (valid) {
+            const double xl = (x - t.x0) / t.R, yl = (y - t.y0) / t.R;
+            const int cx = tile_cell(xl, bd.g.invh, t.gx), cy = tile_cell(yl, bd.g.invh, t.gy);
+            q.x = xl;
+            q.y = yl;
+            q.ix = cx;
+            q.iy = t.oy + cy;
+            q.uq = float(xl - cx * bd.g.h);
+            q.vq = float(yl - cy * bd.g.h);
+        }
+        const EvalFrame fr{1.0, 1.0, 1.0, 0, t.gx - 1, t.oy, t.oy + t.gy - 1};
+        const double fw = eval_pairs32<KIND>(bd, c, q, fr, lane, sm[wp]);
+        if (valid) atomicAdd(&f[(long long)i * nx + j], wt * fw);
+    }
+}
+
+// f[q] /= the sum of the weights of the windows whose extended box holds node q (0 where none
+// does).
+__global__ void k_eval_windows_finish(WinGeom g, int nx, int ny, double bx0, double by0,
+                                      double bx1, double by1, double sx, double sy,
+                                      double* __restrict__ f) {
     const int64_t Q = int64_t(nx) * ny;
-    const double sx = nx > 1 ? (bx1 - bx0) / (nx - 1) : 0.0;
-    const double sy = ny > 1 ? (by1 - by0) / (ny - 1) : 0.0;
     for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < Q;
          q += int64_t(gridDim.x) * blockDim.x) {
         const int i = int(q / nx), j = int(q % nx);
-        const double x = (j == nx - 1 && nx > 1) ? bx1 : __dadd_rn(__dmul_rn(double(j), sx), bx0);
-        const double y = (i == ny - 1 && ny > 1) ? by1 : __dadd_rn(__dmul_rn(double(i), sy), by0);
-        f[q] = eval_windows_at<KIND>(bd, td, c, g, x, y);
+        const double x = grid_node(j, nx, bx0, bx1, sx), y = grid_node(i, ny, by0, by1, sy);
+        const int2 rx = win_range(x, g.x0, g.inv_cx, g.wx, g.reach_ext);
+        const int2 ry = win_range(y, g.y0, g.inv_cy, g.wy, g.reach_ext);
+        double den = 0.0;
+        for (int jj = ry.x; jj <= ry.y; ++jj) {
+            if (!win_member(y, g.ty, jj, g.wy, false)) continue;
+            const double wy = win_axis_weight(y, g.ty, jj, g.wy, g.d);
+            if (wy == 0.0) continue;
+            for (int ii = rx.x; ii <= rx.y; ++ii) {
+                if (!win_member(x, g.tx, ii, g.wx, false)) continue;
+                const double wt = wy * win_axis_weight(x, g.tx, ii, g.wx, g.d);
+                if (wt == 0.0) continue;
+                den += wt;
+            }
+        }
+        f[q] = den > 0.0 ? f[q] / den : 0.0;
     }
+}
+
+// Node range [j0, j1] of an n-node linspace from lo (step) that may lie in [a, b] (either
+// side possibly infinite), with one node of slack; j0 > j1 when none can.
+inline void node_range(double a, double b, int n, double lo, double step, int& j0, int& j1) {
+    if (n == 1 || !(step > 0.0)) {   // one node, or a degenerate or reversed box: every node
+        j0 = 0;
+        j1 = n - 1;
+        return;
+    }
+    const double u0 = std::isfinite(a) ? floor((a - lo) / step) - 1.0 : 0.0;
+    const double u1 = std::isfinite(b) ? ceil((b - lo) / step) + 1.0 : double(n - 1);
+    j0 = int(std::min(std::max(u0, 0.0), double(n - 1)));
+    j1 = int(std::min(std::max(u1, 0.0), double(n - 1)));
+    if (u1 < 0.0 || u0 > double(n - 1)) j1 = j0 - 1;
 }
 
 // The layout's geometry over its bounds table (DEVICE, 4 (wx + wy) values).
@@ -1988,17 +2085,64 @@ rbf_status window_eval_run(rbf_ctx* ctx, const double* c, const double* qx, cons
     const int64_t n = qx ? Q : int64_t(nx) * ny;
     if (n == 0) return RBF_OK;
     const int grid = int(std::min<int64_t>(div_up(n, 256), 152 * 16));
-#define EVAL_WIN(K)                                                                          \
-    if (qx) k_eval_windows<K><<<grid, 256, 0, st>>>(bd, td, cs, g, qx, qy, Q, f);             \
-    else k_eval_windows_grid<K><<<grid, 256, 0, st>>>(bd, td, cs, g, nx, ny, box[0], box[1],  \
-                                                       box[2], box[3], f);
-    switch (ctx->kernel) {
-        case RBF_W30: EVAL_WIN(0) break;
-        case RBF_W31: EVAL_WIN(1) break;
-        case RBF_W32: EVAL_WIN(2) break;
-        default: EVAL_WIN(3) break;
-    }
+    if (qx) {
+#define EVAL_WIN(K) k_eval_windows<K><<<grid, 256, 0, st>>>(bd, td, cs, g, qx, qy, Q, f);
+        switch (ctx->kernel) {
+            case RBF_W30: EVAL_WIN(0) break;
+            case RBF_W31: EVAL_WIN(1) break;
+            case RBF_W32: EVAL_WIN(2) break;
+            default: EVAL_WIN(3) break;
+        }
 #undef EVAL_WIN
+        ctx->launches += 1;
+        RBF_CUDA_TRY(cudaGetLastError());
+        return RBF_OK;
+    }
+    // the grid: per window its node ranges and first work item (host), then the windows'
+    // weighted values added into f, then the division by the weights
+    const int wx = ctx->win_wx, wy = ctx->win_wy, T = wx * wy;
+    const std::vector<double> tab = win_table(ctx->win_bbox, wx, wy, ctx->win_overlap, ctx->win_margin);
+    const double* tx = tab.data();
+    const double* ty = tab.data() + 4 * size_t(wx);
+    const double x0 = box[0], y0 = box[1], x1 = box[2], y1 = box[3];
+    const double sx = nx > 1 ? (x1 - x0) / double(nx - 1) : 0.0;
+    const double sy = ny > 1 ? (y1 - y0) / double(ny - 1) : 0.0;
+    std::vector<WinNodes> wn(T);
+    std::vector<long long> woff(size_t(T) + 1, 0);
+    for (int w = 0; w < T; ++w) {
+        const int i = w % wx, j = w / wx;
+        WinNodes& r = wn[w];
+        node_range(tx[2 * wx + i], tx[3 * wx + i], nx, x0, sx, r.j0, r.j1);
+        node_range(ty[2 * wy + j], ty[3 * wy + j], ny, y0, sy, r.i0, r.i1);
+        long long items = 0;
+        if (r.j1 >= r.j0 && r.i1 >= r.i0) items = (long long)(r.i1 - r.i0 + 1) * ((r.j1 - r.j0 + 32) / 32);
+        woff[w + 1] = woff[w] + items;
+    }
+    const size_t wn_bytes = (sizeof(WinNodes) * size_t(T) + 15) & ~size_t(15);
+    if ((s = ensure(ctx, ctx->win_eval, wn_bytes + sizeof(long long) * woff.size(), st)) != RBF_OK) return s;
+    WinNodes* dwn = reinterpret_cast<WinNodes*>(ctx->win_eval.p);
+    long long* dwoff = reinterpret_cast<long long*>(ctx->win_eval.as<char>() + wn_bytes);
+    // the host vectors are pageable: each copy has read its source when cudaMemcpyAsync returns
+    RBF_CUDA_TRY(cudaMemcpyAsync(dwn, wn.data(), sizeof(WinNodes) * size_t(T), cudaMemcpyHostToDevice, st));
+    RBF_CUDA_TRY(cudaMemcpyAsync(dwoff, woff.data(), sizeof(long long) * woff.size(),
+                                 cudaMemcpyHostToDevice, st));
+    RBF_CUDA_TRY(cudaMemsetAsync(f, 0, sizeof(double) * size_t(n), st));
+    const long long items = woff[T];
+    if (items > 0) {
+        const int eg = int(std::min<long long>((items + kWinEvalWarps - 1) / kWinEvalWarps, 152 * 8));
+#define EVAL_WG(K)                                                                               \
+    k_eval_windows_grid<K><<<eg, kWinEvalWarps * 32, 0, st>>>(bd, td, cs, g, dwn, dwoff, T, nx, ny, \
+                                                            x0, y0, x1, y1, sx, sy, f);
+        switch (ctx->kernel) {
+            case RBF_W30: EVAL_WG(0) break;
+            case RBF_W31: EVAL_WG(1) break;
+            case RBF_W32: EVAL_WG(2) break;
+            default: EVAL_WG(3) break;
+        }
+#undef EVAL_WG
+        ctx->launches += 1;
+    }
+    k_eval_windows_finish<<<grid, 256, 0, st>>>(g, nx, ny, x0, y0, x1, y1, sx, sy, f);
     ctx->launches += 1;
     RBF_CUDA_TRY(cudaGetLastError());
     return RBF_OK;

@@ -6,6 +6,7 @@
 #include <algorithm>
 
 #include "rbf_internal.h"
+#include "rbf_evalpairs.cuh"
 
 namespace rbf {
 namespace {
@@ -25,118 +26,28 @@ __device__ __forceinline__ double poly_at(const double* __restrict__ k, double x
     return k ? fma(k[0], x, fma(k[1], y, k[2])) : 0.0;
 }
 
-// f at 32 queries by one warp, lane l owning query l (x, y; `valid` false for a lane without
-// one): the result in the owner lane. Each lane first locates its own query (cell, cell-frame
-// FP32 coordinates), so that per-query FP64 work runs once per 32 queries. Then, query after
-// query, the lanes sweep the centres of its 3x3 cells (three contiguous ranges) with the FP32
-// prefilter and append the passing (centre, query) pairs to the warp's ring; whenever 32 pairs
-// wait, the lanes take one pair each through the FP64 distance, exact support test and
-// Wendland value, and a segmented shuffle reduction (pairs of one query are contiguous) gives
-// each query's part of the round to one lane, which adds it to the query's sum in shared
-// memory. The FP64 pipe thus sees full rounds of pairs inside the support instead of one
-// query's ~K pairs spread over two rounds, and no per-query reduction.
-constexpr int kEvalRing = 64;        // pending pairs: < 32 before an append of <= 32
 constexpr int kEvalWarps = 8;
 
-struct EvalWarpSmem {
-    int s[kEvalRing];                // centre (sorted index)
-    int q[kEvalRing];                // query lane
-    double f[32];                    // per query: the sum so far
-};
-
+// f at 32 queries (lane l owning query l) in the single system's frame.
 template <int KIND>
 __device__ __forceinline__ double eval_warp32(const Binned& bd, const double* __restrict__ c,
                                               double x, double y, bool valid, int lane,
                                               EvalWarpSmem& sm) {
     const Grid& g = bd.g;
-    int ix = 0, iy = 0;
-    float uq = 0.0f, vq = 0.0f;
+    EvalQuery q;
+    q.valid = valid;
+    q.x = valid ? x : 0.0;
+    q.y = valid ? y : 0.0;
+    q.ix = q.iy = 0;
+    q.uq = q.vq = 0.0f;
     if (valid) {
-        ix = cell_ix(g, x);
-        iy = cell_iy(g, y);
-        uq = float((x - (g.x0 + ix * g.h)) * g.invR);
-        vq = float((y - (g.y0 + iy * g.h)) * g.invR);
-    } else {
-        x = y = 0.0;
+        q.ix = cell_ix(g, x);
+        q.iy = cell_iy(g, y);
+        q.uq = float((x - (g.x0 + q.ix * g.h)) * g.invR);
+        q.vq = float((y - (g.y0 + q.iy * g.h)) * g.invR);
     }
-    sm.f[lane] = 0.0;
-    __syncwarp();
-    const unsigned vmask = __ballot_sync(0xffffffffu, valid);
-    int head = 0, tail = 0;          // pending pairs [head, tail) of the ring (warp-uniform)
-
-    // one round: lane k takes pending pair head + k (k < cnt)
-    auto round = [&](int cnt) {
-        __syncwarp();
-        const bool act = lane < cnt;
-        const int slot = (head + lane) & (kEvalRing - 1);
-        const int sidx = act ? sm.s[slot] : 0;
-        const int key = act ? sm.q[slot] : -1;
-        const double xq = __shfl_sync(0xffffffffu, x, key & 31);
-        const double yq = __shfl_sync(0xffffffffu, y, key & 31);
-        double t = 0.0;
-        if (act) {
-            const double dx = xq - bd.cx[sidx], dy = yq - bd.cy[sidx];
-            double d2;
-            if (inside_exact_d2(dx, dy, g.R, g.R2, d2)) {
-                const double r = sqrt_fast(d2) * g.invR;
-                t = c[sidx] * wendland<KIND, double>(r);
-            }
-        }
-        // segmented sum towards the first lane of each query's run
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const double tv = __shfl_down_sync(0xffffffffu, t, o);
-            const int kv = __shfl_down_sync(0xffffffffu, key, o);
-            if (lane + o < 32 && kv == key) t += tv;
-        }
-        const int kp = __shfl_up_sync(0xffffffffu, key, 1);
-        if (act && (lane == 0 || kp != key)) sm.f[key] += t;
-        head += cnt;
-        __syncwarp();
-    };
-
-    for (unsigned pend = vmask; pend; pend &= pend - 1) {
-        const int qn = __ffs(pend) - 1;
-        const int qix = __shfl_sync(0xffffffffu, ix, qn), qiy = __shfl_sync(0xffffffffu, iy, qn);
-        const float quq = __shfl_sync(0xffffffffu, uq, qn), qvq = __shfl_sync(0xffffffffu, vq, qn);
-        const int xa = max(qix - 1, 0), xb = min(qix + 1, g.gx - 1);
-        int rs[3], rl[3];
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            const int row = qiy - 1 + d;
-            if (row < 0 || row >= g.gy) {
-                rs[d] = rl[d] = 0;
-            } else {
-                rs[d] = bd.cstart[row * g.gx + xa];
-                rl[d] = bd.cstart[row * g.gx + xb + 1] - rs[d];
-            }
-        }
-        const int n = rl[0] + rl[1] + rl[2];
-        for (int a0 = 0; a0 < n; a0 += 32) {
-            const int a = a0 + lane;
-            bool pass = false;
-            int s = 0;
-            if (a < n) {
-                const int d = a < rl[0] ? 0 : (a < rl[0] + rl[1] ? 1 : 2);
-                s = rs[d] + (d == 0 ? a : (d == 1 ? a - rl[0] : a - rl[0] - rl[1]));
-                // the candidate in the query cell's frame (its cell is ox, oy cells away)
-                const int cc = bd.crow[s].z;
-                const float ox = float(cc % g.gx - qix), oy = float(cc / g.gx - qiy);
-                const float du = quq - (bd.cu[s] + ox), dv = qvq - (bd.cv[s] + oy);
-                pass = du * du + dv * dv < kPrefilterR2;
-            }
-            const unsigned bal = __ballot_sync(0xffffffffu, pass);
-            if (pass) {
-                const int slot = (tail + __popc(bal & ((1u << lane) - 1u))) & (kEvalRing - 1);
-                sm.s[slot] = s;
-                sm.q[slot] = qn;
-            }
-            tail += __popc(bal);
-            if (tail - head >= 32) round(32);
-        }
-    }
-    if (tail > head) round(tail - head);
-    return sm.f[lane];
+    const EvalFrame fr{g.R, g.R2, g.invR, 0, g.gx - 1, 0, g.gy - 1};
+    return eval_pairs32<KIND>(bd, c, q, fr, lane, sm);
 }
 
 // Persistent warps over groups of 32 query points.

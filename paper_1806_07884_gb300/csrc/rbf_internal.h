@@ -164,6 +164,7 @@ struct rbf_ctx {
     int win_wx = 0, win_wy = 0;
     double win_overlap = 0.0, win_margin = 0.0, win_bbox[4] = {0.0, 0.0, 1.0, 1.0};
     int64_t win_M = 0, win_N = 0;    // centres and points summed over the windows
+    rbf_buf win_eval;                // grid evaluation: per window its node ranges, item offsets
     rbf_buf win_edges;               // window bounds: per axis data lo / hi, extended lo / hi
     rbf_buf win_count;               // per window: centre and point counts, scatter cursors
     rbf_buf win_off;                 // per window: first centre, first point (and the totals)

@@ -345,7 +345,9 @@ def test_device_sqrt_against_cuda_sqrt():
 def test_stored_a_residual_matches_matrix_free(case):
     """FP32 + refinement with the stored FP64 values of A and with the matrix-free residual
     reach the oracle's surface alike (the stored values are those the matrix-free pass
-    computes)."""
+    computes). Solved to a normal residual of 1e-12: on the clustered case a residual of 1e-10
+    leaves surface errors of ~1e-6 (the system's condition number times the residual), so the
+    FP32 iterates' run-to-run rounding decided the 1e-6 bar."""
     pb = _assembly_case(case)
     c_ref, _ = O.fit(pb.points, pb.h, pb.centres, pb.R, pb.kernel, method="cholesky")
     f_ref = O.evaluate_grid(c_ref, pb.centres, pb.R, pb.kernel, 65)
@@ -355,7 +357,7 @@ def test_stored_a_residual_matches_matrix_free(case):
         C, P = pb.centres, pb.points
         ctx.bin(_dev(C[:, 0]), _dev(C[:, 1]), _dev(P[:, 0]), _dev(P[:, 1]), _dev(pb.h), pb.R, pb.bbox)
         ctx.assemble(pb.kernel, "fp32_refine")
-        c, info = ctx.solve(tol=1e-10)
+        c, info = ctx.solve(tol=1e-12)
         assert info["refinements"] >= 1
         assert O.rel_err(ctx.eval_grid(c, 65, 65).cpu().numpy(), f_ref) <= MIXED_BAR
         ctx.close()
