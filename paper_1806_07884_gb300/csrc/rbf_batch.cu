@@ -396,35 +396,81 @@ __device__ __forceinline__ double eval_tile_at(const Binned& bd, const TileDev& 
     return f;
 }
 
-// Queries of tile blockIdx.y: [qoff[t], qoff[t+1]) of qx, qy, f.
+// A query at (x, y) located in tile t's frame for the pair-stream evaluation engine: the frame
+// coordinates (x - x0_t) / R_t, the packed cell and the FP32 cell-frame coordinates.
+__device__ __forceinline__ EvalQuery tile_query(const Binned& bd, const TileDev& t, double x,
+                                                double y, bool valid) {
+    EvalQuery q;
+    q.valid = valid;
+    q.x = q.y = 0.0;
+    q.ix = q.iy = 0;
+    q.uq = q.vq = 0.0f;
+    if (valid) {
+        const double xl = (x - t.x0) / t.R, yl = (y - t.y0) / t.R;
+        const int cx = tile_cell(xl, bd.g.invh, t.gx), cy = tile_cell(yl, bd.g.invh, t.gy);
+        q.x = xl;
+        q.y = yl;
+        q.ix = cx;
+        q.iy = t.oy + cy;
+        q.uq = float(xl - cx * bd.g.h);
+        q.vq = float(yl - cy * bd.g.h);
+    }
+    return q;
+}
+// Tile t's frame: R = 1 in its coordinates, the cells of its band of the packed grid.
+__device__ __forceinline__ EvalFrame tile_frame(const TileDev& t) {
+    return EvalFrame{1.0, 1.0, 1.0, 0, t.gx - 1, t.oy, t.oy + t.gy - 1};
+}
+
+constexpr int kTileEvalWarps = 8;
+
+// Queries of tile blockIdx.y: [qoff[t], qoff[t+1]) of qx, qy, f; a warp per 32 of them.
 template <int KIND>
-__global__ void k_eval_tiles(Binned bd, const TileDev* __restrict__ td, const double* __restrict__ c,
-                             const double* __restrict__ qx, const double* __restrict__ qy,
-                             const long long* __restrict__ qoff, double* __restrict__ f) {
+__global__ void __launch_bounds__(kTileEvalWarps * 32)
+k_eval_tiles(Binned bd, const TileDev* __restrict__ td, const double* __restrict__ c,
+             const double* __restrict__ qx, const double* __restrict__ qy,
+             const long long* __restrict__ qoff, double* __restrict__ f) {
+    __shared__ EvalWarpSmem sm[kTileEvalWarps];
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     const TileDev t = td[blockIdx.y];
+    const EvalFrame fr = tile_frame(t);
     const long long q0 = qoff[blockIdx.y], q1 = qoff[blockIdx.y + 1];
-    for (long long q = q0 + blockIdx.x * (long long)blockDim.x + threadIdx.x; q < q1;
-         q += (long long)gridDim.x * blockDim.x)
-        f[q] = eval_tile_at<KIND>(bd, t, c, qx[q], qy[q]);
+    for (long long g0 = q0 + (blockIdx.x * (long long)kTileEvalWarps + wp) * 32; g0 < q1;
+         g0 += (long long)gridDim.x * kTileEvalWarps * 32) {
+        const long long q = g0 + lane;
+        const bool valid = q < q1;
+        const EvalQuery e = tile_query(bd, t, valid ? qx[q] : 0.0, valid ? qy[q] : 0.0, valid);
+        const double v = eval_pairs32<KIND>(bd, c, e, fr, lane, sm[wp]);
+        if (valid) f[q] = v;
+    }
 }
 
 // The nx x ny node grid over each tile's own box (inclusive linspace, last node exactly at the
-// box's end), tile t's values at f[t nx ny + i nx + j].
+// box's end), tile t's values at f[t nx ny + i nx + j]; a warp per 32 nodes.
 template <int KIND>
-__global__ void k_eval_tiles_grid(Binned bd, const TileDev* __restrict__ td,
-                                  const double* __restrict__ c, int nx, int ny,
-                                  double* __restrict__ f) {
+__global__ void __launch_bounds__(kTileEvalWarps * 32)
+k_eval_tiles_grid(Binned bd, const TileDev* __restrict__ td, const double* __restrict__ c,
+                  int nx, int ny, double* __restrict__ f) {
+    __shared__ EvalWarpSmem sm[kTileEvalWarps];
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     const TileDev t = td[blockIdx.y];
+    const EvalFrame fr = tile_frame(t);
     const long long Q = (long long)nx * ny;
     const double sx = nx > 1 ? (t.x1 - t.x0) / (nx - 1) : 0.0;
     const double sy = ny > 1 ? (t.y1 - t.y0) / (ny - 1) : 0.0;
     double* ft = f + (long long)blockIdx.y * Q;
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < Q;
-         q += (long long)gridDim.x * blockDim.x) {
-        const int i = int(q / nx), j = int(q % nx);
-        const double x = (j == nx - 1 && nx > 1) ? t.x1 : __dadd_rn(__dmul_rn(double(j), sx), t.x0);
-        const double y = (i == ny - 1 && ny > 1) ? t.y1 : __dadd_rn(__dmul_rn(double(i), sy), t.y0);
-        ft[q] = eval_tile_at<KIND>(bd, t, c, x, y);
+    for (long long g0 = (blockIdx.x * (long long)kTileEvalWarps + wp) * 32; g0 < Q;
+         g0 += (long long)gridDim.x * kTileEvalWarps * 32) {
+        const long long q = g0 + lane;
+        const bool valid = q < Q;
+        double x = 0.0, y = 0.0;
+        if (valid) {
+            const int i = int(q / nx), j = int(q % nx);
+            x = (j == nx - 1 && nx > 1) ? t.x1 : __dadd_rn(__dmul_rn(double(j), sx), t.x0);
+            y = (i == ny - 1 && ny > 1) ? t.y1 : __dadd_rn(__dmul_rn(double(i), sy), t.y0);
+        }
+        const double v = eval_pairs32<KIND>(bd, c, tile_query(bd, t, x, y, valid), fr, lane, sm[wp]);
+        if (valid) ft[q] = v;
     }
 }
 
@@ -1875,23 +1921,8 @@ k_eval_windows_grid(Binned bd, const TileDev* __restrict__ td, const double* __r
             }
         }
         const TileDev t = td[win];
-        EvalQuery q;
-        q.valid = valid;
-        q.x = q.y = 0.0;
-        q.ix = q.iy = 0;
-        q.uq = q.vq = 0.0f;
-        if (valid) {
-            const double xl = (x - t.x0) / t.R, yl = (y - t.y0) / t.R;
-            const int cx = tile_cell(xl, bd.g.invh, t.gx), cy = tile_cell(yl, bd.g.invh, t.gy);
-            q.x = xl;
-            q.y = yl;
-            q.ix = cx;
-            q.iy = t.oy + cy;
-            q.uq = float(xl - cx * bd.g.h);
-            q.vq = float(yl - cy * bd.g.h);
-        }
-        const EvalFrame fr{1.0, 1.0, 1.0, 0, t.gx - 1, t.oy, t.oy + t.gy - 1};
-        const double fw = eval_pairs32<KIND>(bd, c, q, fr, lane, sm[wp]);
+        const double fw = eval_pairs32<KIND>(bd, c, tile_query(bd, t, x, y, valid), tile_frame(t),
+                                             lane, sm[wp]);
         if (valid) atomicAdd(&f[(long long)i * nx + j], wt * fw);
     }
 }
