@@ -139,6 +139,9 @@ def parse():
     ap.add_argument("--inner-tol", type=float, default=1e-2,
                     help="relative tolerance of each FP32 inner solve of the terrain fit (the "
                          "library's default, 1e-3, suits the big-data and batched systems)")
+    ap.add_argument("--tiles-inner-tol", type=float, default=None,
+                    help="relative tolerance of each FP32 inner solve of the batched tiles "
+                         "(default: the library's, 1e-3)")
     ap.add_argument("--windows", type=int, default=4,
                     help="also time the big-data fit as W x W moving windows (0: skip)")
     ap.add_argument("--window-overlap", type=float, default=2.0,
@@ -369,6 +372,8 @@ def bench_batched(args, rank, dev, stream, flush, hbm, peak_source):
     Ntot, Mtot = int(px.size), int(cx.size)
     cbuf = torch.empty(Mtot, dtype=torch.float64, device=dev)
     ctx = pkg.Context(dev.index)
+    if args.tiles_inner_tol is not None:
+        ctx.set_param("inner_tol", args.tiles_inner_tol)
 
     def step(prec, tol):
         ctx.bin_tiles(tiles, *d)
@@ -469,7 +474,8 @@ def bench_batched(args, rank, dev, stream, flush, hbm, peak_source):
                        f"Wendland phi_3,1, K=30, sum N = {Ntot}, sum M = {Mtot}",
            "value": Ntot / (ms * 1e-3), "unit": "points/s", "ms_per_step": round(ms, 3),
            "step_ms": timed.step_ms,
-           "prec": args.prec, "tol": args.tol, "gpu_launches_per_step": launches,
+           "prec": args.prec, "tol": args.tol, "inner_tol": args.tiles_inner_tol or 1e-3,
+           "gpu_launches_per_step": launches,
            "iterations_max": info["iterations"], "refinements_max": info["refinements"],
            "iterations_mean": round(float(np.mean([t["iterations"] for t in tinfo])), 1),
            "all_converged": all(t["status"] == 0 for t in tinfo), "promoted": info["promoted"],
