@@ -418,7 +418,10 @@ rbf_status rbf_eval_windows(rbf_ctx* ctx, const double* c, const double* qx, con
                             int64_t Q, double* f, void* stream);
 
 /* The same on the node-centred nx x ny grid over box (HOST {x0, y0, x1, y1}); f[i nx + j]
- * (DEVICE, nx ny values). Asynchronous. */
+ * (DEVICE, nx ny values). Each window's node range is computed on the host and copied from
+ * pageable memory, which waits for the work already queued on `stream`; the evaluation itself
+ * is queued asynchronously. The windows' values are summed into f with atomics, so repeated
+ * calls agree up to the order of FP additions. */
 rbf_status rbf_eval_windows_grid(rbf_ctx* ctx, const double* c, int nx, int ny, const double* box,
                                  double* f, void* stream);
 
